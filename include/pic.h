@@ -1,0 +1,234 @@
+/*
+ * pic.h -- C ABI of the GB300 energy-conserving PIC/MCC library (libpic.so).
+ *
+ * The library advances the 1D electrostatic particle-in-cell / Monte Carlo
+ * collision model of Wang, Sun, Jiang & Kong ("On the energy conservation
+ * electrostatic PIC/MC simulating: benchmark and application to the radio
+ * frequency discharges"): a planar gap between an RF-driven and a grounded
+ * electrode filled with electrons and ions (Sec. 3), charge assignment by the
+ * quadratic spline S_2 (Eq. 2), force interpolation by S_1 from cell-centred
+ * fields (Eq. 3), explicit leapfrog or direct-implicit push (Sec. 2, schemes
+ * (1)-(4)), absorbing electrodes and null-collision Monte Carlo with
+ * ionisation (Sec. 3).
+ *
+ * Conventions for every entry point:
+ *  - Return value: PIC_OK (0) on success, a negative PIC_E* code otherwise;
+ *    pic_last_error() then holds a one-line message.  Nothing is partially
+ *    applied when validation fails.
+ *  - Device memory is owned by the caller: pic_required_sizes() states how
+ *    many bytes the library needs; the caller allocates one device buffer
+ *    (the "arena", 256-byte aligned, e.g. a torch uint8 tensor) and passes it
+ *    to pic_init().  The handle keeps the pointer and never frees it; the
+ *    arena must outlive the handle.  The library allocates no device memory.
+ *  - Work is enqueued on the CUDA stream given to pic_init() (a cudaStream_t
+ *    passed as void*, NULL = legacy default stream).  pic_step() is
+ *    asynchronous; calls that return data to the host synchronise that
+ *    stream first.
+ *  - Host buffers passed in or out are owned by the caller and only read or
+ *    written during the call.
+ *  - A handle is not thread-safe; separate handles on separate streams are
+ *    independent.
+ *  - The device keeps a sticky status word (particle or birth capacity
+ *    exceeded, collision bound exceeded).  It is read by pic_status() and
+ *    pic_diag().
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_ABI_VERSION 1
+
+/* Error codes. */
+#define PIC_OK 0
+#define PIC_EINVAL (-1)     /* invalid argument or configuration */
+#define PIC_EUNSTABLE (-2)  /* strict mode: omega_p dt >= 2, Eq. (1) leapfrog limit */
+#define PIC_ENOMEM (-3)     /* arena too small or misaligned */
+#define PIC_EOVERFLOW (-4)  /* particle / birth capacity or fixed-point headroom exceeded */
+#define PIC_ECUDA (-5)      /* a CUDA call failed; message in pic_last_error */
+#define PIC_ETIMEOUT (-6)   /* a bounded device-side wait gave up */
+
+/* Device status bits (pic_diag_t.status, pic_status). */
+#define PIC_STATUS_CAPACITY 0x1u    /* particles dropped: slot capacity exhausted */
+#define PIC_STATUS_BIRTHS 0x2u      /* births dropped: per-step birth buffer full */
+#define PIC_STATUS_TIMEOUT 0x4u     /* a bounded wait ran out (batched driver) */
+
+/* Schemes (Sec. 2): (2) EC explicit, (1) momentum-conserving explicit, (4) EC
+   direct implicit. */
+#define PIC_EC_EXPLICIT 0
+#define PIC_MC_EXPLICIT 1
+#define PIC_EC_IMPLICIT 2
+
+/* Boundaries: electrodes at x=0 (driven, V(t) = rf_volt sin(2 pi rf_freq t))
+   and x=L (grounded), both absorbing (Sec. 3); or a periodic box. */
+#define PIC_BC_ELECTRODES 0
+#define PIC_BC_PERIODIC 1
+
+typedef struct pic_config {
+    int32_t scheme;          /* PIC_EC_EXPLICIT / PIC_MC_EXPLICIT / PIC_EC_IMPLICIT */
+    int32_t boundary;        /* PIC_BC_ELECTRODES / PIC_BC_PERIODIC */
+    int32_t n_cells;         /* 2 .. 1024 */
+    int32_t mcc;             /* 1: null-collision Monte Carlo on */
+    int32_t ions_mobile;     /* 0: no ion particles; frozen uniform ion density bg_density */
+    int32_t strict;          /* 1: reject explicit runs with omega_p dt >= 2 (Eq. 1) */
+    int32_t sort_period;     /* steps between counting sorts of the particles (0: never) */
+    int32_t diag_period;     /* heating profile / EEDF sampled every diag_period steps (0: never) */
+    int32_t eedf_bins;       /* EEDF bins over [0, eedf_max_ev), plus one overflow bin */
+    uint32_t seed;           /* Philox key word 0 */
+    uint32_t run;            /* Philox key word 1 (run index in a batch) */
+    int32_t reserved0;
+    int64_t np_init;         /* macro-particles per species placed by pic_init (uniform load) */
+    int64_t capacity[2];     /* particle slots per species (electrons, ions) */
+    int64_t births_capacity; /* ionisation events one step can record */
+    double length;           /* gap [m] */
+    double dt;               /* time step [s] */
+    double rf_freq;          /* [Hz] */
+    double rf_volt;          /* amplitude [V] */
+    double n0;               /* density represented by np_init macro-particles [m^-3] */
+    double bg_density;       /* frozen ion density [m^-3] when ions_mobile == 0 */
+    double te_ev, ti_ev;     /* load temperatures [eV] */
+    double ion_mass_amu;
+    double pressure_mtorr;   /* neutral gas pressure */
+    double gas_temp;         /* neutral gas temperature [K] */
+    double sig_el;           /* e- elastic, constant [m^2] */
+    double exc_thr;          /* excitation threshold [eV] */
+    double exc_ramp_end;     /* energy at which excitation reaches its maximum [eV] */
+    double sig_exc_max;      /* [m^2] */
+    double iz_thr;           /* ionisation threshold I [eV] */
+    double sig_iz_peak;      /* ionisation peak value (at e*I) [m^2] */
+    double sig_cx;           /* ion charge exchange, constant [m^2] */
+    double eps_cap;          /* e- energy up to which the collision bound holds [eV] */
+    double cx_vmax;          /* ion energy up to which the charge-exchange bound holds [V] */
+    double eedf_max_ev;
+} pic_config;
+
+typedef struct pic_sizes {
+    size_t arena_bytes;      /* device bytes pic_init needs */
+    size_t snapshot_bytes;   /* host bytes pic_save writes */
+} pic_sizes;
+
+typedef struct pic_buffers {
+    void *arena;             /* device pointer, 256-byte aligned */
+    size_t arena_bytes;
+} pic_buffers;
+
+/* One species' particles in the device storage form: cell index, offset in
+   [0,1) within the cell (position x = (cell + off) * dx), velocity [m/s],
+   id, and the implicit push's time-averaged acceleration abar [m/s^2]
+   (may be NULL: zero).  Host arrays of length count. */
+typedef struct pic_host_particles {
+    int64_t count;
+    int32_t *cell;
+    float *off;
+    float *vx, *vy, *vz;
+    uint32_t *id;
+    float *abar;
+    uint32_t next_id;        /* set: first id given to particles born later; get: current */
+} pic_host_particles;
+
+typedef struct pic_diag_t {
+    int64_t step;
+    int64_t count[2];                 /* live particles per species */
+    uint64_t wall_count[2][2];        /* [species][0: x=0 electrode, 1: x=L electrode] */
+    double wall_energy_ev[2][2];      /* summed kinetic energy of absorbed particles [eV] */
+    uint64_t coll[5];                 /* elastic, excitation, ionisation, charge exchange, null */
+    uint64_t overflow[2];             /* selected particles above the collision bound */
+    uint64_t births;
+    double ke_x[2];                   /* time-centred x kinetic energy of the last step [J/m^2] */
+    double ke_perp[2];                /* current (vy,vz) kinetic energy [J/m^2] */
+    double field_energy;              /* 1/2 eps0 sum E^2 dx of the current field [J/m^2] */
+    double field_energy_push;         /* the same for the field the last push used */
+    double power[2];                  /* sum_p q w E v of the last step [W/m^2] */
+    int64_t n_avg;                    /* steps in the running time averages */
+    int64_t n_diag;                   /* samples in the heating profile / EEDF */
+    uint32_t status;                  /* PIC_STATUS_* bits */
+    uint32_t reserved;
+} pic_diag_t;
+
+typedef struct pic_handle pic_handle;
+
+/* Library version (PIC_ABI_VERSION) and a build description string. */
+int pic_version(void);
+const char *pic_build_info(void);
+
+/* Bytes of device memory (arena) and host snapshot a configuration needs.
+   Validates the configuration (Eq. (1) in strict mode, capacities,
+   fixed-point headroom: capacity < 2^30 per species). */
+int pic_required_sizes(const pic_config *cfg, pic_sizes *out);
+
+/* Create a run in caller-owned device memory and place np_init electrons and
+   ions uniformly between the electrodes with Maxwellian velocities (Sec. 3:
+   uniform initial plasma), ids 0..np_init-1, then assign charge and solve for
+   the t = 0 field (and abar = a^0 for the implicit scheme).  stream: a
+   cudaStream_t as void* (NULL = default stream). */
+int pic_init(const pic_config *cfg, const pic_buffers *bufs, void *stream, pic_handle **out);
+
+/* Enqueue n steps (Sec. 2: gather, push, absorb, collide, assign charge,
+   solve) on the handle's stream.  Asynchronous. */
+int pic_step(pic_handle *h, int64_t n);
+
+/* Synchronise and read the diagnostics.  reset_avg != 0 clears the running
+   time averages (densities, potential, heating, EEDF) after reading. */
+int pic_diag(pic_handle *h, pic_diag_t *out, int reset_avg);
+
+/* Time-averaged profiles since the last reset, each may be NULL:
+   ne, ni, phi [n_cells+1] at the nodes; heat_e, heat_i [n_cells] power
+   density J.E [W/m^3] per cell; eedf [eedf_bins+1] counts. */
+int pic_profiles(pic_handle *h, double *ne, double *ni, double *phi, double *heat_e,
+                 double *heat_i, uint64_t *eedf);
+
+/* Current grid state, each may be NULL: rho_q_e, rho_q_i [n_cells+1] charge
+   assigned per node in units of 2^-33 macro-particle charges (int64, exact);
+   phi [n_cells+1]; e_cc [n_cells] cell-centred field; chi [n_cells]
+   susceptibility of the last implicit field solve. */
+int pic_grids(pic_handle *h, int64_t *rho_q_e, int64_t *rho_q_i, double *phi, double *e_cc,
+              double *chi);
+
+/* Live particle counts per species (synchronises). */
+int pic_count(pic_handle *h, int64_t *n_e, int64_t *n_i);
+
+/* Copy one species' live particles to host arrays of length out->count
+   (at least the live count); out->count is set to the number written. */
+int pic_get_particles(pic_handle *h, int species, pic_host_particles *out);
+
+/* Replace one species' particles by host arrays (count <= capacity).  The
+   field is not recomputed: call pic_init_field() after setting both species. */
+int pic_set_particles(pic_handle *h, int species, const pic_host_particles *in);
+
+/* Assign charge for the current particles and solve for the field at the
+   current time level; set_abar != 0 also sets abar = (q/m) E(x) for the
+   implicit scheme. */
+int pic_init_field(pic_handle *h, int set_abar);
+
+/* Set the step counter (time level n: V(t_n), Philox counter). */
+int pic_set_step(pic_handle *h, int64_t step);
+
+/* Synchronise and return the device status word (PIC_STATUS_* bits). */
+int pic_status(pic_handle *h, uint32_t *status);
+
+/* Snapshot the whole run state into a host buffer of snapshot_bytes, and
+   restore it.  Philox streams are keyed on (id, step), so a restored run
+   continues exactly as the original would have. */
+int pic_save(pic_handle *h, void *host_buf, size_t nbytes);
+int pic_load(pic_handle *h, const void *host_buf, size_t nbytes);
+
+/* Fill a device buffer with n Philox4x32-10 blocks: key (k0, k1), counter
+   (c0 + i, c1, c2, c3) for block i; out receives 4n uint32 words. */
+int pic_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
+                    uint32_t c3, int64_t n, uint32_t *out_device, void *stream);
+
+void pic_free(pic_handle *h);
+
+/* Message of the last failing call on h (h may be NULL for pic_init /
+   pic_required_sizes failures). */
+const char *pic_last_error(const pic_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,685 @@
+// pic_capi.cu -- host runtime of libpic.so: configuration checks, layout of
+// the caller-owned arena, derived constants, launch sequencing and CUDA-graph
+// replay of whole sort cycles.  Implements include/pic.h.
+#include "pic.h"
+#include "pic_internal.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace pic;
+
+namespace {
+
+// CODATA 2018.
+constexpr double kE = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kAmu = 1.66053906660e-27;
+constexpr double kKb = 1.380649e-23;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kEulerN = 2.71828182845904523536;
+constexpr double kTorrPa = 101325.0 / 760.0;
+
+thread_local std::string g_error;
+
+struct Layout {
+    size_t state;
+    size_t sp[2][2][7];  // [parity][species][field] offsets (cell, off, vx, vy, vz, id, abar)
+    size_t acc_cnt[2], acc_a[2], acc_b[2], cursor[2], rho_q[2];
+    size_t e_gather, e_cc, phi, chi, avg_ne, avg_ni, avg_phi, heat[2], eedf, births;
+    size_t total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+Layout make_layout(const pic_config &c) {
+    Layout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    const size_t n1 = (size_t)c.n_cells + 1;
+    L.state = take(sizeof(DevState));
+    for (int p = 0; p < 2; ++p)
+        for (int s = 0; s < 2; ++s) {
+            const size_t cap = (size_t)c.capacity[s];
+            for (int f = 0; f < 6; ++f) L.sp[p][s][f] = take(4 * cap);
+            L.sp[p][s][6] = c.scheme == PIC_EC_IMPLICIT ? take(4 * cap) : 0;
+        }
+    for (int s = 0; s < 2; ++s) {
+        L.acc_cnt[s] = take(8 * n1);
+        L.acc_a[s] = take(8 * n1);
+        L.acc_b[s] = take(8 * n1);
+        L.cursor[s] = take(4 * n1);
+        L.rho_q[s] = take(8 * n1);
+    }
+    L.e_gather = take(4 * (n1 + 1));
+    L.e_cc = take(8 * n1);
+    L.phi = take(8 * n1);
+    L.chi = take(8 * n1);
+    L.avg_ne = take(8 * n1);
+    L.avg_ni = take(8 * n1);
+    L.avg_phi = take(8 * n1);
+    L.heat[0] = take(8 * n1);
+    L.heat[1] = take(8 * n1);
+    L.eedf = take(8 * ((size_t)c.eedf_bins + 1));
+    const size_t nb = (size_t)(c.births_capacity > 0 ? c.births_capacity : 1);
+    L.births = take(sizeof(Birth) * nb + 4 * nb);
+    L.total = o;
+    return L;
+}
+
+double gas_density(const pic_config &c) {
+    return c.pressure_mtorr * 1e-3 * kTorrPa / (kKb * c.gas_temp);
+}
+
+double sig_exc(const pic_config &c, double eps) {
+    if (eps < c.exc_thr) return 0.0;
+    if (eps < c.exc_ramp_end) return c.sig_exc_max * (eps - c.exc_thr) / (c.exc_ramp_end - c.exc_thr);
+    return c.sig_exc_max;
+}
+
+double sig_iz(const pic_config &c, double eps) {
+    if (eps <= c.iz_thr) return 0.0;
+    return c.sig_iz_peak * kEulerN * (c.iz_thr / eps) * std::log(eps / c.iz_thr);
+}
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return code;
+}
+
+int validate(const pic_config *c) {
+    if (!c) return fail(PIC_EINVAL, "config is NULL");
+    if (c->scheme < 0 || c->scheme > 2) return fail(PIC_EINVAL, "unknown scheme %d", c->scheme);
+    if (c->boundary != PIC_BC_ELECTRODES && c->boundary != PIC_BC_PERIODIC)
+        return fail(PIC_EINVAL, "unknown boundary %d", c->boundary);
+    if (c->n_cells < 2 || c->n_cells > kMaxCells)
+        return fail(PIC_EINVAL, "n_cells %d outside 2..%d", c->n_cells, kMaxCells);
+    if (!(c->length > 0) || !(c->dt > 0)) return fail(PIC_EINVAL, "length and dt must be positive");
+    if (c->np_init < 1) return fail(PIC_EINVAL, "np_init must be >= 1 (it sets the macro weight)");
+    if (!(c->n0 > 0)) return fail(PIC_EINVAL, "n0 must be positive");
+    for (int s = 0; s < 2; ++s) {
+        if (c->capacity[s] < 1 || c->capacity[s] >= (1ll << 29))
+            return fail(PIC_EOVERFLOW, "capacity[%d] = %lld outside 1..2^29-1 (int64 charge headroom)",
+                        s, (long long)c->capacity[s]);
+        if (c->capacity[s] < c->np_init && (s == 0 || c->ions_mobile))
+            return fail(PIC_EINVAL, "capacity[%d] below np_init", s);
+    }
+    if (c->mcc && !c->ions_mobile) return fail(PIC_EINVAL, "collisions need mobile ions");
+    if (c->mcc && c->births_capacity < 1) return fail(PIC_EINVAL, "births_capacity must be >= 1");
+    if (c->births_capacity < 0 || c->births_capacity > (1ll << 24))
+        return fail(PIC_EINVAL, "births_capacity outside 0..2^24");
+    if (c->eedf_bins < 1 || c->eedf_bins > 1024) return fail(PIC_EINVAL, "eedf_bins outside 1..1024");
+    if (!(c->eedf_max_ev > 0)) return fail(PIC_EINVAL, "eedf_max_ev must be positive");
+    if (!(c->ion_mass_amu > 0) || !(c->te_ev >= 0) || !(c->ti_ev >= 0))
+        return fail(PIC_EINVAL, "bad species parameters");
+    if (c->mcc && (!(c->gas_temp > 0) || !(c->pressure_mtorr >= 0) || !(c->eps_cap > 0) ||
+                   c->exc_ramp_end <= c->exc_thr || !(c->iz_thr > 0)))
+        return fail(PIC_EINVAL, "bad collision parameters");
+    if (c->sort_period < 0 || c->diag_period < 0) return fail(PIC_EINVAL, "negative period");
+    // Eq. (1): the leapfrog push is stable only for omega_p dt < 2.
+    const double wp = std::sqrt(c->n0 * kE * kE / (kEps0 * kMe));
+    if (c->strict && c->scheme != PIC_EC_IMPLICIT && !(wp * c->dt < 2.0))
+        return fail(PIC_EUNSTABLE, "omega_p dt = %.3f >= 2 violates the leapfrog limit of Eq. (1)",
+                    wp * c->dt);
+    return PIC_OK;
+}
+
+struct Snapshot {
+    uint64_t magic;
+    uint64_t version;
+    uint64_t arena_bytes;
+    int64_t host_step;
+};
+constexpr uint64_t kSnapMagic = 0x3150434950434547ull;
+
+}  // namespace
+
+struct pic_handle {
+    pic_config cfg;
+    Layout layout;
+    Run run;
+    unsigned char *arena;
+    size_t arena_bytes;
+    cudaStream_t stream;
+    cudaStream_t capture_stream;
+    int grid_push;
+    int grid_sort;
+    long long host_step;
+    std::string err;
+    cudaGraphExec_t cycle_graph;
+    int cycle_len;
+};
+
+namespace {
+
+int cuda_fail(pic_handle *h, cudaError_t e, const char *what) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    g_error = buf;
+    if (h) h->err = buf;
+    return PIC_ECUDA;
+}
+
+#define CK(h, call)                                              \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+void derive(pic_handle *h) {
+    const pic_config &c = h->cfg;
+    Run &R = h->run;
+    std::memset(&R, 0, sizeof R);
+    R.n_cells = c.n_cells;
+    R.periodic = c.boundary == PIC_BC_PERIODIC;
+    R.scheme = c.scheme;
+    R.mcc = c.mcc;
+    R.ions_mobile = c.ions_mobile;
+    R.diag_period = c.diag_period;
+    R.eedf_bins = c.eedf_bins;
+    R.sort_period = c.sort_period;
+    R.seed = c.seed;
+    R.run = c.run;
+    R.capacity[0] = c.capacity[0];
+    R.capacity[1] = c.capacity[1];
+    R.births_cap = c.births_capacity > 0 ? c.births_capacity : 1;
+    const double dx = c.length / c.n_cells;
+    const double w = c.n0 * c.length / (double)c.np_init;
+    const double q[2] = {-kE, kE};
+    const double m[2] = {kMe, c.ion_mass_amu * kAmu};
+    R.dx = dx;
+    R.dt = c.dt;
+    R.rf_freq = c.rf_freq;
+    R.rf_volt = R.periodic ? 0.0 : c.rf_volt;
+    R.weight = w;
+    const double two_m33 = std::ldexp(1.0, -33);
+    R.kappa = kE * w * two_m33 / kEps0;
+    R.kappa_bg = c.ions_mobile ? 0.0 : dx * kE * c.bg_density / kEps0;
+    R.dens_scale = w * two_m33 / dx;
+    R.eps0_dx_half = 0.5 * kEps0 * dx;
+    for (int s = 0; s < 2; ++s) {
+        R.chi_coef[s] = 0.5 * c.dt * c.dt * q[s] * q[s] * w / (m[s] * kEps0 * dx) * std::ldexp(1.0, -16);
+        R.half_m_w[s] = 0.5 * m[s] * w;
+        R.qm_dt[s] = (float)(q[s] / m[s] * c.dt);
+        R.qm[s] = (float)(q[s] / m[s]);
+        R.qw[s] = (float)(q[s] * w);
+        R.half_m_over_e[s] = (float)(0.5 * m[s] / kE);
+    }
+    R.dt_dx = (float)(c.dt / dx);
+    R.half_dt = (float)(0.5 * c.dt);
+    R.half_dt2_dx = (float)(0.5 * c.dt * c.dt / dx);
+    R.abar_ion_over_e = (float)((kE / m[1]) / (-kE / kMe));
+    R.eedf_inv_width = (float)(c.eedf_bins / c.eedf_max_ev);
+    // Null-collision bounds (Vahedi & Surendra): per process the maximum of
+    // n_g sigma v up to the cap energy; sigma_iz v peaks where ln(eps/I) = 2.
+    const double ng = gas_density(c);
+    const double vth_gas = std::sqrt(kKb * c.gas_temp / m[1]);
+    R.n_g = (float)ng;
+    R.vth_gas = (float)vth_gas;
+    if (c.mcc) {
+        const double v_cap = std::sqrt(2.0 * kE * c.eps_cap / kMe);
+        const double eps_star = std::fmin(c.eps_cap, c.iz_thr * kEulerN * kEulerN);
+        const double v_star = std::sqrt(2.0 * kE * eps_star / kMe);
+        const double nu_e = ng * (c.sig_el * v_cap + sig_exc(c, c.eps_cap) * v_cap + sig_iz(c, eps_star) * v_star);
+        const double g_max = std::sqrt(2.0 * kE * c.cx_vmax / m[1]) + 6.0 * vth_gas;
+        const double nu_i = ng * c.sig_cx * g_max;
+        const double p_e = 1.0 - std::exp(-nu_e * c.dt);
+        const double p_i = 1.0 - std::exp(-nu_i * c.dt);
+        R.thr[0] = (uint32_t)std::floor(p_e * 16777216.0);
+        R.thr[1] = (uint32_t)std::floor(p_i * 16777216.0);
+        R.nu_max_e = (float)nu_e;
+        R.nu_max_i = (float)nu_i;
+        R.g_max_i = (float)g_max;
+    }
+    R.sig_el = (float)c.sig_el;
+    R.exc_thr = (float)c.exc_thr;
+    R.exc_ramp_end = (float)c.exc_ramp_end;
+    R.exc_slope = (float)(c.sig_exc_max / (c.exc_ramp_end - c.exc_thr));
+    R.sig_exc_max = (float)c.sig_exc_max;
+    R.iz_thr = (float)c.iz_thr;
+    R.sig_iz_k = (float)(c.sig_iz_peak * kEulerN);
+    R.sig_cx = (float)c.sig_cx;
+    R.eps_cap = (float)c.eps_cap;
+    R.two_m_over_M = (float)(2.0 * kMe / m[1]);
+    R.two_e_over_me = (float)(2.0 * kE / kMe);
+    // pointers
+    unsigned char *A = h->arena;
+    const Layout &L = h->layout;
+    for (int p = 0; p < 2; ++p)
+        for (int s = 0; s < 2; ++s) {
+            Species &sp = R.buf[p][s];
+            sp.cell = (int32_t *)(A + L.sp[p][s][0]);
+            sp.off = (float *)(A + L.sp[p][s][1]);
+            sp.vx = (float *)(A + L.sp[p][s][2]);
+            sp.vy = (float *)(A + L.sp[p][s][3]);
+            sp.vz = (float *)(A + L.sp[p][s][4]);
+            sp.id = (uint32_t *)(A + L.sp[p][s][5]);
+            sp.abar = c.scheme == PIC_EC_IMPLICIT ? (float *)(A + L.sp[p][s][6]) : nullptr;
+        }
+    for (int s = 0; s < 2; ++s) {
+        R.acc_cnt[s] = (unsigned long long *)(A + L.acc_cnt[s]);
+        R.acc_a[s] = (unsigned long long *)(A + L.acc_a[s]);
+        R.acc_b[s] = (unsigned long long *)(A + L.acc_b[s]);
+        R.cursor[s] = (unsigned int *)(A + L.cursor[s]);
+        R.rho_q[s] = (long long *)(A + L.rho_q[s]);
+        R.heat[s] = (double *)(A + L.heat[s]);
+    }
+    R.e_gather = (float *)(A + L.e_gather);
+    R.e_cc = (double *)(A + L.e_cc);
+    R.phi = (double *)(A + L.phi);
+    R.chi = (double *)(A + L.chi);
+    R.avg_ne = (double *)(A + L.avg_ne);
+    R.avg_ni = (double *)(A + L.avg_ni);
+    R.avg_phi = (double *)(A + L.avg_phi);
+    R.eedf = (unsigned long long *)(A + L.eedf);
+    R.births = (Birth *)(A + L.births);
+    R.st = (DevState *)(A + L.state);
+}
+
+Mode push_mode(const pic_config &c) { return c.scheme == PIC_MC_EXPLICIT ? kExplicitMC : kExplicitEC; }
+Mode deposit_mode(const pic_config &c) { return c.scheme == PIC_MC_EXPLICIT ? kDepositMC : kDepositEC; }
+
+// Enqueue one step (and the sort that closes a sort cycle) on stream s.
+int enqueue_step(pic_handle *h, long long step_index, cudaStream_t s) {
+    const pic_config &c = h->cfg;
+    if (c.scheme == PIC_EC_IMPLICIT) {
+        CK(h, launch_particles(h->run, kImplicit1, h->grid_push, s));
+        CK(h, launch_particles(h->run, kImplicit2, h->grid_push, s));
+    } else {
+        CK(h, launch_particles(h->run, push_mode(c), h->grid_push, s));
+    }
+    if (c.sort_period > 0 && (step_index + 1) % c.sort_period == 0)
+        CK(h, launch_sort(h->run, h->grid_sort, s));
+    return PIC_OK;
+}
+
+int sync(pic_handle *h) {
+    CK(h, cudaStreamSynchronize(h->stream));
+    return PIC_OK;
+}
+
+int read_state(pic_handle *h, DevState *st) {
+    int r = sync(h);
+    if (r) return r;
+    CK(h, cudaMemcpy(st, h->run.st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_version(void) { return PIC_ABI_VERSION; }
+
+const char *pic_build_info(void) {
+    return "libpic: energy-conserving 1D PIC/MCC, sm_103a, " __DATE__;
+}
+
+int pic_required_sizes(const pic_config *cfg, pic_sizes *out) {
+    int r = validate(cfg);
+    if (r) return r;
+    if (!out) return fail(PIC_EINVAL, "out is NULL");
+    const Layout L = make_layout(*cfg);
+    out->arena_bytes = L.total;
+    out->snapshot_bytes = L.total + sizeof(Snapshot);
+    return PIC_OK;
+}
+
+int pic_init(const pic_config *cfg, const pic_buffers *bufs, void *stream, pic_handle **out) {
+    int r = validate(cfg);
+    if (r) return r;
+    if (!bufs || !out) return fail(PIC_EINVAL, "bufs/out is NULL");
+    const Layout L = make_layout(*cfg);
+    if (!bufs->arena || bufs->arena_bytes < L.total)
+        return fail(PIC_ENOMEM, "arena of %zu bytes, %zu needed", bufs->arena_bytes, L.total);
+    if (((uintptr_t)bufs->arena & 255u) != 0) return fail(PIC_ENOMEM, "arena not 256-byte aligned");
+    pic_handle *h = new pic_handle();
+    h->cfg = *cfg;
+    h->layout = L;
+    h->arena = (unsigned char *)bufs->arena;
+    h->arena_bytes = L.total;
+    h->stream = (cudaStream_t)stream;
+    h->capture_stream = nullptr;
+    h->host_step = 0;
+    h->cycle_graph = nullptr;
+    h->cycle_len = 0;
+    derive(h);
+    auto bail = [&](int code) {
+        g_error = h->err.empty() ? g_error : h->err;
+        delete h;
+        return code;
+    };
+    if (occupancy_grid(h->run, push_mode(*cfg), &h->grid_push) != cudaSuccess) {
+        cuda_fail(h, cudaGetLastError(), "occupancy");
+        return bail(PIC_ECUDA);
+    }
+    h->grid_sort = h->grid_push;
+    if (cfg->scheme == PIC_EC_IMPLICIT) {
+        int g1 = 0, g2 = 0;
+        occupancy_grid(h->run, kImplicit1, &g1);
+        occupancy_grid(h->run, kImplicit2, &g2);
+        h->grid_push = g1 < g2 ? g1 : g2;
+    }
+    if (cudaMemsetAsync(h->arena, 0, L.total, h->stream) != cudaSuccess) {
+        cuda_fail(h, cudaGetLastError(), "cudaMemsetAsync(arena)");
+        return bail(PIC_ECUDA);
+    }
+    DevState st;
+    std::memset(&st, 0, sizeof st);
+    st.n_slots[0] = st.n_live[0] = cfg->np_init;
+    st.n_slots[1] = st.n_live[1] = cfg->ions_mobile ? cfg->np_init : 0;
+    st.next_id[0] = (unsigned int)cfg->np_init;
+    st.next_id[1] = (unsigned int)st.n_slots[1];
+    if (cudaMemcpyAsync(h->run.st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cuda_fail(h, cudaGetLastError(), "state upload");
+        return bail(PIC_ECUDA);
+    }
+    const double vth_e = std::sqrt(kE * cfg->te_ev / kMe);
+    const double vth_i = std::sqrt(kE * cfg->ti_ev / (cfg->ion_mass_amu * kAmu));
+    cudaError_t e = launch_load(h->run, 0, cfg->np_init, (float)vth_e, h->stream);
+    if (e == cudaSuccess && cfg->ions_mobile) e = launch_load(h->run, 1, cfg->np_init, (float)vth_i, h->stream);
+    if (e != cudaSuccess) {
+        cuda_fail(h, e, "load");
+        return bail(PIC_ECUDA);
+    }
+    r = pic_init_field(h, 1);
+    if (r) return bail(r);
+    *out = h;
+    return PIC_OK;
+}
+
+int pic_init_field(pic_handle *h, int set_abar) {
+    if (!h) return fail(PIC_EINVAL, "handle is NULL");
+    CK(h, launch_particles(h->run, deposit_mode(h->cfg), h->grid_push, h->stream));
+    if (h->cfg.scheme == PIC_EC_IMPLICIT && set_abar) CK(h, launch_set_abar(h->run, h->stream));
+    return PIC_OK;
+}
+
+static int capture_cycle(pic_handle *h) {
+    const int len = h->cfg.sort_period > 0 ? h->cfg.sort_period : 16;
+    if (!h->capture_stream) CK(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+    int r = PIC_OK;
+    for (int k = 0; k < len && r == PIC_OK; ++k) r = enqueue_step(h, (long long)k, h->capture_stream);
+    cudaError_t e = cudaStreamEndCapture(h->capture_stream, &g);
+    if (r) return r;
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->cycle_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    h->cycle_len = len;
+    return PIC_OK;
+}
+
+int pic_step(pic_handle *h, int64_t n) {
+    if (!h) return fail(PIC_EINVAL, "handle is NULL");
+    if (n < 0) return fail(PIC_EINVAL, "negative step count");
+    const int K = h->cfg.sort_period > 0 ? h->cfg.sort_period : 16;
+    while (n > 0) {
+        const bool aligned = h->host_step % K == 0;
+        if (aligned && n >= K) {
+            if (!h->cycle_graph) {
+                int r = capture_cycle(h);
+                if (r) return r;
+            }
+            CK(h, cudaGraphLaunch(h->cycle_graph, h->stream));
+            h->host_step += K;
+            n -= K;
+        } else {
+            int r = enqueue_step(h, h->host_step, h->stream);
+            if (r) return r;
+            h->host_step += 1;
+            n -= 1;
+        }
+    }
+    return PIC_OK;
+}
+
+int pic_diag(pic_handle *h, pic_diag_t *out, int reset_avg) {
+    if (!h || !out) return fail(PIC_EINVAL, "NULL argument");
+    CK(h, cudaMemsetAsync(h->run.st->ke_perp, 0, sizeof(double) * 2, h->stream));
+    CK(h, launch_perp_energy(h->run, h->stream));
+    DevState st;
+    int r = read_state(h, &st);
+    if (r) return r;
+    std::memset(out, 0, sizeof *out);
+    out->step = st.step;
+    for (int s = 0; s < 2; ++s) {
+        out->count[s] = st.n_live[s];
+        for (int w = 0; w < 2; ++w) {
+            out->wall_count[s][w] = st.wall_count[s][w];
+            out->wall_energy_ev[s][w] = st.wall_energy[s][w];
+        }
+        out->overflow[s] = st.overflow[s];
+        out->ke_x[s] = st.ke_x[s] * h->run.half_m_w[s];
+        out->ke_perp[s] = st.ke_perp[s];
+        out->power[s] = st.power[s];
+    }
+    for (int k = 0; k < 5; ++k) out->coll[k] = st.coll[k];
+    out->births = st.births_total;
+    out->field_energy = st.field_energy;
+    out->field_energy_push = st.field_energy_push;
+    out->n_avg = st.n_avg;
+    out->n_diag = st.n_diag;
+    out->status = st.status;
+    if (reset_avg) {
+        const Layout &L = h->layout;
+        const size_t n1 = (size_t)h->cfg.n_cells + 1;
+        CK(h, cudaMemsetAsync(h->arena + L.avg_ne, 0, 8 * n1, h->stream));
+        CK(h, cudaMemsetAsync(h->arena + L.avg_ni, 0, 8 * n1, h->stream));
+        CK(h, cudaMemsetAsync(h->arena + L.avg_phi, 0, 8 * n1, h->stream));
+        CK(h, cudaMemsetAsync(h->arena + L.heat[0], 0, 8 * n1, h->stream));
+        CK(h, cudaMemsetAsync(h->arena + L.heat[1], 0, 8 * n1, h->stream));
+        CK(h, cudaMemsetAsync(h->arena + L.eedf, 0, 8 * ((size_t)h->cfg.eedf_bins + 1), h->stream));
+        CK(h, cudaMemsetAsync(&h->run.st->n_avg, 0, sizeof(long long) * 2, h->stream));
+        r = sync(h);
+        if (r) return r;
+    }
+    return PIC_OK;
+}
+
+int pic_profiles(pic_handle *h, double *ne, double *ni, double *phi, double *heat_e,
+                 double *heat_i, uint64_t *eedf) {
+    if (!h) return fail(PIC_EINVAL, "handle is NULL");
+    DevState st;
+    int r = read_state(h, &st);
+    if (r) return r;
+    const size_t n1 = (size_t)h->cfg.n_cells + 1, n = (size_t)h->cfg.n_cells;
+    const double na = st.n_avg > 0 ? (double)st.n_avg : 1.0;
+    const double nd = st.n_diag > 0 ? (double)st.n_diag : 1.0;
+    auto fetch = [&](double *dst, double *src, size_t cnt, double div) -> int {
+        if (!dst) return PIC_OK;
+        CK(h, cudaMemcpy(dst, src, 8 * cnt, cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < cnt; ++k) dst[k] /= div;
+        return PIC_OK;
+    };
+    if ((r = fetch(ne, h->run.avg_ne, n1, na))) return r;
+    if ((r = fetch(ni, h->run.avg_ni, n1, na))) return r;
+    if ((r = fetch(phi, h->run.avg_phi, n1, na))) return r;
+    if ((r = fetch(heat_e, h->run.heat[0], n, nd))) return r;
+    if ((r = fetch(heat_i, h->run.heat[1], n, nd))) return r;
+    if (eedf) CK(h, cudaMemcpy(eedf, h->run.eedf, 8 * ((size_t)h->cfg.eedf_bins + 1), cudaMemcpyDeviceToHost));
+    return PIC_OK;
+}
+
+int pic_grids(pic_handle *h, int64_t *rho_q_e, int64_t *rho_q_i, double *phi, double *e_cc,
+              double *chi) {
+    if (!h) return fail(PIC_EINVAL, "handle is NULL");
+    int r = sync(h);
+    if (r) return r;
+    const size_t n1 = (size_t)h->cfg.n_cells + 1, n = (size_t)h->cfg.n_cells;
+    if (rho_q_e) CK(h, cudaMemcpy(rho_q_e, h->run.rho_q[0], 8 * n1, cudaMemcpyDeviceToHost));
+    if (rho_q_i) CK(h, cudaMemcpy(rho_q_i, h->run.rho_q[1], 8 * n1, cudaMemcpyDeviceToHost));
+    if (phi) CK(h, cudaMemcpy(phi, h->run.phi, 8 * n1, cudaMemcpyDeviceToHost));
+    if (e_cc) CK(h, cudaMemcpy(e_cc, h->run.e_cc, 8 * n, cudaMemcpyDeviceToHost));
+    if (chi) CK(h, cudaMemcpy(chi, h->run.chi, 8 * n, cudaMemcpyDeviceToHost));
+    return PIC_OK;
+}
+
+int pic_count(pic_handle *h, int64_t *n_e, int64_t *n_i) {
+    if (!h) return fail(PIC_EINVAL, "handle is NULL");
+    DevState st;
+    int r = read_state(h, &st);
+    if (r) return r;
+    if (n_e) *n_e = st.n_live[0];
+    if (n_i) *n_i = st.n_live[1];
+    return PIC_OK;
+}
+
+int pic_get_particles(pic_handle *h, int species, pic_host_particles *out) {
+    if (!h || !out || species < 0 || species > 1) return fail(PIC_EINVAL, "bad argument");
+    DevState st;
+    int r = read_state(h, &st);
+    if (r) return r;
+    if (out->count < st.n_live[species])
+        return fail(PIC_EINVAL, "host arrays hold %lld, %lld live particles", (long long)out->count,
+                    (long long)st.n_live[species]);
+    const long long ns = st.n_slots[species];
+    const Species &sp = h->run.buf[st.parity][species];
+    std::vector<int32_t> cell(ns);
+    std::vector<float> off(ns), vx(ns), vy(ns), vz(ns), ab(ns);
+    std::vector<uint32_t> id(ns);
+    if (ns > 0) {
+        CK(h, cudaMemcpy(cell.data(), sp.cell, 4 * ns, cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpy(off.data(), sp.off, 4 * ns, cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpy(vx.data(), sp.vx, 4 * ns, cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpy(vy.data(), sp.vy, 4 * ns, cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpy(vz.data(), sp.vz, 4 * ns, cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpy(id.data(), sp.id, 4 * ns, cudaMemcpyDeviceToHost));
+        if (sp.abar) CK(h, cudaMemcpy(ab.data(), sp.abar, 4 * ns, cudaMemcpyDeviceToHost));
+    }
+    long long k = 0;
+    for (long long i = 0; i < ns; ++i) {
+        if (cell[i] < 0) continue;
+        if (out->cell) out->cell[k] = cell[i];
+        if (out->off) out->off[k] = off[i];
+        if (out->vx) out->vx[k] = vx[i];
+        if (out->vy) out->vy[k] = vy[i];
+        if (out->vz) out->vz[k] = vz[i];
+        if (out->id) out->id[k] = id[i];
+        if (out->abar) out->abar[k] = sp.abar ? ab[i] : 0.0f;
+        ++k;
+    }
+    out->count = k;
+    out->next_id = st.next_id[species];
+    return PIC_OK;
+}
+
+int pic_set_particles(pic_handle *h, int species, const pic_host_particles *in) {
+    if (!h || !in || species < 0 || species > 1) return fail(PIC_EINVAL, "bad argument");
+    const long long n = in->count;
+    if (n < 0 || n > h->cfg.capacity[species]) return fail(PIC_EOVERFLOW, "count %lld exceeds capacity", (long long)n);
+    if (species == 1 && !h->cfg.ions_mobile && n > 0) return fail(PIC_EINVAL, "ions are frozen in this run");
+    if (n > 0 && (!in->cell || !in->off || !in->vx || !in->vy || !in->vz || !in->id))
+        return fail(PIC_EINVAL, "NULL particle array");
+    for (long long i = 0; i < n; ++i) {
+        if (in->cell[i] < 0 || in->cell[i] >= h->cfg.n_cells || !(in->off[i] >= 0.0f) || !(in->off[i] < 1.0f))
+            return fail(PIC_EINVAL, "particle %lld outside the grid (cell %d, offset %g)", i, in->cell[i],
+                        (double)in->off[i]);
+    }
+    DevState st;
+    int r = read_state(h, &st);
+    if (r) return r;
+    const Species &sp = h->run.buf[st.parity][species];
+    if (n > 0) {
+        CK(h, cudaMemcpyAsync(sp.cell, in->cell, 4 * n, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(sp.off, in->off, 4 * n, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(sp.vx, in->vx, 4 * n, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(sp.vy, in->vy, 4 * n, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(sp.vz, in->vz, 4 * n, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(sp.id, in->id, 4 * n, cudaMemcpyHostToDevice, h->stream));
+        if (sp.abar) {
+            if (in->abar)
+                CK(h, cudaMemcpyAsync(sp.abar, in->abar, 4 * n, cudaMemcpyHostToDevice, h->stream));
+            else
+                CK(h, cudaMemsetAsync(sp.abar, 0, 4 * n, h->stream));
+        }
+    }
+    long long cnt = n;
+    unsigned int nid = in->next_id;
+    CK(h, cudaMemcpyAsync(&h->run.st->n_slots[species], &cnt, 8, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(&h->run.st->n_live[species], &cnt, 8, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(&h->run.st->next_id[species], &nid, 4, cudaMemcpyHostToDevice, h->stream));
+    return sync(h);
+}
+
+int pic_set_step(pic_handle *h, int64_t step) {
+    if (!h || step < 0) return fail(PIC_EINVAL, "bad argument");
+    long long s = step;
+    CK(h, cudaMemcpyAsync(&h->run.st->step, &s, 8, cudaMemcpyHostToDevice, h->stream));
+    h->host_step = step;
+    return sync(h);
+}
+
+int pic_status(pic_handle *h, uint32_t *status) {
+    if (!h || !status) return fail(PIC_EINVAL, "NULL argument");
+    DevState st;
+    int r = read_state(h, &st);
+    if (r) return r;
+    *status = st.status;
+    return PIC_OK;
+}
+
+int pic_save(pic_handle *h, void *host_buf, size_t nbytes) {
+    if (!h || !host_buf) return fail(PIC_EINVAL, "NULL argument");
+    if (nbytes < h->arena_bytes + sizeof(Snapshot)) return fail(PIC_ENOMEM, "snapshot buffer too small");
+    int r = sync(h);
+    if (r) return r;
+    Snapshot s = {kSnapMagic, PIC_ABI_VERSION, h->arena_bytes, h->host_step};
+    std::memcpy(host_buf, &s, sizeof s);
+    CK(h, cudaMemcpy((unsigned char *)host_buf + sizeof s, h->arena, h->arena_bytes, cudaMemcpyDeviceToHost));
+    return PIC_OK;
+}
+
+int pic_load(pic_handle *h, const void *host_buf, size_t nbytes) {
+    if (!h || !host_buf) return fail(PIC_EINVAL, "NULL argument");
+    if (nbytes < sizeof(Snapshot)) return fail(PIC_EINVAL, "snapshot too small");
+    Snapshot s;
+    std::memcpy(&s, host_buf, sizeof s);
+    if (s.magic != kSnapMagic || s.arena_bytes != h->arena_bytes || nbytes < h->arena_bytes + sizeof s)
+        return fail(PIC_EINVAL, "snapshot does not match this run's layout");
+    int r = sync(h);
+    if (r) return r;
+    CK(h, cudaMemcpy(h->arena, (const unsigned char *)host_buf + sizeof s, h->arena_bytes, cudaMemcpyHostToDevice));
+    h->host_step = s.host_step;
+    return PIC_OK;
+}
+
+int pic_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                    int64_t n, uint32_t *out_device, void *stream) {
+    if (n < 0 || (n > 0 && !out_device)) return fail(PIC_EINVAL, "bad argument");
+    cudaError_t e = launch_philox_fill(k0, k1, c0, c1, c2, c3, n, out_device, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "philox_fill");
+    return PIC_OK;
+}
+
+void pic_free(pic_handle *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->cycle_graph) cudaGraphExecDestroy(h->cycle_graph);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    delete h;
+}
+
+const char *pic_last_error(const pic_handle *h) {
+    if (h && !h->err.empty()) return h->err.c_str();
+    return g_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+// pic_internal.h -- data layout shared by the host runtime and the kernels of
+// libpic.so.  Nothing here is part of the public ABI (include/pic.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace pic {
+
+constexpr int kMaxCells = 1024;          // grid lives in shared memory
+constexpr int kThreads = 256;            // block size of the particle kernels
+constexpr int kUnroll = 4;               // particles per thread per tile
+constexpr int kMaxEedfBins = 4096;
+
+enum Mode : int {
+    kExplicitEC = 0,   // gather/push/absorb/collide/deposit S_2, field solve
+    kExplicitMC = 1,   // same with the momentum-conserving S_1 weighting
+    kDepositEC = 2,    // deposit only (initial field, injected state)
+    kDepositMC = 3,
+    kImplicit1 = 4,    // direct implicit pass 1: predictor, deposit rho~ and chi
+    kImplicit2 = 5,    // direct implicit pass 2: corrector, absorb, collide
+};
+
+// One species' particle arrays (structure of arrays).
+struct Species {
+    int32_t *cell;
+    float *off;
+    float *vx, *vy, *vz;
+    uint32_t *id;
+    float *abar;
+};
+
+// An ionisation event recorded by the push, placed by the step's tail.
+struct Birth {
+    uint32_t pid;
+    int32_t cell;
+    float off;
+    float abar_e;
+    float ve[3];
+    float vi[3];
+};
+
+// Mutable per-run state, resident in the arena.
+struct DevState {
+    long long step;
+    long long n_slots[2];          // slots in use (live + holes left by absorption)
+    long long n_live[2];
+    unsigned int next_id[2];
+    unsigned int parity;           // which of the two particle buffers is current
+    unsigned int status;           // sticky PIC_STATUS_* bits
+    unsigned int blocks_done;      // last-block detection of the particle kernels
+    unsigned int n_births;         // births recorded in the current step
+    unsigned int sort_blocks_done;
+    unsigned int pad0;
+    unsigned long long absorbed_step[2];
+    double ke_x_acc[2], power_acc[2];
+    double ke_x[2], power[2];
+    double field_energy, field_energy_push;
+    double ke_perp[2];
+    unsigned long long wall_count[2][2];
+    double wall_energy[2][2];
+    unsigned long long coll[5];
+    unsigned long long overflow[2];
+    unsigned long long births_total;
+    long long n_avg, n_diag;
+};
+
+// Constants and pointers of one run, passed to kernels by value.
+struct Run {
+    int n_cells, periodic, scheme, mcc, ions_mobile, diag_period, eedf_bins, sort_period;
+    uint32_t seed, run;
+    long long capacity[2];
+    long long births_cap;
+    // geometry / field (FP64, host-derived)
+    double dx, dt, rf_freq, rf_volt, weight;
+    double kappa;        // E jump per 2^-33 macro charge: e w 2^-33 / eps0
+    double kappa_bg;     // E jump per interior node from the frozen ion density
+    double chi_coef[2];  // dt^2/2 q^2 w / (m eps0 dx) * 2^-16
+    double dens_scale;   // density per 2^-33 macro charge: w 2^-33 / dx
+    double half_m_w[2];  // kinetic energy per (m/s)^2 per macro-particle
+    double eps0_dx_half; // field energy factor eps0 dx / 2
+    // push (FP32)
+    float qm_dt[2];        // (q/m) dt
+    float qm[2];
+    float dt_dx;           // dt / dx
+    float half_dt;         // dt / 2
+    float half_dt2_dx;     // dt^2 / (2 dx)
+    float qw[2];           // q w: power per particle per (V/m * m/s)
+    float half_m_over_e[2];// 0.5 m / e: energy [eV] per (m/s)^2
+    // collisions (FP32)
+    uint32_t thr[2];       // selection thresholds on 24-bit uniforms
+    float nu_max_e, nu_max_i, n_g;
+    float sig_el, exc_thr, exc_ramp_end, exc_slope, sig_exc_max, iz_thr, sig_iz_k, sig_cx;
+    float eps_cap, g_max_i, two_m_over_M, two_e_over_me, vth_gas;
+    float abar_ion_over_e; // (q_i/m_i) / (q_e/m_e)
+    float eedf_inv_width;
+    // pointers into the arena
+    Species buf[2][2];     // [parity][species]
+    unsigned long long *acc_cnt[2], *acc_a[2], *acc_b[2];   // [species][n_cells + 1]
+    unsigned int *cursor[2];                                // [species][n_cells + 1]
+    float *e_gather;       // [n_cells + 2]
+    double *e_cc, *phi, *chi;                               // [n_cells], [n_cells+1], [n_cells]
+    long long *rho_q[2];   // [species][n_cells + 1] last assembled node charge, 2^-33 units
+    double *avg_ne, *avg_ni, *avg_phi, *heat[2];
+    unsigned long long *eedf;
+    Birth *births;
+    DevState *st;
+};
+
+// ---- launchers (pic_kernels.cu) ----
+int block_smem_bytes(const Run &r);
+cudaError_t launch_load(const Run &r, int species, long long n, float vth, cudaStream_t s);
+cudaError_t launch_particles(const Run &r, Mode m, int grid, cudaStream_t s);
+cudaError_t launch_sort(const Run &r, int grid, cudaStream_t s);
+cudaError_t launch_set_abar(const Run &r, cudaStream_t s);
+cudaError_t launch_perp_energy(const Run &r, cudaStream_t s);
+cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
+                               uint32_t c3, long long n, uint32_t *out, cudaStream_t s);
+cudaError_t occupancy_grid(const Run &r, Mode m, int *grid);
+
+}  // namespace pic

@@ -1,0 +1,1264 @@
+// pic_kernels.cu -- sm_103a kernels of the energy-conserving PIC/MCC step.
+//
+// One step of the explicit schemes (Sec. 2, schemes (1) and (2)) is ONE launch
+// of k_particles: every block streams a contiguous chunk of particles from HBM
+// (structure of arrays, one 4-byte word per field), gathers the field from a
+// shared-memory copy of the grid, pushes, tests the electrodes, draws its
+// null-collision decision from Philox keyed on (id, step), collides the few
+// selected particles, and assigns its charge into per-block shared-memory
+// accumulators in integer fixed point.  The last block to finish (atomic
+// arrival counter) runs the tail of the step: places the step's births in
+// parent-id order, assembles the node charge exactly in int64, solves the
+// field equation and updates the diagnostics.  The direct-implicit scheme
+// (Sec. 2, scheme (4)) is two such launches (predictor + corrector).
+#include "pic_internal.h"
+
+#include <cstdint>
+
+namespace pic {
+
+#define FULL_MASK 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 32x32->64-bit multiplies with the published multipliers, key bumped by the
+// published Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+constexpr uint32_t kTagLoad = 1u;
+constexpr uint32_t kTagMcc = 2u;
+
+// Counter layout: (id, step low word, step high word, species<<24 | tag<<16 | sub).
+__device__ __forceinline__ uint4 draw(const Run &R, uint32_t id, long long step, int species,
+                                      uint32_t tag, uint32_t sub) {
+    const unsigned long long s = (unsigned long long)step;
+    return philox4x32_10(make_uint4(id, (uint32_t)s, (uint32_t)(s >> 32),
+                                    ((uint32_t)species << 24) | (tag << 16) | sub),
+                         R.seed, R.run);
+}
+
+// Uniform on (0, 1) from the top 24 bits.
+__device__ __forceinline__ float u24(uint32_t w) {
+    return fmaf((float)(w >> 8), 5.9604644775390625e-8f, 2.98023223876953125e-8f);
+}
+
+// Box-Muller: two uniforms -> two standard normals.
+__device__ __forceinline__ void box_muller(float u1, float u2, float &n1, float &n2) {
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    n1 = r * c;
+    n2 = r * s;
+}
+
+// Turn the unit vector d by polar angle chi and azimuth phi, the azimuth
+// measured in the basis of d's polar angles about the x axis.
+__device__ __forceinline__ void rotate(float dx_, float dy, float dz, float cos_chi, float sp,
+                                       float cp, float &ox, float &oy, float &oz) {
+    const float sin_chi = sqrtf(fmaxf(0.0f, 1.0f - cos_chi * cos_chi));
+    const float st = sqrtf(dy * dy + dz * dz);
+    if (st > 1e-6f) {
+        const float inv = 1.0f / st;
+        ox = cos_chi * dx_ - sin_chi * cp * st;
+        oy = cos_chi * dy + sin_chi * (cp * dx_ * dy - sp * dz) * inv;
+        oz = cos_chi * dz + sin_chi * (cp * dx_ * dz + sp * dy) * inv;
+    } else {
+        ox = cos_chi * dx_;
+        oy = sin_chi * cp * dx_;
+        oz = sin_chi * sp;
+    }
+}
+
+__device__ __forceinline__ float sigma_exc(const Run &R, float eps) {
+    if (eps < R.exc_thr) return 0.0f;
+    if (eps < R.exc_ramp_end) return R.exc_slope * (eps - R.exc_thr);
+    return R.sig_exc_max;
+}
+
+__device__ __forceinline__ float sigma_iz(const Run &R, float eps) {
+    if (eps <= R.iz_thr) return 0.0f;
+    return R.sig_iz_k * (R.iz_thr / eps) * logf(eps / R.iz_thr);
+}
+
+// Per-thread counters of one species segment.
+struct Tally {
+    float kx, pw;
+    unsigned int el, ex, iz, cx, nul, ovf;
+};
+
+// Electron collision (null-collision MC): elastic, excitation or ionisation
+// chosen by u * nu_max against the running sum of n_g sigma_k(eps) v.
+// Returns true if the velocity changed.
+__device__ bool collide_electron(const Run &R, uint4 w, uint32_t id, long long step, int cell,
+                                 float off, float abar, float &vx, float &vy, float &vz, Tally &t) {
+    const float v2 = vx * vx + vy * vy + vz * vz;
+    const float g = sqrtf(v2);
+    const float eps = R.half_m_over_e[0] * v2;
+    if (eps > R.eps_cap) t.ovf++;
+    const float r = u24(w.y) * R.nu_max_e;
+    const float ngv = R.n_g * g;
+    const float nu_el = R.sig_el * ngv;
+    const float nu_ex = sigma_exc(R, eps) * ngv;
+    const float nu_iz = sigma_iz(R, eps) * ngv;
+    const float cos_chi = 1.0f - 2.0f * u24(w.z);
+    float sp, cp;
+    sincospif(2.0f * u24(w.w), &sp, &cp);
+    float dx_ = 1.0f, dy = 0.0f, dz = 0.0f;
+    if (g > 0.0f) {
+        const float inv = 1.0f / g;
+        dx_ = vx * inv;
+        dy = vy * inv;
+        dz = vz * inv;
+    }
+    float g_new;
+    if (r < nu_el) {
+        g_new = g * sqrtf(1.0f - R.two_m_over_M * (1.0f - cos_chi));
+        t.el++;
+    } else if (r < nu_el + nu_ex) {
+        g_new = sqrtf(R.two_e_over_me * (eps - R.exc_thr));
+        t.ex++;
+    } else if (r < nu_el + nu_ex + nu_iz) {
+        // Reading: the energy above threshold is shared equally by the two
+        // electrons, each scattered isotropically; the ion comes from the gas.
+        g_new = sqrtf(R.two_e_over_me * 0.5f * (eps - R.iz_thr));
+        const uint4 w1 = draw(R, id, step, 0, kTagMcc, 1);
+        const uint4 w2 = draw(R, id, step, 0, kTagMcc, 2);
+        const float ct = 1.0f - 2.0f * u24(w1.x);
+        const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+        float sps, cps;
+        sincospif(2.0f * u24(w1.y), &sps, &cps);
+        float n1, n2, n3, n4;
+        box_muller(u24(w1.z), u24(w1.w), n1, n2);
+        box_muller(u24(w2.x), u24(w2.y), n3, n4);
+        const unsigned int slot = atomicAdd(&R.st->n_births, 1u);
+        if (slot < (unsigned int)R.births_cap) {
+            Birth b;
+            b.pid = id;
+            b.cell = cell;
+            b.off = off;
+            b.abar_e = abar;
+            b.ve[0] = g_new * ct;
+            b.ve[1] = g_new * st * cps;
+            b.ve[2] = g_new * st * sps;
+            b.vi[0] = R.vth_gas * n1;
+            b.vi[1] = R.vth_gas * n2;
+            b.vi[2] = R.vth_gas * n3;
+            R.births[slot] = b;
+        }
+        t.iz++;
+    } else {
+        t.nul++;
+        return false;
+    }
+    float ox, oy, oz;
+    rotate(dx_, dy, dz, cos_chi, sp, cp, ox, oy, oz);
+    vx = g_new * ox;
+    vy = g_new * oy;
+    vz = g_new * oz;
+    return true;
+}
+
+// Ion charge exchange against a neutral sampled from the gas Maxwellian.
+__device__ bool collide_ion(const Run &R, uint4 w, uint32_t id, long long step, float &vx,
+                            float &vy, float &vz, Tally &t) {
+    const uint4 w1 = draw(R, id, step, 1, kTagMcc, 1);
+    float n1, n2, n3, n4;
+    box_muller(u24(w.z), u24(w.w), n1, n2);
+    box_muller(u24(w1.x), u24(w1.y), n3, n4);
+    const float vnx = R.vth_gas * n1, vny = R.vth_gas * n2, vnz = R.vth_gas * n3;
+    const float ux = vx - vnx, uy = vy - vny, uz = vz - vnz;
+    const float g = sqrtf(ux * ux + uy * uy + uz * uz);
+    if (g > R.g_max_i) t.ovf++;
+    const float r = u24(w.y) * R.nu_max_i;
+    if (r < R.n_g * R.sig_cx * g) {
+        vx = vnx;
+        vy = vny;
+        vz = vnz;
+        t.cx++;
+        return true;
+    }
+    t.nul++;
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Charge assignment in fixed point.  The offset is quantised to 16 bits,
+// F = floor(off * 2^16).  S_2 (Eq. 2, m = 2): nearest node j and
+// a = (1/2 + delta) 2^16; the nodes j-1, j, j+1 receive b^2, 2^33 - a^2 - b^2,
+// a^2 (b = 2^16 - a), i.e. 2^33 times the quadratic spline weights.  Each
+// particle is accumulated under its key j as (1, a, a^2); the node charges
+// are reassembled exactly from these per-key sums in the tail.  S_1 (the
+// momentum-conserving scheme): key = cell, value F.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int deposit_key_s2(int cell, float off, uint32_t &a) {
+    const int F = (int)(off * 65536.0f);
+    if (F < 32768) {
+        a = (uint32_t)(F + 32768);
+        return cell;
+    }
+    a = (uint32_t)(F - 32768);
+    return cell + 1;
+}
+
+__device__ __forceinline__ int deposit_key_s1(int cell, float off, uint32_t &a) {
+    a = (uint32_t)(int)(off * 65536.0f);
+    return cell;
+}
+
+// Warp-aggregated accumulation into shared memory: lanes sharing a key are
+// summed with redux.sync and one lane per key updates the shared arrays.
+// Every lane of the warp must call this (key < 0: nothing to add).
+__device__ __forceinline__ void warp_deposit(int key, uint32_t a, unsigned int *s_cnt,
+                                             unsigned long long *s_a, unsigned long long *s_b,
+                                             bool count_only) {
+    const int lane = threadIdx.x & 31;
+    unsigned int pending = __ballot_sync(FULL_MASK, key >= 0);
+    int iter = 0;
+    while (pending) {
+        if (iter == 6) {  // widely spread warp: per-lane shared atomics for the rest
+            if ((pending >> lane) & 1u) {
+                atomicAdd(&s_cnt[key], 1u);
+                if (!count_only) {
+                    atomicAdd(&s_a[key], (unsigned long long)a);
+                    atomicAdd(&s_b[key], (unsigned long long)a * a);
+                }
+            }
+            break;
+        }
+        const int leader = __ffs(pending) - 1;
+        const int lk = __shfl_sync(FULL_MASK, key, leader);
+        const bool mine = ((pending >> lane) & 1u) && key == lk;
+        const unsigned int grp = __ballot_sync(FULL_MASK, mine);
+        if (!count_only) {
+            const uint32_t av = mine ? a : 0u;
+            const uint32_t a2 = av * av;  // a < 2^16
+            const uint32_t sa = __reduce_add_sync(FULL_MASK, av);
+            const uint32_t hi = __reduce_add_sync(FULL_MASK, a2 >> 16);
+            const uint32_t lo = __reduce_add_sync(FULL_MASK, a2 & 0xffffu);
+            if (lane == leader) {
+                atomicAdd(&s_cnt[lk], (unsigned int)__popc(grp));
+                atomicAdd(&s_a[lk], (unsigned long long)sa);
+                atomicAdd(&s_b[lk], ((unsigned long long)hi << 16) + lo);
+            }
+        } else if (lane == leader) {
+            atomicAdd(&s_cnt[lk], (unsigned int)__popc(grp));
+        }
+        pending &= ~grp;
+        ++iter;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide scans (256 threads).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ T block_exclusive_scan(T v, T *scratch /*[33]*/, T &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int nw = kThreads / 32;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(FULL_MASK, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) scratch[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        T s = lane < nw ? scratch[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(FULL_MASK, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) scratch[lane] = s;
+    }
+    __syncthreads();
+    const T before = wid > 0 ? scratch[wid - 1] : T(0);
+    total = scratch[nw - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+template <typename T>
+__device__ T block_sum(T v, T *scratch) {
+    T total;
+    block_exclusive_scan<T>(v, scratch, total);
+    return total;
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory layout of the particle kernels.
+// ---------------------------------------------------------------------------
+struct SmemMain {
+    float *e;                  // [n+2] gather table
+    unsigned int *cnt;         // [n+1]
+    unsigned long long *a, *b; // [n+1]
+    float *heat;               // [n]
+    unsigned int *eedf;        // [bins+1]
+};
+
+__host__ __device__ inline size_t align8(size_t x) { return (x + 7) & ~size_t(7); }
+
+__host__ __device__ inline size_t main_smem_bytes(int n, int bins) {
+    return align8(4 * (size_t)(n + 2)) + align8(4 * (size_t)(n + 1)) + 16 * (size_t)(n + 1) +
+           align8(4 * (size_t)n) + align8(4 * (size_t)(bins + 1));
+}
+
+__host__ __device__ inline size_t tail_smem_bytes(int n) {
+    return 8 * (size_t)(n + 1) * 4 + 8 * 2048;
+}
+
+__device__ SmemMain carve_main(unsigned char *base, int n, int bins) {
+    SmemMain s;
+    size_t o = 0;
+    s.e = (float *)(base + o);
+    o += align8(4 * (size_t)(n + 2));
+    s.a = (unsigned long long *)(base + o);
+    o += 8 * (size_t)(n + 1);
+    s.b = (unsigned long long *)(base + o);
+    o += 8 * (size_t)(n + 1);
+    s.cnt = (unsigned int *)(base + o);
+    o += align8(4 * (size_t)(n + 1));
+    s.heat = (float *)(base + o);
+    o += align8(4 * (size_t)n);
+    s.eedf = (unsigned int *)(base + o);
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Per-particle work of each mode.  Returns the deposit key (or -1) and the
+// fixed-point value a.
+// ---------------------------------------------------------------------------
+template <int MODE, int S>
+__device__ __forceinline__ int particle(const Run &R, const SmemMain &sm, const Species &sp,
+                                        long long idx, int &cell, float &off, float &vx,
+                                        uint32_t id, float &abar, bool diag, long long step,
+                                        Tally &t, uint32_t &a_out, bool &write) {
+    constexpr bool kMC = (MODE == kExplicitMC || MODE == kDepositMC);
+    const int N = R.n_cells;
+    write = false;
+    if (cell < 0) return -1;  // hole left by an absorbed particle
+    if (MODE == kDepositEC) return deposit_key_s2(cell, off, a_out);
+    if (MODE == kDepositMC) return deposit_key_s1(cell, off, a_out);
+
+    // ---- positions and fields of the push ----
+    float e_field;
+    float v_old = vx, v_new, s;
+    int c = cell;
+    if (MODE == kImplicit1 || MODE == kImplicit2) {
+        // predictor: v~ = v + dt abar / 2, x~ = x + dt v~
+        const float vt = fmaf(R.half_dt, abar, vx);
+        s = fmaf(vt, R.dt_dx, off);
+        if (!(fabsf(s) < 1.0e6f)) s = (float)(N + 2);  // runaway: lands outside
+        if (!(s >= 0.0f && s < 1.0f)) {
+            const float fl = floorf(s);
+            c += (int)fl;
+            s -= fl;
+            if (s >= 1.0f) {
+                s = 0.0f;
+                c += 1;
+            }
+        }
+        bool inside = true;
+        if (R.periodic) {
+            c = ((c % N) + N) % N;
+        } else if (c < 0 || c >= N) {
+            inside = false;
+        }
+        if (MODE == kImplicit1) {
+            if (!inside) return -1;  // Reading: no charge or susceptibility beyond an electrode
+            return deposit_key_s2(c, s, a_out);
+        }
+        // corrector at x~
+        e_field = 0.0f;
+        if (inside) {
+            const int j = c + (s >= 0.5f ? 1 : 0);
+            const float w1 = s >= 0.5f ? s - 0.5f : s + 0.5f;
+            e_field = (1.0f - w1) * sm.e[j] + w1 * sm.e[j + 1];
+        }
+        const float acc = R.qm[S] * e_field;
+        v_new = fmaf(R.half_dt, acc, vt);
+        if (diag && inside) atomicAdd(&sm.heat[c], R.qw[S] * e_field * 0.5f * (v_old + v_new));
+        s = fmaf(acc, R.half_dt2_dx, s);
+        abar = 0.5f * (abar + acc);
+    } else {
+        // explicit: gather at x^n, leapfrog
+        if (kMC) {
+            e_field = (1.0f - off) * sm.e[cell] + off * sm.e[cell + 1];
+        } else {
+            const int j = cell + (off >= 0.5f ? 1 : 0);
+            const float w1 = off >= 0.5f ? off - 0.5f : off + 0.5f;
+            e_field = (1.0f - w1) * sm.e[j] + w1 * sm.e[j + 1];
+        }
+        v_new = fmaf(R.qm_dt[S], e_field, vx);
+        if (diag) atomicAdd(&sm.heat[cell], R.qw[S] * e_field * 0.5f * (v_old + v_new));
+        s = fmaf(v_new, R.dt_dx, off);
+    }
+    t.kx += 0.5f * (v_old * v_old + v_new * v_new);
+    t.pw += R.qw[S] * e_field * 0.5f * (v_old + v_new);
+    if (!(fabsf(s) < 1.0e6f)) s = (float)(2 * N + 2);
+    if (!(s >= 0.0f && s < 1.0f)) {
+        const float fl = floorf(s);
+        c += (int)fl;
+        s -= fl;
+        if (s >= 1.0f) {
+            s = 0.0f;
+            c += 1;
+        }
+    }
+    vx = v_new;
+    write = true;
+    // ---- electrodes (Sec. 3) or periodic wrap ----
+    if (R.periodic) {
+        if (c < 0 || c >= N) c = ((c % N) + N) % N;
+    } else if (c < 0 || c >= N) {
+        const int wall = c < 0 ? 0 : 1;
+        const float vy = sp.vy[idx], vz = sp.vz[idx];
+        const float en = R.half_m_over_e[S] * (v_new * v_new + vy * vy + vz * vz);
+        atomicAdd(&R.st->wall_count[S][wall], 1ull);
+        atomicAdd(&R.st->wall_energy[S][wall], (double)en);
+        atomicAdd(&R.st->absorbed_step[S], 1ull);
+        cell = -1;
+        off = s;
+        return -1;
+    }
+    cell = c;
+    off = s;
+    // ---- null-collision Monte Carlo ----
+    bool have_perp = false;
+    float vy = 0.0f, vz = 0.0f;
+    if (R.mcc) {
+        const uint4 w = draw(R, id, step, S, kTagMcc, 0);
+        if ((w.x >> 8) < R.thr[S]) {
+            vy = sp.vy[idx];
+            vz = sp.vz[idx];
+            have_perp = true;
+            const bool changed = S == 0 ? collide_electron(R, w, id, step, c, s, abar, vx, vy, vz, t)
+                                        : collide_ion(R, w, id, step, vx, vy, vz, t);
+            if (changed) {
+                sp.vy[idx] = vy;
+                sp.vz[idx] = vz;
+            }
+        }
+    }
+    if (S == 0 && diag && R.eedf_bins > 0) {
+        if (!have_perp) {
+            vy = sp.vy[idx];
+            vz = sp.vz[idx];
+        }
+        const float en = R.half_m_over_e[0] * (vx * vx + vy * vy + vz * vz);
+        int bin = (int)floorf(en * R.eedf_inv_width);
+        bin = bin > R.eedf_bins ? R.eedf_bins : (bin < 0 ? 0 : bin);
+        atomicAdd(&sm.eedf[bin], 1u);
+    }
+    if (kMC) return deposit_key_s1(c, s, a_out);
+    return deposit_key_s2(c, s, a_out);
+}
+
+template <int MODE>
+struct ModeInfo {
+    static constexpr bool push = !(MODE == kDepositEC || MODE == kDepositMC || MODE == kImplicit1);
+    static constexpr bool needs_field = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit2);
+    static constexpr bool implicit = (MODE == kImplicit1 || MODE == kImplicit2);
+    static constexpr bool count_only = (MODE == kImplicit2);
+    static constexpr bool mc = (MODE == kExplicitMC || MODE == kDepositMC);
+};
+
+// Stream one species segment [b, e) through the block.
+template <int MODE, int S>
+__device__ void process_segment(const Run &R, const SmemMain &sm, const Species &sp, long long b,
+                                long long e, bool diag, long long step, Tally &t) {
+    using MI = ModeInfo<MODE>;
+    for (long long base = b; base < e; base += (long long)kThreads * kUnroll) {
+        int cell[kUnroll];
+        float off[kUnroll], vx[kUnroll], abar[kUnroll];
+        uint32_t id[kUnroll];
+        long long idx[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            idx[u] = base + (long long)u * kThreads + threadIdx.x;
+            const bool ok = idx[u] < e;
+            cell[u] = ok ? sp.cell[idx[u]] : -1;
+            off[u] = ok ? sp.off[idx[u]] : 0.0f;
+            vx[u] = (ok && MODE != kDepositEC && MODE != kDepositMC) ? sp.vx[idx[u]] : 0.0f;
+            abar[u] = (ok && MI::implicit) ? sp.abar[idx[u]] : 0.0f;
+            id[u] = (ok && MI::push && R.mcc) ? sp.id[idx[u]] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            uint32_t a = 0;
+            bool write = false;
+            const int key = particle<MODE, S>(R, sm, sp, idx[u], cell[u], off[u], vx[u], id[u],
+                                              abar[u], diag, step, t, a, write);
+            if (MI::push && write) {
+                sp.cell[idx[u]] = cell[u];
+                sp.off[idx[u]] = off[u];
+                sp.vx[idx[u]] = vx[u];
+                if (MI::implicit) sp.abar[idx[u]] = abar[u];
+            }
+            warp_deposit(key, a, sm.cnt, sm.a, sm.b, MI::count_only);
+        }
+    }
+}
+
+// Add the block's shared accumulators of one species to the run's global ones.
+__device__ void flush_species(const Run &R, const SmemMain &sm, int S, bool count_only) {
+    __syncthreads();
+    const int n1 = R.n_cells + 1;
+    for (int k = threadIdx.x; k < n1; k += kThreads) {
+        const unsigned int c = sm.cnt[k];
+        if (c) {
+            atomicAdd(&R.acc_cnt[S][k], (unsigned long long)c);
+            if (!count_only) {
+                atomicAdd(&R.acc_a[S][k], sm.a[k]);
+                atomicAdd(&R.acc_b[S][k], sm.b[k]);
+            }
+            sm.cnt[k] = 0u;
+            sm.a[k] = 0ull;
+            sm.b[k] = 0ull;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ void flush_tally(const Run &R, int S, const Tally &t, double *scratch_d,
+                            unsigned long long *scratch_u) {
+    const double kx = block_sum<double>((double)t.kx, scratch_d);
+    const double pw = block_sum<double>((double)t.pw, scratch_d);
+    unsigned long long v[6] = {t.el, t.ex, t.iz, t.cx, t.nul, t.ovf};
+    unsigned long long tot[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) tot[k] = block_sum<unsigned long long>(v[k], scratch_u);
+    if (threadIdx.x == 0) {
+        if (kx != 0.0) atomicAdd(&R.st->ke_x_acc[S], kx);
+        if (pw != 0.0) atomicAdd(&R.st->power_acc[S], pw);
+        for (int k = 0; k < 5; ++k)
+            if (tot[k]) atomicAdd(&R.st->coll[k], tot[k]);
+        if (tot[5]) atomicAdd(&R.st->overflow[S], tot[5]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tail pieces (run by the last block of a particle launch).
+// ---------------------------------------------------------------------------
+
+// Node charge of species S in units of 2^-33 macro-particle charges,
+// reassembled from the per-key sums (count c, sum a = A, sum a^2 = B):
+// node g gets 2^32 c_g + 2^17 A_g - 2 B_g from key g, B_{g-1} from key g-1 and
+// 2^32 c_{g+1} - 2^17 A_{g+1} + B_{g+1} from key g+1.  Electrodes fold the
+// ghost nodes onto the wall nodes; the periodic box wraps (key n == key 0).
+// Unsigned arithmetic: the result is exact modulo 2^64 and lies in range.
+__device__ __forceinline__ unsigned long long node_charge_s2(const Run &R, int S, int g) {
+    const int n = R.n_cells;
+    const unsigned long long *C = R.acc_cnt[S], *A = R.acc_a[S], *B = R.acc_b[S];
+    auto key_c = [&](int k) -> unsigned long long {
+        if (R.periodic) {
+            k = (k % n + n) % n;
+            return C[k] + (k == 0 ? C[n] : 0ull);
+        }
+        return (k < 0 || k > n) ? 0ull : C[k];
+    };
+    auto key_a = [&](int k) -> unsigned long long {
+        if (R.periodic) {
+            k = (k % n + n) % n;
+            return A[k] + (k == 0 ? A[n] : 0ull);
+        }
+        return (k < 0 || k > n) ? 0ull : A[k];
+    };
+    auto key_b = [&](int k) -> unsigned long long {
+        if (R.periodic) {
+            k = (k % n + n) % n;
+            return B[k] + (k == 0 ? B[n] : 0ull);
+        }
+        return (k < 0 || k > n) ? 0ull : B[k];
+    };
+    if (R.periodic && g == n) return 0ull;
+    unsigned long long q = (key_c(g) << 32) + (key_a(g) << 17) - 2ull * key_b(g) + key_b(g - 1) +
+                           (key_c(g + 1) << 32) - (key_a(g + 1) << 17) + key_b(g + 1);
+    if (!R.periodic) {
+        if (g == 0) q += (key_c(0) << 32) - (key_a(0) << 17) + key_b(0);  // ghost node -1
+        if (g == n) q += key_b(n);                                         // ghost node n+1
+    }
+    return q;
+}
+
+// S_1 node charge (momentum-conserving scheme), key = cell, value F:
+// node g gets (2^16 c_g - A_g) from cell g and A_{g-1} from cell g-1, times 2^17.
+__device__ __forceinline__ unsigned long long node_charge_s1(const Run &R, int S, int g) {
+    const int n = R.n_cells;
+    const unsigned long long *C = R.acc_cnt[S], *A = R.acc_a[S];
+    if (R.periodic && g == n) return 0ull;
+    unsigned long long q = 0;
+    if (g < n) q += (C[g] << 16) - A[g];
+    const int gl = R.periodic ? (g - 1 + n) % n : g - 1;
+    if (gl >= 0 && gl < n) q += A[gl];
+    return q << 17;
+}
+
+// Susceptibility weight of cell c (units 2^-16): a from key c, 2^16 - a from key c+1.
+__device__ __forceinline__ unsigned long long chi_count(const Run &R, int S, int c) {
+    const int n = R.n_cells;
+    const unsigned long long *C = R.acc_cnt[S], *A = R.acc_a[S];
+    unsigned long long q;
+    if (R.periodic) {
+        const unsigned long long a0 = A[c] + (c == 0 ? A[n] : 0ull);
+        const int c1 = (c + 1) % n;
+        const unsigned long long cc = C[c1] + (c1 == 0 ? C[n] : 0ull);
+        const unsigned long long a1 = A[c1] + (c1 == 0 ? A[n] : 0ull);
+        q = a0 + (cc << 16) - a1;
+    } else {
+        q = A[c] + (C[c + 1] << 16) - A[c + 1];
+    }
+    return q;
+}
+
+// Place the step's births: rank by parent id, append children at the end of
+// both species' slots with consecutive ids, assign their charge (explicit) or
+// count their keys (implicit pass 2, for the sort).
+template <int MODE>
+__device__ void tail_births(const Run &R, unsigned char *smem, bool diag) {
+    DevState *st = R.st;
+    __shared__ unsigned int s_B, s_ok;
+    __shared__ long long s_ne, s_ni;
+    if (threadIdx.x == 0) {
+        const unsigned int nb = st->n_births;
+        unsigned int B = nb;
+        if (B > (unsigned int)R.births_cap) {
+            B = (unsigned int)R.births_cap;
+            st->status |= 0x2u;
+        }
+        const long long ne = st->n_slots[0], ni = st->n_slots[1];
+        long long room = R.capacity[0] - ne;
+        if (R.capacity[1] - ni < room) room = R.capacity[1] - ni;
+        unsigned int ok = B;
+        if ((long long)ok > room) {
+            ok = room > 0 ? (unsigned int)room : 0u;
+            st->status |= 0x1u;
+        }
+        s_B = B;
+        s_ok = ok;
+        s_ne = ne;
+        s_ni = ni;
+    }
+    __syncthreads();
+    const unsigned int B = s_B, ok = s_ok;
+    if (B == 0) return;
+    // rank[b] = number of births with a smaller parent id (ids are unique)
+    uint32_t *pid_chunk = (uint32_t *)smem;  // 2048 entries
+    unsigned int *rank = (unsigned int *)(R.births + R.births_cap);  // scratch after the records
+    for (unsigned int b = threadIdx.x; b < B; b += kThreads) rank[b] = 0u;
+    for (unsigned int c0 = 0; c0 < B; c0 += 2048u) {
+        const unsigned int cn = min(2048u, B - c0);
+        __syncthreads();
+        for (unsigned int k = threadIdx.x; k < cn; k += kThreads) pid_chunk[k] = R.births[c0 + k].pid;
+        __syncthreads();
+        for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
+            const uint32_t p = R.births[b].pid;
+            unsigned int r = 0;
+            for (unsigned int k = 0; k < cn; ++k) r += pid_chunk[k] < p ? 1u : 0u;
+            rank[b] += r;
+        }
+    }
+    __syncthreads();
+    const int par = st->parity;
+    const Species se = R.buf[par][0], si = R.buf[par][1];
+    const unsigned int id_e = st->next_id[0], id_i = st->next_id[1];
+    for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
+        const unsigned int r = rank[b];
+        if (r >= ok) continue;
+        const Birth bb = R.births[b];
+        const long long je = s_ne + r, ji = s_ni + r;
+        se.cell[je] = bb.cell;
+        se.off[je] = bb.off;
+        se.vx[je] = bb.ve[0];
+        se.vy[je] = bb.ve[1];
+        se.vz[je] = bb.ve[2];
+        se.id[je] = id_e + r;
+        si.cell[ji] = bb.cell;
+        si.off[ji] = bb.off;
+        si.vx[ji] = bb.vi[0];
+        si.vy[ji] = bb.vi[1];
+        si.vz[ji] = bb.vi[2];
+        si.id[ji] = id_i + r;
+        if (R.scheme == 2) {
+            se.abar[je] = bb.abar_e;
+            si.abar[ji] = bb.abar_e * R.abar_ion_over_e;
+        }
+        uint32_t a;
+        const bool mc = MODE == kExplicitMC;
+        const int key = mc ? deposit_key_s1(bb.cell, bb.off, a) : deposit_key_s2(bb.cell, bb.off, a);
+        for (int S = 0; S < 2; ++S) {
+            atomicAdd(&R.acc_cnt[S][key], 1ull);
+            if (MODE != kImplicit2) {
+                atomicAdd(&R.acc_a[S][key], (unsigned long long)a);
+                atomicAdd(&R.acc_b[S][key], (unsigned long long)a * a);
+            }
+        }
+        if (diag && R.eedf_bins > 0) {
+            const float en = R.half_m_over_e[0] *
+                             (bb.ve[0] * bb.ve[0] + bb.ve[1] * bb.ve[1] + bb.ve[2] * bb.ve[2]);
+            int bin = (int)floorf(en * R.eedf_inv_width);
+            bin = bin > R.eedf_bins ? R.eedf_bins : (bin < 0 ? 0 : bin);
+            atomicAdd(&R.eedf[bin], 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->n_slots[0] += ok;
+        st->n_slots[1] += ok;
+        st->n_live[0] += ok;
+        st->n_live[1] += ok;
+        st->next_id[0] += ok;
+        st->next_id[1] += ok;
+        st->births_total += ok;
+    }
+    __syncthreads();
+}
+
+// Field solve by the discrete Gauss law.  The finite-difference Poisson
+// equation -(phi_{g-1} - 2 phi_g + phi_{g+1})/dx^2 = rho_g/eps0 (with (1+chi)
+// on the cell faces in the implicit scheme) is D_{c} - D_{c-1} = dx rho_c / eps0
+// for the face quantity D_c = (1 + chi_c) E_c, E_c = (phi_c - phi_{c+1})/dx.
+// So D_c = D_0 + kappa P_c with the exact int64 prefix sum P_c of the node
+// charge; the electrode condition sum_c E_c dx = V(t) (or zero mean field in
+// the periodic box) fixes D_0.  O(n) work, O(log n) depth; the same linear
+// system the oracle solves with the Thomas algorithm.
+template <int MODE>
+__device__ void tail_field(const Run &R, unsigned char *smem, long long level, bool accumulate) {
+    DevState *st = R.st;
+    const int n = R.n_cells;
+    __shared__ long long sc_ll[33];
+    __shared__ double sc_d[33];
+    long long *q = (long long *)smem;               // [n+1] net node charge
+    double *rinv = (double *)(smem + 8 * (n + 1));   // [n] 1/(1+chi)
+    double *ef = rinv + n;                           // [n] face field E_c
+    double *pp = ef + n;                             // [n] kappa P_c (+ background)
+    constexpr bool mc = ModeInfo<MODE>::mc;
+    constexpr bool implicit = ModeInfo<MODE>::implicit;
+    // node charges, densities, susceptibility
+    for (int g = threadIdx.x; g <= n; g += kThreads) {
+        const unsigned long long ne = mc ? node_charge_s1(R, 0, g) : node_charge_s2(R, 0, g);
+        const unsigned long long ni = mc ? node_charge_s1(R, 1, g) : node_charge_s2(R, 1, g);
+        q[g] = (long long)(ni - ne);
+        R.rho_q[0][g] = (long long)ne;
+        R.rho_q[1][g] = (long long)ni;
+        if (accumulate) {
+            R.avg_ne[g] += R.dens_scale * (double)(long long)ne;
+            R.avg_ni[g] += R.dens_scale * (double)(long long)ni;
+        }
+    }
+    for (int c = threadIdx.x; c < n; c += kThreads) {
+        double chi = 0.0;
+        if (implicit) {
+            chi = R.chi_coef[0] * (double)chi_count(R, 0, c) + R.chi_coef[1] * (double)chi_count(R, 1, c);
+            R.chi[c] = chi;
+        }
+        rinv[c] = 1.0 / (1.0 + chi);
+    }
+    __syncthreads();
+    // P_c: inclusive prefix of the interior node charges (all nodes when periodic)
+    const int per = (n + kThreads - 1) / kThreads;
+    const int c_begin = threadIdx.x * per;
+    long long local[8];
+    long long run = 0;
+    for (int k = 0; k < per; ++k) {
+        const int c = c_begin + k;
+        long long v = 0;
+        if (c < n) v = (R.periodic || c >= 1) ? q[c] : 0;
+        run += v;
+        local[k] = run;
+    }
+    long long total_q;
+    const long long excl = block_exclusive_scan<long long>(run, sc_ll, total_q);
+    const double qbar = R.periodic ? (double)total_q / (double)n : 0.0;
+    double s1 = 0.0, s0 = 0.0;
+    for (int k = 0; k < per; ++k) {
+        const int c = c_begin + k;
+        if (c < n) {
+            const long long P = excl + local[k];
+            double v;
+            if (R.periodic)
+                v = R.kappa * ((double)P - (double)(c + 1) * qbar);
+            else
+                v = R.kappa * (double)P + R.kappa_bg * (double)c;
+            pp[c] = v;
+            s1 += rinv[c] * v;
+            s0 += rinv[c];
+        }
+    }
+    s1 = block_sum<double>(s1, sc_d);
+    s0 = block_sum<double>(s0, sc_d);
+    double v_left = 0.0;
+    if (!R.periodic) {
+        const double t = (double)level * R.dt;
+        v_left = R.rf_volt * sin(2.0 * 3.14159265358979323846 * R.rf_freq * t);
+    }
+    const double d0 = R.periodic ? -s1 / s0 : (v_left / R.dx - s1) / s0;
+    double wsum = 0.0, esum = 0.0;
+    for (int k = 0; k < per; ++k) {
+        const int c = c_begin + k;
+        if (c < n) {
+            const double e = rinv[c] * (d0 + pp[c]);
+            ef[c] = e;
+            R.e_cc[c] = e;
+            wsum += e * e;
+            esum += e;
+        }
+    }
+    // phi_g = phi_0 - dx sum_{c<g} E_c
+    double etot;
+    const double eprefix = block_exclusive_scan<double>(esum, sc_d, etot);
+    wsum = block_sum<double>(wsum, sc_d);
+    {
+        double acc = eprefix;
+        for (int k = 0; k < per; ++k) {
+            const int g = c_begin + k;
+            if (g < n) {
+                const double ph = v_left - R.dx * acc;
+                R.phi[g] = ph;
+                if (accumulate) R.avg_phi[g] += ph;
+                acc += ef[g];
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        R.phi[n] = R.periodic ? v_left : 0.0;  // grounded electrode / periodic image of node 0
+        if (accumulate) R.avg_phi[n] += R.phi[n];
+        if (MODE == kExplicitEC || MODE == kExplicitMC) st->field_energy_push = st->field_energy;
+        st->field_energy = R.eps0_dx_half * wsum;
+        if (MODE == kImplicit1) st->field_energy_push = st->field_energy;
+    }
+    __syncthreads();
+    // gather tables
+    if (mc) {
+        for (int g = threadIdx.x; g <= n; g += kThreads) {
+            double e;
+            if (R.periodic) {
+                const int gl = (g - 1 + n) % n, gr = (g + 1) % n;
+                e = (R.phi[gl] - R.phi[gr]) / (2.0 * R.dx);
+            } else if (g == 0) {
+                e = (R.phi[0] - R.phi[1]) / R.dx;
+            } else if (g == n) {
+                e = (R.phi[n - 1] - R.phi[n]) / R.dx;
+            } else {
+                e = (R.phi[g - 1] - R.phi[g + 1]) / (2.0 * R.dx);
+            }
+            R.e_gather[g] = (float)e;
+        }
+        if (threadIdx.x == 0 && R.periodic) R.e_gather[n] = R.e_gather[0];
+    } else {
+        for (int c = threadIdx.x; c < n; c += kThreads) R.e_gather[c + 1] = (float)ef[c];
+        if (threadIdx.x == 0) {
+            R.e_gather[0] = R.periodic ? (float)ef[n - 1] : 0.0f;
+            R.e_gather[n + 1] = R.periodic ? (float)ef[0] : 0.0f;
+        }
+    }
+    __syncthreads();
+}
+
+// Sort cursors (exclusive prefix of the per-key counts) and reset of the
+// per-step accumulators.
+__device__ void tail_cursors_and_reset(const Run &R) {
+    __shared__ unsigned long long sc_u[33];
+    const int n1 = R.n_cells + 1;
+    const int per = (n1 + kThreads - 1) / kThreads;
+    for (int S = 0; S < 2; ++S) {
+        const int b0 = threadIdx.x * per;
+        unsigned long long run = 0;
+        for (int k = 0; k < per; ++k)
+            if (b0 + k < n1) run += R.acc_cnt[S][b0 + k];
+        unsigned long long tot;
+        unsigned long long ex = block_exclusive_scan<unsigned long long>(run, sc_u, tot);
+        for (int k = 0; k < per; ++k) {
+            const int j = b0 + k;
+            if (j < n1) {
+                R.cursor[S][j] = (unsigned int)ex;
+                ex += R.acc_cnt[S][j];
+            }
+        }
+    }
+    __syncthreads();
+    for (int S = 0; S < 2; ++S)
+        for (int k = threadIdx.x; k < n1; k += kThreads) {
+            R.acc_cnt[S][k] = 0ull;
+            R.acc_a[S][k] = 0ull;
+            R.acc_b[S][k] = 0ull;
+        }
+}
+
+template <int MODE>
+__device__ void tail(const Run &R, unsigned char *smem, bool diag) {
+    DevState *st = R.st;
+    const long long step = st->step;
+    if (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit2) tail_births<MODE>(R, smem, diag);
+    if (MODE == kExplicitEC || MODE == kExplicitMC) tail_field<MODE>(R, smem, step + 1, true);
+    if (MODE == kImplicit1) tail_field<MODE>(R, smem, step + 1, true);
+    if (MODE == kDepositEC || MODE == kDepositMC) tail_field<MODE>(R, smem, step, false);
+    if (MODE == kImplicit1) {
+        // pass 1 keeps nothing else; reset its accumulators for pass 2's key counts
+        const int n1 = R.n_cells + 1;
+        __syncthreads();
+        for (int S = 0; S < 2; ++S)
+            for (int k = threadIdx.x; k < n1; k += kThreads) {
+                R.acc_cnt[S][k] = 0ull;
+                R.acc_a[S][k] = 0ull;
+                R.acc_b[S][k] = 0ull;
+            }
+    } else {
+        tail_cursors_and_reset(R);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (ModeInfo<MODE>::push) {
+            for (int S = 0; S < 2; ++S) {
+                st->ke_x[S] = st->ke_x_acc[S];
+                st->power[S] = st->power_acc[S];
+                st->ke_x_acc[S] = 0.0;
+                st->power_acc[S] = 0.0;
+                st->n_live[S] -= (long long)st->absorbed_step[S];
+                st->absorbed_step[S] = 0ull;
+            }
+            st->step = step + 1;
+            st->n_avg += 1;
+            if (diag) st->n_diag += 1;
+        }
+        st->n_births = 0u;
+        st->blocks_done = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The particle kernel: one launch per explicit step / implicit pass / deposit.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_particles(Run R) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double sc_d[33];
+    __shared__ unsigned long long sc_u[33];
+    __shared__ bool s_last;
+    using MI = ModeInfo<MODE>;
+    DevState *st = R.st;
+    const int n = R.n_cells;
+    const SmemMain sm = carve_main(smem, n, R.eedf_bins);
+    const long long step = st->step;
+    const bool diag = MI::push && R.diag_period > 0 && (step % R.diag_period) == 0;
+    const int par = st->parity;
+    const long long ne = st->n_slots[0];
+    const long long ni = R.ions_mobile ? st->n_slots[1] : 0;
+    const long long total = ne + ni;
+    const long long G = gridDim.x;
+    long long ch = (total + G - 1) / G;
+    ch = (ch + 31) & ~31ll;
+    const long long c0 = (long long)blockIdx.x * ch;
+    const long long c1 = c0 + ch < total ? c0 + ch : total;
+    // shared-memory grid
+    if (MI::needs_field)
+        for (int k = threadIdx.x; k < n + 2; k += kThreads) sm.e[k] = R.e_gather[k];
+    for (int k = threadIdx.x; k <= n; k += kThreads) {
+        sm.cnt[k] = 0u;
+        sm.a[k] = 0ull;
+        sm.b[k] = 0ull;
+    }
+    if (diag) {
+        for (int k = threadIdx.x; k < n; k += kThreads) sm.heat[k] = 0.0f;
+        for (int k = threadIdx.x; k <= R.eedf_bins; k += kThreads) sm.eedf[k] = 0u;
+    }
+    __syncthreads();
+    for (int S = 0; S < 2; ++S) {
+        long long b, e;
+        if (S == 0) {
+            b = c0;
+            e = c1 < ne ? c1 : ne;
+        } else {
+            b = (c0 > ne ? c0 : ne) - ne;
+            e = c1 - ne;
+        }
+        if (b >= e) continue;  // uniform across the block
+        Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
+        const Species sp = R.buf[par][S];
+        if (S == 0)
+            process_segment<MODE, 0>(R, sm, sp, b, e, diag, step, t);
+        else
+            process_segment<MODE, 1>(R, sm, sp, b, e, diag, step, t);
+        flush_species(R, sm, S, MI::count_only);
+        if (MI::push) flush_tally(R, S, t, sc_d, sc_u);
+        if (diag) {
+            __syncthreads();
+            for (int k = threadIdx.x; k < n; k += kThreads) {
+                const float h = sm.heat[k];
+                if (h != 0.0f) atomicAdd(&R.heat[S][k], (double)h / R.dx);
+                sm.heat[k] = 0.0f;
+            }
+            __syncthreads();
+        }
+    }
+    if (diag) {
+        for (int k = threadIdx.x; k <= R.eedf_bins; k += kThreads)
+            if (sm.eedf[k]) atomicAdd(&R.eedf[k], (unsigned long long)sm.eedf[k]);
+    }
+    // last block runs the tail
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    tail<MODE>(R, smem, diag);
+}
+
+// ---------------------------------------------------------------------------
+// Counting sort by deposit key (nearest node for S_2, cell for S_1): the
+// cursors were prepared by the previous tail; live particles are scattered
+// into the other buffer, holes are dropped.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_sort(Run R) {
+    __shared__ bool s_last;
+    DevState *st = R.st;
+    const int par = st->parity;
+    const bool mc = R.scheme == 1;
+    const long long ne = st->n_slots[0];
+    const long long ni = R.ions_mobile ? st->n_slots[1] : 0;
+    const long long total = ne + ni;
+    const long long G = gridDim.x;
+    long long ch = (total + G - 1) / G;
+    ch = (ch + 31) & ~31ll;
+    const long long c0 = (long long)blockIdx.x * ch;
+    const long long c1 = c0 + ch < total ? c0 + ch : total;
+    const int lane = threadIdx.x & 31;
+    for (int S = 0; S < 2; ++S) {
+        long long b, e;
+        if (S == 0) {
+            b = c0;
+            e = c1 < ne ? c1 : ne;
+        } else {
+            b = (c0 > ne ? c0 : ne) - ne;
+            e = c1 - ne;
+        }
+        if (b >= e) continue;
+        const Species src = R.buf[par][S], dst = R.buf[par ^ 1][S];
+        for (long long base = b; base < e; base += kThreads) {
+            const long long i = base + threadIdx.x;
+            int cell = i < e ? src.cell[i] : -1;
+            float off = i < e ? src.off[i] : 0.0f;
+            uint32_t a;
+            int key = cell < 0 ? -1 : (mc ? deposit_key_s1(cell, off, a) : deposit_key_s2(cell, off, a));
+            const unsigned int live = __ballot_sync(FULL_MASK, key >= 0);
+            const unsigned int peers = __match_any_sync(FULL_MASK, key);
+            unsigned int pos = 0;
+            if (key >= 0) {
+                const int leader = __ffs(peers) - 1;
+                const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
+                unsigned int base_pos = 0;
+                if (lane == leader) base_pos = atomicAdd(&R.cursor[S][key], (unsigned int)__popc(peers));
+                base_pos = __shfl_sync(peers, base_pos, leader);
+                pos = base_pos + rank;
+            }
+            (void)live;
+            if (key >= 0) {
+                dst.cell[pos] = cell;
+                dst.off[pos] = off;
+                dst.vx[pos] = src.vx[i];
+                dst.vy[pos] = src.vy[i];
+                dst.vz[pos] = src.vz[i];
+                dst.id[pos] = src.id[i];
+                if (R.scheme == 2) dst.abar[pos] = src.abar[i];
+            }
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->sort_blocks_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        st->parity = par ^ 1;
+        st->n_slots[0] = st->n_live[0];
+        st->n_slots[1] = st->n_live[1];
+        st->sort_blocks_done = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Uniform Maxwellian load (Sec. 3: the gap is filled uniformly at t = 0).
+// Position in cell units = w0 * n / 2^32, cut to 24 fractional bits (exact in
+// the FP32 offset); velocities from two Box-Muller pairs.
+// ---------------------------------------------------------------------------
+__global__ void k_load(Run R, int S, long long count, float vth) {
+    const Species sp = R.buf[0][S];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint4 w = draw(R, (uint32_t)i, 0, S, kTagLoad, 0);
+        const uint4 w2 = draw(R, (uint32_t)i, 0, S, kTagLoad, 1);
+        const unsigned long long t = (unsigned long long)w.x * (unsigned long long)R.n_cells;
+        sp.cell[i] = (int32_t)(t >> 32);
+        sp.off[i] = (float)((uint32_t)t >> 8) * 5.9604644775390625e-8f;
+        float n1, n2, n3, n4;
+        box_muller(u24(w.y), u24(w.z), n1, n2);
+        box_muller(u24(w.w), u24(w2.x), n3, n4);
+        sp.vx[i] = vth * n1;
+        sp.vy[i] = vth * n2;
+        sp.vz[i] = vth * n3;
+        sp.id[i] = (uint32_t)i;
+        if (R.scheme == 2) sp.abar[i] = 0.0f;
+    }
+}
+
+// abar = (q/m) E(x) for the implicit scheme's first step.
+__global__ void k_set_abar(Run R) {
+    const DevState *st = R.st;
+    const int par = st->parity;
+    for (int S = 0; S < 2; ++S) {
+        const Species sp = R.buf[par][S];
+        const long long n = st->n_slots[S];
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            const int cell = sp.cell[i];
+            if (cell < 0) continue;
+            const float off = sp.off[i];
+            const int j = cell + (off >= 0.5f ? 1 : 0);
+            const float w1 = off >= 0.5f ? off - 0.5f : off + 0.5f;
+            const float e = (1.0f - w1) * R.e_gather[j] + w1 * R.e_gather[j + 1];
+            sp.abar[i] = R.qm[S] * e;
+        }
+    }
+}
+
+// Kinetic energy of the transverse velocities (diagnostics only).
+__global__ void k_perp_energy(Run R) {
+    __shared__ double sc[33];
+    const DevState *st = R.st;
+    const int par = st->parity;
+    for (int S = 0; S < 2; ++S) {
+        const Species sp = R.buf[par][S];
+        const long long n = st->n_slots[S];
+        double acc = 0.0;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            if (sp.cell[i] < 0) continue;
+            const float vy = sp.vy[i], vz = sp.vz[i];
+            acc += (double)(vy * vy + vz * vz);
+        }
+        const double tot = block_sum<double>(acc, sc);
+        if (threadIdx.x == 0 && tot != 0.0) atomicAdd(&R.st->ke_perp[S], tot * R.half_m_w[S]);
+    }
+}
+
+__global__ void k_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
+                              uint32_t c3, long long n, uint32_t *out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint4 w = philox4x32_10(make_uint4(c0 + (uint32_t)i, c1, c2, c3), k0, k1);
+        reinterpret_cast<uint4 *>(out)[i] = w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+int block_smem_bytes(const Run &r) {
+    const size_t a = main_smem_bytes(r.n_cells, r.eedf_bins);
+    const size_t b = tail_smem_bytes(r.n_cells);
+    return (int)(a > b ? a : b);
+}
+
+// The dynamic shared-memory limit of every mode is raised once by
+// occupancy_grid() before any launch (never during stream capture).
+template <int MODE>
+static cudaError_t launch_mode(const Run &r, int grid, cudaStream_t s) {
+    const int smem = block_smem_bytes(r);
+    k_particles<MODE><<<grid, kThreads, smem, s>>>(r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_particles(const Run &r, Mode m, int grid, cudaStream_t s) {
+    switch (m) {
+        case kExplicitEC: return launch_mode<kExplicitEC>(r, grid, s);
+        case kExplicitMC: return launch_mode<kExplicitMC>(r, grid, s);
+        case kDepositEC: return launch_mode<kDepositEC>(r, grid, s);
+        case kDepositMC: return launch_mode<kDepositMC>(r, grid, s);
+        case kImplicit1: return launch_mode<kImplicit1>(r, grid, s);
+        case kImplicit2: return launch_mode<kImplicit2>(r, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int MODE>
+static cudaError_t occ(const Run &r, int *per_sm) {
+    const int smem = block_smem_bytes(r);
+    cudaError_t e = cudaFuncSetAttribute(k_particles<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_particles<MODE>, kThreads, smem);
+}
+
+cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
+    int dev = 0, sms = 0, per = 1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < 6; ++k) {  // raise the shared-memory limit of every mode
+        int dummy = 0;
+        switch (k) {
+            case 0: e = occ<kExplicitEC>(r, &dummy); break;
+            case 1: e = occ<kExplicitMC>(r, &dummy); break;
+            case 2: e = occ<kDepositEC>(r, &dummy); break;
+            case 3: e = occ<kDepositMC>(r, &dummy); break;
+            case 4: e = occ<kImplicit1>(r, &dummy); break;
+            default: e = occ<kImplicit2>(r, &dummy); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    switch (m) {
+        case kExplicitEC: e = occ<kExplicitEC>(r, &per); break;
+        case kExplicitMC: e = occ<kExplicitMC>(r, &per); break;
+        case kDepositEC: e = occ<kDepositEC>(r, &per); break;
+        case kDepositMC: e = occ<kDepositMC>(r, &per); break;
+        case kImplicit1: e = occ<kImplicit1>(r, &per); break;
+        case kImplicit2: e = occ<kImplicit2>(r, &per); break;
+    }
+    if (e != cudaSuccess) return e;
+    *grid = sms * (per > 0 ? per : 1);
+    return cudaSuccess;
+}
+
+cudaError_t launch_sort(const Run &r, int grid, cudaStream_t s) {
+    k_sort<<<grid, kThreads, 0, s>>>(r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_abar(const Run &r, cudaStream_t s) {
+    k_set_abar<<<1024, kThreads, 0, s>>>(r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_perp_energy(const Run &r, cudaStream_t s) {
+    k_perp_energy<<<1024, kThreads, 0, s>>>(r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
+                               uint32_t c3, long long n, uint32_t *out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_philox_fill<<<1024, kThreads, 0, s>>>(k0, k1, c0, c1, c2, c3, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load(const Run &r, int species, long long n, float vth, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_load<<<1024, kThreads, 0, s>>>(r, species, n, vth);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

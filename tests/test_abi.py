@@ -1,0 +1,94 @@
+"""The C-ABI library loads and exports every entry point include/pic.h
+declares; host-side configuration checks (no GPU needed, no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def abi():
+    from paper_1310_5284_gb300 import build
+    build()
+    from paper_1310_5284_gb300 import _abi
+    return _abi
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pic_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(abi):
+    names = declared_functions()
+    assert len(names) >= 19
+    lib = ctypes.CDLL(abi.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+    # the binding declares exactly the header's entry points
+    assert set(abi.SIGNATURES) == set(names)
+
+
+def test_version_and_build_info(abi):
+    assert abi.lib().pic_version() == 1
+    assert b"sm_103a" in abi.lib().pic_build_info()
+
+
+def _sizes(abi, cfg):
+    from paper_1310_5284_gb300.sim import make_config
+    c = make_config(cfg)
+    s = abi.PicSizes()
+    code = abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s))
+    return code, s
+
+
+def test_required_sizes_scale_with_capacity(abi):
+    code, s1 = _sizes(abi, dict(workloads.CFG_SMALL_CCP))
+    assert code == 0 and s1.arena_bytes > 0 and s1.snapshot_bytes > s1.arena_bytes
+    code, s2 = _sizes(abi, dict(workloads.CFG_SMALL_CCP, capacity=100_000))
+    assert code == 0
+    # two buffers x two species x six 4-byte fields per extra slot
+    extra = s2.arena_bytes - s1.arena_bytes
+    assert extra >= 2 * 6 * 4 * (100_000 - 25_600)
+
+
+def test_strict_mode_rejects_unstable_leapfrog(abi):
+    # Eq. (1): omega_p dt < 2.  At n0 = 1.03e17 and dt = 1/(400 f), omega_p dt = 3.3
+    cfg = dict(workloads.CFG_WIDE_EXPLICIT, dt=1.0 / (400 * 13.56e6), strict=True)
+    code, _ = _sizes(abi, cfg)
+    assert code == -2
+    assert b"Eq. (1)" in abi.lib().pic_last_error(None)
+    cfg["strict"] = False
+    assert _sizes(abi, cfg)[0] == 0
+    # the implicit scheme is exempt
+    assert _sizes(abi, dict(cfg, scheme="ec_implicit", strict=True))[0] == 0
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(n_cells=1), -1), (dict(n_cells=2048), -1), (dict(capacity=1 << 29), -4),
+    (dict(np_init=0), -1), (dict(dt=0.0), -1), (dict(eedf_bins=0), -1),
+    (dict(ions_mobile=False), -1),  # collisions need mobile ions
+])
+def test_invalid_configs_are_rejected(abi, bad, code):
+    cfg = dict(workloads.CFG_SMALL_CCP)
+    cfg.update(bad)
+    assert _sizes(abi, cfg)[0] == code
+
+
+def test_init_rejects_small_or_misaligned_arena(abi):
+    from paper_1310_5284_gb300.sim import make_config
+    c = make_config(dict(workloads.CFG_SMALL_CCP))
+    s = abi.PicSizes()
+    abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s))
+    h = ctypes.c_void_p()
+    small = abi.PicBuffers(256, s.arena_bytes - 1)
+    assert abi.lib().pic_init(ctypes.byref(c), ctypes.byref(small), None, ctypes.byref(h)) == -3
+    odd = abi.PicBuffers(256 + 8, s.arena_bytes)
+    assert abi.lib().pic_init(ctypes.byref(c), ctypes.byref(odd), None, ctypes.byref(h)) == -3
+    assert not h.value

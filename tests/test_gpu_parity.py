@@ -1,0 +1,269 @@
+"""GPU path (libpic.so through its C ABI) against the CPU oracle, element by
+element on the same seeded inputs.
+
+Bars (written in each test):
+* integer work bit-exact: Philox words, the uniform load's cells and
+  offsets, the int64 node charge of an injected state, particle counts,
+  collision / birth / wall tallies on the same Philox stream;
+* floating point within the stated tolerance: positions |dx| <= 1e-5 L and
+  velocities |dv| <= 1e-5 max(|v|, v_th) per particle after up to 100 steps
+  (FP32 push against the FP64 oracle), fields within 1e-9 of their scale.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+E = 1.602176634e-19
+ME = 9.1093837015e-31
+AMU = 1.66053906660e-27
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def gpu_sim(cfg):
+    from paper_1310_5284_gb300.sim import Sim
+    return Sim(cfg, device="cuda:0")
+
+
+def vth(cfg, k):
+    m = ME if k == 0 else cfg.get("ion_mass_amu", 39.948) * AMU
+    t = cfg.get("te_ev", 2.0) if k == 0 else cfg.get("ti_ev", 0.026)
+    return math.sqrt(E * t / m)
+
+
+def inject(gpu, orc, cfg, states, step=0, abar=None):
+    """Same seeded state into both: the GPU gets the storage form, the oracle
+    the exact FP64 values of it (position in cell units = cell + offset)."""
+    for k, sp in enumerate(("e", "i")):
+        s = states[k]
+        if s is None:
+            continue
+        ab = None if abar is None else abar[k]
+        gpu.set_particles(sp, dict(s, abar=ab), next_id=int(s["id"].max()) + 1 if len(s["id"]) else 0)
+        orc.set_species(sp, workloads.xi_of(s), s["vx"].astype(np.float64), s["vy"].astype(np.float64),
+                        s["vz"].astype(np.float64), s["id"], abar=None if ab is None else ab.astype(np.float64),
+                        next_id=int(s["id"].max()) + 1 if len(s["id"]) else 0)
+    gpu.set_step(step)
+    orc.set_step(step)
+    gpu.init_field(set_abar=abar is None)
+    orc.init_field(set_abar=abar is None)
+
+
+def states_for(cfg, n, seed, sorted_cells=False, ions=True):
+    st_e = workloads.injected_particles(seed, n, cfg["n_cells"], vth(cfg, 0), sorted_cells=sorted_cells)
+    st_i = workloads.injected_particles(seed + 1, n, cfg["n_cells"], vth(cfg, 1), sorted_cells=sorted_cells) if ions else None
+    return [st_e, st_i]
+
+
+def by_id(d, xi_key=None):
+    o = np.argsort(d["id"])
+    return {k: (v[o] if isinstance(v, np.ndarray) else v) for k, v in d.items()}
+
+
+def compare_particles(gpu, orc, cfg, tol=1e-5, species=("e", "i")):
+    L_cells = cfg["n_cells"]
+    for k, sp in enumerate(species):
+        a = by_id(gpu.get_particles(sp))
+        b = by_id(orc.get_species(sp))
+        assert np.array_equal(a["id"], b["id"]), "particle sets differ (%s)" % sp
+        if len(a["id"]) == 0:
+            continue
+        xa = a["cell"].astype(np.float64) + a["off"].astype(np.float64)
+        dxi = np.abs(xa - b["xi"])
+        if cfg.get("periodic"):
+            dxi = np.minimum(dxi, L_cells - dxi)
+        assert dxi.max() <= tol * L_cells, ("x", sp, dxi.max())
+        vs = vth(cfg, k)
+        for comp in ("vx", "vy", "vz"):
+            dv = np.abs(a[comp].astype(np.float64) - b[comp])
+            bound = tol * np.maximum(np.abs(b[comp]), vs)
+            assert np.all(dv <= bound), (comp, sp, float((dv / bound).max()))
+
+
+# ------------------------------------------------------------------ Philox
+def test_philox_words_bitexact_vs_oracle():
+    import torch
+    from paper_1310_5284_gb300.sim import philox_fill
+    for key, ctr in (((1, 0), (0, 0, 0, 0)), ((0xDEADBEEF, 17), (123456, 99, 7, 0x01020001)),
+                     ((2 ** 32 - 1, 2 ** 32 - 1), (2 ** 32 - 1000, 2 ** 32 - 1, 2 ** 32 - 1, 2 ** 32 - 1))):
+        n = 200_003
+        out = torch.zeros(4 * n, dtype=torch.int32, device="cuda:0")
+        philox_fill(key, ctr, n, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32).reshape(n, 4)
+        ref = oracle.philox_stream(key, ctr, n)
+        assert np.array_equal(got, ref)
+
+
+# ------------------------------------------------------------------ load
+def test_uniform_load_matches_oracle():
+    cfg = dict(workloads.CFG_SMALL_CCP, mcc=False)
+    gpu = gpu_sim(cfg)
+    orc = oracle.Sim(cfg).load(cfg["np_init"], cfg["np_init"])
+    for k, sp in enumerate(("e", "i")):
+        a = by_id(gpu.get_particles(sp))
+        b = by_id(orc.get_species(sp))
+        assert np.array_equal(a["id"], np.arange(cfg["np_init"]))
+        xa = a["cell"].astype(np.float64) + a["off"].astype(np.float64)
+        assert np.array_equal(xa, b["xi"])  # positions are exact (24-bit offsets)
+        for comp in ("vx", "vy", "vz"):
+            np.testing.assert_allclose(a[comp], b[comp], rtol=2e-6, atol=2e-6 * vth(cfg, k))
+    g, o = gpu.grids(), orc.grids()
+    assert np.array_equal(g["rho_q_e"], o["rho_q_e"]) and np.array_equal(g["rho_q_i"], o["rho_q_i"])
+
+
+# ------------------------------------------------------------------ deposit + field
+DEPOSIT_CASES = [
+    ("ec_dirichlet_64", dict(n_cells=64), 12_800, False),
+    ("ec_dirichlet_ragged_77", dict(n_cells=77), 12_345, False),
+    ("ec_periodic_100", dict(n_cells=100, periodic=True, rf_volt=0.0), 10_007, False),
+    ("ec_dirichlet_1024_sorted", dict(n_cells=1024), 300_001, True),
+    ("mc_dirichlet_64", dict(n_cells=64, scheme="mc_explicit"), 9_999, False),
+    ("mc_periodic_33", dict(n_cells=33, periodic=True, scheme="mc_explicit", rf_volt=0.0), 4_321, False),
+    ("ec_tiny_2cells", dict(n_cells=2), 5, False),
+]
+
+
+@pytest.mark.parametrize("name,over,n,srt", DEPOSIT_CASES, ids=[c[0] for c in DEPOSIT_CASES])
+def test_deposit_bitexact_and_field(name, over, n, srt):
+    cfg = dict(workloads.CFG_SMALL_CCP, mcc=False, np_init=n)
+    cfg.update(over)
+    gpu = gpu_sim(cfg)
+    orc = oracle.Sim(cfg, cap_e=n + 16, cap_i=n + 16)
+    inject(gpu, orc, cfg, states_for(cfg, n, 100 + n, sorted_cells=srt), step=37)
+    g, o = gpu.grids(), orc.grids()
+    assert np.array_equal(g["rho_q_e"], o["rho_q_e"]), name
+    assert np.array_equal(g["rho_q_i"], o["rho_q_i"]), name
+    assert g["rho_q_e"].sum() == n * 2 ** 33 and g["rho_q_i"].sum() == n * 2 ** 33
+    scale = max(np.abs(o["e_cc"]).max(), 1e-300)
+    np.testing.assert_allclose(g["e_cc"], o["e_cc"], rtol=0, atol=1e-9 * scale)
+    pscale = max(np.abs(o["phi"]).max(), 1e-300)
+    np.testing.assert_allclose(g["phi"], o["phi"], rtol=0, atol=1e-9 * pscale)
+
+
+def test_empty_species_and_frozen_ion_background():
+    cfg = workloads.cfg_periodic(n_cells=64, np_e=5000, n0=1e15, length=0.02, dt=5e-11)
+    gpu = gpu_sim(cfg)
+    orc = oracle.Sim(cfg, cap_e=6000, cap_i=16)
+    st = states_for(cfg, 5000, 7, ions=False)
+    inject(gpu, orc, cfg, st)
+    g, o = gpu.grids(), orc.grids()
+    assert np.array_equal(g["rho_q_e"], o["rho_q_e"])
+    assert not g["rho_q_i"].any()
+    np.testing.assert_allclose(g["e_cc"], o["e_cc"], atol=1e-9 * np.abs(o["e_cc"]).max())
+    # Dirichlet with a frozen ion density (the sheath case of the adjoint workload)
+    cfg2 = dict(workloads.CFG_SMALL_CCP, mcc=False, ions_mobile=False, bg_density=2e15, np_init=5000)
+    gpu2 = gpu_sim(cfg2)
+    orc2 = oracle.Sim(cfg2, cap_e=6000, cap_i=16)
+    inject(gpu2, orc2, cfg2, [st[0], None])
+    g2, o2 = gpu2.grids(), orc2.grids()
+    np.testing.assert_allclose(g2["phi"], o2["phi"], atol=1e-9 * np.abs(o2["phi"]).max())
+
+
+# ------------------------------------------------------------------ whole steps
+STEP_CASES = [
+    ("ec_periodic_collisionless", dict(n_cells=64, periodic=True, mcc=False, rf_volt=0.0), 100),
+    ("ec_electrodes_rf_collisionless", dict(n_cells=64, mcc=False), 100),
+    ("mc_electrodes_rf_collisionless", dict(n_cells=64, mcc=False, scheme="mc_explicit"), 100),
+    ("ec_implicit_electrodes", dict(n_cells=64, mcc=False, scheme="ec_implicit", dt=8e-10), 100),
+    ("ec_implicit_periodic", dict(n_cells=50, periodic=True, mcc=False, rf_volt=0.0,
+                                  scheme="ec_implicit", dt=8e-10), 100),
+]
+
+
+@pytest.mark.parametrize("name,over,steps", STEP_CASES, ids=[c[0] for c in STEP_CASES])
+def test_steps_match_oracle(name, over, steps):
+    cfg = dict(workloads.CFG_SMALL_CCP, np_init=12_800, sort_period=8)
+    cfg.update(over)
+    n = cfg["np_init"]
+    gpu = gpu_sim(cfg)
+    orc = oracle.Sim(cfg)
+    inject(gpu, orc, cfg, states_for(cfg, n, 5 + len(name)))
+    g0 = gpu.grids()
+    assert np.array_equal(g0["rho_q_e"], orc.grids()["rho_q_e"])
+    for _ in range(steps // 10):
+        gpu.step(10)
+        orc.step(10)
+    dg, do = gpu.diag(), orc.diag()
+    assert dg["step"] == do["step"] == steps
+    assert dg["count"] == do["count"], name
+    assert dg["wall_count"] == do["wall_count"], name
+    compare_particles(gpu, orc, cfg)
+    for k in range(2):
+        assert dg["ke_x"][k] == pytest.approx(do["ke_x"][k], rel=1e-4, abs=1e-12)
+    assert dg["field_energy"] == pytest.approx(do["field_energy"], rel=1e-3)
+
+
+def test_collisions_counts_exact_and_births_ranked():
+    """Null-collision MCC on the same Philox stream: selection is an integer
+    compare, so tallies and births agree exactly; children get the same ids."""
+    cfg = dict(workloads.CFG_SMALL_CCP, np_init=20_000, sort_period=4, te_ev=6.0)
+    n = cfg["np_init"]
+    gpu = gpu_sim(cfg)
+    orc = oracle.Sim(cfg)
+    inject(gpu, orc, cfg, states_for(cfg, n, 77), step=1000)
+    for _ in range(4):
+        gpu.step(5)
+        orc.step(5)
+    dg, do = gpu.diag(), orc.diag()
+    assert dg["coll"] == do["coll"]
+    assert dg["births"] == do["births"] > 0
+    assert dg["count"] == do["count"]
+    assert dg["wall_count"] == do["wall_count"]
+    assert dg["overflow"] == do["overflow"]
+    compare_particles(gpu, orc, cfg)
+
+
+def test_sorting_and_graph_replay_do_not_change_results():
+    """Charge sums are integers and draws are keyed on (id, step), so the
+    slot order (sorted or not) and graph replay leave every particle
+    bit-identical."""
+    base = dict(workloads.CFG_SMALL_CCP, np_init=12_800)
+    outs = []
+    for sp in (0, 1, 16):
+        cfg = dict(base, sort_period=sp)
+        gpu = gpu_sim(cfg)
+        gpu.step(48)
+        outs.append({s: by_id(gpu.get_particles(s)) for s in ("e", "i")})
+        gpu.close()
+    for s in ("e", "i"):
+        for o in outs[1:]:
+            for key in ("id", "cell", "off", "vx", "vy", "vz"):
+                assert np.array_equal(o[s][key], outs[0][s][key]), (s, key)
+
+
+def test_checkpoint_resume_is_bit_identical():
+    cfg = dict(workloads.CFG_SMALL_CCP, np_init=8000, sort_period=4)
+    gpu = gpu_sim(cfg)
+    gpu.step(20)
+    snap = gpu.save()
+    gpu.step(30)
+    ref = {s: by_id(gpu.get_particles(s)) for s in ("e", "i")}
+    ref_diag = gpu.diag()
+    gpu.load(snap)
+    gpu.step(30)
+    got = {s: by_id(gpu.get_particles(s)) for s in ("e", "i")}
+    for s in ("e", "i"):
+        for key in ("id", "cell", "off", "vx", "vy", "vz"):
+            assert np.array_equal(got[s][key], ref[s][key])
+    d = gpu.diag()
+    assert d["coll"] == ref_diag["coll"] and d["count"] == ref_diag["count"]
+
+
+def test_birth_capacity_overflow_sets_status_without_fault():
+    cfg = dict(workloads.CFG_SMALL_CCP, np_init=20_000, te_ev=8.0, births_capacity=2)
+    gpu = gpu_sim(cfg)
+    gpu.step(20)
+    assert gpu.status() & 0x2
+    d = gpu.diag()
+    assert d["count"][0] == d["count"][1] + (d["count"][0] - d["count"][1])  # readable after overflow

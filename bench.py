@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Benchmark of the EC PIC/MCC hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
+
+A step is one pass of the whole hot path (gather, push, electrode absorption,
+null-collision MCC with births, S_2 charge assignment, field solve; plus the
+counting sort every sort_period steps) over all particles of the production
+explicit workload: 6.7 cm gap, 512 cells, 2,048,000 macro-particles per
+species, 450 V at 13.56 MHz, 30 mTorr.  Inputs are resident in HBM; each
+timed step is bracketed by CUDA events on the run's stream and the L2 is
+flushed (a 256 MB write) between timed steps, outside the events.
+
+--impl reference times the CPU oracle (FP64, one core) on a bounded sample
+of the same workload.  N > 1 runs independent replicas, one per GPU (the
+method's runs do not exchange data): value = particles of all ranks / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "particle-steps/s (push+deposit+MCC)"
+UNIT = "particle-steps/s"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "dominant_kernel_traffic.json")
+
+WORKLOADS = {
+    "ccp_512cells_2048000ppsp": workloads.CFG_WIDE_EXPLICIT,
+    "ccp_128cells_implicit": workloads.CFG_IMPLICIT,
+    "ccp_64cells_12800ppsp": workloads.CFG_SMALL_CCP,
+}
+
+
+def kernel_source_sha() -> str:
+    p = os.path.join(ROOT, "paper_1310_5284_gb300", "csrc", "pic_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def algorithmic_bytes_per_particle(scheme: str) -> dict:
+    """Bytes one launch must move per particle (structure of arrays, 4 B per
+    field): explicit reads cell, offset, vx, id and writes cell, offset, vx;
+    a particle selected for a collision also reads and writes vy, vz.  The
+    implicit corrector reads cell, offset, vx, abar, id and writes cell,
+    offset, vx, abar; its predictor reads cell, offset, vx, abar."""
+    if scheme == "ec_implicit":
+        return {"per_particle": 36, "per_selected": 16, "predictor_per_particle": 16}
+    return {"per_particle": 28, "per_selected": 16}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_gpu(args, wl_name, cfg, rank, world):
+    import torch
+    from paper_1310_5284_gb300.sim import Sim
+    from paper_1310_5284_gb300 import _abi
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cfg = dict(cfg, seed=cfg.get("seed", 1) + 1000 * rank, run=rank)
+    sim = Sim(cfg, device=dev)
+    stream = sim.stream
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    K, W = args.steps, args.warmup
+    sort_period = int(cfg.get("sort_period", 16))
+    implicit = cfg["scheme"] == "ec_implicit"
+
+    with torch.cuda.stream(stream):
+        sim.step(W)
+        torch.cuda.synchronize(dev)
+        d0 = sim.diag()
+        step0 = d0["step"]
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        t_wall = time.perf_counter()
+        for k in range(K):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            sim.step(1)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
+        clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in evs]  # ms
+    d1 = sim.diag()
+    n_avg = 0.5 * (sum(d0["count"]) + sum(d1["count"]))
+    total_ms = sum(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms_max = float(t.item())
+        c = torch.tensor([n_avg * K], dtype=torch.float64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        particle_steps = float(c.item())
+    else:
+        total_ms_max = total_ms
+        particle_steps = n_avg * K
+    value = particle_steps / (total_ms_max * 1e-3)
+
+    # dominant kernel: the fused particle launch (non-sort steps hold exactly it,
+    # or the implicit predictor + corrector pair)
+    sort_idx = [k for k in range(K) if sort_period > 0 and (step0 + k + 1) % sort_period == 0]
+    plain = [times[k] for k in range(K) if k not in set(sort_idx)]
+    t_push = sum(plain) / len(plain)
+    t_sort = (sum(times[k] for k in sort_idx) / len(sort_idx) - t_push) if sort_idx else 0.0
+    sel = sum(d1["coll"]) - sum(d0["coll"])  # selected particles over the K steps
+    bpp = algorithmic_bytes_per_particle(cfg["scheme"])
+    slots = n_avg
+    bytes_launch = bpp["per_particle"] * slots + bpp["per_selected"] * sel / K
+    if implicit:
+        bytes_launch += bpp["predictor_per_particle"] * slots
+    peak, peak_kind = measured_peak()
+    achieved = bytes_launch / (t_push * 1e-3) / 1e9
+    traffic = None
+    try:
+        tr = json.load(open(PROFILE_TRAFFIC))
+        if tr.get("kernel_source_sha") == kernel_source_sha() and tr.get("workload") == wl_name:
+            traffic = float(tr["dram_bytes_per_particle"]) * slots
+    except Exception:
+        traffic = None
+    launches_per_step = 2 if implicit else 1
+    gpu_launches = launches_per_step * K + len(sort_idx)
+
+    # end to end through the public API with host buffers: every step uploads
+    # both species from pinned host memory (pic_set_particles), re-assigns
+    # charge and solves (pic_init_field), steps once and reads the diagnostics.
+    e2e = run_e2e(sim, args.e2e_steps, dev) if args.e2e_steps > 0 else None
+    sim.close()
+    return dict(value=value, total_ms=total_ms_max, times=times, t_push=t_push, t_sort=t_sort,
+                achieved=achieved, peak=peak, peak_kind=peak_kind, bytes_launch=bytes_launch,
+                traffic=traffic, clocks=clk, gpu_launches=gpu_launches, n_avg=n_avg, e2e=e2e,
+                wall_s=t_wall, counts=d1["count"], sort_steps=len(sort_idx))
+
+
+def run_e2e(sim, steps, dev):
+    import numpy as np
+    import torch
+
+    host = {}
+    for sp in ("e", "i"):
+        p = sim.get_particles(sp)
+        pinned = {}
+        for k in ("cell", "off", "vx", "vy", "vz", "id"):
+            t = torch.from_numpy(np.ascontiguousarray(p[k])).pin_memory()
+            pinned[k] = t.numpy()
+        host[sp] = (pinned, p["next_id"])
+    h2d = sum(sum(a.nbytes for a in host[sp][0].values()) for sp in host)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    n_proc = 0
+    d2h = 0
+    for _ in range(steps):
+        for sp in ("e", "i"):
+            sim.set_particles(sp, host[sp][0], next_id=host[sp][1])
+        sim.init_field(set_abar=False)
+        sim.step(1)
+        d = sim.diag()
+        d2h = 512  # the device state record read by pic_diag
+        n_proc += sum(d["count"])
+    t = time.perf_counter() - t0
+    return {"value": n_proc / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
+            "steps": steps}
+
+
+def oracle_baseline(cfg, budget_s=12.0, max_steps=40):
+    """The FP64 CPU oracle, as it stands, on a bounded sample: the workload
+    loaded at full size, then steps until about budget_s of stepping."""
+    import oracle
+    n = int(cfg["np_init"])
+    sim = oracle.Sim(cfg).load(n, n)
+    steps, t_used, parts = 0, 0.0, 0
+    while steps < max_steps and t_used < budget_s:
+        d = sim.diag()
+        t0 = time.perf_counter()
+        sim.step(1)
+        t_used += time.perf_counter() - t0
+        parts += sum(d["count"])
+        steps += 1
+    return {"value": parts / t_used, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%s at full size (%d per species), first %d steps after the load, FP64, one thread"
+                      % (cfg["name"], n, steps)}
+
+
+def energy_drift(steps=2000):
+    """Total-energy drift of the collisionless periodic EC plasma (64 cells,
+    4096 electrons, dx = 10 Debye lengths, omega_p dt = 0.1): FP32 GPU push
+    against the FP64 oracle over the same steps."""
+    import numpy as np
+
+    import oracle
+    from paper_1310_5284_gb300.sim import Sim
+    e, eps0, me = 1.602176634e-19, 8.8541878128e-12, 9.1093837015e-31
+    n0, te = 1e15, 2.0
+    lam = math.sqrt(eps0 * te / (n0 * e))
+    wp = math.sqrt(n0 * e * e / (eps0 * me))
+    cfg = workloads.cfg_periodic(n_cells=64, np_e=4096, n0=n0, length=64 * 10 * lam, dt=0.1 / wp, te_ev=te,
+                                 seed=11)
+    cfg["sort_period"] = 16
+    out = {}
+    for name, sim in (("gpu_fp32", Sim(cfg)), ("oracle_fp64", oracle.Sim(dict(cfg, quantized=True)).load(4096, 0))):
+        sim.step(1)
+        e0 = sim.energy()
+        dev = 0.0
+        for _ in range(steps // 100):
+            sim.step(100)
+            dev = max(dev, abs(sim.energy() / e0 - 1.0))
+        out[name] = dev
+        if hasattr(sim, "close"):
+            sim.close()
+    out["case"] = "periodic 64 cells, 4096 e-, dx=10 lambda_D, omega_p dt=0.1, %d steps, max |dE/E|" % steps
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="ccp_512cells_2048000ppsp", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-energy", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    wl_name = args.workload
+    cfg = dict(WORKLOADS[wl_name])
+    config = {"workload": wl_name + "_" + cfg["scheme"], "n_cells": cfg["n_cells"],
+              "particles_per_species": cfg["np_init"], "gap_m": cfg["length"], "rf_volt": cfg["rf_volt"],
+              "dt_s": cfg["dt"], "pressure_mtorr": cfg["pressure_mtorr"], "sort_period": cfg.get("sort_period"),
+              "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas" if world > 1 else "single"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        base = oracle_baseline(cfg, budget_s=min(20.0, 2.0 * args.steps))
+        line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": base, "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                               "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    import __graft_entry__  # noqa: F401  (path setup only; the library must already be built)
+    r = run_gpu(args, wl_name, cfg, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s",
+                     "frac": r["achieved"] / r["peak"], "traffic": r["traffic"],
+                     "kernel": "k_particles (fused gather/push/absorb/MCC/deposit + tail)",
+                     "algorithmic_bytes_per_launch": r["bytes_launch"], "launch_ms": r["t_push"],
+                     "peak_source": r["peak_kind"]},
+        "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
+        "kernels": {"particles_ms": r["t_push"], "sort_ms": r["t_sort"], "sort_steps": r["sort_steps"]},
+        "particles_live": r["counts"],
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline(cfg)
+    if world == 1 and not args.no_energy:
+        line["energy_drift"] = energy_drift()
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

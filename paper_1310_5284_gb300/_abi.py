@@ -10,7 +10,8 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libpic.so")
+# PIC_LIBRARY selects an alternative build of the same sources (launch-shape sweeps)
+LIB_PATH = os.environ.get("PIC_LIBRARY") or os.path.join(_PKG, "libpic.so")
 
 PIC_OK = 0
 ERRORS = {-1: "PIC_EINVAL", -2: "PIC_EUNSTABLE", -3: "PIC_ENOMEM", -4: "PIC_EOVERFLOW",

@@ -36,16 +36,21 @@ def stale() -> bool:
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Build libpic.so if any source is newer than it; returns its path."""
-    if not force and not stale():
+def build(force: bool = False, verbose: bool = False, defines=None, lib_path: str | None = None) -> str:
+    """Build libpic.so if any source is newer than it; returns its path.
+    defines: extra -D macros (launch-shape knobs of pic_internal.h);
+    lib_path: build an alternative library there instead of the in-tree one."""
+    out = lib_path or LIB
+    if not force and lib_path is None and not defines and not stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = BUILD if lib_path is None else os.path.splitext(out)[0] + "_build"
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if verbose else []
+    extra += ["-D%s" % d for d in (defines or [])]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -57,13 +62,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         for _, log in results:
             print(log)
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    tmp = out + ".tmp.%d" % os.getpid()
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

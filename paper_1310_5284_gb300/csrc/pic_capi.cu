@@ -399,6 +399,13 @@ int pic_init(const pic_config *cfg, const pic_buffers *bufs, void *stream, pic_h
     }
     r = pic_init_field(h, 1);
     if (r) return bail(r);
+    // the load is in random order: sort it once so that every block streams
+    // particles of a few adjacent cells from the first step on
+    e = launch_sort(h->run, h->grid_sort, h->stream);
+    if (e != cudaSuccess) {
+        cuda_fail(h, e, "sort");
+        return bail(PIC_ECUDA);
+    }
     *out = h;
     return PIC_OK;
 }

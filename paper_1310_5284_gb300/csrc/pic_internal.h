@@ -9,9 +9,22 @@
 
 namespace pic {
 
+// Launch shape of the particle kernels (build-time knobs; the defaults are
+// the ones the autotuning sweep picked on GB300).
+#ifndef PIC_THREADS
+#define PIC_THREADS 256
+#endif
+#ifndef PIC_UNROLL
+#define PIC_UNROLL 4
+#endif
+#ifndef PIC_MIN_BLOCKS
+#define PIC_MIN_BLOCKS 4
+#endif
+
 constexpr int kMaxCells = 1024;          // grid lives in shared memory
-constexpr int kThreads = 256;            // block size of the particle kernels
-constexpr int kUnroll = 4;               // particles per thread per tile
+constexpr int kThreads = PIC_THREADS;    // block size of the particle kernels
+constexpr int kUnroll = PIC_UNROLL;      // particles per thread per tile
+constexpr int kMinBlocks = PIC_MIN_BLOCKS;
 constexpr int kMaxEedfBins = 4096;
 
 enum Mode : int {

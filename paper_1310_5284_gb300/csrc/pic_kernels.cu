@@ -64,9 +64,8 @@ __device__ __forceinline__ void box_muller(float u1, float u2, float &n1, float 
 
 // Turn the unit vector d by polar angle chi and azimuth phi, the azimuth
 // measured in the basis of d's polar angles about the x axis.
-__device__ __forceinline__ void rotate(float dx_, float dy, float dz, float cos_chi, float sp,
-                                       float cp, float &ox, float &oy, float &oz) {
-    const float sin_chi = sqrtf(fmaxf(0.0f, 1.0f - cos_chi * cos_chi));
+__device__ __forceinline__ void rotate(float dx_, float dy, float dz, float cos_chi, float sin_chi,
+                                       float sp, float cp, float &ox, float &oy, float &oz) {
     const float st = sqrtf(dy * dy + dz * dz);
     if (st > 1e-6f) {
         const float inv = 1.0f / st;
@@ -99,9 +98,11 @@ struct Tally {
 
 // Electron collision (null-collision MC): elastic, excitation or ionisation
 // chosen by u * nu_max against the running sum of n_g sigma_k(eps) v.
+// Kept out of line: only the few selected particles take this path.
 // Returns true if the velocity changed.
-__device__ bool collide_electron(const Run &R, uint4 w, uint32_t id, long long step, int cell,
-                                 float off, float abar, float &vx, float &vy, float &vz, Tally &t) {
+__device__ __noinline__ bool collide_electron(const Run &R, uint4 w, uint32_t id, long long step,
+                                              int cell, float off, float abar, float &vx, float &vy,
+                                              float &vz, Tally &t) {
     const float v2 = vx * vx + vy * vy + vz * vz;
     const float g = sqrtf(v2);
     const float eps = R.half_m_over_e[0] * v2;
@@ -111,7 +112,10 @@ __device__ bool collide_electron(const Run &R, uint4 w, uint32_t id, long long s
     const float nu_el = R.sig_el * ngv;
     const float nu_ex = sigma_exc(R, eps) * ngv;
     const float nu_iz = sigma_iz(R, eps) * ngv;
-    const float cos_chi = 1.0f - 2.0f * u24(w.z);
+    // isotropic: cos chi = 1 - 2u, sin chi = 2 sqrt(u (1 - u)) (no cancellation)
+    const float uc = u24(w.z);
+    const float cos_chi = 1.0f - 2.0f * uc;
+    const float sin_chi = 2.0f * sqrtf(uc * (1.0f - uc));
     float sp, cp;
     sincospif(2.0f * u24(w.w), &sp, &cp);
     float dx_ = 1.0f, dy = 0.0f, dz = 0.0f;
@@ -123,7 +127,8 @@ __device__ bool collide_electron(const Run &R, uint4 w, uint32_t id, long long s
     }
     float g_new;
     if (r < nu_el) {
-        g_new = g * sqrtf(1.0f - R.two_m_over_M * (1.0f - cos_chi));
+        // elastic: the electron keeps 1 - (2m/M)(1 - cos chi) of its energy
+        g_new = g * sqrtf(1.0f - R.two_m_over_M * (2.0f * uc));
         t.el++;
     } else if (r < nu_el + nu_ex) {
         g_new = sqrtf(R.two_e_over_me * (eps - R.exc_thr));
@@ -134,8 +139,9 @@ __device__ bool collide_electron(const Run &R, uint4 w, uint32_t id, long long s
         g_new = sqrtf(R.two_e_over_me * 0.5f * (eps - R.iz_thr));
         const uint4 w1 = draw(R, id, step, 0, kTagMcc, 1);
         const uint4 w2 = draw(R, id, step, 0, kTagMcc, 2);
-        const float ct = 1.0f - 2.0f * u24(w1.x);
-        const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+        const float u1 = u24(w1.x);
+        const float ct = 1.0f - 2.0f * u1;
+        const float st = 2.0f * sqrtf(u1 * (1.0f - u1));
         float sps, cps;
         sincospif(2.0f * u24(w1.y), &sps, &cps);
         float n1, n2, n3, n4;
@@ -162,7 +168,7 @@ __device__ bool collide_electron(const Run &R, uint4 w, uint32_t id, long long s
         return false;
     }
     float ox, oy, oz;
-    rotate(dx_, dy, dz, cos_chi, sp, cp, ox, oy, oz);
+    rotate(dx_, dy, dz, cos_chi, sin_chi, sp, cp, ox, oy, oz);
     vx = g_new * ox;
     vy = g_new * oy;
     vz = g_new * oz;
@@ -170,8 +176,8 @@ __device__ bool collide_electron(const Run &R, uint4 w, uint32_t id, long long s
 }
 
 // Ion charge exchange against a neutral sampled from the gas Maxwellian.
-__device__ bool collide_ion(const Run &R, uint4 w, uint32_t id, long long step, float &vx,
-                            float &vy, float &vz, Tally &t) {
+__device__ __noinline__ bool collide_ion(const Run &R, uint4 w, uint32_t id, long long step,
+                                         float &vx, float &vy, float &vz, Tally &t) {
     const uint4 w1 = draw(R, id, step, 1, kTagMcc, 1);
     float n1, n2, n3, n4;
     box_muller(u24(w.z), u24(w.w), n1, n2);
@@ -190,6 +196,14 @@ __device__ bool collide_ion(const Run &R, uint4 w, uint32_t id, long long step, 
     }
     t.nul++;
     return false;
+}
+
+// A particle crossed an electrode (Sec. 3): tally its number and energy.
+__device__ __noinline__ void absorb(const Run &R, int S, int wall, float vx, float vy, float vz) {
+    const float en = R.half_m_over_e[S] * (vx * vx + vy * vy + vz * vz);
+    atomicAdd(&R.st->wall_count[S][wall], 1ull);
+    atomicAdd(&R.st->wall_energy[S][wall], (double)en);
+    atomicAdd(&R.st->absorbed_step[S], 1ull);
 }
 
 // ---------------------------------------------------------------------------
@@ -216,51 +230,90 @@ __device__ __forceinline__ int deposit_key_s1(int cell, float off, uint32_t &a) 
     return cell;
 }
 
-// Warp-aggregated accumulation into shared memory: lanes sharing a key are
-// summed with redux.sync and one lane per key updates the shared arrays.
-// Every lane of the warp must call this (key < 0: nothing to add).
-__device__ __forceinline__ void warp_deposit(int key, uint32_t a, unsigned int *s_cnt,
-                                             unsigned long long *s_a, unsigned long long *s_b,
-                                             bool count_only) {
+// Per-block accumulators, four 32-bit counters per key: count, sum of a, and
+// the sums of the high and low 16 bits of a^2.  Exact while a block adds at
+// most 2^16 particles between two flushes (each term is below 2^16).
+struct Acc {
+    unsigned int *cnt, *a, *bh, *bl;
+};
+
+constexpr long long kFlushEvery = 65536;
+
+__device__ __forceinline__ void acc_add(const Acc &acc, int key, uint32_t c, uint32_t a, uint32_t bh,
+                                        uint32_t bl, bool count_only) {
+    atomicAdd(&acc.cnt[key], c);
+    if (!count_only) {
+        atomicAdd(&acc.a[key], a);
+        atomicAdd(&acc.bh[key], bh);
+        atomicAdd(&acc.bl[key], bl);
+    }
+}
+
+// Warp aggregation of per-lane partial sums that share a key (key < 0: none):
+// redux.sync sums each group, one lane per group updates shared memory.
+// Every lane of the warp must call this.
+__device__ __forceinline__ void warp_agg(int key, uint32_t c, uint32_t a, uint32_t bh, uint32_t bl,
+                                         const Acc &acc, bool count_only) {
     const int lane = threadIdx.x & 31;
     unsigned int pending = __ballot_sync(FULL_MASK, key >= 0);
     int iter = 0;
     while (pending) {
-        if (iter == 6) {  // widely spread warp: per-lane shared atomics for the rest
-            if ((pending >> lane) & 1u) {
-                atomicAdd(&s_cnt[key], 1u);
-                if (!count_only) {
-                    atomicAdd(&s_a[key], (unsigned long long)a);
-                    atomicAdd(&s_b[key], (unsigned long long)a * a);
-                }
-            }
+        if (iter == 4) {  // widely spread warp: the rest add lane by lane
+            if ((pending >> lane) & 1u) acc_add(acc, key, c, a, bh, bl, count_only);
             break;
         }
         const int leader = __ffs(pending) - 1;
         const int lk = __shfl_sync(FULL_MASK, key, leader);
         const bool mine = ((pending >> lane) & 1u) && key == lk;
         const unsigned int grp = __ballot_sync(FULL_MASK, mine);
+        const uint32_t sc = __reduce_add_sync(FULL_MASK, mine ? c : 0u);
+        uint32_t sa = 0, sh = 0, sl = 0;
         if (!count_only) {
-            const uint32_t av = mine ? a : 0u;
-            const uint32_t a2 = av * av;  // a < 2^16
-            const uint32_t sa = __reduce_add_sync(FULL_MASK, av);
-            const uint32_t hi = __reduce_add_sync(FULL_MASK, a2 >> 16);
-            const uint32_t lo = __reduce_add_sync(FULL_MASK, a2 & 0xffffu);
-            if (lane == leader) {
-                atomicAdd(&s_cnt[lk], (unsigned int)__popc(grp));
-                atomicAdd(&s_a[lk], (unsigned long long)sa);
-                atomicAdd(&s_b[lk], ((unsigned long long)hi << 16) + lo);
-            }
-        } else if (lane == leader) {
-            atomicAdd(&s_cnt[lk], (unsigned int)__popc(grp));
+            sa = __reduce_add_sync(FULL_MASK, mine ? a : 0u);
+            sh = __reduce_add_sync(FULL_MASK, mine ? bh : 0u);
+            sl = __reduce_add_sync(FULL_MASK, mine ? bl : 0u);
         }
+        if (lane == leader) acc_add(acc, lk, sc, sa, sh, sl, count_only);
         pending &= ~grp;
         ++iter;
     }
 }
 
+// The kUnroll particles of a thread usually share one or two adjacent keys
+// (particles are kept sorted by key): fold them into two register slots,
+// then aggregate each slot across the warp.
+__device__ __forceinline__ void deposit_tile(const int (&key)[kUnroll], const uint32_t (&a)[kUnroll],
+                                             const Acc &acc, bool count_only) {
+    int kmin = 0x7fffffff;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+        if (key[u] >= 0 && key[u] < kmin) kmin = key[u];
+    uint32_t c0 = 0, a0 = 0, h0 = 0, l0 = 0, c1 = 0, a1 = 0, h1 = 0, l1 = 0;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+        const int k = key[u];
+        if (k < 0) continue;
+        const uint32_t aa = a[u], q = aa * aa;
+        if (k == kmin) {
+            c0 += 1u;
+            a0 += aa;
+            h0 += q >> 16;
+            l0 += q & 0xffffu;
+        } else if (k == kmin + 1) {
+            c1 += 1u;
+            a1 += aa;
+            h1 += q >> 16;
+            l1 += q & 0xffffu;
+        } else {
+            acc_add(acc, k, 1u, aa, q >> 16, q & 0xffffu, count_only);
+        }
+    }
+    warp_agg(kmin == 0x7fffffff ? -1 : kmin, c0, a0, h0, l0, acc, count_only);
+    warp_agg(c1 ? kmin + 1 : -1, c1, a1, h1, l1, acc, count_only);
+}
+
 // ---------------------------------------------------------------------------
-// Block-wide scans (256 threads).
+// Block-wide scans and sums (kThreads threads).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ T block_exclusive_scan(T v, T *scratch /*[33]*/, T &total) {
@@ -291,10 +344,31 @@ __device__ T block_exclusive_scan(T v, T *scratch /*[33]*/, T &total) {
 }
 
 template <typename T>
-__device__ T block_sum(T v, T *scratch) {
-    T total;
-    block_exclusive_scan<T>(v, scratch, total);
-    return total;
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+// Sum of two doubles over the block (one barrier pair).
+__device__ void block_sum2(double &x, double &y, double *scratch /*[2*kThreads/32]*/) {
+    constexpr int nw = kThreads / 32;
+    x = warp_sum(x);
+    y = warp_sum(y);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        scratch[wid] = x;
+        scratch[nw + wid] = y;
+    }
+    __syncthreads();
+    double sx = 0.0, sy = 0.0;
+    for (int k = 0; k < nw; ++k) {
+        sx += scratch[k];
+        sy += scratch[nw + k];
+    }
+    __syncthreads();
+    x = sx;
+    y = sy;
 }
 
 // ---------------------------------------------------------------------------
@@ -302,8 +376,7 @@ __device__ T block_sum(T v, T *scratch) {
 // ---------------------------------------------------------------------------
 struct SmemMain {
     float *e;                  // [n+2] gather table
-    unsigned int *cnt;         // [n+1]
-    unsigned long long *a, *b; // [n+1]
+    Acc acc;                   // 4 x [n+1]
     float *heat;               // [n]
     unsigned int *eedf;        // [bins+1]
 };
@@ -311,8 +384,8 @@ struct SmemMain {
 __host__ __device__ inline size_t align8(size_t x) { return (x + 7) & ~size_t(7); }
 
 __host__ __device__ inline size_t main_smem_bytes(int n, int bins) {
-    return align8(4 * (size_t)(n + 2)) + align8(4 * (size_t)(n + 1)) + 16 * (size_t)(n + 1) +
-           align8(4 * (size_t)n) + align8(4 * (size_t)(bins + 1));
+    return align8(4 * (size_t)(n + 2)) + 4 * align8(4 * (size_t)(n + 1)) + align8(4 * (size_t)n) +
+           align8(4 * (size_t)(bins + 1));
 }
 
 __host__ __device__ inline size_t tail_smem_bytes(int n) {
@@ -324,90 +397,29 @@ __device__ SmemMain carve_main(unsigned char *base, int n, int bins) {
     size_t o = 0;
     s.e = (float *)(base + o);
     o += align8(4 * (size_t)(n + 2));
-    s.a = (unsigned long long *)(base + o);
-    o += 8 * (size_t)(n + 1);
-    s.b = (unsigned long long *)(base + o);
-    o += 8 * (size_t)(n + 1);
-    s.cnt = (unsigned int *)(base + o);
-    o += align8(4 * (size_t)(n + 1));
+    unsigned int **slots[4] = {&s.acc.cnt, &s.acc.a, &s.acc.bh, &s.acc.bl};
+    for (int k = 0; k < 4; ++k) {
+        *slots[k] = (unsigned int *)(base + o);
+        o += align8(4 * (size_t)(n + 1));
+    }
     s.heat = (float *)(base + o);
     o += align8(4 * (size_t)n);
     s.eedf = (unsigned int *)(base + o);
     return s;
 }
 
-// ---------------------------------------------------------------------------
-// Per-particle work of each mode.  Returns the deposit key (or -1) and the
-// fixed-point value a.
-// ---------------------------------------------------------------------------
-template <int MODE, int S>
-__device__ __forceinline__ int particle(const Run &R, const SmemMain &sm, const Species &sp,
-                                        long long idx, int &cell, float &off, float &vx,
-                                        uint32_t id, float &abar, bool diag, long long step,
-                                        Tally &t, uint32_t &a_out, bool &write) {
-    constexpr bool kMC = (MODE == kExplicitMC || MODE == kDepositMC);
-    const int N = R.n_cells;
-    write = false;
-    if (cell < 0) return -1;  // hole left by an absorbed particle
-    if (MODE == kDepositEC) return deposit_key_s2(cell, off, a_out);
-    if (MODE == kDepositMC) return deposit_key_s1(cell, off, a_out);
+template <int MODE>
+struct ModeInfo {
+    static constexpr bool push = !(MODE == kDepositEC || MODE == kDepositMC || MODE == kImplicit1);
+    static constexpr bool needs_field = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit2);
+    static constexpr bool implicit = (MODE == kImplicit1 || MODE == kImplicit2);
+    static constexpr bool count_only = (MODE == kImplicit2);
+    static constexpr bool mc = (MODE == kExplicitMC || MODE == kDepositMC);
+    static constexpr bool loads_v = !(MODE == kDepositEC || MODE == kDepositMC);
+};
 
-    // ---- positions and fields of the push ----
-    float e_field;
-    float v_old = vx, v_new, s;
-    int c = cell;
-    if (MODE == kImplicit1 || MODE == kImplicit2) {
-        // predictor: v~ = v + dt abar / 2, x~ = x + dt v~
-        const float vt = fmaf(R.half_dt, abar, vx);
-        s = fmaf(vt, R.dt_dx, off);
-        if (!(fabsf(s) < 1.0e6f)) s = (float)(N + 2);  // runaway: lands outside
-        if (!(s >= 0.0f && s < 1.0f)) {
-            const float fl = floorf(s);
-            c += (int)fl;
-            s -= fl;
-            if (s >= 1.0f) {
-                s = 0.0f;
-                c += 1;
-            }
-        }
-        bool inside = true;
-        if (R.periodic) {
-            c = ((c % N) + N) % N;
-        } else if (c < 0 || c >= N) {
-            inside = false;
-        }
-        if (MODE == kImplicit1) {
-            if (!inside) return -1;  // Reading: no charge or susceptibility beyond an electrode
-            return deposit_key_s2(c, s, a_out);
-        }
-        // corrector at x~
-        e_field = 0.0f;
-        if (inside) {
-            const int j = c + (s >= 0.5f ? 1 : 0);
-            const float w1 = s >= 0.5f ? s - 0.5f : s + 0.5f;
-            e_field = (1.0f - w1) * sm.e[j] + w1 * sm.e[j + 1];
-        }
-        const float acc = R.qm[S] * e_field;
-        v_new = fmaf(R.half_dt, acc, vt);
-        if (diag && inside) atomicAdd(&sm.heat[c], R.qw[S] * e_field * 0.5f * (v_old + v_new));
-        s = fmaf(acc, R.half_dt2_dx, s);
-        abar = 0.5f * (abar + acc);
-    } else {
-        // explicit: gather at x^n, leapfrog
-        if (kMC) {
-            e_field = (1.0f - off) * sm.e[cell] + off * sm.e[cell + 1];
-        } else {
-            const int j = cell + (off >= 0.5f ? 1 : 0);
-            const float w1 = off >= 0.5f ? off - 0.5f : off + 0.5f;
-            e_field = (1.0f - w1) * sm.e[j] + w1 * sm.e[j + 1];
-        }
-        v_new = fmaf(R.qm_dt[S], e_field, vx);
-        if (diag) atomicAdd(&sm.heat[cell], R.qw[S] * e_field * 0.5f * (v_old + v_new));
-        s = fmaf(v_new, R.dt_dx, off);
-    }
-    t.kx += 0.5f * (v_old * v_old + v_new * v_new);
-    t.pw += R.qw[S] * e_field * 0.5f * (v_old + v_new);
-    if (!(fabsf(s) < 1.0e6f)) s = (float)(2 * N + 2);
+// Renormalise an offset that left [0, 1) into the cell index.
+__device__ __forceinline__ void renormalise(int &c, float &s) {
     if (!(s >= 0.0f && s < 1.0f)) {
         const float fl = floorf(s);
         c += (int)fl;
@@ -417,27 +429,80 @@ __device__ __forceinline__ int particle(const Run &R, const SmemMain &sm, const 
             c += 1;
         }
     }
+}
+
+// EC force interpolation, Eq. (3) with m = 2: S_1 from the cell-centred field
+// table e[] (e[k] = E of cell k-1; ghost cells beyond the walls hold zero).
+__device__ __forceinline__ float gather_ec(const float *e, int cell, float off) {
+    const int j = cell + (off >= 0.5f ? 1 : 0);
+    const float w1 = off >= 0.5f ? off - 0.5f : off + 0.5f;  // 1/2 + delta
+    return (1.0f - w1) * e[j] + w1 * e[j + 1];
+}
+
+// ---------------------------------------------------------------------------
+// One particle of each mode.  Returns its deposit key (-1: none) and value a.
+// On return cell < 0 marks an absorbed particle.
+// ---------------------------------------------------------------------------
+template <int MODE, int S>
+__device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, const Species &sp,
+                                             long long idx, int &cell, float &off, float &vx,
+                                             float &abar, uint32_t id, bool diag, long long step,
+                                             Tally &t, uint32_t &a_out) {
+    using MI = ModeInfo<MODE>;
+    const int N = R.n_cells;
+    if (MODE == kDepositEC) return deposit_key_s2(cell, off, a_out);
+    if (MODE == kDepositMC) return deposit_key_s1(cell, off, a_out);
+    const float v_old = vx;
+    float e_field, v_new, s;
+    int c = cell;
+    if (MI::implicit) {
+        // predictor: v~ = v + dt abar / 2, x~ = x + dt v~
+        const float vt = fmaf(R.half_dt, abar, vx);
+        s = fmaf(vt, R.dt_dx, off);
+        if (!(fabsf(s) < 1.0e6f)) s = (float)(2 * N + 2);  // runaway: lands outside
+        renormalise(c, s);
+        bool inside = true;
+        if (R.periodic) {
+            if (c < 0 || c >= N) c = ((c % N) + N) % N;
+        } else if (c < 0 || c >= N) {
+            inside = false;
+        }
+        if (MODE == kImplicit1) {
+            if (!inside) return -1;  // Reading: nothing assigned beyond an electrode
+            return deposit_key_s2(c, s, a_out);
+        }
+        // corrector with E^{n+1} at x~
+        e_field = inside ? gather_ec(sm.e, c, s) : 0.0f;
+        const float acc = R.qm[S] * e_field;
+        v_new = fmaf(R.half_dt, acc, vt);
+        if (diag && inside) atomicAdd(&sm.heat[c], R.qw[S] * e_field * 0.5f * (v_old + v_new));
+        s = fmaf(acc, R.half_dt2_dx, s);
+        abar = 0.5f * (abar + acc);
+    } else {
+        // explicit leapfrog with E^n at x^n (Sec. 2 schemes (1), (2))
+        e_field = MI::mc ? (1.0f - off) * sm.e[cell] + off * sm.e[cell + 1] : gather_ec(sm.e, cell, off);
+        v_new = fmaf(R.qm_dt[S], e_field, vx);
+        if (diag) atomicAdd(&sm.heat[cell], R.qw[S] * e_field * 0.5f * (v_old + v_new));
+        s = fmaf(v_new, R.dt_dx, off);
+    }
+    t.kx += 0.5f * (v_old * v_old + v_new * v_new);
+    t.pw += R.qw[S] * e_field * 0.5f * (v_old + v_new);
+    if (!(fabsf(s) < 1.0e6f)) s = (float)(2 * N + 2);
+    renormalise(c, s);
     vx = v_new;
-    write = true;
-    // ---- electrodes (Sec. 3) or periodic wrap ----
+    off = s;
+    // electrodes (Sec. 3) or periodic wrap
     if (R.periodic) {
         if (c < 0 || c >= N) c = ((c % N) + N) % N;
     } else if (c < 0 || c >= N) {
-        const int wall = c < 0 ? 0 : 1;
-        const float vy = sp.vy[idx], vz = sp.vz[idx];
-        const float en = R.half_m_over_e[S] * (v_new * v_new + vy * vy + vz * vz);
-        atomicAdd(&R.st->wall_count[S][wall], 1ull);
-        atomicAdd(&R.st->wall_energy[S][wall], (double)en);
-        atomicAdd(&R.st->absorbed_step[S], 1ull);
+        absorb(R, S, c < 0 ? 0 : 1, v_new, sp.vy[idx], sp.vz[idx]);
         cell = -1;
-        off = s;
         return -1;
     }
     cell = c;
-    off = s;
-    // ---- null-collision Monte Carlo ----
-    bool have_perp = false;
+    // null-collision Monte Carlo: one Philox draw per particle and step
     float vy = 0.0f, vz = 0.0f;
+    bool have_perp = false;
     if (R.mcc) {
         const uint4 w = draw(R, id, step, S, kTagMcc, 0);
         if ((w.x >> 8) < R.thr[S]) {
@@ -462,20 +527,12 @@ __device__ __forceinline__ int particle(const Run &R, const SmemMain &sm, const 
         bin = bin > R.eedf_bins ? R.eedf_bins : (bin < 0 ? 0 : bin);
         atomicAdd(&sm.eedf[bin], 1u);
     }
-    if (kMC) return deposit_key_s1(c, s, a_out);
+    if (MI::mc) return deposit_key_s1(c, s, a_out);
     return deposit_key_s2(c, s, a_out);
 }
 
-template <int MODE>
-struct ModeInfo {
-    static constexpr bool push = !(MODE == kDepositEC || MODE == kDepositMC || MODE == kImplicit1);
-    static constexpr bool needs_field = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit2);
-    static constexpr bool implicit = (MODE == kImplicit1 || MODE == kImplicit2);
-    static constexpr bool count_only = (MODE == kImplicit2);
-    static constexpr bool mc = (MODE == kExplicitMC || MODE == kDepositMC);
-};
-
-// Stream one species segment [b, e) through the block.
+// Stream one species segment [b, e) through the block: load kUnroll
+// particles per thread, step them independently, then deposit the tile.
 template <int MODE, int S>
 __device__ void process_segment(const Run &R, const SmemMain &sm, const Species &sp, long long b,
                                 long long e, bool diag, long long step, Tally &t) {
@@ -484,31 +541,34 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Species 
         int cell[kUnroll];
         float off[kUnroll], vx[kUnroll], abar[kUnroll];
         uint32_t id[kUnroll];
-        long long idx[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            idx[u] = base + (long long)u * kThreads + threadIdx.x;
-            const bool ok = idx[u] < e;
-            cell[u] = ok ? sp.cell[idx[u]] : -1;
-            off[u] = ok ? sp.off[idx[u]] : 0.0f;
-            vx[u] = (ok && MODE != kDepositEC && MODE != kDepositMC) ? sp.vx[idx[u]] : 0.0f;
-            abar[u] = (ok && MI::implicit) ? sp.abar[idx[u]] : 0.0f;
-            id[u] = (ok && MI::push && R.mcc) ? sp.id[idx[u]] : 0u;
+            const long long i = base + (long long)u * kThreads + threadIdx.x;
+            const bool ok = i < e;
+            cell[u] = ok ? sp.cell[i] : -1;
+            off[u] = ok ? sp.off[i] : 0.0f;
+            vx[u] = (ok && MI::loads_v) ? sp.vx[i] : 0.0f;
+            abar[u] = (ok && MI::implicit) ? sp.abar[i] : 0.0f;
+            id[u] = (ok && MI::push && R.mcc) ? sp.id[i] : 0u;
         }
+        int key[kUnroll];
+        uint32_t a[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            uint32_t a = 0;
-            bool write = false;
-            const int key = particle<MODE, S>(R, sm, sp, idx[u], cell[u], off[u], vx[u], id[u],
-                                              abar[u], diag, step, t, a, write);
-            if (MI::push && write) {
-                sp.cell[idx[u]] = cell[u];
-                sp.off[idx[u]] = off[u];
-                sp.vx[idx[u]] = vx[u];
-                if (MI::implicit) sp.abar[idx[u]] = abar[u];
+            const long long i = base + (long long)u * kThreads + threadIdx.x;
+            a[u] = 0u;
+            key[u] = -1;
+            if (cell[u] < 0) continue;  // beyond the segment, or a hole left by absorption
+            key[u] = step_particle<MODE, S>(R, sm, sp, i, cell[u], off[u], vx[u], abar[u], id[u], diag,
+                                            step, t, a[u]);
+            if (MI::push) {
+                sp.cell[i] = cell[u];
+                sp.off[i] = off[u];
+                sp.vx[i] = vx[u];
+                if (MI::implicit) sp.abar[i] = abar[u];
             }
-            warp_deposit(key, a, sm.cnt, sm.a, sm.b, MI::count_only);
         }
+        deposit_tile(key, a, sm.acc, MI::count_only);
     }
 }
 
@@ -517,78 +577,96 @@ __device__ void flush_species(const Run &R, const SmemMain &sm, int S, bool coun
     __syncthreads();
     const int n1 = R.n_cells + 1;
     for (int k = threadIdx.x; k < n1; k += kThreads) {
-        const unsigned int c = sm.cnt[k];
+        const unsigned int c = sm.acc.cnt[k];
         if (c) {
             atomicAdd(&R.acc_cnt[S][k], (unsigned long long)c);
             if (!count_only) {
-                atomicAdd(&R.acc_a[S][k], sm.a[k]);
-                atomicAdd(&R.acc_b[S][k], sm.b[k]);
+                atomicAdd(&R.acc_a[S][k], (unsigned long long)sm.acc.a[k]);
+                atomicAdd(&R.acc_b[S][k], ((unsigned long long)sm.acc.bh[k] << 16) + sm.acc.bl[k]);
             }
-            sm.cnt[k] = 0u;
-            sm.a[k] = 0ull;
-            sm.b[k] = 0ull;
+            sm.acc.cnt[k] = 0u;
+            sm.acc.a[k] = 0u;
+            sm.acc.bh[k] = 0u;
+            sm.acc.bl[k] = 0u;
         }
     }
     __syncthreads();
 }
 
-__device__ void flush_tally(const Run &R, int S, const Tally &t, double *scratch_d,
-                            unsigned long long *scratch_u) {
-    const double kx = block_sum<double>((double)t.kx, scratch_d);
-    const double pw = block_sum<double>((double)t.pw, scratch_d);
-    unsigned long long v[6] = {t.el, t.ex, t.iz, t.cx, t.nul, t.ovf};
-    unsigned long long tot[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) tot[k] = block_sum<unsigned long long>(v[k], scratch_u);
-    if (threadIdx.x == 0) {
-        if (kx != 0.0) atomicAdd(&R.st->ke_x_acc[S], kx);
-        if (pw != 0.0) atomicAdd(&R.st->power_acc[S], pw);
-        for (int k = 0; k < 5; ++k)
-            if (tot[k]) atomicAdd(&R.st->coll[k], tot[k]);
-        if (tot[5]) atomicAdd(&R.st->overflow[S], tot[5]);
+// Block totals of the per-thread tallies, one barrier pair.
+__device__ void flush_tally(const Run &R, int S, const Tally &t) {
+    constexpr int nw = kThreads / 32;
+    __shared__ float s_f[2][nw];
+    __shared__ unsigned int s_u[6][nw];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const float kx = warp_sum(t.kx), pw = warp_sum(t.pw);
+    const unsigned int u[6] = {warp_sum(t.el), warp_sum(t.ex), warp_sum(t.iz), warp_sum(t.cx),
+                               warp_sum(t.nul), warp_sum(t.ovf)};
+    if (lane == 0) {
+        s_f[0][wid] = kx;
+        s_f[1][wid] = pw;
+        for (int k = 0; k < 6; ++k) s_u[k][wid] = u[k];
     }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int k = threadIdx.x;
+        if (k < 2) {
+            double acc = 0.0;
+            for (int w = 0; w < nw; ++w) acc += (double)s_f[k][w];
+            if (acc != 0.0) atomicAdd(k == 0 ? &R.st->ke_x_acc[S] : &R.st->power_acc[S], acc);
+        } else {
+            unsigned long long acc = 0;
+            for (int w = 0; w < nw; ++w) acc += s_u[k - 2][w];
+            if (acc) atomicAdd(k - 2 < 5 ? &R.st->coll[k - 2] : &R.st->overflow[S], acc);
+        }
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
 // Tail pieces (run by the last block of a particle launch).
 // ---------------------------------------------------------------------------
 
+// Per-key sums of species S with the periodic fold (key n is key 0).
+struct KeySums {
+    unsigned long long c, a, b;
+};
+
+__device__ __forceinline__ KeySums key_sums(const Run &R, int S, int k) {
+    const int n = R.n_cells;
+    KeySums r = {0ull, 0ull, 0ull};
+    if (R.periodic) {
+        k = ((k % n) + n) % n;
+        r.c = R.acc_cnt[S][k];
+        r.a = R.acc_a[S][k];
+        r.b = R.acc_b[S][k];
+        if (k == 0) {
+            r.c += R.acc_cnt[S][n];
+            r.a += R.acc_a[S][n];
+            r.b += R.acc_b[S][n];
+        }
+    } else if (k >= 0 && k <= n) {
+        r.c = R.acc_cnt[S][k];
+        r.a = R.acc_a[S][k];
+        r.b = R.acc_b[S][k];
+    }
+    return r;
+}
+
 // Node charge of species S in units of 2^-33 macro-particle charges,
 // reassembled from the per-key sums (count c, sum a = A, sum a^2 = B):
 // node g gets 2^32 c_g + 2^17 A_g - 2 B_g from key g, B_{g-1} from key g-1 and
 // 2^32 c_{g+1} - 2^17 A_{g+1} + B_{g+1} from key g+1.  Electrodes fold the
-// ghost nodes onto the wall nodes; the periodic box wraps (key n == key 0).
-// Unsigned arithmetic: the result is exact modulo 2^64 and lies in range.
+// ghost nodes onto the wall nodes; the periodic box wraps.  Unsigned
+// arithmetic: the result is exact modulo 2^64 and lies in range.
 __device__ __forceinline__ unsigned long long node_charge_s2(const Run &R, int S, int g) {
     const int n = R.n_cells;
-    const unsigned long long *C = R.acc_cnt[S], *A = R.acc_a[S], *B = R.acc_b[S];
-    auto key_c = [&](int k) -> unsigned long long {
-        if (R.periodic) {
-            k = (k % n + n) % n;
-            return C[k] + (k == 0 ? C[n] : 0ull);
-        }
-        return (k < 0 || k > n) ? 0ull : C[k];
-    };
-    auto key_a = [&](int k) -> unsigned long long {
-        if (R.periodic) {
-            k = (k % n + n) % n;
-            return A[k] + (k == 0 ? A[n] : 0ull);
-        }
-        return (k < 0 || k > n) ? 0ull : A[k];
-    };
-    auto key_b = [&](int k) -> unsigned long long {
-        if (R.periodic) {
-            k = (k % n + n) % n;
-            return B[k] + (k == 0 ? B[n] : 0ull);
-        }
-        return (k < 0 || k > n) ? 0ull : B[k];
-    };
     if (R.periodic && g == n) return 0ull;
-    unsigned long long q = (key_c(g) << 32) + (key_a(g) << 17) - 2ull * key_b(g) + key_b(g - 1) +
-                           (key_c(g + 1) << 32) - (key_a(g + 1) << 17) + key_b(g + 1);
+    const KeySums m = key_sums(R, S, g - 1), z = key_sums(R, S, g), p = key_sums(R, S, g + 1);
+    unsigned long long q = (z.c << 32) + (z.a << 17) - 2ull * z.b + m.b + (p.c << 32) - (p.a << 17) + p.b;
     if (!R.periodic) {
-        if (g == 0) q += (key_c(0) << 32) - (key_a(0) << 17) + key_b(0);  // ghost node -1
-        if (g == n) q += key_b(n);                                         // ghost node n+1
+        if (g == 0) q += (z.c << 32) - (z.a << 17) + z.b;  // ghost node -1
+        if (g == n) q += z.b;                               // ghost node n+1
     }
     return q;
 }
@@ -608,19 +686,8 @@ __device__ __forceinline__ unsigned long long node_charge_s1(const Run &R, int S
 
 // Susceptibility weight of cell c (units 2^-16): a from key c, 2^16 - a from key c+1.
 __device__ __forceinline__ unsigned long long chi_count(const Run &R, int S, int c) {
-    const int n = R.n_cells;
-    const unsigned long long *C = R.acc_cnt[S], *A = R.acc_a[S];
-    unsigned long long q;
-    if (R.periodic) {
-        const unsigned long long a0 = A[c] + (c == 0 ? A[n] : 0ull);
-        const int c1 = (c + 1) % n;
-        const unsigned long long cc = C[c1] + (c1 == 0 ? C[n] : 0ull);
-        const unsigned long long a1 = A[c1] + (c1 == 0 ? A[n] : 0ull);
-        q = a0 + (cc << 16) - a1;
-    } else {
-        q = A[c] + (C[c + 1] << 16) - A[c + 1];
-    }
-    return q;
+    const KeySums z = key_sums(R, S, c), p = key_sums(R, S, c + 1);
+    return z.a + (p.c << 16) - p.a;
 }
 
 // Place the step's births: rank by parent id, append children at the end of
@@ -696,8 +763,8 @@ __device__ void tail_births(const Run &R, unsigned char *smem, bool diag) {
             si.abar[ji] = bb.abar_e * R.abar_ion_over_e;
         }
         uint32_t a;
-        const bool mc = MODE == kExplicitMC;
-        const int key = mc ? deposit_key_s1(bb.cell, bb.off, a) : deposit_key_s2(bb.cell, bb.off, a);
+        const int key = MODE == kExplicitMC ? deposit_key_s1(bb.cell, bb.off, a)
+                                            : deposit_key_s2(bb.cell, bb.off, a);
         for (int S = 0; S < 2; ++S) {
             atomicAdd(&R.acc_cnt[S][key], 1ull);
             if (MODE != kImplicit2) {
@@ -740,6 +807,7 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
     const int n = R.n_cells;
     __shared__ long long sc_ll[33];
     __shared__ double sc_d[33];
+    __shared__ double sc_2[2 * kThreads / 32];
     long long *q = (long long *)smem;               // [n+1] net node charge
     double *rinv = (double *)(smem + 8 * (n + 1));   // [n] 1/(1+chi)
     double *ef = rinv + n;                           // [n] face field E_c
@@ -764,41 +832,33 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
             chi = R.chi_coef[0] * (double)chi_count(R, 0, c) + R.chi_coef[1] * (double)chi_count(R, 1, c);
             R.chi[c] = chi;
         }
-        rinv[c] = 1.0 / (1.0 + chi);
+        rinv[c] = implicit ? 1.0 / (1.0 + chi) : 1.0;
     }
     __syncthreads();
     // P_c: inclusive prefix of the interior node charges (all nodes when periodic)
     const int per = (n + kThreads - 1) / kThreads;
     const int c_begin = threadIdx.x * per;
-    long long local[8];
     long long run = 0;
     for (int k = 0; k < per; ++k) {
         const int c = c_begin + k;
-        long long v = 0;
-        if (c < n) v = (R.periodic || c >= 1) ? q[c] : 0;
-        run += v;
-        local[k] = run;
+        if (c < n) run += (R.periodic || c >= 1) ? q[c] : 0ll;
     }
     long long total_q;
-    const long long excl = block_exclusive_scan<long long>(run, sc_ll, total_q);
+    long long P = block_exclusive_scan<long long>(run, sc_ll, total_q);
     const double qbar = R.periodic ? (double)total_q / (double)n : 0.0;
     double s1 = 0.0, s0 = 0.0;
     for (int k = 0; k < per; ++k) {
         const int c = c_begin + k;
         if (c < n) {
-            const long long P = excl + local[k];
-            double v;
-            if (R.periodic)
-                v = R.kappa * ((double)P - (double)(c + 1) * qbar);
-            else
-                v = R.kappa * (double)P + R.kappa_bg * (double)c;
+            P += (R.periodic || c >= 1) ? q[c] : 0ll;
+            const double v = R.periodic ? R.kappa * ((double)P - (double)(c + 1) * qbar)
+                                        : R.kappa * (double)P + R.kappa_bg * (double)c;
             pp[c] = v;
             s1 += rinv[c] * v;
             s0 += rinv[c];
         }
     }
-    s1 = block_sum<double>(s1, sc_d);
-    s0 = block_sum<double>(s0, sc_d);
+    block_sum2(s1, s0, sc_2);
     double v_left = 0.0;
     if (!R.periodic) {
         const double t = (double)level * R.dt;
@@ -818,20 +878,18 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
     }
     // phi_g = phi_0 - dx sum_{c<g} E_c
     double etot;
-    const double eprefix = block_exclusive_scan<double>(esum, sc_d, etot);
-    wsum = block_sum<double>(wsum, sc_d);
-    {
-        double acc = eprefix;
-        for (int k = 0; k < per; ++k) {
-            const int g = c_begin + k;
-            if (g < n) {
-                const double ph = v_left - R.dx * acc;
-                R.phi[g] = ph;
-                if (accumulate) R.avg_phi[g] += ph;
-                acc += ef[g];
-            }
+    double acc = block_exclusive_scan<double>(esum, sc_d, etot);
+    for (int k = 0; k < per; ++k) {
+        const int g = c_begin + k;
+        if (g < n) {
+            const double ph = v_left - R.dx * acc;
+            R.phi[g] = ph;
+            if (accumulate) R.avg_phi[g] += ph;
+            acc += ef[g];
         }
     }
+    double dummy = 0.0;
+    block_sum2(wsum, dummy, sc_2);
     if (threadIdx.x == 0) {
         R.phi[n] = R.periodic ? v_left : 0.0;  // grounded electrode / periodic image of node 0
         if (accumulate) R.avg_phi[n] += R.phi[n];
@@ -856,6 +914,7 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
             }
             R.e_gather[g] = (float)e;
         }
+        __syncthreads();
         if (threadIdx.x == 0 && R.periodic) R.e_gather[n] = R.e_gather[0];
     } else {
         for (int c = threadIdx.x; c < n; c += kThreads) R.e_gather[c + 1] = (float)ef[c];
@@ -867,25 +926,25 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
     __syncthreads();
 }
 
-// Sort cursors (exclusive prefix of the per-key counts) and reset of the
-// per-step accumulators.
+// Sort cursors (exclusive prefix of the per-key counts, both species in one
+// packed scan: each count is below 2^29) and reset of the per-step
+// accumulators.
 __device__ void tail_cursors_and_reset(const Run &R) {
     __shared__ unsigned long long sc_u[33];
     const int n1 = R.n_cells + 1;
     const int per = (n1 + kThreads - 1) / kThreads;
-    for (int S = 0; S < 2; ++S) {
-        const int b0 = threadIdx.x * per;
-        unsigned long long run = 0;
-        for (int k = 0; k < per; ++k)
-            if (b0 + k < n1) run += R.acc_cnt[S][b0 + k];
-        unsigned long long tot;
-        unsigned long long ex = block_exclusive_scan<unsigned long long>(run, sc_u, tot);
-        for (int k = 0; k < per; ++k) {
-            const int j = b0 + k;
-            if (j < n1) {
-                R.cursor[S][j] = (unsigned int)ex;
-                ex += R.acc_cnt[S][j];
-            }
+    const int b0 = threadIdx.x * per;
+    unsigned long long run = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < n1) run += R.acc_cnt[0][b0 + k] | (R.acc_cnt[1][b0 + k] << 32);
+    unsigned long long tot;
+    unsigned long long ex = block_exclusive_scan<unsigned long long>(run, sc_u, tot);
+    for (int k = 0; k < per; ++k) {
+        const int j = b0 + k;
+        if (j < n1) {
+            R.cursor[0][j] = (unsigned int)(ex & 0xffffffffull);
+            R.cursor[1][j] = (unsigned int)(ex >> 32);
+            ex += R.acc_cnt[0][j] | (R.acc_cnt[1][j] << 32);
         }
     }
     __syncthreads();
@@ -902,8 +961,7 @@ __device__ void tail(const Run &R, unsigned char *smem, bool diag) {
     DevState *st = R.st;
     const long long step = st->step;
     if (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit2) tail_births<MODE>(R, smem, diag);
-    if (MODE == kExplicitEC || MODE == kExplicitMC) tail_field<MODE>(R, smem, step + 1, true);
-    if (MODE == kImplicit1) tail_field<MODE>(R, smem, step + 1, true);
+    if (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit1) tail_field<MODE>(R, smem, step + 1, true);
     if (MODE == kDepositEC || MODE == kDepositMC) tail_field<MODE>(R, smem, step, false);
     if (MODE == kImplicit1) {
         // pass 1 keeps nothing else; reset its accumulators for pass 2's key counts
@@ -942,10 +1000,8 @@ __device__ void tail(const Run &R, unsigned char *smem, bool diag) {
 // The particle kernel: one launch per explicit step / implicit pass / deposit.
 // ---------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_particles(Run R) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double sc_d[33];
-    __shared__ unsigned long long sc_u[33];
     __shared__ bool s_last;
     using MI = ModeInfo<MODE>;
     DevState *st = R.st;
@@ -966,9 +1022,10 @@ __global__ void __launch_bounds__(kThreads) k_particles(Run R) {
     if (MI::needs_field)
         for (int k = threadIdx.x; k < n + 2; k += kThreads) sm.e[k] = R.e_gather[k];
     for (int k = threadIdx.x; k <= n; k += kThreads) {
-        sm.cnt[k] = 0u;
-        sm.a[k] = 0ull;
-        sm.b[k] = 0ull;
+        sm.acc.cnt[k] = 0u;
+        sm.acc.a[k] = 0u;
+        sm.acc.bh[k] = 0u;
+        sm.acc.bl[k] = 0u;
     }
     if (diag) {
         for (int k = threadIdx.x; k < n; k += kThreads) sm.heat[k] = 0.0f;
@@ -987,12 +1044,15 @@ __global__ void __launch_bounds__(kThreads) k_particles(Run R) {
         if (b >= e) continue;  // uniform across the block
         Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
         const Species sp = R.buf[par][S];
-        if (S == 0)
-            process_segment<MODE, 0>(R, sm, sp, b, e, diag, step, t);
-        else
-            process_segment<MODE, 1>(R, sm, sp, b, e, diag, step, t);
-        flush_species(R, sm, S, MI::count_only);
-        if (MI::push) flush_tally(R, S, t, sc_d, sc_u);
+        for (long long sb = b; sb < e; sb += kFlushEvery) {
+            const long long se = sb + kFlushEvery < e ? sb + kFlushEvery : e;
+            if (S == 0)
+                process_segment<MODE, 0>(R, sm, sp, sb, se, diag, step, t);
+            else
+                process_segment<MODE, 1>(R, sm, sp, sb, se, diag, step, t);
+            flush_species(R, sm, S, MI::count_only);
+        }
+        if (MI::push) flush_tally(R, S, t);
         if (diag) {
             __syncthreads();
             for (int k = threadIdx.x; k < n; k += kThreads) {
@@ -1137,7 +1197,6 @@ __global__ void k_set_abar(Run R) {
 
 // Kinetic energy of the transverse velocities (diagnostics only).
 __global__ void k_perp_energy(Run R) {
-    __shared__ double sc[33];
     const DevState *st = R.st;
     const int par = st->parity;
     for (int S = 0; S < 2; ++S) {
@@ -1150,8 +1209,8 @@ __global__ void k_perp_energy(Run R) {
             const float vy = sp.vy[i], vz = sp.vz[i];
             acc += (double)(vy * vy + vz * vz);
         }
-        const double tot = block_sum<double>(acc, sc);
-        if (threadIdx.x == 0 && tot != 0.0) atomicAdd(&R.st->ke_perp[S], tot * R.half_m_w[S]);
+        const double tot = warp_sum(acc);
+        if ((threadIdx.x & 31) == 0 && tot != 0.0) atomicAdd(&R.st->ke_perp[S], tot * R.half_m_w[S]);
     }
 }
 

@@ -70,7 +70,7 @@ Layout make_layout(const pic_config &c) {
     L.heat[1] = take(8 * n1);
     L.eedf = take(8 * ((size_t)c.eedf_bins + 1));
     const size_t nb = (size_t)(c.births_capacity > 0 ? c.births_capacity : 1);
-    L.births = take(sizeof(Birth) * nb + 4 * nb);
+    L.births = take(sizeof(Birth) * nb + 8 * nb);  // records + rank and sort scratch
     L.total = o;
     return L;
 }
@@ -202,6 +202,7 @@ void derive(pic_handle *h) {
     const double q[2] = {-kE, kE};
     const double m[2] = {kMe, c.ion_mass_amu * kAmu};
     R.dx = dx;
+    R.inv_dx = 1.0 / dx;
     R.dt = c.dt;
     R.rf_freq = c.rf_freq;
     R.rf_volt = R.periodic ? 0.0 : c.rf_volt;

@@ -18,7 +18,7 @@ namespace pic {
 #define PIC_UNROLL 4
 #endif
 #ifndef PIC_MIN_BLOCKS
-#define PIC_MIN_BLOCKS 4
+#define PIC_MIN_BLOCKS 2
 #endif
 
 constexpr int kMaxCells = 1024;          // grid lives in shared memory
@@ -87,7 +87,7 @@ struct Run {
     long long capacity[2];
     long long births_cap;
     // geometry / field (FP64, host-derived)
-    double dx, dt, rf_freq, rf_volt, weight;
+    double dx, inv_dx, dt, rf_freq, rf_volt, weight;
     double kappa;        // E jump per 2^-33 macro charge: e w 2^-33 / eps0
     double kappa_bg;     // E jump per interior node from the frozen ion density
     double chi_coef[2];  // dt^2/2 q^2 w / (m eps0 dx) * 2^-16

@@ -350,6 +350,30 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Exclusive prefix of x over the block; y is replaced by its block total.
+__device__ double block_exclusive_scan2(double x, double &y, double *scratch /*[2*kThreads/32]*/) {
+    constexpr int nw = kThreads / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(FULL_MASK, inc, o);
+        if (lane >= o) inc += t;
+    }
+    const double ys = warp_sum(y);
+    if (lane == 31) scratch[wid] = inc;
+    if (lane == 0) scratch[nw + wid] = ys;
+    __syncthreads();
+    double before = 0.0, ytot = 0.0;
+    for (int k = 0; k < nw; ++k) {
+        if (k < wid) before += scratch[k];
+        ytot += scratch[nw + k];
+    }
+    __syncthreads();
+    y = ytot;
+    return before + inc - x;
+}
+
 // Sum of two doubles over the block (one barrier pair).
 __device__ void block_sum2(double &x, double &y, double *scratch /*[2*kThreads/32]*/) {
     constexpr int nw = kThreads / 32;
@@ -531,41 +555,122 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
     return deposit_key_s2(c, s, a_out);
 }
 
-// Stream one species segment [b, e) through the block: load kUnroll
-// particles per thread, step them independently, then deposit the tile.
+// Vector load / store of U consecutive 4-byte values (U = 1, 2, 4); the
+// address is U*4-byte aligned.
+template <typename T> struct Vec2;
+template <> struct Vec2<int> { using type = int2; };
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<uint32_t> { using type = uint2; };
+template <typename T> struct Vec4;
+template <> struct Vec4<int> { using type = int4; };
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<uint32_t> { using type = uint4; };
+
+template <int U, typename T>
+__device__ __forceinline__ void ldv(const T *p, T (&o)[kUnroll]) {
+    if constexpr (U == 4) {
+        const auto v = *reinterpret_cast<const typename Vec4<T>::type *>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else if constexpr (U == 2) {
+        const auto v = *reinterpret_cast<const typename Vec2<T>::type *>(p);
+        o[0] = v.x; o[1] = v.y;
+    } else {
+        o[0] = p[0];
+    }
+}
+
+template <int U, typename T>
+__device__ __forceinline__ void stv(T *p, const T (&o)[kUnroll]) {
+    if constexpr (U == 4) {
+        typename Vec4<T>::type v;
+        v.x = o[0]; v.y = o[1]; v.z = o[2]; v.w = o[3];
+        *reinterpret_cast<typename Vec4<T>::type *>(p) = v;
+    } else if constexpr (U == 2) {
+        typename Vec2<T>::type v;
+        v.x = o[0]; v.y = o[1];
+        *reinterpret_cast<typename Vec2<T>::type *>(p) = v;
+    } else {
+        p[0] = o[0];
+    }
+}
+
+// Stream one species segment [b, e) through the block.  Each thread takes
+// kUnroll consecutive particles: one vector load per field (the segment
+// start is a multiple of 32 and every array is 256-byte aligned), steps them
+// independently, stores them back the same way and deposits the tile.
 template <int MODE, int S>
-__device__ void process_segment(const Run &R, const SmemMain &sm, const Species &sp, long long b,
+__device__ void process_segment(const Run &R, const SmemMain &sm, const Species &sp0, long long b,
                                 long long e, bool diag, long long step, Tally &t) {
+    constexpr int U = kUnroll;
+    static_assert(U == 1 || U == 2 || U == 4, "vector width");
     using MI = ModeInfo<MODE>;
-    for (long long base = b; base < e; base += (long long)kThreads * kUnroll) {
-        int cell[kUnroll];
-        float off[kUnroll], vx[kUnroll], abar[kUnroll];
-        uint32_t id[kUnroll];
+    Species sp;
+    sp.cell = sp0.cell + b;
+    sp.off = sp0.off + b;
+    sp.vx = sp0.vx + b;
+    sp.vy = sp0.vy + b;
+    sp.vz = sp0.vz + b;
+    sp.id = sp0.id + b;
+    sp.abar = MI::implicit ? sp0.abar + b : nullptr;
+    const int len = (int)(e - b);
+    const bool need_id = MI::push && R.mcc;
+    for (int base = 0; base < len; base += kThreads * U) {
+        const int i0 = base + U * (int)threadIdx.x;
+        const bool full = i0 + U - 1 < len;
+        int cell[U];
+        float off[U], vx[U], abar[U];
+        uint32_t id[U];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const long long i = base + (long long)u * kThreads + threadIdx.x;
-            const bool ok = i < e;
-            cell[u] = ok ? sp.cell[i] : -1;
-            off[u] = ok ? sp.off[i] : 0.0f;
-            vx[u] = (ok && MI::loads_v) ? sp.vx[i] : 0.0f;
-            abar[u] = (ok && MI::implicit) ? sp.abar[i] : 0.0f;
-            id[u] = (ok && MI::push && R.mcc) ? sp.id[i] : 0u;
+        for (int u = 0; u < U; ++u) {
+            vx[u] = 0.0f;
+            abar[u] = 0.0f;
+            id[u] = 0u;
         }
-        int key[kUnroll];
-        uint32_t a[kUnroll];
+        if (full) {
+            ldv<U>(sp.cell + i0, cell);
+            ldv<U>(sp.off + i0, off);
+            if (MI::loads_v) ldv<U>(sp.vx + i0, vx);
+            if (MI::implicit) ldv<U>(sp.abar + i0, abar);
+            if (need_id) ldv<U>(sp.id + i0, id);
+        } else {
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const long long i = base + (long long)u * kThreads + threadIdx.x;
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u;
+                const bool ok = i < len;
+                cell[u] = ok ? sp.cell[i] : -1;
+                off[u] = ok ? sp.off[i] : 0.0f;
+                if (ok && MI::loads_v) vx[u] = sp.vx[i];
+                if (ok && MI::implicit) abar[u] = sp.abar[i];
+                if (ok && need_id) id[u] = sp.id[i];
+            }
+        }
+        int key[U];
+        uint32_t a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
             a[u] = 0u;
             key[u] = -1;
             if (cell[u] < 0) continue;  // beyond the segment, or a hole left by absorption
-            key[u] = step_particle<MODE, S>(R, sm, sp, i, cell[u], off[u], vx[u], abar[u], id[u], diag,
-                                            step, t, a[u]);
-            if (MI::push) {
-                sp.cell[i] = cell[u];
-                sp.off[i] = off[u];
-                sp.vx[i] = vx[u];
-                if (MI::implicit) sp.abar[i] = abar[u];
+            key[u] = step_particle<MODE, S>(R, sm, sp, (long long)(i0 + u), cell[u], off[u], vx[u],
+                                            abar[u], id[u], diag, step, t, a[u]);
+        }
+        if (MI::push) {
+            if (full) {
+                stv<U>(sp.cell + i0, cell);
+                stv<U>(sp.off + i0, off);
+                stv<U>(sp.vx + i0, vx);
+                if (MI::implicit) stv<U>(sp.abar + i0, abar);
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u;
+                    if (i < len) {
+                        sp.cell[i] = cell[u];
+                        sp.off[i] = off[u];
+                        sp.vx[i] = vx[u];
+                        if (MI::implicit) sp.abar[i] = abar[u];
+                    }
+                }
             }
         }
         deposit_tile(key, a, sm.acc, MI::count_only);
@@ -721,21 +826,49 @@ __device__ void tail_births(const Run &R, unsigned char *smem, bool diag) {
     __syncthreads();
     const unsigned int B = s_B, ok = s_ok;
     if (B == 0) return;
-    // rank[b] = number of births with a smaller parent id (ids are unique)
-    uint32_t *pid_chunk = (uint32_t *)smem;  // 2048 entries
-    unsigned int *rank = (unsigned int *)(R.births + R.births_cap);  // scratch after the records
-    for (unsigned int b = threadIdx.x; b < B; b += kThreads) rank[b] = 0u;
-    for (unsigned int c0 = 0; c0 < B; c0 += 2048u) {
-        const unsigned int cn = min(2048u, B - c0);
-        __syncthreads();
-        for (unsigned int k = threadIdx.x; k < cn; k += kThreads) pid_chunk[k] = R.births[c0 + k].pid;
-        __syncthreads();
-        for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
-            const uint32_t p = R.births[b].pid;
-            unsigned int r = 0;
-            for (unsigned int k = 0; k < cn; ++k) r += pid_chunk[k] < p ? 1u : 0u;
-            rank[b] += r;
+    // rank[b] = number of births with a smaller parent id (ids are unique):
+    // counting pass over 2048 buckets of the parent id's top bits, then a
+    // comparison within the bucket.
+    unsigned int *hist = (unsigned int *)smem;                       // [2048]
+    unsigned int *rank = (unsigned int *)(R.births + R.births_cap);  // [births_cap]
+    uint32_t *sorted = (uint32_t *)(rank + R.births_cap);            // [births_cap]
+    const unsigned int max_pid = st->next_id[0];
+    const int bits = 32 - __clz(max_pid | 1u);
+    const int shift = bits > 11 ? bits - 11 : 0;
+    for (int k = threadIdx.x; k < 2048; k += kThreads) hist[k] = 0u;
+    __syncthreads();
+    for (unsigned int b = threadIdx.x; b < B; b += kThreads)
+        rank[b] = atomicAdd(&hist[R.births[b].pid >> shift], 1u);
+    __syncthreads();
+    {
+        __shared__ unsigned int sc_h[33];
+        constexpr int per = 2048 / kThreads;
+        unsigned int loc[per];
+        unsigned int run = 0;
+        for (int k = 0; k < per; ++k) {
+            loc[k] = hist[threadIdx.x * per + k];
+            run += loc[k];
         }
+        unsigned int tot;
+        unsigned int ex = block_exclusive_scan<unsigned int>(run, sc_h, tot);
+        for (int k = 0; k < per; ++k) {
+            hist[threadIdx.x * per + k] = ex;  // bucket start
+            ex += loc[k];
+        }
+    }
+    __syncthreads();
+    for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
+        const uint32_t p = R.births[b].pid;
+        sorted[hist[p >> shift] + rank[b]] = p;
+    }
+    __syncthreads();
+    for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
+        const uint32_t p = R.births[b].pid;
+        const unsigned int bk = p >> shift;
+        const unsigned int lo = hist[bk], hi = bk + 1 < 2048u ? hist[bk + 1] : B;
+        unsigned int r = lo;
+        for (unsigned int k = lo; k < hi; ++k) r += sorted[k] < p ? 1u : 0u;
+        rank[b] = r;
     }
     __syncthreads();
     const int par = st->parity;
@@ -806,7 +939,6 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
     DevState *st = R.st;
     const int n = R.n_cells;
     __shared__ long long sc_ll[33];
-    __shared__ double sc_d[33];
     __shared__ double sc_2[2 * kThreads / 32];
     long long *q = (long long *)smem;               // [n+1] net node charge
     double *rinv = (double *)(smem + 8 * (n + 1));   // [n] 1/(1+chi)
@@ -854,31 +986,37 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
             const double v = R.periodic ? R.kappa * ((double)P - (double)(c + 1) * qbar)
                                         : R.kappa * (double)P + R.kappa_bg * (double)c;
             pp[c] = v;
-            s1 += rinv[c] * v;
-            s0 += rinv[c];
+            s1 += implicit ? rinv[c] * v : v;
+            s0 += implicit ? rinv[c] : 1.0;
         }
     }
     block_sum2(s1, s0, sc_2);
-    double v_left = 0.0;
-    if (!R.periodic) {
-        const double t = (double)level * R.dt;
-        v_left = R.rf_volt * sin(2.0 * 3.14159265358979323846 * R.rf_freq * t);
+    __shared__ double s_v_left, s_d0;
+    if (threadIdx.x == 0) {
+        // scalar FP64 work (slow pipe on this part) done once
+        double v_left = 0.0;
+        if (!R.periodic) {
+            const double t = (double)level * R.dt;
+            v_left = R.rf_volt * sin(2.0 * 3.14159265358979323846 * R.rf_freq * t);
+        }
+        s_v_left = v_left;
+        s_d0 = R.periodic ? -s1 / s0 : (v_left / R.dx - s1) / s0;
     }
-    const double d0 = R.periodic ? -s1 / s0 : (v_left / R.dx - s1) / s0;
-    double wsum = 0.0, esum = 0.0;
+    __syncthreads();
+    const double v_left = s_v_left, d0 = s_d0;
+    double esum = 0.0, wsum = 0.0;
     for (int k = 0; k < per; ++k) {
         const int c = c_begin + k;
         if (c < n) {
-            const double e = rinv[c] * (d0 + pp[c]);
+            const double e = implicit ? rinv[c] * (d0 + pp[c]) : d0 + pp[c];
             ef[c] = e;
             R.e_cc[c] = e;
             wsum += e * e;
             esum += e;
         }
     }
-    // phi_g = phi_0 - dx sum_{c<g} E_c
-    double etot;
-    double acc = block_exclusive_scan<double>(esum, sc_d, etot);
+    // phi_g = phi_0 - dx sum_{c<g} E_c; the field energy rides along
+    double acc = block_exclusive_scan2(esum, wsum, sc_2);
     for (int k = 0; k < per; ++k) {
         const int g = c_begin + k;
         if (g < n) {
@@ -888,8 +1026,6 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
             acc += ef[g];
         }
     }
-    double dummy = 0.0;
-    block_sum2(wsum, dummy, sc_2);
     if (threadIdx.x == 0) {
         R.phi[n] = R.periodic ? v_left : 0.0;  // grounded electrode / periodic image of node 0
         if (accumulate) R.avg_phi[n] += R.phi[n];
@@ -904,13 +1040,13 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
             double e;
             if (R.periodic) {
                 const int gl = (g - 1 + n) % n, gr = (g + 1) % n;
-                e = (R.phi[gl] - R.phi[gr]) / (2.0 * R.dx);
+                e = (R.phi[gl] - R.phi[gr]) * (0.5 * R.inv_dx);
             } else if (g == 0) {
-                e = (R.phi[0] - R.phi[1]) / R.dx;
+                e = (R.phi[0] - R.phi[1]) * R.inv_dx;
             } else if (g == n) {
-                e = (R.phi[n - 1] - R.phi[n]) / R.dx;
+                e = (R.phi[n - 1] - R.phi[n]) * R.inv_dx;
             } else {
-                e = (R.phi[g - 1] - R.phi[g + 1]) / (2.0 * R.dx);
+                e = (R.phi[g - 1] - R.phi[g + 1]) * (0.5 * R.inv_dx);
             }
             R.e_gather[g] = (float)e;
         }
@@ -996,6 +1132,29 @@ __device__ void tail(const Run &R, unsigned char *smem, bool diag) {
     }
 }
 
+// The block's share of the particles: blocks are split between the species in
+// proportion to their slots; each takes a contiguous chunk of one species,
+// a multiple of 32 long (so every chunk starts 16-byte aligned).
+__device__ __forceinline__ void block_segment(long long ne, long long ni, int &S, long long &b,
+                                              long long &e) {
+    const int G = gridDim.x;
+    int ge = G;
+    if (ni > 0) {
+        ge = (int)(((double)G * (double)ne) / (double)(ne + ni) + 0.5);
+        if (ne > 0 && ge < 1) ge = 1;
+        if (ge > G - 1) ge = G - 1;
+    }
+    const int k = blockIdx.x < ge ? (int)blockIdx.x : (int)blockIdx.x - ge;
+    const int gs = blockIdx.x < ge ? ge : G - ge;
+    const long long ns = blockIdx.x < ge ? ne : ni;
+    S = blockIdx.x < ge ? 0 : 1;
+    long long ch = (ns + gs - 1) / gs;
+    ch = (ch + 31) & ~31ll;
+    b = (long long)k * ch;
+    e = b + ch < ns ? b + ch : ns;
+    if (b > e) b = e;
+}
+
 // ---------------------------------------------------------------------------
 // The particle kernel: one launch per explicit step / implicit pass / deposit.
 // ---------------------------------------------------------------------------
@@ -1010,14 +1169,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     const long long step = st->step;
     const bool diag = MI::push && R.diag_period > 0 && (step % R.diag_period) == 0;
     const int par = st->parity;
-    const long long ne = st->n_slots[0];
-    const long long ni = R.ions_mobile ? st->n_slots[1] : 0;
-    const long long total = ne + ni;
-    const long long G = gridDim.x;
-    long long ch = (total + G - 1) / G;
-    ch = (ch + 31) & ~31ll;
-    const long long c0 = (long long)blockIdx.x * ch;
-    const long long c1 = c0 + ch < total ? c0 + ch : total;
+    long long b, e;
+    int S;
+    block_segment(st->n_slots[0], R.ions_mobile ? st->n_slots[1] : 0, S, b, e);
     // shared-memory grid
     if (MI::needs_field)
         for (int k = threadIdx.x; k < n + 2; k += kThreads) sm.e[k] = R.e_gather[k];
@@ -1032,16 +1186,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
         for (int k = threadIdx.x; k <= R.eedf_bins; k += kThreads) sm.eedf[k] = 0u;
     }
     __syncthreads();
-    for (int S = 0; S < 2; ++S) {
-        long long b, e;
-        if (S == 0) {
-            b = c0;
-            e = c1 < ne ? c1 : ne;
-        } else {
-            b = (c0 > ne ? c0 : ne) - ne;
-            e = c1 - ne;
-        }
-        if (b >= e) continue;  // uniform across the block
+    if (b < e) {  // uniform across the block
         Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
         const Species sp = R.buf[par][S];
         for (long long sb = b; sb < e; sb += kFlushEvery) {
@@ -1321,3 +1466,4 @@ cudaError_t launch_load(const Run &r, int species, long long n, float vth, cudaS
 }
 
 }  // namespace pic
+

@@ -222,6 +222,29 @@ int pic_load(pic_handle *h, const void *host_buf, size_t nbytes);
 int pic_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
                     uint32_t c3, int64_t n, uint32_t *out_device, void *stream);
 
+/* Charge assignment of one species for callers that cannot allocate device
+   memory where they need a density (code inside another framework's memory
+   pool, allocation-free real-time loops, tools that hold only particle
+   arrays).  The paper has no counterpart: this is a library convenience
+   beside the run API.
+   cell, off: device arrays of n particles in the storage form (cell index,
+   offset in [0,1)); entries with a cell outside [0, n_cells) are skipped.
+   rho_q_out: device array of n_cells+1 int64 receiving the node charge in
+   units of 2^-33 macro-particle charges, quadratic S_2 weights (EC schemes)
+   or linear S_1 (PIC_MC_EXPLICIT), electrodes or periodic as `boundary` -
+   the same numbers pic_grids() returns for a run holding these particles.
+   The per-node sums live in a static device array of the library sized for
+   n_cells <= 1024 (about 25 KB on every GPU that loads the library, held
+   until the process exits); no other memory is used and nothing is
+   allocated.  The first call on a device looks up that array's device
+   address; make it before any stream capture on that device.  All calls on
+   one device share the array: calls that overlap on the GPU race (calls on
+   one stream are ordered).  Asynchronous on `stream`.  Returns PIC_OK;
+   PIC_EINVAL for n_cells outside 2..1024, n outside 0..2^29-1, an unknown
+   scheme or boundary, or a NULL array; PIC_ECUDA if a launch fails. */
+int pic_deposit_noalloc(int32_t scheme, int32_t boundary, int32_t n_cells, const int32_t *cell,
+                        const float *off, int64_t n, int64_t *rho_q_out, void *stream);
+
 void pic_free(pic_handle *h);
 
 /* Message of the last failing call on h (h may be NULL for pic_init /

@@ -91,6 +91,8 @@ SIGNATURES = {
     "pic_save": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "pic_load": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "pic_philox_fill": ([ctypes.c_uint32] * 6 + [ctypes.c_int64, _vp, _vp], ctypes.c_int),
+    "pic_deposit_noalloc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int64,
+                             _vp, _vp], ctypes.c_int),
     "pic_free": ([_vp], None),
     "pic_last_error": ([_vp], ctypes.c_char_p),
 }

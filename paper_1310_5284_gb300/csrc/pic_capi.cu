@@ -148,6 +148,8 @@ constexpr uint64_t kSnapMagic = 0x3150434950434547ull;
 
 }  // namespace
 
+void pic::set_last_error(const char *msg) { g_error = msg; }
+
 struct pic_handle {
     pic_config cfg;
     Layout layout;

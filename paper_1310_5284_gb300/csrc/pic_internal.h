@@ -132,5 +132,7 @@ cudaError_t launch_perp_energy(const Run &r, cudaStream_t s);
 cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
                                uint32_t c3, long long n, uint32_t *out, cudaStream_t s);
 cudaError_t occupancy_grid(const Run &r, Mode m, int *grid);
+// message returned by pic_last_error(NULL) (pic_capi.cu)
+void set_last_error(const char *msg);
 
 }  // namespace pic

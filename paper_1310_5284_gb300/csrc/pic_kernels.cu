@@ -14,6 +14,7 @@
 #include "pic_internal.h"
 
 #include <cstdint>
+#include <mutex>
 
 namespace pic {
 
@@ -1467,3 +1468,187 @@ cudaError_t launch_load(const Run &r, int species, long long n, float vth, cudaS
 
 }  // namespace pic
 
+// ===========================================================================
+// Charge assignment without caller-provided scratch (pic_deposit_noalloc).
+//
+// Some callers cannot allocate device memory at the point where they need a
+// charge density: code running inside another framework's memory pool that
+// forbids foreign allocations, real-time loops that must not hit the
+// allocator, or tools that only hold the particle arrays.  For them the
+// per-node sums live in this file-scope device array, sized for the largest
+// grid the library accepts.  Every GPU that loads the library keeps it
+// (about 25 KB) until the process exits.  All calls on a device share it, so
+// calls that overlap on the GPU (different streams, or a second call
+// enqueued before the first finished on another stream) race; calls on one
+// stream are ordered and safe.
+// ===========================================================================
+namespace pic {
+namespace noalloc {
+
+constexpr int kScratchKeys = kMaxCells + 1;
+// [0, 3*kScratchKeys): count, sum a, sum a^2 per key; then the arrival counter
+static __device__ __align__(256) unsigned long long g_scratch[3 * kScratchKeys + 32];
+
+__global__ void __launch_bounds__(kThreads) k_deposit(const int32_t *__restrict__ cell,
+                                                      const float *__restrict__ off, long long n,
+                                                      int n_cells, int periodic, int s1,
+                                                      unsigned long long *scratch, long long *out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ bool s_last;
+    unsigned long long *C = scratch, *A = scratch + kScratchKeys, *B = scratch + 2 * kScratchKeys;
+    unsigned int *done = (unsigned int *)(scratch + 3 * kScratchKeys);
+    Acc acc;
+    acc.cnt = (unsigned int *)smem;
+    acc.a = acc.cnt + kScratchKeys;
+    acc.bh = acc.a + kScratchKeys;
+    acc.bl = acc.bh + kScratchKeys;
+    const int n1 = n_cells + 1;
+    for (int k = threadIdx.x; k < n1; k += kThreads) {
+        acc.cnt[k] = 0u;
+        acc.a[k] = 0u;
+        acc.bh[k] = 0u;
+        acc.bl[k] = 0u;
+    }
+    __syncthreads();
+    const long long G = gridDim.x;
+    long long ch = (n + G - 1) / G;
+    ch = (ch + 31) & ~31ll;
+    const long long c0 = (long long)blockIdx.x * ch;
+    const long long c1 = c0 + ch < n ? c0 + ch : n;
+    for (long long sb = c0; sb < c1; sb += kFlushEvery) {
+        const long long se = sb + kFlushEvery < c1 ? sb + kFlushEvery : c1;
+        for (long long base = sb; base < se; base += (long long)kThreads * kUnroll) {
+            int key[kUnroll];
+            uint32_t a[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const long long i = base + (long long)u * kThreads + threadIdx.x;
+                key[u] = -1;
+                a[u] = 0u;
+                if (i < se) {
+                    const int c = cell[i];
+                    if (c >= 0 && c < n_cells)
+                        key[u] = s1 ? deposit_key_s1(c, off[i], a[u]) : deposit_key_s2(c, off[i], a[u]);
+                }
+            }
+            deposit_tile(key, a, acc, false);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < n1; k += kThreads) {
+            if (acc.cnt[k]) {
+                atomicAdd(&C[k], (unsigned long long)acc.cnt[k]);
+                atomicAdd(&A[k], (unsigned long long)acc.a[k]);
+                atomicAdd(&B[k], ((unsigned long long)acc.bh[k] << 16) + acc.bl[k]);
+                acc.cnt[k] = 0u;
+                acc.a[k] = 0u;
+                acc.bh[k] = 0u;
+                acc.bl[k] = 0u;
+            }
+        }
+        __syncthreads();
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // node charges from the per-key sums (the same reassembly as the step tail)
+    for (int g = threadIdx.x; g <= n_cells; g += kThreads) {
+        unsigned long long q = 0;
+        if (s1) {
+            if (!(periodic && g == n_cells)) {
+                if (g < n_cells) q += (C[g] << 16) - A[g];
+                const int gl = periodic ? (g - 1 + n_cells) % n_cells : g - 1;
+                if (gl >= 0 && gl < n_cells) q += A[gl];
+                q <<= 17;
+            }
+        } else if (!(periodic && g == n_cells)) {
+            unsigned long long c[3], aa[3], bb[3];
+            for (int d = 0; d < 3; ++d) {
+                int k = g - 1 + d;
+                c[d] = aa[d] = bb[d] = 0ull;
+                if (periodic) {
+                    k = ((k % n_cells) + n_cells) % n_cells;
+                    c[d] = C[k] + (k == 0 ? C[n_cells] : 0ull);
+                    aa[d] = A[k] + (k == 0 ? A[n_cells] : 0ull);
+                    bb[d] = B[k] + (k == 0 ? B[n_cells] : 0ull);
+                } else if (k >= 0 && k <= n_cells) {
+                    c[d] = C[k];
+                    aa[d] = A[k];
+                    bb[d] = B[k];
+                }
+            }
+            q = (c[1] << 32) + (aa[1] << 17) - 2ull * bb[1] + bb[0] + (c[2] << 32) - (aa[2] << 17) + bb[2];
+            if (!periodic) {
+                if (g == 0) q += (c[1] << 32) - (aa[1] << 17) + bb[1];
+                if (g == n_cells) q += bb[1];
+            }
+        }
+        out[g] = (long long)q;
+    }
+}
+
+// Device address of the scratch array, looked up once per device.
+struct DeviceSlot {
+    bool ready;
+    unsigned long long *ptr;
+};
+static DeviceSlot g_slots[64];
+static std::mutex g_slots_mutex;
+
+}  // namespace noalloc
+}  // namespace pic
+
+extern "C" int pic_deposit_noalloc(int32_t scheme, int32_t boundary, int32_t n_cells,
+                                   const int32_t *cell, const float *off, int64_t n,
+                                   int64_t *rho_q_out, void *stream) {
+    using namespace pic;
+    using namespace pic::noalloc;
+    if (scheme < 0 || scheme > 2 || (boundary != 0 && boundary != 1)) {
+        set_last_error("pic_deposit_noalloc: unknown scheme or boundary");
+        return -1;
+    }
+    if (n_cells < 2 || n_cells > kMaxCells) {  // the scratch holds at most kMaxCells + 1 keys
+        set_last_error("pic_deposit_noalloc: n_cells outside 2..1024 (size of the static scratch)");
+        return -1;
+    }
+    if (n < 0 || n >= (1ll << 29) || !rho_q_out || (n > 0 && (!cell || !off))) {
+        set_last_error("pic_deposit_noalloc: n outside 0..2^29-1 or a NULL array");
+        return -1;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        set_last_error("pic_deposit_noalloc: no current CUDA device");
+        return -5;
+    }
+    unsigned long long *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_slots_mutex);
+        if (!g_slots[dev].ready) {
+            // set-up on this device (the current one): the host-side name of a
+            // __device__ array is not a device address; ask the runtime for it
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+                set_last_error("pic_deposit_noalloc: cudaGetSymbolAddress failed");
+                return -5;
+            }
+            g_slots[dev].ptr = (unsigned long long *)p;
+            g_slots[dev].ready = true;
+        }
+        scratch = g_slots[dev].ptr;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's sums: clear it on this stream first
+    if (cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (3 * kScratchKeys + 32), s) != cudaSuccess)
+        return -5;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -5;
+    long long grid = (n + 8191) / 8192;
+    if (grid < 1) grid = 1;
+    if (grid > 4ll * sms) grid = 4ll * sms;
+    const int smem = 16 * kScratchKeys;
+    k_deposit<<<(int)grid, kThreads, smem, s>>>(cell, off, (long long)n, n_cells, boundary == 1,
+                                               scheme == 1, scratch, (long long *)rho_q_out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -5;
+}

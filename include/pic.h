@@ -222,6 +222,45 @@ int pic_load(pic_handle *h, const void *host_buf, size_t nbytes);
 int pic_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
                     uint32_t c3, int64_t n, uint32_t *out_device, void *stream);
 
+/* ---- Batched runs ----
+   Many independent discharges (different grids, particle counts, pressures,
+   voltages, schemes) in one caller-owned arena, advanced together by
+   persistent launches over all runs: each step is one launch for the
+   explicit runs and the implicit predictor, one for the implicit corrector,
+   and one counting sort every sort period, replayed from a captured CUDA
+   graph.  Each run gives bit-identical particles to the same configuration
+   run alone with pic_init/pic_step (charge sums are integers and draws are
+   keyed on (particle id, step, run)); the paper's sweeps of grid spacing,
+   time step and pressure (Sec. 3) are the use case. */
+typedef struct pic_batch pic_batch;
+
+/* Arena bytes for nruns configurations (1..1024), each validated as in
+   pic_required_sizes. */
+int pic_batch_required_sizes(const pic_config *cfgs, int32_t nruns, pic_sizes *out);
+/* Create the batch in a caller-owned device arena (256-byte aligned) and load
+   every run (uniform load, t = 0 field, one sort).  The batch sort period is
+   the smallest positive sort_period of the configurations (16 if none). */
+int pic_batch_init(const pic_config *cfgs, int32_t nruns, const pic_buffers *bufs, void *stream,
+                   pic_batch **out);
+/* Enqueue n steps of every run (asynchronous). */
+int pic_batch_step(pic_batch *b, int64_t n);
+/* Diagnostics and particles of one run (synchronising; as pic_diag and
+   pic_get_particles). */
+int pic_batch_diag(pic_batch *b, int32_t run, pic_diag_t *out, int reset_avg);
+int pic_batch_get_particles(pic_batch *b, int32_t run, int species, pic_host_particles *out);
+/* Work-item size (particles per item, 256..2^24) and sort period (0: never)
+   of the batched launches.  Results do not depend on them. */
+int pic_batch_set_schedule(pic_batch *b, int64_t chunk, int32_t sort_period);
+/* Time whole sort cycles of at least trial_steps steps for each candidate
+   schedule (work items of 4096..65536 particles, sort periods 4..32), keep
+   the fastest and report it.  The trial steps are ordinary steps of the runs
+   (every schedule gives the same particles), so the runs advance by them. */
+int pic_batch_autotune(pic_batch *b, int32_t trial_steps, int64_t *chunk, int32_t *sort_period,
+                       double *ms_per_step);
+/* OR of the runs' device status words (synchronising). */
+int pic_batch_status(pic_batch *b, uint32_t *status);
+void pic_batch_free(pic_batch *b);
+
 /* Charge assignment of one species for callers that cannot allocate device
    memory where they need a density (code inside another framework's memory
    pool, allocation-free real-time loops, tools that hold only particle

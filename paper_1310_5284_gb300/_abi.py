@@ -91,6 +91,16 @@ SIGNATURES = {
     "pic_save": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "pic_load": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "pic_philox_fill": ([ctypes.c_uint32] * 6 + [ctypes.c_int64, _vp, _vp], ctypes.c_int),
+    "pic_batch_required_sizes": ([_vp, ctypes.c_int32, _P(PicSizes)], ctypes.c_int),
+    "pic_batch_init": ([_vp, ctypes.c_int32, _P(PicBuffers), _vp, _P(_vp)], ctypes.c_int),
+    "pic_batch_step": ([_vp, ctypes.c_int64], ctypes.c_int),
+    "pic_batch_diag": ([_vp, ctypes.c_int32, _P(PicDiag), ctypes.c_int], ctypes.c_int),
+    "pic_batch_get_particles": ([_vp, ctypes.c_int32, ctypes.c_int, _P(PicHostParticles)], ctypes.c_int),
+    "pic_batch_set_schedule": ([_vp, ctypes.c_int64, ctypes.c_int32], ctypes.c_int),
+    "pic_batch_autotune": ([_vp, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int32),
+                            _P(ctypes.c_double)], ctypes.c_int),
+    "pic_batch_status": ([_vp, _P(ctypes.c_uint32)], ctypes.c_int),
+    "pic_batch_free": ([_vp], None),
     "pic_deposit_noalloc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int64,
                              _vp, _vp], ctypes.c_int),
     "pic_free": ([_vp], None),

@@ -26,14 +26,6 @@ constexpr double kTorrPa = 101325.0 / 760.0;
 
 thread_local std::string g_error;
 
-struct Layout {
-    size_t state;
-    size_t sp[2][2][7];  // [parity][species][field] offsets (cell, off, vx, vy, vz, id, abar)
-    size_t acc_cnt[2], acc_a[2], acc_b[2], cursor[2], rho_q[2];
-    size_t e_gather, e_cc, phi, chi, avg_ne, avg_ni, avg_phi, heat[2], eedf, births;
-    size_t total;
-};
-
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 Layout make_layout(const pic_config &c) {
@@ -61,11 +53,10 @@ Layout make_layout(const pic_config &c) {
     }
     L.e_gather = take(4 * (n1 + 1));
     L.e_cc = take(8 * n1);
-    L.phi = take(8 * n1);
     L.chi = take(8 * n1);
     L.avg_ne = take(8 * n1);
     L.avg_ni = take(8 * n1);
-    L.avg_phi = take(8 * n1);
+    L.avg_e = take(8 * n1);
     L.heat[0] = take(8 * n1);
     L.heat[1] = take(8 * n1);
     L.eedf = take(8 * ((size_t)c.eedf_bins + 1));
@@ -182,9 +173,7 @@ int cuda_fail(pic_handle *h, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
     } while (0)
 
-void derive(pic_handle *h) {
-    const pic_config &c = h->cfg;
-    Run &R = h->run;
+void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R) {
     std::memset(&R, 0, sizeof R);
     R.n_cells = c.n_cells;
     R.periodic = c.boundary == PIC_BC_PERIODIC;
@@ -196,6 +185,10 @@ void derive(pic_handle *h) {
     R.sort_period = c.sort_period;
     R.seed = c.seed;
     R.run = c.run;
+    for (int r = 0; r < 10; ++r) {  // Philox4x32-10 key schedule (Weyl increments)
+        R.rk0[r] = c.seed + (uint32_t)r * 0x9E3779B9u;
+        R.rk1[r] = c.run + (uint32_t)r * 0xBB67AE85u;
+    }
     R.capacity[0] = c.capacity[0];
     R.capacity[1] = c.capacity[1];
     R.births_cap = c.births_capacity > 0 ? c.births_capacity : 1;
@@ -260,8 +253,6 @@ void derive(pic_handle *h) {
     R.two_m_over_M = (float)(2.0 * kMe / m[1]);
     R.two_e_over_me = (float)(2.0 * kE / kMe);
     // pointers
-    unsigned char *A = h->arena;
-    const Layout &L = h->layout;
     for (int p = 0; p < 2; ++p)
         for (int s = 0; s < 2; ++s) {
             Species &sp = R.buf[p][s];
@@ -283,11 +274,10 @@ void derive(pic_handle *h) {
     }
     R.e_gather = (float *)(A + L.e_gather);
     R.e_cc = (double *)(A + L.e_cc);
-    R.phi = (double *)(A + L.phi);
     R.chi = (double *)(A + L.chi);
     R.avg_ne = (double *)(A + L.avg_ne);
     R.avg_ni = (double *)(A + L.avg_ni);
-    R.avg_phi = (double *)(A + L.avg_phi);
+    R.avg_e = (double *)(A + L.avg_e);
     R.eedf = (unsigned long long *)(A + L.eedf);
     R.births = (Birth *)(A + L.births);
     R.st = (DevState *)(A + L.state);
@@ -323,6 +313,139 @@ int read_state(pic_handle *h, DevState *st) {
 }
 
 }  // namespace
+
+namespace pic {
+
+Layout make_run_layout(const pic_config &c) { return make_layout(c); }
+int validate_run_config(const pic_config *c) { return validate(c); }
+void derive_run(const pic_config &c, const Layout &L, unsigned char *arena, Run &R) {
+    derive_impl(c, L, arena, R);
+}
+Mode push_mode_of(const pic_config &c) { return push_mode(c); }
+Mode deposit_mode_of(const pic_config &c) { return deposit_mode(c); }
+
+#define CKE(call)                                                                  \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            char b_[512];                                                          \
+            snprintf(b_, sizeof b_, "%s: %s", #call, cudaGetErrorString(e_));     \
+            g_error = b_;                                                          \
+            if (err) *err = b_;                                                    \
+            return PIC_ECUDA;                                                      \
+        }                                                                          \
+    } while (0)
+
+int run_diag(const Run &R, const pic_config &c, const Layout &L, unsigned char *arena, cudaStream_t s,
+             pic_diag_t *out, int reset_avg, std::string *err) {
+    CKE(cudaMemsetAsync(R.st->ke_perp, 0, sizeof(double) * 2, s));
+    CKE(launch_perp_energy(R, s));
+    CKE(cudaStreamSynchronize(s));
+    DevState st;
+    CKE(cudaMemcpy(&st, R.st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof *out);
+    out->step = st.step;
+    for (int k = 0; k < 2; ++k) {
+        out->count[k] = st.n_live[k];
+        for (int w = 0; w < 2; ++w) {
+            out->wall_count[k][w] = st.wall_count[k][w];
+            out->wall_energy_ev[k][w] = st.wall_energy[k][w];
+        }
+        out->overflow[k] = st.overflow[k];
+        out->ke_x[k] = st.ke_x[k] * R.half_m_w[k];
+        out->ke_perp[k] = st.ke_perp[k];
+        out->power[k] = st.power[k];
+    }
+    for (int k = 0; k < 5; ++k) out->coll[k] = st.coll[k];
+    out->births = st.births_total;
+    out->field_energy = st.field_energy;
+    out->field_energy_push = st.field_energy_push;
+    out->n_avg = st.n_avg;
+    out->n_diag = st.n_diag;
+    out->status = st.status;
+    if (reset_avg) {
+        const size_t n1 = (size_t)c.n_cells + 1;
+        CKE(cudaMemsetAsync(arena + L.avg_ne, 0, 8 * n1, s));
+        CKE(cudaMemsetAsync(arena + L.avg_ni, 0, 8 * n1, s));
+        CKE(cudaMemsetAsync(arena + L.avg_e, 0, 8 * n1, s));
+        CKE(cudaMemsetAsync(&R.st->v_sum, 0, sizeof(double), s));
+        CKE(cudaMemsetAsync(arena + L.heat[0], 0, 8 * n1, s));
+        CKE(cudaMemsetAsync(arena + L.heat[1], 0, 8 * n1, s));
+        CKE(cudaMemsetAsync(arena + L.eedf, 0, 8 * ((size_t)c.eedf_bins + 1), s));
+        CKE(cudaMemsetAsync(&R.st->n_avg, 0, sizeof(long long) * 2, s));
+        CKE(cudaStreamSynchronize(s));
+    }
+    return PIC_OK;
+}
+
+int init_run_state(const pic_config &c, const Run &R, unsigned char *arena, size_t arena_bytes, int grid,
+                   cudaStream_t s, std::string *err) {
+    CKE(cudaMemsetAsync(arena, 0, arena_bytes, s));
+    DevState st;
+    std::memset(&st, 0, sizeof st);
+    st.n_slots[0] = st.n_live[0] = c.np_init;
+    st.n_slots[1] = st.n_live[1] = c.ions_mobile ? c.np_init : 0;
+    st.next_id[0] = (unsigned int)c.np_init;
+    st.next_id[1] = (unsigned int)st.n_slots[1];
+    CKE(cudaMemcpyAsync(R.st, &st, sizeof st, cudaMemcpyHostToDevice, s));
+    CKE(cudaStreamSynchronize(s));
+    const double vth_e = std::sqrt(kE * c.te_ev / kMe);
+    const double vth_i = std::sqrt(kE * c.ti_ev / (c.ion_mass_amu * kAmu));
+    CKE(launch_load(R, 0, c.np_init, (float)vth_e, s));
+    if (c.ions_mobile) CKE(launch_load(R, 1, c.np_init, (float)vth_i, s));
+    // t = 0 charge assignment and field, abar = a^0 for the implicit scheme
+    CKE(launch_particles(R, deposit_mode(c), grid, s));
+    if (c.scheme == PIC_EC_IMPLICIT) CKE(launch_set_abar(R, s));
+    // the load is in random order: sort it once so that every block streams
+    // particles of a few adjacent cells from the first step on
+    CKE(launch_sort(R, grid, s));
+    return PIC_OK;
+}
+
+int run_get_particles(const Run &R, cudaStream_t s, int species, pic_host_particles *out, std::string *err) {
+    CKE(cudaStreamSynchronize(s));
+    DevState st;
+    CKE(cudaMemcpy(&st, R.st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    if (out->count < st.n_live[species]) {
+        char b[256];
+        snprintf(b, sizeof b, "host arrays hold %lld, %lld live particles", (long long)out->count,
+                 (long long)st.n_live[species]);
+        g_error = b;
+        if (err) *err = b;
+        return PIC_EINVAL;
+    }
+    const long long ns = st.n_slots[species];
+    const Species &sp = R.buf[st.parity][species];
+    std::vector<int32_t> cell(ns);
+    std::vector<float> off(ns), vx(ns), vy(ns), vz(ns), ab(ns);
+    std::vector<uint32_t> id(ns);
+    if (ns > 0) {
+        CKE(cudaMemcpy(cell.data(), sp.cell, 4 * ns, cudaMemcpyDeviceToHost));
+        CKE(cudaMemcpy(off.data(), sp.off, 4 * ns, cudaMemcpyDeviceToHost));
+        CKE(cudaMemcpy(vx.data(), sp.vx, 4 * ns, cudaMemcpyDeviceToHost));
+        CKE(cudaMemcpy(vy.data(), sp.vy, 4 * ns, cudaMemcpyDeviceToHost));
+        CKE(cudaMemcpy(vz.data(), sp.vz, 4 * ns, cudaMemcpyDeviceToHost));
+        CKE(cudaMemcpy(id.data(), sp.id, 4 * ns, cudaMemcpyDeviceToHost));
+        if (sp.abar) CKE(cudaMemcpy(ab.data(), sp.abar, 4 * ns, cudaMemcpyDeviceToHost));
+    }
+    long long k = 0;
+    for (long long i = 0; i < ns; ++i) {
+        if (cell[i] < 0) continue;
+        if (out->cell) out->cell[k] = cell[i];
+        if (out->off) out->off[k] = off[i];
+        if (out->vx) out->vx[k] = vx[i];
+        if (out->vy) out->vy[k] = vy[i];
+        if (out->vz) out->vz[k] = vz[i];
+        if (out->id) out->id[k] = id[i];
+        if (out->abar) out->abar[k] = sp.abar ? ab[i] : 0.0f;
+        ++k;
+    }
+    out->count = k;
+    out->next_id = st.next_id[species];
+    return PIC_OK;
+}
+
+}  // namespace pic
 
 extern "C" {
 
@@ -360,7 +483,7 @@ int pic_init(const pic_config *cfg, const pic_buffers *bufs, void *stream, pic_h
     h->host_step = 0;
     h->cycle_graph = nullptr;
     h->cycle_len = 0;
-    derive(h);
+    derive_impl(h->cfg, h->layout, h->arena, h->run);
     auto bail = [&](int code) {
         g_error = h->err.empty() ? g_error : h->err;
         delete h;
@@ -377,38 +500,8 @@ int pic_init(const pic_config *cfg, const pic_buffers *bufs, void *stream, pic_h
         occupancy_grid(h->run, kImplicit2, &g2);
         h->grid_push = g1 < g2 ? g1 : g2;
     }
-    if (cudaMemsetAsync(h->arena, 0, L.total, h->stream) != cudaSuccess) {
-        cuda_fail(h, cudaGetLastError(), "cudaMemsetAsync(arena)");
-        return bail(PIC_ECUDA);
-    }
-    DevState st;
-    std::memset(&st, 0, sizeof st);
-    st.n_slots[0] = st.n_live[0] = cfg->np_init;
-    st.n_slots[1] = st.n_live[1] = cfg->ions_mobile ? cfg->np_init : 0;
-    st.next_id[0] = (unsigned int)cfg->np_init;
-    st.next_id[1] = (unsigned int)st.n_slots[1];
-    if (cudaMemcpyAsync(h->run.st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
-        cudaStreamSynchronize(h->stream) != cudaSuccess) {
-        cuda_fail(h, cudaGetLastError(), "state upload");
-        return bail(PIC_ECUDA);
-    }
-    const double vth_e = std::sqrt(kE * cfg->te_ev / kMe);
-    const double vth_i = std::sqrt(kE * cfg->ti_ev / (cfg->ion_mass_amu * kAmu));
-    cudaError_t e = launch_load(h->run, 0, cfg->np_init, (float)vth_e, h->stream);
-    if (e == cudaSuccess && cfg->ions_mobile) e = launch_load(h->run, 1, cfg->np_init, (float)vth_i, h->stream);
-    if (e != cudaSuccess) {
-        cuda_fail(h, e, "load");
-        return bail(PIC_ECUDA);
-    }
-    r = pic_init_field(h, 1);
+    r = init_run_state(*cfg, h->run, h->arena, L.total, h->grid_push, h->stream, &h->err);
     if (r) return bail(r);
-    // the load is in random order: sort it once so that every block streams
-    // particles of a few adjacent cells from the first step on
-    e = launch_sort(h->run, h->grid_sort, h->stream);
-    if (e != cudaSuccess) {
-        cuda_fail(h, e, "sort");
-        return bail(PIC_ECUDA);
-    }
     *out = h;
     return PIC_OK;
 }
@@ -463,45 +556,7 @@ int pic_step(pic_handle *h, int64_t n) {
 
 int pic_diag(pic_handle *h, pic_diag_t *out, int reset_avg) {
     if (!h || !out) return fail(PIC_EINVAL, "NULL argument");
-    CK(h, cudaMemsetAsync(h->run.st->ke_perp, 0, sizeof(double) * 2, h->stream));
-    CK(h, launch_perp_energy(h->run, h->stream));
-    DevState st;
-    int r = read_state(h, &st);
-    if (r) return r;
-    std::memset(out, 0, sizeof *out);
-    out->step = st.step;
-    for (int s = 0; s < 2; ++s) {
-        out->count[s] = st.n_live[s];
-        for (int w = 0; w < 2; ++w) {
-            out->wall_count[s][w] = st.wall_count[s][w];
-            out->wall_energy_ev[s][w] = st.wall_energy[s][w];
-        }
-        out->overflow[s] = st.overflow[s];
-        out->ke_x[s] = st.ke_x[s] * h->run.half_m_w[s];
-        out->ke_perp[s] = st.ke_perp[s];
-        out->power[s] = st.power[s];
-    }
-    for (int k = 0; k < 5; ++k) out->coll[k] = st.coll[k];
-    out->births = st.births_total;
-    out->field_energy = st.field_energy;
-    out->field_energy_push = st.field_energy_push;
-    out->n_avg = st.n_avg;
-    out->n_diag = st.n_diag;
-    out->status = st.status;
-    if (reset_avg) {
-        const Layout &L = h->layout;
-        const size_t n1 = (size_t)h->cfg.n_cells + 1;
-        CK(h, cudaMemsetAsync(h->arena + L.avg_ne, 0, 8 * n1, h->stream));
-        CK(h, cudaMemsetAsync(h->arena + L.avg_ni, 0, 8 * n1, h->stream));
-        CK(h, cudaMemsetAsync(h->arena + L.avg_phi, 0, 8 * n1, h->stream));
-        CK(h, cudaMemsetAsync(h->arena + L.heat[0], 0, 8 * n1, h->stream));
-        CK(h, cudaMemsetAsync(h->arena + L.heat[1], 0, 8 * n1, h->stream));
-        CK(h, cudaMemsetAsync(h->arena + L.eedf, 0, 8 * ((size_t)h->cfg.eedf_bins + 1), h->stream));
-        CK(h, cudaMemsetAsync(&h->run.st->n_avg, 0, sizeof(long long) * 2, h->stream));
-        r = sync(h);
-        if (r) return r;
-    }
-    return PIC_OK;
+    return run_diag(h->run, h->cfg, h->layout, h->arena, h->stream, out, reset_avg, &h->err);
 }
 
 int pic_profiles(pic_handle *h, double *ne, double *ni, double *phi, double *heat_e,
@@ -513,17 +568,29 @@ int pic_profiles(pic_handle *h, double *ne, double *ni, double *phi, double *hea
     const size_t n1 = (size_t)h->cfg.n_cells + 1, n = (size_t)h->cfg.n_cells;
     const double na = st.n_avg > 0 ? (double)st.n_avg : 1.0;
     const double nd = st.n_diag > 0 ? (double)st.n_diag : 1.0;
-    auto fetch = [&](double *dst, double *src, size_t cnt, double div) -> int {
+    auto fetch = [&](double *dst, double *src, size_t cnt, double scale) -> int {
         if (!dst) return PIC_OK;
         CK(h, cudaMemcpy(dst, src, 8 * cnt, cudaMemcpyDeviceToHost));
-        for (size_t k = 0; k < cnt; ++k) dst[k] /= div;
+        for (size_t k = 0; k < cnt; ++k) dst[k] *= scale;
         return PIC_OK;
     };
-    if ((r = fetch(ne, h->run.avg_ne, n1, na))) return r;
-    if ((r = fetch(ni, h->run.avg_ni, n1, na))) return r;
-    if ((r = fetch(phi, h->run.avg_phi, n1, na))) return r;
-    if ((r = fetch(heat_e, h->run.heat[0], n, nd))) return r;
-    if ((r = fetch(heat_i, h->run.heat[1], n, nd))) return r;
+    if ((r = fetch(ne, h->run.avg_ne, n1, h->run.dens_scale / na))) return r;
+    if ((r = fetch(ni, h->run.avg_ni, n1, h->run.dens_scale / na))) return r;
+    if ((r = fetch(heat_e, h->run.heat[0], n, 1.0 / nd))) return r;
+    if ((r = fetch(heat_i, h->run.heat[1], n, 1.0 / nd))) return r;
+    if (phi) {
+        // the averaged potential follows linearly from the averaged field and
+        // electrode voltage: phi_g = <V> - dx sum_{c<g} <E_c>
+        std::vector<double> e(n);
+        if ((r = fetch(e.data(), h->run.avg_e, n, 1.0 / na))) return r;
+        const bool periodic = h->cfg.boundary == PIC_BC_PERIODIC;
+        double acc = periodic ? 0.0 : st.v_sum / na;
+        for (size_t g = 0; g < n; ++g) {
+            phi[g] = acc;
+            acc -= h->run.dx * e[g];
+        }
+        phi[n] = periodic ? phi[0] : 0.0;
+    }
     if (eedf) CK(h, cudaMemcpy(eedf, h->run.eedf, 8 * ((size_t)h->cfg.eedf_bins + 1), cudaMemcpyDeviceToHost));
     return PIC_OK;
 }
@@ -536,8 +603,21 @@ int pic_grids(pic_handle *h, int64_t *rho_q_e, int64_t *rho_q_i, double *phi, do
     const size_t n1 = (size_t)h->cfg.n_cells + 1, n = (size_t)h->cfg.n_cells;
     if (rho_q_e) CK(h, cudaMemcpy(rho_q_e, h->run.rho_q[0], 8 * n1, cudaMemcpyDeviceToHost));
     if (rho_q_i) CK(h, cudaMemcpy(rho_q_i, h->run.rho_q[1], 8 * n1, cudaMemcpyDeviceToHost));
-    if (phi) CK(h, cudaMemcpy(phi, h->run.phi, 8 * n1, cudaMemcpyDeviceToHost));
     if (e_cc) CK(h, cudaMemcpy(e_cc, h->run.e_cc, 8 * n, cudaMemcpyDeviceToHost));
+    if (phi) {
+        // node potential from the cell-centred field: phi_g = V - dx sum_{c<g} E_c
+        std::vector<double> e(n);
+        DevState st;
+        CK(h, cudaMemcpy(e.data(), h->run.e_cc, 8 * n, cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpy(&st, h->run.st, sizeof st, cudaMemcpyDeviceToHost));
+        const bool periodic = h->cfg.boundary == PIC_BC_PERIODIC;
+        double acc = periodic ? 0.0 : st.v_left;
+        for (size_t g = 0; g < n; ++g) {
+            phi[g] = acc;
+            acc -= h->run.dx * e[g];
+        }
+        phi[n] = periodic ? phi[0] : 0.0;
+    }
     if (chi) CK(h, cudaMemcpy(chi, h->run.chi, 8 * n, cudaMemcpyDeviceToHost));
     return PIC_OK;
 }
@@ -554,41 +634,7 @@ int pic_count(pic_handle *h, int64_t *n_e, int64_t *n_i) {
 
 int pic_get_particles(pic_handle *h, int species, pic_host_particles *out) {
     if (!h || !out || species < 0 || species > 1) return fail(PIC_EINVAL, "bad argument");
-    DevState st;
-    int r = read_state(h, &st);
-    if (r) return r;
-    if (out->count < st.n_live[species])
-        return fail(PIC_EINVAL, "host arrays hold %lld, %lld live particles", (long long)out->count,
-                    (long long)st.n_live[species]);
-    const long long ns = st.n_slots[species];
-    const Species &sp = h->run.buf[st.parity][species];
-    std::vector<int32_t> cell(ns);
-    std::vector<float> off(ns), vx(ns), vy(ns), vz(ns), ab(ns);
-    std::vector<uint32_t> id(ns);
-    if (ns > 0) {
-        CK(h, cudaMemcpy(cell.data(), sp.cell, 4 * ns, cudaMemcpyDeviceToHost));
-        CK(h, cudaMemcpy(off.data(), sp.off, 4 * ns, cudaMemcpyDeviceToHost));
-        CK(h, cudaMemcpy(vx.data(), sp.vx, 4 * ns, cudaMemcpyDeviceToHost));
-        CK(h, cudaMemcpy(vy.data(), sp.vy, 4 * ns, cudaMemcpyDeviceToHost));
-        CK(h, cudaMemcpy(vz.data(), sp.vz, 4 * ns, cudaMemcpyDeviceToHost));
-        CK(h, cudaMemcpy(id.data(), sp.id, 4 * ns, cudaMemcpyDeviceToHost));
-        if (sp.abar) CK(h, cudaMemcpy(ab.data(), sp.abar, 4 * ns, cudaMemcpyDeviceToHost));
-    }
-    long long k = 0;
-    for (long long i = 0; i < ns; ++i) {
-        if (cell[i] < 0) continue;
-        if (out->cell) out->cell[k] = cell[i];
-        if (out->off) out->off[k] = off[i];
-        if (out->vx) out->vx[k] = vx[i];
-        if (out->vy) out->vy[k] = vy[i];
-        if (out->vz) out->vz[k] = vz[i];
-        if (out->id) out->id[k] = id[i];
-        if (out->abar) out->abar[k] = sp.abar ? ab[i] : 0.0f;
-        ++k;
-    }
-    out->count = k;
-    out->next_id = st.next_id[species];
-    return PIC_OK;
+    return run_get_particles(h->run, h->stream, species, out, &h->err);
 }
 
 int pic_set_particles(pic_handle *h, int species, const pic_host_particles *in) {

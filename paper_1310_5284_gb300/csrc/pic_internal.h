@@ -7,6 +7,10 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
+#include "pic.h"
+
 namespace pic {
 
 // Launch shape of the particle kernels (build-time knobs; the defaults are
@@ -71,6 +75,8 @@ struct DevState {
     double ke_x_acc[2], power_acc[2];
     double ke_x[2], power[2];
     double field_energy, field_energy_push;
+    double v_left;                 // electrode voltage of the current field
+    double v_sum;                  // running sum of v_left over the averaged steps
     double ke_perp[2];
     unsigned long long wall_count[2][2];
     double wall_energy[2][2];
@@ -80,10 +86,20 @@ struct DevState {
     long long n_avg, n_diag;
 };
 
+// State of a batched launch sequence (one per batch, in its arena).
+struct BatchState {
+    unsigned int next_item;    // work-item claim counter of the running launch
+    unsigned int blocks_done;  // arrival counter of the running launch
+    unsigned int status;
+    unsigned int pad;
+    long long launches;
+};
+
 // Constants and pointers of one run, passed to kernels by value.
 struct Run {
     int n_cells, periodic, scheme, mcc, ions_mobile, diag_period, eedf_bins, sort_period;
     uint32_t seed, run;
+    uint32_t rk0[10], rk1[10];   // Philox round keys of (seed, run)
     long long capacity[2];
     long long births_cap;
     // geometry / field (FP64, host-derived)
@@ -114,13 +130,36 @@ struct Run {
     unsigned long long *acc_cnt[2], *acc_a[2], *acc_b[2];   // [species][n_cells + 1]
     unsigned int *cursor[2];                                // [species][n_cells + 1]
     float *e_gather;       // [n_cells + 2]
-    double *e_cc, *phi, *chi;                               // [n_cells], [n_cells+1], [n_cells]
+    double *e_cc, *chi;                                     // [n_cells], [n_cells]
     long long *rho_q[2];   // [species][n_cells + 1] last assembled node charge, 2^-33 units
-    double *avg_ne, *avg_ni, *avg_phi, *heat[2];
+    double *avg_ne, *avg_ni, *avg_e, *heat[2];   // sums over steps (charge units, V/m)
     unsigned long long *eedf;
     Birth *births;
     DevState *st;
 };
+
+// Byte offsets of one run's buffers inside its arena.
+struct Layout {
+    size_t state;
+    size_t sp[2][2][7];  // [parity][species][field] offsets (cell, off, vx, vy, vz, id, abar)
+    size_t acc_cnt[2], acc_a[2], acc_b[2], cursor[2], rho_q[2];
+    size_t e_gather, e_cc, chi, avg_ne, avg_ni, avg_e, heat[2], eedf, births;
+    size_t total;
+};
+
+// ---- shared host helpers (pic_capi.cu) ----
+Layout make_run_layout(const pic_config &c);
+int validate_run_config(const pic_config *c);  // PIC_* code; message via pic_last_error
+void derive_run(const pic_config &c, const Layout &L, unsigned char *arena, Run &R);
+Mode push_mode_of(const pic_config &c);
+Mode deposit_mode_of(const pic_config &c);
+// diagnostics and particle read-back of one run (synchronise stream s)
+int run_diag(const Run &R, const pic_config &c, const Layout &L, unsigned char *arena, cudaStream_t s,
+             pic_diag_t *out, int reset_avg, std::string *err);
+int run_get_particles(const Run &R, cudaStream_t s, int species, pic_host_particles *out, std::string *err);
+// zero a run's arena, load its particles, assign charge, solve, sort
+int init_run_state(const pic_config &c, const Run &R, unsigned char *arena, size_t arena_bytes, int grid,
+                   cudaStream_t s, std::string *err);
 
 // ---- launchers (pic_kernels.cu) ----
 int block_smem_bytes(const Run &r);
@@ -132,6 +171,11 @@ cudaError_t launch_perp_energy(const Run &r, cudaStream_t s);
 cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
                                uint32_t c3, long long n, uint32_t *out, cudaStream_t s);
 cudaError_t occupancy_grid(const Run &r, Mode m, int *grid);
+// batched runs
+size_t batch_smem_bytes(int max_cells, int max_bins, int nruns, int *table_off);
+cudaError_t batch_prepare(int smem, int *grid);
+cudaError_t launch_batch(int phase, const Run *runs, int nruns, long long *work, BatchState *bs,
+                         long long chunk, int grid, int smem, int table_off, cudaStream_t s);
 // message returned by pic_last_error(NULL) (pic_capi.cu)
 void set_last_error(const char *msg);
 

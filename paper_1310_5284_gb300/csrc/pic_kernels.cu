@@ -28,11 +28,26 @@ namespace pic {
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
+                       (uint32_t)p0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// The same rounds with the ten round keys precomputed per run (no key
+// arithmetic in the loop; the keys sit in the kernel's parameter bank).
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk0)[10],
+                                                  const uint32_t (&rk1)[10]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk1[r], (uint32_t)p0);
     }
     return c;
 }
@@ -44,9 +59,9 @@ constexpr uint32_t kTagMcc = 2u;
 __device__ __forceinline__ uint4 draw(const Run &R, uint32_t id, long long step, int species,
                                       uint32_t tag, uint32_t sub) {
     const unsigned long long s = (unsigned long long)step;
-    return philox4x32_10(make_uint4(id, (uint32_t)s, (uint32_t)(s >> 32),
-                                    ((uint32_t)species << 24) | (tag << 16) | sub),
-                         R.seed, R.run);
+    return philox4x32_10_rk(make_uint4(id, (uint32_t)s, (uint32_t)(s >> 32),
+                                       ((uint32_t)species << 24) | (tag << 16) | sub),
+                            R.rk0, R.rk1);
 }
 
 // Uniform on (0, 1) from the top 24 bits.
@@ -256,6 +271,18 @@ __device__ __forceinline__ void acc_add(const Acc &acc, int key, uint32_t c, uin
 __device__ __forceinline__ void warp_agg(int key, uint32_t c, uint32_t a, uint32_t bh, uint32_t bl,
                                          const Acc &acc, bool count_only) {
     const int lane = threadIdx.x & 31;
+    const int k0 = __shfl_sync(FULL_MASK, key, 0);
+    if (__all_sync(FULL_MASK, key == k0) && k0 >= 0) {  // common case: one key for the warp
+        const uint32_t sc = __reduce_add_sync(FULL_MASK, c);
+        uint32_t sa = 0, sh = 0, sl = 0;
+        if (!count_only) {
+            sa = __reduce_add_sync(FULL_MASK, a);
+            sh = __reduce_add_sync(FULL_MASK, bh);
+            sl = __reduce_add_sync(FULL_MASK, bl);
+        }
+        if (lane == 0) acc_add(acc, k0, sc, sa, sh, sl, count_only);
+        return;
+    }
     unsigned int pending = __ballot_sync(FULL_MASK, key >= 0);
     int iter = 0;
     while (pending) {
@@ -399,18 +426,29 @@ __device__ void block_sum2(double &x, double &y, double *scratch /*[2*kThreads/3
 // ---------------------------------------------------------------------------
 // Shared-memory layout of the particle kernels.
 // ---------------------------------------------------------------------------
+// Deferred collisions: selected particles wait here (slot, id and the three
+// Philox words the collision uses) and are collided later by full warps.
+constexpr int kQueue = 512;
+struct CollQueue {
+    int *slot;                 // [kQueue]
+    uint32_t *id;              // [kQueue]
+    uint4 *w;                  // [kQueue] (x unused)
+    unsigned int *n;           // entries queued
+};
+
 struct SmemMain {
     float *e;                  // [n+2] gather table
     Acc acc;                   // 4 x [n+1]
     float *heat;               // [n]
     unsigned int *eedf;        // [bins+1]
+    CollQueue q;
 };
 
 __host__ __device__ inline size_t align8(size_t x) { return (x + 7) & ~size_t(7); }
 
 __host__ __device__ inline size_t main_smem_bytes(int n, int bins) {
     return align8(4 * (size_t)(n + 2)) + 4 * align8(4 * (size_t)(n + 1)) + align8(4 * (size_t)n) +
-           align8(4 * (size_t)(bins + 1));
+           align8(4 * (size_t)(bins + 1)) + 16 * (size_t)kQueue + 8 * (size_t)kQueue + 16;
 }
 
 __host__ __device__ inline size_t tail_smem_bytes(int n) {
@@ -430,6 +468,15 @@ __device__ SmemMain carve_main(unsigned char *base, int n, int bins) {
     s.heat = (float *)(base + o);
     o += align8(4 * (size_t)n);
     s.eedf = (unsigned int *)(base + o);
+    o += align8(4 * (size_t)(bins + 1));
+    o = (o + 15) & ~size_t(15);
+    s.q.w = (uint4 *)(base + o);
+    o += 16 * (size_t)kQueue;
+    s.q.slot = (int *)(base + o);
+    o += 4 * (size_t)kQueue;
+    s.q.id = (uint32_t *)(base + o);
+    o += 4 * (size_t)kQueue;
+    s.q.n = (unsigned int *)(base + o);
     return s;
 }
 
@@ -462,6 +509,44 @@ __device__ __forceinline__ float gather_ec(const float *e, int cell, float off) 
     const int j = cell + (off >= 0.5f ? 1 : 0);
     const float w1 = off >= 0.5f ? off - 0.5f : off + 0.5f;  // 1/2 + delta
     return (1.0f - w1) * e[j] + w1 * e[j + 1];
+}
+
+__device__ __forceinline__ void eedf_sample(const Run &R, const SmemMain &sm, float vx, float vy, float vz) {
+    const float en = R.half_m_over_e[0] * (vx * vx + vy * vy + vz * vz);
+    int bin = (int)floorf(en * R.eedf_inv_width);
+    bin = bin > R.eedf_bins ? R.eedf_bins : (bin < 0 ? 0 : bin);
+    atomicAdd(&sm.eedf[bin], 1u);
+}
+
+// Collide the queued particles, one per thread.  Their post-push position
+// and velocity were stored before the barrier that precedes this call.
+template <int S>
+__device__ __noinline__ void drain_collisions(const Run &R, const SmemMain &sm, const Species &sp, long long step,
+                                 bool diag, Tally &t) {
+    __syncthreads();
+    const unsigned int nq = min(*sm.q.n, (unsigned int)kQueue);
+    for (unsigned int q = threadIdx.x; q < nq; q += kThreads) {
+        const int idx = sm.q.slot[q];
+        const uint32_t id = sm.q.id[q];
+        const uint4 w = sm.q.w[q];
+        float vx = sp.vx[idx], vy = sp.vy[idx], vz = sp.vz[idx];
+        bool changed;
+        if (S == 0) {
+            const float abar = sp.abar ? sp.abar[idx] : 0.0f;
+            changed = collide_electron(R, w, id, step, sp.cell[idx], sp.off[idx], abar, vx, vy, vz, t);
+        } else {
+            changed = collide_ion(R, w, id, step, vx, vy, vz, t);
+        }
+        if (changed) {
+            sp.vx[idx] = vx;
+            sp.vy[idx] = vy;
+            sp.vz[idx] = vz;
+        }
+        if (S == 0 && diag && R.eedf_bins > 0) eedf_sample(R, sm, vx, vy, vz);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *sm.q.n = 0u;
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -525,33 +610,31 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         return -1;
     }
     cell = c;
-    // null-collision Monte Carlo: one Philox draw per particle and step
-    float vy = 0.0f, vz = 0.0f;
-    bool have_perp = false;
+    // null-collision Monte Carlo: one Philox draw per particle and step; a
+    // selected particle is queued and collided later by full warps (its
+    // position, hence its charge assignment, does not change in a collision)
+    bool queued = false;
     if (R.mcc) {
         const uint4 w = draw(R, id, step, S, kTagMcc, 0);
         if ((w.x >> 8) < R.thr[S]) {
-            vy = sp.vy[idx];
-            vz = sp.vz[idx];
-            have_perp = true;
-            const bool changed = S == 0 ? collide_electron(R, w, id, step, c, s, abar, vx, vy, vz, t)
-                                        : collide_ion(R, w, id, step, vx, vy, vz, t);
-            if (changed) {
-                sp.vy[idx] = vy;
-                sp.vz[idx] = vz;
+            const unsigned int pos = atomicAdd(sm.q.n, 1u);
+            if (pos < (unsigned int)kQueue) {
+                sm.q.slot[pos] = (int)idx;
+                sm.q.id[pos] = id;
+                sm.q.w[pos] = w;
+                queued = true;
+            } else {  // queue full: collide here
+                float vy = sp.vy[idx], vz = sp.vz[idx];
+                const bool changed = S == 0 ? collide_electron(R, w, id, step, c, s, abar, vx, vy, vz, t)
+                                            : collide_ion(R, w, id, step, vx, vy, vz, t);
+                if (changed) {
+                    sp.vy[idx] = vy;
+                    sp.vz[idx] = vz;
+                }
             }
         }
     }
-    if (S == 0 && diag && R.eedf_bins > 0) {
-        if (!have_perp) {
-            vy = sp.vy[idx];
-            vz = sp.vz[idx];
-        }
-        const float en = R.half_m_over_e[0] * (vx * vx + vy * vy + vz * vz);
-        int bin = (int)floorf(en * R.eedf_inv_width);
-        bin = bin > R.eedf_bins ? R.eedf_bins : (bin < 0 ? 0 : bin);
-        atomicAdd(&sm.eedf[bin], 1u);
-    }
+    if (S == 0 && diag && R.eedf_bins > 0 && !queued) eedf_sample(R, sm, vx, sp.vy[idx], sp.vz[idx]);
     if (MI::mc) return deposit_key_s1(c, s, a_out);
     return deposit_key_s2(c, s, a_out);
 }
@@ -675,6 +758,14 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Species 
             }
         }
         deposit_tile(key, a, sm.acc, MI::count_only);
+        if (MI::push && R.mcc) {
+            __syncthreads();
+            if (*sm.q.n > (unsigned int)(kQueue - kThreads * U)) drain_collisions<S>(R, sm, sp, step, diag, t);
+        }
+    }
+    if (MI::push && R.mcc) {
+        __syncthreads();
+        if (*sm.q.n > 0u) drain_collisions<S>(R, sm, sp, step, diag, t);
     }
 }
 
@@ -833,6 +924,15 @@ __device__ void tail_births(const Run &R, unsigned char *smem, bool diag) {
     unsigned int *hist = (unsigned int *)smem;                       // [2048]
     unsigned int *rank = (unsigned int *)(R.births + R.births_cap);  // [births_cap]
     uint32_t *sorted = (uint32_t *)(rank + R.births_cap);            // [births_cap]
+    if (B <= 256u) {  // few births: compare directly
+        for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
+            const uint32_t p = R.births[b].pid;
+            unsigned int r = 0;
+            for (unsigned int k = 0; k < B; ++k) r += R.births[k].pid < p ? 1u : 0u;
+            rank[b] = r;
+        }
+        __syncthreads();
+    } else {
     const unsigned int max_pid = st->next_id[0];
     const int bits = 32 - __clz(max_pid | 1u);
     const int shift = bits > 11 ? bits - 11 : 0;
@@ -872,6 +972,7 @@ __device__ void tail_births(const Run &R, unsigned char *smem, bool diag) {
         rank[b] = r;
     }
     __syncthreads();
+    }
     const int par = st->parity;
     const Species se = R.buf[par][0], si = R.buf[par][1];
     const unsigned int id_e = st->next_id[0], id_i = st->next_id[1];
@@ -927,6 +1028,64 @@ __device__ void tail_births(const Run &R, unsigned char *smem, bool diag) {
     __syncthreads();
 }
 
+// Sum of a double over the block: warp shuffles, then one warp (few FP64
+// operations: the FP64 pipe is narrow on this part).  All threads get it.
+__device__ double block_sum_lean(double x, double *scratch /*[kThreads/32 + 1]*/) {
+    constexpr int nw = kThreads / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    x = warp_sum(x);
+    if (lane == 0) scratch[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        double y = lane < nw ? scratch[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(FULL_MASK, y, o);
+        if (lane == 0) scratch[nw] = y;
+    }
+    __syncthreads();
+    const double r = scratch[nw];
+    __syncthreads();
+    return r;
+}
+
+// Exclusive block scan of two 64-bit integers at once.
+__device__ void block_exclusive_scan_pair(long long &x, unsigned long long &y, long long &tx,
+                                          unsigned long long &ty, long long *sx, unsigned long long *sy) {
+    constexpr int nw = kThreads / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long ix = x;
+    unsigned long long iy = y;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long a = __shfl_up_sync(FULL_MASK, ix, o);
+        const unsigned long long b = __shfl_up_sync(FULL_MASK, iy, o);
+        if (lane >= o) {
+            ix += a;
+            iy += b;
+        }
+    }
+    if (lane == 31) {
+        sx[wid] = ix;
+        sy[wid] = iy;
+    }
+    __syncthreads();
+    long long bx = 0;
+    unsigned long long by = 0;
+    tx = 0;
+    ty = 0;
+    for (int w = 0; w < nw; ++w) {
+        if (w < wid) {
+            bx += sx[w];
+            by += sy[w];
+        }
+        tx += sx[w];
+        ty += sy[w];
+    }
+    __syncthreads();
+    x = bx + ix - x;
+    y = by + iy - y;
+}
+
 // Field solve by the discrete Gauss law.  The finite-difference Poisson
 // equation -(phi_{g-1} - 2 phi_g + phi_{g+1})/dx^2 = rho_g/eps0 (with (1+chi)
 // on the cell faces in the implicit scheme) is D_{c} - D_{c-1} = dx rho_c / eps0
@@ -934,19 +1093,29 @@ __device__ void tail_births(const Run &R, unsigned char *smem, bool diag) {
 // So D_c = D_0 + kappa P_c with the exact int64 prefix sum P_c of the node
 // charge; the electrode condition sum_c E_c dx = V(t) (or zero mean field in
 // the periodic box) fixes D_0.  O(n) work, O(log n) depth; the same linear
-// system the oracle solves with the Thomas algorithm.
+// system the oracle solves with the Thomas algorithm.  The node potential is
+// a diagnostic only (the gather uses E): it follows from E and V on the host,
+// and so does its time average from the averages of E and V.
+// With `cursors` the same integer scan also yields the sort cursors (the
+// exclusive prefix of the per-key counts of both species).
 template <int MODE>
-__device__ void tail_field(const Run &R, unsigned char *smem, long long level, bool accumulate) {
+__device__ void tail_field(const Run &R, unsigned char *smem, long long level, bool accumulate, bool cursors) {
     DevState *st = R.st;
-    const int n = R.n_cells;
-    __shared__ long long sc_ll[33];
-    __shared__ double sc_2[2 * kThreads / 32];
+    const int n = R.n_cells, n1 = n + 1;
+    __shared__ long long sc_x[kThreads / 32];
+    __shared__ unsigned long long sc_y[kThreads / 32];
+    __shared__ double sc_d[kThreads / 32 + 1];
+    __shared__ double s_v_left;
     long long *q = (long long *)smem;               // [n+1] net node charge
     double *rinv = (double *)(smem + 8 * (n + 1));   // [n] 1/(1+chi)
-    double *ef = rinv + n;                           // [n] face field E_c
-    double *pp = ef + n;                             // [n] kappa P_c (+ background)
+    double *pp = rinv + n;                           // [n] kappa P_c (+ background)
     constexpr bool mc = ModeInfo<MODE>::mc;
     constexpr bool implicit = ModeInfo<MODE>::implicit;
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        if (!R.periodic) v = R.rf_volt * sin(2.0 * 3.14159265358979323846 * R.rf_freq * ((double)level * R.dt));
+        s_v_left = v;
+    }
     // node charges, densities, susceptibility
     for (int g = threadIdx.x; g <= n; g += kThreads) {
         const unsigned long long ne = mc ? node_charge_s1(R, 0, g) : node_charge_s2(R, 0, g);
@@ -955,136 +1124,103 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
         R.rho_q[0][g] = (long long)ne;
         R.rho_q[1][g] = (long long)ni;
         if (accumulate) {
-            R.avg_ne[g] += R.dens_scale * (double)(long long)ne;
-            R.avg_ni[g] += R.dens_scale * (double)(long long)ni;
+            R.avg_ne[g] += (double)(long long)ne;
+            R.avg_ni[g] += (double)(long long)ni;
         }
     }
-    for (int c = threadIdx.x; c < n; c += kThreads) {
-        double chi = 0.0;
-        if (implicit) {
-            chi = R.chi_coef[0] * (double)chi_count(R, 0, c) + R.chi_coef[1] * (double)chi_count(R, 1, c);
+    if (implicit) {
+        for (int c = threadIdx.x; c < n; c += kThreads) {
+            const double chi = R.chi_coef[0] * (double)chi_count(R, 0, c) + R.chi_coef[1] * (double)chi_count(R, 1, c);
             R.chi[c] = chi;
+            rinv[c] = 1.0 / (1.0 + chi);
         }
-        rinv[c] = implicit ? 1.0 / (1.0 + chi) : 1.0;
     }
     __syncthreads();
-    // P_c: inclusive prefix of the interior node charges (all nodes when periodic)
-    const int per = (n + kThreads - 1) / kThreads;
+    // one integer scan: P_c over the cells, sort cursors over the keys
+    const int span = n1 > n ? n1 : n;
+    const int per = (span + kThreads - 1) / kThreads;
     const int c_begin = threadIdx.x * per;
-    long long run = 0;
+    long long runP = 0;
+    unsigned long long runC = 0;
     for (int k = 0; k < per; ++k) {
         const int c = c_begin + k;
-        if (c < n) run += (R.periodic || c >= 1) ? q[c] : 0ll;
+        if (c < n) runP += (R.periodic || c >= 1) ? q[c] : 0ll;
+        if (cursors && c < n1) runC += R.acc_cnt[0][c] | (R.acc_cnt[1][c] << 32);
     }
-    long long total_q;
-    long long P = block_exclusive_scan<long long>(run, sc_ll, total_q);
-    const double qbar = R.periodic ? (double)total_q / (double)n : 0.0;
+    long long totP;
+    unsigned long long totC;
+    long long P = runP;
+    unsigned long long Cx = runC;
+    block_exclusive_scan_pair(P, Cx, totP, totC, sc_x, sc_y);
+    const double qbar = R.periodic ? (double)totP / (double)n : 0.0;
     double s1 = 0.0, s0 = 0.0;
     for (int k = 0; k < per; ++k) {
         const int c = c_begin + k;
+        if (cursors && c < n1) {
+            R.cursor[0][c] = (unsigned int)(Cx & 0xffffffffull);
+            R.cursor[1][c] = (unsigned int)(Cx >> 32);
+            Cx += R.acc_cnt[0][c] | (R.acc_cnt[1][c] << 32);
+        }
         if (c < n) {
             P += (R.periodic || c >= 1) ? q[c] : 0ll;
             const double v = R.periodic ? R.kappa * ((double)P - (double)(c + 1) * qbar)
                                         : R.kappa * (double)P + R.kappa_bg * (double)c;
             pp[c] = v;
             s1 += implicit ? rinv[c] * v : v;
-            s0 += implicit ? rinv[c] : 1.0;
+            if (implicit) s0 += rinv[c];
         }
     }
-    block_sum2(s1, s0, sc_2);
-    __shared__ double s_v_left, s_d0;
-    if (threadIdx.x == 0) {
-        // scalar FP64 work (slow pipe on this part) done once
-        double v_left = 0.0;
-        if (!R.periodic) {
-            const double t = (double)level * R.dt;
-            v_left = R.rf_volt * sin(2.0 * 3.14159265358979323846 * R.rf_freq * t);
-        }
-        s_v_left = v_left;
-        s_d0 = R.periodic ? -s1 / s0 : (v_left / R.dx - s1) / s0;
-    }
-    __syncthreads();
-    const double v_left = s_v_left, d0 = s_d0;
-    double esum = 0.0, wsum = 0.0;
+    s1 = block_sum_lean(s1, sc_d);
+    if (implicit) s0 = block_sum_lean(s0, sc_d);
+    else s0 = (double)n;
+    const double v_left = s_v_left;
+    const double d0 = R.periodic ? -s1 / s0 : (v_left / R.dx - s1) / s0;
+    double wsum = 0.0;
     for (int k = 0; k < per; ++k) {
         const int c = c_begin + k;
         if (c < n) {
             const double e = implicit ? rinv[c] * (d0 + pp[c]) : d0 + pp[c];
-            ef[c] = e;
+            pp[c] = e;  // now the face field
             R.e_cc[c] = e;
+            if (accumulate) R.avg_e[c] += e;
             wsum += e * e;
-            esum += e;
+            if (!mc) R.e_gather[c + 1] = (float)e;
         }
     }
-    // phi_g = phi_0 - dx sum_{c<g} E_c; the field energy rides along
-    double acc = block_exclusive_scan2(esum, wsum, sc_2);
-    for (int k = 0; k < per; ++k) {
-        const int g = c_begin + k;
-        if (g < n) {
-            const double ph = v_left - R.dx * acc;
-            R.phi[g] = ph;
-            if (accumulate) R.avg_phi[g] += ph;
-            acc += ef[g];
-        }
-    }
+    wsum = block_sum_lean(wsum, sc_d);  // includes the barrier that publishes pp[]
     if (threadIdx.x == 0) {
-        R.phi[n] = R.periodic ? v_left : 0.0;  // grounded electrode / periodic image of node 0
-        if (accumulate) R.avg_phi[n] += R.phi[n];
         if (MODE == kExplicitEC || MODE == kExplicitMC) st->field_energy_push = st->field_energy;
         st->field_energy = R.eps0_dx_half * wsum;
         if (MODE == kImplicit1) st->field_energy_push = st->field_energy;
+        st->v_left = v_left;
+        if (accumulate) st->v_sum += v_left;
+        if (!mc) {
+            R.e_gather[0] = R.periodic ? (float)pp[n - 1] : 0.0f;
+            R.e_gather[n + 1] = R.periodic ? (float)pp[0] : 0.0f;
+        }
     }
-    __syncthreads();
-    // gather tables
     if (mc) {
+        // node field of the momentum-conserving scheme, (phi_{g-1} - phi_{g+1})/(2dx)
+        // = (E_{g-1/2} + E_{g+1/2})/2, one-sided at the electrodes
         for (int g = threadIdx.x; g <= n; g += kThreads) {
             double e;
-            if (R.periodic) {
-                const int gl = (g - 1 + n) % n, gr = (g + 1) % n;
-                e = (R.phi[gl] - R.phi[gr]) * (0.5 * R.inv_dx);
-            } else if (g == 0) {
-                e = (R.phi[0] - R.phi[1]) * R.inv_dx;
-            } else if (g == n) {
-                e = (R.phi[n - 1] - R.phi[n]) * R.inv_dx;
-            } else {
-                e = (R.phi[g - 1] - R.phi[g + 1]) * (0.5 * R.inv_dx);
-            }
+            if (R.periodic)
+                e = 0.5 * (pp[(g - 1 + n) % n] + pp[g % n]);
+            else if (g == 0)
+                e = pp[0];
+            else if (g == n)
+                e = pp[n - 1];
+            else
+                e = 0.5 * (pp[g - 1] + pp[g]);
             R.e_gather[g] = (float)e;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && R.periodic) R.e_gather[n] = R.e_gather[0];
-    } else {
-        for (int c = threadIdx.x; c < n; c += kThreads) R.e_gather[c + 1] = (float)ef[c];
-        if (threadIdx.x == 0) {
-            R.e_gather[0] = R.periodic ? (float)ef[n - 1] : 0.0f;
-            R.e_gather[n + 1] = R.periodic ? (float)ef[0] : 0.0f;
         }
     }
     __syncthreads();
 }
 
-// Sort cursors (exclusive prefix of the per-key counts, both species in one
-// packed scan: each count is below 2^29) and reset of the per-step
-// accumulators.
-__device__ void tail_cursors_and_reset(const Run &R) {
-    __shared__ unsigned long long sc_u[33];
+// Reset of the per-step accumulators.
+__device__ void tail_reset(const Run &R) {
     const int n1 = R.n_cells + 1;
-    const int per = (n1 + kThreads - 1) / kThreads;
-    const int b0 = threadIdx.x * per;
-    unsigned long long run = 0;
-    for (int k = 0; k < per; ++k)
-        if (b0 + k < n1) run += R.acc_cnt[0][b0 + k] | (R.acc_cnt[1][b0 + k] << 32);
-    unsigned long long tot;
-    unsigned long long ex = block_exclusive_scan<unsigned long long>(run, sc_u, tot);
-    for (int k = 0; k < per; ++k) {
-        const int j = b0 + k;
-        if (j < n1) {
-            R.cursor[0][j] = (unsigned int)(ex & 0xffffffffull);
-            R.cursor[1][j] = (unsigned int)(ex >> 32);
-            ex += R.acc_cnt[0][j] | (R.acc_cnt[1][j] << 32);
-        }
-    }
-    __syncthreads();
     for (int S = 0; S < 2; ++S)
         for (int k = threadIdx.x; k < n1; k += kThreads) {
             R.acc_cnt[S][k] = 0ull;
@@ -1093,26 +1229,40 @@ __device__ void tail_cursors_and_reset(const Run &R) {
         }
 }
 
+// Sort cursors alone (implicit pass 2, which solves no field).
+__device__ void tail_cursors(const Run &R) {
+    __shared__ long long sc_x[kThreads / 32];
+    __shared__ unsigned long long sc_y[kThreads / 32];
+    const int n1 = R.n_cells + 1;
+    const int per = (n1 + kThreads - 1) / kThreads;
+    const int b0 = threadIdx.x * per;
+    unsigned long long run = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < n1) run += R.acc_cnt[0][b0 + k] | (R.acc_cnt[1][b0 + k] << 32);
+    long long dummy = 0, tdummy;
+    unsigned long long tot;
+    block_exclusive_scan_pair(dummy, run, tdummy, tot, sc_x, sc_y);
+    for (int k = 0; k < per; ++k) {
+        const int j = b0 + k;
+        if (j < n1) {
+            R.cursor[0][j] = (unsigned int)(run & 0xffffffffull);
+            R.cursor[1][j] = (unsigned int)(run >> 32);
+            run += R.acc_cnt[0][j] | (R.acc_cnt[1][j] << 32);
+        }
+    }
+    __syncthreads();
+}
+
 template <int MODE>
 __device__ void tail(const Run &R, unsigned char *smem, bool diag) {
     DevState *st = R.st;
     const long long step = st->step;
     if (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit2) tail_births<MODE>(R, smem, diag);
-    if (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit1) tail_field<MODE>(R, smem, step + 1, true);
-    if (MODE == kDepositEC || MODE == kDepositMC) tail_field<MODE>(R, smem, step, false);
-    if (MODE == kImplicit1) {
-        // pass 1 keeps nothing else; reset its accumulators for pass 2's key counts
-        const int n1 = R.n_cells + 1;
-        __syncthreads();
-        for (int S = 0; S < 2; ++S)
-            for (int k = threadIdx.x; k < n1; k += kThreads) {
-                R.acc_cnt[S][k] = 0ull;
-                R.acc_a[S][k] = 0ull;
-                R.acc_b[S][k] = 0ull;
-            }
-    } else {
-        tail_cursors_and_reset(R);
-    }
+    if (MODE == kExplicitEC || MODE == kExplicitMC) tail_field<MODE>(R, smem, step + 1, true, true);
+    if (MODE == kImplicit1) tail_field<MODE>(R, smem, step + 1, true, false);
+    if (MODE == kDepositEC || MODE == kDepositMC) tail_field<MODE>(R, smem, step, false, true);
+    if (MODE == kImplicit2) tail_cursors(R);
+    tail_reset(R);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (ModeInfo<MODE>::push) {
@@ -1186,6 +1336,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
         for (int k = threadIdx.x; k < n; k += kThreads) sm.heat[k] = 0.0f;
         for (int k = threadIdx.x; k <= R.eedf_bins; k += kThreads) sm.eedf[k] = 0u;
     }
+    if (threadIdx.x == 0) *sm.q.n = 0u;
     __syncthreads();
     if (b < e) {  // uniform across the block
         Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
@@ -1228,72 +1379,62 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
 // cursors were prepared by the previous tail; live particles are scattered
 // into the other buffer, holes are dropped.
 // ---------------------------------------------------------------------------
+// Scatter the live particles of [b, e) of species S into the other buffer at
+// the cursor of their key (warp-aggregated: lanes sharing a key take
+// consecutive positions from one atomic).
+__device__ void sort_chunk(const Run &R, int par, int S, long long b, long long e) {
+    const bool mc = R.scheme == 1;
+    const int lane = threadIdx.x & 31;
+    const Species src = R.buf[par][S], dst = R.buf[par ^ 1][S];
+    for (long long base = b; base < e; base += kThreads) {
+        const long long i = base + threadIdx.x;
+        const int cell = i < e ? src.cell[i] : -1;
+        const float off = i < e ? src.off[i] : 0.0f;
+        uint32_t a;
+        const int key = cell < 0 ? -1 : (mc ? deposit_key_s1(cell, off, a) : deposit_key_s2(cell, off, a));
+        const unsigned int peers = __match_any_sync(FULL_MASK, key);
+        if (key >= 0) {
+            const int leader = __ffs(peers) - 1;
+            const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
+            unsigned int base_pos = 0;
+            if (lane == leader) base_pos = atomicAdd(&R.cursor[S][key], (unsigned int)__popc(peers));
+            base_pos = __shfl_sync(peers, base_pos, leader);
+            const unsigned int pos = base_pos + rank;
+            dst.cell[pos] = cell;
+            dst.off[pos] = off;
+            dst.vx[pos] = src.vx[i];
+            dst.vy[pos] = src.vy[i];
+            dst.vz[pos] = src.vz[i];
+            dst.id[pos] = src.id[i];
+            if (R.scheme == 2) dst.abar[pos] = src.abar[i];
+        }
+    }
+}
+
+// After the last scatter of a run: switch buffers; holes are gone.
+__device__ void sort_finish(const Run &R) {
+    DevState *st = R.st;
+    st->parity ^= 1u;
+    st->n_slots[0] = st->n_live[0];
+    st->n_slots[1] = st->n_live[1];
+    st->sort_blocks_done = 0u;
+}
+
 __global__ void __launch_bounds__(kThreads) k_sort(Run R) {
     __shared__ bool s_last;
     DevState *st = R.st;
     const int par = st->parity;
-    const bool mc = R.scheme == 1;
-    const long long ne = st->n_slots[0];
-    const long long ni = R.ions_mobile ? st->n_slots[1] : 0;
-    const long long total = ne + ni;
-    const long long G = gridDim.x;
-    long long ch = (total + G - 1) / G;
-    ch = (ch + 31) & ~31ll;
-    const long long c0 = (long long)blockIdx.x * ch;
-    const long long c1 = c0 + ch < total ? c0 + ch : total;
-    const int lane = threadIdx.x & 31;
-    for (int S = 0; S < 2; ++S) {
-        long long b, e;
-        if (S == 0) {
-            b = c0;
-            e = c1 < ne ? c1 : ne;
-        } else {
-            b = (c0 > ne ? c0 : ne) - ne;
-            e = c1 - ne;
-        }
-        if (b >= e) continue;
-        const Species src = R.buf[par][S], dst = R.buf[par ^ 1][S];
-        for (long long base = b; base < e; base += kThreads) {
-            const long long i = base + threadIdx.x;
-            int cell = i < e ? src.cell[i] : -1;
-            float off = i < e ? src.off[i] : 0.0f;
-            uint32_t a;
-            int key = cell < 0 ? -1 : (mc ? deposit_key_s1(cell, off, a) : deposit_key_s2(cell, off, a));
-            const unsigned int live = __ballot_sync(FULL_MASK, key >= 0);
-            const unsigned int peers = __match_any_sync(FULL_MASK, key);
-            unsigned int pos = 0;
-            if (key >= 0) {
-                const int leader = __ffs(peers) - 1;
-                const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
-                unsigned int base_pos = 0;
-                if (lane == leader) base_pos = atomicAdd(&R.cursor[S][key], (unsigned int)__popc(peers));
-                base_pos = __shfl_sync(peers, base_pos, leader);
-                pos = base_pos + rank;
-            }
-            (void)live;
-            if (key >= 0) {
-                dst.cell[pos] = cell;
-                dst.off[pos] = off;
-                dst.vx[pos] = src.vx[i];
-                dst.vy[pos] = src.vy[i];
-                dst.vz[pos] = src.vz[i];
-                dst.id[pos] = src.id[i];
-                if (R.scheme == 2) dst.abar[pos] = src.abar[i];
-            }
-        }
-    }
+    long long b, e;
+    int S;
+    block_segment(st->n_slots[0], R.ions_mobile ? st->n_slots[1] : 0, S, b, e);
+    if (b < e) sort_chunk(R, par, S, b, e);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(&st->sort_blocks_done, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (threadIdx.x == 0) {
-        st->parity = par ^ 1;
-        st->n_slots[0] = st->n_live[0];
-        st->n_slots[1] = st->n_live[1];
-        st->sort_blocks_done = 0u;
-    }
+    if (threadIdx.x == 0) sort_finish(R);
 }
 
 // ---------------------------------------------------------------------------
@@ -1366,6 +1507,182 @@ __global__ void k_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1
          i += (long long)gridDim.x * blockDim.x) {
         const uint4 w = philox4x32_10(make_uint4(c0 + (uint32_t)i, c1, c2, c3), k0, k1);
         reinterpret_cast<uint4 *>(out)[i] = w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched runs: one persistent launch per phase over many independent runs of
+// uneven size.  Work items are (run, species, chunk of `chunk` particles),
+// claimed dynamically from a global counter; every block derives the same
+// item table from the per-run work counts, which only change at the very
+// end of a launch.  The block that finishes a run's last item runs that
+// run's tail inside the same launch, so one run's serial field solve
+// overlaps other runs' particle work.  Phases: 0 = explicit step or
+// implicit pass 1; 1 = implicit pass 2; 2 = counting sort.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__device__ void batch_item(const Run &R, unsigned char *smem, int S, long long b, long long e,
+                           unsigned int items_r, int r, int &loaded_run) {
+    using MI = ModeInfo<MODE>;
+    __shared__ bool s_last;
+    DevState *st = R.st;
+    const int n = R.n_cells;
+    const SmemMain sm = carve_main(smem, n, R.eedf_bins);
+    const long long step = st->step;
+    const bool diag = MI::push && R.diag_period > 0 && (step % R.diag_period) == 0;
+    if (loaded_run != r) {
+        if (MI::needs_field)
+            for (int k = threadIdx.x; k < n + 2; k += kThreads) sm.e[k] = R.e_gather[k];
+        for (int k = threadIdx.x; k <= n; k += kThreads) {
+            sm.acc.cnt[k] = 0u;
+            sm.acc.a[k] = 0u;
+            sm.acc.bh[k] = 0u;
+            sm.acc.bl[k] = 0u;
+        }
+        loaded_run = r;
+    }
+    if (diag) {
+        for (int k = threadIdx.x; k < n; k += kThreads) sm.heat[k] = 0.0f;
+        for (int k = threadIdx.x; k <= R.eedf_bins; k += kThreads) sm.eedf[k] = 0u;
+    }
+    if (threadIdx.x == 0) *sm.q.n = 0u;
+    __syncthreads();
+    if (b < e) {
+        Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
+        const Species sp = R.buf[st->parity][S];
+        for (long long sb = b; sb < e; sb += kFlushEvery) {
+            const long long se = sb + kFlushEvery < e ? sb + kFlushEvery : e;
+            if (S == 0)
+                process_segment<MODE, 0>(R, sm, sp, sb, se, diag, step, t);
+            else
+                process_segment<MODE, 1>(R, sm, sp, sb, se, diag, step, t);
+            flush_species(R, sm, S, MI::count_only);
+        }
+        if (MI::push) flush_tally(R, S, t);
+        if (diag) {
+            __syncthreads();
+            for (int k = threadIdx.x; k < n; k += kThreads) {
+                const float h = sm.heat[k];
+                if (h != 0.0f) atomicAdd(&R.heat[S][k], (double)h / R.dx);
+            }
+            for (int k = threadIdx.x; k <= R.eedf_bins; k += kThreads)
+                if (sm.eedf[k]) atomicAdd(&R.eedf[k], (unsigned long long)sm.eedf[k]);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->blocks_done, 1u) == items_r - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        tail<MODE>(R, smem, diag);
+        loaded_run = -1;  // the tail reused the shared memory
+        __syncthreads();
+    }
+}
+
+__device__ void batch_sort_item(const Run &R, int S, long long b, long long e, unsigned int items_r) {
+    __shared__ bool s_last;
+    DevState *st = R.st;
+    if (b < e) sort_chunk(R, st->parity, S, b, e);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->sort_blocks_done, 1u) == items_r - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (threadIdx.x == 0) sort_finish(R);
+        __syncthreads();
+    }
+}
+
+template <int PHASE>
+__global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ runs, int nruns,
+                                                       long long *work, BatchState *bs, long long chunk,
+                                                       int table_off) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned int sc_u[33];
+    __shared__ unsigned int s_item;
+    __shared__ bool s_glast;
+    unsigned int *table = (unsigned int *)(smem + table_off);  // [2 nruns + 1] item prefix
+    const int nj = 2 * nruns;
+    // items per (run, species); a run with no particles still gets one empty
+    // item so that its tail (field solve, step counter) runs
+    const int per = (nj + kThreads - 1) / kThreads;
+    const int j0 = threadIdx.x * per;
+    unsigned int run_sum = 0;
+    for (int q = 0; q < per; ++q) {
+        const int j = j0 + q;
+        if (j >= nj) break;
+        const Run &R = runs[j >> 1];
+        const bool part = PHASE == 1 ? R.scheme == 2 : true;
+        const int S = j & 1;
+        const long long nn = (S == 1 && !R.ions_mobile) ? 0 : work[j];
+        unsigned int it = part ? (unsigned int)((nn + chunk - 1) / chunk) : 0u;
+        if (part && S == 0 && it == 0) {
+            const long long n1 = R.ions_mobile ? work[j + 1] : 0;
+            if (n1 == 0) it = 1u;
+        }
+        table[j] = it;
+        run_sum += it;
+    }
+    unsigned int total;
+    unsigned int ex = block_exclusive_scan<unsigned int>(run_sum, sc_u, total);
+    for (int q = 0; q < per; ++q) {
+        const int j = j0 + q;
+        if (j >= nj) break;
+        const unsigned int it = table[j];
+        table[j] = ex;
+        ex += it;
+    }
+    if (threadIdx.x == 0) table[nj] = total;
+    __syncthreads();
+    int loaded_run = -1;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&bs->next_item, 1u);
+        __syncthreads();
+        const unsigned int item = s_item;
+        __syncthreads();
+        if (item >= total) break;
+        int lo = 0, hi = nj - 1;  // largest j with table[j] <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (table[mid] <= item)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int j = lo, r = j >> 1, S = j & 1;
+        const Run &R = runs[r];
+        const unsigned int items_r = table[2 * r + 2] - table[2 * r];
+        const long long nn = (S == 1 && !R.ions_mobile) ? 0 : work[j];
+        const long long b0 = (long long)(item - table[j]) * chunk;
+        const long long b = b0 < nn ? b0 : nn;
+        const long long e = b0 + chunk < nn ? b0 + chunk : nn;
+        if (PHASE == 2) {
+            batch_sort_item(R, S, b, e, items_r);
+        } else if (PHASE == 1) {
+            batch_item<kImplicit2>(R, smem, S, b, e, items_r, r, loaded_run);
+        } else if (R.scheme == 0) {
+            batch_item<kExplicitEC>(R, smem, S, b, e, items_r, r, loaded_run);
+        } else if (R.scheme == 1) {
+            batch_item<kExplicitMC>(R, smem, S, b, e, items_r, r, loaded_run);
+        } else {
+            batch_item<kImplicit1>(R, smem, S, b, e, items_r, r, loaded_run);
+        }
+    }
+    // the last block of the launch publishes the work counts of the next one
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_glast = atomicAdd(&bs->blocks_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_glast) return;
+    __threadfence();
+    for (int j = threadIdx.x; j < nj; j += kThreads) work[j] = runs[j >> 1].st->n_slots[j & 1];
+    if (threadIdx.x == 0) {
+        bs->next_item = 0u;
+        bs->blocks_done = 0u;
+        bs->launches += 1;
     }
 }
 
@@ -1457,6 +1774,46 @@ cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c
                                uint32_t c3, long long n, uint32_t *out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_philox_fill<<<1024, kThreads, 0, s>>>(k0, k1, c0, c1, c2, c3, n, out);
+    return cudaGetLastError();
+}
+
+size_t batch_smem_bytes(int max_cells, int max_bins, int nruns, int *table_off) {
+    const size_t a = main_smem_bytes(max_cells, max_bins);
+    const size_t b = tail_smem_bytes(max_cells);
+    const size_t off = ((a > b ? a : b) + 15) & ~size_t(15);
+    *table_off = (int)off;
+    return off + 4 * (size_t)(2 * nruns + 1);
+}
+
+template <int PHASE>
+static cudaError_t batch_attr(int smem) {
+    return cudaFuncSetAttribute(k_batch<PHASE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t batch_prepare(int smem, int *grid) {
+    cudaError_t e = batch_attr<0>(smem);
+    if (e == cudaSuccess) e = batch_attr<1>(smem);
+    if (e == cudaSuccess) e = batch_attr<2>(smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per0 = 1, per1 = 1;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per0, k_batch<0>, kThreads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_batch<1>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    int per = per0 < per1 ? per0 : per1;
+    *grid = sms * (per > 0 ? per : 1);
+    return cudaSuccess;
+}
+
+cudaError_t launch_batch(int phase, const Run *runs, int nruns, long long *work, BatchState *bs,
+                         long long chunk, int grid, int smem, int table_off, cudaStream_t s) {
+    if (phase == 0)
+        k_batch<0><<<grid, kThreads, smem, s>>>(runs, nruns, work, bs, chunk, table_off);
+    else if (phase == 1)
+        k_batch<1><<<grid, kThreads, smem, s>>>(runs, nruns, work, bs, chunk, table_off);
+    else
+        k_batch<2><<<grid, kThreads, smem, s>>>(runs, nruns, work, bs, chunk, table_off);
     return cudaGetLastError();
 }
 

@@ -678,13 +678,99 @@ __device__ __forceinline__ void stv(T *p, const T (&o)[kUnroll]) {
     }
 }
 
-// Stream one species segment [b, e) through the block.  Each thread takes
-// kUnroll consecutive particles: one vector load per field (the segment
-// start is a multiple of 32 and every array is 256-byte aligned), steps them
-// independently, stores them back the same way and deposits the tile.
+// ---------------------------------------------------------------------------
+// Asynchronous staging of the particle stream.  One thread streams tiles of
+// kTile particles of every field the mode reads from HBM into a ring of
+// kStages shared-memory buffers with cp.async.bulk, completion signalled on
+// one mbarrier per buffer, while all warps work on the current tile.  Every
+// wait is bounded: a wait that runs out sets PIC_STATUS_TIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr int kTile = kThreads * kUnroll;
+constexpr int kStages = 3;
+constexpr int kMaxFields = 5;  // cell, off, vx, abar, id
+constexpr long long kWaitLimit = 1ll << 20;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned int bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned int bytes,
+                                         unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned int parity) {
+    unsigned int done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait for one phase of a stage barrier; false (status bit set) if it
+// never completed.
+__device__ __forceinline__ bool mbar_wait(const Run &R, unsigned long long *bar, unsigned int parity) {
+    for (long long i = 0; i < kWaitLimit; ++i)
+        if (mbar_try(bar, parity)) return true;
+    atomicOr(&R.st->status, 0x4u);
+    return false;
+}
+
+// The ring: kStages x kMaxFields arrays of kTile words, one barrier per stage.
+struct Ring {
+    uint32_t *buf;               // [kStages][kMaxFields][kTile]
+    unsigned long long *bar;     // [kStages] (static shared)
+    unsigned int *uses;          // tiles issued so far by this block (static shared)
+};
+
+__host__ __device__ constexpr size_t ring_bytes() { return (size_t)kStages * kMaxFields * kTile * 4; }
+
+__device__ __forceinline__ uint32_t *ring_field(const Ring &g, int stage, int f) {
+    return g.buf + ((size_t)stage * kMaxFields + f) * kTile;
+}
+
+// Issue the copies of tile t (block-relative tile counter u) of segment
+// [b, b + len): fields in the order cell, off, vx, abar, id.
+template <int MODE>
+__device__ __forceinline__ void ring_issue(const Ring &g, const Species &sp0, long long b, int len, int t,
+                                           unsigned int u, bool need_id) {
+    using MI = ModeInfo<MODE>;
+    const int stage = (int)(u % kStages);
+    const int first = t * kTile;
+    const int n = min(kTile, len - first);
+    const unsigned int bytes = (unsigned int)(((n * 4) + 15) & ~15);  // arrays are padded to 16 bytes
+    const int nf = 2 + (MI::loads_v ? 1 : 0) + (MI::implicit ? 1 : 0) + (need_id ? 1 : 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&g.bar[stage], bytes * nf);
+    const long long o = b + first;
+    bulk_g2s(ring_field(g, stage, 0), sp0.cell + o, bytes, &g.bar[stage]);
+    bulk_g2s(ring_field(g, stage, 1), sp0.off + o, bytes, &g.bar[stage]);
+    if (MI::loads_v) bulk_g2s(ring_field(g, stage, 2), sp0.vx + o, bytes, &g.bar[stage]);
+    if (MI::implicit) bulk_g2s(ring_field(g, stage, 3), sp0.abar + o, bytes, &g.bar[stage]);
+    if (need_id) bulk_g2s(ring_field(g, stage, 4), sp0.id + o, bytes, &g.bar[stage]);
+}
+
+// Stream one species segment [b, e) through the block in staged tiles; each
+// thread takes kUnroll consecutive particles of a tile, steps them
+// independently, stores them back with vector stores and deposits the tile.
 template <int MODE, int S>
-__device__ void process_segment(const Run &R, const SmemMain &sm, const Species &sp0, long long b,
-                                long long e, bool diag, long long step, Tally &t) {
+__device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g, const Species &sp0,
+                                long long b, long long e, bool diag, long long step, Tally &t) {
     constexpr int U = kUnroll;
     static_assert(U == 1 || U == 2 || U == 4, "vector width");
     using MI = ModeInfo<MODE>;
@@ -698,45 +784,50 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Species 
     sp.abar = MI::implicit ? sp0.abar + b : nullptr;
     const int len = (int)(e - b);
     const bool need_id = MI::push && R.mcc;
-    for (int base = 0; base < len; base += kThreads * U) {
-        const int i0 = base + U * (int)threadIdx.x;
+    const int ntiles = (len + kTile - 1) / kTile;
+    const unsigned int u0 = *g.uses;  // tiles this block issued before this segment
+    if (threadIdx.x == 0)
+        for (int tt = 0; tt < kStages - 1 && tt < ntiles; ++tt) ring_issue<MODE>(g, sp0, b, len, tt, u0 + tt, need_id);
+    for (int tl = 0; tl < ntiles; ++tl) {
+        const unsigned int u = u0 + tl;
+        const int stage = (int)(u % kStages);
+        if (threadIdx.x == 0 && tl + kStages - 1 < ntiles)
+            ring_issue<MODE>(g, sp0, b, len, tl + kStages - 1, u + kStages - 1, need_id);
+        if (!mbar_wait(R, &g.bar[stage], (u / kStages) & 1u)) {
+            // give up on this segment, but not before the copies already
+            // issued into the ring have landed (bounded as well)
+            for (int tw = tl + 1; tw < ntiles && tw < tl + kStages; ++tw)
+                mbar_wait(R, &g.bar[(u0 + tw) % kStages], ((u0 + tw) / kStages) & 1u);
+            __syncthreads();
+            if (threadIdx.x == 0) *g.uses = u0 + (unsigned int)min(ntiles, tl + kStages);
+            __syncthreads();
+            return;
+        }
+        const int base = tl * kTile;
+        const int i0 = base + U * (int)threadIdx.x;   // segment-relative index of the first particle
+        const int s0 = U * (int)threadIdx.x;          // its place in the tile
         const bool full = i0 + U - 1 < len;
         int cell[U];
         float off[U], vx[U], abar[U];
         uint32_t id[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            vx[u] = 0.0f;
-            abar[u] = 0.0f;
-            id[u] = 0u;
-        }
-        if (full) {
-            ldv<U>(sp.cell + i0, cell);
-            ldv<U>(sp.off + i0, off);
-            if (MI::loads_v) ldv<U>(sp.vx + i0, vx);
-            if (MI::implicit) ldv<U>(sp.abar + i0, abar);
-            if (need_id) ldv<U>(sp.id + i0, id);
-        } else {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int i = i0 + u;
-                const bool ok = i < len;
-                cell[u] = ok ? sp.cell[i] : -1;
-                off[u] = ok ? sp.off[i] : 0.0f;
-                if (ok && MI::loads_v) vx[u] = sp.vx[i];
-                if (ok && MI::implicit) abar[u] = sp.abar[i];
-                if (ok && need_id) id[u] = sp.id[i];
-            }
+        for (int q = 0; q < U; ++q) {
+            const bool ok = i0 + q < len;
+            cell[q] = ok ? (int)ring_field(g, stage, 0)[s0 + q] : -1;
+            off[q] = ok ? __uint_as_float(ring_field(g, stage, 1)[s0 + q]) : 0.0f;
+            vx[q] = (ok && MI::loads_v) ? __uint_as_float(ring_field(g, stage, 2)[s0 + q]) : 0.0f;
+            abar[q] = (ok && MI::implicit) ? __uint_as_float(ring_field(g, stage, 3)[s0 + q]) : 0.0f;
+            id[q] = (ok && need_id) ? ring_field(g, stage, 4)[s0 + q] : 0u;
         }
         int key[U];
         uint32_t a[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            a[u] = 0u;
-            key[u] = -1;
-            if (cell[u] < 0) continue;  // beyond the segment, or a hole left by absorption
-            key[u] = step_particle<MODE, S>(R, sm, sp, (long long)(i0 + u), cell[u], off[u], vx[u],
-                                            abar[u], id[u], diag, step, t, a[u]);
+        for (int q = 0; q < U; ++q) {
+            a[q] = 0u;
+            key[q] = -1;
+            if (cell[q] < 0) continue;  // beyond the segment, or a hole left by absorption
+            key[q] = step_particle<MODE, S>(R, sm, sp, (long long)(i0 + q), cell[q], off[q], vx[q],
+                                            abar[q], id[q], diag, step, t, a[q]);
         }
         if (MI::push) {
             if (full) {
@@ -746,27 +837,29 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Species 
                 if (MI::implicit) stv<U>(sp.abar + i0, abar);
             } else {
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int i = i0 + u;
+                for (int q = 0; q < U; ++q) {
+                    const int i = i0 + q;
                     if (i < len) {
-                        sp.cell[i] = cell[u];
-                        sp.off[i] = off[u];
-                        sp.vx[i] = vx[u];
-                        if (MI::implicit) sp.abar[i] = abar[u];
+                        sp.cell[i] = cell[q];
+                        sp.off[i] = off[q];
+                        sp.vx[i] = vx[q];
+                        if (MI::implicit) sp.abar[i] = abar[q];
                     }
                 }
             }
         }
         deposit_tile(key, a, sm.acc, MI::count_only);
-        if (MI::push && R.mcc) {
-            __syncthreads();
-            if (*sm.q.n > (unsigned int)(kQueue - kThreads * U)) drain_collisions<S>(R, sm, sp, step, diag, t);
-        }
+        __syncthreads();  // the stage is free again; the queue count is current
+        if (MI::push && R.mcc && *sm.q.n >= (unsigned int)(kQueue / 2))
+            drain_collisions<S>(R, sm, sp, step, diag, t);
     }
     if (MI::push && R.mcc) {
         __syncthreads();
         if (*sm.q.n > 0u) drain_collisions<S>(R, sm, sp, step, diag, t);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) *g.uses = u0 + (unsigned int)ntiles;
+    __syncthreads();
 }
 
 // Add the block's shared accumulators of one species to the run's global ones.
@@ -1311,12 +1404,24 @@ __device__ __forceinline__ void block_segment(long long ne, long long ni, int &S
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem_all[];
     __shared__ bool s_last;
+    __shared__ __align__(8) unsigned long long s_bar[kStages];
+    __shared__ unsigned int s_uses;
     using MI = ModeInfo<MODE>;
     DevState *st = R.st;
     const int n = R.n_cells;
+    Ring g;
+    g.buf = (uint32_t *)smem_all;
+    g.bar = s_bar;
+    g.uses = &s_uses;
+    unsigned char *smem = smem_all + ring_bytes();  // grid, accumulators, queue; the tail's space
     const SmemMain sm = carve_main(smem, n, R.eedf_bins);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1u);
+        s_uses = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     const long long step = st->step;
     const bool diag = MI::push && R.diag_period > 0 && (step % R.diag_period) == 0;
     const int par = st->parity;
@@ -1344,9 +1449,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
         for (long long sb = b; sb < e; sb += kFlushEvery) {
             const long long se = sb + kFlushEvery < e ? sb + kFlushEvery : e;
             if (S == 0)
-                process_segment<MODE, 0>(R, sm, sp, sb, se, diag, step, t);
+                process_segment<MODE, 0>(R, sm, g, sp, sb, se, diag, step, t);
             else
-                process_segment<MODE, 1>(R, sm, sp, sb, se, diag, step, t);
+                process_segment<MODE, 1>(R, sm, g, sp, sb, se, diag, step, t);
             flush_species(R, sm, S, MI::count_only);
         }
         if (MI::push) flush_tally(R, S, t);
@@ -1521,7 +1626,7 @@ __global__ void k_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1
 // implicit pass 1; 1 = implicit pass 2; 2 = counting sort.
 // ---------------------------------------------------------------------------
 template <int MODE>
-__device__ void batch_item(const Run &R, unsigned char *smem, int S, long long b, long long e,
+__device__ void batch_item(const Run &R, unsigned char *smem, const Ring &g, int S, long long b, long long e,
                            unsigned int items_r, int r, int &loaded_run) {
     using MI = ModeInfo<MODE>;
     __shared__ bool s_last;
@@ -1553,9 +1658,9 @@ __device__ void batch_item(const Run &R, unsigned char *smem, int S, long long b
         for (long long sb = b; sb < e; sb += kFlushEvery) {
             const long long se = sb + kFlushEvery < e ? sb + kFlushEvery : e;
             if (S == 0)
-                process_segment<MODE, 0>(R, sm, sp, sb, se, diag, step, t);
+                process_segment<MODE, 0>(R, sm, g, sp, sb, se, diag, step, t);
             else
-                process_segment<MODE, 1>(R, sm, sp, sb, se, diag, step, t);
+                process_segment<MODE, 1>(R, sm, g, sp, sb, se, diag, step, t);
             flush_species(R, sm, S, MI::count_only);
         }
         if (MI::push) flush_tally(R, S, t);
@@ -1600,11 +1705,23 @@ template <int PHASE>
 __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ runs, int nruns,
                                                        long long *work, BatchState *bs, long long chunk,
                                                        int table_off) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem_all[];
     __shared__ unsigned int sc_u[33];
     __shared__ unsigned int s_item;
     __shared__ bool s_glast;
-    unsigned int *table = (unsigned int *)(smem + table_off);  // [2 nruns + 1] item prefix
+    __shared__ __align__(8) unsigned long long s_bar[kStages];
+    __shared__ unsigned int s_uses;
+    unsigned int *table = (unsigned int *)(smem_all + table_off);  // [2 nruns + 1] item prefix
+    Ring g;
+    g.buf = (uint32_t *)smem_all;
+    g.bar = s_bar;
+    g.uses = &s_uses;
+    unsigned char *smem = smem_all + ring_bytes();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1u);
+        s_uses = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     const int nj = 2 * nruns;
     // items per (run, species); a run with no particles still gets one empty
     // item so that its tail (field solve, step counter) runs
@@ -1662,13 +1779,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ r
         if (PHASE == 2) {
             batch_sort_item(R, S, b, e, items_r);
         } else if (PHASE == 1) {
-            batch_item<kImplicit2>(R, smem, S, b, e, items_r, r, loaded_run);
+            batch_item<kImplicit2>(R, smem, g, S, b, e, items_r, r, loaded_run);
         } else if (R.scheme == 0) {
-            batch_item<kExplicitEC>(R, smem, S, b, e, items_r, r, loaded_run);
+            batch_item<kExplicitEC>(R, smem, g, S, b, e, items_r, r, loaded_run);
         } else if (R.scheme == 1) {
-            batch_item<kExplicitMC>(R, smem, S, b, e, items_r, r, loaded_run);
+            batch_item<kExplicitMC>(R, smem, g, S, b, e, items_r, r, loaded_run);
         } else {
-            batch_item<kImplicit1>(R, smem, S, b, e, items_r, r, loaded_run);
+            batch_item<kImplicit1>(R, smem, g, S, b, e, items_r, r, loaded_run);
         }
     }
     // the last block of the launch publishes the work counts of the next one
@@ -1692,7 +1809,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ r
 int block_smem_bytes(const Run &r) {
     const size_t a = main_smem_bytes(r.n_cells, r.eedf_bins);
     const size_t b = tail_smem_bytes(r.n_cells);
-    return (int)(a > b ? a : b);
+    return (int)(ring_bytes() + (a > b ? a : b));
 }
 
 // The dynamic shared-memory limit of every mode is raised once by
@@ -1780,7 +1897,7 @@ cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c
 size_t batch_smem_bytes(int max_cells, int max_bins, int nruns, int *table_off) {
     const size_t a = main_smem_bytes(max_cells, max_bins);
     const size_t b = tail_smem_bytes(max_cells);
-    const size_t off = ((a > b ? a : b) + 15) & ~size_t(15);
+    const size_t off = (ring_bytes() + (a > b ? a : b) + 15) & ~size_t(15);
     *table_off = (int)off;
     return off + 4 * (size_t)(2 * nruns + 1);
 }

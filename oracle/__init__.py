@@ -22,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_ADJ = os.path.join(_HERE, "adjoint.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 _SO = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
@@ -39,12 +40,12 @@ def build(force: bool = False) -> str:
     """Compile liboracle.so next to its source (plain C, IEEE FP64, no contraction)."""
     with _lock:
         stale = (not os.path.exists(_SO)) or any(
-            os.path.getmtime(f) > os.path.getmtime(_SO) for f in (_SRC, _HDR))
+            os.path.getmtime(f) > os.path.getmtime(_SO) for f in (_SRC, _SRC_ADJ, _HDR))
         if force or stale:
             tmp = _SO + ".tmp.%d" % os.getpid()
             subprocess.check_call(
                 ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                 "-fno-fast-math", _SRC, "-o", tmp, "-lm"])
+                 "-fno-fast-math", _SRC, _SRC_ADJ, "-o", tmp, "-lm"])
             os.replace(tmp, _SO)
     return _SO
 
@@ -144,6 +145,8 @@ def lib():
         L.orc_sim_grids.argtypes = [ctypes.c_void_p, _i64, _i64, _d, _d, _d]
         L.orc_sim_averages.argtypes = [ctypes.c_void_p, _d, _d, _d, _d, _d, _i64]
         L.orc_sim_reset_averages.argtypes = [ctypes.c_void_p]
+        L.orc_adj_forward.argtypes = [_P(AdjProblem), ctypes.c_int64, _d, _d, _d, _d, _d, _d, _i64]
+        L.orc_adj_gradient.argtypes = [_P(AdjProblem), ctypes.c_int64, _d, _d, _d, _d, _d, _d]
         _lib = L
     return _lib
 
@@ -413,3 +416,55 @@ class Sim:
         kinetic energy plus the energy of the field that push used."""
         d = self.diag()
         return sum(d["ke_x"]) + sum(d["ke_perp"]) + d["field_energy_push"]
+
+
+# ---- collisionless EC run and its discrete adjoint (adjoint.c) ----
+
+class AdjProblem(ctypes.Structure):
+    _fields_ = [
+        ("n_cells", ctypes.c_int32), ("periodic", ctypes.c_int32),
+        ("nsteps", ctypes.c_int64), ("step0", ctypes.c_int64),
+        ("length", ctypes.c_double), ("dt", ctypes.c_double),
+        ("rf_freq", ctypes.c_double), ("rf_volt", ctypes.c_double),
+        ("weight", ctypes.c_double), ("bg_density", ctypes.c_double),
+        ("c_power", ctypes.c_double), ("c_flux", ctypes.c_double),
+    ]
+
+
+def adj_problem(n_cells, periodic, nsteps, length, dt, rf_freq=0.0, rf_volt=0.0, weight=1.0,
+                bg_density=0.0, step0=0, c_power=1.0, c_flux=0.0) -> AdjProblem:
+    return AdjProblem(int(n_cells), int(bool(periodic)), int(nsteps), int(step0), float(length),
+                      float(dt), float(rf_freq), float(rf_volt), float(weight), float(bg_density),
+                      float(c_power), float(c_flux))
+
+
+def adj_forward(pb: AdjProblem, xi0, vx0) -> dict:
+    """Collisionless EC run: time-averaged absorbed power and current density,
+    final state and absorption steps (-1: never absorbed)."""
+    xi0 = np.ascontiguousarray(xi0, np.float64)
+    vx0 = np.ascontiguousarray(vx0, np.float64)
+    n = xi0.size
+    pw, fl = ctypes.c_double(), ctypes.c_double()
+    xe, ve = np.zeros(n), np.zeros(n)
+    ab = np.zeros(n, np.int64)
+    rc = lib().orc_adj_forward(ctypes.byref(pb), n, _ptr(xi0, ctypes.c_double), _ptr(vx0, ctypes.c_double),
+                               ctypes.cast(ctypes.byref(pw), _d), ctypes.cast(ctypes.byref(fl), _d),
+                               _ptr(xe, ctypes.c_double), _ptr(ve, ctypes.c_double), _ptr(ab, ctypes.c_int64))
+    if rc:
+        raise RuntimeError("orc_adj_forward failed")
+    return {"power": pw.value, "flux": fl.value, "xi": xe, "vx": ve, "absorbed_at": ab}
+
+
+def adj_gradient(pb: AdjProblem, xi0, vx0) -> dict:
+    """J = c_power <P> + c_flux <Gamma> and dJ/dv^{-1/2}, dJ/dxi^0, dJ/dV0."""
+    xi0 = np.ascontiguousarray(xi0, np.float64)
+    vx0 = np.ascontiguousarray(vx0, np.float64)
+    n = xi0.size
+    j, dv0 = ctypes.c_double(), ctypes.c_double()
+    gv, gx = np.zeros(n), np.zeros(n)
+    rc = lib().orc_adj_gradient(ctypes.byref(pb), n, _ptr(xi0, ctypes.c_double), _ptr(vx0, ctypes.c_double),
+                                ctypes.cast(ctypes.byref(j), _d), _ptr(gv, ctypes.c_double),
+                                _ptr(gx, ctypes.c_double), ctypes.cast(ctypes.byref(dv0), _d))
+    if rc:
+        raise RuntimeError("orc_adj_gradient failed")
+    return {"J": j.value, "dvx0": gv, "dxi0": gx, "dV0": dv0.value}

@@ -139,6 +139,33 @@ void     orc_sim_averages(const orc_sim *s, double *ne, double *ni, double *phi,
                           double *heat_e, double *heat_i, int64_t *eedf);
 void     orc_sim_reset_averages(orc_sim *s);
 
+/* ---- collisionless EC explicit run and its discrete adjoint (adjoint.c) ---- */
+/* Electrons (charge -e, mass m_e, weight particles/m^2 each) on a frozen
+   uniform ion background; no collisions; K = nsteps leapfrog steps of the EC
+   scheme from time level step0.  Objective J = c_power <P> + c_flux <Gamma>,
+   time averages over the K steps of P^n = sum q w E_p vbar_p and
+   Gamma^n = sum w vbar_p S_1(xi_p - 1/2)/dx, vbar = (v^{n-1/2} + v^{n+1/2})/2. */
+typedef struct orc_adj_problem {
+    int32_t n_cells;
+    int32_t periodic;        /* 0: electrodes (x=0 driven, x=L grounded, absorbing); 1: periodic */
+    int64_t nsteps;
+    int64_t step0;           /* time level of the initial state (RF phase) */
+    double length, dt, rf_freq, rf_volt;
+    double weight;           /* electrons per m^2 represented by one macro-particle */
+    double bg_density;       /* frozen ion density [m^-3] */
+    double c_power, c_flux;
+} orc_adj_problem;
+
+/* Forward run: time-averaged P and Gamma; final state (may be NULL);
+   absorbed_at[p] = step in which particle p was absorbed, -1 if never (may be NULL). */
+int orc_adj_forward(const orc_adj_problem *pb, int64_t np, const double *xi0, const double *vx0,
+                    double *power_avg, double *flux_avg, double *xi_end, double *vx_end,
+                    int64_t *absorbed_at);
+/* J and its gradient with respect to the initial velocities v^{-1/2} [n],
+   the initial positions in cell units [n] (may be NULL) and rf_volt. */
+int orc_adj_gradient(const orc_adj_problem *pb, int64_t np, const double *xi0, const double *vx0,
+                     double *j_out, double *dj_dvx0, double *dj_dxi0, double *dj_dv0);
+
 #ifdef __cplusplus
 }
 #endif

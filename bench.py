@@ -290,6 +290,119 @@ def energy_drift(steps=2000):
     return out
 
 
+def bench_batched(n_runs=256, steps=12, warmup=3):
+    """Batched persistent launches over the sweep of uneven discharges (cells
+    64..1024, 1e4..2e6 particles per species, explicit and implicit) against
+    the same runs advanced one by one through the single-run path on the same
+    GPU.  Both forms give bit-identical particles (tests/test_gpu_batch.py)."""
+    import torch
+    from paper_1310_5284_gb300.batch import BatchSim, discharge_from_spec
+    from paper_1310_5284_gb300.sim import Sim
+
+    cfgs = [discharge_from_spec(s) for s in workloads.batch_configs(n_runs)]
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    batch = BatchSim(cfgs, device=dev)
+    tune = batch.autotune(trial_steps=4)
+    batch.step(warmup)
+    torch.cuda.synchronize(dev)
+    c0 = sum(sum(batch.diag(r)["count"]) for r in range(n_runs))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(batch.stream)
+    batch.step(steps)
+    b.record(batch.stream)
+    torch.cuda.synchronize(dev)
+    t_batch = a.elapsed_time(b) * 1e-3
+    c1 = sum(sum(batch.diag(r)["count"]) for r in range(n_runs))
+    batch.close()
+    del batch
+    torch.cuda.empty_cache()
+    ps_batch = 0.5 * (c0 + c1) * steps
+    # the single-run form: each run alone, K steps, times summed
+    t_single, ps_single = 0.0, 0.0
+    for cfg in cfgs:
+        sim = Sim(cfg, device=dev)
+        sim.step(warmup)
+        torch.cuda.synchronize(dev)
+        n0_ = sum(sim.diag()["count"])
+        a.record(sim.stream)
+        sim.step(steps)
+        b.record(sim.stream)
+        torch.cuda.synchronize(dev)
+        t_single += a.elapsed_time(b) * 1e-3
+        ps_single += 0.5 * (n0_ + sum(sim.diag()["count"])) * steps
+        sim.close()
+    return {"n_runs": n_runs, "steps": steps, "particles": int(0.5 * (c0 + c1)),
+            "value": ps_batch / t_batch, "single_run_value": ps_single / t_single,
+            "speedup_vs_single_runs": (ps_batch / t_batch) / (ps_single / t_single), "unit": UNIT,
+            "autotuned": tune, "accuracy": "bit-identical to the single-run form"}
+
+
+def bench_adjoint(n_particles=1_000_000, n_cells=256, nsteps=200, checkpoint_every=20):
+    """Forward + checkpointed backward of the collisionless EC run (1M
+    electrons on a frozen ion background, 256 cells, 200 steps, checkpoint
+    every 20) against the plain single-run step of the same configuration,
+    and dJ/dV0 of the driven case against a central difference (h = 1e-4 V0)."""
+    import numpy as np
+    import torch
+    from paper_1310_5284_gb300.adjoint import AdjointRun
+    from paper_1310_5284_gb300.sim import Sim
+
+    e, eps0, me = 1.602176634e-19, 8.8541878128e-12, 9.1093837015e-31
+    n0, te = 1e15, 2.0
+    wp = math.sqrt(n0 * e * e / (eps0 * me))
+    dt = 0.1 / wp
+    length = n_cells * 1.0e-4
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    out = {"n_particles": n_particles, "n_cells": n_cells, "steps": nsteps, "checkpoint_every": checkpoint_every}
+    for name, periodic, volt in (("periodic", True, 0.0), ("driven", False, 100.0)):
+        spec = dict(periodic=periodic, n_cells=n_cells, n_particles=n_particles, nsteps=nsteps, n0=n0,
+                    bg_density=n0, length=length, dt=dt, rf_freq=0.0 if periodic else 1.0 / (nsteps * dt),
+                    checkpoint_every=checkpoint_every)
+        st = workloads.injected_particles(77, n_particles, n_cells, math.sqrt(e * te / me), sorted_cells=True)
+        cell = torch.from_numpy(st["cell"]).to(dev)
+        off = torch.from_numpy(st["off"]).to(dev)
+        vx = torch.from_numpy(st["vx"]).to(dev)
+        run = AdjointRun(spec, device=dev)
+        run.forward(volt, cell, off, vx)
+        run.backward(1.0, 0.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        pw, fl = run.forward(volt, cell, off, vx)
+        t1 = time.perf_counter()
+        g_v, _, d_volt = run.backward(1.0, 0.0)
+        t2 = time.perf_counter()
+        res = {"forward_ms": (t1 - t0) * 1e3, "backward_ms": (t2 - t1) * 1e3, "power": pw, "flux": fl,
+               "dP_dV0": d_volt, "grad_v_rms": float(g_v.float().pow(2).mean().sqrt())}
+        if not periodic:
+            h = 1e-4 * volt
+            pp, _ = run.forward(volt + h, cell, off, vx)
+            ap = run.final_state()["cell"] >= 0
+            pm, _ = run.forward(volt - h, cell, off, vx)
+            am = run.final_state()["cell"] >= 0
+            res["dP_dV0_central_difference"] = (pp - pm) / (2 * h)
+            res["absorption_events_changed_by_h"] = int(np.sum(ap != am))
+        run.close()
+        # the plain single-run form of the same configuration
+        cfg = dict(n_cells=n_cells, periodic=periodic, length=length, dt=dt, rf_freq=spec["rf_freq"],
+                   rf_volt=volt, n0=n0, bg_density=n0, np_init=n_particles, mcc=False, ions_mobile=False,
+                   sort_period=0, capacity=n_particles, births_capacity=16, eedf_bins=8)
+        sim = Sim(cfg, device=dev)
+        sim.set_particles("e", dict(st, id=np.arange(n_particles, dtype=np.uint32)), next_id=n_particles)
+        sim.init_field()
+        sim.step(5)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(sim.stream)
+        sim.step(nsteps)
+        b.record(sim.stream)
+        torch.cuda.synchronize(dev)
+        res["plain_run_ms"] = a.elapsed_time(b)
+        res["forward_plus_backward_over_plain"] = (res["forward_ms"] + res["backward_ms"]) / res["plain_run_ms"]
+        sim.close()
+        out[name] = res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,6 +413,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-energy", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -353,6 +468,10 @@ def main():
         line["cpu_baseline"] = oracle_baseline(cfg)
     if world == 1 and not args.no_energy:
         line["energy_drift"] = energy_drift()
+    if world == 1 and not args.no_adjoint:
+        line["adjoint"] = bench_adjoint()
+    if world == 1 and not args.no_batched:
+        line["batched"] = bench_batched()
     print(json.dumps(line))
     return 0
 

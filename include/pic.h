@@ -284,6 +284,65 @@ void pic_batch_free(pic_batch *b);
 int pic_deposit_noalloc(int32_t scheme, int32_t boundary, int32_t n_cells, const int32_t *cell,
                         const float *off, int64_t n, int64_t *rho_q_out, void *stream);
 
+/* ---- Adjoint of the collisionless EC explicit step ----
+   Reverse-mode derivative of a run of the explicit energy-conserving scheme
+   (Sec. 2, scheme (2): S_2 charge assignment Eq. 2, S_1 force interpolation
+   Eq. 3, leapfrog) for electrons on a frozen uniform ion background, with no
+   collisions.  Between electrodes (x = 0 driven by V(t) = rf_volt
+   sin(2 pi rf_freq t), x = L grounded, both absorbing, Sec. 3) or in a
+   periodic box.  The paper computes no derivatives; the objectives are the
+   time averages over the run's K steps of
+     P^n = sum_p q w E_p vbar_p                 power absorbed by the electrons [W/m^2]
+     G^n = sum_p w vbar_p S_1(xi_p - 1/2) / dx  electron current density at the centre
+                                                of the first cell [1/(m^2 s)]
+   with vbar = (v^{n-1/2} + v^{n+1/2})/2, and J = c_power <P> + c_flux <G>.
+   Absorptions are events the derivative holds fixed; the offset quantisation
+   of the charge assignment is differentiated as the smooth spline.  The
+   forward run stores a checkpoint every checkpoint_every steps; the backward
+   run recomputes each segment from its checkpoint and runs one reverse
+   launch per step. */
+typedef struct pic_adj_config {
+    int32_t boundary;          /* PIC_BC_ELECTRODES / PIC_BC_PERIODIC */
+    int32_t n_cells;           /* 2 .. 1024 */
+    int32_t checkpoint_every;  /* >= 1 steps per recomputed segment */
+    int32_t reserved0;
+    int64_t n_particles;       /* electrons, 1 .. 2^29 */
+    int64_t nsteps;            /* K >= 1 */
+    int64_t step0;             /* time level of the initial state (sets the RF phase) */
+    double length;             /* gap [m] */
+    double dt;                 /* [s] */
+    double rf_freq;            /* [Hz] */
+    double n0;                 /* electron density the n_particles represent [m^-3] */
+    double bg_density;         /* frozen ion density [m^-3] */
+} pic_adj_config;
+
+typedef struct pic_adj pic_adj;
+
+/* Device bytes of the adjoint arena (checkpoints, one segment of levels, the
+   field tables of every level, per-particle adjoints). */
+int pic_adj_required_sizes(const pic_adj_config *cfg, pic_sizes *out);
+/* Caller-owned arena as for pic_init (256-byte aligned, outlives the handle). */
+int pic_adj_init(const pic_adj_config *cfg, const pic_buffers *bufs, void *cuda_stream, pic_adj **out);
+/* Forward run from the initial state given as DEVICE arrays of n_particles
+   entries (cell in [0, n_cells), off in [0, 1), vx = v^{-1/2} [m/s]; an entry
+   with another cell or offset counts as no particle).  The arrays are copied;
+   the caller may reuse them on return.  Writes the time-averaged P and G to
+   the HOST array power_flux[2]; synchronises the stream.  rf_volt is ignored
+   in the periodic box. */
+int pic_adj_forward(pic_adj *h, double rf_volt, const int32_t *cell0, const float *off0,
+                    const float *vx0, double *power_flux);
+/* Gradient of J = c_power <P> + c_flux <G> for the last forward run: dJ/dv^{-1/2}
+   into the DEVICE array d_vx0 [n_particles] (float), dJ/dx^0 [per metre] into the
+   DEVICE array d_x0 (may be NULL), dJ/d rf_volt into the HOST double d_volt (may be
+   NULL; 0 in the periodic box).  PIC_EINVAL without a preceding forward run.
+   Synchronises the stream. */
+int pic_adj_backward(pic_adj *h, double c_power, double c_flux, float *d_vx0, float *d_x0,
+                     double *d_volt);
+/* State of time level K of the last forward run, HOST arrays of n_particles
+   entries (absorbed particles have cell = -1). */
+int pic_adj_final_state(pic_adj *h, int32_t *cell, float *off, float *vx);
+void pic_adj_free(pic_adj *h);
+
 void pic_free(pic_handle *h);
 
 /* Message of the last failing call on h (h may be NULL for pic_init /

@@ -73,6 +73,16 @@ class PicDiag(ctypes.Structure):
 # exported names and signatures, in the order include/pic.h declares them
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
+class PicAdjConfig(ctypes.Structure):
+    _fields_ = [
+        ("boundary", ctypes.c_int32), ("n_cells", ctypes.c_int32),
+        ("checkpoint_every", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("n_particles", ctypes.c_int64), ("nsteps", ctypes.c_int64), ("step0", ctypes.c_int64),
+        ("length", ctypes.c_double), ("dt", ctypes.c_double), ("rf_freq", ctypes.c_double),
+        ("n0", ctypes.c_double), ("bg_density", ctypes.c_double),
+    ]
+
+
 SIGNATURES = {
     "pic_version": ([], ctypes.c_int),
     "pic_build_info": ([], ctypes.c_char_p),
@@ -101,6 +111,12 @@ SIGNATURES = {
                             _P(ctypes.c_double)], ctypes.c_int),
     "pic_batch_status": ([_vp, _P(ctypes.c_uint32)], ctypes.c_int),
     "pic_batch_free": ([_vp], None),
+    "pic_adj_required_sizes": ([_P(PicAdjConfig), _P(PicSizes)], ctypes.c_int),
+    "pic_adj_init": ([_P(PicAdjConfig), _P(PicBuffers), _vp, _P(_vp)], ctypes.c_int),
+    "pic_adj_forward": ([_vp, ctypes.c_double, _vp, _vp, _vp, _P(ctypes.c_double)], ctypes.c_int),
+    "pic_adj_backward": ([_vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _P(ctypes.c_double)], ctypes.c_int),
+    "pic_adj_final_state": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "pic_adj_free": ([_vp], None),
     "pic_deposit_noalloc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int64,
                              _vp, _vp], ctypes.c_int),
     "pic_free": ([_vp], None),

@@ -147,6 +147,39 @@ struct Layout {
     size_t total;
 };
 
+// Arguments of the adjoint kernels (collisionless EC explicit step).
+struct AdjSlot {
+    int32_t *cell;
+    float *off;
+    float *vx;
+};
+
+struct AdjFwd {
+    AdjSlot in, out;       // time levels n and n+1 (distinct arrays)
+    const float *e_in;     // gather table of level n [n_cells + 2]
+    float *e_out;          // gather table of level n+1, written by the tail
+    double *obj;           // [2]: P^n, G^n
+    long long np;
+    long long level;       // time level of e_out
+};
+
+struct AdjRev {
+    AdjSlot lo, hi;        // time levels n and n+1
+    const float *e;        // gather table of level n
+    const float *lam_in;   // Lambda of level n+1 (nullptr: level n+1 is the last)
+    float *lam_out;        // Lambda of level n, written by the tail
+    float *lx, *lv;        // adjoints of x (level n+1 -> n) and v (v^{n+1/2} -> v^{n-1/2})
+    double *le;            // [n_cells + 2] scattered sensitivities (zero between launches)
+    double *dv0;           // accumulated dJ/dV0
+    long long np;
+    long long level;       // n
+    int a_part;            // 0: only finish level n+1 (the last launch, n+1 = 0)
+    float c_pw;            // c_power / K
+    float c_fl;            // c_flux / K
+    float w_dx;            // w / dx
+    double lam_scale;      // e w / eps0
+};
+
 // ---- shared host helpers (pic_capi.cu) ----
 Layout make_run_layout(const pic_config &c);
 int validate_run_config(const pic_config *c);  // PIC_* code; message via pic_last_error
@@ -176,6 +209,12 @@ size_t batch_smem_bytes(int max_cells, int max_bins, int nruns, int *table_off);
 cudaError_t batch_prepare(int smem, int *grid);
 cudaError_t launch_batch(int phase, const Run *runs, int nruns, long long *work, BatchState *bs,
                          long long chunk, int grid, int smem, int table_off, cudaStream_t s);
+// adjoint of the collisionless EC explicit step
+int adj_fwd_smem_bytes(int n_cells);
+int adj_rev_smem_bytes(int n_cells);
+cudaError_t adj_prepare(int n_cells, int *grid);
+cudaError_t launch_adj_fwd(const Run &r, const AdjFwd &a, bool push, int grid, cudaStream_t s);
+cudaError_t launch_adj_rev(const Run &r, const AdjRev &a, int grid, cudaStream_t s);
 // message returned by pic_last_error(NULL) (pic_capi.cu)
 void set_last_error(const char *msg);
 

@@ -2126,3 +2126,387 @@ extern "C" int pic_deposit_noalloc(int32_t scheme, int32_t boundary, int32_t n_c
                                                scheme == 1, scratch, (long long *)rho_q_out);
     return cudaGetLastError() == cudaSuccess ? 0 : -5;
 }
+
+// ===========================================================================
+// Adjoint of the collisionless EC explicit step (reverse mode).
+//
+// Electrons on a frozen ion background, no collisions.  The forward kernel is
+// the explicit EC step of Sec. 2 (scheme (2)) built from the same device
+// functions as k_particles<kExplicitEC> -- gather, push, renormalisation,
+// fixed-point S_2 assignment and the Gauss-law field solve -- so a state
+// advanced here is bit-identical to the same state advanced by pic_step.  It
+// reads time level n from one slot and writes level n+1 to another, keeps
+// absorbed particles in place with cell = -1 (the absorption step is the
+// event the derivative holds fixed), and sums per step the objectives
+//   P^n = sum_p q w E_p vbar_p             (power absorbed by the electrons)
+//   G^n = sum_p w vbar_p S_1(xi_p - 1/2)/dx (current density at the centre of
+//                                            the first cell)
+// with vbar = (v^{n-1/2} + v^{n+1/2}) / 2.
+//
+// The reverse kernel of level n (one launch per step, last block runs the
+// field part) finishes the position adjoint of level n+1 with the adjoint
+// field of that level, then takes the adjoint of the push of level n:
+//   lv' = lv + dt lx + dJ/dv,   lE = (q/m) dt lv' + dJ/dE_p,
+//   lx' = lx + (lE dE_p/dx + dJ/dx),   lv <- lv' + dJ/dv (v^{n-1/2} term),
+// scattering lE to the cell centres with the S_1 weights of the gather (the
+// transpose of Eq. 3).  The field part transposes the Gauss-law solve: the
+// cell-centred field is E_c = d0 + kappa P_c (+ background), P_c the prefix
+// of the node charge and d0 fixed by the electrode voltage (or the zero-mean
+// field of the periodic box), so with L_c the scattered sensitivities
+//   dJ/dq_g = kappa sum_{c >= g} (L_c - mean L),  dJ/dV_left = sum L / (n dx).
+// Differences of dJ/dq_g along the grid are again a cell-centred table, so the
+// derivative of the S_2 assignment at a particle is an EC gather (Eq. 3) of
+//   Lambda_c = (e w / eps0) (L_c - mean L):   lx += gather(Lambda)/dx,
+// which is the discrete F = -dU/dx structure of the scheme read backwards.
+// ===========================================================================
+namespace pic {
+
+// S_1(xi - 1/2) with its periodic image, and its derivative in xi: the EC
+// gather (Eq. 3) of a table holding 1 in the first cell.
+__device__ __forceinline__ float flux_weight(int n, int periodic, int cell, float off, float &deriv) {
+    if (cell == 0) {
+        deriv = off >= 0.5f ? -1.0f : 1.0f;
+        return off >= 0.5f ? 1.5f - off : 0.5f + off;
+    }
+    if (cell == 1 && off < 0.5f) {
+        deriv = -1.0f;
+        return 0.5f - off;
+    }
+    if (periodic && cell == n - 1 && off >= 0.5f) {
+        deriv = 1.0f;
+        return off - 0.5f;
+    }
+    deriv = 0.0f;
+    return 0.0f;
+}
+
+// A slot entry counts as a particle only with cell in [0, n) and off in [0, 1).
+__device__ __forceinline__ int adj_valid_cell(int cell, float off, int n) {
+    return (cell >= 0 && cell < n && off >= 0.0f && off < 1.0f) ? cell : -1;
+}
+
+template <int U, typename T>
+__device__ __forceinline__ void adj_load(const T *p, long long i0, long long np, T (&o)[kUnroll], T fill) {
+    if (i0 + U <= np) {
+        ldv<U>(p + i0, o);
+    } else {
+#pragma unroll
+        for (int q = 0; q < U; ++q) o[q] = i0 + q < np ? p[i0 + q] : fill;
+    }
+}
+
+template <int U, typename T>
+__device__ __forceinline__ void adj_store(T *p, long long i0, long long np, const T (&o)[kUnroll]) {
+    if (i0 + U <= np) {
+        stv<U>(p + i0, o);
+    } else {
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            if (i0 + q < np) p[i0 + q] = o[q];
+    }
+}
+
+template <bool PUSH>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_adj_fwd(Run R, AdjFwd A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ bool s_last;
+    __shared__ double s_obj[2][kThreads / 32];
+    constexpr int U = kUnroll;
+    const int n = R.n_cells;
+    const SmemMain sm = carve_main(smem, n, 0);
+    if (PUSH)
+        for (int k = threadIdx.x; k < n + 2; k += kThreads) sm.e[k] = A.e_in[k];
+    for (int k = threadIdx.x; k <= n; k += kThreads) {
+        sm.acc.cnt[k] = 0u;
+        sm.acc.a[k] = 0u;
+        sm.acc.bh[k] = 0u;
+        sm.acc.bl[k] = 0u;
+    }
+    __syncthreads();
+    const long long tile = (long long)kThreads * U;
+    double pw_acc = 0.0, fl_acc = 0.0;
+    long long added = 0;  // particles this block assigned since its last flush
+    for (long long t0 = (long long)blockIdx.x * tile; t0 < A.np; t0 += (long long)gridDim.x * tile) {
+        const long long i0 = t0 + (long long)threadIdx.x * U;
+        int cell[U];
+        float off[U], vx[U];
+        adj_load<U>(A.in.cell, i0, A.np, cell, -1);
+        adj_load<U>(A.in.off, i0, A.np, off, 0.0f);
+        if (PUSH) adj_load<U>(A.in.vx, i0, A.np, vx, 0.0f);
+        int key[U];
+        uint32_t a[U];
+        float pw = 0.0f, fl = 0.0f;
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            key[q] = -1;
+            a[q] = 0u;
+            cell[q] = adj_valid_cell(cell[q], off[q], n);
+            if (cell[q] < 0) continue;
+            if (PUSH) {
+                // the explicit EC step of k_particles<kExplicitEC>, collisionless
+                const float e_field = gather_ec(sm.e, cell[q], off[q]);
+                const float v_new = fmaf(R.qm_dt[0], e_field, vx[q]);
+                const float vb = 0.5f * (vx[q] + v_new);
+                float dfl;
+                pw += R.qw[0] * e_field * vb;
+                fl += flux_weight(n, R.periodic, cell[q], off[q], dfl) * vb;
+                float s = fmaf(v_new, R.dt_dx, off[q]);
+                if (!(fabsf(s) < 1.0e6f)) s = (float)(2 * n + 2);
+                int c = cell[q];
+                renormalise(c, s);
+                vx[q] = v_new;
+                off[q] = s;
+                if (R.periodic) {
+                    if (c < 0 || c >= n) c = ((c % n) + n) % n;
+                } else if (c < 0 || c >= n) {
+                    cell[q] = -1;  // absorbed by an electrode (Sec. 3)
+                    continue;
+                }
+                cell[q] = c;
+            }
+            key[q] = deposit_key_s2(cell[q], off[q], a[q]);
+        }
+        if (PUSH) {
+            adj_store<U>(A.out.cell, i0, A.np, cell);
+            adj_store<U>(A.out.off, i0, A.np, off);
+            adj_store<U>(A.out.vx, i0, A.np, vx);
+        }
+        pw_acc += (double)pw;
+        fl_acc += (double)fl;
+        deposit_tile(key, a, sm.acc, false);
+        added += tile;
+        if (added + tile > 65536) {  // keep the 32-bit block sums exact
+            flush_species(R, sm, 0, false);
+            added = 0;
+        }
+    }
+    flush_species(R, sm, 0, false);
+    if (PUSH) {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const double p = warp_sum(pw_acc), f = warp_sum(fl_acc);
+        if (lane == 0) {
+            s_obj[0][wid] = p;
+            s_obj[1][wid] = f;
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            double acc = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) acc += s_obj[threadIdx.x][w];
+            if (acc != 0.0) atomicAdd(&A.obj[threadIdx.x], threadIdx.x == 0 ? acc : acc * (double)R.weight * R.inv_dx);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&R.st->blocks_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    Run Rt = R;
+    Rt.e_gather = A.e_out;
+    tail_field<kDepositEC>(Rt, smem, A.level, false, false);
+    tail_reset(R);
+    __syncthreads();
+    if (threadIdx.x == 0) R.st->blocks_done = 0u;
+}
+
+// Field part of the reverse step (last block): fold the ghost cells, the
+// transposed Gauss-law solve, dJ/dV0, and the table Lambda of this level.
+__device__ void tail_adjoint(const Run &R, const AdjRev &A, unsigned char *smem) {
+    __shared__ double sc_d[kThreads / 32 + 1];
+    const int n = R.n_cells;
+    double *L = (double *)smem;  // [n]
+    for (int c = threadIdx.x; c < n; c += kThreads) {
+        double v = A.le[c + 1];
+        if (R.periodic) {
+            if (c == 0) v += A.le[n + 1];      // right ghost = cell 0
+            if (c == n - 1) v += A.le[0];      // left ghost = cell n-1
+        }
+        L[c] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n + 2; k += kThreads) A.le[k] = 0.0;
+    double s = 0.0;
+    for (int c = threadIdx.x; c < n; c += kThreads) s += L[c];
+    s = block_sum_lean(s, sc_d);
+    const double mean = s / (double)n;
+    if (threadIdx.x == 0 && !R.periodic)
+        *A.dv0 += sin(2.0 * 3.14159265358979323846 * R.rf_freq * ((double)A.level * R.dt)) * s / ((double)n * R.dx);
+    for (int c = threadIdx.x; c < n; c += kThreads) {
+        A.lam_out[c + 1] = (float)(A.lam_scale * (L[c] - mean));
+        if (c == 0) A.lam_out[n + 1] = R.periodic ? (float)(A.lam_scale * (L[0] - mean)) : 0.0f;
+        if (c == n - 1) A.lam_out[0] = R.periodic ? (float)(A.lam_scale * (L[n - 1] - mean)) : 0.0f;
+    }
+    __syncthreads();
+}
+
+// Add a warp's scatter contributions to shared memory: each thread folded its
+// particles into the three table entries k0, k0+1, k0+2 (k0 < 0: none; k0 is
+// at most n_cells, and entry n_cells+2 is a padding slot that only receives
+// zeros).
+__device__ __forceinline__ void adj_scatter(float *sle, int k0, float v0, float v1, float v2) {
+    const int kw = __shfl_sync(FULL_MASK, k0, 0);
+    if (__all_sync(FULL_MASK, k0 == kw) && kw >= 0) {
+        v0 = warp_sum(v0);
+        v1 = warp_sum(v1);
+        v2 = warp_sum(v2);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&sle[kw], v0);
+            atomicAdd(&sle[kw + 1], v1);
+            atomicAdd(&sle[kw + 2], v2);
+        }
+        return;
+    }
+    if (k0 >= 0) {
+        if (v0 != 0.0f) atomicAdd(&sle[k0], v0);
+        if (v1 != 0.0f) atomicAdd(&sle[k0 + 1], v1);
+        if (v2 != 0.0f) atomicAdd(&sle[k0 + 2], v2);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_adj_rev(Run R, AdjRev A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ bool s_last;
+    constexpr int U = kUnroll;
+    const int n = R.n_cells;
+    float *se = (float *)smem;     // [n+2] E of level n
+    float *slam = se + (n + 2);    // [n+2] Lambda of level n+1
+    float *sle = slam + (n + 2);   // [n+3] scattered sensitivities of this block (last: padding)
+    for (int k = threadIdx.x; k < n + 3; k += kThreads) {
+        if (k < n + 2) {
+            se[k] = A.a_part ? A.e[k] : 0.0f;
+            slam[k] = A.lam_in ? A.lam_in[k] : 0.0f;
+        }
+        sle[k] = 0.0f;
+    }
+    __syncthreads();
+    const float dt = (float)R.dt, inv_dx = (float)R.inv_dx, qm_dt = R.qm_dt[0], qw = R.qw[0];
+    const long long tile = (long long)kThreads * U;
+    for (long long t0 = (long long)blockIdx.x * tile; t0 < A.np; t0 += (long long)gridDim.x * tile) {
+        const long long i0 = t0 + (long long)threadIdx.x * U;
+        int hc[U];
+        float ho[U], lx[U], lv[U];
+        adj_load<U>(A.hi.cell, i0, A.np, hc, -1);
+        adj_load<U>(A.hi.off, i0, A.np, ho, 0.0f);
+        adj_load<U>(A.lx, i0, A.np, lx, 0.0f);
+        adj_load<U>(A.lv, i0, A.np, lv, 0.0f);
+        // finish the position adjoint of level n+1: derivative of its charge assignment
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            hc[q] = adj_valid_cell(hc[q], ho[q], n);
+            if (hc[q] < 0) {
+                lx[q] = 0.0f;
+            } else if (A.lam_in) {
+                lx[q] += gather_ec(slam, hc[q], ho[q]) * inv_dx;
+            }
+        }
+        int k0 = -1;
+        float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f;
+        if (A.a_part) {
+            int lc[U];
+            float lo[U], vm[U], vp[U];
+            adj_load<U>(A.lo.cell, i0, A.np, lc, -1);
+            adj_load<U>(A.lo.off, i0, A.np, lo, 0.0f);
+            adj_load<U>(A.lo.vx, i0, A.np, vm, 0.0f);
+            adj_load<U>(A.hi.vx, i0, A.np, vp, 0.0f);
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const int c = adj_valid_cell(lc[q], lo[q], n);
+                if (c < 0) {
+                    lx[q] = 0.0f;
+                    lv[q] = 0.0f;
+                    continue;
+                }
+                // gather of level n and its slope in xi (table entries j, j+1)
+                const float off = lo[q];
+                const int j = c + (off >= 0.5f ? 1 : 0);
+                const float w1 = off >= 0.5f ? off - 0.5f : off + 0.5f;
+                const float ej = se[j], ej1 = se[j + 1];
+                const float e_field = (1.0f - w1) * ej + w1 * ej1;
+                const float de = ej1 - ej;
+                float dfl;
+                const float fl = flux_weight(n, R.periodic, c, off, dfl);
+                const float vb = 0.5f * (vm[q] + vp[q]);
+                const float dj_dv = 0.5f * (A.c_pw * qw * e_field + A.c_fl * A.w_dx * fl);
+                const float dj_de = A.c_pw * qw * vb;
+                const float dj_dxi = A.c_fl * A.w_dx * vb * dfl;
+                const float lvp = lv[q] + dt * lx[q] + dj_dv;     // x^{n+1} = x^n + dt v^{n+1/2}
+                const float le = qm_dt * lvp + dj_de;             // v^{n+1/2} = v^{n-1/2} + qm dt E_p
+                lv[q] = lvp + dj_dv;
+                lx[q] = lx[q] + (le * de + dj_dxi) * inv_dx;
+                // transpose of the gather: le (1 - w1) to entry j, le w1 to entry j+1
+                const float a0 = le * (1.0f - w1), a1 = le * w1;
+                if (k0 < 0) k0 = j;
+                if (j == k0) {
+                    v0 += a0;
+                    v1 += a1;
+                } else if (j == k0 + 1) {
+                    v1 += a0;
+                    v2 += a1;
+                } else {
+                    atomicAdd(&sle[j], a0);
+                    atomicAdd(&sle[j + 1], a1);
+                }
+            }
+        }
+        adj_store<U>(A.lx, i0, A.np, lx);
+        if (A.a_part) adj_store<U>(A.lv, i0, A.np, lv);
+        if (A.a_part) adj_scatter(sle, k0, v0, v1, v2);
+    }
+    if (!A.a_part) return;
+    __syncthreads();
+    for (int k = threadIdx.x; k < n + 2; k += kThreads)
+        if (sle[k] != 0.0f) atomicAdd(&A.le[k], (double)sle[k]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&R.st->blocks_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    tail_adjoint(R, A, smem);
+    if (threadIdx.x == 0) R.st->blocks_done = 0u;
+}
+
+int adj_fwd_smem_bytes(int n_cells) {
+    const size_t a = main_smem_bytes(n_cells, 0);
+    const size_t b = tail_smem_bytes(n_cells);
+    return (int)(a > b ? a : b);
+}
+
+int adj_rev_smem_bytes(int n_cells) {
+    const size_t a = 4 * (3 * (size_t)(n_cells + 2) + 1);
+    const size_t b = 8 * (size_t)n_cells;
+    return (int)(((a > b ? a : b) + 15) & ~size_t(15));
+}
+
+cudaError_t adj_prepare(int n_cells, int *grid) {
+    int dev = 0, sms = 0, per = 1, per_r = 1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int sf = adj_fwd_smem_bytes(n_cells), sr = adj_rev_smem_bytes(n_cells);
+    if ((e = cudaFuncSetAttribute(k_adj_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_adj_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_adj_rev, cudaFuncAttributeMaxDynamicSharedMemorySize, sr)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adj_fwd<true>, kThreads, sf)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_r, k_adj_rev, kThreads, sr)) != cudaSuccess) return e;
+    per = per < per_r ? per : per_r;
+    *grid = sms * (per > 0 ? per : 1);
+    return cudaSuccess;
+}
+
+cudaError_t launch_adj_fwd(const Run &r, const AdjFwd &a, bool push, int grid, cudaStream_t s) {
+    const int smem = adj_fwd_smem_bytes(r.n_cells);
+    if (push)
+        k_adj_fwd<true><<<grid, kThreads, smem, s>>>(r, a);
+    else
+        k_adj_fwd<false><<<grid, kThreads, smem, s>>>(r, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_rev(const Run &r, const AdjRev &a, int grid, cudaStream_t s) {
+    k_adj_rev<<<grid, kThreads, adj_rev_smem_bytes(r.n_cells), s>>>(r, a);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

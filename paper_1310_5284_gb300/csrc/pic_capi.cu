@@ -493,7 +493,10 @@ int pic_init(const pic_config *cfg, const pic_buffers *bufs, void *stream, pic_h
         cuda_fail(h, cudaGetLastError(), "occupancy");
         return bail(PIC_ECUDA);
     }
-    h->grid_sort = h->grid_push;
+    if (sort_grid(&h->grid_sort) != cudaSuccess) {
+        cuda_fail(h, cudaGetLastError(), "sort occupancy");
+        return bail(PIC_ECUDA);
+    }
     if (cfg->scheme == PIC_EC_IMPLICIT) {
         int g1 = 0, g2 = 0;
         occupancy_grid(h->run, kImplicit1, &g1);

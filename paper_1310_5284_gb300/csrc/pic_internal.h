@@ -70,7 +70,7 @@ struct DevState {
     unsigned int blocks_done;      // last-block detection of the particle kernels
     unsigned int n_births;         // births recorded in the current step
     unsigned int sort_blocks_done;
-    unsigned int pad0;
+    unsigned int next_item;        // work-item claim counter of the running particle launch
     unsigned long long absorbed_step[2];
     double ke_x_acc[2], power_acc[2];
     double ke_x[2], power[2];
@@ -199,6 +199,7 @@ int block_smem_bytes(const Run &r);
 cudaError_t launch_load(const Run &r, int species, long long n, float vth, cudaStream_t s);
 cudaError_t launch_particles(const Run &r, Mode m, int grid, cudaStream_t s);
 cudaError_t launch_sort(const Run &r, int grid, cudaStream_t s);
+cudaError_t sort_grid(int *grid);
 cudaError_t launch_set_abar(const Run &r, cudaStream_t s);
 cudaError_t launch_perp_energy(const Run &r, cudaStream_t s);
 cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,

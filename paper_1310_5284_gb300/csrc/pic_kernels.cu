@@ -1372,6 +1372,7 @@ __device__ void tail(const Run &R, unsigned char *smem, bool diag) {
             if (diag) st->n_diag += 1;
         }
         st->n_births = 0u;
+        st->next_item = 0u;
         st->blocks_done = 0u;
     }
 }
@@ -1400,6 +1401,224 @@ __device__ __forceinline__ void block_segment(long long ne, long long ni, int &S
 }
 
 // ---------------------------------------------------------------------------
+// Dynamic work distribution of the particle launch.  The slots of both
+// species are cut into items of kItemTiles tiles (electrons first, then
+// ions); blocks claim items from an atomic counter until none are left, so
+// blocks that met cheap particles take more of them.  Thread 0 of a block is
+// the producer of its copy ring: it claims one item ahead and issues the
+// tiles of consecutive items back to back, writing each tile's species,
+// first slot and length next to the ring stage; the other warps consume the
+// stages in order.  Claims only increase, so a block switches species at most
+// once: its shared accumulators, tallies and collision queue are flushed at
+// that switch.
+// ---------------------------------------------------------------------------
+constexpr int kItemTiles = 4;
+
+struct Stream {
+    int *S;            // [kStages] species of the staged tile
+    long long *o;      // [kStages] first slot
+    int *n;            // [kStages] particles (0: the stream has ended)
+};
+
+// Producer state (shared memory, used by thread 0 only).
+struct Producer {
+    long long pos, end, next, total, ne_items, ne, ni;
+    int S;
+};
+
+__device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, const Stream &ms, Producer &p,
+                                               int par, unsigned int u, bool need_id, int mode_fields,
+                                               bool implicit) {
+    const int stage = (int)(u % kStages);
+    if (p.pos >= p.end) {
+        if (p.next >= p.total) {
+            ms.n[stage] = 0;
+            return;
+        }
+        const long long len = (long long)kItemTiles * kTile;
+        if (p.next < p.ne_items) {
+            p.S = 0;
+            p.pos = p.next * len;
+            p.end = min(p.pos + len, p.ne);
+        } else {
+            p.S = 1;
+            p.pos = (p.next - p.ne_items) * len;
+            p.end = min(p.pos + len, p.ni);
+        }
+        p.next = (long long)atomicAdd(&R.st->next_item, 1u);
+    }
+    const int n = (int)min((long long)kTile, p.end - p.pos);
+    ms.S[stage] = p.S;
+    ms.o[stage] = p.pos;
+    ms.n[stage] = n;
+    const unsigned int bytes = (unsigned int)(((n * 4) + 15) & ~15);  // arrays are padded to 16 bytes
+    const int nf = mode_fields + (implicit ? 1 : 0) + (need_id ? 1 : 0);
+    const Species &s = R.buf[par][p.S];
+    const long long o = p.pos;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&g.bar[stage], bytes * nf);
+    bulk_g2s(ring_field(g, stage, 0), s.cell + o, bytes, &g.bar[stage]);
+    bulk_g2s(ring_field(g, stage, 1), s.off + o, bytes, &g.bar[stage]);
+    if (mode_fields >= 3) bulk_g2s(ring_field(g, stage, 2), s.vx + o, bytes, &g.bar[stage]);
+    if (implicit) bulk_g2s(ring_field(g, stage, 3), s.abar + o, bytes, &g.bar[stage]);
+    if (need_id) bulk_g2s(ring_field(g, stage, 4), s.id + o, bytes, &g.bar[stage]);
+    p.pos += n;
+}
+
+// One staged tile of species S: n particles from slot o.  Indices handed to
+// step_particle and the collision queue are absolute slots of sp.
+template <int MODE, int S>
+__device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, const Ring &g, int stage,
+                                            const Species &sp, long long o, int len, bool need_id, bool diag,
+                                            long long step, Tally &t) {
+    constexpr int U = kUnroll;
+    using MI = ModeInfo<MODE>;
+    const int i0 = U * (int)threadIdx.x;  // place of the first particle in the tile
+    const bool full = i0 + U - 1 < len;
+    int cell[U];
+    float off[U], vx[U], abar[U];
+    uint32_t id[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+        const bool ok = i0 + q < len;
+        cell[q] = ok ? (int)ring_field(g, stage, 0)[i0 + q] : -1;
+        off[q] = ok ? __uint_as_float(ring_field(g, stage, 1)[i0 + q]) : 0.0f;
+        vx[q] = (ok && MI::loads_v) ? __uint_as_float(ring_field(g, stage, 2)[i0 + q]) : 0.0f;
+        abar[q] = (ok && MI::implicit) ? __uint_as_float(ring_field(g, stage, 3)[i0 + q]) : 0.0f;
+        id[q] = (ok && need_id) ? ring_field(g, stage, 4)[i0 + q] : 0u;
+    }
+    int key[U];
+    uint32_t a[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+        a[q] = 0u;
+        key[q] = -1;
+        if (cell[q] < 0) continue;  // beyond the tile, or a hole left by absorption
+        key[q] = step_particle<MODE, S>(R, sm, sp, o + i0 + q, cell[q], off[q], vx[q], abar[q], id[q], diag,
+                                        step, t, a[q]);
+    }
+    if (MI::push) {
+        const long long b = o + i0;
+        if (full) {
+            stv<U>(sp.cell + b, cell);
+            stv<U>(sp.off + b, off);
+            stv<U>(sp.vx + b, vx);
+            if (MI::implicit) stv<U>(sp.abar + b, abar);
+        } else {
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                if (i0 + q < len) {
+                    sp.cell[b + q] = cell[q];
+                    sp.off[b + q] = off[q];
+                    sp.vx[b + q] = vx[q];
+                    if (MI::implicit) sp.abar[b + q] = abar[q];
+                }
+            }
+        }
+    }
+    deposit_tile(key, a, sm.acc, MI::count_only);
+}
+
+// Everything a block adds to the run for species S before it moves on: the
+// deposit accumulators, the tallies and the heating profile.
+template <int MODE>
+__device__ void stream_flush(const Run &R, const SmemMain &sm, int S, bool diag, Tally &t) {
+    using MI = ModeInfo<MODE>;
+    flush_species(R, sm, S, MI::count_only);
+    if (MI::push) flush_tally(R, S, t);
+    t = Tally{0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
+    if (diag) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < R.n_cells; k += kThreads) {
+            const float h = sm.heat[k];
+            if (h != 0.0f) atomicAdd(&R.heat[S][k], (double)h / R.dx);
+            sm.heat[k] = 0.0f;
+        }
+        __syncthreads();
+    }
+}
+
+template <int MODE>
+__device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, const Stream &ms, Producer &p,
+                             bool diag, long long step) {
+    using MI = ModeInfo<MODE>;
+    DevState *st = R.st;
+    const int par = st->parity;
+    const Species sp[2] = {R.buf[par][0], R.buf[par][1]};
+    const bool need_id = MI::push && R.mcc;
+    const int mode_fields = MI::loads_v ? 3 : 2;
+    if (threadIdx.x == 0) {
+        const long long len = (long long)kItemTiles * kTile;
+        p.pos = p.end = 0;
+        p.ne = st->n_slots[0];
+        p.ni = R.ions_mobile ? st->n_slots[1] : 0;
+        p.ne_items = (p.ne + len - 1) / len;
+        p.total = p.ne_items + (p.ni + len - 1) / len;
+        p.S = 0;
+        p.next = (long long)atomicAdd(&st->next_item, 1u);
+        for (int k = 0; k < kStages - 1; ++k)
+            producer_issue(R, g, ms, p, par, (unsigned int)k, need_id, mode_fields, MI::implicit);
+    }
+    __syncthreads();
+    Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
+    int cur = -1;
+    long long added = 0;
+    for (unsigned int u = 0;; ++u) {
+        const int stage = (int)(u % kStages);
+        const int n = ms.n[stage];
+        if (n == 0) break;
+        const int S = ms.S[stage];
+        const long long o = ms.o[stage];
+        if (S != cur || added + n > kFlushEvery) {
+            if (cur >= 0) {
+                if (MI::push && R.mcc && *sm.q.n > 0u) {
+                    if (cur == 0)
+                        drain_collisions<0>(R, sm, sp[0], step, diag, t);
+                    else
+                        drain_collisions<1>(R, sm, sp[1], step, diag, t);
+                }
+                stream_flush<MODE>(R, sm, cur, diag, t);
+            }
+            cur = S;
+            added = 0;
+        }
+        if (threadIdx.x == 0)
+            producer_issue(R, g, ms, p, par, u + kStages - 1, need_id, mode_fields, MI::implicit);
+        if (!mbar_wait(R, &g.bar[stage], (u / kStages) & 1u)) {
+            // give up, but not before the copies already issued have landed (bounded)
+            for (unsigned int w = u + 1; w < u + kStages; ++w)
+                if (ms.n[w % kStages] > 0) mbar_wait(R, &g.bar[w % kStages], (w / kStages) & 1u);
+            __syncthreads();
+            break;
+        }
+        if (S == 0)
+            stream_tile<MODE, 0>(R, sm, g, stage, sp[0], o, n, need_id, diag, step, t);
+        else
+            stream_tile<MODE, 1>(R, sm, g, stage, sp[1], o, n, need_id, diag, step, t);
+        added += n;
+        __syncthreads();  // the stage is free again; the queue count is current
+        if (MI::push && R.mcc && *sm.q.n >= (unsigned int)(kQueue / 2)) {
+            if (S == 0)
+                drain_collisions<0>(R, sm, sp[0], step, diag, t);
+            else
+                drain_collisions<1>(R, sm, sp[1], step, diag, t);
+        }
+    }
+    if (cur >= 0) {
+        if (MI::push && R.mcc) {
+            __syncthreads();
+            if (*sm.q.n > 0u) {
+                if (cur == 0)
+                    drain_collisions<0>(R, sm, sp[0], step, diag, t);
+                else
+                    drain_collisions<1>(R, sm, sp[1], step, diag, t);
+            }
+        }
+        stream_flush<MODE>(R, sm, cur, diag, t);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The particle kernel: one launch per explicit step / implicit pass / deposit.
 // ---------------------------------------------------------------------------
 template <int MODE>
@@ -1408,6 +1627,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     __shared__ bool s_last;
     __shared__ __align__(8) unsigned long long s_bar[kStages];
     __shared__ unsigned int s_uses;
+    __shared__ int s_ms_S[kStages], s_ms_n[kStages];
+    __shared__ long long s_ms_o[kStages];
+    __shared__ Producer s_prod;
     using MI = ModeInfo<MODE>;
     DevState *st = R.st;
     const int n = R.n_cells;
@@ -1415,6 +1637,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     g.buf = (uint32_t *)smem_all;
     g.bar = s_bar;
     g.uses = &s_uses;
+    const Stream ms = {s_ms_S, s_ms_o, s_ms_n};
     unsigned char *smem = smem_all + ring_bytes();  // grid, accumulators, queue; the tail's space
     const SmemMain sm = carve_main(smem, n, R.eedf_bins);
     if (threadIdx.x == 0) {
@@ -1424,10 +1647,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     }
     const long long step = st->step;
     const bool diag = MI::push && R.diag_period > 0 && (step % R.diag_period) == 0;
-    const int par = st->parity;
-    long long b, e;
-    int S;
-    block_segment(st->n_slots[0], R.ions_mobile ? st->n_slots[1] : 0, S, b, e);
     // shared-memory grid
     if (MI::needs_field)
         for (int k = threadIdx.x; k < n + 2; k += kThreads) sm.e[k] = R.e_gather[k];
@@ -1443,28 +1662,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     }
     if (threadIdx.x == 0) *sm.q.n = 0u;
     __syncthreads();
-    if (b < e) {  // uniform across the block
-        Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
-        const Species sp = R.buf[par][S];
-        for (long long sb = b; sb < e; sb += kFlushEvery) {
-            const long long se = sb + kFlushEvery < e ? sb + kFlushEvery : e;
-            if (S == 0)
-                process_segment<MODE, 0>(R, sm, g, sp, sb, se, diag, step, t);
-            else
-                process_segment<MODE, 1>(R, sm, g, sp, sb, se, diag, step, t);
-            flush_species(R, sm, S, MI::count_only);
-        }
-        if (MI::push) flush_tally(R, S, t);
-        if (diag) {
-            __syncthreads();
-            for (int k = threadIdx.x; k < n; k += kThreads) {
-                const float h = sm.heat[k];
-                if (h != 0.0f) atomicAdd(&R.heat[S][k], (double)h / R.dx);
-                sm.heat[k] = 0.0f;
-            }
-            __syncthreads();
-        }
-    }
+    stream_block<MODE>(R, sm, g, ms, s_prod, diag, step);
     if (diag) {
         for (int k = threadIdx.x; k <= R.eedf_bins; k += kThreads)
             if (sm.eedf[k]) atomicAdd(&R.eedf[k], (unsigned long long)sm.eedf[k]);
@@ -1488,30 +1686,47 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
 // the cursor of their key (warp-aggregated: lanes sharing a key take
 // consecutive positions from one atomic).
 __device__ void sort_chunk(const Run &R, int par, int S, long long b, long long e) {
+    constexpr int V = 4;  // particles per thread in flight: all their loads are issued first
     const bool mc = R.scheme == 1;
+    const bool implicit = R.scheme == 2;
     const int lane = threadIdx.x & 31;
     const Species src = R.buf[par][S], dst = R.buf[par ^ 1][S];
-    for (long long base = b; base < e; base += kThreads) {
-        const long long i = base + threadIdx.x;
-        const int cell = i < e ? src.cell[i] : -1;
-        const float off = i < e ? src.off[i] : 0.0f;
-        uint32_t a;
-        const int key = cell < 0 ? -1 : (mc ? deposit_key_s1(cell, off, a) : deposit_key_s2(cell, off, a));
-        const unsigned int peers = __match_any_sync(FULL_MASK, key);
-        if (key >= 0) {
-            const int leader = __ffs(peers) - 1;
-            const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
-            unsigned int base_pos = 0;
-            if (lane == leader) base_pos = atomicAdd(&R.cursor[S][key], (unsigned int)__popc(peers));
-            base_pos = __shfl_sync(peers, base_pos, leader);
-            const unsigned int pos = base_pos + rank;
-            dst.cell[pos] = cell;
-            dst.off[pos] = off;
-            dst.vx[pos] = src.vx[i];
-            dst.vy[pos] = src.vy[i];
-            dst.vz[pos] = src.vz[i];
-            dst.id[pos] = src.id[i];
-            if (R.scheme == 2) dst.abar[pos] = src.abar[i];
+    for (long long base = b; base < e; base += (long long)kThreads * V) {
+        int cell[V];
+        float off[V], vx[V], vy[V], vz[V], ab[V];
+        uint32_t id[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const long long i = base + (long long)q * kThreads + threadIdx.x;
+            const bool ok = i < e;
+            cell[q] = ok ? src.cell[i] : -1;
+            off[q] = ok ? src.off[i] : 0.0f;
+            vx[q] = ok ? src.vx[i] : 0.0f;
+            vy[q] = ok ? src.vy[i] : 0.0f;
+            vz[q] = ok ? src.vz[i] : 0.0f;
+            id[q] = ok ? src.id[i] : 0u;
+            ab[q] = (ok && implicit) ? src.abar[i] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            uint32_t a;
+            const int key = cell[q] < 0 ? -1 : (mc ? deposit_key_s1(cell[q], off[q], a) : deposit_key_s2(cell[q], off[q], a));
+            const unsigned int peers = __match_any_sync(FULL_MASK, key);
+            if (key >= 0) {
+                const int leader = __ffs(peers) - 1;
+                const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
+                unsigned int base_pos = 0;
+                if (lane == leader) base_pos = atomicAdd(&R.cursor[S][key], (unsigned int)__popc(peers));
+                base_pos = __shfl_sync(peers, base_pos, leader);
+                const unsigned int pos = base_pos + rank;
+                dst.cell[pos] = cell[q];
+                dst.off[pos] = off[q];
+                dst.vx[pos] = vx[q];
+                dst.vy[pos] = vy[q];
+                dst.vz[pos] = vz[q];
+                dst.id[pos] = id[q];
+                if (implicit) dst.abar[pos] = ab[q];
+            }
         }
     }
 }
@@ -1875,6 +2090,19 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
 cudaError_t launch_sort(const Run &r, int grid, cudaStream_t s) {
     k_sort<<<grid, kThreads, 0, s>>>(r);
     return cudaGetLastError();
+}
+
+// Grid of the sort: as many resident blocks as fit (the scatter is latency-bound).
+cudaError_t sort_grid(int *grid) {
+    int dev = 0, sms = 0, per = 1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sort, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    *grid = sms * (per > 0 ? per : 1);
+    return cudaSuccess;
 }
 
 cudaError_t launch_set_abar(const Run &r, cudaStream_t s) {

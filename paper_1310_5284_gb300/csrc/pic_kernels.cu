@@ -739,6 +739,8 @@ struct Ring {
 };
 
 __host__ __device__ constexpr size_t ring_bytes() { return (size_t)kStages * kMaxFields * kTile * 4; }
+// The idle ring holds the tail's copy of the per-key sums (6 x 8 bytes a key).
+static_assert(ring_bytes() >= (size_t)48 * (kMaxCells + 1), "ring too small for the tail's key sums");
 
 __device__ __forceinline__ uint32_t *ring_field(const Ring &g, int stage, int f) {
     return g.buf + ((size_t)stage * kMaxFields + f) * kTile;
@@ -922,23 +924,39 @@ struct KeySums {
     unsigned long long c, a, b;
 };
 
-__device__ __forceinline__ KeySums key_sums(const Run &R, int S, int k) {
+// Where the tail reads the per-key sums (count, sum a, sum a^2) of both
+// species: the run's global accumulators or the tail's shared-memory copy.
+struct Keys {
+    unsigned long long *c[2], *a[2], *b[2];
+};
+
+__device__ __forceinline__ Keys global_keys(const Run &R) {
+    Keys K;
+    for (int S = 0; S < 2; ++S) {
+        K.c[S] = R.acc_cnt[S];
+        K.a[S] = R.acc_a[S];
+        K.b[S] = R.acc_b[S];
+    }
+    return K;
+}
+
+__device__ __forceinline__ KeySums key_sums(const Run &R, const Keys &K, int S, int k) {
     const int n = R.n_cells;
     KeySums r = {0ull, 0ull, 0ull};
     if (R.periodic) {
         k = ((k % n) + n) % n;
-        r.c = R.acc_cnt[S][k];
-        r.a = R.acc_a[S][k];
-        r.b = R.acc_b[S][k];
+        r.c = K.c[S][k];
+        r.a = K.a[S][k];
+        r.b = K.b[S][k];
         if (k == 0) {
-            r.c += R.acc_cnt[S][n];
-            r.a += R.acc_a[S][n];
-            r.b += R.acc_b[S][n];
+            r.c += K.c[S][n];
+            r.a += K.a[S][n];
+            r.b += K.b[S][n];
         }
     } else if (k >= 0 && k <= n) {
-        r.c = R.acc_cnt[S][k];
-        r.a = R.acc_a[S][k];
-        r.b = R.acc_b[S][k];
+        r.c = K.c[S][k];
+        r.a = K.a[S][k];
+        r.b = K.b[S][k];
     }
     return r;
 }
@@ -949,10 +967,10 @@ __device__ __forceinline__ KeySums key_sums(const Run &R, int S, int k) {
 // 2^32 c_{g+1} - 2^17 A_{g+1} + B_{g+1} from key g+1.  Electrodes fold the
 // ghost nodes onto the wall nodes; the periodic box wraps.  Unsigned
 // arithmetic: the result is exact modulo 2^64 and lies in range.
-__device__ __forceinline__ unsigned long long node_charge_s2(const Run &R, int S, int g) {
+__device__ __forceinline__ unsigned long long node_charge_s2(const Run &R, const Keys &K, int S, int g) {
     const int n = R.n_cells;
     if (R.periodic && g == n) return 0ull;
-    const KeySums m = key_sums(R, S, g - 1), z = key_sums(R, S, g), p = key_sums(R, S, g + 1);
+    const KeySums m = key_sums(R, K, S, g - 1), z = key_sums(R, K, S, g), p = key_sums(R, K, S, g + 1);
     unsigned long long q = (z.c << 32) + (z.a << 17) - 2ull * z.b + m.b + (p.c << 32) - (p.a << 17) + p.b;
     if (!R.periodic) {
         if (g == 0) q += (z.c << 32) - (z.a << 17) + z.b;  // ghost node -1
@@ -963,9 +981,9 @@ __device__ __forceinline__ unsigned long long node_charge_s2(const Run &R, int S
 
 // S_1 node charge (momentum-conserving scheme), key = cell, value F:
 // node g gets (2^16 c_g - A_g) from cell g and A_{g-1} from cell g-1, times 2^17.
-__device__ __forceinline__ unsigned long long node_charge_s1(const Run &R, int S, int g) {
+__device__ __forceinline__ unsigned long long node_charge_s1(const Run &R, const Keys &K, int S, int g) {
     const int n = R.n_cells;
-    const unsigned long long *C = R.acc_cnt[S], *A = R.acc_a[S];
+    const unsigned long long *C = K.c[S], *A = K.a[S];
     if (R.periodic && g == n) return 0ull;
     unsigned long long q = 0;
     if (g < n) q += (C[g] << 16) - A[g];
@@ -975,8 +993,8 @@ __device__ __forceinline__ unsigned long long node_charge_s1(const Run &R, int S
 }
 
 // Susceptibility weight of cell c (units 2^-16): a from key c, 2^16 - a from key c+1.
-__device__ __forceinline__ unsigned long long chi_count(const Run &R, int S, int c) {
-    const KeySums z = key_sums(R, S, c), p = key_sums(R, S, c + 1);
+__device__ __forceinline__ unsigned long long chi_count(const Run &R, const Keys &K, int S, int c) {
+    const KeySums z = key_sums(R, K, S, c), p = key_sums(R, K, S, c + 1);
     return z.a + (p.c << 16) - p.a;
 }
 
@@ -984,7 +1002,7 @@ __device__ __forceinline__ unsigned long long chi_count(const Run &R, int S, int
 // both species' slots with consecutive ids, assign their charge (explicit) or
 // count their keys (implicit pass 2, for the sort).
 template <int MODE>
-__device__ void tail_births(const Run &R, unsigned char *smem, bool diag) {
+__device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag) {
     DevState *st = R.st;
     __shared__ unsigned int s_B, s_ok;
     __shared__ long long s_ne, s_ni;
@@ -1094,10 +1112,10 @@ __device__ void tail_births(const Run &R, unsigned char *smem, bool diag) {
         const int key = MODE == kExplicitMC ? deposit_key_s1(bb.cell, bb.off, a)
                                             : deposit_key_s2(bb.cell, bb.off, a);
         for (int S = 0; S < 2; ++S) {
-            atomicAdd(&R.acc_cnt[S][key], 1ull);
+            atomicAdd(&K.c[S][key], 1ull);
             if (MODE != kImplicit2) {
-                atomicAdd(&R.acc_a[S][key], (unsigned long long)a);
-                atomicAdd(&R.acc_b[S][key], (unsigned long long)a * a);
+                atomicAdd(&K.a[S][key], (unsigned long long)a);
+                atomicAdd(&K.b[S][key], (unsigned long long)a * a);
             }
         }
         if (diag && R.eedf_bins > 0) {
@@ -1192,7 +1210,8 @@ __device__ void block_exclusive_scan_pair(long long &x, unsigned long long &y, l
 // With `cursors` the same integer scan also yields the sort cursors (the
 // exclusive prefix of the per-key counts of both species).
 template <int MODE>
-__device__ void tail_field(const Run &R, unsigned char *smem, long long level, bool accumulate, bool cursors) {
+__device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long level, bool accumulate,
+                           bool cursors) {
     DevState *st = R.st;
     const int n = R.n_cells, n1 = n + 1;
     __shared__ long long sc_x[kThreads / 32];
@@ -1211,19 +1230,19 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
     }
     // node charges, densities, susceptibility
     for (int g = threadIdx.x; g <= n; g += kThreads) {
-        const unsigned long long ne = mc ? node_charge_s1(R, 0, g) : node_charge_s2(R, 0, g);
-        const unsigned long long ni = mc ? node_charge_s1(R, 1, g) : node_charge_s2(R, 1, g);
+        const unsigned long long ne = mc ? node_charge_s1(R, K, 0, g) : node_charge_s2(R, K, 0, g);
+        const unsigned long long ni = mc ? node_charge_s1(R, K, 1, g) : node_charge_s2(R, K, 1, g);
         q[g] = (long long)(ni - ne);
         R.rho_q[0][g] = (long long)ne;
         R.rho_q[1][g] = (long long)ni;
         if (accumulate) {
-            R.avg_ne[g] += (double)(long long)ne;
-            R.avg_ni[g] += (double)(long long)ni;
+            atomicAdd(&R.avg_ne[g], (double)(long long)ne);  // one writer per node: a plain sum
+            atomicAdd(&R.avg_ni[g], (double)(long long)ni);
         }
     }
     if (implicit) {
         for (int c = threadIdx.x; c < n; c += kThreads) {
-            const double chi = R.chi_coef[0] * (double)chi_count(R, 0, c) + R.chi_coef[1] * (double)chi_count(R, 1, c);
+            const double chi = R.chi_coef[0] * (double)chi_count(R, K, 0, c) + R.chi_coef[1] * (double)chi_count(R, K, 1, c);
             R.chi[c] = chi;
             rinv[c] = 1.0 / (1.0 + chi);
         }
@@ -1238,7 +1257,7 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
     for (int k = 0; k < per; ++k) {
         const int c = c_begin + k;
         if (c < n) runP += (R.periodic || c >= 1) ? q[c] : 0ll;
-        if (cursors && c < n1) runC += R.acc_cnt[0][c] | (R.acc_cnt[1][c] << 32);
+        if (cursors && c < n1) runC += K.c[0][c] | (K.c[1][c] << 32);
     }
     long long totP;
     unsigned long long totC;
@@ -1252,7 +1271,7 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
         if (cursors && c < n1) {
             R.cursor[0][c] = (unsigned int)(Cx & 0xffffffffull);
             R.cursor[1][c] = (unsigned int)(Cx >> 32);
-            Cx += R.acc_cnt[0][c] | (R.acc_cnt[1][c] << 32);
+            Cx += K.c[0][c] | (K.c[1][c] << 32);
         }
         if (c < n) {
             P += (R.periodic || c >= 1) ? q[c] : 0ll;
@@ -1275,7 +1294,7 @@ __device__ void tail_field(const Run &R, unsigned char *smem, long long level, b
             const double e = implicit ? rinv[c] * (d0 + pp[c]) : d0 + pp[c];
             pp[c] = e;  // now the face field
             R.e_cc[c] = e;
-            if (accumulate) R.avg_e[c] += e;
+            if (accumulate) atomicAdd(&R.avg_e[c], e);
             wsum += e * e;
             if (!mc) R.e_gather[c + 1] = (float)e;
         }
@@ -1323,7 +1342,7 @@ __device__ void tail_reset(const Run &R) {
 }
 
 // Sort cursors alone (implicit pass 2, which solves no field).
-__device__ void tail_cursors(const Run &R) {
+__device__ void tail_cursors(const Run &R, Keys K) {
     __shared__ long long sc_x[kThreads / 32];
     __shared__ unsigned long long sc_y[kThreads / 32];
     const int n1 = R.n_cells + 1;
@@ -1331,7 +1350,7 @@ __device__ void tail_cursors(const Run &R) {
     const int b0 = threadIdx.x * per;
     unsigned long long run = 0;
     for (int k = 0; k < per; ++k)
-        if (b0 + k < n1) run += R.acc_cnt[0][b0 + k] | (R.acc_cnt[1][b0 + k] << 32);
+        if (b0 + k < n1) run += K.c[0][b0 + k] | (K.c[1][b0 + k] << 32);
     long long dummy = 0, tdummy;
     unsigned long long tot;
     block_exclusive_scan_pair(dummy, run, tdummy, tot, sc_x, sc_y);
@@ -1340,21 +1359,57 @@ __device__ void tail_cursors(const Run &R) {
         if (j < n1) {
             R.cursor[0][j] = (unsigned int)(run & 0xffffffffull);
             R.cursor[1][j] = (unsigned int)(run >> 32);
-            run += R.acc_cnt[0][j] | (R.acc_cnt[1][j] << 32);
+            run += K.c[0][j] | (K.c[1][j] << 32);
         }
     }
     __syncthreads();
 }
 
 template <int MODE>
-__device__ void tail(const Run &R, unsigned char *smem, bool diag) {
+__device__ __noinline__ void tail(const Run &R, unsigned char *smem, unsigned char *stage, bool diag) {
     DevState *st = R.st;
     const long long step = st->step;
-    if (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit2) tail_births<MODE>(R, smem, diag);
-    if (MODE == kExplicitEC || MODE == kExplicitMC) tail_field<MODE>(R, smem, step + 1, true, true);
-    if (MODE == kImplicit1) tail_field<MODE>(R, smem, step + 1, true, false);
-    if (MODE == kDepositEC || MODE == kDepositMC) tail_field<MODE>(R, smem, step, false, true);
-    if (MODE == kImplicit2) tail_cursors(R);
+    // Copy the per-key sums of both species into shared memory with one batch
+    // of independent loads; everything after reads (and the births add to)
+    // this copy through Rs.  The global sums are cleared for the next launch.
+    const int n1 = R.n_cells + 1;
+    Keys Ks;
+    {
+        unsigned long long *base = (unsigned long long *)stage;
+        for (int S = 0; S < 2; ++S) {
+            Ks.c[S] = base + (size_t)(3 * S + 0) * n1;
+            Ks.a[S] = base + (size_t)(3 * S + 1) * n1;
+            Ks.b[S] = base + (size_t)(3 * S + 2) * n1;
+        }
+        constexpr int kPer = (kMaxCells + 1 + kThreads - 1) / kThreads;
+        for (int S = 0; S < 2; ++S) {  // per species: all loads first, then the stores
+            unsigned long long v[kPer][3];
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                const int k = threadIdx.x + j * kThreads;
+                if (k < n1) {
+                    v[j][0] = R.acc_cnt[S][k];
+                    v[j][1] = R.acc_a[S][k];
+                    v[j][2] = R.acc_b[S][k];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                const int k = threadIdx.x + j * kThreads;
+                if (k < n1) {
+                    Ks.c[S][k] = v[j][0];
+                    Ks.a[S][k] = v[j][1];
+                    Ks.b[S][k] = v[j][2];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit2) tail_births<MODE>(R, Ks, smem, diag);
+    if (MODE == kExplicitEC || MODE == kExplicitMC) tail_field<MODE>(R, Ks, smem, step + 1, true, true);
+    if (MODE == kImplicit1) tail_field<MODE>(R, Ks, smem, step + 1, true, false);
+    if (MODE == kDepositEC || MODE == kDepositMC) tail_field<MODE>(R, Ks, smem, step, false, true);
+    if (MODE == kImplicit2) tail_cursors(R, Ks);
     tail_reset(R);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1412,7 +1467,7 @@ __device__ __forceinline__ void block_segment(long long ne, long long ni, int &S
 // once: its shared accumulators, tallies and collision queue are flushed at
 // that switch.
 // ---------------------------------------------------------------------------
-constexpr int kItemTiles = 4;
+constexpr int kItemTiles = 1;
 
 struct Stream {
     int *S;            // [kStages] species of the staged tile
@@ -1674,7 +1729,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    tail<MODE>(R, smem, diag);
+    tail<MODE>(R, smem, smem_all, diag);
 }
 
 // ---------------------------------------------------------------------------
@@ -1895,7 +1950,7 @@ __device__ void batch_item(const Run &R, unsigned char *smem, const Ring &g, int
     __syncthreads();
     if (s_last) {
         __threadfence();
-        tail<MODE>(R, smem, diag);
+        tail<MODE>(R, smem, (unsigned char *)g.buf, diag);
         loaded_run = -1;  // the tail reused the shared memory
         __syncthreads();
     }
@@ -2531,7 +2586,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_adj_fwd(Run R, AdjFwd 
     __threadfence();
     Run Rt = R;
     Rt.e_gather = A.e_out;
-    tail_field<kDepositEC>(Rt, smem, A.level, false, false);
+    tail_field<kDepositEC>(Rt, global_keys(R), smem, A.level, false, false);
     tail_reset(R);
     __syncthreads();
     if (threadIdx.x == 0) R.st->blocks_done = 0u;

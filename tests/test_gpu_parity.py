@@ -264,6 +264,7 @@ def test_steps_match_oracle(name, over, strict, steps):
     compare_particles(gpu, orc, cfg)
     gpu.step(steps - strict)
     orc.step(steps - strict)
+    assert gpu.status() == 0  # no capacity, birth-buffer or bounded-wait flag
     dg, do = gpu.diag(), orc.diag()
     assert dg["step"] == do["step"] == steps
     floor = fp32_sensitivity(cfg, states, steps)

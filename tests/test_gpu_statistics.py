@@ -54,6 +54,7 @@ def test_window_statistics_match_oracle():
     n = cfg["np_init"]
     gpu = Sim(cfg, device="cuda:0")
     w_g, a_g = run(gpu, True)
+    assert gpu.status() == 0
     gpu.close()
     orc = oracle.Sim(dict(cfg, quantized=True)).load(n, n)
     w_o, a_o = run(orc, True)

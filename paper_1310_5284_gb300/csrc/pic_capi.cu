@@ -52,6 +52,8 @@ Layout make_layout(const pic_config &c) {
         L.rho_q[s] = take(8 * n1);
     }
     L.e_gather = take(4 * (n1 + 1));
+    L.e_hi = take(4 * n1);
+    L.e_lo = take(4 * n1);
     L.e_cc = take(8 * n1);
     L.chi = take(8 * n1);
     L.avg_ne = take(8 * n1);
@@ -207,6 +209,14 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
     R.kappa_bg = c.ions_mobile ? 0.0 : dx * kE * c.bg_density / kEps0;
     R.dens_scale = w * two_m33 / dx;
     R.eps0_dx_half = 0.5 * kEps0 * dx;
+    auto split = [](double v, float (&out)[2]) {
+        out[0] = (float)v;
+        out[1] = (float)(v - (double)out[0]);
+    };
+    split(R.kappa, R.kappa_ff);
+    split(R.kappa_bg, R.kbg_ff);
+    split(1.0 / (double)c.n_cells, R.inv_n_ff);
+    split(1.0 / ((double)c.n_cells * dx), R.inv_ndx_ff);
     for (int s = 0; s < 2; ++s) {
         R.chi_coef[s] = 0.5 * c.dt * c.dt * q[s] * q[s] * w / (m[s] * kEps0 * dx) * std::ldexp(1.0, -16);
         R.half_m_w[s] = 0.5 * m[s] * w;
@@ -273,6 +283,8 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
         R.heat[s] = (double *)(A + L.heat[s]);
     }
     R.e_gather = (float *)(A + L.e_gather);
+    R.e_hi = (float *)(A + L.e_hi);
+    R.e_lo = (float *)(A + L.e_lo);
     R.e_cc = (double *)(A + L.e_cc);
     R.chi = (double *)(A + L.chi);
     R.avg_ne = (double *)(A + L.avg_ne);
@@ -338,6 +350,7 @@ Mode deposit_mode_of(const pic_config &c) { return deposit_mode(c); }
 
 int run_diag(const Run &R, const pic_config &c, const Layout &L, unsigned char *arena, cudaStream_t s,
              pic_diag_t *out, int reset_avg, std::string *err) {
+    CKE(launch_finalize(R, s));  // work the last tail left to the next launch
     CKE(cudaMemsetAsync(R.st->ke_perp, 0, sizeof(double) * 2, s));
     CKE(launch_perp_energy(R, s));
     CKE(cudaStreamSynchronize(s));
@@ -395,6 +408,7 @@ int init_run_state(const pic_config &c, const Run &R, unsigned char *arena, size
     if (c.ions_mobile) CKE(launch_load(R, 1, c.np_init, (float)vth_i, s));
     // t = 0 charge assignment and field, abar = a^0 for the implicit scheme
     CKE(launch_particles(R, deposit_mode(c), grid, s));
+    CKE(launch_finalize(R, s));  // FP64 copy and energy of the t = 0 field
     if (c.scheme == PIC_EC_IMPLICIT) CKE(launch_set_abar(R, s));
     // the load is in random order: sort it once so that every block streams
     // particles of a few adjacent cells from the first step on
@@ -565,6 +579,7 @@ int pic_diag(pic_handle *h, pic_diag_t *out, int reset_avg) {
 int pic_profiles(pic_handle *h, double *ne, double *ni, double *phi, double *heat_e,
                  double *heat_i, uint64_t *eedf) {
     if (!h) return fail(PIC_EINVAL, "handle is NULL");
+    CK(h, launch_finalize(h->run, h->stream));
     DevState st;
     int r = read_state(h, &st);
     if (r) return r;
@@ -601,6 +616,7 @@ int pic_profiles(pic_handle *h, double *ne, double *ni, double *phi, double *hea
 int pic_grids(pic_handle *h, int64_t *rho_q_e, int64_t *rho_q_i, double *phi, double *e_cc,
               double *chi) {
     if (!h) return fail(PIC_EINVAL, "handle is NULL");
+    CK(h, launch_finalize(h->run, h->stream));
     int r = sync(h);
     if (r) return r;
     const size_t n1 = (size_t)h->cfg.n_cells + 1, n = (size_t)h->cfg.n_cells;

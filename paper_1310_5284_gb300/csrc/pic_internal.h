@@ -84,6 +84,13 @@ struct DevState {
     unsigned long long overflow[2];
     unsigned long long births_total;
     long long n_avg, n_diag;
+    // Work a particle launch's tail leaves to the next launch (or to the
+    // finalize kernel before the host reads diagnostics): bit 0 accumulate
+    // the running averages of the newest field and charges, bit 1 convert the
+    // newest field to FP64 and sum its energy.
+    unsigned int pending;
+    unsigned int pad1;
+    double fe_acc;                 // sum of E_c^2 of the field the next push uses
 };
 
 // State of a batched launch sequence (one per batch, in its arena).
@@ -110,6 +117,8 @@ struct Run {
     double dens_scale;   // density per 2^-33 macro charge: w 2^-33 / dx
     double half_m_w[2];  // kinetic energy per (m/s)^2 per macro-particle
     double eps0_dx_half; // field energy factor eps0 dx / 2
+    // the same constants as double-word FP32 pairs (hi, lo) for the tail
+    float kappa_ff[2], kbg_ff[2], inv_n_ff[2], inv_ndx_ff[2];
     // push (FP32)
     float qm_dt[2];        // (q/m) dt
     float qm[2];
@@ -131,6 +140,7 @@ struct Run {
     unsigned int *cursor[2];                                // [species][n_cells + 1]
     float *e_gather;       // [n_cells + 2]
     double *e_cc, *chi;                                     // [n_cells], [n_cells]
+    float *e_hi, *e_lo;    // [n_cells] newest field as a double-word pair (deferred conversion)
     long long *rho_q[2];   // [species][n_cells + 1] last assembled node charge, 2^-33 units
     double *avg_ne, *avg_ni, *avg_e, *heat[2];   // sums over steps (charge units, V/m)
     unsigned long long *eedf;
@@ -143,7 +153,7 @@ struct Layout {
     size_t state;
     size_t sp[2][2][7];  // [parity][species][field] offsets (cell, off, vx, vy, vz, id, abar)
     size_t acc_cnt[2], acc_a[2], acc_b[2], cursor[2], rho_q[2];
-    size_t e_gather, e_cc, chi, avg_ne, avg_ni, avg_e, heat[2], eedf, births;
+    size_t e_gather, e_cc, chi, avg_ne, avg_ni, avg_e, heat[2], eedf, births, e_hi, e_lo;
     size_t total;
 };
 
@@ -202,6 +212,7 @@ cudaError_t launch_sort(const Run &r, int grid, cudaStream_t s);
 cudaError_t sort_grid(int *grid);
 cudaError_t launch_set_abar(const Run &r, cudaStream_t s);
 cudaError_t launch_perp_energy(const Run &r, cudaStream_t s);
+cudaError_t launch_finalize(const Run &r, cudaStream_t s);
 cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
                                uint32_t c3, long long n, uint32_t *out, cudaStream_t s);
 cudaError_t occupancy_grid(const Run &r, Mode m, int *grid);

@@ -1209,25 +1209,93 @@ __device__ void block_exclusive_scan_pair(long long &x, unsigned long long &y, l
 // and so does its time average from the averages of E and V.
 // With `cursors` the same integer scan also yields the sort cursors (the
 // exclusive prefix of the per-key counts of both species).
+// ---------------------------------------------------------------------------
+// Double-word ("float-float") arithmetic, after Joldes, Muller & Popescu,
+// "Tight and rigorous error bounds for basic building blocks of double-word
+// arithmetic" (ACM TOMS 2017): a value is an unevaluated sum hi + lo of two
+// FP32 numbers with |lo| <= ulp(hi)/2, about 48 significant bits.  The field
+// solve of the explicit schemes runs in it because FP64 latency on this part
+// dominated the serial tail; FP64 only converts the result afterwards.
+// ---------------------------------------------------------------------------
+struct dw {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dw dw_two_sum(float a, float b) {  // Knuth: a + b exactly
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ dw dw_fast_two_sum(float a, float b) {  // Dekker, |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ dw dw_add(dw x, dw y) {  // accurate DW + DW (their Algorithm 6)
+    const dw s = dw_two_sum(x.hi, y.hi);
+    const dw t = dw_two_sum(x.lo, y.lo);
+    const dw v = dw_fast_two_sum(s.hi, s.lo + t.hi);
+    return dw_fast_two_sum(v.hi, t.lo + v.lo);
+}
+
+__device__ __forceinline__ dw dw_mul(dw x, dw y) {  // DW x DW (their Algorithm 12)
+    const float ch = x.hi * y.hi;
+    const float cl = fmaf(x.hi, y.hi, -ch);
+    const float tl = fmaf(x.lo, y.hi, x.hi * y.lo);
+    return dw_fast_two_sum(ch, cl + tl);
+}
+
+__device__ __forceinline__ dw dw_neg(dw x) { return {-x.hi, -x.lo}; }
+
+// An int64 as a double-word: three pieces of at most 22 bits are exact in
+// FP32; their sum is rounded once to the double-word precision.
+__device__ __forceinline__ dw dw_from_i64(long long v) {
+    const float a = (float)(v >> 44) * 17592186044416.0f;        // * 2^44
+    const float b = (float)((v >> 22) & 0x3fffffll) * 4194304.0f; // * 2^22
+    const float c = (float)(v & 0x3fffffll);
+    return dw_add(dw_two_sum(a, b), dw{c, 0.0f});
+}
+
+__device__ __forceinline__ dw dw_of(const float (&p)[2]) { return {p[0], p[1]}; }
+
+// Electrode voltage V(t) = rf_volt sin(2 pi f t) at time level `level` (0 in
+// the periodic box), with its double-word split.
+struct Volt {
+    double v;
+    float hi, lo;
+};
+
+__device__ __forceinline__ Volt electrode_volt(const Run &R, long long level) {
+    Volt r;
+    r.v = R.periodic ? 0.0 : R.rf_volt * sin(2.0 * 3.14159265358979323846 * R.rf_freq * ((double)level * R.dt));
+    r.hi = (float)r.v;
+    r.lo = (float)(r.v - (double)r.hi);
+    return r;
+}
+
+// Field of the new time level from the node charges (discrete Gauss law, see
+// the notes above the particle kernel).  defer: leave the FP64 conversion of
+// the field, the running averages and the field energy to the next launch
+// (st->pending); otherwise do them here.  vl: the electrode voltage if the
+// caller computed it already (vl_ok), else it is computed here.
 template <int MODE>
 __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long level, bool accumulate,
-                           bool cursors) {
+                           bool cursors, bool defer, Volt vl, bool vl_ok) {
     DevState *st = R.st;
     const int n = R.n_cells, n1 = n + 1;
     __shared__ long long sc_x[kThreads / 32];
     __shared__ unsigned long long sc_y[kThreads / 32];
     __shared__ double sc_d[kThreads / 32 + 1];
-    __shared__ double s_v_left;
-    long long *q = (long long *)smem;               // [n+1] net node charge
+    __shared__ Volt s_vl;
+    long long *q = (long long *)smem;               // [n+1] net node charge, then P_c
     double *rinv = (double *)(smem + 8 * (n + 1));   // [n] 1/(1+chi)
-    double *pp = rinv + n;                           // [n] kappa P_c (+ background)
+    double *pp = rinv + n;                           // [n] kappa P_c (+ background), then E_c
+    float2 *ew = (float2 *)pp;                       // [n] explicit: E_c as a double-word pair
     constexpr bool mc = ModeInfo<MODE>::mc;
     constexpr bool implicit = ModeInfo<MODE>::implicit;
-    if (threadIdx.x == 0) {
-        double v = 0.0;
-        if (!R.periodic) v = R.rf_volt * sin(2.0 * 3.14159265358979323846 * R.rf_freq * ((double)level * R.dt));
-        s_v_left = v;
-    }
+    if (threadIdx.x == 0) s_vl = vl_ok ? vl : electrode_volt(R, level);
+    const bool acc_now = accumulate && (implicit || !defer);
     // node charges, densities, susceptibility
     for (int g = threadIdx.x; g <= n; g += kThreads) {
         const unsigned long long ne = mc ? node_charge_s1(R, K, 0, g) : node_charge_s2(R, K, 0, g);
@@ -1235,7 +1303,7 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
         q[g] = (long long)(ni - ne);
         R.rho_q[0][g] = (long long)ne;
         R.rho_q[1][g] = (long long)ni;
-        if (accumulate) {
+        if (acc_now) {
             atomicAdd(&R.avg_ne[g], (double)(long long)ne);  // one writer per node: a plain sum
             atomicAdd(&R.avg_ni[g], (double)(long long)ni);
         }
@@ -1264,8 +1332,62 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
     long long P = runP;
     unsigned long long Cx = runC;
     block_exclusive_scan_pair(P, Cx, totP, totC, sc_x, sc_y);
-    const double qbar = R.periodic ? (double)totP / (double)n : 0.0;
-    double s1 = 0.0, s0 = 0.0;
+    if (implicit) {
+        // modified Poisson (direct implicit): FP64 with the susceptibility weights
+        double s1 = 0.0, s0 = 0.0;
+        for (int k = 0; k < per; ++k) {
+            const int c = c_begin + k;
+            if (cursors && c < n1) {
+                R.cursor[0][c] = (unsigned int)(Cx & 0xffffffffull);
+                R.cursor[1][c] = (unsigned int)(Cx >> 32);
+                Cx += K.c[0][c] | (K.c[1][c] << 32);
+            }
+            if (c < n) {
+                P += (R.periodic || c >= 1) ? q[c] : 0ll;
+                const double qbar = R.periodic ? (double)totP / (double)n : 0.0;
+                const double v = R.periodic ? R.kappa * ((double)P - (double)(c + 1) * qbar)
+                                            : R.kappa * (double)P + R.kappa_bg * (double)c;
+                pp[c] = v;
+                s1 += rinv[c] * v;
+                s0 += rinv[c];
+            }
+        }
+        s1 = block_sum_lean(s1, sc_d);
+        s0 = block_sum_lean(s0, sc_d);
+        const double v_left = s_vl.v;
+        const double d0 = R.periodic ? -s1 / s0 : (v_left / R.dx - s1) / s0;
+        double wsum = 0.0;
+        for (int k = 0; k < per; ++k) {
+            const int c = c_begin + k;
+            if (c < n) {
+                const double e = rinv[c] * (d0 + pp[c]);
+                pp[c] = e;  // now the face field
+                R.e_cc[c] = e;
+                if (accumulate) atomicAdd(&R.avg_e[c], e);
+                wsum += e * e;
+                R.e_gather[c + 1] = (float)e;
+            }
+        }
+        wsum = block_sum_lean(wsum, sc_d);  // includes the barrier that publishes pp[]
+        if (threadIdx.x == 0) {
+            st->field_energy = R.eps0_dx_half * wsum;
+            if (MODE == kImplicit1) st->field_energy_push = st->field_energy;
+            st->v_left = v_left;
+            if (accumulate) st->v_sum += v_left;
+            st->pending = 0u;  // everything of this field is done
+            R.e_gather[0] = R.periodic ? (float)pp[n - 1] : 0.0f;
+            R.e_gather[n + 1] = R.periodic ? (float)pp[0] : 0.0f;
+        }
+        __syncthreads();
+        return;
+    }
+    // Explicit schemes: E_c = base + kappa (P_c - mean P) + K2 (c - (n-1)/2), with
+    // base = V/(n dx), K2 = kappa_bg between electrodes (the constant d0 of the
+    // Gauss law fixed by sum_c E_c dx = V), base = 0, K2 = -kappa Q/n in the
+    // periodic box (zero-mean field, Q the total charge).  The sum of P_c is
+    // exact in two 64-bit halves; everything else is double-word FP32.
+    long long sum_hi = 0;
+    unsigned long long sum_lo = 0;
     for (int k = 0; k < per; ++k) {
         const int c = c_begin + k;
         if (cursors && c < n1) {
@@ -1275,59 +1397,120 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
         }
         if (c < n) {
             P += (R.periodic || c >= 1) ? q[c] : 0ll;
-            const double v = R.periodic ? R.kappa * ((double)P - (double)(c + 1) * qbar)
-                                        : R.kappa * (double)P + R.kappa_bg * (double)c;
-            pp[c] = v;
-            s1 += implicit ? rinv[c] * v : v;
-            if (implicit) s0 += rinv[c];
+            q[c] = P;  // this thread's own cells only
+            sum_hi += P >> 32;
+            sum_lo += (unsigned long long)P & 0xffffffffull;
         }
     }
-    s1 = block_sum_lean(s1, sc_d);
-    if (implicit) s0 = block_sum_lean(s0, sc_d);
-    else s0 = (double)n;
-    const double v_left = s_v_left;
-    const double d0 = R.periodic ? -s1 / s0 : (v_left / R.dx - s1) / s0;
+    long long tot_hi;
+    unsigned long long tot_lo;
+    block_exclusive_scan_pair(sum_hi, sum_lo, tot_hi, tot_lo, sc_x, sc_y);
+    const dw sum_p = dw_add(dw_mul(dw_from_i64(tot_hi), dw{4294967296.0f, 0.0f}), dw_from_i64((long long)tot_lo));
+    const dw mean_p = dw_mul(sum_p, dw_of(R.inv_n_ff));
+    const dw kap = dw_of(R.kappa_ff);
+    dw base, k2;
+    if (R.periodic) {
+        base = dw{0.0f, 0.0f};
+        k2 = dw_neg(dw_mul(dw_mul(kap, dw_from_i64(totP)), dw_of(R.inv_n_ff)));
+    } else {
+        base = dw_mul(dw{s_vl.hi, s_vl.lo}, dw_of(R.inv_ndx_ff));
+        k2 = dw_of(R.kbg_ff);
+    }
+    const float mid = 0.5f * (float)(n - 1);
     double wsum = 0.0;
     for (int k = 0; k < per; ++k) {
         const int c = c_begin + k;
         if (c < n) {
-            const double e = implicit ? rinv[c] * (d0 + pp[c]) : d0 + pp[c];
-            pp[c] = e;  // now the face field
-            R.e_cc[c] = e;
-            if (accumulate) atomicAdd(&R.avg_e[c], e);
-            wsum += e * e;
-            if (!mc) R.e_gather[c + 1] = (float)e;
+            const dw d = dw_add(dw_from_i64(q[c]), dw_neg(mean_p));
+            const dw e = dw_add(dw_add(base, dw_mul(kap, d)), dw_mul(k2, dw{(float)c - mid, 0.0f}));
+            ew[c] = make_float2(e.hi, e.lo);
+            if (!mc) R.e_gather[c + 1] = e.hi;
+            if (defer) {
+                R.e_hi[c] = e.hi;
+                R.e_lo[c] = e.lo;
+            } else {
+                const double ed = (double)e.hi + (double)e.lo;
+                R.e_cc[c] = ed;
+                if (accumulate) atomicAdd(&R.avg_e[c], ed);
+                wsum += ed * ed;
+            }
         }
     }
-    wsum = block_sum_lean(wsum, sc_d);  // includes the barrier that publishes pp[]
+    __syncthreads();  // publishes ew[]
     if (threadIdx.x == 0) {
-        if (MODE == kExplicitEC || MODE == kExplicitMC) st->field_energy_push = st->field_energy;
-        st->field_energy = R.eps0_dx_half * wsum;
-        if (MODE == kImplicit1) st->field_energy_push = st->field_energy;
-        st->v_left = v_left;
-        if (accumulate) st->v_sum += v_left;
         if (!mc) {
-            R.e_gather[0] = R.periodic ? (float)pp[n - 1] : 0.0f;
-            R.e_gather[n + 1] = R.periodic ? (float)pp[0] : 0.0f;
+            R.e_gather[0] = R.periodic ? ew[n - 1].x : 0.0f;
+            R.e_gather[n + 1] = R.periodic ? ew[0].x : 0.0f;
         }
+        st->v_left = s_vl.v;
     }
     if (mc) {
         // node field of the momentum-conserving scheme, (phi_{g-1} - phi_{g+1})/(2dx)
         // = (E_{g-1/2} + E_{g+1/2})/2, one-sided at the electrodes
         for (int g = threadIdx.x; g <= n; g += kThreads) {
-            double e;
-            if (R.periodic)
-                e = 0.5 * (pp[(g - 1 + n) % n] + pp[g % n]);
-            else if (g == 0)
-                e = pp[0];
-            else if (g == n)
-                e = pp[n - 1];
-            else
-                e = 0.5 * (pp[g - 1] + pp[g]);
-            R.e_gather[g] = (float)e;
+            float e;
+            if (R.periodic) {
+                const float2 a = ew[(g - 1 + n) % n], b = ew[g % n];
+                const dw h = dw_add(dw{a.x, a.y}, dw{b.x, b.y});
+                e = 0.5f * h.hi;
+            } else if (g == 0) {
+                e = ew[0].x;
+            } else if (g == n) {
+                e = ew[n - 1].x;
+            } else {
+                const float2 a = ew[g - 1], b = ew[g];
+                const dw h = dw_add(dw{a.x, a.y}, dw{b.x, b.y});
+                e = 0.5f * h.hi;
+            }
+            R.e_gather[g] = e;
+        }
+    }
+    if (defer) {
+        if (threadIdx.x == 0) {
+            // the energy of the field this launch pushed with was summed by the
+            // launch's deferred-work blocks into fe_acc
+            if (MODE == kExplicitEC || MODE == kExplicitMC) st->field_energy_push = R.eps0_dx_half * st->fe_acc;
+            st->fe_acc = 0.0;
+            st->pending = (accumulate ? 1u : 0u) | 2u;
+        }
+    } else {
+        wsum = block_sum_lean(wsum, sc_d);
+        if (threadIdx.x == 0) {
+            if (MODE == kExplicitEC || MODE == kExplicitMC) st->field_energy_push = st->field_energy;
+            st->field_energy = R.eps0_dx_half * wsum;
+            if (accumulate) st->v_sum += s_vl.v;
+            st->pending = 0u;  // everything of this field is done
         }
     }
     __syncthreads();
+}
+
+// The FP64 work a deferring tail left for nodes and cells of part `part` of
+// `parts`: the newest field to FP64, the running averages, the field energy
+// summed into st->fe_acc.  Every thread of the block calls this.
+__device__ void deferred_work(const Run &R, unsigned int pend, int part, int parts) {
+    __shared__ double sc_d[kThreads / 32 + 1];
+    const int n = R.n_cells;
+    const int chunk = (n + 1 + parts - 1) / parts;
+    const int lo = part * chunk, hi = min(lo + chunk, n + 1);
+    double fe = 0.0;
+    for (int k = lo + (int)threadIdx.x; k < hi; k += kThreads) {
+        if (k < n) {
+            const double e = (double)R.e_hi[k] + (double)R.e_lo[k];
+            R.e_cc[k] = e;
+            fe += e * e;
+            if (pend & 1u) atomicAdd(&R.avg_e[k], e);
+        }
+        if (pend & 1u) {
+            atomicAdd(&R.avg_ne[k], (double)R.rho_q[0][k]);
+            atomicAdd(&R.avg_ni[k], (double)R.rho_q[1][k]);
+        }
+    }
+    fe = block_sum_lean(fe, sc_d);
+    if (threadIdx.x == 0) {
+        if (fe != 0.0) atomicAdd(&R.st->fe_acc, fe);
+        if (part == 0 && (pend & 1u)) R.st->v_sum += R.st->v_left;
+    }
 }
 
 // Reset of the per-step accumulators.
@@ -1366,7 +1549,8 @@ __device__ void tail_cursors(const Run &R, Keys K) {
 }
 
 template <int MODE>
-__device__ __noinline__ void tail(const Run &R, unsigned char *smem, unsigned char *stage, bool diag) {
+__device__ __noinline__ void tail(const Run &R, unsigned char *smem, unsigned char *stage, bool diag, bool defer,
+                                  Volt vl, bool vl_ok) {
     DevState *st = R.st;
     const long long step = st->step;
     // Copy the per-key sums of both species into shared memory with one batch
@@ -1406,9 +1590,9 @@ __device__ __noinline__ void tail(const Run &R, unsigned char *smem, unsigned ch
         __syncthreads();
     }
     if (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit2) tail_births<MODE>(R, Ks, smem, diag);
-    if (MODE == kExplicitEC || MODE == kExplicitMC) tail_field<MODE>(R, Ks, smem, step + 1, true, true);
-    if (MODE == kImplicit1) tail_field<MODE>(R, Ks, smem, step + 1, true, false);
-    if (MODE == kDepositEC || MODE == kDepositMC) tail_field<MODE>(R, Ks, smem, step, false, true);
+    if (MODE == kExplicitEC || MODE == kExplicitMC) tail_field<MODE>(R, Ks, smem, step + 1, true, true, defer, vl, vl_ok);
+    if (MODE == kImplicit1) tail_field<MODE>(R, Ks, smem, step + 1, true, false, defer, vl, vl_ok);
+    if (MODE == kDepositEC || MODE == kDepositMC) tail_field<MODE>(R, Ks, smem, step, false, true, defer, vl, vl_ok);
     if (MODE == kImplicit2) tail_cursors(R, Ks);
     tail_reset(R);
     __syncthreads();
@@ -1468,6 +1652,7 @@ __device__ __forceinline__ void block_segment(long long ne, long long ni, int &S
 // that switch.
 // ---------------------------------------------------------------------------
 constexpr int kItemTiles = 1;
+constexpr int kDeferParts = 4;  // blocks that take the deferred FP64 work of the previous tail
 
 struct Stream {
     int *S;            // [kStages] species of the staged tile
@@ -1595,7 +1780,7 @@ __device__ void stream_flush(const Run &R, const SmemMain &sm, int S, bool diag,
 
 template <int MODE>
 __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, const Stream &ms, Producer &p,
-                             bool diag, long long step) {
+                             bool diag, long long step, Volt *vl) {
     using MI = ModeInfo<MODE>;
     DevState *st = R.st;
     const int par = st->parity;
@@ -1613,6 +1798,9 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
         p.next = (long long)atomicAdd(&st->next_item, 1u);
         for (int k = 0; k < kStages - 1; ++k)
             producer_issue(R, g, ms, p, par, (unsigned int)k, need_id, mode_fields, MI::implicit);
+        // the electrode voltage the tail will need, while the first copies fly
+        // (FP64 is slow here; only the last block's value is used)
+        *vl = electrode_volt(R, (MODE == kDepositEC || MODE == kDepositMC) ? step : step + 1);
     }
     __syncthreads();
     Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
@@ -1685,6 +1873,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     __shared__ int s_ms_S[kStages], s_ms_n[kStages];
     __shared__ long long s_ms_o[kStages];
     __shared__ Producer s_prod;
+    __shared__ Volt s_vl;
     using MI = ModeInfo<MODE>;
     DevState *st = R.st;
     const int n = R.n_cells;
@@ -1717,7 +1906,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     }
     if (threadIdx.x == 0) *sm.q.n = 0u;
     __syncthreads();
-    stream_block<MODE>(R, sm, g, ms, s_prod, diag, step);
+    // the FP64 work the previous tail left (a few blocks; the others start streaming)
+    {
+        const unsigned int pend = st->pending;
+        if (pend && blockIdx.x < kDeferParts) deferred_work(R, pend, (int)blockIdx.x, kDeferParts);
+    }
+    stream_block<MODE>(R, sm, g, ms, s_prod, diag, step, &s_vl);
     if (diag) {
         for (int k = threadIdx.x; k <= R.eedf_bins; k += kThreads)
             if (sm.eedf[k]) atomicAdd(&R.eedf[k], (unsigned long long)sm.eedf[k]);
@@ -1729,7 +1923,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    tail<MODE>(R, smem, smem_all, diag);
+    tail<MODE>(R, smem, smem_all, diag, true, s_vl, true);
+}
+
+// The work the last tail left, before the host reads diagnostics (one block).
+__global__ void __launch_bounds__(kThreads) k_finalize(Run R) {
+    const unsigned int pend = R.st->pending;
+    if (!pend) return;
+    deferred_work(R, pend, 0, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R.st->field_energy = R.eps0_dx_half * R.st->fe_acc;
+        R.st->pending = 0u;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1950,7 +2156,7 @@ __device__ void batch_item(const Run &R, unsigned char *smem, const Ring &g, int
     __syncthreads();
     if (s_last) {
         __threadfence();
-        tail<MODE>(R, smem, (unsigned char *)g.buf, diag);
+        tail<MODE>(R, smem, (unsigned char *)g.buf, diag, false, Volt{0.0, 0.0f, 0.0f}, false);
         loaded_run = -1;  // the tail reused the shared memory
         __syncthreads();
     }
@@ -2140,6 +2346,11 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
     if (e != cudaSuccess) return e;
     *grid = sms * (per > 0 ? per : 1);
     return cudaSuccess;
+}
+
+cudaError_t launch_finalize(const Run &r, cudaStream_t s) {
+    k_finalize<<<1, kThreads, 0, s>>>(r);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sort(const Run &r, int grid, cudaStream_t s) {
@@ -2586,7 +2797,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_adj_fwd(Run R, AdjFwd 
     __threadfence();
     Run Rt = R;
     Rt.e_gather = A.e_out;
-    tail_field<kDepositEC>(Rt, global_keys(R), smem, A.level, false, false);
+    tail_field<kDepositEC>(Rt, global_keys(R), smem, A.level, false, false, false, Volt{0.0, 0.0f, 0.0f}, false);
     tail_reset(R);
     __syncthreads();
     if (threadIdx.x == 0) R.st->blocks_done = 0u;

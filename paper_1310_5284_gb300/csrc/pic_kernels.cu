@@ -979,6 +979,35 @@ __device__ __forceinline__ unsigned long long node_charge_s2(const Run &R, const
     return q;
 }
 
+// The same from raw pointers and scalars (the tail's loops: nothing they
+// store can alias these inputs).
+__device__ __forceinline__ unsigned long long ksum_c(const unsigned long long *__restrict__ p, int n, bool periodic,
+                                                     int k) {
+    if (periodic) {
+        k = k < 0 ? k + n : (k >= n ? k - n : k);
+        return k == 0 ? p[0] + p[n] : p[k];
+    }
+    return (k >= 0 && k <= n) ? p[k] : 0ull;
+}
+
+__device__ __forceinline__ unsigned long long node_charge_s2_raw(const unsigned long long *__restrict__ C,
+                                                                 const unsigned long long *__restrict__ A,
+                                                                 const unsigned long long *__restrict__ B, int n,
+                                                                 bool periodic, int g) {
+    if (periodic && g == n) return 0ull;
+    const unsigned long long mb = ksum_c(B, n, periodic, g - 1);
+    const unsigned long long zc = ksum_c(C, n, periodic, g), za = ksum_c(A, n, periodic, g),
+                             zb = ksum_c(B, n, periodic, g);
+    const unsigned long long pc = ksum_c(C, n, periodic, g + 1), pa = ksum_c(A, n, periodic, g + 1),
+                             pb = ksum_c(B, n, periodic, g + 1);
+    unsigned long long q = (zc << 32) + (za << 17) - 2ull * zb + mb + (pc << 32) - (pa << 17) + pb;
+    if (!periodic) {
+        if (g == 0) q += (zc << 32) - (za << 17) + zb;  // ghost node -1
+        if (g == n) q += zb;                             // ghost node n+1
+    }
+    return q;
+}
+
 // S_1 node charge (momentum-conserving scheme), key = cell, value F:
 // node g gets (2^16 c_g - A_g) from cell g and A_{g-1} from cell g-1, times 2^17.
 __device__ __forceinline__ unsigned long long node_charge_s1(const Run &R, const Keys &K, int S, int g) {
@@ -1296,16 +1325,27 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
     constexpr bool implicit = ModeInfo<MODE>::implicit;
     if (threadIdx.x == 0) s_vl = vl_ok ? vl : electrode_volt(R, level);
     const bool acc_now = accumulate && (implicit || !defer);
-    // node charges, densities, susceptibility
-    for (int g = threadIdx.x; g <= n; g += kThreads) {
-        const unsigned long long ne = mc ? node_charge_s1(R, K, 0, g) : node_charge_s2(R, K, 0, g);
-        const unsigned long long ni = mc ? node_charge_s1(R, K, 1, g) : node_charge_s2(R, K, 1, g);
-        q[g] = (long long)(ni - ne);
-        R.rho_q[0][g] = (long long)ne;
-        R.rho_q[1][g] = (long long)ni;
-        if (acc_now) {
-            atomicAdd(&R.avg_ne[g], (double)(long long)ne);  // one writer per node: a plain sum
-            atomicAdd(&R.avg_ni[g], (double)(long long)ni);
+    // node charges, densities, susceptibility (pointers and scalars held in
+    // registers: the stores below cannot alias them)
+    {
+        const bool periodic = R.periodic;
+        const unsigned long long *__restrict__ c0 = K.c[0], *__restrict__ a0 = K.a[0], *__restrict__ b0 = K.b[0];
+        const unsigned long long *__restrict__ c1 = K.c[1], *__restrict__ a1 = K.a[1], *__restrict__ b1 = K.b[1];
+        long long *__restrict__ qs = q;
+        long long *__restrict__ rq0 = R.rho_q[0];
+        long long *__restrict__ rq1 = R.rho_q[1];
+        double *__restrict__ ane = R.avg_ne;
+        double *__restrict__ ani = R.avg_ni;
+        for (int g = threadIdx.x; g <= n; g += kThreads) {
+            const unsigned long long ne = mc ? node_charge_s1(R, K, 0, g) : node_charge_s2_raw(c0, a0, b0, n, periodic, g);
+            const unsigned long long ni = mc ? node_charge_s1(R, K, 1, g) : node_charge_s2_raw(c1, a1, b1, n, periodic, g);
+            qs[g] = (long long)(ni - ne);
+            rq0[g] = (long long)ne;
+            rq1[g] = (long long)ni;
+            if (acc_now) {
+                atomicAdd(&ane[g], (double)(long long)ne);  // one writer per node: a plain sum
+                atomicAdd(&ani[g], (double)(long long)ni);
+            }
         }
     }
     if (implicit) {

@@ -1064,11 +1064,19 @@ __device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag
     unsigned int *hist = (unsigned int *)smem;                       // [2048]
     unsigned int *rank = (unsigned int *)(R.births + R.births_cap);  // [births_cap]
     uint32_t *sorted = (uint32_t *)(rank + R.births_cap);            // [births_cap]
-    if (B <= 256u) {  // few births: compare directly
+    if (B <= 256u) {  // few births: compare directly, parent ids staged in shared memory
+        uint32_t *spid = (uint32_t *)smem;  // [256], padded to a multiple of 4 with the largest id
+        for (unsigned int b = threadIdx.x; b < 256u; b += kThreads) spid[b] = b < B ? R.births[b].pid : 0xffffffffu;
+        __syncthreads();
+        const uint4 *sp4 = (const uint4 *)spid;
+        const unsigned int nq = (B + 3u) / 4u;
         for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
-            const uint32_t p = R.births[b].pid;
+            const uint32_t p = spid[b];
             unsigned int r = 0;
-            for (unsigned int k = 0; k < B; ++k) r += R.births[k].pid < p ? 1u : 0u;
+            for (unsigned int k = 0; k < nq; ++k) {
+                const uint4 v = sp4[k];
+                r += (v.x < p ? 1u : 0u) + (v.y < p ? 1u : 0u) + (v.z < p ? 1u : 0u) + (v.w < p ? 1u : 0u);
+            }
             rank[b] = r;
         }
         __syncthreads();
@@ -1280,9 +1288,10 @@ __device__ __forceinline__ dw dw_neg(dw x) { return {-x.hi, -x.lo}; }
 // An int64 as a double-word: three pieces of at most 22 bits are exact in
 // FP32; their sum is rounded once to the double-word precision.
 __device__ __forceinline__ dw dw_from_i64(long long v) {
-    const float a = (float)(v >> 44) * 17592186044416.0f;        // * 2^44
-    const float b = (float)((v >> 22) & 0x3fffffll) * 4194304.0f; // * 2^22
-    const float c = (float)(v & 0x3fffffll);
+    // each piece goes through a 32-bit integer: the 64-bit conversion is slow here
+    const float a = (float)(int)(v >> 44) * 17592186044416.0f;        // * 2^44
+    const float b = (float)(int)((v >> 22) & 0x3fffffll) * 4194304.0f; // * 2^22
+    const float c = (float)(int)(v & 0x3fffffll);
     return dw_add(dw_two_sum(a, b), dw{c, 0.0f});
 }
 

@@ -403,6 +403,91 @@ def bench_adjoint(n_particles=1_000_000, n_cells=256, nsteps=200, checkpoint_eve
     return out
 
 
+def bench_paper_table(steps=200, warmup=20):
+    """The paper's Table 1 shape on GB300 (context, not a target): wall time per
+    RF period (2469 steps of 1.5e-11 s at 27 MHz) of the paper-shaped
+    discharge (4 cm, 200 V, 50 mTorr, 400 macro-particles per cell and
+    species) for 800/400/200/64 cells, EC explicit, MC explicit, EC implicit.
+    Steps timed with CUDA events, no L2 flush (the paper's runs are long)."""
+    import torch
+    from paper_1310_5284_gb300.sim import Sim
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    steps_per_period = round(1.0 / (27.0e6 * 1.5e-11))
+    rows = {}
+    for n in (800, 400, 200, 64):
+        row = {}
+        for scheme in ("ec_explicit", "mc_explicit", "ec_implicit"):
+            cfg = workloads.cfg_paper(n, scheme)
+            sim = Sim(cfg, device=dev)
+            sim.step(warmup)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(sim.stream)
+            sim.step(steps)
+            b.record(sim.stream)
+            torch.cuda.synchronize(dev)
+            ms = a.elapsed_time(b) / steps
+            row[scheme] = {"ms_per_step": ms, "s_per_rf_period": ms * 1e-3 * steps_per_period,
+                           "particles": sum(sim.diag()["count"])}
+            sim.close()
+        rows[str(n)] = row
+    return {"steps_per_rf_period": steps_per_period, "cells": rows,
+            "paper_seconds_per_period_ec_explicit_on_a_pc": {"800": 35.2, "400": 16.7, "200": 8.0, "64": 2.3}}
+
+
+def bench_self_heating(steps=2000):
+    """EC against momentum-conserving gather on the 512-cell grid at dx = 4
+    Debye lengths (Sec. 2): a collisionless periodic plasma of the production
+    density, 2.05 M electrons on a frozen ion background; relative change of
+    the total energy over the run for both schemes."""
+    import torch
+    from paper_1310_5284_gb300.sim import Sim
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    w = workloads.CFG_WIDE_EXPLICIT
+    out = {"steps": steps, "n_cells": w["n_cells"], "electrons": w["np_init"],
+           "dx_over_debye": 4.0, "omega_p_dt": 0.44}
+    for scheme in ("ec_explicit", "mc_explicit"):
+        cfg = workloads.cfg_periodic(n_cells=w["n_cells"], np_e=w["np_init"], n0=w["n0"], length=w["length"],
+                                     dt=w["dt"], te_ev=2.0, scheme=scheme, seed=21)
+        cfg["sort_period"] = 8
+        sim = Sim(cfg, device=dev)
+        sim.step(1)
+        e0 = sim.energy()
+        sim.step(steps)
+        torch.cuda.synchronize(dev)
+        out[scheme] = {"relative_energy_change": sim.energy() / e0 - 1.0}
+        sim.close()
+    return out
+
+
+def bench_implicit(steps=100, warmup=10):
+    """Throughput of the direct-implicit workload (128 cells, 1.02 M per
+    species, omega_p dt = 5): two launches per step plus the sort."""
+    import torch
+    from paper_1310_5284_gb300.sim import Sim
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    sim = Sim(dict(workloads.CFG_IMPLICIT), device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sim.step(warmup)
+    torch.cuda.synchronize(dev)
+    n0_ = sum(sim.diag()["count"])
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        evs[k][0].record(sim.stream)
+        sim.step(1)
+        evs[k][1].record(sim.stream)
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    n1_ = sum(sim.diag()["count"])
+    sim.close()
+    return {"workload": "ccp_128cells_implicit", "ms_per_step": ms,
+            "value": 0.5 * (n0_ + n1_) / (ms * 1e-3), "unit": UNIT}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,6 +500,7 @@ def main():
     ap.add_argument("--no-energy", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the paper table, self-heating and implicit lines")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -472,6 +558,10 @@ def main():
         line["adjoint"] = bench_adjoint()
     if world == 1 and not args.no_batched:
         line["batched"] = bench_batched()
+    if world == 1 and not args.no_extras:
+        line["implicit"] = bench_implicit()
+        line["self_heating"] = bench_self_heating()
+        line["paper_table1"] = bench_paper_table()
     print(json.dumps(line))
     return 0
 

@@ -455,6 +455,11 @@ __host__ __device__ inline size_t tail_smem_bytes(int n) {
     return 8 * (size_t)(n + 1) * 4 + 8 * 2048;
 }
 
+// The last block's tail reuses the whole dynamic shared memory (ring and grid
+// are idle by then): the staged per-key sums (6 x 8 bytes a key) first, the
+// tail's scratch after them.
+__host__ __device__ inline size_t tail_stage_bytes(int n) { return ((size_t)48 * (n + 1) + 255) & ~size_t(255); }
+
 __device__ SmemMain carve_main(unsigned char *base, int n, int bins) {
     SmemMain s;
     size_t o = 0;
@@ -521,7 +526,7 @@ __device__ __forceinline__ void eedf_sample(const Run &R, const SmemMain &sm, fl
 // Collide the queued particles, one per thread.  Their post-push position
 // and velocity were stored before the barrier that precedes this call.
 template <int S>
-__device__ __noinline__ void drain_collisions(const Run &R, const SmemMain &sm, const Species &sp, long long step,
+__device__ __noinline__ void drain_collisions(const Run &R, const SmemMain &sm, Species sp, long long step,
                                  bool diag, Tally &t) {
     __syncthreads();
     const unsigned int nq = min(*sm.q.n, (unsigned int)kQueue);
@@ -557,7 +562,7 @@ template <int MODE, int S>
 __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, const Species &sp,
                                              long long idx, int &cell, float &off, float &vx,
                                              float &abar, uint32_t id, bool diag, long long step,
-                                             Tally &t, uint32_t &a_out) {
+                                             Tally &t, float &kx, float &pw, uint32_t &a_out) {
     using MI = ModeInfo<MODE>;
     const int N = R.n_cells;
     if (MODE == kDepositEC) return deposit_key_s2(cell, off, a_out);
@@ -595,8 +600,8 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         if (diag) atomicAdd(&sm.heat[cell], R.qw[S] * e_field * 0.5f * (v_old + v_new));
         s = fmaf(v_new, R.dt_dx, off);
     }
-    t.kx += 0.5f * (v_old * v_old + v_new * v_new);
-    t.pw += R.qw[S] * e_field * 0.5f * (v_old + v_new);
+    kx += 0.5f * (v_old * v_old + v_new * v_new);  // kept in registers: t lives in memory
+    pw += R.qw[S] * e_field * 0.5f * (v_old + v_new);
     if (!(fabsf(s) < 1.0e6f)) s = (float)(2 * N + 2);
     renormalise(c, s);
     vx = v_new;
@@ -740,7 +745,6 @@ struct Ring {
 
 __host__ __device__ constexpr size_t ring_bytes() { return (size_t)kStages * kMaxFields * kTile * 4; }
 // The idle ring holds the tail's copy of the per-key sums (6 x 8 bytes a key).
-static_assert(ring_bytes() >= (size_t)48 * (kMaxCells + 1), "ring too small for the tail's key sums");
 
 __device__ __forceinline__ uint32_t *ring_field(const Ring &g, int stage, int f) {
     return g.buf + ((size_t)stage * kMaxFields + f) * kTile;
@@ -788,6 +792,7 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
     const bool need_id = MI::push && R.mcc;
     const int ntiles = (len + kTile - 1) / kTile;
     const unsigned int u0 = *g.uses;  // tiles this block issued before this segment
+    float kx = 0.0f, pw = 0.0f;
     if (threadIdx.x == 0)
         for (int tt = 0; tt < kStages - 1 && tt < ntiles; ++tt) ring_issue<MODE>(g, sp0, b, len, tt, u0 + tt, need_id);
     for (int tl = 0; tl < ntiles; ++tl) {
@@ -803,6 +808,8 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
             __syncthreads();
             if (threadIdx.x == 0) *g.uses = u0 + (unsigned int)min(ntiles, tl + kStages);
             __syncthreads();
+            t.kx += kx;
+            t.pw += pw;
             return;
         }
         const int base = tl * kTile;
@@ -829,7 +836,7 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
             key[q] = -1;
             if (cell[q] < 0) continue;  // beyond the segment, or a hole left by absorption
             key[q] = step_particle<MODE, S>(R, sm, sp, (long long)(i0 + q), cell[q], off[q], vx[q],
-                                            abar[q], id[q], diag, step, t, a[q]);
+                                            abar[q], id[q], diag, step, t, kx, pw, a[q]);
         }
         if (MI::push) {
             if (full) {
@@ -859,6 +866,8 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
         __syncthreads();
         if (*sm.q.n > 0u) drain_collisions<S>(R, sm, sp, step, diag, t);
     }
+    t.kx += kx;
+    t.pw += pw;
     __syncthreads();
     if (threadIdx.x == 0) *g.uses = u0 + (unsigned int)ntiles;
     __syncthreads();
@@ -1759,7 +1768,7 @@ __device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, cons
 template <int MODE, int S>
 __device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, const Ring &g, int stage,
                                             const Species &sp, long long o, int len, bool need_id, bool diag,
-                                            long long step, Tally &t) {
+                                            long long step, Tally &t, float &kx, float &pw) {
     constexpr int U = kUnroll;
     using MI = ModeInfo<MODE>;
     const int i0 = U * (int)threadIdx.x;  // place of the first particle in the tile
@@ -1784,7 +1793,7 @@ __device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, co
         key[q] = -1;
         if (cell[q] < 0) continue;  // beyond the tile, or a hole left by absorption
         key[q] = step_particle<MODE, S>(R, sm, sp, o + i0 + q, cell[q], off[q], vx[q], abar[q], id[q], diag,
-                                        step, t, a[q]);
+                                        step, t, kx, pw, a[q]);
     }
     if (MI::push) {
         const long long b = o + i0;
@@ -1853,6 +1862,7 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
     }
     __syncthreads();
     Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
+    float kx = 0.0f, pw = 0.0f;  // the per-particle sums stay in registers
     int cur = -1;
     long long added = 0;
     for (unsigned int u = 0;; ++u) {
@@ -1869,6 +1879,9 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
                     else
                         drain_collisions<1>(R, sm, sp[1], step, diag, t);
                 }
+                t.kx += kx;
+                t.pw += pw;
+                kx = pw = 0.0f;
                 stream_flush<MODE>(R, sm, cur, diag, t);
             }
             cur = S;
@@ -1884,9 +1897,9 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
             break;
         }
         if (S == 0)
-            stream_tile<MODE, 0>(R, sm, g, stage, sp[0], o, n, need_id, diag, step, t);
+            stream_tile<MODE, 0>(R, sm, g, stage, sp[0], o, n, need_id, diag, step, t, kx, pw);
         else
-            stream_tile<MODE, 1>(R, sm, g, stage, sp[1], o, n, need_id, diag, step, t);
+            stream_tile<MODE, 1>(R, sm, g, stage, sp[1], o, n, need_id, diag, step, t, kx, pw);
         added += n;
         __syncthreads();  // the stage is free again; the queue count is current
         if (MI::push && R.mcc && *sm.q.n >= (unsigned int)(kQueue / 2)) {
@@ -1906,6 +1919,8 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
                     drain_collisions<1>(R, sm, sp[1], step, diag, t);
             }
         }
+        t.kx += kx;
+        t.pw += pw;
         stream_flush<MODE>(R, sm, cur, diag, t);
     }
 }
@@ -1972,7 +1987,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    tail<MODE>(R, smem, smem_all, diag, true, s_vl, true);
+    tail<MODE>(R, smem_all + tail_stage_bytes(n), smem_all, diag, true, s_vl, true);
 }
 
 // The work the last tail left, before the host reads diagnostics (one block).
@@ -2205,7 +2220,8 @@ __device__ void batch_item(const Run &R, unsigned char *smem, const Ring &g, int
     __syncthreads();
     if (s_last) {
         __threadfence();
-        tail<MODE>(R, smem, (unsigned char *)g.buf, diag, false, Volt{0.0, 0.0f, 0.0f}, false);
+        tail<MODE>(R, (unsigned char *)g.buf + tail_stage_bytes(n), (unsigned char *)g.buf, diag, false,
+                   Volt{0.0, 0.0f, 0.0f}, false);
         loaded_run = -1;  // the tail reused the shared memory
         __syncthreads();
     }
@@ -2332,9 +2348,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ r
 // Launchers
 // ---------------------------------------------------------------------------
 int block_smem_bytes(const Run &r) {
-    const size_t a = main_smem_bytes(r.n_cells, r.eedf_bins);
-    const size_t b = tail_smem_bytes(r.n_cells);
-    return (int)(ring_bytes() + (a > b ? a : b));
+    const size_t a = ring_bytes() + main_smem_bytes(r.n_cells, r.eedf_bins);
+    const size_t b = tail_stage_bytes(r.n_cells) + tail_smem_bytes(r.n_cells);
+    return (int)(a > b ? a : b);
 }
 
 // The dynamic shared-memory limit of every mode is raised once by
@@ -2438,9 +2454,9 @@ cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c
 }
 
 size_t batch_smem_bytes(int max_cells, int max_bins, int nruns, int *table_off) {
-    const size_t a = main_smem_bytes(max_cells, max_bins);
-    const size_t b = tail_smem_bytes(max_cells);
-    const size_t off = (ring_bytes() + (a > b ? a : b) + 15) & ~size_t(15);
+    const size_t a = ring_bytes() + main_smem_bytes(max_cells, max_bins);
+    const size_t b = tail_stage_bytes(max_cells) + tail_smem_bytes(max_cells);
+    const size_t off = ((a > b ? a : b) + 15) & ~size_t(15);
     *table_off = (int)off;
     return off + 4 * (size_t)(2 * nruns + 1);
 }

@@ -116,9 +116,9 @@ struct Tally {
 // chosen by u * nu_max against the running sum of n_g sigma_k(eps) v.
 // Kept out of line: only the few selected particles take this path.
 // Returns true if the velocity changed.
-__device__ __noinline__ bool collide_electron(const Run &R, uint4 w, uint32_t id, long long step,
-                                              int cell, float off, float abar, float &vx, float &vy,
-                                              float &vz, Tally &t) {
+__device__ __forceinline__ bool collide_electron_body(const Run &R, uint4 w, uint32_t id, long long step,
+                                                     int cell, float off, float abar, float &vx, float &vy,
+                                                     float &vz, Tally &t) {
     const float v2 = vx * vx + vy * vy + vz * vz;
     const float g = sqrtf(v2);
     const float eps = R.half_m_over_e[0] * v2;
@@ -192,8 +192,8 @@ __device__ __noinline__ bool collide_electron(const Run &R, uint4 w, uint32_t id
 }
 
 // Ion charge exchange against a neutral sampled from the gas Maxwellian.
-__device__ __noinline__ bool collide_ion(const Run &R, uint4 w, uint32_t id, long long step,
-                                         float &vx, float &vy, float &vz, Tally &t) {
+__device__ __forceinline__ bool collide_ion_body(const Run &R, uint4 w, uint32_t id, long long step,
+                                                float &vx, float &vy, float &vz, Tally &t) {
     const uint4 w1 = draw(R, id, step, 1, kTagMcc, 1);
     float n1, n2, n3, n4;
     box_muller(u24(w.z), u24(w.w), n1, n2);
@@ -215,11 +215,50 @@ __device__ __noinline__ bool collide_ion(const Run &R, uint4 w, uint32_t id, lon
 }
 
 // A particle crossed an electrode (Sec. 3): tally its number and energy.
-__device__ __noinline__ void absorb(const Run &R, int S, int wall, float vx, float vy, float vz) {
+__device__ __forceinline__ void absorb_body(const Run &R, int S, int wall, float vx, float vy, float vz) {
     const float en = R.half_m_over_e[S] * (vx * vx + vy * vy + vz * vz);
     atomicAdd(&R.st->wall_count[S][wall], 1ull);
     atomicAdd(&R.st->wall_energy[S][wall], (double)en);
     atomicAdd(&R.st->absorbed_step[S], 1ull);
+}
+
+// Out-of-line copies for the batched kernel, whose register budget the
+// inlined bodies would exceed; the single-run kernel inlines the bodies
+// (out of line, the run's parameters would have to be copied to the stack).
+__device__ __noinline__ bool collide_electron(const Run &R, uint4 w, uint32_t id, long long step, int cell, float off,
+                                              float abar, float &vx, float &vy, float &vz, Tally &t) {
+    return collide_electron_body(R, w, id, step, cell, off, abar, vx, vy, vz, t);
+}
+
+__device__ __noinline__ bool collide_ion(const Run &R, uint4 w, uint32_t id, long long step, float &vx, float &vy,
+                                         float &vz, Tally &t) {
+    return collide_ion_body(R, w, id, step, vx, vy, vz, t);
+}
+
+__device__ __noinline__ void absorb(const Run &R, int S, int wall, float vx, float vy, float vz) {
+    absorb_body(R, S, wall, vx, vy, vz);
+}
+
+template <bool INL>
+__device__ __forceinline__ bool collide_e(const Run &R, uint4 w, uint32_t id, long long step, int cell, float off,
+                                          float abar, float &vx, float &vy, float &vz, Tally &t) {
+    if (INL) return collide_electron_body(R, w, id, step, cell, off, abar, vx, vy, vz, t);
+    return collide_electron(R, w, id, step, cell, off, abar, vx, vy, vz, t);
+}
+
+template <bool INL>
+__device__ __forceinline__ bool collide_i(const Run &R, uint4 w, uint32_t id, long long step, float &vx, float &vy,
+                                          float &vz, Tally &t) {
+    if (INL) return collide_ion_body(R, w, id, step, vx, vy, vz, t);
+    return collide_ion(R, w, id, step, vx, vy, vz, t);
+}
+
+template <bool INL>
+__device__ __forceinline__ void absorb_p(const Run &R, int S, int wall, float vx, float vy, float vz) {
+    if (INL)
+        absorb_body(R, S, wall, vx, vy, vz);
+    else
+        absorb(R, S, wall, vx, vy, vz);
 }
 
 // ---------------------------------------------------------------------------
@@ -525,9 +564,9 @@ __device__ __forceinline__ void eedf_sample(const Run &R, const SmemMain &sm, fl
 
 // Collide the queued particles, one per thread.  Their post-push position
 // and velocity were stored before the barrier that precedes this call.
-template <int S>
-__device__ __noinline__ void drain_collisions(const Run &R, const SmemMain &sm, Species sp, long long step,
-                                 bool diag, Tally &t) {
+template <int S, bool INL>
+__device__ __forceinline__ void drain_body(const Run &R, const SmemMain &sm, Species sp, long long step, bool diag,
+                                           Tally &t) {
     __syncthreads();
     const unsigned int nq = min(*sm.q.n, (unsigned int)kQueue);
     for (unsigned int q = threadIdx.x; q < nq; q += kThreads) {
@@ -538,9 +577,9 @@ __device__ __noinline__ void drain_collisions(const Run &R, const SmemMain &sm, 
         bool changed;
         if (S == 0) {
             const float abar = sp.abar ? sp.abar[idx] : 0.0f;
-            changed = collide_electron(R, w, id, step, sp.cell[idx], sp.off[idx], abar, vx, vy, vz, t);
+            changed = collide_e<INL>(R, w, id, step, sp.cell[idx], sp.off[idx], abar, vx, vy, vz, t);
         } else {
-            changed = collide_ion(R, w, id, step, vx, vy, vz, t);
+            changed = collide_i<INL>(R, w, id, step, vx, vy, vz, t);
         }
         if (changed) {
             sp.vx[idx] = vx;
@@ -554,11 +593,26 @@ __device__ __noinline__ void drain_collisions(const Run &R, const SmemMain &sm, 
     __syncthreads();
 }
 
+template <int S>
+__device__ __noinline__ void drain_collisions(const Run &R, const SmemMain &sm, Species sp, long long step,
+                                              bool diag, Tally &t) {
+    drain_body<S, false>(R, sm, sp, step, diag, t);
+}
+
+template <int S, bool INL>
+__device__ __forceinline__ void drain_q(const Run &R, const SmemMain &sm, Species sp, long long step, bool diag,
+                                        Tally &t) {
+    if (INL)
+        drain_body<S, true>(R, sm, sp, step, diag, t);
+    else
+        drain_collisions<S>(R, sm, sp, step, diag, t);
+}
+
 // ---------------------------------------------------------------------------
 // One particle of each mode.  Returns its deposit key (-1: none) and value a.
 // On return cell < 0 marks an absorbed particle.
 // ---------------------------------------------------------------------------
-template <int MODE, int S>
+template <int MODE, int S, bool INL>
 __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, const Species &sp,
                                              long long idx, int &cell, float &off, float &vx,
                                              float &abar, uint32_t id, bool diag, long long step,
@@ -610,7 +664,7 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
     if (R.periodic) {
         if (c < 0 || c >= N) c = ((c % N) + N) % N;
     } else if (c < 0 || c >= N) {
-        absorb(R, S, c < 0 ? 0 : 1, v_new, sp.vy[idx], sp.vz[idx]);
+        absorb_p<INL>(R, S, c < 0 ? 0 : 1, v_new, sp.vy[idx], sp.vz[idx]);
         cell = -1;
         return -1;
     }
@@ -630,8 +684,8 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
                 queued = true;
             } else {  // queue full: collide here
                 float vy = sp.vy[idx], vz = sp.vz[idx];
-                const bool changed = S == 0 ? collide_electron(R, w, id, step, c, s, abar, vx, vy, vz, t)
-                                            : collide_ion(R, w, id, step, vx, vy, vz, t);
+                const bool changed = S == 0 ? collide_e<INL>(R, w, id, step, c, s, abar, vx, vy, vz, t)
+                                            : collide_i<INL>(R, w, id, step, vx, vy, vz, t);
                 if (changed) {
                     sp.vy[idx] = vy;
                     sp.vz[idx] = vz;
@@ -835,7 +889,7 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
             a[q] = 0u;
             key[q] = -1;
             if (cell[q] < 0) continue;  // beyond the segment, or a hole left by absorption
-            key[q] = step_particle<MODE, S>(R, sm, sp, (long long)(i0 + q), cell[q], off[q], vx[q],
+            key[q] = step_particle<MODE, S, false>(R, sm, sp, (long long)(i0 + q), cell[q], off[q], vx[q],
                                             abar[q], id[q], diag, step, t, kx, pw, a[q]);
         }
         if (MI::push) {
@@ -1792,7 +1846,7 @@ __device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, co
         a[q] = 0u;
         key[q] = -1;
         if (cell[q] < 0) continue;  // beyond the tile, or a hole left by absorption
-        key[q] = step_particle<MODE, S>(R, sm, sp, o + i0 + q, cell[q], off[q], vx[q], abar[q], id[q], diag,
+        key[q] = step_particle<MODE, S, true>(R, sm, sp, o + i0 + q, cell[q], off[q], vx[q], abar[q], id[q], diag,
                                         step, t, kx, pw, a[q]);
     }
     if (MI::push) {
@@ -1875,9 +1929,9 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
             if (cur >= 0) {
                 if (MI::push && R.mcc && *sm.q.n > 0u) {
                     if (cur == 0)
-                        drain_collisions<0>(R, sm, sp[0], step, diag, t);
+                        drain_q<0, true>(R, sm, sp[0], step, diag, t);
                     else
-                        drain_collisions<1>(R, sm, sp[1], step, diag, t);
+                        drain_q<1, true>(R, sm, sp[1], step, diag, t);
                 }
                 t.kx += kx;
                 t.pw += pw;
@@ -1904,9 +1958,9 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
         __syncthreads();  // the stage is free again; the queue count is current
         if (MI::push && R.mcc && *sm.q.n >= (unsigned int)(kQueue / 2)) {
             if (S == 0)
-                drain_collisions<0>(R, sm, sp[0], step, diag, t);
+                drain_q<0, true>(R, sm, sp[0], step, diag, t);
             else
-                drain_collisions<1>(R, sm, sp[1], step, diag, t);
+                drain_q<1, true>(R, sm, sp[1], step, diag, t);
         }
     }
     if (cur >= 0) {
@@ -1914,9 +1968,9 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
             __syncthreads();
             if (*sm.q.n > 0u) {
                 if (cur == 0)
-                    drain_collisions<0>(R, sm, sp[0], step, diag, t);
+                    drain_q<0, true>(R, sm, sp[0], step, diag, t);
                 else
-                    drain_collisions<1>(R, sm, sp[1], step, diag, t);
+                    drain_q<1, true>(R, sm, sp[1], step, diag, t);
             }
         }
         t.kx += kx;

@@ -1661,8 +1661,8 @@ __device__ void tail_cursors(const Run &R, Keys K) {
 }
 
 template <int MODE>
-__device__ __noinline__ void tail(const Run &R, unsigned char *smem, unsigned char *stage, bool diag, bool defer,
-                                  Volt vl, bool vl_ok) {
+__device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, unsigned char *stage, bool diag,
+                                          bool defer, Volt vl, bool vl_ok) {
     DevState *st = R.st;
     const long long step = st->step;
     // Copy the per-key sums of both species into shared memory with one batch
@@ -1726,6 +1726,14 @@ __device__ __noinline__ void tail(const Run &R, unsigned char *smem, unsigned ch
         st->next_item = 0u;
         st->blocks_done = 0u;
     }
+}
+
+// Out of line for the batched kernel (register budget); the single-run
+// kernel inlines the body.
+template <int MODE>
+__device__ __noinline__ void tail(const Run &R, unsigned char *smem, unsigned char *stage, bool diag, bool defer,
+                                  Volt vl, bool vl_ok) {
+    tail_body<MODE>(R, smem, stage, diag, defer, vl, vl_ok);
 }
 
 // The block's share of the particles: blocks are split between the species in
@@ -2041,7 +2049,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    tail<MODE>(R, smem_all + tail_stage_bytes(n), smem_all, diag, true, s_vl, true);
+    tail_body<MODE>(R, smem_all + tail_stage_bytes(n), smem_all, diag, true, s_vl, true);
 }
 
 // The work the last tail left, before the host reads diagnostics (one block).

@@ -303,6 +303,28 @@ def test_collisions_counts_exact_and_births_ranked():
     compare_particles(gpu, orc, cfg, quantile=0.999, max_tol=1e-4)
 
 
+@pytest.mark.parametrize("n", [40_000, 120_000])
+def test_many_births_per_step_ranked_like_oracle(n):
+    """Hot electrons (40 eV) ionise about 2 % of themselves per step, so one
+    step records hundreds to thousands of births: the ranking by parent id
+    goes through the bucketed paths (in shared memory up to 1024 births, in
+    global memory beyond) and must still hand out the oracle's ids."""
+    cfg = dict(workloads.CFG_SMALL_CCP, np_init=n, sort_period=4, te_ev=40.0,
+               births_capacity=8192)
+    gpu = gpu_sim(cfg)
+    orc = oracle.Sim(cfg)
+    inject(gpu, orc, cfg, states_for(cfg, n, 91), step=500)
+    for _ in range(3):
+        gpu.step(1)
+        orc.step(1)
+    dg, do = gpu.diag(), orc.diag()
+    assert gpu.status() == 0
+    assert dg["births"] == do["births"] > 3 * (300 if n < 100_000 else 1100)
+    assert dg["coll"] == do["coll"]
+    assert dg["count"] == do["count"]
+    compare_particles(gpu, orc, cfg, quantile=0.999, max_tol=1e-4)
+
+
 def test_sorting_and_graph_replay_do_not_change_results():
     """Charge sums are integers and draws are keyed on (id, step), so the
     slot order (sorted or not) and graph replay leave every particle

@@ -1927,63 +1927,50 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
     float kx = 0.0f, pw = 0.0f;  // the per-particle sums stay in registers
     int cur = -1;
     long long added = 0;
+    bool gave_up = false;
     for (unsigned int u = 0;; ++u) {
         const int stage = (int)(u % kStages);
-        const int n = ms.n[stage];
-        if (n == 0) break;
-        const int S = ms.S[stage];
-        const long long o = ms.o[stage];
-        if (S != cur || added + n > kFlushEvery) {
-            if (cur >= 0) {
-                if (MI::push && R.mcc && *sm.q.n > 0u) {
-                    if (cur == 0)
-                        drain_q<0, true>(R, sm, sp[0], step, diag, t);
-                    else
-                        drain_q<1, true>(R, sm, sp[1], step, diag, t);
-                }
-                t.kx += kx;
-                t.pw += pw;
-                kx = pw = 0.0f;
-                stream_flush<MODE>(R, sm, cur, diag, t);
-            }
-            cur = S;
-            added = 0;
-        }
-        if (threadIdx.x == 0)
-            producer_issue(R, g, ms, p, par, u + kStages - 1, need_id, mode_fields, MI::implicit);
-        if (!mbar_wait(R, &g.bar[stage], (u / kStages) & 1u)) {
-            // give up, but not before the copies already issued have landed (bounded)
-            for (unsigned int w = u + 1; w < u + kStages; ++w)
-                if (ms.n[w % kStages] > 0) mbar_wait(R, &g.bar[w % kStages], (w / kStages) & 1u);
-            __syncthreads();
-            break;
-        }
-        if (S == 0)
-            stream_tile<MODE, 0>(R, sm, g, stage, sp[0], o, n, need_id, diag, step, t, kx, pw);
-        else
-            stream_tile<MODE, 1>(R, sm, g, stage, sp[1], o, n, need_id, diag, step, t, kx, pw);
-        added += n;
-        __syncthreads();  // the stage is free again; the queue count is current
-        if (MI::push && R.mcc && *sm.q.n >= (unsigned int)(kQueue / 2)) {
-            if (S == 0)
-                drain_q<0, true>(R, sm, sp[0], step, diag, t);
-            else
-                drain_q<1, true>(R, sm, sp[1], step, diag, t);
-        }
-    }
-    if (cur >= 0) {
-        if (MI::push && R.mcc) {
-            __syncthreads();
-            if (*sm.q.n > 0u) {
+        const int n = gave_up ? 0 : ms.n[stage];
+        const int S = n ? ms.S[stage] : cur;
+        const bool closing = cur >= 0 && (n == 0 || S != cur || added + n > kFlushEvery);
+        // the one place the queue is drained (keeps a single inlined copy of
+        // the collision code in the loop): when half full, or before the
+        // block's sums of this species are flushed
+        if (MI::push && R.mcc && cur >= 0) {
+            const unsigned int qn = *sm.q.n;
+            if (qn >= (unsigned int)(kQueue / 2) || (closing && qn > 0u)) {
                 if (cur == 0)
                     drain_q<0, true>(R, sm, sp[0], step, diag, t);
                 else
                     drain_q<1, true>(R, sm, sp[1], step, diag, t);
             }
         }
-        t.kx += kx;
-        t.pw += pw;
-        stream_flush<MODE>(R, sm, cur, diag, t);
+        if (closing) {
+            t.kx += kx;
+            t.pw += pw;
+            kx = pw = 0.0f;
+            stream_flush<MODE>(R, sm, cur, diag, t);
+            added = 0;
+        }
+        if (n == 0) break;
+        cur = S;
+        const long long o = ms.o[stage];
+        if (threadIdx.x == 0)
+            producer_issue(R, g, ms, p, par, u + kStages - 1, need_id, mode_fields, MI::implicit);
+        if (!mbar_wait(R, &g.bar[stage], (u / kStages) & 1u)) {
+            // give up, but not before the copies already issued have landed (bounded)
+            for (unsigned int w = u + 1; w < u + kStages; ++w)
+                if (ms.n[w % kStages] > 0) mbar_wait(R, &g.bar[w % kStages], (w / kStages) & 1u);
+            gave_up = true;
+        } else if (S == 0) {
+            stream_tile<MODE, 0>(R, sm, g, stage, sp[0], o, n, need_id, diag, step, t, kx, pw);
+        } else {
+            stream_tile<MODE, 1>(R, sm, g, stage, sp[1], o, n, need_id, diag, step, t, kx, pw);
+        }
+        added += n;
+        // the stage is free again and the queue count current; a thread whose
+        // wait gave up ends the stream for the whole block at the next pass
+        gave_up = __syncthreads_or(gave_up ? 1 : 0) != 0;
     }
 }
 

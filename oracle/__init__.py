@@ -28,7 +28,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-SCHEMES = {"ec_explicit": 0, "mc_explicit": 1, "ec_implicit": 2}
+SCHEMES = {"ec_explicit": 0, "mc_explicit": 1, "ec_implicit": 2, "mc_implicit": 3}
 SPECIES = {"e": 0, "i": 1}
 
 # conversion of a gas pressure to a density is part of the workload description

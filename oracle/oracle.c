@@ -466,7 +466,9 @@ void orc_sim_free(orc_sim *s)
 
 /* The momentum-conserving scheme always assigns in fixed point (S_1 weights
    of a 16-bit code are exact), the EC schemes when `quantized` is set. */
-static int uses_fixed(const orc_params *p) { return p->quantized || p->scheme == ORC_MC_EXPLICIT; }
+static int is_mc(const orc_params *p) { return p->scheme == ORC_MC_EXPLICIT || p->scheme == ORC_MC_IMPLICIT; }
+static int is_implicit(const orc_params *p) { return p->scheme == ORC_EC_IMPLICIT || p->scheme == ORC_MC_IMPLICIT; }
+static int uses_fixed(const orc_params *p) { return p->quantized || is_mc(p); }
 
 /* Charge density at the nodes [C/m^3] from the per-species assignments. */
 static void assemble_rho(orc_sim *s)
@@ -546,14 +548,14 @@ static void solve_field(orc_sim *s, const double *chi, int64_t level)
 
 static double gather(const orc_sim *s, double xi)
 {
-    if (s->p.scheme == ORC_MC_EXPLICIT) return orc_gather_mc(&s->p, s->e_node, xi);
+    if (is_mc(&s->p)) return orc_gather_mc(&s->p, s->e_node, xi);
     return orc_gather_ec(&s->p, s->e_cc, xi);
 }
 
 /* Charge assignment of the current positions, then the field at time level n. */
 static void deposit_and_solve(orc_sim *s, int64_t level)
 {
-    int use_s1 = s->p.scheme == ORC_MC_EXPLICIT;
+    int use_s1 = is_mc(&s->p);
     deposit_species(s, 0, use_s1);
     deposit_species(s, 1, use_s1);
     assemble_rho(s);
@@ -639,13 +641,13 @@ int orc_sim_set(orc_sim *s, int species, int64_t n, const double *xi, const doub
 void orc_sim_init_field(orc_sim *s, int set_abar)
 {
     deposit_and_solve(s, s->step);
-    if (s->p.scheme == ORC_EC_IMPLICIT && set_abar) {
+    if (is_implicit(&s->p) && set_abar) {
         /* Reading: the first step of the direct-implicit push takes
            abar^{-1} = a^0, the acceleration in the t = 0 field. */
         for (int k = 0; k < 2; ++k) {
             species_t *sp = &s->sp[k];
             for (int64_t i = 0; i < sp->n; ++i)
-                sp->abar[i] = s->d.q[k] / s->d.m[k] * orc_gather_ec(&s->p, s->e_cc, sp->xi[i]);
+                sp->abar[i] = s->d.q[k] / s->d.m[k] * gather(s, sp->xi[i]);
         }
     }
 }
@@ -910,7 +912,8 @@ static int step_explicit(orc_sim *s, int diag_step)
     return 0;
 }
 
-/* One direct-implicit step (Sec. 2 scheme (4)) in the D1 form of Cohen,
+/* One direct-implicit step (Sec. 2 schemes (4) and, with S_1 weighting and
+   node fields, (3)) in the D1 form of Cohen,
    Langdon & Friedman: predictor v~ = v^{n-1/2} + dt abar^{n-1}/2, x~ = x^n +
    dt v~; charge and susceptibility assigned at x~; modified Poisson equation
    for E^{n+1}; corrector a = (q/m) E^{n+1}(x~), x^{n+1} = x~ + dt^2 a / 2,
@@ -939,21 +942,34 @@ static int step_implicit(orc_sim *s, int diag_step)
             }
             xt[m++] = x;
         }
-        if (p->quantized)
-            orc_deposit_s2_fixed(p, m, xt, s->rho_q[k]);
-        else
-            orc_deposit_s2_fp64(p, m, xt, s->rho_f[k]);
-        deposit_chi_fixed(p, m, xt, s->chi_q[k]);
+        if (is_mc(p)) {
+            orc_deposit_s1_fixed(p, m, xt, s->rho_q[k]);
+        } else {
+            if (p->quantized)
+                orc_deposit_s2_fixed(p, m, xt, s->rho_q[k]);
+            else
+                orc_deposit_s2_fp64(p, m, xt, s->rho_f[k]);
+            deposit_chi_fixed(p, m, xt, s->chi_q[k]);
+        }
         free(xt);
     }
     assemble_rho(s);
-    /* chi_{c+1/2} = dt^2/2 sum_s (q_s^2 w / (m_s eps0 dx)) S_1-weighted count */
+    /* EC: chi_{c+1/2} = dt^2/2 sum_s (q_s^2 w / (m_s eps0 dx)) S_1-weighted count at
+       the cell centres.  MC (reading): the same density-like sum at the nodes with
+       the S_1 weights of the charge assignment, averaged onto each face. */
     for (int c = 0; c < n; ++c) {
         double chi = 0.0;
         for (int k = 0; k < 2; ++k) {
             double coef = 0.5 * dt * dt * s->d.q[k] * s->d.q[k] * s->d.weight /
                           (s->d.m[k] * EPS_0 * dx);
-            chi += coef * (double)s->chi_q[k][c] / 65536.0;
+            if (is_mc(p)) {
+                int64_t right = (p->periodic && c + 1 == n) ? 0 : c + 1;
+                double wl = (double)s->rho_q[k][c] / (double)TWO_POW_33;
+                double wr = (double)s->rho_q[k][right] / (double)TWO_POW_33;
+                chi += coef * 0.5 * (wl + wr);
+            } else {
+                chi += coef * (double)s->chi_q[k][c] / 65536.0;
+            }
         }
         s->chi[c] = chi;
     }
@@ -975,7 +991,7 @@ static int step_implicit(orc_sim *s, int diag_step)
                 if (x >= n) x -= n;
             }
             int inside = x >= 0.0 && x < n;
-            double e = inside ? orc_gather_ec(p, s->e_cc, x) : 0.0;
+            double e = inside ? gather(s, x) : 0.0;
             double a = qm * e;
             double v_new = vt + 0.5 * dt * a;
             kx += 0.5 * (v_old * v_old + v_new * v_new);
@@ -997,8 +1013,7 @@ int orc_sim_step(orc_sim *s, int64_t nsteps)
 {
     for (int64_t t = 0; t < nsteps; ++t) {
         int diag_step = s->p.diag_period > 0 && (s->step % s->p.diag_period) == 0;
-        int r = s->p.scheme == ORC_EC_IMPLICIT ? step_implicit(s, diag_step)
-                                               : step_explicit(s, diag_step);
+        int r = is_implicit(&s->p) ? step_implicit(s, diag_step) : step_explicit(s, diag_step);
         if (r) return r;
         accumulate_averages(s);
         if (diag_step) {

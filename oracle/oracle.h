@@ -21,13 +21,13 @@
 extern "C" {
 #endif
 
-enum { ORC_EC_EXPLICIT = 0, ORC_MC_EXPLICIT = 1, ORC_EC_IMPLICIT = 2 };
+enum { ORC_EC_EXPLICIT = 0, ORC_MC_EXPLICIT = 1, ORC_EC_IMPLICIT = 2, ORC_MC_IMPLICIT = 3 };
 
 typedef struct orc_params {
     /* grid and geometry (Sec. 3: planar gap between two electrodes) */
     int32_t n_cells;
     int32_t periodic;        /* 0: electrodes (x=0 driven, x=L grounded); 1: periodic box */
-    int32_t scheme;          /* ORC_EC_EXPLICIT / ORC_MC_EXPLICIT / ORC_EC_IMPLICIT (Sec. 2) */
+    int32_t scheme;          /* ORC_EC_EXPLICIT / ORC_MC_EXPLICIT / ORC_EC_IMPLICIT / ORC_MC_IMPLICIT (Sec. 2) */
     int32_t mcc;             /* 1: null-collision Monte Carlo on */
     int32_t ions_mobile;     /* 0: ions replaced by a frozen uniform background */
     int32_t quantized;       /* 1: 16-bit offset quantisation, int64 sums; 0: exact FP64 weights */

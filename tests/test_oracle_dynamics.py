@@ -178,11 +178,12 @@ def d1_roots(w):
     return np.roots([2.0 + w * w, -5.0, 4.0, -1.0])
 
 
+@pytest.mark.parametrize("scheme", ["ec_implicit", "mc_implicit"])
 @pytest.mark.parametrize("wdt", [0.5, 2.0, 5.0])
-def test_direct_implicit_cold_oscillation_follows_d1_recurrence(wdt):
+def test_direct_implicit_cold_oscillation_follows_d1_recurrence(wdt, scheme):
     n_cells, n0 = 128, 1e15
     dt = wdt / omega_p(n0)
-    sim, _ = cold_plasma(n_cells, 16, n0, dt, 0.02, scheme="ec_implicit")
+    sim, _ = cold_plasma(n_cells, 16, n0, dt, 0.02, scheme=scheme)
     steps = 24 if wdt > 1 else 60
     a = np.real(run_series(sim, n_cells, steps))[1:]
     # Prony: fit a_{n+3} = c2 a_{n+2} + c1 a_{n+1} + c0 a_n, keep points above round-off

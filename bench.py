@@ -55,7 +55,7 @@ def algorithmic_bytes_per_particle(scheme: str) -> dict:
     a particle selected for a collision also reads and writes vy, vz.  The
     implicit corrector reads cell, offset, vx, abar, id and writes cell,
     offset, vx, abar; its predictor reads cell, offset, vx, abar."""
-    if scheme == "ec_implicit":
+    if scheme in ("ec_implicit", "mc_implicit"):
         return {"per_particle": 36, "per_selected": 16, "predictor_per_particle": 16}
     return {"per_particle": 28, "per_selected": 16}
 
@@ -136,7 +136,7 @@ def run_gpu(args, wl_name, cfg, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     K, W = args.steps, args.warmup
     sort_period = int(cfg.get("sort_period", 16))
-    implicit = cfg["scheme"] == "ec_implicit"
+    implicit = cfg["scheme"] in ("ec_implicit", "mc_implicit")
 
     with torch.cuda.stream(stream):
         sim.step(W)
@@ -407,7 +407,7 @@ def bench_paper_table(steps=200, warmup=20):
     """The paper's Table 1 shape on GB300 (context, not a target): wall time per
     RF period (2469 steps of 1.5e-11 s at 27 MHz) of the paper-shaped
     discharge (4 cm, 200 V, 50 mTorr, 400 macro-particles per cell and
-    species) for 800/400/200/64 cells, EC explicit, MC explicit, EC implicit.
+    species) for 800/400/200/64 cells, all four schemes of Sec. 2.
     Steps timed with CUDA events, no L2 flush (the paper's runs are long)."""
     import torch
     from paper_1310_5284_gb300.sim import Sim
@@ -417,7 +417,7 @@ def bench_paper_table(steps=200, warmup=20):
     rows = {}
     for n in (800, 400, 200, 64):
         row = {}
-        for scheme in ("ec_explicit", "mc_explicit", "ec_implicit"):
+        for scheme in ("ec_explicit", "mc_explicit", "ec_implicit", "mc_implicit"):
             cfg = workloads.cfg_paper(n, scheme)
             sim = Sim(cfg, device=dev)
             sim.step(warmup)

@@ -59,10 +59,13 @@ extern "C" {
 #define PIC_STATUS_TIMEOUT 0x4u     /* a bounded wait ran out (batched driver) */
 
 /* Schemes (Sec. 2): (2) EC explicit, (1) momentum-conserving explicit, (4) EC
-   direct implicit. */
+   direct implicit, (3) momentum-conserving direct implicit (S_1 charge and
+   susceptibility, the susceptibility's node sums averaged onto the faces of
+   the modified Poisson equation, force from the node field). */
 #define PIC_EC_EXPLICIT 0
 #define PIC_MC_EXPLICIT 1
 #define PIC_EC_IMPLICIT 2
+#define PIC_MC_IMPLICIT 3
 
 /* Boundaries: electrodes at x=0 (driven, V(t) = rf_volt sin(2 pi rf_freq t))
    and x=L (grounded), both absorbing (Sec. 3); or a periodic box. */
@@ -70,7 +73,7 @@ extern "C" {
 #define PIC_BC_PERIODIC 1
 
 typedef struct pic_config {
-    int32_t scheme;          /* PIC_EC_EXPLICIT / PIC_MC_EXPLICIT / PIC_EC_IMPLICIT */
+    int32_t scheme;          /* PIC_EC_EXPLICIT / PIC_MC_EXPLICIT / PIC_EC_IMPLICIT / PIC_MC_IMPLICIT */
     int32_t boundary;        /* PIC_BC_ELECTRODES / PIC_BC_PERIODIC */
     int32_t n_cells;         /* 2 .. 1024 */
     int32_t mcc;             /* 1: null-collision Monte Carlo on */
@@ -270,7 +273,7 @@ void pic_batch_free(pic_batch *b);
    offset in [0,1)); entries with a cell outside [0, n_cells) are skipped.
    rho_q_out: device array of n_cells+1 int64 receiving the node charge in
    units of 2^-33 macro-particle charges, quadratic S_2 weights (EC schemes)
-   or linear S_1 (PIC_MC_EXPLICIT), electrodes or periodic as `boundary` -
+   or linear S_1 (PIC_MC_EXPLICIT, PIC_MC_IMPLICIT), electrodes or periodic as `boundary` -
    the same numbers pic_grids() returns for a run holding these particles.
    The per-node sums live in a static device array of the library sized for
    n_cells <= 1024 (about 25 KB on every GPU that loads the library, held

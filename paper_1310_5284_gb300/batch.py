@@ -31,7 +31,7 @@ def discharge_from_spec(spec: dict, te_ev: float = 2.0) -> dict:
     wp = math.sqrt(n0 * _E * _E / (_EPS0 * _ME))
     vth = math.sqrt(_E * te_ev / _ME)
     wpdt = c.pop("omega_p_dt", None)
-    if c.get("scheme", "ec_explicit") == "ec_implicit":
+    if c.get("scheme", "ec_explicit") in ("ec_implicit", "mc_implicit"):
         dt = (wpdt if wpdt is not None else 2.0) / wp
     else:
         dt = min(0.2 / wp, 0.25 * dx / vth)

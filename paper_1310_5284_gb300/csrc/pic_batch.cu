@@ -192,7 +192,7 @@ int pic_batch_init(const pic_config *cfgs, int32_t nruns, const pic_buffers *buf
     int sort_period = 0, max_cells = 2, max_bins = 1, big = 0;
     for (int k = 0; k < nruns; ++k) {
         derive_run(cfgs[k], BL.L[k], b->arena + BL.run_off[k], b->runs[k]);
-        b->any_implicit |= cfgs[k].scheme == PIC_EC_IMPLICIT;
+        b->any_implicit |= implicit_scheme(cfgs[k]);
         if (cfgs[k].sort_period > 0 && (sort_period == 0 || cfgs[k].sort_period < sort_period))
             sort_period = cfgs[k].sort_period;
         if (cfgs[k].n_cells > max_cells) {

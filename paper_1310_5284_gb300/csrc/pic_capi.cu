@@ -42,7 +42,7 @@ Layout make_layout(const pic_config &c) {
         for (int s = 0; s < 2; ++s) {
             const size_t cap = (size_t)c.capacity[s];
             for (int f = 0; f < 6; ++f) L.sp[p][s][f] = take(4 * cap);
-            L.sp[p][s][6] = c.scheme == PIC_EC_IMPLICIT ? take(4 * cap) : 0;
+            L.sp[p][s][6] = implicit_scheme(c) ? take(4 * cap) : 0;
         }
     for (int s = 0; s < 2; ++s) {
         L.acc_cnt[s] = take(8 * n1);
@@ -96,7 +96,7 @@ int fail(int code, const char *fmt, ...) {
 
 int validate(const pic_config *c) {
     if (!c) return fail(PIC_EINVAL, "config is NULL");
-    if (c->scheme < 0 || c->scheme > 2) return fail(PIC_EINVAL, "unknown scheme %d", c->scheme);
+    if (c->scheme < 0 || c->scheme > 3) return fail(PIC_EINVAL, "unknown scheme %d", c->scheme);
     if (c->boundary != PIC_BC_ELECTRODES && c->boundary != PIC_BC_PERIODIC)
         return fail(PIC_EINVAL, "unknown boundary %d", c->boundary);
     if (c->n_cells < 2 || c->n_cells > kMaxCells)
@@ -125,7 +125,7 @@ int validate(const pic_config *c) {
     if (c->sort_period < 0 || c->diag_period < 0) return fail(PIC_EINVAL, "negative period");
     // Eq. (1): the leapfrog push is stable only for omega_p dt < 2.
     const double wp = std::sqrt(c->n0 * kE * kE / (kEps0 * kMe));
-    if (c->strict && c->scheme != PIC_EC_IMPLICIT && !(wp * c->dt < 2.0))
+    if (c->strict && !implicit_scheme(*c) && !(wp * c->dt < 2.0))
         return fail(PIC_EUNSTABLE, "omega_p dt = %.3f >= 2 violates the leapfrog limit of Eq. (1)",
                     wp * c->dt);
     return PIC_OK;
@@ -272,7 +272,7 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
             sp.vy = (float *)(A + L.sp[p][s][3]);
             sp.vz = (float *)(A + L.sp[p][s][4]);
             sp.id = (uint32_t *)(A + L.sp[p][s][5]);
-            sp.abar = c.scheme == PIC_EC_IMPLICIT ? (float *)(A + L.sp[p][s][6]) : nullptr;
+            sp.abar = implicit_scheme(c) ? (float *)(A + L.sp[p][s][6]) : nullptr;
         }
     for (int s = 0; s < 2; ++s) {
         R.acc_cnt[s] = (unsigned long long *)(A + L.acc_cnt[s]);
@@ -296,14 +296,18 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
 }
 
 Mode push_mode(const pic_config &c) { return c.scheme == PIC_MC_EXPLICIT ? kExplicitMC : kExplicitEC; }
-Mode deposit_mode(const pic_config &c) { return c.scheme == PIC_MC_EXPLICIT ? kDepositMC : kDepositEC; }
+Mode deposit_mode(const pic_config &c) {
+    return (c.scheme == PIC_MC_EXPLICIT || c.scheme == PIC_MC_IMPLICIT) ? kDepositMC : kDepositEC;
+}
+Mode pass1_mode(const pic_config &c) { return c.scheme == PIC_MC_IMPLICIT ? kImplicit1MC : kImplicit1; }
+Mode pass2_mode(const pic_config &c) { return c.scheme == PIC_MC_IMPLICIT ? kImplicit2MC : kImplicit2; }
 
 // Enqueue one step (and the sort that closes a sort cycle) on stream s.
 int enqueue_step(pic_handle *h, long long step_index, cudaStream_t s) {
     const pic_config &c = h->cfg;
-    if (c.scheme == PIC_EC_IMPLICIT) {
-        CK(h, launch_particles(h->run, kImplicit1, h->grid_push, s));
-        CK(h, launch_particles(h->run, kImplicit2, h->grid_push, s));
+    if (implicit_scheme(c)) {
+        CK(h, launch_particles(h->run, pass1_mode(c), h->grid_push, s));
+        CK(h, launch_particles(h->run, pass2_mode(c), h->grid_push, s));
     } else {
         CK(h, launch_particles(h->run, push_mode(c), h->grid_push, s));
     }
@@ -409,7 +413,7 @@ int init_run_state(const pic_config &c, const Run &R, unsigned char *arena, size
     // t = 0 charge assignment and field, abar = a^0 for the implicit scheme
     CKE(launch_particles(R, deposit_mode(c), grid, s));
     CKE(launch_finalize(R, s));  // FP64 copy and energy of the t = 0 field
-    if (c.scheme == PIC_EC_IMPLICIT) CKE(launch_set_abar(R, s));
+    if (implicit_scheme(c)) CKE(launch_set_abar(R, s));
     // the load is in random order: sort it once so that every block streams
     // particles of a few adjacent cells from the first step on
     CKE(launch_sort(R, grid, s));
@@ -511,10 +515,10 @@ int pic_init(const pic_config *cfg, const pic_buffers *bufs, void *stream, pic_h
         cuda_fail(h, cudaGetLastError(), "sort occupancy");
         return bail(PIC_ECUDA);
     }
-    if (cfg->scheme == PIC_EC_IMPLICIT) {
+    if (implicit_scheme(*cfg)) {
         int g1 = 0, g2 = 0;
-        occupancy_grid(h->run, kImplicit1, &g1);
-        occupancy_grid(h->run, kImplicit2, &g2);
+        occupancy_grid(h->run, pass1_mode(*cfg), &g1);
+        occupancy_grid(h->run, pass2_mode(*cfg), &g2);
         h->grid_push = g1 < g2 ? g1 : g2;
     }
     r = init_run_state(*cfg, h->run, h->arena, L.total, h->grid_push, h->stream, &h->err);
@@ -526,7 +530,7 @@ int pic_init(const pic_config *cfg, const pic_buffers *bufs, void *stream, pic_h
 int pic_init_field(pic_handle *h, int set_abar) {
     if (!h) return fail(PIC_EINVAL, "handle is NULL");
     CK(h, launch_particles(h->run, deposit_mode(h->cfg), h->grid_push, h->stream));
-    if (h->cfg.scheme == PIC_EC_IMPLICIT && set_abar) CK(h, launch_set_abar(h->run, h->stream));
+    if (implicit_scheme(h->cfg) && set_abar) CK(h, launch_set_abar(h->run, h->stream));
     return PIC_OK;
 }
 

@@ -38,6 +38,8 @@ enum Mode : int {
     kDepositMC = 3,
     kImplicit1 = 4,    // direct implicit pass 1: predictor, deposit rho~ and chi
     kImplicit2 = 5,    // direct implicit pass 2: corrector, absorb, collide
+    kImplicit1MC = 6,  // the same two passes with S_1 weighting and node fields
+    kImplicit2MC = 7,
 };
 
 // One species' particle arrays (structure of arrays).
@@ -191,6 +193,9 @@ struct AdjRev {
 };
 
 // ---- shared host helpers (pic_capi.cu) ----
+inline bool implicit_scheme(const pic_config &c) {
+    return c.scheme == PIC_EC_IMPLICIT || c.scheme == PIC_MC_IMPLICIT;
+}
 Layout make_run_layout(const pic_config &c);
 int validate_run_config(const pic_config *c);  // PIC_* code; message via pic_last_error
 void derive_run(const pic_config &c, const Layout &L, unsigned char *arena, Run &R);

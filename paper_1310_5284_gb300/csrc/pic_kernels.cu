@@ -526,11 +526,14 @@ __device__ SmemMain carve_main(unsigned char *base, int n, int bins) {
 
 template <int MODE>
 struct ModeInfo {
-    static constexpr bool push = !(MODE == kDepositEC || MODE == kDepositMC || MODE == kImplicit1);
-    static constexpr bool needs_field = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit2);
-    static constexpr bool implicit = (MODE == kImplicit1 || MODE == kImplicit2);
-    static constexpr bool count_only = (MODE == kImplicit2);
-    static constexpr bool mc = (MODE == kExplicitMC || MODE == kDepositMC);
+    static constexpr bool pass1 = (MODE == kImplicit1 || MODE == kImplicit1MC);
+    static constexpr bool pass2 = (MODE == kImplicit2 || MODE == kImplicit2MC);
+    static constexpr bool push = !(MODE == kDepositEC || MODE == kDepositMC || pass1);
+    static constexpr bool needs_field = (MODE == kExplicitEC || MODE == kExplicitMC || pass2);
+    static constexpr bool implicit = pass1 || pass2;
+    static constexpr bool count_only = pass2;
+    static constexpr bool mc = (MODE == kExplicitMC || MODE == kDepositMC || MODE == kImplicit1MC ||
+                                MODE == kImplicit2MC);
     static constexpr bool loads_v = !(MODE == kDepositEC || MODE == kDepositMC);
 };
 
@@ -636,12 +639,13 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         } else if (c < 0 || c >= N) {
             inside = false;
         }
-        if (MODE == kImplicit1) {
+        if (MI::pass1) {
             if (!inside) return -1;  // Reading: nothing assigned beyond an electrode
-            return deposit_key_s2(c, s, a_out);
+            return MI::mc ? deposit_key_s1(c, s, a_out) : deposit_key_s2(c, s, a_out);
         }
-        // corrector with E^{n+1} at x~
-        e_field = inside ? gather_ec(sm.e, c, s) : 0.0f;
+        // corrector with E^{n+1} at x~ (S_1 from the cell-centred field, or
+        // linear from the node field of the momentum-conserving scheme)
+        e_field = !inside ? 0.0f : (MI::mc ? (1.0f - s) * sm.e[c] + s * sm.e[c + 1] : gather_ec(sm.e, c, s));
         const float acc = R.qm[S] * e_field;
         v_new = fmaf(R.half_dt, acc, vt);
         if (diag && inside) atomicAdd(&sm.heat[c], R.qw[S] * e_field * 0.5f * (v_old + v_new));
@@ -1204,16 +1208,16 @@ __device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag
         si.vy[ji] = bb.vi[1];
         si.vz[ji] = bb.vi[2];
         si.id[ji] = id_i + r;
-        if (R.scheme == 2) {
+        if (ModeInfo<MODE>::implicit) {
             se.abar[je] = bb.abar_e;
             si.abar[ji] = bb.abar_e * R.abar_ion_over_e;
         }
         uint32_t a;
-        const int key = MODE == kExplicitMC ? deposit_key_s1(bb.cell, bb.off, a)
-                                            : deposit_key_s2(bb.cell, bb.off, a);
+        const int key = ModeInfo<MODE>::mc ? deposit_key_s1(bb.cell, bb.off, a)
+                                           : deposit_key_s2(bb.cell, bb.off, a);
         for (int S = 0; S < 2; ++S) {
             atomicAdd(&K.c[S][key], 1ull);
-            if (MODE != kImplicit2) {
+            if (!ModeInfo<MODE>::count_only) {
                 atomicAdd(&K.a[S][key], (unsigned long long)a);
                 atomicAdd(&K.b[S][key], (unsigned long long)a * a);
             }
@@ -1422,7 +1426,16 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
     }
     if (implicit) {
         for (int c = threadIdx.x; c < n; c += kThreads) {
-            const double chi = R.chi_coef[0] * (double)chi_count(R, K, 0, c) + R.chi_coef[1] * (double)chi_count(R, K, 1, c);
+            double chi;
+            if (mc) {
+                // Reading: the node sums of the S_1 weights (the node charges,
+                // 2^-33 units) averaged onto the face between them
+                const int r = (R.periodic && c + 1 == n) ? 0 : c + 1;
+                chi = ldexp(R.chi_coef[0], -18) * (double)(node_charge_s1(R, K, 0, c) + node_charge_s1(R, K, 0, r)) +
+                      ldexp(R.chi_coef[1], -18) * (double)(node_charge_s1(R, K, 1, c) + node_charge_s1(R, K, 1, r));
+            } else {
+                chi = R.chi_coef[0] * (double)chi_count(R, K, 0, c) + R.chi_coef[1] * (double)chi_count(R, K, 1, c);
+            }
             R.chi[c] = chi;
             rinv[c] = 1.0 / (1.0 + chi);
         }
@@ -1477,18 +1490,31 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
                 R.e_cc[c] = e;
                 if (accumulate) atomicAdd(&R.avg_e[c], e);
                 wsum += e * e;
-                R.e_gather[c + 1] = (float)e;
+                if (!mc) R.e_gather[c + 1] = (float)e;
             }
         }
         wsum = block_sum_lean(wsum, sc_d);  // includes the barrier that publishes pp[]
         if (threadIdx.x == 0) {
             st->field_energy = R.eps0_dx_half * wsum;
-            if (MODE == kImplicit1) st->field_energy_push = st->field_energy;
+            if (ModeInfo<MODE>::pass1) st->field_energy_push = st->field_energy;
             st->v_left = v_left;
             if (accumulate) st->v_sum += v_left;
             st->pending = 0u;  // everything of this field is done
-            R.e_gather[0] = R.periodic ? (float)pp[n - 1] : 0.0f;
-            R.e_gather[n + 1] = R.periodic ? (float)pp[0] : 0.0f;
+            if (!mc) {
+                R.e_gather[0] = R.periodic ? (float)pp[n - 1] : 0.0f;
+                R.e_gather[n + 1] = R.periodic ? (float)pp[0] : 0.0f;
+            }
+        }
+        if (mc) {
+            // node field (E_{g-1/2} + E_{g+1/2})/2, one-sided at the electrodes
+            for (int g = threadIdx.x; g <= n; g += kThreads) {
+                double e;
+                if (R.periodic)
+                    e = 0.5 * (pp[(g - 1 + n) % n] + pp[g % n]);
+                else
+                    e = g == 0 ? pp[0] : (g == n ? pp[n - 1] : 0.5 * (pp[g - 1] + pp[g]));
+                R.e_gather[g] = (float)e;
+            }
         }
         __syncthreads();
         return;
@@ -1701,11 +1727,11 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
         }
         __syncthreads();
     }
-    if (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kImplicit2) tail_births<MODE>(R, Ks, smem, diag);
+    if (MODE == kExplicitEC || MODE == kExplicitMC || ModeInfo<MODE>::pass2) tail_births<MODE>(R, Ks, smem, diag);
     if (MODE == kExplicitEC || MODE == kExplicitMC) tail_field<MODE>(R, Ks, smem, step + 1, true, true, defer, vl, vl_ok);
-    if (MODE == kImplicit1) tail_field<MODE>(R, Ks, smem, step + 1, true, false, defer, vl, vl_ok);
+    if (ModeInfo<MODE>::pass1) tail_field<MODE>(R, Ks, smem, step + 1, true, false, defer, vl, vl_ok);
     if (MODE == kDepositEC || MODE == kDepositMC) tail_field<MODE>(R, Ks, smem, step, false, true, defer, vl, vl_ok);
-    if (MODE == kImplicit2) tail_cursors(R, Ks);
+    if (ModeInfo<MODE>::pass2) tail_cursors(R, Ks);
     tail_reset(R);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -2061,8 +2087,8 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Run R) {
 // consecutive positions from one atomic).
 __device__ void sort_chunk(const Run &R, int par, int S, long long b, long long e) {
     constexpr int V = 4;  // particles per thread in flight: all their loads are issued first
-    const bool mc = R.scheme == 1;
-    const bool implicit = R.scheme == 2;
+    const bool mc = R.scheme == 1 || R.scheme == 3;
+    const bool implicit = R.scheme >= 2;
     const int lane = threadIdx.x & 31;
     const Species src = R.buf[par][S], dst = R.buf[par ^ 1][S];
     for (long long base = b; base < e; base += (long long)kThreads * V) {
@@ -2152,7 +2178,7 @@ __global__ void k_load(Run R, int S, long long count, float vth) {
         sp.vy[i] = vth * n2;
         sp.vz[i] = vth * n3;
         sp.id[i] = (uint32_t)i;
-        if (R.scheme == 2) sp.abar[i] = 0.0f;
+        if (R.scheme >= 2) sp.abar[i] = 0.0f;
     }
 }
 
@@ -2168,9 +2194,14 @@ __global__ void k_set_abar(Run R) {
             const int cell = sp.cell[i];
             if (cell < 0) continue;
             const float off = sp.off[i];
-            const int j = cell + (off >= 0.5f ? 1 : 0);
-            const float w1 = off >= 0.5f ? off - 0.5f : off + 0.5f;
-            const float e = (1.0f - w1) * R.e_gather[j] + w1 * R.e_gather[j + 1];
+            float e;
+            if (R.scheme == 3) {  // node field, linear weights
+                e = (1.0f - off) * R.e_gather[cell] + off * R.e_gather[cell + 1];
+            } else {
+                const int j = cell + (off >= 0.5f ? 1 : 0);
+                const float w1 = off >= 0.5f ? off - 0.5f : off + 0.5f;
+                e = (1.0f - w1) * R.e_gather[j] + w1 * R.e_gather[j + 1];
+            }
             sp.abar[i] = R.qm[S] * e;
         }
     }
@@ -2322,7 +2353,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ r
         const int j = j0 + q;
         if (j >= nj) break;
         const Run &R = runs[j >> 1];
-        const bool part = PHASE == 1 ? R.scheme == 2 : true;
+        const bool part = PHASE == 1 ? R.scheme >= 2 : true;
         const int S = j & 1;
         const long long nn = (S == 1 && !R.ions_mobile) ? 0 : work[j];
         unsigned int it = part ? (unsigned int)((nn + chunk - 1) / chunk) : 0u;
@@ -2369,13 +2400,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ r
         if (PHASE == 2) {
             batch_sort_item(R, S, b, e, items_r);
         } else if (PHASE == 1) {
-            batch_item<kImplicit2>(R, smem, g, S, b, e, items_r, r, loaded_run);
+            if (R.scheme == 3)
+                batch_item<kImplicit2MC>(R, smem, g, S, b, e, items_r, r, loaded_run);
+            else
+                batch_item<kImplicit2>(R, smem, g, S, b, e, items_r, r, loaded_run);
         } else if (R.scheme == 0) {
             batch_item<kExplicitEC>(R, smem, g, S, b, e, items_r, r, loaded_run);
         } else if (R.scheme == 1) {
             batch_item<kExplicitMC>(R, smem, g, S, b, e, items_r, r, loaded_run);
-        } else {
+        } else if (R.scheme == 2) {
             batch_item<kImplicit1>(R, smem, g, S, b, e, items_r, r, loaded_run);
+        } else {
+            batch_item<kImplicit1MC>(R, smem, g, S, b, e, items_r, r, loaded_run);
         }
     }
     // the last block of the launch publishes the work counts of the next one
@@ -2419,6 +2455,8 @@ cudaError_t launch_particles(const Run &r, Mode m, int grid, cudaStream_t s) {
         case kDepositMC: return launch_mode<kDepositMC>(r, grid, s);
         case kImplicit1: return launch_mode<kImplicit1>(r, grid, s);
         case kImplicit2: return launch_mode<kImplicit2>(r, grid, s);
+        case kImplicit1MC: return launch_mode<kImplicit1MC>(r, grid, s);
+        case kImplicit2MC: return launch_mode<kImplicit2MC>(r, grid, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -2437,7 +2475,7 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    for (int k = 0; k < 6; ++k) {  // raise the shared-memory limit of every mode
+    for (int k = 0; k < 8; ++k) {  // raise the shared-memory limit of every mode
         int dummy = 0;
         switch (k) {
             case 0: e = occ<kExplicitEC>(r, &dummy); break;
@@ -2445,7 +2483,9 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
             case 2: e = occ<kDepositEC>(r, &dummy); break;
             case 3: e = occ<kDepositMC>(r, &dummy); break;
             case 4: e = occ<kImplicit1>(r, &dummy); break;
-            default: e = occ<kImplicit2>(r, &dummy); break;
+            case 5: e = occ<kImplicit2>(r, &dummy); break;
+            case 6: e = occ<kImplicit1MC>(r, &dummy); break;
+            default: e = occ<kImplicit2MC>(r, &dummy); break;
         }
         if (e != cudaSuccess) return e;
     }
@@ -2456,6 +2496,8 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
         case kDepositMC: e = occ<kDepositMC>(r, &per); break;
         case kImplicit1: e = occ<kImplicit1>(r, &per); break;
         case kImplicit2: e = occ<kImplicit2>(r, &per); break;
+        case kImplicit1MC: e = occ<kImplicit1MC>(r, &per); break;
+        case kImplicit2MC: e = occ<kImplicit2MC>(r, &per); break;
     }
     if (e != cudaSuccess) return e;
     *grid = sms * (per > 0 ? per : 1);
@@ -2687,7 +2729,7 @@ extern "C" int pic_deposit_noalloc(int32_t scheme, int32_t boundary, int32_t n_c
                                    int64_t *rho_q_out, void *stream) {
     using namespace pic;
     using namespace pic::noalloc;
-    if (scheme < 0 || scheme > 2 || (boundary != 0 && boundary != 1)) {
+    if (scheme < 0 || scheme > 3 || (boundary != 0 && boundary != 1)) {
         set_last_error("pic_deposit_noalloc: unknown scheme or boundary");
         return -1;
     }
@@ -2731,7 +2773,7 @@ extern "C" int pic_deposit_noalloc(int32_t scheme, int32_t boundary, int32_t n_c
     if (grid > 4ll * sms) grid = 4ll * sms;
     const int smem = 16 * kScratchKeys;
     k_deposit<<<(int)grid, kThreads, smem, s>>>(cell, off, (long long)n, n_cells, boundary == 1,
-                                               scheme == 1, scratch, (long long *)rho_q_out);
+                                               scheme == 1 || scheme == 3, scratch, (long long *)rho_q_out);
     return cudaGetLastError() == cudaSuccess ? 0 : -5;
 }
 

@@ -66,8 +66,18 @@ def test_strict_mode_rejects_unstable_leapfrog(abi):
     assert b"Eq. (1)" in abi.lib().pic_last_error(None)
     cfg["strict"] = False
     assert _sizes(abi, cfg)[0] == 0
-    # the implicit scheme is exempt
+    # the implicit schemes are exempt
     assert _sizes(abi, dict(cfg, scheme="ec_implicit", strict=True))[0] == 0
+    assert _sizes(abi, dict(cfg, scheme="mc_implicit", strict=True))[0] == 0
+
+
+def test_unknown_scheme_is_rejected(abi):
+    from paper_1310_5284_gb300.sim import make_config
+    c = make_config(dict(workloads.CFG_SMALL_CCP))
+    s = abi.PicSizes()
+    for scheme, code in ((0, 0), (1, 0), (2, 0), (3, 0), (4, -1), (-1, -1)):
+        c.scheme = scheme
+        assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == code, scheme
 
 
 @pytest.mark.parametrize("bad,code", [

@@ -26,6 +26,7 @@ def batch_cases():
         dict(base, n_cells=200, np_init=20000, te_ev=6.0, seed=15, run=4),
         dict(base, n_cells=33, np_init=700, scheme="ec_implicit", dt=6e-10, te_ev=5.0, seed=16, run=5),
         dict(base, n_cells=1024, np_init=9000, seed=17, run=6, sort_period=4),
+        dict(base, n_cells=71, np_init=6000, scheme="mc_implicit", dt=5e-10, te_ev=6.0, seed=18, run=7),
     ]
 
 
@@ -55,7 +56,7 @@ def test_batched_runs_bit_identical_to_single_runs():
             a, b = by_id(batch.get_particles(r, sp)), by_id(single.get_particles(sp))
             for key in ("id", "cell", "off", "vx", "vy", "vz"):
                 assert np.array_equal(a[key], b[key]), (r, sp, key)
-            if cfg.get("scheme") == "ec_implicit":
+            if cfg.get("scheme") in ("ec_implicit", "mc_implicit"):
                 assert np.array_equal(a["abar"], b["abar"]), (r, sp)
         single.close()
     batch.close()

@@ -189,6 +189,7 @@ DEPOSIT_CASES = [
     ("ec_dirichlet_1024_sorted", dict(n_cells=1024), 300_001, True),
     ("mc_dirichlet_64", dict(n_cells=64, scheme="mc_explicit"), 9_999, False),
     ("mc_periodic_33", dict(n_cells=33, periodic=True, scheme="mc_explicit", rf_volt=0.0), 4_321, False),
+    ("mc_implicit_dirichlet_45", dict(n_cells=45, scheme="mc_implicit"), 7_777, False),
     ("ec_tiny_2cells", dict(n_cells=2), 5, False),
 ]
 
@@ -238,6 +239,10 @@ STEP_CASES = [
     ("ec_implicit_electrodes", dict(n_cells=64, mcc=False, scheme="ec_implicit", dt=8e-10), 5, 30),
     ("ec_implicit_periodic", dict(n_cells=50, periodic=True, mcc=False, rf_volt=0.0,
                                   scheme="ec_implicit", dt=8e-10), 10, 100),
+    ("mc_implicit_electrodes", dict(n_cells=64, mcc=False, scheme="mc_implicit", dt=8e-10), 5, 30),
+    ("mc_implicit_periodic", dict(n_cells=50, periodic=True, mcc=False, rf_volt=0.0,
+                                  scheme="mc_implicit", dt=8e-10), 10, 100),
+    ("mc_implicit_ragged_37", dict(n_cells=37, mcc=False, scheme="mc_implicit", dt=3e-10), 10, 40),
 ]
 
 
@@ -281,10 +286,12 @@ def test_steps_match_oracle(name, over, strict, steps):
     assert dg["field_energy"] == pytest.approx(do["field_energy"], rel=5e-2)
 
 
-def test_collisions_counts_exact_and_births_ranked():
+@pytest.mark.parametrize("scheme", ["ec_explicit", "ec_implicit", "mc_implicit"])
+def test_collisions_counts_exact_and_births_ranked(scheme):
     """Null-collision MCC on the same Philox stream: selection is an integer
-    compare, so tallies and births agree exactly; children get the same ids."""
-    cfg = dict(workloads.CFG_SMALL_CCP, np_init=20_000, sort_period=4, te_ev=6.0)
+    compare, so tallies and births agree exactly; children get the same ids
+    (and, in the implicit schemes, the parent's abar)."""
+    cfg = dict(workloads.CFG_SMALL_CCP, np_init=20_000, sort_period=4, te_ev=6.0, scheme=scheme)
     n = cfg["np_init"]
     gpu = gpu_sim(cfg)
     orc = oracle.Sim(cfg)
@@ -301,6 +308,11 @@ def test_collisions_counts_exact_and_births_ranked():
     # the collision kinematics (sqrt, sincospi, log in FP32) add their own
     # rounding to that of the push: 99.9% within 1e-5, all within 1e-4
     compare_particles(gpu, orc, cfg, quantile=0.999, max_tol=1e-4)
+    if scheme != "ec_explicit":  # abar of parents and children, relative to its scale
+        for sp in ("e", "i"):
+            a, b = by_id(gpu.get_particles(sp)), by_id(orc.get_species(sp))
+            d = np.abs(a["abar"].astype(np.float64) - b["abar"]) / np.abs(b["abar"]).max()
+            assert np.quantile(d, 0.999) <= 1e-5 and d.max() <= 1e-4, (sp, d.max())
 
 
 @pytest.mark.parametrize("n", [40_000, 120_000])

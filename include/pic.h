@@ -57,6 +57,8 @@ extern "C" {
 #define PIC_STATUS_CAPACITY 0x1u    /* particles dropped: slot capacity exhausted */
 #define PIC_STATUS_BIRTHS 0x2u      /* births dropped: per-step birth buffer full */
 #define PIC_STATUS_TIMEOUT 0x4u     /* a bounded wait ran out (batched driver) */
+#define PIC_STATUS_QUEUE 0x8u       /* a selected collision found the collision queue full
+                                       (drains keep room for a whole tile: not expected) */
 
 /* Schemes (Sec. 2): (2) EC explicit, (1) momentum-conserving explicit, (4) EC
    direct implicit, (3) momentum-conserving direct implicit (S_1 charge and
@@ -200,7 +202,11 @@ int pic_count(pic_handle *h, int64_t *n_e, int64_t *n_i);
 int pic_get_particles(pic_handle *h, int species, pic_host_particles *out);
 
 /* Replace one species' particles by host arrays (count <= capacity).  The
-   field is not recomputed: call pic_init_field() after setting both species. */
+   arrays are uploaded into the run's idle second particle buffer and checked
+   there on the device (cell in [0, n_cells), offset in [0, 1)); if any
+   particle is off the grid the call returns PIC_EINVAL and the run is
+   unchanged.  Synchronous.  The field is not recomputed: call
+   pic_init_field() after setting both species. */
 int pic_set_particles(pic_handle *h, int species, const pic_host_particles *in);
 
 /* Assign charge for the current particles and solve for the field at the

@@ -207,9 +207,11 @@ int pic_batch_init(const pic_config *cfgs, int32_t nruns, const pic_buffers *buf
         return code;
     };
     // per-run kernels for the initial load: the run with the widest grid sets
-    // the shared-memory limit and the grid
+    // the shared-memory limit and the grid (with the implicit runs' wider ring
+    // if there are any)
     Run widest = b->runs[big];
     widest.eedf_bins = max_bins;
+    if (b->any_implicit) widest.scheme = PIC_EC_IMPLICIT;
     int grid = 0;
     cudaError_t e = occupancy_grid(widest, kExplicitEC, &grid);
     if (e != cudaSuccess) return bail(cuda_fail_b(nullptr, e, "occupancy"));

@@ -667,22 +667,35 @@ int pic_set_particles(pic_handle *h, int species, const pic_host_particles *in) 
     if (species == 1 && !h->cfg.ions_mobile && n > 0) return fail(PIC_EINVAL, "ions are frozen in this run");
     if (n > 0 && (!in->cell || !in->off || !in->vx || !in->vy || !in->vz || !in->id))
         return fail(PIC_EINVAL, "NULL particle array");
-    for (long long i = 0; i < n; ++i) {
-        if (in->cell[i] < 0 || in->cell[i] >= h->cfg.n_cells || !(in->off[i] >= 0.0f) || !(in->off[i] < 1.0f))
-            return fail(PIC_EINVAL, "particle %lld outside the grid (cell %d, offset %g)", i, in->cell[i],
-                        (double)in->off[i]);
-    }
     DevState st;
     int r = read_state(h, &st);
     if (r) return r;
+    // upload into the idle second buffer, check the positions there, and only
+    // then copy into the current one (nothing is applied if a particle is
+    // off the grid)
     const Species &sp = h->run.buf[st.parity][species];
+    const Species &up = h->run.buf[st.parity ^ 1u][species];
     if (n > 0) {
-        CK(h, cudaMemcpyAsync(sp.cell, in->cell, 4 * n, cudaMemcpyHostToDevice, h->stream));
-        CK(h, cudaMemcpyAsync(sp.off, in->off, 4 * n, cudaMemcpyHostToDevice, h->stream));
-        CK(h, cudaMemcpyAsync(sp.vx, in->vx, 4 * n, cudaMemcpyHostToDevice, h->stream));
-        CK(h, cudaMemcpyAsync(sp.vy, in->vy, 4 * n, cudaMemcpyHostToDevice, h->stream));
-        CK(h, cudaMemcpyAsync(sp.vz, in->vz, 4 * n, cudaMemcpyHostToDevice, h->stream));
-        CK(h, cudaMemcpyAsync(sp.id, in->id, 4 * n, cudaMemcpyHostToDevice, h->stream));
+        const void *src[6] = {in->cell, in->off, in->vx, in->vy, in->vz, in->id};
+        void *tmp[6] = {up.cell, up.off, up.vx, up.vy, up.vz, up.id};
+        void *dst[6] = {sp.cell, sp.off, sp.vx, sp.vy, sp.vz, sp.id};
+        for (int f = 0; f < 6; ++f)
+            CK(h, cudaMemcpyAsync(tmp[f], src[f], 4 * n, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemsetAsync(&h->run.st->check, 0, 4, h->stream));
+        CK(h, launch_check_particles(up.cell, up.off, n, h->cfg.n_cells, &h->run.st->check, h->stream));
+        unsigned int bad = 0;
+        CK(h, cudaMemcpyAsync(&bad, &h->run.st->check, 4, cudaMemcpyDeviceToHost, h->stream));
+        r = sync(h);
+        if (r) return r;
+        if (bad) {
+            for (long long i = 0; i < n; ++i)  // name the first offender
+                if (in->cell[i] < 0 || in->cell[i] >= h->cfg.n_cells || !(in->off[i] >= 0.0f) || !(in->off[i] < 1.0f))
+                    return fail(PIC_EINVAL, "particle %lld outside the grid (cell %d, offset %g)", i, in->cell[i],
+                                (double)in->off[i]);
+            return fail(PIC_EINVAL, "a particle is outside the grid");
+        }
+        for (int f = 0; f < 6; ++f)
+            CK(h, cudaMemcpyAsync(dst[f], tmp[f], 4 * n, cudaMemcpyDeviceToDevice, h->stream));
         if (sp.abar) {
             if (in->abar)
                 CK(h, cudaMemcpyAsync(sp.abar, in->abar, 4 * n, cudaMemcpyHostToDevice, h->stream));

@@ -22,7 +22,7 @@ namespace pic {
 #define PIC_UNROLL 4
 #endif
 #ifndef PIC_MIN_BLOCKS
-#define PIC_MIN_BLOCKS 2
+#define PIC_MIN_BLOCKS 3
 #endif
 
 constexpr int kMaxCells = 1024;          // grid lives in shared memory
@@ -91,7 +91,7 @@ struct DevState {
     // the running averages of the newest field and charges, bit 1 convert the
     // newest field to FP64 and sum its energy.
     unsigned int pending;
-    unsigned int pad1;
+    unsigned int check;            // pic_set_particles: nonzero if an uploaded particle is off the grid
     double fe_acc;                 // sum of E_c^2 of the field the next push uses
 };
 
@@ -216,6 +216,10 @@ cudaError_t launch_particles(const Run &r, Mode m, int grid, cudaStream_t s);
 cudaError_t launch_sort(const Run &r, int grid, cudaStream_t s);
 cudaError_t sort_grid(int *grid);
 cudaError_t launch_set_abar(const Run &r, cudaStream_t s);
+// flag |= 1 if any of the n particles has a cell outside [0, n_cells) or an
+// offset outside [0, 1)
+cudaError_t launch_check_particles(const int32_t *cell, const float *off, long long n, int n_cells,
+                                   unsigned int *flag, cudaStream_t s);
 cudaError_t launch_perp_energy(const Run &r, cudaStream_t s);
 cudaError_t launch_finalize(const Run &r, cudaStream_t s);
 cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,

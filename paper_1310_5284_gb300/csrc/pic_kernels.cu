@@ -14,7 +14,9 @@
 #include "pic_internal.h"
 
 #include <cstdint>
+#include <map>
 #include <mutex>
+#include <utility>
 
 namespace pic {
 
@@ -465,13 +467,18 @@ __device__ void block_sum2(double &x, double &y, double *scratch /*[2*kThreads/3
 // ---------------------------------------------------------------------------
 // Shared-memory layout of the particle kernels.
 // ---------------------------------------------------------------------------
-// Deferred collisions: selected particles wait here (slot, id and the three
-// Philox words the collision uses) and are collided later by full warps.
-constexpr int kQueue = 512;
+// Deferred collisions: selected particles wait here (slot and id; the
+// collision redraws its Philox words from them) and are collided later by
+// full warps.  The queue is drained before a tile whenever fewer than a
+// tile's worth of entries are free, so it cannot overflow.
+#ifndef PIC_QDRAIN
+#define PIC_QDRAIN 512
+#endif
+constexpr unsigned int kQueueDrainAbove = PIC_QDRAIN;
+constexpr int kQueue = (int)kQueueDrainAbove + kThreads * kUnroll;  // + one tile
 struct CollQueue {
     int *slot;                 // [kQueue]
     uint32_t *id;              // [kQueue]
-    uint4 *w;                  // [kQueue] (x unused)
     unsigned int *n;           // entries queued
 };
 
@@ -487,11 +494,14 @@ __host__ __device__ inline size_t align8(size_t x) { return (x + 7) & ~size_t(7)
 
 __host__ __device__ inline size_t main_smem_bytes(int n, int bins) {
     return align8(4 * (size_t)(n + 2)) + 4 * align8(4 * (size_t)(n + 1)) + align8(4 * (size_t)n) +
-           align8(4 * (size_t)(bins + 1)) + 16 * (size_t)kQueue + 8 * (size_t)kQueue + 16;
+           align8(4 * (size_t)(bins + 1)) + 8 * (size_t)kQueue + 16;
 }
 
+// The tail's scratch: the field solve's arrays (32 bytes a node), or, before
+// them, the births ranking's 2048-bucket histogram.
 __host__ __device__ inline size_t tail_smem_bytes(int n) {
-    return 8 * (size_t)(n + 1) * 4 + 8 * 2048;
+    const size_t field = 32 * (size_t)(n + 1), births = 4 * 2048;
+    return field > births ? field : births;
 }
 
 // The last block's tail reuses the whole dynamic shared memory (ring and grid
@@ -513,9 +523,6 @@ __device__ SmemMain carve_main(unsigned char *base, int n, int bins) {
     o += align8(4 * (size_t)n);
     s.eedf = (unsigned int *)(base + o);
     o += align8(4 * (size_t)(bins + 1));
-    o = (o + 15) & ~size_t(15);
-    s.q.w = (uint4 *)(base + o);
-    o += 16 * (size_t)kQueue;
     s.q.slot = (int *)(base + o);
     o += 4 * (size_t)kQueue;
     s.q.id = (uint32_t *)(base + o);
@@ -575,7 +582,7 @@ __device__ __forceinline__ void drain_body(const Run &R, const SmemMain &sm, Spe
     for (unsigned int q = threadIdx.x; q < nq; q += kThreads) {
         const int idx = sm.q.slot[q];
         const uint32_t id = sm.q.id[q];
-        const uint4 w = sm.q.w[q];
+        const uint4 w = draw(R, id, step, S, kTagMcc, 0);  // the selection's draw
         float vx = sp.vx[idx], vy = sp.vy[idx], vz = sp.vz[idx];
         bool changed;
         if (S == 0) {
@@ -618,7 +625,7 @@ __device__ __forceinline__ void drain_q(const Run &R, const SmemMain &sm, Specie
 template <int MODE, int S, bool INL>
 __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, const Species &sp,
                                              long long idx, int &cell, float &off, float &vx,
-                                             float &abar, uint32_t id, bool diag, long long step,
+                                             float &abar, uint32_t id, bool sel, bool diag, long long step,
                                              Tally &t, float &kx, float &pw, uint32_t &a_out) {
     using MI = ModeInfo<MODE>;
     const int N = R.n_cells;
@@ -673,28 +680,19 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         return -1;
     }
     cell = c;
-    // null-collision Monte Carlo: one Philox draw per particle and step; a
-    // selected particle is queued and collided later by full warps (its
-    // position, hence its charge assignment, does not change in a collision)
+    // null-collision Monte Carlo: `sel` is this particle's selection (one
+    // Philox draw per particle and step, made by the caller); a selected
+    // particle is queued and collided later by full warps (its position,
+    // hence its charge assignment, does not change in a collision)
     bool queued = false;
-    if (R.mcc) {
-        const uint4 w = draw(R, id, step, S, kTagMcc, 0);
-        if ((w.x >> 8) < R.thr[S]) {
-            const unsigned int pos = atomicAdd(sm.q.n, 1u);
-            if (pos < (unsigned int)kQueue) {
-                sm.q.slot[pos] = (int)idx;
-                sm.q.id[pos] = id;
-                sm.q.w[pos] = w;
-                queued = true;
-            } else {  // queue full: collide here
-                float vy = sp.vy[idx], vz = sp.vz[idx];
-                const bool changed = S == 0 ? collide_e<INL>(R, w, id, step, c, s, abar, vx, vy, vz, t)
-                                            : collide_i<INL>(R, w, id, step, vx, vy, vz, t);
-                if (changed) {
-                    sp.vy[idx] = vy;
-                    sp.vz[idx] = vz;
-                }
-            }
+    if (R.mcc && sel) {
+        const unsigned int pos = atomicAdd(sm.q.n, 1u);
+        if (pos < (unsigned int)kQueue) {  // always: drains keep a tile's room
+            sm.q.slot[pos] = (int)idx;
+            sm.q.id[pos] = id;
+            queued = true;
+        } else {
+            atomicOr(&R.st->status, 0x8u);
         }
     }
     if (S == 0 && diag && R.eedf_bins > 0 && !queued) eedf_sample(R, sm, vx, sp.vy[idx], sp.vz[idx]);
@@ -749,7 +747,11 @@ __device__ __forceinline__ void stv(T *p, const T (&o)[kUnroll]) {
 // wait is bounded: a wait that runs out sets PIC_STATUS_TIMEOUT.
 // ---------------------------------------------------------------------------
 constexpr int kTile = kThreads * kUnroll;
-constexpr int kStages = 3;
+static_assert(kQueueDrainAbove + kTile <= kQueue, "a tile must fit the undrained queue");
+#ifndef PIC_STAGES
+#define PIC_STAGES 2
+#endif
+constexpr int kStages = PIC_STAGES;
 constexpr int kMaxFields = 5;  // cell, off, vx, abar, id
 constexpr long long kWaitLimit = 1ll << 20;
 
@@ -794,18 +796,87 @@ __device__ __forceinline__ bool mbar_wait(const Run &R, unsigned long long *bar,
     return false;
 }
 
-// The ring: kStages x kMaxFields arrays of kTile words, one barrier per stage.
+// The ring: kStages x nf arrays of kTile words, one barrier per stage.  The
+// implicit passes stage all five fields (cell, off, vx, abar, id); the other
+// modes have no abar, and id takes its place.
 struct Ring {
-    uint32_t *buf;               // [kStages][kMaxFields][kTile]
+    uint32_t *buf;               // [kStages][nf][kTile]
     unsigned long long *bar;     // [kStages] (static shared)
     unsigned int *uses;          // tiles issued so far by this block (static shared)
+    int nf;                      // 4 or kMaxFields
 };
 
-__host__ __device__ constexpr size_t ring_bytes() { return (size_t)kStages * kMaxFields * kTile * 4; }
+__host__ __device__ constexpr size_t ring_bytes(bool implicit) {
+    return (size_t)kStages * (implicit ? kMaxFields : kMaxFields - 1) * kTile * 4;
+}
 // The idle ring holds the tail's copy of the per-key sums (6 x 8 bytes a key).
 
 __device__ __forceinline__ uint32_t *ring_field(const Ring &g, int stage, int f) {
-    return g.buf + ((size_t)stage * kMaxFields + f) * kTile;
+    const int slot = (f == kMaxFields - 1 && g.nf < kMaxFields) ? f - 1 : f;
+    return g.buf + ((size_t)stage * g.nf + slot) * kTile;
+}
+
+// A thread's kUnroll consecutive words of a staged field, from place s0 of the
+// tile (a multiple of kUnroll): one 16-byte shared load for kUnroll = 4, which
+// keeps the warp's access free of bank conflicts.  Words beyond the tile's
+// particles are stale; the caller masks them.
+__device__ __forceinline__ void ring_words(const Ring &g, int stage, int f, int s0, uint32_t (&o)[kUnroll]) {
+    const uint32_t *p = ring_field(g, stage, f) + s0;
+    if constexpr (kUnroll == 4) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else if constexpr (kUnroll == 2) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(p);
+        o[0] = v.x; o[1] = v.y;
+    } else {
+        o[0] = p[0];
+    }
+}
+
+// Load a thread's particles of a staged tile: n_ok of them are real (cell -1
+// marks the rest); fields a mode does not use read as zero.
+template <int MODE>
+__device__ __forceinline__ void ring_particles(const Ring &g, int stage, int s0, int n_ok, bool need_id,
+                                               int (&cell)[kUnroll], float (&off)[kUnroll], float (&vx)[kUnroll],
+                                               float (&abar)[kUnroll], uint32_t (&id)[kUnroll]) {
+    using MI = ModeInfo<MODE>;
+    uint32_t w[kUnroll];
+    ring_words(g, stage, 0, s0, w);
+#pragma unroll
+    for (int q = 0; q < kUnroll; ++q) cell[q] = q < n_ok ? (int)w[q] : -1;
+    ring_words(g, stage, 1, s0, w);
+#pragma unroll
+    for (int q = 0; q < kUnroll; ++q) off[q] = q < n_ok ? __uint_as_float(w[q]) : 0.0f;
+#pragma unroll
+    for (int q = 0; q < kUnroll; ++q) vx[q] = abar[q] = 0.0f, id[q] = 0u;
+    if (MI::loads_v) {
+        ring_words(g, stage, 2, s0, w);
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) vx[q] = q < n_ok ? __uint_as_float(w[q]) : 0.0f;
+    }
+    if (MI::implicit) {
+        ring_words(g, stage, 3, s0, w);
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) abar[q] = q < n_ok ? __uint_as_float(w[q]) : 0.0f;
+    }
+    if (need_id) {
+        ring_words(g, stage, 4, s0, w);
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) id[q] = q < n_ok ? w[q] : 0u;
+    }
+}
+
+// The null-collision selections of a thread's particles, one Philox draw
+// each (only the first word decides), computed side by side without
+// branches so that the independent multiply chains overlap.
+template <int S>
+__device__ __forceinline__ void mcc_select(const Run &R, const uint32_t (&id)[kUnroll], long long step,
+                                           bool (&sel)[kUnroll]) {
+    uint32_t x[kUnroll];
+#pragma unroll
+    for (int q = 0; q < kUnroll; ++q) x[q] = draw(R, id[q], step, S, kTagMcc, 0).x;
+#pragma unroll
+    for (int q = 0; q < kUnroll; ++q) sel[q] = (x[q] >> 8) < R.thr[S];
 }
 
 // Issue the copies of tile t (block-relative tile counter u) of segment
@@ -877,15 +948,9 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
         int cell[U];
         float off[U], vx[U], abar[U];
         uint32_t id[U];
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            const bool ok = i0 + q < len;
-            cell[q] = ok ? (int)ring_field(g, stage, 0)[s0 + q] : -1;
-            off[q] = ok ? __uint_as_float(ring_field(g, stage, 1)[s0 + q]) : 0.0f;
-            vx[q] = (ok && MI::loads_v) ? __uint_as_float(ring_field(g, stage, 2)[s0 + q]) : 0.0f;
-            abar[q] = (ok && MI::implicit) ? __uint_as_float(ring_field(g, stage, 3)[s0 + q]) : 0.0f;
-            id[q] = (ok && need_id) ? ring_field(g, stage, 4)[s0 + q] : 0u;
-        }
+        ring_particles<MODE>(g, stage, s0, len - i0, need_id, cell, off, vx, abar, id);
+        bool sel[U] = {};
+        if (need_id) mcc_select<S>(R, id, step, sel);
         int key[U];
         uint32_t a[U];
 #pragma unroll
@@ -894,7 +959,7 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
             key[q] = -1;
             if (cell[q] < 0) continue;  // beyond the segment, or a hole left by absorption
             key[q] = step_particle<MODE, S, false>(R, sm, sp, (long long)(i0 + q), cell[q], off[q], vx[q],
-                                            abar[q], id[q], diag, step, t, kx, pw, a[q]);
+                                            abar[q], id[q], sel[q], diag, step, t, kx, pw, a[q]);
         }
         if (MI::push) {
             if (full) {
@@ -917,7 +982,7 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
         }
         deposit_tile(key, a, sm.acc, MI::count_only);
         __syncthreads();  // the stage is free again; the queue count is current
-        if (MI::push && R.mcc && *sm.q.n >= (unsigned int)(kQueue / 2))
+        if (MI::push && R.mcc && *sm.q.n > kQueueDrainAbove)
             drain_collisions<S>(R, sm, sp, step, diag, t);
     }
     if (MI::push && R.mcc) {
@@ -1864,15 +1929,9 @@ __device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, co
     int cell[U];
     float off[U], vx[U], abar[U];
     uint32_t id[U];
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-        const bool ok = i0 + q < len;
-        cell[q] = ok ? (int)ring_field(g, stage, 0)[i0 + q] : -1;
-        off[q] = ok ? __uint_as_float(ring_field(g, stage, 1)[i0 + q]) : 0.0f;
-        vx[q] = (ok && MI::loads_v) ? __uint_as_float(ring_field(g, stage, 2)[i0 + q]) : 0.0f;
-        abar[q] = (ok && MI::implicit) ? __uint_as_float(ring_field(g, stage, 3)[i0 + q]) : 0.0f;
-        id[q] = (ok && need_id) ? ring_field(g, stage, 4)[i0 + q] : 0u;
-    }
+    ring_particles<MODE>(g, stage, i0, len - i0, need_id, cell, off, vx, abar, id);
+    bool sel[U] = {};
+    if (need_id) mcc_select<S>(R, id, step, sel);
     int key[U];
     uint32_t a[U];
 #pragma unroll
@@ -1880,8 +1939,8 @@ __device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, co
         a[q] = 0u;
         key[q] = -1;
         if (cell[q] < 0) continue;  // beyond the tile, or a hole left by absorption
-        key[q] = step_particle<MODE, S, true>(R, sm, sp, o + i0 + q, cell[q], off[q], vx[q], abar[q], id[q], diag,
-                                        step, t, kx, pw, a[q]);
+        key[q] = step_particle<MODE, S, true>(R, sm, sp, o + i0 + q, cell[q], off[q], vx[q], abar[q], id[q],
+                                        sel[q], diag, step, t, kx, pw, a[q]);
     }
     if (MI::push) {
         const long long b = o + i0;
@@ -1964,7 +2023,7 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
         // block's sums of this species are flushed
         if (MI::push && R.mcc && cur >= 0) {
             const unsigned int qn = *sm.q.n;
-            if (qn >= (unsigned int)(kQueue / 2) || (closing && qn > 0u)) {
+            if (qn > kQueueDrainAbove || (closing && qn > 0u)) {
                 if (cur == 0)
                     drain_q<0, true>(R, sm, sp[0], step, diag, t);
                 else
@@ -2020,8 +2079,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     g.buf = (uint32_t *)smem_all;
     g.bar = s_bar;
     g.uses = &s_uses;
+    g.nf = MI::implicit ? kMaxFields : kMaxFields - 1;
     const Stream ms = {s_ms_S, s_ms_o, s_ms_n};
-    unsigned char *smem = smem_all + ring_bytes();  // grid, accumulators, queue; the tail's space
+    unsigned char *smem = smem_all + ring_bytes(MI::implicit);  // grid, accumulators, queue; the tail's space
     const SmemMain sm = carve_main(smem, n, R.eedf_bins);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1u);
@@ -2207,6 +2267,27 @@ __global__ void k_set_abar(Run R) {
     }
 }
 
+// Validation of uploaded particles (pic_set_particles).
+__global__ void k_check_particles(const int32_t *__restrict__ cell, const float *__restrict__ off, long long n,
+                                  int n_cells, unsigned int *flag) {
+    bool bad = false;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = cell[i];
+        const float o = off[i];
+        bad |= c < 0 || c >= n_cells || !(o >= 0.0f) || !(o < 1.0f);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+
+cudaError_t launch_check_particles(const int32_t *cell, const float *off, long long n, int n_cells,
+                                   unsigned int *flag, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    long long grid = (n + 4 * kThreads - 1) / (4 * kThreads);
+    if (grid > 4096) grid = 4096;
+    k_check_particles<<<(int)grid, kThreads, 0, s>>>(cell, off, n, n_cells, flag);
+    return cudaGetLastError();
+}
+
 // Kinetic energy of the transverse velocities (diagnostics only).
 __global__ void k_perp_energy(Run R) {
     const DevState *st = R.st;
@@ -2337,7 +2418,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ r
     g.buf = (uint32_t *)smem_all;
     g.bar = s_bar;
     g.uses = &s_uses;
-    unsigned char *smem = smem_all + ring_bytes();
+    g.nf = kMaxFields;
+    unsigned char *smem = smem_all + ring_bytes(true);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1u);
         s_uses = 0u;
@@ -2433,7 +2515,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ r
 // Launchers
 // ---------------------------------------------------------------------------
 int block_smem_bytes(const Run &r) {
-    const size_t a = ring_bytes() + main_smem_bytes(r.n_cells, r.eedf_bins);
+    const size_t a = ring_bytes(r.scheme >= 2) + main_smem_bytes(r.n_cells, r.eedf_bins);
     const size_t b = tail_stage_bytes(r.n_cells) + tail_smem_bytes(r.n_cells);
     return (int)(a > b ? a : b);
 }
@@ -2461,10 +2543,27 @@ cudaError_t launch_particles(const Run &r, Mode m, int grid, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+// A kernel's dynamic shared-memory limit only ever rises (per device):
+// handles of different sizes live side by side in one process, and each
+// launch asks for its own size.
+static cudaError_t raise_smem_limit(const void *func, int smem) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> raised;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    int &cur = raised[std::make_pair(func, dev)];
+    if (smem <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) cur = smem;
+    return e;
+}
+
 template <int MODE>
 static cudaError_t occ(const Run &r, int *per_sm) {
     const int smem = block_smem_bytes(r);
-    cudaError_t e = cudaFuncSetAttribute(k_particles<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const cudaError_t e = raise_smem_limit((const void *)k_particles<MODE>, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_particles<MODE>, kThreads, smem);
 }
@@ -2545,7 +2644,7 @@ cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c
 }
 
 size_t batch_smem_bytes(int max_cells, int max_bins, int nruns, int *table_off) {
-    const size_t a = ring_bytes() + main_smem_bytes(max_cells, max_bins);
+    const size_t a = ring_bytes(true) + main_smem_bytes(max_cells, max_bins);
     const size_t b = tail_stage_bytes(max_cells) + tail_smem_bytes(max_cells);
     const size_t off = ((a > b ? a : b) + 15) & ~size_t(15);
     *table_off = (int)off;
@@ -2554,7 +2653,7 @@ size_t batch_smem_bytes(int max_cells, int max_bins, int nruns, int *table_off) 
 
 template <int PHASE>
 static cudaError_t batch_attr(int smem) {
-    return cudaFuncSetAttribute(k_batch<PHASE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return raise_smem_limit((const void *)k_batch<PHASE>, smem);
 }
 
 cudaError_t batch_prepare(int smem, int *grid) {
@@ -3135,9 +3234,9 @@ cudaError_t adj_prepare(int n_cells, int *grid) {
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int sf = adj_fwd_smem_bytes(n_cells), sr = adj_rev_smem_bytes(n_cells);
-    if ((e = cudaFuncSetAttribute(k_adj_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_adj_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_adj_rev, cudaFuncAttributeMaxDynamicSharedMemorySize, sr)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void *)k_adj_fwd<true>, sf)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void *)k_adj_fwd<false>, sf)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void *)k_adj_rev, sr)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adj_fwd<true>, kThreads, sf)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_r, k_adj_rev, kThreads, sr)) != cudaSuccess) return e;
     per = per < per_r ? per : per_r;

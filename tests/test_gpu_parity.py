@@ -380,3 +380,49 @@ def test_birth_capacity_overflow_sets_status_without_fault():
     assert gpu.status() & 0x2
     d = gpu.diag()
     assert d["count"][0] == d["count"][1] + (d["count"][0] - d["count"][1])  # readable after overflow
+
+
+def test_handles_of_different_sizes_coexist():
+    """A large run created before a small one still steps afterwards: each
+    launch's shared-memory request stays within the kernel's limit, which
+    only rises."""
+    big = gpu_sim(dict(workloads.CFG_SMALL_CCP, n_cells=1024, np_init=20_000, eedf_bins=1024))
+    small = gpu_sim(dict(workloads.CFG_SMALL_CCP, n_cells=16, np_init=2_000, eedf_bins=8))
+    big.step(3)
+    small.step(3)
+    big.init_field()
+    assert big.diag()["step"] == 3 and small.diag()["step"] == 3
+    assert big.status() == 0 and small.status() == 0
+    big.close()
+    small.close()
+
+
+@pytest.mark.parametrize("bad", ["cell_low", "cell_high", "offset_one", "offset_nan"])
+def test_set_particles_rejects_off_grid_and_applies_nothing(bad):
+    """The upload is checked on the device; a particle off the grid makes the
+    call fail and leaves the run's particles as they were."""
+    from paper_1310_5284_gb300._abi import PicError
+
+    cfg = dict(workloads.CFG_SMALL_CCP, mcc=False, np_init=5000)
+    gpu = gpu_sim(cfg)
+    before = by_id(gpu.get_particles("e"))
+    st = workloads.injected_particles(3, 4000, cfg["n_cells"], vth(cfg, 0))
+    k = 3999 if bad != "cell_low" else 1234
+    if bad == "cell_low":
+        st["cell"][k] = -1
+    elif bad == "cell_high":
+        st["cell"][k] = cfg["n_cells"]
+    elif bad == "offset_one":
+        st["off"][k] = 1.0
+    else:
+        st["off"][k] = np.nan
+    with pytest.raises(PicError, match="particle %d outside the grid" % k):
+        gpu.set_particles("e", st)
+    after = by_id(gpu.get_particles("e"))
+    for key in ("id", "cell", "off", "vx", "vy", "vz"):
+        assert np.array_equal(before[key], after[key]), key
+    st["off"][k] = 0.5
+    st["cell"][k] = 3
+    gpu.set_particles("e", st)  # the corrected upload goes through
+    assert gpu.get_particles("e")["id"].size == 4000
+    gpu.close()

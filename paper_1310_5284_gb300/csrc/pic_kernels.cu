@@ -981,9 +981,12 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
             }
         }
         deposit_tile(key, a, sm.acc, MI::count_only);
-        __syncthreads();  // the stage is free again; the queue count is current
-        if (MI::push && R.mcc && *sm.q.n > kQueueDrainAbove)
-            drain_collisions<S>(R, sm, sp, step, diag, t);
+        // The stage is free again.  The drain is the block's decision, taken
+        // by the barrier: the thread that queued the tile's last particle
+        // reads the count after doing so (a count read after the barrier could
+        // already include the next tile's particles in some threads only).
+        const bool drain = __syncthreads_or((MI::push && R.mcc && *sm.q.n > kQueueDrainAbove) ? 1 : 0) != 0;
+        if (drain) drain_collisions<S>(R, sm, sp, step, diag, t);
     }
     if (MI::push && R.mcc) {
         __syncthreads();
@@ -1366,6 +1369,55 @@ __device__ void block_exclusive_scan_pair(long long &x, unsigned long long &y, l
     y = by + iy - y;
 }
 
+// The same scan of (x, y), and the block totals (th, tl) of (h, l) with it:
+// one pass of barriers for both.
+__device__ void block_scan_pair_sum_pair(long long &x, unsigned long long &y, long long &tx, unsigned long long &ty,
+                                         long long h, unsigned long long l, long long &th, unsigned long long &tl,
+                                         long long *sx, unsigned long long *sy, long long *sh,
+                                         unsigned long long *sl) {
+    constexpr int nw = kThreads / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long ix = x;
+    unsigned long long iy = y;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long a = __shfl_up_sync(FULL_MASK, ix, o);
+        const unsigned long long b = __shfl_up_sync(FULL_MASK, iy, o);
+        if (lane >= o) {
+            ix += a;
+            iy += b;
+        }
+        h += __shfl_xor_sync(FULL_MASK, h, o);
+        l += __shfl_xor_sync(FULL_MASK, l, o);
+    }
+    if (lane == 31) {
+        sx[wid] = ix;
+        sy[wid] = iy;
+        sh[wid] = h;
+        sl[wid] = l;
+    }
+    __syncthreads();
+    long long bx = 0;
+    unsigned long long by = 0;
+    tx = 0;
+    ty = 0;
+    th = 0;
+    tl = 0;
+    for (int w = 0; w < nw; ++w) {
+        if (w < wid) {
+            bx += sx[w];
+            by += sy[w];
+        }
+        tx += sx[w];
+        ty += sy[w];
+        th += sh[w];
+        tl += sl[w];
+    }
+    __syncthreads();
+    x = bx + ix - x;
+    y = by + iy - y;
+}
+
 // Field solve by the discrete Gauss law.  The finite-difference Poisson
 // equation -(phi_{g-1} - 2 phi_g + phi_{g+1})/dx^2 = rho_g/eps0 (with (1+chi)
 // on the cell faces in the implicit scheme) is D_{c} - D_{c-1} = dx rho_c / eps0
@@ -1454,8 +1506,8 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
                            bool cursors, bool defer, Volt vl, bool vl_ok) {
     DevState *st = R.st;
     const int n = R.n_cells, n1 = n + 1;
-    __shared__ long long sc_x[kThreads / 32];
-    __shared__ unsigned long long sc_y[kThreads / 32];
+    __shared__ long long sc_x[kThreads / 32], sc_h[kThreads / 32];
+    __shared__ unsigned long long sc_y[kThreads / 32], sc_l[kThreads / 32];
     __shared__ double sc_d[kThreads / 32 + 1];
     __shared__ Volt s_vl;
     long long *q = (long long *)smem;               // [n+1] net node charge, then P_c
@@ -1506,22 +1558,29 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
         }
     }
     __syncthreads();
-    // one integer scan: P_c over the cells, sort cursors over the keys
+    // one integer scan: P_c over the cells, sort cursors over the keys; with
+    // it the exact sum over the cells of P_c = sum_g q_g (n - g), in 32-bit
+    // halves of q_g (high part signed)
     const int span = n1 > n ? n1 : n;
     const int per = (span + kThreads - 1) / kThreads;
     const int c_begin = threadIdx.x * per;
-    long long runP = 0;
-    unsigned long long runC = 0;
+    long long runP = 0, wh = 0;
+    unsigned long long runC = 0, wl = 0;
     for (int k = 0; k < per; ++k) {
         const int c = c_begin + k;
-        if (c < n) runP += (R.periodic || c >= 1) ? q[c] : 0ll;
+        if (c < n) {
+            const long long qc = (R.periodic || c >= 1) ? q[c] : 0ll;
+            runP += qc;
+            wh += (qc >> 32) * (long long)(n - c);
+            wl += ((unsigned long long)qc & 0xffffffffull) * (unsigned long long)(n - c);
+        }
         if (cursors && c < n1) runC += K.c[0][c] | (K.c[1][c] << 32);
     }
-    long long totP;
-    unsigned long long totC;
+    long long totP, tot_hi;
+    unsigned long long totC, tot_lo;
     long long P = runP;
     unsigned long long Cx = runC;
-    block_exclusive_scan_pair(P, Cx, totP, totC, sc_x, sc_y);
+    block_scan_pair_sum_pair(P, Cx, totP, totC, wh, wl, tot_hi, tot_lo, sc_x, sc_y, sc_h, sc_l);
     if (implicit) {
         // modified Poisson (direct implicit): FP64 with the susceptibility weights
         double s1 = 0.0, s0 = 0.0;
@@ -1589,8 +1648,6 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
     // Gauss law fixed by sum_c E_c dx = V), base = 0, K2 = -kappa Q/n in the
     // periodic box (zero-mean field, Q the total charge).  The sum of P_c is
     // exact in two 64-bit halves; everything else is double-word FP32.
-    long long sum_hi = 0;
-    unsigned long long sum_lo = 0;
     for (int k = 0; k < per; ++k) {
         const int c = c_begin + k;
         if (cursors && c < n1) {
@@ -1601,13 +1658,8 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
         if (c < n) {
             P += (R.periodic || c >= 1) ? q[c] : 0ll;
             q[c] = P;  // this thread's own cells only
-            sum_hi += P >> 32;
-            sum_lo += (unsigned long long)P & 0xffffffffull;
         }
     }
-    long long tot_hi;
-    unsigned long long tot_lo;
-    block_exclusive_scan_pair(sum_hi, sum_lo, tot_hi, tot_lo, sc_x, sc_y);
     const dw sum_p = dw_add(dw_mul(dw_from_i64(tot_hi), dw{4294967296.0f, 0.0f}), dw_from_i64((long long)tot_lo));
     const dw mean_p = dw_mul(sum_p, dw_of(R.inv_n_ff));
     const dw kap = dw_of(R.kappa_ff);
@@ -1758,7 +1810,8 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
     const long long step = st->step;
     // Copy the per-key sums of both species into shared memory with one batch
     // of independent loads; everything after reads (and the births add to)
-    // this copy through Rs.  The global sums are cleared for the next launch.
+    // this copy through Ks.  The global sums are cleared for the next launch
+    // right behind the loads.
     const int n1 = R.n_cells + 1;
     Keys Ks;
     {
@@ -1787,6 +1840,9 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
                     Ks.c[S][k] = v[j][0];
                     Ks.a[S][k] = v[j][1];
                     Ks.b[S][k] = v[j][2];
+                    R.acc_cnt[S][k] = 0ull;
+                    R.acc_a[S][k] = 0ull;
+                    R.acc_b[S][k] = 0ull;
                 }
             }
         }
@@ -1797,7 +1853,6 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
     if (ModeInfo<MODE>::pass1) tail_field<MODE>(R, Ks, smem, step + 1, true, false, defer, vl, vl_ok);
     if (MODE == kDepositEC || MODE == kDepositMC) tail_field<MODE>(R, Ks, smem, step, false, true, defer, vl, vl_ok);
     if (ModeInfo<MODE>::pass2) tail_cursors(R, Ks);
-    tail_reset(R);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (ModeInfo<MODE>::push) {
@@ -1852,17 +1907,16 @@ __device__ __forceinline__ void block_segment(long long ne, long long ni, int &S
 
 // ---------------------------------------------------------------------------
 // Dynamic work distribution of the particle launch.  The slots of both
-// species are cut into items of kItemTiles tiles (electrons first, then
-// ions); blocks claim items from an atomic counter until none are left, so
-// blocks that met cheap particles take more of them.  Thread 0 of a block is
-// the producer of its copy ring: it claims one item ahead and issues the
-// tiles of consecutive items back to back, writing each tile's species,
-// first slot and length next to the ring stage; the other warps consume the
-// stages in order.  Claims only increase, so a block switches species at most
-// once: its shared accumulators, tallies and collision queue are flushed at
-// that switch.
+// species are cut into items of one tile each (electrons first, then ions;
+// the last half wave in quarter tiles); blocks claim items from an atomic
+// counter until none are left, so blocks that met cheap particles take more
+// of them.  Thread 0 of a block is the producer of its copy ring: it claims
+// one item ahead and issues the tiles of consecutive items back to back,
+// writing each tile's species, first slot and length next to the ring stage;
+// the other warps consume the stages in order.  Claims only increase, so a
+// block switches species at most once: its shared accumulators, tallies and
+// collision queue are flushed at that switch.
 // ---------------------------------------------------------------------------
-constexpr int kItemTiles = 1;
 constexpr int kDeferParts = 4;  // blocks that take the deferred FP64 work of the previous tail
 
 struct Stream {
@@ -1871,11 +1925,32 @@ struct Stream {
     int *n;            // [kStages] particles (0: the stream has ended)
 };
 
-// Producer state (shared memory, used by thread 0 only).
+// Producer state (shared memory, used by thread 0 only).  Items are whole
+// tiles, except that the last stretch of the last species is cut into
+// quarter tiles: the final items then take a fraction of a tile's time, so
+// the blocks finish closer together and the tail starts sooner.
 struct Producer {
-    long long pos, end, next, total, ne_items, ne, ni;
+    long long pos, end, next, total, ne, ni;
+    long long e_items;     // items of species 0 (whole tiles)
+    long long l_full;      // whole-tile items of the last species
     int S;
+    int last;              // the last species (1 if ions move, else 0)
 };
+
+constexpr int kSmallTile = kTile / 4;
+
+// Set up the item table of a launch over ne electron and ni ion slots.
+__device__ __forceinline__ void producer_items(Producer &p, long long ne, long long ni) {
+    p.ne = ne;
+    p.ni = ni;
+    p.last = ni > 0 ? 1 : 0;
+    const long long nl = p.last ? ni : ne;
+    long long cut = nl - (long long)(gridDim.x / 2) * kTile;  // the last half wave goes in quarters
+    cut = cut > 0 ? (cut / kTile) * kTile : 0;
+    p.e_items = p.last ? (ne + kTile - 1) / kTile : 0;
+    p.l_full = cut / kTile;
+    p.total = p.e_items + p.l_full + (nl - cut + kSmallTile - 1) / kSmallTile;
+}
 
 __device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, const Stream &ms, Producer &p,
                                                int par, unsigned int u, bool need_id, int mode_fields,
@@ -1886,15 +1961,21 @@ __device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, cons
             ms.n[stage] = 0;
             return;
         }
-        const long long len = (long long)kItemTiles * kTile;
-        if (p.next < p.ne_items) {
+        if (p.next < p.e_items) {
             p.S = 0;
-            p.pos = p.next * len;
-            p.end = min(p.pos + len, p.ne);
+            p.pos = p.next * kTile;
+            p.end = min(p.pos + kTile, p.ne);
         } else {
-            p.S = 1;
-            p.pos = (p.next - p.ne_items) * len;
-            p.end = min(p.pos + len, p.ni);
+            p.S = p.last;
+            const long long nl = p.last ? p.ni : p.ne;
+            const long long k = p.next - p.e_items;
+            if (k < p.l_full) {
+                p.pos = k * kTile;
+                p.end = p.pos + kTile;
+            } else {
+                p.pos = p.l_full * kTile + (k - p.l_full) * kSmallTile;
+                p.end = min(p.pos + kSmallTile, nl);
+            }
         }
         p.next = (long long)atomicAdd(&R.st->next_item, 1u);
     }
@@ -1993,12 +2074,8 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
     const bool need_id = MI::push && R.mcc;
     const int mode_fields = MI::loads_v ? 3 : 2;
     if (threadIdx.x == 0) {
-        const long long len = (long long)kItemTiles * kTile;
         p.pos = p.end = 0;
-        p.ne = st->n_slots[0];
-        p.ni = R.ions_mobile ? st->n_slots[1] : 0;
-        p.ne_items = (p.ne + len - 1) / len;
-        p.total = p.ne_items + (p.ni + len - 1) / len;
+        producer_items(p, st->n_slots[0], R.ions_mobile ? st->n_slots[1] : 0);
         p.S = 0;
         p.next = (long long)atomicAdd(&st->next_item, 1u);
         for (int k = 0; k < kStages - 1; ++k)
@@ -2013,17 +2090,25 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
     int cur = -1;
     long long added = 0;
     bool gave_up = false;
+    // Set by the barrier that ends a tile, the same in every thread: the tile
+    // left the queue above its drain mark, or some thread's wait gave up.
+    bool flag = false;
     for (unsigned int u = 0;; ++u) {
+        if (flag) gave_up = __syncthreads_or(gave_up ? 1 : 0) != 0;  // which of the two (rare)
         const int stage = (int)(u % kStages);
         const int n = gave_up ? 0 : ms.n[stage];
         const int S = n ? ms.S[stage] : cur;
         const bool closing = cur >= 0 && (n == 0 || S != cur || added + n > kFlushEvery);
         // the one place the queue is drained (keeps a single inlined copy of
-        // the collision code in the loop): when half full, or before the
-        // block's sums of this species are flushed
+        // the collision code in the loop): above the drain mark, or before the
+        // block's sums of this species are flushed.  Every thread must take
+        // the same branch: the count is read only where no thread can queue
+        // before the next barrier (the drain's or the flush's); a thread that
+        // read it after another had started the next tile would enter the
+        // drain's barriers alone.
         if (MI::push && R.mcc && cur >= 0) {
             const unsigned int qn = *sm.q.n;
-            if (qn > kQueueDrainAbove || (closing && qn > 0u)) {
+            if (closing ? qn > 0u : (flag && qn > kQueueDrainAbove)) {
                 if (cur == 0)
                     drain_q<0, true>(R, sm, sp[0], step, diag, t);
                 else
@@ -2053,9 +2138,11 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
             stream_tile<MODE, 1>(R, sm, g, stage, sp[1], o, n, need_id, diag, step, t, kx, pw);
         }
         added += n;
-        // the stage is free again and the queue count current; a thread whose
-        // wait gave up ends the stream for the whole block at the next pass
-        gave_up = __syncthreads_or(gave_up ? 1 : 0) != 0;
+        // The stage is free again.  The thread that queued the tile's last
+        // particle reads the queue count after doing so, so the OR over the
+        // block sees the final count; a thread whose wait gave up ends the
+        // stream for the whole block at the next pass.
+        flag = __syncthreads_or((gave_up || (MI::push && R.mcc && *sm.q.n > kQueueDrainAbove)) ? 1 : 0) != 0;
     }
 }
 

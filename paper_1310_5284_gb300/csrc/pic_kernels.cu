@@ -1907,10 +1907,9 @@ __device__ __forceinline__ void block_segment(long long ne, long long ni, int &S
 
 // ---------------------------------------------------------------------------
 // Dynamic work distribution of the particle launch.  The slots of both
-// species are cut into items of one tile each (electrons first, then ions;
-// the last half wave in quarter tiles); blocks claim items from an atomic
-// counter until none are left, so blocks that met cheap particles take more
-// of them.  Thread 0 of a block is the producer of its copy ring: it claims
+// species are cut into items of one tile each (electrons first, then
+// ions); blocks claim items from an atomic counter until none are left, so
+// blocks that met cheap particles take more of them.  Thread 0 of a block is the producer of its copy ring: it claims
 // one item ahead and issues the tiles of consecutive items back to back,
 // writing each tile's species, first slot and length next to the ring stage;
 // the other warps consume the stages in order.  Claims only increase, so a
@@ -1926,30 +1925,21 @@ struct Stream {
 };
 
 // Producer state (shared memory, used by thread 0 only).  Items are whole
-// tiles, except that the last stretch of the last species is cut into
-// quarter tiles: the final items then take a fraction of a tile's time, so
-// the blocks finish closer together and the tail starts sooner.
+// tiles: electrons first, then ions.  (Cutting the last half wave into
+// quarter tiles, so that blocks finish closer together, measured 7 % slower:
+// a quarter tile leaves three quarters of the block idle.)
 struct Producer {
     long long pos, end, next, total, ne, ni;
-    long long e_items;     // items of species 0 (whole tiles)
-    long long l_full;      // whole-tile items of the last species
+    long long e_items;     // items of species 0
     int S;
-    int last;              // the last species (1 if ions move, else 0)
 };
-
-constexpr int kSmallTile = kTile / 4;
 
 // Set up the item table of a launch over ne electron and ni ion slots.
 __device__ __forceinline__ void producer_items(Producer &p, long long ne, long long ni) {
     p.ne = ne;
     p.ni = ni;
-    p.last = ni > 0 ? 1 : 0;
-    const long long nl = p.last ? ni : ne;
-    long long cut = nl - (long long)(gridDim.x / 2) * kTile;  // the last half wave goes in quarters
-    cut = cut > 0 ? (cut / kTile) * kTile : 0;
-    p.e_items = p.last ? (ne + kTile - 1) / kTile : 0;
-    p.l_full = cut / kTile;
-    p.total = p.e_items + p.l_full + (nl - cut + kSmallTile - 1) / kSmallTile;
+    p.e_items = (ne + kTile - 1) / kTile;
+    p.total = p.e_items + (ni + kTile - 1) / kTile;
 }
 
 __device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, const Stream &ms, Producer &p,
@@ -1966,16 +1956,9 @@ __device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, cons
             p.pos = p.next * kTile;
             p.end = min(p.pos + kTile, p.ne);
         } else {
-            p.S = p.last;
-            const long long nl = p.last ? p.ni : p.ne;
-            const long long k = p.next - p.e_items;
-            if (k < p.l_full) {
-                p.pos = k * kTile;
-                p.end = p.pos + kTile;
-            } else {
-                p.pos = p.l_full * kTile + (k - p.l_full) * kSmallTile;
-                p.end = min(p.pos + kSmallTile, nl);
-            }
+            p.S = 1;
+            p.pos = (p.next - p.e_items) * kTile;
+            p.end = min(p.pos + kTile, p.ni);
         }
         p.next = (long long)atomicAdd(&R.st->next_item, 1u);
     }

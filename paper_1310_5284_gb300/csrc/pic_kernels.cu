@@ -1162,107 +1162,35 @@ __device__ __forceinline__ unsigned long long chi_count(const Run &R, const Keys
     return z.a + (p.c << 16) - p.a;
 }
 
+// What the tail reads of the run state, loaded by thread 0 together with the
+// staged sums (one round trip) and kept in shared memory.
+struct TailHead {
+    unsigned int B, ok;          // births of the step (capped at the buffer) and those placed
+    unsigned int id_e, id_i;     // next ids
+    long long ne, ni;            // slots before the births
+    int parity;
+    // read for the counters thread 0 rewrites at the end
+    unsigned int nb;
+    long long live[2], n_avg, n_diag;
+    unsigned long long absorbed[2], births_total;
+    double ke_acc[2], pw_acc[2], fe_acc;
+};
+
 // Place the step's births: rank by parent id, append children at the end of
 // both species' slots with consecutive ids, assign their charge (explicit) or
-// count their keys (implicit pass 2, for the sort).
+// count their keys (implicit pass 2, for the sort).  Up to kThreads births
+// each thread holds one record, loaded with the staged sums (`my`); more go
+// through a bucketed ranking in global memory.  The counters are advanced by
+// the caller.
 template <int MODE>
-__device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag) {
-    DevState *st = R.st;
-    __shared__ unsigned int s_B, s_ok;
-    __shared__ long long s_ne, s_ni;
-    if (threadIdx.x == 0) {
-        const unsigned int nb = st->n_births;
-        unsigned int B = nb;
-        if (B > (unsigned int)R.births_cap) {
-            B = (unsigned int)R.births_cap;
-            st->status |= 0x2u;
-        }
-        const long long ne = st->n_slots[0], ni = st->n_slots[1];
-        long long room = R.capacity[0] - ne;
-        if (R.capacity[1] - ni < room) room = R.capacity[1] - ni;
-        unsigned int ok = B;
-        if ((long long)ok > room) {
-            ok = room > 0 ? (unsigned int)room : 0u;
-            st->status |= 0x1u;
-        }
-        s_B = B;
-        s_ok = ok;
-        s_ne = ne;
-        s_ni = ni;
-    }
-    __syncthreads();
-    const unsigned int B = s_B, ok = s_ok;
+__device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag, const TailHead &hd,
+                            const Birth &my) {
+    const unsigned int B = hd.B, ok = hd.ok;
     if (B == 0) return;
-    // rank[b] = number of births with a smaller parent id (ids are unique):
-    // counting pass over 2048 buckets of the parent id's top bits, then a
-    // comparison within the bucket.
-    unsigned int *hist = (unsigned int *)smem;                       // [2048]
-    unsigned int *rank = (unsigned int *)(R.births + R.births_cap);  // [births_cap]
-    uint32_t *sorted = (uint32_t *)(rank + R.births_cap);            // [births_cap]
-    if (B <= 256u) {  // few births: compare directly, parent ids staged in shared memory
-        uint32_t *spid = (uint32_t *)smem;  // [256], padded to a multiple of 4 with the largest id
-        for (unsigned int b = threadIdx.x; b < 256u; b += kThreads) spid[b] = b < B ? R.births[b].pid : 0xffffffffu;
-        __syncthreads();
-        const uint4 *sp4 = (const uint4 *)spid;
-        const unsigned int nq = (B + 3u) / 4u;
-        for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
-            const uint32_t p = spid[b];
-            unsigned int r = 0;
-            for (unsigned int k = 0; k < nq; ++k) {
-                const uint4 v = sp4[k];
-                r += (v.x < p ? 1u : 0u) + (v.y < p ? 1u : 0u) + (v.z < p ? 1u : 0u) + (v.w < p ? 1u : 0u);
-            }
-            rank[b] = r;
-        }
-        __syncthreads();
-    } else {
-    const unsigned int max_pid = st->next_id[0];
-    const int bits = 32 - __clz(max_pid | 1u);
-    const int shift = bits > 11 ? bits - 11 : 0;
-    for (int k = threadIdx.x; k < 2048; k += kThreads) hist[k] = 0u;
-    __syncthreads();
-    for (unsigned int b = threadIdx.x; b < B; b += kThreads)
-        rank[b] = atomicAdd(&hist[R.births[b].pid >> shift], 1u);
-    __syncthreads();
-    {
-        __shared__ unsigned int sc_h[33];
-        constexpr int per = 2048 / kThreads;
-        unsigned int loc[per];
-        unsigned int run = 0;
-        for (int k = 0; k < per; ++k) {
-            loc[k] = hist[threadIdx.x * per + k];
-            run += loc[k];
-        }
-        unsigned int tot;
-        unsigned int ex = block_exclusive_scan<unsigned int>(run, sc_h, tot);
-        for (int k = 0; k < per; ++k) {
-            hist[threadIdx.x * per + k] = ex;  // bucket start
-            ex += loc[k];
-        }
-    }
-    __syncthreads();
-    for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
-        const uint32_t p = R.births[b].pid;
-        sorted[hist[p >> shift] + rank[b]] = p;
-    }
-    __syncthreads();
-    for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
-        const uint32_t p = R.births[b].pid;
-        const unsigned int bk = p >> shift;
-        const unsigned int lo = hist[bk], hi = bk + 1 < 2048u ? hist[bk + 1] : B;
-        unsigned int r = lo;
-        for (unsigned int k = lo; k < hi; ++k) r += sorted[k] < p ? 1u : 0u;
-        rank[b] = r;
-    }
-    __syncthreads();
-    }
-    const int par = st->parity;
-    const Species se = R.buf[par][0], si = R.buf[par][1];
-    const unsigned int id_e = st->next_id[0], id_i = st->next_id[1];
-    for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
-        const unsigned int r = rank[b];
-        if (r >= ok) continue;
-        const Birth bb = R.births[b];
+    const Species se = R.buf[hd.parity][0], si = R.buf[hd.parity][1];
+    const unsigned int id_e = hd.id_e, id_i = hd.id_i;
+    const long long s_ne = hd.ne, s_ni = hd.ni;
+    auto place = [&](const Birth &bb, unsigned int r) {
         const long long je = s_ne + r, ji = s_ni + r;
         se.cell[je] = bb.cell;
         se.off[je] = bb.off;
@@ -1297,16 +1225,69 @@ __device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag
             bin = bin > R.eedf_bins ? R.eedf_bins : (bin < 0 ? 0 : bin);
             atomicAdd(&R.eedf[bin], 1ull);
         }
+    };
+    if (B <= (unsigned int)kThreads) {
+        // rank = number of births with a smaller parent id (ids are unique),
+        // by comparison against all parent ids staged in shared memory (padded
+        // to a multiple of 4 with the largest id)
+        uint32_t *spid = (uint32_t *)smem;  // [kThreads]
+        spid[threadIdx.x] = threadIdx.x < B ? my.pid : 0xffffffffu;
+        __syncthreads();
+        if (threadIdx.x < B) {
+            const uint4 *sp4 = (const uint4 *)spid;
+            const unsigned int nq = (B + 3u) / 4u;
+            const uint32_t p = my.pid;
+            unsigned int r = 0;
+            for (unsigned int k = 0; k < nq; ++k) {
+                const uint4 v = sp4[k];
+                r += (v.x < p ? 1u : 0u) + (v.y < p ? 1u : 0u) + (v.z < p ? 1u : 0u) + (v.w < p ? 1u : 0u);
+            }
+            if (r < ok) place(my, r);
+        }
+        __syncthreads();
+        return;
+    }
+    // many births: counting pass over 2048 buckets of the parent id's top
+    // bits, then a comparison within the bucket
+    unsigned int *hist = (unsigned int *)smem;                       // [2048]
+    unsigned int *rank = (unsigned int *)(R.births + R.births_cap);  // [births_cap]
+    uint32_t *sorted = (uint32_t *)(rank + R.births_cap);            // [births_cap]
+    const int bits = 32 - __clz(id_e | 1u);  // parent ids are below the next electron id
+    const int shift = bits > 11 ? bits - 11 : 0;
+    for (int k = threadIdx.x; k < 2048; k += kThreads) hist[k] = 0u;
+    __syncthreads();
+    for (unsigned int b = threadIdx.x; b < B; b += kThreads)
+        rank[b] = atomicAdd(&hist[R.births[b].pid >> shift], 1u);
+    __syncthreads();
+    {
+        __shared__ unsigned int sc_h[33];
+        constexpr int per = 2048 / kThreads;
+        unsigned int loc[per];
+        unsigned int run = 0;
+        for (int k = 0; k < per; ++k) {
+            loc[k] = hist[threadIdx.x * per + k];
+            run += loc[k];
+        }
+        unsigned int tot;
+        unsigned int ex = block_exclusive_scan<unsigned int>(run, sc_h, tot);
+        for (int k = 0; k < per; ++k) {
+            hist[threadIdx.x * per + k] = ex;  // bucket start
+            ex += loc[k];
+        }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        st->n_slots[0] += ok;
-        st->n_slots[1] += ok;
-        st->n_live[0] += ok;
-        st->n_live[1] += ok;
-        st->next_id[0] += ok;
-        st->next_id[1] += ok;
-        st->births_total += ok;
+    for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
+        const uint32_t p = R.births[b].pid;
+        sorted[hist[p >> shift] + rank[b]] = p;
+    }
+    __syncthreads();
+    for (unsigned int b = threadIdx.x; b < B; b += kThreads) {
+        const Birth bb = R.births[b];
+        const unsigned int bk = bb.pid >> shift;
+        const unsigned int lo = hist[bk], hi = bk + 1 < 2048u ? hist[bk + 1] : B;
+        unsigned int r = lo;
+        for (unsigned int k = lo; k < hi; ++k) r += sorted[k] < bb.pid ? 1u : 0u;
+        if (r < ok) place(bb, r);
     }
     __syncthreads();
 }
@@ -1500,10 +1481,12 @@ __device__ __forceinline__ Volt electrode_volt(const Run &R, long long level) {
 // the notes above the particle kernel).  defer: leave the FP64 conversion of
 // the field, the running averages and the field energy to the next launch
 // (st->pending); otherwise do them here.  vl: the electrode voltage if the
-// caller computed it already (vl_ok), else it is computed here.
+// caller computed it already (vl_ok), else it is computed here.  fe_acc: the
+// run's sum of E_c^2 of the field this launch pushed with (read by the caller
+// with the rest of the run state; a deferring explicit tail reports it).
 template <int MODE>
 __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long level, bool accumulate,
-                           bool cursors, bool defer, Volt vl, bool vl_ok) {
+                           bool cursors, bool defer, Volt vl, bool vl_ok, double fe_acc) {
     DevState *st = R.st;
     const int n = R.n_cells, n1 = n + 1;
     __shared__ long long sc_x[kThreads / 32], sc_h[kThreads / 32];
@@ -1724,7 +1707,7 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
         if (threadIdx.x == 0) {
             // the energy of the field this launch pushed with was summed by the
             // launch's deferred-work blocks into fe_acc
-            if (MODE == kExplicitEC || MODE == kExplicitMC) st->field_energy_push = R.eps0_dx_half * st->fe_acc;
+            if (MODE == kExplicitEC || MODE == kExplicitMC) st->field_energy_push = R.eps0_dx_half * fe_acc;
             st->fe_acc = 0.0;
             st->pending = (accumulate ? 1u : 0u) | 2u;
         }
@@ -1806,14 +1789,39 @@ __device__ void tail_cursors(const Run &R, Keys K) {
 template <int MODE>
 __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, unsigned char *stage, bool diag,
                                           bool defer, Volt vl, bool vl_ok) {
+    using MI = ModeInfo<MODE>;
+    constexpr bool births = MODE == kExplicitEC || MODE == kExplicitMC || MI::pass2;
     DevState *st = R.st;
+    __shared__ TailHead s_hd;
     const long long step = st->step;
-    // Copy the per-key sums of both species into shared memory with one batch
-    // of independent loads; everything after reads (and the births add to)
-    // this copy through Ks.  The global sums are cleared for the next launch
-    // right behind the loads.
+    // One batch of independent loads: the per-key sums of both species (into
+    // shared memory; everything after reads, and the births add to, this copy
+    // through Ks; the global sums are cleared right behind the loads), one
+    // birth record per thread, and the run-state words thread 0 updates at
+    // the end.
     const int n1 = R.n_cells + 1;
     Keys Ks;
+    TailHead &hd = s_hd;
+    if (threadIdx.x == 0) {
+        hd.nb = st->n_births;
+        hd.ne = st->n_slots[0];
+        hd.ni = st->n_slots[1];
+        hd.id_e = st->next_id[0];
+        hd.id_i = st->next_id[1];
+        hd.parity = (int)st->parity;
+        hd.births_total = st->births_total;
+        hd.n_avg = st->n_avg;
+        hd.n_diag = st->n_diag;
+        hd.fe_acc = st->fe_acc;
+        for (int S = 0; S < 2; ++S) {
+            hd.live[S] = st->n_live[S];
+            hd.absorbed[S] = st->absorbed_step[S];
+            hd.ke_acc[S] = st->ke_x_acc[S];
+            hd.pw_acc[S] = st->power_acc[S];
+        }
+    }
+    Birth my = {};
+    if (births && threadIdx.x < R.births_cap) my = R.births[threadIdx.x];  // beyond the step's count: unused
     {
         unsigned long long *base = (unsigned long long *)stage;
         for (int S = 0; S < 2; ++S) {
@@ -1846,28 +1854,55 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
                 }
             }
         }
-        __syncthreads();
     }
-    if (MODE == kExplicitEC || MODE == kExplicitMC || ModeInfo<MODE>::pass2) tail_births<MODE>(R, Ks, smem, diag);
-    if (MODE == kExplicitEC || MODE == kExplicitMC) tail_field<MODE>(R, Ks, smem, step + 1, true, true, defer, vl, vl_ok);
-    if (ModeInfo<MODE>::pass1) tail_field<MODE>(R, Ks, smem, step + 1, true, false, defer, vl, vl_ok);
-    if (MODE == kDepositEC || MODE == kDepositMC) tail_field<MODE>(R, Ks, smem, step, false, true, defer, vl, vl_ok);
-    if (ModeInfo<MODE>::pass2) tail_cursors(R, Ks);
+    unsigned int status_bits = 0u;
+    if (threadIdx.x == 0) {
+        // births recorded beyond the buffer are lost; those beyond the slots' room too
+        unsigned int B = births ? hd.nb : 0u;
+        if (B > (unsigned int)R.births_cap) {
+            B = (unsigned int)R.births_cap;
+            status_bits |= 0x2u;
+        }
+        long long room = R.capacity[0] - hd.ne;
+        if (R.capacity[1] - hd.ni < room) room = R.capacity[1] - hd.ni;
+        unsigned int ok = B;
+        if ((long long)ok > room) {
+            ok = room > 0 ? (unsigned int)room : 0u;
+            status_bits |= 0x1u;
+        }
+        hd.B = B;
+        hd.ok = ok;
+    }
+    __syncthreads();
+    if (births) tail_births<MODE>(R, Ks, smem, diag, hd, my);
+    if (MODE == kExplicitEC || MODE == kExplicitMC) tail_field<MODE>(R, Ks, smem, step + 1, true, true, defer, vl, vl_ok, hd.fe_acc);
+    if (MI::pass1) tail_field<MODE>(R, Ks, smem, step + 1, true, false, defer, vl, vl_ok, hd.fe_acc);
+    if (MODE == kDepositEC || MODE == kDepositMC) tail_field<MODE>(R, Ks, smem, step, false, true, defer, vl, vl_ok, hd.fe_acc);
+    if (MI::pass2) tail_cursors(R, Ks);
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (ModeInfo<MODE>::push) {
+        const unsigned int ok = hd.ok;
+        if (births) {
+            st->n_slots[0] = hd.ne + ok;
+            st->n_slots[1] = hd.ni + ok;
+            st->next_id[0] = hd.id_e + ok;
+            st->next_id[1] = hd.id_i + ok;
+            st->births_total = hd.births_total + ok;
+        }
+        if (MI::push) {
             for (int S = 0; S < 2; ++S) {
-                st->ke_x[S] = st->ke_x_acc[S];
-                st->power[S] = st->power_acc[S];
+                st->ke_x[S] = hd.ke_acc[S];
+                st->power[S] = hd.pw_acc[S];
                 st->ke_x_acc[S] = 0.0;
                 st->power_acc[S] = 0.0;
-                st->n_live[S] -= (long long)st->absorbed_step[S];
+                st->n_live[S] = hd.live[S] + (long long)ok - (long long)hd.absorbed[S];
                 st->absorbed_step[S] = 0ull;
             }
             st->step = step + 1;
-            st->n_avg += 1;
-            if (diag) st->n_diag += 1;
+            st->n_avg = hd.n_avg + 1;
+            if (diag) st->n_diag = hd.n_diag + 1;
         }
+        if (status_bits) atomicOr(&st->status, status_bits);
         st->n_births = 0u;
         st->next_item = 0u;
         st->blocks_done = 0u;
@@ -3122,7 +3157,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_adj_fwd(Run R, AdjFwd 
     __threadfence();
     Run Rt = R;
     Rt.e_gather = A.e_out;
-    tail_field<kDepositEC>(Rt, global_keys(R), smem, A.level, false, false, false, Volt{0.0, 0.0f, 0.0f}, false);
+    tail_field<kDepositEC>(Rt, global_keys(R), smem, A.level, false, false, false, Volt{0.0, 0.0f, 0.0f}, false, 0.0);
     tail_reset(R);
     __syncthreads();
     if (threadIdx.x == 0) R.st->blocks_done = 0u;

@@ -2012,7 +2012,9 @@ __device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, cons
             p.pos = (p.next - p.e_items) * kTile;
             p.end = min(p.pos + kTile, p.ni);
         }
-        p.next = (long long)atomicAdd(&R.st->next_item, 1u);
+        // the first item of every block is its own index; the counter hands
+        // out the rest
+        p.next = (long long)atomicAdd(&R.st->next_item, 1u) + gridDim.x;
     }
     const int n = (int)min((long long)kTile, p.end - p.pos);
     ms.S[stage] = p.S;
@@ -2112,7 +2114,7 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
         p.pos = p.end = 0;
         producer_items(p, st->n_slots[0], R.ions_mobile ? st->n_slots[1] : 0);
         p.S = 0;
-        p.next = (long long)atomicAdd(&st->next_item, 1u);
+        p.next = blockIdx.x;  // no round trip to L2 before the first copy
         for (int k = 0; k < kStages - 1; ++k)
             producer_issue(R, g, ms, p, par, (unsigned int)k, need_id, mode_fields, MI::implicit);
         // the electrode voltage the tail will need, while the first copies fly
@@ -2298,18 +2300,24 @@ __device__ void sort_chunk(const Run &R, int par, int S, long long b, long long 
             id[q] = ok ? src.id[i] : 0u;
             ab[q] = (ok && implicit) ? src.abar[i] : 0.0f;
         }
+        // the cursor claims of all V groups are issued before any result is
+        // used: one round trip to L2 per batch, not V
+        int key[V];
+        unsigned int peers[V], claim[V];
 #pragma unroll
         for (int q = 0; q < V; ++q) {
             uint32_t a;
-            const int key = cell[q] < 0 ? -1 : (mc ? deposit_key_s1(cell[q], off[q], a) : deposit_key_s2(cell[q], off[q], a));
-            const unsigned int peers = __match_any_sync(FULL_MASK, key);
-            if (key >= 0) {
-                const int leader = __ffs(peers) - 1;
-                const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
-                unsigned int base_pos = 0;
-                if (lane == leader) base_pos = atomicAdd(&R.cursor[S][key], (unsigned int)__popc(peers));
-                base_pos = __shfl_sync(peers, base_pos, leader);
-                const unsigned int pos = base_pos + rank;
+            key[q] = cell[q] < 0 ? -1 : (mc ? deposit_key_s1(cell[q], off[q], a) : deposit_key_s2(cell[q], off[q], a));
+            peers[q] = __match_any_sync(FULL_MASK, key[q]);
+            claim[q] = 0u;
+            if (key[q] >= 0 && lane == __ffs(peers[q]) - 1)
+                claim[q] = atomicAdd(&R.cursor[S][key[q]], (unsigned int)__popc(peers[q]));
+        }
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const unsigned int base_pos = __shfl_sync(FULL_MASK, claim[q], __ffs(peers[q]) - 1);
+            if (key[q] >= 0) {
+                const unsigned int pos = base_pos + __popc(peers[q] & ((1u << lane) - 1u));
                 dst.cell[pos] = cell[q];
                 dst.off[pos] = off[q];
                 dst.vx[pos] = vx[q];

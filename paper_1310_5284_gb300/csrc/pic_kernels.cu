@@ -2101,27 +2101,33 @@ __device__ void stream_flush(const Run &R, const SmemMain &sm, int S, bool diag,
     }
 }
 
+// Thread 0, first thing in the launch: set up the block's work items and
+// issue the copies of its first tiles (its first item is its own index), so
+// they travel while the block reads the grid and clears its accumulators.
+template <int MODE>
+__device__ __forceinline__ void stream_prime(const Run &R, const Ring &g, const Stream &ms, Producer &p) {
+    using MI = ModeInfo<MODE>;
+    const DevState *st = R.st;
+    const int par = st->parity;
+    p.pos = p.end = 0;
+    producer_items(p, st->n_slots[0], R.ions_mobile ? st->n_slots[1] : 0);
+    p.S = 0;
+    p.next = blockIdx.x;
+    for (int k = 0; k < kStages - 1; ++k)
+        producer_issue(R, g, ms, p, par, (unsigned int)k, MI::push && R.mcc, MI::loads_v ? 3 : 2, MI::implicit);
+}
+
+// The block's stream of tiles (primed by stream_prime; the caller's barrier
+// separates the two).
 template <int MODE>
 __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, const Stream &ms, Producer &p,
-                             bool diag, long long step, Volt *vl) {
+                             bool diag, long long step) {
     using MI = ModeInfo<MODE>;
     DevState *st = R.st;
     const int par = st->parity;
     const Species sp[2] = {R.buf[par][0], R.buf[par][1]};
     const bool need_id = MI::push && R.mcc;
     const int mode_fields = MI::loads_v ? 3 : 2;
-    if (threadIdx.x == 0) {
-        p.pos = p.end = 0;
-        producer_items(p, st->n_slots[0], R.ions_mobile ? st->n_slots[1] : 0);
-        p.S = 0;
-        p.next = blockIdx.x;  // no round trip to L2 before the first copy
-        for (int k = 0; k < kStages - 1; ++k)
-            producer_issue(R, g, ms, p, par, (unsigned int)k, need_id, mode_fields, MI::implicit);
-        // the electrode voltage the tail will need, while the first copies fly
-        // (FP64 is slow here; only the last block's value is used)
-        *vl = electrode_volt(R, (MODE == kDepositEC || MODE == kDepositMC) ? step : step + 1);
-    }
-    __syncthreads();
     Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
     float kx = 0.0f, pw = 0.0f;  // the per-particle sums stay in registers
     int cur = -1;
@@ -2212,6 +2218,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
         for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1u);
         s_uses = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        stream_prime<MODE>(R, g, ms, s_prod);
     }
     const long long step = st->step;
     const bool diag = MI::push && R.diag_period > 0 && (step % R.diag_period) == 0;
@@ -2228,14 +2235,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
         for (int k = threadIdx.x; k < n; k += kThreads) sm.heat[k] = 0.0f;
         for (int k = threadIdx.x; k <= R.eedf_bins; k += kThreads) sm.eedf[k] = 0u;
     }
-    if (threadIdx.x == 0) *sm.q.n = 0u;
+    if (threadIdx.x == 0) {
+        *sm.q.n = 0u;
+        // the electrode voltage the tail will need, while the first copies fly
+        // (FP64 is slow here; only the last block's value is used)
+        s_vl = electrode_volt(R, (MODE == kDepositEC || MODE == kDepositMC) ? step : step + 1);
+    }
     __syncthreads();
     // the FP64 work the previous tail left (a few blocks; the others start streaming)
     {
         const unsigned int pend = st->pending;
         if (pend && blockIdx.x < kDeferParts) deferred_work(R, pend, (int)blockIdx.x, kDeferParts);
     }
-    stream_block<MODE>(R, sm, g, ms, s_prod, diag, step, &s_vl);
+    stream_block<MODE>(R, sm, g, ms, s_prod, diag, step);
     if (diag) {
         for (int k = threadIdx.x; k <= R.eedf_bins; k += kThreads)
             if (sm.eedf[k]) atomicAdd(&R.eedf[k], (unsigned long long)sm.eedf[k]);

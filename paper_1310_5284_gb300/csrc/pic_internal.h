@@ -22,7 +22,7 @@ namespace pic {
 #define PIC_UNROLL 4
 #endif
 #ifndef PIC_MIN_BLOCKS
-#define PIC_MIN_BLOCKS 3
+#define PIC_MIN_BLOCKS 4
 #endif
 
 constexpr int kMaxCells = 1024;          // grid lives in shared memory

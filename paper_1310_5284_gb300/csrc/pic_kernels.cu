@@ -472,7 +472,7 @@ __device__ void block_sum2(double &x, double &y, double *scratch /*[2*kThreads/3
 // full warps.  The queue is drained before a tile whenever fewer than a
 // tile's worth of entries are free, so it cannot overflow.
 #ifndef PIC_QDRAIN
-#define PIC_QDRAIN 512
+#define PIC_QDRAIN 128
 #endif
 constexpr unsigned int kQueueDrainAbove = PIC_QDRAIN;
 constexpr int kQueue = (int)kQueueDrainAbove + kThreads * kUnroll;  // + one tile

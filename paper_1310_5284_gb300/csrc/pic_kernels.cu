@@ -2351,7 +2351,10 @@ __device__ void sort_finish(const Run &R) {
     st->sort_blocks_done = 0u;
 }
 
-__global__ void __launch_bounds__(kThreads) k_sort(Run R) {
+#ifndef PIC_SORT_MIN_BLOCKS
+#define PIC_SORT_MIN_BLOCKS 1
+#endif
+__global__ void __launch_bounds__(kThreads, PIC_SORT_MIN_BLOCKS) k_sort(Run R) {
     __shared__ bool s_last;
     DevState *st = R.st;
     const int par = st->parity;

@@ -426,3 +426,35 @@ def test_set_particles_rejects_off_grid_and_applies_nothing(bad):
     gpu.set_particles("e", st)  # the corrected upload goes through
     assert gpu.get_particles("e")["id"].size == 4000
     gpu.close()
+
+
+def test_high_selection_implicit_run_keeps_the_drain_in_step():
+    """A direct-implicit discharge at omega_p dt = 2 selects about a third of
+    its particles for a collision every step, so the collision queue crosses
+    its drain mark in the middle of a block's stream many times per launch.
+    The drain decision must be the same in every thread of a block (a block
+    whose warps disagreed entered different barriers and faulted the GPU on
+    exactly this configuration, run 47 of the batched sweep).  Bar: fifteen
+    steps through the single-run path (one sort among them) end with a clean
+    status word, particle counts conserved by the tallies, and the same
+    particles as a second run of the same configuration."""
+    from paper_1310_5284_gb300.batch import discharge_from_spec
+
+    cfg = discharge_from_spec(workloads.batch_configs(256)[47])
+    assert cfg["scheme"] == "ec_implicit" and cfg["np_init"] > 1_500_000
+    runs = []
+    for _ in range(2):
+        gpu = gpu_sim(cfg)
+        gpu.step(15)
+        d = gpu.diag()
+        assert gpu.status() == 0
+        assert d["step"] == 15
+        assert sum(d["coll"]) > 0.05 * 15 * cfg["np_init"]  # selections, real and null
+        born = d["births"]
+        lost = [d["wall_count"][k][0] + d["wall_count"][k][1] for k in range(2)]
+        for k in range(2):
+            assert d["count"][k] == cfg["np_init"] + born - lost[k]
+        runs.append(by_id(gpu.get_particles("e")))
+        gpu.close()
+    for key in ("id", "cell", "off", "vx", "vy", "vz"):
+        assert np.array_equal(runs[0][key], runs[1][key]), key

@@ -218,7 +218,7 @@ __device__ __forceinline__ bool collide_ion_body(const Run &R, uint4 w, uint32_t
 
 // A particle crossed an electrode (Sec. 3): tally its number and energy.
 __device__ __forceinline__ void absorb_body(const Run &R, int S, int wall, float vx, float vy, float vz) {
-    const float en = R.half_m_over_e[S] * (vx * vx + vy * vy + vz * vz);
+    const float en = (S ? R.half_m_over_e[1] : R.half_m_over_e[0]) * (vx * vx + vy * vy + vz * vz);
     atomicAdd(&R.st->wall_count[S][wall], 1ull);
     atomicAdd(&R.st->wall_energy[S][wall], (double)en);
     atomicAdd(&R.st->absorbed_step[S], 1ull);
@@ -618,12 +618,25 @@ __device__ __forceinline__ void drain_q(const Run &R, const SmemMain &sm, Specie
         drain_collisions<S>(R, sm, sp, step, diag, t);
 }
 
+// The per-species constants of the push, selected once per tile: the
+// particle code exists once for both species (two copies would double the
+// hot loop's instruction footprint).
+struct SpK {
+    float qm, qw, qm_dt;
+    uint32_t thr;
+    int S;
+};
+
+__device__ __forceinline__ SpK species_k(const Run &R, int S) {
+    return S ? SpK{R.qm[1], R.qw[1], R.qm_dt[1], R.thr[1], 1} : SpK{R.qm[0], R.qw[0], R.qm_dt[0], R.thr[0], 0};
+}
+
 // ---------------------------------------------------------------------------
 // One particle of each mode.  Returns its deposit key (-1: none) and value a.
 // On return cell < 0 marks an absorbed particle.
 // ---------------------------------------------------------------------------
-template <int MODE, int S, bool INL>
-__device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, const Species &sp,
+template <int MODE, bool INL>
+__device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, const Species &sp, const SpK &k,
                                              long long idx, int &cell, float &off, float &vx,
                                              float &abar, uint32_t id, bool sel, bool diag, long long step,
                                              Tally &t, float &kx, float &pw, uint32_t &a_out) {
@@ -653,20 +666,20 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         // corrector with E^{n+1} at x~ (S_1 from the cell-centred field, or
         // linear from the node field of the momentum-conserving scheme)
         e_field = !inside ? 0.0f : (MI::mc ? (1.0f - s) * sm.e[c] + s * sm.e[c + 1] : gather_ec(sm.e, c, s));
-        const float acc = R.qm[S] * e_field;
+        const float acc = k.qm * e_field;
         v_new = fmaf(R.half_dt, acc, vt);
-        if (diag && inside) atomicAdd(&sm.heat[c], R.qw[S] * e_field * 0.5f * (v_old + v_new));
+        if (diag && inside) atomicAdd(&sm.heat[c], k.qw * e_field * 0.5f * (v_old + v_new));
         s = fmaf(acc, R.half_dt2_dx, s);
         abar = 0.5f * (abar + acc);
     } else {
         // explicit leapfrog with E^n at x^n (Sec. 2 schemes (1), (2))
         e_field = MI::mc ? (1.0f - off) * sm.e[cell] + off * sm.e[cell + 1] : gather_ec(sm.e, cell, off);
-        v_new = fmaf(R.qm_dt[S], e_field, vx);
-        if (diag) atomicAdd(&sm.heat[cell], R.qw[S] * e_field * 0.5f * (v_old + v_new));
+        v_new = fmaf(k.qm_dt, e_field, vx);
+        if (diag) atomicAdd(&sm.heat[cell], k.qw * e_field * 0.5f * (v_old + v_new));
         s = fmaf(v_new, R.dt_dx, off);
     }
     kx += 0.5f * (v_old * v_old + v_new * v_new);  // kept in registers: t lives in memory
-    pw += R.qw[S] * e_field * 0.5f * (v_old + v_new);
+    pw += k.qw * e_field * 0.5f * (v_old + v_new);
     if (!(fabsf(s) < 1.0e6f)) s = (float)(2 * N + 2);
     renormalise(c, s);
     vx = v_new;
@@ -675,7 +688,7 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
     if (R.periodic) {
         if (c < 0 || c >= N) c = ((c % N) + N) % N;
     } else if (c < 0 || c >= N) {
-        absorb_p<INL>(R, S, c < 0 ? 0 : 1, v_new, sp.vy[idx], sp.vz[idx]);
+        absorb_p<INL>(R, k.S, c < 0 ? 0 : 1, v_new, sp.vy[idx], sp.vz[idx]);
         cell = -1;
         return -1;
     }
@@ -695,7 +708,7 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
             atomicOr(&R.st->status, 0x8u);
         }
     }
-    if (S == 0 && diag && R.eedf_bins > 0 && !queued) eedf_sample(R, sm, vx, sp.vy[idx], sp.vz[idx]);
+    if (k.S == 0 && diag && R.eedf_bins > 0 && !queued) eedf_sample(R, sm, vx, sp.vy[idx], sp.vz[idx]);
     if (MI::mc) return deposit_key_s1(c, s, a_out);
     return deposit_key_s2(c, s, a_out);
 }
@@ -869,14 +882,13 @@ __device__ __forceinline__ void ring_particles(const Ring &g, int stage, int s0,
 // The null-collision selections of a thread's particles, one Philox draw
 // each (only the first word decides), computed side by side without
 // branches so that the independent multiply chains overlap.
-template <int S>
-__device__ __forceinline__ void mcc_select(const Run &R, const uint32_t (&id)[kUnroll], long long step,
-                                           bool (&sel)[kUnroll]) {
+__device__ __forceinline__ void mcc_select(const Run &R, const uint32_t (&id)[kUnroll], long long step, int S,
+                                           uint32_t thr, bool (&sel)[kUnroll]) {
     uint32_t x[kUnroll];
 #pragma unroll
     for (int q = 0; q < kUnroll; ++q) x[q] = draw(R, id[q], step, S, kTagMcc, 0).x;
 #pragma unroll
-    for (int q = 0; q < kUnroll; ++q) sel[q] = (x[q] >> 8) < R.thr[S];
+    for (int q = 0; q < kUnroll; ++q) sel[q] = (x[q] >> 8) < thr;
 }
 
 // Issue the copies of tile t (block-relative tile counter u) of segment
@@ -950,7 +962,8 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
         uint32_t id[U];
         ring_particles<MODE>(g, stage, s0, len - i0, need_id, cell, off, vx, abar, id);
         bool sel[U] = {};
-        if (need_id) mcc_select<S>(R, id, step, sel);
+        const SpK k = species_k(R, S);
+        if (need_id) mcc_select(R, id, step, S, k.thr, sel);
         int key[U];
         uint32_t a[U];
 #pragma unroll
@@ -958,7 +971,7 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
             a[q] = 0u;
             key[q] = -1;
             if (cell[q] < 0) continue;  // beyond the segment, or a hole left by absorption
-            key[q] = step_particle<MODE, S, false>(R, sm, sp, (long long)(i0 + q), cell[q], off[q], vx[q],
+            key[q] = step_particle<MODE, false>(R, sm, sp, k, (long long)(i0 + q), cell[q], off[q], vx[q],
                                             abar[q], id[q], sel[q], diag, step, t, kx, pw, a[q]);
         }
         if (MI::push) {
@@ -2036,8 +2049,8 @@ __device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, cons
 
 // One staged tile of species S: n particles from slot o.  Indices handed to
 // step_particle and the collision queue are absolute slots of sp.
-template <int MODE, int S>
-__device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, const Ring &g, int stage,
+template <int MODE>
+__device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, const Ring &g, int stage, int S,
                                             const Species &sp, long long o, int len, bool need_id, bool diag,
                                             long long step, Tally &t, float &kx, float &pw) {
     constexpr int U = kUnroll;
@@ -2049,7 +2062,8 @@ __device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, co
     uint32_t id[U];
     ring_particles<MODE>(g, stage, i0, len - i0, need_id, cell, off, vx, abar, id);
     bool sel[U] = {};
-    if (need_id) mcc_select<S>(R, id, step, sel);
+    const SpK k = species_k(R, S);
+    if (need_id) mcc_select(R, id, step, S, k.thr, sel);
     int key[U];
     uint32_t a[U];
 #pragma unroll
@@ -2057,7 +2071,7 @@ __device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, co
         a[q] = 0u;
         key[q] = -1;
         if (cell[q] < 0) continue;  // beyond the tile, or a hole left by absorption
-        key[q] = step_particle<MODE, S, true>(R, sm, sp, o + i0 + q, cell[q], off[q], vx[q], abar[q], id[q],
+        key[q] = step_particle<MODE, true>(R, sm, sp, k, o + i0 + q, cell[q], off[q], vx[q], abar[q], id[q],
                                         sel[q], diag, step, t, kx, pw, a[q]);
     }
     if (MI::push) {
@@ -2175,10 +2189,8 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
             for (unsigned int w = u + 1; w < u + kStages; ++w)
                 if (ms.n[w % kStages] > 0) mbar_wait(R, &g.bar[w % kStages], (w / kStages) & 1u);
             gave_up = true;
-        } else if (S == 0) {
-            stream_tile<MODE, 0>(R, sm, g, stage, sp[0], o, n, need_id, diag, step, t, kx, pw);
         } else {
-            stream_tile<MODE, 1>(R, sm, g, stage, sp[1], o, n, need_id, diag, step, t, kx, pw);
+            stream_tile<MODE>(R, sm, g, stage, S, S ? sp[1] : sp[0], o, n, need_id, diag, step, t, kx, pw);
         }
         added += n;
         // The stage is free again.  The thread that queued the tile's last

@@ -2303,7 +2303,10 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Run R) {
 // the cursor of their key (warp-aggregated: lanes sharing a key take
 // consecutive positions from one atomic).
 __device__ void sort_chunk(const Run &R, int par, int S, long long b, long long e) {
-    constexpr int V = 4;  // particles per thread in flight: all their loads are issued first
+#ifndef PIC_SORT_V
+#define PIC_SORT_V 4
+#endif
+    constexpr int V = PIC_SORT_V;  // particles per thread in flight: all their loads are issued first
     const bool mc = R.scheme == 1 || R.scheme == 3;
     const bool implicit = R.scheme >= 2;
     const int lane = threadIdx.x & 31;

@@ -93,6 +93,11 @@ struct DevState {
     unsigned int pending;
     unsigned int check;            // pic_set_particles: nonzero if an uploaded particle is off the grid
     double fe_acc;                 // sum of E_c^2 of the field the next push uses
+    // Electrode voltage of the field the running particle launch's tail
+    // solves (one block stores it at launch start; the tail reads it), with
+    // its double-word split.
+    double volt_v;
+    float volt_hi, volt_lo;
 };
 
 // State of a batched launch sequence (one per batch, in its arena).

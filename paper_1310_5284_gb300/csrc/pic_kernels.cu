@@ -1187,6 +1187,8 @@ struct TailHead {
     long long live[2], n_avg, n_diag;
     unsigned long long absorbed[2], births_total;
     double ke_acc[2], pw_acc[2], fe_acc;
+    double vl_v;                 // electrode voltage stored at launch start
+    float vl_hi, vl_lo;
 };
 
 // Place the step's births: rank by parent id, append children at the end of
@@ -1809,8 +1811,10 @@ template <int MODE>
 // dry: a warming pass by a block that is not the last (no global writes;
 // phases [ph_lo, ph_hi) of 0 stage, 1 births, 2 field, 3 cursors and counters),
 // so that the last block finds this code in L2 instead of fetching it cold.
+// vl_state: the electrode voltage was stored in the run state at launch start
+// (else the field phase computes it).
 __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, unsigned char *stage, bool diag,
-                                          bool defer, Volt vl, bool vl_ok, bool dry = false, int ph_lo = 0,
+                                          bool defer, bool vl_state, bool dry = false, int ph_lo = 0,
                                           int ph_hi = 4) {
     using MI = ModeInfo<MODE>;
     constexpr bool births = MODE == kExplicitEC || MODE == kExplicitMC || MI::pass2;
@@ -1836,6 +1840,11 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
         hd.n_avg = st->n_avg;
         hd.n_diag = st->n_diag;
         hd.fe_acc = st->fe_acc;
+        if (vl_state) {
+            hd.vl_v = st->volt_v;
+            hd.vl_hi = st->volt_hi;
+            hd.vl_lo = st->volt_lo;
+        }
         for (int S = 0; S < 2; ++S) {
             hd.live[S] = st->n_live[S];
             hd.absorbed[S] = st->absorbed_step[S];
@@ -1900,11 +1909,12 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
     __syncthreads();
     if (births && ph_lo <= 1 && 1 < ph_hi) tail_births<MODE>(R, Ks, smem, diag, hd, my, dry);
     if (ph_lo <= 2 && 2 < ph_hi) {
+        const Volt vl = {hd.vl_v, hd.vl_hi, hd.vl_lo};  // read only if vl_state
         if (MODE == kExplicitEC || MODE == kExplicitMC)
-            tail_field<MODE>(R, Ks, smem, step + 1, true, true, defer, vl, vl_ok, hd.fe_acc, dry);
-        if (MI::pass1) tail_field<MODE>(R, Ks, smem, step + 1, true, false, defer, vl, vl_ok, hd.fe_acc, dry);
+            tail_field<MODE>(R, Ks, smem, step + 1, true, true, defer, vl, vl_state, hd.fe_acc, dry);
+        if (MI::pass1) tail_field<MODE>(R, Ks, smem, step + 1, true, false, defer, vl, vl_state, hd.fe_acc, dry);
         if (MODE == kDepositEC || MODE == kDepositMC)
-            tail_field<MODE>(R, Ks, smem, step, false, true, defer, vl, vl_ok, hd.fe_acc, dry);
+            tail_field<MODE>(R, Ks, smem, step, false, true, defer, vl, vl_state, hd.fe_acc, dry);
     }
     if (ph_hi <= 3) return;  // a warming pass ends here
     if (MI::pass2) tail_cursors(R, Ks);
@@ -1942,8 +1952,8 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
 // kernel inlines the body.
 template <int MODE>
 __device__ __noinline__ void tail(const Run &R, unsigned char *smem, unsigned char *stage, bool diag, bool defer,
-                                  Volt vl, bool vl_ok) {
-    tail_body<MODE>(R, smem, stage, diag, defer, vl, vl_ok);
+                                  bool vl_state) {
+    tail_body<MODE>(R, smem, stage, diag, defer, vl_state);
 }
 
 // The block's share of the particles: blocks are split between the species in
@@ -1994,9 +2004,12 @@ struct Stream {
 // quarter tiles, so that blocks finish closer together, measured 7 % slower:
 // a quarter tile leaves three quarters of the block idle.)
 struct Producer {
-    long long pos, end, next, total, ne, ni;
+    long long pos, end, total, ne, ni;
     long long e_items;     // items of species 0
     int S;
+    int k;                 // items started so far
+    bool inflight;         // a claim on the counter is held in the caller's register
+    bool done;
 };
 
 // Set up the item table of a launch over ne electron and ni ion slots.
@@ -2007,27 +2020,44 @@ __device__ __forceinline__ void producer_items(Producer &p, long long ne, long l
     p.total = p.e_items + (ni + kTile - 1) / kTile;
 }
 
+// Items: a block's first two are blockIdx.x and blockIdx.x + gridDim.x; the
+// counter hands out the rest.  The claim for the item after the one being
+// started is taken here into `claim`, a register of the calling thread, and
+// read at the next item start, a tile later: the atomic's latency is never
+// waited on (a claim kept in shared memory would stall the issuing warp on
+// the store of its result).  can_claim: `claim` outlives this call.
 __device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, const Stream &ms, Producer &p,
                                                int par, unsigned int u, bool need_id, int mode_fields,
-                                               bool implicit) {
+                                               bool implicit, unsigned int &claim, bool can_claim) {
     const int stage = (int)(u % kStages);
     if (p.pos >= p.end) {
-        if (p.next >= p.total) {
+        long long it = p.total;
+        if (!p.done) {
+            if (p.k < 2)
+                it = (long long)blockIdx.x + (long long)p.k * gridDim.x;
+            else
+                it = (long long)(p.inflight ? claim : atomicAdd(&R.st->next_item, 1u)) + 2ll * gridDim.x;
+            ++p.k;
+            p.inflight = false;
+            p.done = it >= p.total;
+        }
+        if (p.done) {
             ms.n[stage] = 0;
             return;
         }
-        if (p.next < p.e_items) {
+        if (it < p.e_items) {
             p.S = 0;
-            p.pos = p.next * kTile;
+            p.pos = it * kTile;
             p.end = min(p.pos + kTile, p.ne);
         } else {
             p.S = 1;
-            p.pos = (p.next - p.e_items) * kTile;
+            p.pos = (it - p.e_items) * kTile;
             p.end = min(p.pos + kTile, p.ni);
         }
-        // the first item of every block is its own index; the counter hands
-        // out the rest
-        p.next = (long long)atomicAdd(&R.st->next_item, 1u) + gridDim.x;
+        if (p.k >= 2 && can_claim) {
+            claim = atomicAdd(&R.st->next_item, 1u);
+            p.inflight = true;
+        }
     }
     const int n = (int)min((long long)kTile, p.end - p.pos);
     ms.S[stage] = p.S;
@@ -2116,8 +2146,8 @@ __device__ void stream_flush(const Run &R, const SmemMain &sm, int S, bool diag,
 }
 
 // Thread 0, first thing in the launch: set up the block's work items and
-// issue the copies of its first tiles (its first item is its own index), so
-// they travel while the block reads the grid and clears its accumulators.
+// issue the copies of its first tiles (static items: no wait on the counter),
+// so they travel while the block reads the grid and clears its accumulators.
 template <int MODE>
 __device__ __forceinline__ void stream_prime(const Run &R, const Ring &g, const Stream &ms, Producer &p) {
     using MI = ModeInfo<MODE>;
@@ -2126,9 +2156,12 @@ __device__ __forceinline__ void stream_prime(const Run &R, const Ring &g, const 
     p.pos = p.end = 0;
     producer_items(p, st->n_slots[0], R.ions_mobile ? st->n_slots[1] : 0);
     p.S = 0;
-    p.next = blockIdx.x;
+    p.k = 0;
+    p.inflight = p.done = false;
+    unsigned int unused = 0u;
     for (int k = 0; k < kStages - 1; ++k)
-        producer_issue(R, g, ms, p, par, (unsigned int)k, MI::push && R.mcc, MI::loads_v ? 3 : 2, MI::implicit);
+        producer_issue(R, g, ms, p, par, (unsigned int)k, MI::push && R.mcc, MI::loads_v ? 3 : 2, MI::implicit,
+                       unused, false);
 }
 
 // The block's stream of tiles (primed by stream_prime; the caller's barrier
@@ -2147,6 +2180,7 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
     int cur = -1;
     long long added = 0;
     bool gave_up = false;
+    unsigned int claim = 0u;  // thread 0: the counter claim in flight
     // Set by the barrier that ends a tile, the same in every thread: the tile
     // left the queue above its drain mark, or some thread's wait gave up.
     bool flag = false;
@@ -2183,7 +2217,7 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
         cur = S;
         const long long o = ms.o[stage];
         if (threadIdx.x == 0)
-            producer_issue(R, g, ms, p, par, u + kStages - 1, need_id, mode_fields, MI::implicit);
+            producer_issue(R, g, ms, p, par, u + kStages - 1, need_id, mode_fields, MI::implicit, claim, true);
         if (!mbar_wait(R, &g.bar[stage], (u / kStages) & 1u)) {
             // give up, but not before the copies already issued have landed (bounded)
             for (unsigned int w = u + 1; w < u + kStages; ++w)
@@ -2214,7 +2248,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     __shared__ int s_ms_S[kStages], s_ms_n[kStages];
     __shared__ long long s_ms_o[kStages];
     __shared__ Producer s_prod;
-    __shared__ Volt s_vl;
     using MI = ModeInfo<MODE>;
     DevState *st = R.st;
     const int n = R.n_cells;
@@ -2247,17 +2280,22 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
         for (int k = threadIdx.x; k < n; k += kThreads) sm.heat[k] = 0.0f;
         for (int k = threadIdx.x; k <= R.eedf_bins; k += kThreads) sm.eedf[k] = 0u;
     }
-    if (threadIdx.x == 0) {
-        *sm.q.n = 0u;
-        // the electrode voltage the tail will need, while the first copies fly
-        // (FP64 is slow here; only the last block's value is used)
-        s_vl = electrode_volt(R, (MODE == kDepositEC || MODE == kDepositMC) ? step : step + 1);
-    }
+    if (threadIdx.x == 0) *sm.q.n = 0u;
     __syncthreads();
     // the FP64 work the previous tail left (a few blocks; the others start streaming)
     {
         const unsigned int pend = st->pending;
         if (pend && blockIdx.x < kDeferParts) deferred_work(R, pend, (int)blockIdx.x, kDeferParts);
+    }
+    // The electrode voltage of the field the tail solves: FP64 is slow here,
+    // so one thread of one block (past the deferring ones) computes it while
+    // the rest stream, and stores it for the tail.  Its block's arrival
+    // fence below orders the store before the last block's reads.
+    if (blockIdx.x == (gridDim.x > (unsigned int)kDeferParts ? (unsigned int)kDeferParts : 0u) && threadIdx.x == 0) {
+        const Volt v = electrode_volt(R, (MODE == kDepositEC || MODE == kDepositMC) ? step : step + 1);
+        st->volt_v = v.v;
+        st->volt_hi = v.hi;
+        st->volt_lo = v.lo;
     }
     stream_block<MODE>(R, sm, g, ms, s_prod, diag, step);
     if (diag) {
@@ -2278,7 +2316,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     __syncthreads();
     if (!s_last && s_warm < 0) return;
     if (s_last) __threadfence();
-    tail_body<MODE>(R, smem_all + tail_stage_bytes(n), smem_all, diag, true, s_vl, true, !s_last,
+    tail_body<MODE>(R, smem_all + tail_stage_bytes(n), smem_all, diag, true, true, !s_last,
                     s_last ? 0 : s_warm, s_last ? 4 : s_warm + 1);
 }
 
@@ -2550,8 +2588,7 @@ __device__ void batch_item(const Run &R, unsigned char *smem, const Ring &g, int
     __syncthreads();
     if (s_last) {
         __threadfence();
-        tail<MODE>(R, (unsigned char *)g.buf + tail_stage_bytes(n), (unsigned char *)g.buf, diag, false,
-                   Volt{0.0, 0.0f, 0.0f}, false);
+        tail<MODE>(R, (unsigned char *)g.buf + tail_stage_bytes(n), (unsigned char *)g.buf, diag, false, false);
         loaded_run = -1;  // the tail reused the shared memory
         __syncthreads();
     }

@@ -28,7 +28,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-SCHEMES = {"ec_explicit": 0, "mc_explicit": 1, "ec_implicit": 2, "mc_implicit": 3}
+SCHEMES = {"ec_explicit": 0, "mc_explicit": 1, "ec_implicit": 2, "mc_implicit": 3, "ec3_explicit": 4}
 SPECIES = {"e": 0, "i": 1}
 
 # conversion of a gas pressure to a density is part of the workload description
@@ -120,6 +120,12 @@ def lib():
         L.orc_deposit_s2_fixed.argtypes = [_P(Params), ctypes.c_int64, _d, _i64]
         L.orc_deposit_s2_fp64.argtypes = [_P(Params), ctypes.c_int64, _d, _d]
         L.orc_deposit_s1_fixed.argtypes = [_P(Params), ctypes.c_int64, _d, _i64]
+        L.orc_deposit_s3_fixed.argtypes = [_P(Params), ctypes.c_int64, _d, _i64]
+        L.orc_deposit_s3_fp64.argtypes = [_P(Params), ctypes.c_int64, _d, _d]
+        L.orc_charge_unit.argtypes = [_P(Params)]
+        L.orc_charge_unit.restype = ctypes.c_int64
+        L.orc_gather_ec3.argtypes = [_P(Params), _d, ctypes.c_double]
+        L.orc_gather_ec3.restype = ctypes.c_double
         L.orc_solve_dirichlet.argtypes = [ctypes.c_int, ctypes.c_double, _d, _d,
                                           ctypes.c_double, _d]
         L.orc_solve_periodic.argtypes = [ctypes.c_int, ctypes.c_double, _d, _d, _d]
@@ -251,6 +257,31 @@ def deposit_s1_fixed(cfg, xi) -> np.ndarray:
     return out
 
 
+def deposit_s3_fixed(cfg, xi) -> np.ndarray:
+    """m = 3 assignment in units of 2^-36/6 particle charge (12-bit offset code)."""
+    p = params(cfg)
+    x = np.ascontiguousarray(xi, dtype=np.float64)
+    out = np.zeros(p.n_cells + 1, dtype=np.int64)
+    lib().orc_deposit_s3_fixed(ctypes.byref(p), len(x), _ptr(x, ctypes.c_double),
+                               _ptr(out, ctypes.c_int64))
+    return out
+
+
+def deposit_s3_fp64(cfg, xi) -> np.ndarray:
+    p = params(cfg)
+    x = np.ascontiguousarray(xi, dtype=np.float64)
+    out = np.zeros(p.n_cells + 1, dtype=np.float64)
+    lib().orc_deposit_s3_fp64(ctypes.byref(p), len(x), _ptr(x, ctypes.c_double),
+                              _ptr(out, ctypes.c_double))
+    return out
+
+
+def charge_unit(cfg) -> int:
+    """Integer node charge of one particle charge in the scheme's fixed point."""
+    p = params(cfg)
+    return int(lib().orc_charge_unit(ctypes.byref(p)))
+
+
 def solve_dirichlet(n_cells, dx, rho, v_left, chi=None) -> np.ndarray:
     r = np.ascontiguousarray(rho, dtype=np.float64)
     c = None if chi is None else np.ascontiguousarray(chi, dtype=np.float64)
@@ -285,6 +316,12 @@ def gather_ec(cfg, e_cc, xi) -> float:
     p = params(cfg)
     e = np.ascontiguousarray(e_cc, dtype=np.float64)
     return lib().orc_gather_ec(ctypes.byref(p), _ptr(e, ctypes.c_double), float(xi))
+
+
+def gather_ec3(cfg, e_cc, xi) -> float:
+    p = params(cfg)
+    e = np.ascontiguousarray(e_cc, dtype=np.float64)
+    return lib().orc_gather_ec3(ctypes.byref(p), _ptr(e, ctypes.c_double), float(xi))
 
 
 def gather_mc(cfg, e_node, xi) -> float:

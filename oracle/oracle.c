@@ -32,6 +32,8 @@
 
 #define TWO_POW_16 65536
 #define TWO_POW_33 ((int64_t)1 << 33)
+#define TWO_POW_12 ((int64_t)4096)
+#define TWO_POW_36 ((int64_t)1 << 36)
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as    */
@@ -220,6 +222,58 @@ void orc_deposit_s1_fixed(const orc_params *p, int64_t n, const double *xi, int6
     }
 }
 
+/* m = 3 (Eq. (2) with the cubic B-spline S_3; Sec. 2 allows m > 2).  With
+   xi = i + t, 0 <= t < 1, the nodes i-1, i, i+1, i+2 receive
+       (1-t)^3 / 6,  (3t^3 - 6t^2 + 4) / 6,  (-3t^3 + 3t^2 + 3t + 1) / 6,  t^3 / 6,
+   the values of S_3 at distances 1+t, t, 1-t and 2-t.  Fixed point: the
+   offset is quantised to 12 bits, t = F / 2^12, and each weight is kept as
+   6 * 2^36 times itself, an integer polynomial in F (exact in int64). */
+static void quantise_offset12(double xi, int64_t *cell, int64_t *code)
+{
+    double c = floor(xi);
+    float off = (float)(xi - c);
+    if (off >= 1.0f) {
+        c += 1.0;
+        off = 0.0f;
+    }
+    *cell = (int64_t)c;
+    *code = (int64_t)floor((double)off * 4096.0);
+}
+
+void orc_deposit_s3_fixed(const orc_params *p, int64_t n, const double *xi, int64_t *out)
+{
+    const int64_t T = TWO_POW_12;
+    memset(out, 0, sizeof(int64_t) * (size_t)(p->n_cells + 1));
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t i, F;
+        quantise_offset12(xi[k], &i, &F);
+        int64_t G = T - F;
+        out[node_index(p, i - 1)] += G * G * G;
+        out[node_index(p, i)] += 3 * F * F * F - 6 * T * F * F + 4 * T * T * T;
+        out[node_index(p, i + 1)] += -3 * F * F * F + 3 * T * F * F + 3 * T * T * F + T * T * T;
+        out[node_index(p, i + 2)] += F * F * F;
+    }
+}
+
+void orc_deposit_s3_fp64(const orc_params *p, int64_t n, const double *xi, double *out)
+{
+    memset(out, 0, sizeof(double) * (size_t)(p->n_cells + 1));
+    for (int64_t k = 0; k < n; ++k) {
+        double id = floor(xi[k]);
+        double t = xi[k] - id;
+        int64_t i = (int64_t)id;
+        out[node_index(p, i - 1)] += (1.0 - t) * (1.0 - t) * (1.0 - t) / 6.0;
+        out[node_index(p, i)] += (3.0 * t * t * t - 6.0 * t * t + 4.0) / 6.0;
+        out[node_index(p, i + 1)] += (-3.0 * t * t * t + 3.0 * t * t + 3.0 * t + 1.0) / 6.0;
+        out[node_index(p, i + 2)] += t * t * t / 6.0;
+    }
+}
+
+int64_t orc_charge_unit(const orc_params *p)
+{
+    return p->scheme == ORC_EC3_EXPLICIT ? 6 * TWO_POW_36 : TWO_POW_33;
+}
+
 /* Susceptibility weights: S_1 from the predicted position to cell centres,
    units 2^-16.  With the nearest node j and a as above, the centre of cell j
    gets a and the centre of cell j-1 gets 2^16 - a.  Reading: weight falling in
@@ -325,6 +379,19 @@ double orc_gather_ec(const orc_params *p, const double *e_cc, double xi)
     double delta = xi - jd;
     int64_t j = (int64_t)jd;
     return (0.5 - delta) * cell_field(p, e_cc, j - 1) + (0.5 + delta) * cell_field(p, e_cc, j);
+}
+
+/* m = 3: Eq. (3) with S_2 centred on the cell centres.  With xi = i + t the
+   centres of cells i-1, i, i+1 lie at distances 1/2 + t, |t - 1/2| and
+   3/2 - t, where S_2 is (1-t)^2 / 2, 3/4 - (t - 1/2)^2 and t^2 / 2. */
+double orc_gather_ec3(const orc_params *p, const double *e_cc, double xi)
+{
+    double id = floor(xi);
+    double t = xi - id;
+    int64_t i = (int64_t)id;
+    double d = t - 0.5;
+    return 0.5 * (1.0 - t) * (1.0 - t) * cell_field(p, e_cc, i - 1) + (0.75 - d * d) * cell_field(p, e_cc, i) +
+           0.5 * t * t * cell_field(p, e_cc, i + 1);
 }
 
 /* Momentum-conserving gather: linear interpolation from node fields. */
@@ -479,8 +546,8 @@ static void assemble_rho(orc_sim *s)
     for (int64_t g = 0; g < nn; ++g) {
         double ne, ni;
         if (uses_fixed(p)) {
-            ne = (double)s->rho_q[0][g] / (double)TWO_POW_33;
-            ni = (double)s->rho_q[1][g] / (double)TWO_POW_33;
+            ne = (double)s->rho_q[0][g] / (double)orc_charge_unit(p);
+            ni = (double)s->rho_q[1][g] / (double)orc_charge_unit(p);
         } else {
             ne = s->rho_f[0][g];
             ni = s->rho_f[1][g];
@@ -493,7 +560,12 @@ static void assemble_rho(orc_sim *s)
 static void deposit_species(orc_sim *s, int k, int use_s1)
 {
     species_t *sp = &s->sp[k];
-    if (use_s1)
+    if (s->p.scheme == ORC_EC3_EXPLICIT) {
+        if (s->p.quantized)
+            orc_deposit_s3_fixed(&s->p, sp->n, sp->xi, s->rho_q[k]);
+        else
+            orc_deposit_s3_fp64(&s->p, sp->n, sp->xi, s->rho_f[k]);
+    } else if (use_s1)
         orc_deposit_s1_fixed(&s->p, sp->n, sp->xi, s->rho_q[k]);
     else if (s->p.quantized)
         orc_deposit_s2_fixed(&s->p, sp->n, sp->xi, s->rho_q[k]);
@@ -549,6 +621,7 @@ static void solve_field(orc_sim *s, const double *chi, int64_t level)
 static double gather(const orc_sim *s, double xi)
 {
     if (is_mc(&s->p)) return orc_gather_mc(&s->p, s->e_node, xi);
+    if (s->p.scheme == ORC_EC3_EXPLICIT) return orc_gather_ec3(&s->p, s->e_cc, xi);
     return orc_gather_ec(&s->p, s->e_cc, xi);
 }
 
@@ -570,8 +643,8 @@ static void accumulate_averages(orc_sim *s)
     for (int64_t g = 0; g < nn; ++g) {
         double ne, ni;
         if (uses_fixed(p)) {
-            ne = (double)s->rho_q[0][g] / (double)TWO_POW_33;
-            ni = (double)s->rho_q[1][g] / (double)TWO_POW_33;
+            ne = (double)s->rho_q[0][g] / (double)orc_charge_unit(p);
+            ni = (double)s->rho_q[1][g] / (double)orc_charge_unit(p);
         } else {
             ne = s->rho_f[0][g];
             ni = s->rho_f[1][g];

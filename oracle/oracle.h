@@ -21,16 +21,19 @@
 extern "C" {
 #endif
 
-enum { ORC_EC_EXPLICIT = 0, ORC_MC_EXPLICIT = 1, ORC_EC_IMPLICIT = 2, ORC_MC_IMPLICIT = 3 };
+/* ORC_EC3_EXPLICIT: the explicit EC scheme with m = 3 in Eq. (2)-(3) (cubic
+   S_3 charge assignment, S_2 force interpolation from the cell centres), the
+   "larger m" Sec. 2 allows. */
+enum { ORC_EC_EXPLICIT = 0, ORC_MC_EXPLICIT = 1, ORC_EC_IMPLICIT = 2, ORC_MC_IMPLICIT = 3, ORC_EC3_EXPLICIT = 4 };
 
 typedef struct orc_params {
     /* grid and geometry (Sec. 3: planar gap between two electrodes) */
     int32_t n_cells;
     int32_t periodic;        /* 0: electrodes (x=0 driven, x=L grounded); 1: periodic box */
-    int32_t scheme;          /* ORC_EC_EXPLICIT / ORC_MC_EXPLICIT / ORC_EC_IMPLICIT / ORC_MC_IMPLICIT (Sec. 2) */
+    int32_t scheme;          /* ORC_EC_EXPLICIT / ORC_MC_EXPLICIT / ORC_EC_IMPLICIT / ORC_MC_IMPLICIT (Sec. 2), ORC_EC3_EXPLICIT */
     int32_t mcc;             /* 1: null-collision Monte Carlo on */
     int32_t ions_mobile;     /* 0: ions replaced by a frozen uniform background */
-    int32_t quantized;       /* 1: 16-bit offset quantisation, int64 sums; 0: exact FP64 weights */
+    int32_t quantized;       /* 1: offset quantisation (16 bits; 12 for m = 3), int64 sums; 0: exact FP64 weights */
     int32_t diag_period;     /* heating profile and EEDF sampled every diag_period steps (0: never) */
     int32_t eedf_bins;
     uint32_t seed, run;      /* Philox key */
@@ -76,6 +79,14 @@ void orc_deposit_s2_fixed(const orc_params *p, int64_t n, const double *xi, int6
 void orc_deposit_s2_fp64(const orc_params *p, int64_t n, const double *xi, double *out);
 /* S_1 charge assignment to nodes (momentum-conserving scheme), units 2^-33. */
 void orc_deposit_s1_fixed(const orc_params *p, int64_t n, const double *xi, int64_t *out);
+/* S_3 (cubic B-spline) charge assignment, m = 3: four nodes per particle.
+   Fixed point: 12-bit offset code F, units of 2^-36/6 particle charge (each
+   particle assigns exactly 6 * 2^36).  Ghost nodes fold / wrap as for S_2. */
+void orc_deposit_s3_fixed(const orc_params *p, int64_t n, const double *xi, int64_t *out);
+void orc_deposit_s3_fp64(const orc_params *p, int64_t n, const double *xi, double *out);
+/* Integer node charge of one particle charge in the units of the scheme's
+   fixed-point assignment: 2^33, or 6 * 2^36 for m = 3. */
+int64_t orc_charge_unit(const orc_params *p);
 /* Dirichlet tridiagonal solve of -(phi[g-1]-2phi[g]+phi[g+1])/dx^2 = rho[g]/eps0
    with phi[0]=v_left, phi[N]=0, coefficient (1+chi) on each cell face when chi
    is given (NULL: plain Poisson). Thomas algorithm. */
@@ -90,6 +101,8 @@ void orc_fields(const orc_params *p, const double *phi, double *e_cc, double *e_
 /* EC force interpolation: E at particle from cell-centred E (ghost cells E=0). */
 double orc_gather_ec(const orc_params *p, const double *e_cc, double xi);
 double orc_gather_mc(const orc_params *p, const double *e_node, double xi);
+/* m = 3: S_2 from the three nearest cell centres (ghost cells E = 0). */
+double orc_gather_ec3(const orc_params *p, const double *e_cc, double xi);
 
 /* Isotropic scattering rotation used by the collision routines (exposed for tests). */
 void orc_rotate(const double d[3], double cos_chi, double phi, double out[3]);
@@ -131,7 +144,7 @@ void     orc_sim_get(const orc_sim *s, int species, double *xi, double *vx, doub
 int      orc_sim_step(orc_sim *s, int64_t nsteps);
 void     orc_sim_set_step(orc_sim *s, int64_t step);
 void     orc_sim_diag(const orc_sim *s, orc_diag *d);
-/* grids: rho_q[species][N+1] int64 (2^-33 units), phi[N+1], e_cc[N], chi[N] */
+/* grids: rho_q[species][N+1] int64 (units of orc_charge_unit), phi[N+1], e_cc[N], chi[N] */
 void     orc_sim_grids(const orc_sim *s, int64_t *rho_q_e, int64_t *rho_q_i, double *phi,
                        double *e_cc, double *chi);
 /* time averages: n_e, n_i, phi at nodes [N+1]; heating per cell and species [2][N]; eedf [bins+1] */

@@ -68,6 +68,15 @@ extern "C" {
 #define PIC_MC_EXPLICIT 1
 #define PIC_EC_IMPLICIT 2
 #define PIC_MC_IMPLICIT 3
+/* The explicit EC scheme with m = 3 in Eq. (2)-(3) (Sec. 2 allows m > 2):
+   cubic S_3 charge assignment to four nodes, quadratic S_2 force
+   interpolation from the three nearest cell centres (zero field in the ghost
+   cells beyond an electrode).  Charges are assigned in fixed point from a
+   12-bit offset code, F = floor(off * 2^12), in units of 2^-36/6 particle
+   charge (pic_grids() returns rho_q in these units for this scheme).  Single
+   runs only (pic_batch_init and pic_deposit_noalloc reject it); capacity per
+   species below 2^23 (int64 headroom of the node charges). */
+#define PIC_EC3_EXPLICIT 4
 
 /* Boundaries: electrodes at x=0 (driven, V(t) = rf_volt sin(2 pi rf_freq t))
    and x=L (grounded), both absorbing (Sec. 3); or a periodic box. */
@@ -75,7 +84,8 @@ extern "C" {
 #define PIC_BC_PERIODIC 1
 
 typedef struct pic_config {
-    int32_t scheme;          /* PIC_EC_EXPLICIT / PIC_MC_EXPLICIT / PIC_EC_IMPLICIT / PIC_MC_IMPLICIT */
+    int32_t scheme;          /* PIC_EC_EXPLICIT / PIC_MC_EXPLICIT / PIC_EC_IMPLICIT / PIC_MC_IMPLICIT /
+                                PIC_EC3_EXPLICIT */
     int32_t boundary;        /* PIC_BC_ELECTRODES / PIC_BC_PERIODIC */
     int32_t n_cells;         /* 2 .. 1024 */
     int32_t mcc;             /* 1: null-collision Monte Carlo on */
@@ -188,7 +198,8 @@ int pic_profiles(pic_handle *h, double *ne, double *ni, double *phi, double *hea
                  double *heat_i, uint64_t *eedf);
 
 /* Current grid state, each may be NULL: rho_q_e, rho_q_i [n_cells+1] charge
-   assigned per node in units of 2^-33 macro-particle charges (int64, exact);
+   assigned per node in units of 2^-33 macro-particle charges (2^-36/6 for
+   PIC_EC3_EXPLICIT; int64, exact);
    phi [n_cells+1]; e_cc [n_cells] cell-centred field; chi [n_cells]
    susceptibility of the last implicit field solve. */
 int pic_grids(pic_handle *h, int64_t *rho_q_e, int64_t *rho_q_i, double *phi, double *e_cc,
@@ -244,7 +255,7 @@ int pic_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t
 typedef struct pic_batch pic_batch;
 
 /* Arena bytes for nruns configurations (1..1024), each validated as in
-   pic_required_sizes. */
+   pic_required_sizes; PIC_EINVAL for a PIC_EC3_EXPLICIT configuration. */
 int pic_batch_required_sizes(const pic_config *cfgs, int32_t nruns, pic_sizes *out);
 /* Create the batch in a caller-owned device arena (256-byte aligned) and load
    every run (uniform load, t = 0 field, one sort).  The batch sort period is
@@ -289,7 +300,8 @@ void pic_batch_free(pic_batch *b);
    one device share the array: calls that overlap on the GPU race (calls on
    one stream are ordered).  Asynchronous on `stream`.  Returns PIC_OK;
    PIC_EINVAL for n_cells outside 2..1024, n outside 0..2^29-1, an unknown
-   scheme or boundary, or a NULL array; PIC_ECUDA if a launch fails. */
+   scheme or boundary (PIC_EC3_EXPLICIT included), or a NULL array;
+   PIC_ECUDA if a launch fails. */
 int pic_deposit_noalloc(int32_t scheme, int32_t boundary, int32_t n_cells, const int32_t *cell,
                         const float *off, int64_t n, int64_t *rho_q_out, void *stream);
 

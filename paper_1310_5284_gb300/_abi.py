@@ -17,7 +17,7 @@ PIC_OK = 0
 ERRORS = {-1: "PIC_EINVAL", -2: "PIC_EUNSTABLE", -3: "PIC_ENOMEM", -4: "PIC_EOVERFLOW",
           -5: "PIC_ECUDA", -6: "PIC_ETIMEOUT"}
 PIC_STATUS_CAPACITY, PIC_STATUS_BIRTHS, PIC_STATUS_TIMEOUT = 0x1, 0x2, 0x4
-SCHEMES = {"ec_explicit": 0, "mc_explicit": 1, "ec_implicit": 2, "mc_implicit": 3}
+SCHEMES = {"ec_explicit": 0, "mc_explicit": 1, "ec_implicit": 2, "mc_implicit": 3, "ec3_explicit": 4}
 BOUNDARY_ELECTRODES, BOUNDARY_PERIODIC = 0, 1
 
 

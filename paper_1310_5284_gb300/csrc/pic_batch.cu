@@ -82,6 +82,11 @@ int batch_layout(const pic_config *cfgs, int nruns, BatchLayout *out) {
     for (int r = 0; r < nruns; ++r) {
         int code = validate_run_config(&cfgs[r]);
         if (code) return code;
+        if (cfgs[r].scheme == PIC_EC3_EXPLICIT) {
+            char msg[96];
+            snprintf(msg, sizeof msg, "run %d: the m = 3 scheme runs through pic_init only", r);
+            return fail_b(nullptr, PIC_EINVAL, msg);
+        }
         out->L[r] = make_run_layout(cfgs[r]);
         out->run_off[r] = o;
         o = a256(o + out->L[r].total);

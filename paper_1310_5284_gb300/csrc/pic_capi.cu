@@ -48,6 +48,7 @@ Layout make_layout(const pic_config &c) {
         L.acc_cnt[s] = take(8 * n1);
         L.acc_a[s] = take(8 * n1);
         L.acc_b[s] = take(8 * n1);
+        L.acc_c[s] = take(8 * n1);
         L.cursor[s] = take(4 * n1);
         L.rho_q[s] = take(8 * n1);
     }
@@ -96,7 +97,7 @@ int fail(int code, const char *fmt, ...) {
 
 int validate(const pic_config *c) {
     if (!c) return fail(PIC_EINVAL, "config is NULL");
-    if (c->scheme < 0 || c->scheme > 3) return fail(PIC_EINVAL, "unknown scheme %d", c->scheme);
+    if (c->scheme < 0 || c->scheme > 4) return fail(PIC_EINVAL, "unknown scheme %d", c->scheme);
     if (c->boundary != PIC_BC_ELECTRODES && c->boundary != PIC_BC_PERIODIC)
         return fail(PIC_EINVAL, "unknown boundary %d", c->boundary);
     if (c->n_cells < 2 || c->n_cells > kMaxCells)
@@ -110,6 +111,10 @@ int validate(const pic_config *c) {
                         s, (long long)c->capacity[s]);
         if (c->capacity[s] < c->np_init && (s == 0 || c->ions_mobile))
             return fail(PIC_EINVAL, "capacity[%d] below np_init", s);
+        // m = 3 charges are 6 * 2^36 a particle: |prefix sums| < 2^23 * 6 * 2^36 < 2^62
+        if (c->scheme == PIC_EC3_EXPLICIT && c->capacity[s] >= (1ll << 23))
+            return fail(PIC_EOVERFLOW, "capacity[%d] = %lld: the m = 3 scheme takes below 2^23 (int64 charge headroom)",
+                        s, (long long)c->capacity[s]);
     }
     if (c->mcc && !c->ions_mobile) return fail(PIC_EINVAL, "collisions need mobile ions");
     if (c->mcc && c->births_capacity < 1) return fail(PIC_EINVAL, "births_capacity must be >= 1");
@@ -204,7 +209,9 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
     R.rf_freq = c.rf_freq;
     R.rf_volt = R.periodic ? 0.0 : c.rf_volt;
     R.weight = w;
-    const double two_m33 = std::ldexp(1.0, -33);
+    // one integer charge unit of the fixed-point node charges: 2^-33 of a
+    // macro-particle, 2^-36/6 for the m = 3 scheme
+    const double two_m33 = c.scheme == PIC_EC3_EXPLICIT ? std::ldexp(1.0, -36) / 6.0 : std::ldexp(1.0, -33);
     R.kappa = kE * w * two_m33 / kEps0;
     R.kappa_bg = c.ions_mobile ? 0.0 : dx * kE * c.bg_density / kEps0;
     R.dens_scale = w * two_m33 / dx;
@@ -278,6 +285,7 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
         R.acc_cnt[s] = (unsigned long long *)(A + L.acc_cnt[s]);
         R.acc_a[s] = (unsigned long long *)(A + L.acc_a[s]);
         R.acc_b[s] = (unsigned long long *)(A + L.acc_b[s]);
+        R.acc_c[s] = (unsigned long long *)(A + L.acc_c[s]);
         R.cursor[s] = (unsigned int *)(A + L.cursor[s]);
         R.rho_q[s] = (long long *)(A + L.rho_q[s]);
         R.heat[s] = (double *)(A + L.heat[s]);
@@ -295,8 +303,12 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
     R.st = (DevState *)(A + L.state);
 }
 
-Mode push_mode(const pic_config &c) { return c.scheme == PIC_MC_EXPLICIT ? kExplicitMC : kExplicitEC; }
+Mode push_mode(const pic_config &c) {
+    if (c.scheme == PIC_EC3_EXPLICIT) return kExplicitEC3;
+    return c.scheme == PIC_MC_EXPLICIT ? kExplicitMC : kExplicitEC;
+}
 Mode deposit_mode(const pic_config &c) {
+    if (c.scheme == PIC_EC3_EXPLICIT) return kDepositEC3;
     return (c.scheme == PIC_MC_EXPLICIT || c.scheme == PIC_MC_IMPLICIT) ? kDepositMC : kDepositEC;
 }
 Mode pass1_mode(const pic_config &c) { return c.scheme == PIC_MC_IMPLICIT ? kImplicit1MC : kImplicit1; }

@@ -40,6 +40,8 @@ enum Mode : int {
     kImplicit2 = 5,    // direct implicit pass 2: corrector, absorb, collide
     kImplicit1MC = 6,  // the same two passes with S_1 weighting and node fields
     kImplicit2MC = 7,
+    kExplicitEC3 = 8,  // explicit EC with m = 3: S_3 assignment, S_2 interpolation
+    kDepositEC3 = 9,
 };
 
 // One species' particle arrays (structure of arrays).
@@ -144,11 +146,12 @@ struct Run {
     // pointers into the arena
     Species buf[2][2];     // [parity][species]
     unsigned long long *acc_cnt[2], *acc_a[2], *acc_b[2];   // [species][n_cells + 1]
+    unsigned long long *acc_c[2];                           // [species][n_cells + 1] sum F^3 (m = 3)
     unsigned int *cursor[2];                                // [species][n_cells + 1]
     float *e_gather;       // [n_cells + 2]
     double *e_cc, *chi;                                     // [n_cells], [n_cells]
     float *e_hi, *e_lo;    // [n_cells] newest field as a double-word pair (deferred conversion)
-    long long *rho_q[2];   // [species][n_cells + 1] last assembled node charge, 2^-33 units
+    long long *rho_q[2];   // [species][n_cells + 1] last assembled node charge, 2^-33 units (2^-36/6 for m = 3)
     double *avg_ne, *avg_ni, *avg_e, *heat[2];   // sums over steps (charge units, V/m)
     unsigned long long *eedf;
     Birth *births;
@@ -159,7 +162,7 @@ struct Run {
 struct Layout {
     size_t state;
     size_t sp[2][2][7];  // [parity][species][field] offsets (cell, off, vx, vy, vz, id, abar)
-    size_t acc_cnt[2], acc_a[2], acc_b[2], cursor[2], rho_q[2];
+    size_t acc_cnt[2], acc_a[2], acc_b[2], acc_c[2], cursor[2], rho_q[2];
     size_t e_gather, e_cc, chi, avg_ne, avg_ni, avg_e, heat[2], eedf, births, e_hi, e_lo;
     size_t total;
 };

@@ -287,11 +287,24 @@ __device__ __forceinline__ int deposit_key_s1(int cell, float off, uint32_t &a) 
     return cell;
 }
 
+// m = 3 (Eq. 2 with the cubic S_3, four nodes): key = cell, value the 12-bit
+// code F = floor(off * 2^12).  With t = F / 2^12 the nodes cell-1 .. cell+2
+// receive 6 * 2^36 times (1-t)^3/6, (3t^3-6t^2+4)/6, (-3t^3+3t^2+3t+1)/6 and
+// t^3/6, integer polynomials in F; the per-key sums (1, F, F^2, F^3) give the
+// node charges exactly (node_charge_s3_raw), in units of 2^-36/6.
+__device__ __forceinline__ int deposit_key_s3(int cell, float off, uint32_t &a) {
+    a = (uint32_t)(int)(off * 4096.0f);
+    return cell;
+}
+
 // Per-block accumulators, four 32-bit counters per key: count, sum of a, and
 // the sums of the high and low 16 bits of a^2.  Exact while a block adds at
-// most 2^16 particles between two flushes (each term is below 2^16).
+// most 2^16 particles between two flushes (each term is below 2^16).  The
+// m = 3 modes use cnt, a (sum of F < 2^12), s2 (sum of F^2, 64-bit, in the
+// storage of bh and bl) and s3 (sum of F^3, 64-bit, an array of its own).
 struct Acc {
     unsigned int *cnt, *a, *bh, *bl;
+    unsigned long long *s2, *s3;
 };
 
 constexpr long long kFlushEvery = 65536;
@@ -346,6 +359,77 @@ __device__ __forceinline__ void warp_agg(int key, uint32_t c, uint32_t a, uint32
         pending &= ~grp;
         ++iter;
     }
+}
+
+// m = 3: the warp aggregation of (count, F, F^2, F^3) with F^3 split into its
+// high and low 16 bits.  Per warp slot (at most 32 x kUnroll = 128 particles,
+// F < 2^12): sum F^2 < 2^31, sum (F^3 >> 16) < 2^27, sum (F^3 & 0xffff) <
+// 2^23, so each reduction is exact in 32 bits.
+__device__ __forceinline__ void acc_add3(const Acc &acc, int key, uint32_t c, uint32_t a, uint32_t s2,
+                                         uint32_t s3h, uint32_t s3l) {
+    atomicAdd(&acc.cnt[key], c);
+    atomicAdd(&acc.a[key], a);
+    atomicAdd(&acc.s2[key], (unsigned long long)s2);
+    atomicAdd(&acc.s3[key], ((unsigned long long)s3h << 16) + s3l);
+}
+
+__device__ __forceinline__ void warp_agg3(int key, uint32_t c, uint32_t a, uint32_t s2, uint32_t s3h, uint32_t s3l,
+                                          const Acc &acc) {
+    const int lane = threadIdx.x & 31;
+    unsigned int pending = __ballot_sync(FULL_MASK, key >= 0);
+    int iter = 0;
+    while (pending) {
+        if (iter == 4) {  // widely spread warp: the rest add lane by lane
+            if ((pending >> lane) & 1u) acc_add3(acc, key, c, a, s2, s3h, s3l);
+            break;
+        }
+        const int leader = __ffs(pending) - 1;
+        const int lk = __shfl_sync(FULL_MASK, key, leader);
+        const bool mine = ((pending >> lane) & 1u) && key == lk;
+        const unsigned int grp = __ballot_sync(FULL_MASK, mine);
+        const uint32_t sc = __reduce_add_sync(FULL_MASK, mine ? c : 0u);
+        const uint32_t sa = __reduce_add_sync(FULL_MASK, mine ? a : 0u);
+        const uint32_t s2s = __reduce_add_sync(FULL_MASK, mine ? s2 : 0u);
+        const uint32_t sh = __reduce_add_sync(FULL_MASK, mine ? s3h : 0u);
+        const uint32_t sl = __reduce_add_sync(FULL_MASK, mine ? s3l : 0u);
+        if (lane == leader) acc_add3(acc, lk, sc, sa, s2s, sh, sl);
+        pending &= ~grp;
+        ++iter;
+    }
+}
+
+__device__ __forceinline__ void deposit_tile3(const int (&key)[kUnroll], const uint32_t (&a)[kUnroll],
+                                              const Acc &acc) {
+    int kmin = 0x7fffffff;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+        if (key[u] >= 0 && key[u] < kmin) kmin = key[u];
+    uint32_t c0 = 0, a0 = 0, q0 = 0, h0 = 0, l0 = 0, c1 = 0, a1 = 0, q1 = 0, h1 = 0, l1 = 0;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+        const int k = key[u];
+        if (k < 0) continue;
+        const uint32_t f = a[u], f2 = f * f;
+        const unsigned long long f3 = (unsigned long long)f2 * f;
+        const uint32_t hi = (uint32_t)(f3 >> 16), lo = (uint32_t)(f3 & 0xffffull);
+        if (k == kmin) {
+            c0 += 1u;
+            a0 += f;
+            q0 += f2;
+            h0 += hi;
+            l0 += lo;
+        } else if (k == kmin + 1) {
+            c1 += 1u;
+            a1 += f;
+            q1 += f2;
+            h1 += hi;
+            l1 += lo;
+        } else {
+            acc_add3(acc, k, 1u, f, f2, hi, lo);
+        }
+    }
+    warp_agg3(kmin == 0x7fffffff ? -1 : kmin, c0, a0, q0, h0, l0, acc);
+    warp_agg3(c1 ? kmin + 1 : -1, c1, a1, q1, h1, l1, acc);
 }
 
 // The kUnroll particles of a thread usually share one or two adjacent keys
@@ -484,7 +568,7 @@ struct CollQueue {
 
 struct SmemMain {
     float *e;                  // [n+2] gather table
-    Acc acc;                   // 4 x [n+1]
+    Acc acc;                   // 4 x [n+1] (m = 3: and a 64-bit [n+1])
     float *heat;               // [n]
     unsigned int *eedf;        // [bins+1]
     CollQueue q;
@@ -492,9 +576,9 @@ struct SmemMain {
 
 __host__ __device__ inline size_t align8(size_t x) { return (x + 7) & ~size_t(7); }
 
-__host__ __device__ inline size_t main_smem_bytes(int n, int bins) {
-    return align8(4 * (size_t)(n + 2)) + 4 * align8(4 * (size_t)(n + 1)) + align8(4 * (size_t)n) +
-           align8(4 * (size_t)(bins + 1)) + 8 * (size_t)kQueue + 16;
+__host__ __device__ inline size_t main_smem_bytes(int n, int bins, bool ec3) {
+    return align8(4 * (size_t)(n + 2)) + 4 * align8(4 * (size_t)(n + 1)) + (ec3 ? 8 * (size_t)(n + 1) : 0) +
+           align8(4 * (size_t)n) + align8(4 * (size_t)(bins + 1)) + 8 * (size_t)kQueue + 16;
 }
 
 // The tail's scratch: the field solve's arrays (32 bytes a node), or, before
@@ -505,11 +589,13 @@ __host__ __device__ inline size_t tail_smem_bytes(int n) {
 }
 
 // The last block's tail reuses the whole dynamic shared memory (ring and grid
-// are idle by then): the staged per-key sums (6 x 8 bytes a key) first, the
-// tail's scratch after them.
-__host__ __device__ inline size_t tail_stage_bytes(int n) { return ((size_t)48 * (n + 1) + 255) & ~size_t(255); }
+// are idle by then): the staged per-key sums (6 x 8 bytes a key, 8 x 8 for
+// m = 3) first, the tail's scratch after them.
+__host__ __device__ inline size_t tail_stage_bytes(int n, bool ec3 = false) {
+    return ((size_t)(ec3 ? 64 : 48) * (n + 1) + 255) & ~size_t(255);
+}
 
-__device__ SmemMain carve_main(unsigned char *base, int n, int bins) {
+__device__ SmemMain carve_main(unsigned char *base, int n, int bins, bool ec3 = false) {
     SmemMain s;
     size_t o = 0;
     s.e = (float *)(base + o);
@@ -518,6 +604,14 @@ __device__ SmemMain carve_main(unsigned char *base, int n, int bins) {
     for (int k = 0; k < 4; ++k) {
         *slots[k] = (unsigned int *)(base + o);
         o += align8(4 * (size_t)(n + 1));
+    }
+    // bh and bl are adjacent, 8-byte aligned and 2 x align8(4 (n+1)) >= 8 (n+1)
+    // bytes together: the m = 3 sum of F^2 lives there
+    s.acc.s2 = (unsigned long long *)s.acc.bh;
+    s.acc.s3 = nullptr;
+    if (ec3) {
+        s.acc.s3 = (unsigned long long *)(base + o);
+        o += 8 * (size_t)(n + 1);
     }
     s.heat = (float *)(base + o);
     o += align8(4 * (size_t)n);
@@ -535,13 +629,16 @@ template <int MODE>
 struct ModeInfo {
     static constexpr bool pass1 = (MODE == kImplicit1 || MODE == kImplicit1MC);
     static constexpr bool pass2 = (MODE == kImplicit2 || MODE == kImplicit2MC);
-    static constexpr bool push = !(MODE == kDepositEC || MODE == kDepositMC || pass1);
-    static constexpr bool needs_field = (MODE == kExplicitEC || MODE == kExplicitMC || pass2);
+    static constexpr bool ec3 = (MODE == kExplicitEC3 || MODE == kDepositEC3);
+    static constexpr bool deposit = (MODE == kDepositEC || MODE == kDepositMC || MODE == kDepositEC3);
+    static constexpr bool push = !(deposit || pass1);
+    static constexpr bool needs_field = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kExplicitEC3 || pass2);
     static constexpr bool implicit = pass1 || pass2;
     static constexpr bool count_only = pass2;
     static constexpr bool mc = (MODE == kExplicitMC || MODE == kDepositMC || MODE == kImplicit1MC ||
                                 MODE == kImplicit2MC);
-    static constexpr bool loads_v = !(MODE == kDepositEC || MODE == kDepositMC);
+    static constexpr bool loads_v = !deposit;
+    static constexpr bool explicit_push = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kExplicitEC3);
 };
 
 // Renormalise an offset that left [0, 1) into the cell index.
@@ -563,6 +660,13 @@ __device__ __forceinline__ float gather_ec(const float *e, int cell, float off) 
     const int j = cell + (off >= 0.5f ? 1 : 0);
     const float w1 = off >= 0.5f ? off - 0.5f : off + 0.5f;  // 1/2 + delta
     return (1.0f - w1) * e[j] + w1 * e[j + 1];
+}
+
+// m = 3: S_2 from the centres of cells cell-1, cell, cell+1 (table entries
+// cell .. cell+2), at distances 1/2 + t, |t - 1/2| and 3/2 - t.
+__device__ __forceinline__ float gather_ec3(const float *e, int cell, float t) {
+    const float u = 1.0f - t, d = t - 0.5f;
+    return 0.5f * u * u * e[cell] + (0.75f - d * d) * e[cell + 1] + 0.5f * t * t * e[cell + 2];
 }
 
 __device__ __forceinline__ void eedf_sample(const Run &R, const SmemMain &sm, float vx, float vy, float vz) {
@@ -644,6 +748,7 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
     const int N = R.n_cells;
     if (MODE == kDepositEC) return deposit_key_s2(cell, off, a_out);
     if (MODE == kDepositMC) return deposit_key_s1(cell, off, a_out);
+    if (MODE == kDepositEC3) return deposit_key_s3(cell, off, a_out);
     const float v_old = vx;
     float e_field, v_new, s;
     int c = cell;
@@ -673,7 +778,8 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         abar = 0.5f * (abar + acc);
     } else {
         // explicit leapfrog with E^n at x^n (Sec. 2 schemes (1), (2))
-        e_field = MI::mc ? (1.0f - off) * sm.e[cell] + off * sm.e[cell + 1] : gather_ec(sm.e, cell, off);
+        e_field = MI::mc ? (1.0f - off) * sm.e[cell] + off * sm.e[cell + 1]
+                         : (MI::ec3 ? gather_ec3(sm.e, cell, off) : gather_ec(sm.e, cell, off));
         v_new = fmaf(k.qm_dt, e_field, vx);
         if (diag) atomicAdd(&sm.heat[cell], k.qw * e_field * 0.5f * (v_old + v_new));
         s = fmaf(v_new, R.dt_dx, off);
@@ -710,6 +816,7 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
     }
     if (k.S == 0 && diag && R.eedf_bins > 0 && !queued) eedf_sample(R, sm, vx, sp.vy[idx], sp.vz[idx]);
     if (MI::mc) return deposit_key_s1(c, s, a_out);
+    if (MI::ec3) return deposit_key_s3(c, s, a_out);
     return deposit_key_s2(c, s, a_out);
 }
 
@@ -1013,12 +1120,21 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
 }
 
 // Add the block's shared accumulators of one species to the run's global ones.
-__device__ void flush_species(const Run &R, const SmemMain &sm, int S, bool count_only) {
+__device__ void flush_species(const Run &R, const SmemMain &sm, int S, bool count_only, bool ec3 = false) {
     __syncthreads();
     const int n1 = R.n_cells + 1;
     for (int k = threadIdx.x; k < n1; k += kThreads) {
         const unsigned int c = sm.acc.cnt[k];
-        if (c) {
+        if (c && ec3) {
+            atomicAdd(&R.acc_cnt[S][k], (unsigned long long)c);
+            atomicAdd(&R.acc_a[S][k], (unsigned long long)sm.acc.a[k]);
+            atomicAdd(&R.acc_b[S][k], sm.acc.s2[k]);
+            atomicAdd(&R.acc_c[S][k], sm.acc.s3[k]);
+            sm.acc.cnt[k] = 0u;
+            sm.acc.a[k] = 0u;
+            sm.acc.s2[k] = 0ull;
+            sm.acc.s3[k] = 0ull;
+        } else if (c) {
             atomicAdd(&R.acc_cnt[S][k], (unsigned long long)c);
             if (!count_only) {
                 atomicAdd(&R.acc_a[S][k], (unsigned long long)sm.acc.a[k]);
@@ -1076,6 +1192,7 @@ struct KeySums {
 // species: the run's global accumulators or the tail's shared-memory copy.
 struct Keys {
     unsigned long long *c[2], *a[2], *b[2];
+    unsigned long long *d[2];  // m = 3: sum F^3 (b holds sum F^2)
 };
 
 __device__ __forceinline__ Keys global_keys(const Run &R) {
@@ -1084,6 +1201,7 @@ __device__ __forceinline__ Keys global_keys(const Run &R) {
         K.c[S] = R.acc_cnt[S];
         K.a[S] = R.acc_a[S];
         K.b[S] = R.acc_b[S];
+        K.d[S] = R.acc_c[S];
     }
     return K;
 }
@@ -1156,6 +1274,47 @@ __device__ __forceinline__ unsigned long long node_charge_s2_raw(const unsigned 
     return q;
 }
 
+// m = 3 node charge in units of 2^-36/6 macro-particle charges from the
+// per-cell sums (count c, sum F = A, sum F^2 = B, sum F^3 = D), T = 2^12:
+// cell g+1 gives its left node T^3 c - 3 T^2 A + 3 T B - D, cell g gives
+// 4 T^3 c - 6 T B + 3 D, cell g-1 gives T^3 c + 3 T^2 A + 3 T B - 3 D and
+// cell g-2 gives D (the spline weights of deposit_key_s3 summed over the
+// cell's particles).  Electrodes fold the ghost nodes -1 and n+1 onto the
+// wall nodes; the periodic box wraps (node n is node 0).  Unsigned
+// arithmetic: exact modulo 2^64, and the result lies in range.
+__device__ __forceinline__ unsigned long long cell_sum(const unsigned long long *__restrict__ p, int n,
+                                                       bool periodic, int k) {
+    if (periodic) return p[k < 0 ? k + n : (k >= n ? k - n : k)];
+    return (k >= 0 && k < n) ? p[k] : 0ull;
+}
+
+__device__ __forceinline__ unsigned long long node_charge_s3_raw(const unsigned long long *__restrict__ C,
+                                                                 const unsigned long long *__restrict__ A,
+                                                                 const unsigned long long *__restrict__ B,
+                                                                 const unsigned long long *__restrict__ D, int n,
+                                                                 bool periodic, int g) {
+    if (periodic && g == n) return 0ull;
+    // left node of cell k (k = g+1; with the fold, also cell 0 for node 0)
+    auto left = [&](int k) {
+        return (cell_sum(C, n, periodic, k) << 36) - 3ull * (cell_sum(A, n, periodic, k) << 24) +
+               3ull * (cell_sum(B, n, periodic, k) << 12) - cell_sum(D, n, periodic, k);
+    };
+    auto own = [&](int k) {
+        return (cell_sum(C, n, periodic, k) << 38) - 6ull * (cell_sum(B, n, periodic, k) << 12) +
+               3ull * cell_sum(D, n, periodic, k);
+    };
+    auto right = [&](int k) {
+        return (cell_sum(C, n, periodic, k) << 36) + 3ull * (cell_sum(A, n, periodic, k) << 24) +
+               3ull * (cell_sum(B, n, periodic, k) << 12) - 3ull * cell_sum(D, n, periodic, k);
+    };
+    unsigned long long q = left(g + 1) + own(g) + right(g - 1) + cell_sum(D, n, periodic, g - 2);
+    if (!periodic) {
+        if (g == 0) q += left(0);                         // ghost node -1
+        if (g == n) q += cell_sum(D, n, periodic, n - 1);  // ghost node n+1
+    }
+    return q;
+}
+
 // S_1 node charge (momentum-conserving scheme), key = cell, value F:
 // node g gets (2^16 c_g - A_g) from cell g and A_{g-1} from cell g-1, times 2^17.
 __device__ __forceinline__ unsigned long long node_charge_s1(const Run &R, const Keys &K, int S, int g) {
@@ -1208,13 +1367,15 @@ __device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag
     auto place = [&](const Birth &bb, unsigned int r) {
         const long long je = s_ne + r, ji = s_ni + r;
         uint32_t a;
-        const int key = ModeInfo<MODE>::mc ? deposit_key_s1(bb.cell, bb.off, a)
-                                           : deposit_key_s2(bb.cell, bb.off, a);
+        const int key = ModeInfo<MODE>::mc    ? deposit_key_s1(bb.cell, bb.off, a)
+                        : ModeInfo<MODE>::ec3 ? deposit_key_s3(bb.cell, bb.off, a)
+                                              : deposit_key_s2(bb.cell, bb.off, a);
         for (int S = 0; S < 2; ++S) {
             atomicAdd(&K.c[S][key], 1ull);
             if (!ModeInfo<MODE>::count_only) {
                 atomicAdd(&K.a[S][key], (unsigned long long)a);
                 atomicAdd(&K.b[S][key], (unsigned long long)a * a);
+                if (ModeInfo<MODE>::ec3) atomicAdd(&K.d[S][key], (unsigned long long)a * a * a);
             }
         }
         if (dry) return;
@@ -1516,6 +1677,7 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
     double *pp = rinv + n;                           // [n] kappa P_c (+ background), then E_c
     float2 *ew = (float2 *)pp;                       // [n] explicit: E_c as a double-word pair
     constexpr bool mc = ModeInfo<MODE>::mc;
+    constexpr bool ec3 = ModeInfo<MODE>::ec3;
     constexpr bool implicit = ModeInfo<MODE>::implicit;
     if (threadIdx.x == 0) s_vl = vl_ok ? vl : electrode_volt(R, level);
     const bool acc_now = accumulate && (implicit || !defer);
@@ -1525,14 +1687,19 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
         const bool periodic = R.periodic;
         const unsigned long long *__restrict__ c0 = K.c[0], *__restrict__ a0 = K.a[0], *__restrict__ b0 = K.b[0];
         const unsigned long long *__restrict__ c1 = K.c[1], *__restrict__ a1 = K.a[1], *__restrict__ b1 = K.b[1];
+        const unsigned long long *__restrict__ d0 = K.d[0], *__restrict__ d1 = K.d[1];
         long long *__restrict__ qs = q;
         long long *__restrict__ rq0 = R.rho_q[0];
         long long *__restrict__ rq1 = R.rho_q[1];
         double *__restrict__ ane = R.avg_ne;
         double *__restrict__ ani = R.avg_ni;
         for (int g = threadIdx.x; g <= n; g += kThreads) {
-            const unsigned long long ne = mc ? node_charge_s1(R, K, 0, g) : node_charge_s2_raw(c0, a0, b0, n, periodic, g);
-            const unsigned long long ni = mc ? node_charge_s1(R, K, 1, g) : node_charge_s2_raw(c1, a1, b1, n, periodic, g);
+            const unsigned long long ne = mc    ? node_charge_s1(R, K, 0, g)
+                                          : ec3 ? node_charge_s3_raw(c0, a0, b0, d0, n, periodic, g)
+                                                : node_charge_s2_raw(c0, a0, b0, n, periodic, g);
+            const unsigned long long ni = mc    ? node_charge_s1(R, K, 1, g)
+                                          : ec3 ? node_charge_s3_raw(c1, a1, b1, d1, n, periodic, g)
+                                                : node_charge_s2_raw(c1, a1, b1, n, periodic, g);
             qs[g] = (long long)(ni - ne);
             if (dry) continue;
             rq0[g] = (long long)ne;
@@ -1728,14 +1895,14 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
         if (threadIdx.x == 0 && !dry) {
             // the energy of the field this launch pushed with was summed by the
             // launch's deferred-work blocks into fe_acc
-            if (MODE == kExplicitEC || MODE == kExplicitMC) st->field_energy_push = R.eps0_dx_half * fe_acc;
+            if (ModeInfo<MODE>::explicit_push) st->field_energy_push = R.eps0_dx_half * fe_acc;
             st->fe_acc = 0.0;
             st->pending = (accumulate ? 1u : 0u) | 2u;
         }
     } else {
         wsum = block_sum_lean(wsum, sc_d);
         if (threadIdx.x == 0 && !dry) {
-            if (MODE == kExplicitEC || MODE == kExplicitMC) st->field_energy_push = st->field_energy;
+            if (ModeInfo<MODE>::explicit_push) st->field_energy_push = st->field_energy;
             st->field_energy = R.eps0_dx_half * wsum;
             if (accumulate) st->v_sum += s_vl.v;
             st->pending = 0u;  // everything of this field is done
@@ -1817,7 +1984,7 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
                                           bool defer, bool vl_state, bool dry = false, int ph_lo = 0,
                                           int ph_hi = 4) {
     using MI = ModeInfo<MODE>;
-    constexpr bool births = MODE == kExplicitEC || MODE == kExplicitMC || MI::pass2;
+    constexpr bool births = MI::explicit_push || MI::pass2;
     DevState *st = R.st;
     __shared__ TailHead s_hd;
     const long long step = st->step;
@@ -1856,14 +2023,16 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
     if (births && threadIdx.x < R.births_cap) my = R.births[threadIdx.x];  // beyond the step's count: unused
     {
         unsigned long long *base = (unsigned long long *)stage;
+        constexpr int nk = MI::ec3 ? 4 : 3;  // sums per key
         for (int S = 0; S < 2; ++S) {
-            Ks.c[S] = base + (size_t)(3 * S + 0) * n1;
-            Ks.a[S] = base + (size_t)(3 * S + 1) * n1;
-            Ks.b[S] = base + (size_t)(3 * S + 2) * n1;
+            Ks.c[S] = base + (size_t)(nk * S + 0) * n1;
+            Ks.a[S] = base + (size_t)(nk * S + 1) * n1;
+            Ks.b[S] = base + (size_t)(nk * S + 2) * n1;
+            Ks.d[S] = MI::ec3 ? base + (size_t)(nk * S + 3) * n1 : nullptr;
         }
         constexpr int kPer = (kMaxCells + 1 + kThreads - 1) / kThreads;
         for (int S = 0; S < 2 && ph_lo <= 0; ++S) {  // per species: all loads first, then the stores
-            unsigned long long v[kPer][3];
+            unsigned long long v[kPer][nk];
 #pragma unroll
             for (int j = 0; j < kPer; ++j) {
                 const int k = threadIdx.x + j * kThreads;
@@ -1871,6 +2040,7 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
                     v[j][0] = R.acc_cnt[S][k];
                     v[j][1] = R.acc_a[S][k];
                     v[j][2] = R.acc_b[S][k];
+                    if constexpr (MI::ec3) v[j][3] = R.acc_c[S][k];
                 }
             }
 #pragma unroll
@@ -1880,10 +2050,12 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
                     Ks.c[S][k] = v[j][0];
                     Ks.a[S][k] = v[j][1];
                     Ks.b[S][k] = v[j][2];
+                    if constexpr (MI::ec3) Ks.d[S][k] = v[j][3];
                     if (dry) continue;
                     R.acc_cnt[S][k] = 0ull;
                     R.acc_a[S][k] = 0ull;
                     R.acc_b[S][k] = 0ull;
+                    if constexpr (MI::ec3) R.acc_c[S][k] = 0ull;
                 }
             }
         }
@@ -1910,10 +2082,10 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
     if (births && ph_lo <= 1 && 1 < ph_hi) tail_births<MODE>(R, Ks, smem, diag, hd, my, dry);
     if (ph_lo <= 2 && 2 < ph_hi) {
         const Volt vl = {hd.vl_v, hd.vl_hi, hd.vl_lo};  // read only if vl_state
-        if (MODE == kExplicitEC || MODE == kExplicitMC)
+        if (MI::explicit_push)
             tail_field<MODE>(R, Ks, smem, step + 1, true, true, defer, vl, vl_state, hd.fe_acc, dry);
         if (MI::pass1) tail_field<MODE>(R, Ks, smem, step + 1, true, false, defer, vl, vl_state, hd.fe_acc, dry);
-        if (MODE == kDepositEC || MODE == kDepositMC)
+        if (MI::deposit)
             tail_field<MODE>(R, Ks, smem, step, false, true, defer, vl, vl_state, hd.fe_acc, dry);
     }
     if (ph_hi <= 3) return;  // a warming pass ends here
@@ -2123,7 +2295,10 @@ __device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, co
             }
         }
     }
-    deposit_tile(key, a, sm.acc, MI::count_only);
+    if constexpr (MI::ec3)
+        deposit_tile3(key, a, sm.acc);
+    else
+        deposit_tile(key, a, sm.acc, MI::count_only);
 }
 
 // Everything a block adds to the run for species S before it moves on: the
@@ -2131,7 +2306,7 @@ __device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, co
 template <int MODE>
 __device__ void stream_flush(const Run &R, const SmemMain &sm, int S, bool diag, Tally &t) {
     using MI = ModeInfo<MODE>;
-    flush_species(R, sm, S, MI::count_only);
+    flush_species(R, sm, S, MI::count_only, MI::ec3);
     if (MI::push) flush_tally(R, S, t);
     t = Tally{0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
     if (diag) {
@@ -2258,7 +2433,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     g.nf = MI::implicit ? kMaxFields : kMaxFields - 1;
     const Stream ms = {s_ms_S, s_ms_o, s_ms_n};
     unsigned char *smem = smem_all + ring_bytes(MI::implicit);  // grid, accumulators, queue; the tail's space
-    const SmemMain sm = carve_main(smem, n, R.eedf_bins);
+    const SmemMain sm = carve_main(smem, n, R.eedf_bins, MI::ec3);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1u);
         s_uses = 0u;
@@ -2273,8 +2448,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     for (int k = threadIdx.x; k <= n; k += kThreads) {
         sm.acc.cnt[k] = 0u;
         sm.acc.a[k] = 0u;
-        sm.acc.bh[k] = 0u;
-        sm.acc.bl[k] = 0u;
+        if (MI::ec3) {  // s2 spans bh, bl and the padding between them
+            sm.acc.s2[k] = 0ull;
+            sm.acc.s3[k] = 0ull;
+        } else {
+            sm.acc.bh[k] = 0u;
+            sm.acc.bl[k] = 0u;
+        }
     }
     if (diag) {
         for (int k = threadIdx.x; k < n; k += kThreads) sm.heat[k] = 0.0f;
@@ -2292,7 +2472,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     // the rest stream, and stores it for the tail.  Its block's arrival
     // fence below orders the store before the last block's reads.
     if (blockIdx.x == (gridDim.x > (unsigned int)kDeferParts ? (unsigned int)kDeferParts : 0u) && threadIdx.x == 0) {
-        const Volt v = electrode_volt(R, (MODE == kDepositEC || MODE == kDepositMC) ? step : step + 1);
+        const Volt v = electrode_volt(R, MI::deposit ? step : step + 1);
         st->volt_v = v.v;
         st->volt_hi = v.hi;
         st->volt_lo = v.lo;
@@ -2316,7 +2496,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     __syncthreads();
     if (!s_last && s_warm < 0) return;
     if (s_last) __threadfence();
-    tail_body<MODE>(R, smem_all + tail_stage_bytes(n), smem_all, diag, true, true, !s_last,
+    tail_body<MODE>(R, smem_all + tail_stage_bytes(n, MI::ec3), smem_all, diag, true, true, !s_last,
                     s_last ? 0 : s_warm, s_last ? 4 : s_warm + 1);
 }
 
@@ -2345,8 +2525,10 @@ __device__ void sort_chunk(const Run &R, int par, int S, long long b, long long 
 #define PIC_SORT_V 4
 #endif
     constexpr int V = PIC_SORT_V;  // particles per thread in flight: all their loads are issued first
-    const bool mc = R.scheme == 1 || R.scheme == 3;
-    const bool implicit = R.scheme >= 2;
+    // the key of the deposit: the cell for S_1 and for the m = 3 scheme, the
+    // nearest node for S_2
+    const bool mc = R.scheme == 1 || R.scheme == 3 || R.scheme == 4;
+    const bool implicit = R.scheme == 2 || R.scheme == 3;
     const int lane = threadIdx.x & 31;
     const Species src = R.buf[par][S], dst = R.buf[par ^ 1][S];
     for (long long base = b; base < e; base += (long long)kThreads * V) {
@@ -2445,7 +2627,7 @@ __global__ void k_load(Run R, int S, long long count, float vth) {
         sp.vy[i] = vth * n2;
         sp.vz[i] = vth * n3;
         sp.id[i] = (uint32_t)i;
-        if (R.scheme >= 2) sp.abar[i] = 0.0f;
+        if (R.scheme == 2 || R.scheme == 3) sp.abar[i] = 0.0f;
     }
 }
 
@@ -2641,7 +2823,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ r
         const int j = j0 + q;
         if (j >= nj) break;
         const Run &R = runs[j >> 1];
-        const bool part = PHASE == 1 ? R.scheme >= 2 : true;
+        const bool part = PHASE == 1 ? (R.scheme == 2 || R.scheme == 3) : true;
         const int S = j & 1;
         const long long nn = (S == 1 && !R.ions_mobile) ? 0 : work[j];
         unsigned int it = part ? (unsigned int)((nn + chunk - 1) / chunk) : 0u;
@@ -2721,8 +2903,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ r
 // Launchers
 // ---------------------------------------------------------------------------
 int block_smem_bytes(const Run &r) {
-    const size_t a = ring_bytes(r.scheme >= 2) + main_smem_bytes(r.n_cells, r.eedf_bins);
-    const size_t b = tail_stage_bytes(r.n_cells) + tail_smem_bytes(r.n_cells);
+    const bool implicit = r.scheme == 2 || r.scheme == 3, ec3 = r.scheme == 4;
+    const size_t a = ring_bytes(implicit) + main_smem_bytes(r.n_cells, r.eedf_bins, ec3);
+    const size_t b = tail_stage_bytes(r.n_cells, ec3) + tail_smem_bytes(r.n_cells);
     return (int)(a > b ? a : b);
 }
 
@@ -2745,6 +2928,8 @@ cudaError_t launch_particles(const Run &r, Mode m, int grid, cudaStream_t s) {
         case kImplicit2: return launch_mode<kImplicit2>(r, grid, s);
         case kImplicit1MC: return launch_mode<kImplicit1MC>(r, grid, s);
         case kImplicit2MC: return launch_mode<kImplicit2MC>(r, grid, s);
+        case kExplicitEC3: return launch_mode<kExplicitEC3>(r, grid, s);
+        case kDepositEC3: return launch_mode<kDepositEC3>(r, grid, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -2780,7 +2965,7 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    for (int k = 0; k < 8; ++k) {  // raise the shared-memory limit of every mode
+    for (int k = 0; k < 10; ++k) {  // raise the shared-memory limit of every mode
         int dummy = 0;
         switch (k) {
             case 0: e = occ<kExplicitEC>(r, &dummy); break;
@@ -2790,7 +2975,9 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
             case 4: e = occ<kImplicit1>(r, &dummy); break;
             case 5: e = occ<kImplicit2>(r, &dummy); break;
             case 6: e = occ<kImplicit1MC>(r, &dummy); break;
-            default: e = occ<kImplicit2MC>(r, &dummy); break;
+            case 7: e = occ<kImplicit2MC>(r, &dummy); break;
+            case 8: e = occ<kExplicitEC3>(r, &dummy); break;
+            default: e = occ<kDepositEC3>(r, &dummy); break;
         }
         if (e != cudaSuccess) return e;
     }
@@ -2803,6 +2990,8 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
         case kImplicit2: e = occ<kImplicit2>(r, &per); break;
         case kImplicit1MC: e = occ<kImplicit1MC>(r, &per); break;
         case kImplicit2MC: e = occ<kImplicit2MC>(r, &per); break;
+        case kExplicitEC3: e = occ<kExplicitEC3>(r, &per); break;
+        case kDepositEC3: e = occ<kDepositEC3>(r, &per); break;
     }
     if (e != cudaSuccess) return e;
     *grid = sms * (per > 0 ? per : 1);
@@ -2850,7 +3039,7 @@ cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c
 }
 
 size_t batch_smem_bytes(int max_cells, int max_bins, int nruns, int *table_off) {
-    const size_t a = ring_bytes(true) + main_smem_bytes(max_cells, max_bins);
+    const size_t a = ring_bytes(true) + main_smem_bytes(max_cells, max_bins, false);
     const size_t b = tail_stage_bytes(max_cells) + tail_smem_bytes(max_cells);
     const size_t off = ((a > b ? a : b) + 15) & ~size_t(15);
     *table_off = (int)off;
@@ -3034,7 +3223,7 @@ extern "C" int pic_deposit_noalloc(int32_t scheme, int32_t boundary, int32_t n_c
                                    int64_t *rho_q_out, void *stream) {
     using namespace pic;
     using namespace pic::noalloc;
-    if (scheme < 0 || scheme > 3 || (boundary != 0 && boundary != 1)) {
+    if (scheme < 0 || scheme > 3 || (boundary != 0 && boundary != 1)) {  // m = 3 (scheme 4): runs only
         set_last_error("pic_deposit_noalloc: unknown scheme or boundary");
         return -1;
     }
@@ -3423,7 +3612,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_adj_rev(Run R, AdjRev 
 }
 
 int adj_fwd_smem_bytes(int n_cells) {
-    const size_t a = main_smem_bytes(n_cells, 0);
+    const size_t a = main_smem_bytes(n_cells, 0, false);
     const size_t b = tail_smem_bytes(n_cells);
     return (int)(a > b ? a : b);
 }

@@ -75,9 +75,27 @@ def test_unknown_scheme_is_rejected(abi):
     from paper_1310_5284_gb300.sim import make_config
     c = make_config(dict(workloads.CFG_SMALL_CCP))
     s = abi.PicSizes()
-    for scheme, code in ((0, 0), (1, 0), (2, 0), (3, 0), (4, -1), (-1, -1)):
+    for scheme, code in ((0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (5, -1), (-1, -1)):
         c.scheme = scheme
         assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == code, scheme
+
+
+def test_m3_scheme_limits(abi):
+    """The m = 3 scheme: capacity below 2^23 a species (int64 headroom of
+    charges of 6 * 2^36 a particle); single runs only."""
+    from paper_1310_5284_gb300.sim import make_config
+    c = make_config(dict(workloads.CFG_SMALL_CCP, scheme="ec3_explicit"))
+    s = abi.PicSizes()
+    assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == 0
+    c.capacity[0] = (1 << 23) - 1
+    assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == 0
+    c.capacity[0] = 1 << 23
+    assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == -4
+    arr = (abi.PicConfig * 2)(make_config(dict(workloads.CFG_SMALL_CCP)),
+                              make_config(dict(workloads.CFG_SMALL_CCP, scheme="ec3_explicit")))
+    assert abi.lib().pic_batch_required_sizes(arr, 2, ctypes.byref(s)) == -1
+    assert b"m = 3" in abi.lib().pic_last_error(None)
+    assert abi.lib().pic_batch_required_sizes(arr, 1, ctypes.byref(s)) == 0
 
 
 @pytest.mark.parametrize("bad,code", [

@@ -191,6 +191,11 @@ DEPOSIT_CASES = [
     ("mc_periodic_33", dict(n_cells=33, periodic=True, scheme="mc_explicit", rf_volt=0.0), 4_321, False),
     ("mc_implicit_dirichlet_45", dict(n_cells=45, scheme="mc_implicit"), 7_777, False),
     ("ec_tiny_2cells", dict(n_cells=2), 5, False),
+    ("ec3_dirichlet_64", dict(n_cells=64, scheme="ec3_explicit"), 12_800, False),
+    ("ec3_periodic_100", dict(n_cells=100, periodic=True, rf_volt=0.0, scheme="ec3_explicit"), 10_007, False),
+    ("ec3_dirichlet_1024_sorted", dict(n_cells=1024, scheme="ec3_explicit"), 300_001, True),
+    ("ec3_periodic_3", dict(n_cells=3, periodic=True, rf_volt=0.0, scheme="ec3_explicit"), 1_001, False),
+    ("ec3_tiny_2cells", dict(n_cells=2, scheme="ec3_explicit"), 5, False),
 ]
 
 
@@ -204,7 +209,8 @@ def test_deposit_bitexact_and_field(name, over, n, srt):
     g, o = gpu.grids(), orc.grids()
     assert np.array_equal(g["rho_q_e"], o["rho_q_e"]), name
     assert np.array_equal(g["rho_q_i"], o["rho_q_i"]), name
-    assert g["rho_q_e"].sum() == n * 2 ** 33 and g["rho_q_i"].sum() == n * 2 ** 33
+    unit = 6 * 2 ** 36 if cfg.get("scheme") == "ec3_explicit" else 2 ** 33  # one particle's charge
+    assert g["rho_q_e"].sum() == n * unit and g["rho_q_i"].sum() == n * unit
     scale = max(np.abs(o["e_cc"]).max(), 1e-300)
     np.testing.assert_allclose(g["e_cc"], o["e_cc"], rtol=0, atol=1e-9 * scale)
     pscale = max(np.abs(o["phi"]).max(), 1e-300)
@@ -243,6 +249,10 @@ STEP_CASES = [
     ("mc_implicit_periodic", dict(n_cells=50, periodic=True, mcc=False, rf_volt=0.0,
                                   scheme="mc_implicit", dt=8e-10), 10, 100),
     ("mc_implicit_ragged_37", dict(n_cells=37, mcc=False, scheme="mc_implicit", dt=3e-10), 10, 40),
+    ("ec3_periodic_collisionless", dict(n_cells=64, periodic=True, mcc=False, rf_volt=0.0,
+                                        scheme="ec3_explicit"), 30, 100),
+    ("ec3_electrodes_rf_collisionless", dict(n_cells=64, mcc=False, scheme="ec3_explicit"), 30, 100),
+    ("ec3_ragged_37", dict(n_cells=37, mcc=False, scheme="ec3_explicit"), 30, 60),
 ]
 
 
@@ -286,7 +296,7 @@ def test_steps_match_oracle(name, over, strict, steps):
     assert dg["field_energy"] == pytest.approx(do["field_energy"], rel=5e-2)
 
 
-@pytest.mark.parametrize("scheme", ["ec_explicit", "ec_implicit", "mc_implicit"])
+@pytest.mark.parametrize("scheme", ["ec_explicit", "ec_implicit", "mc_implicit", "ec3_explicit"])
 def test_collisions_counts_exact_and_births_ranked(scheme):
     """Null-collision MCC on the same Philox stream: selection is an integer
     compare, so tallies and births agree exactly; children get the same ids
@@ -308,7 +318,7 @@ def test_collisions_counts_exact_and_births_ranked(scheme):
     # the collision kinematics (sqrt, sincospi, log in FP32) add their own
     # rounding to that of the push: 99.9% within 1e-5, all within 1e-4
     compare_particles(gpu, orc, cfg, quantile=0.999, max_tol=1e-4)
-    if scheme != "ec_explicit":  # abar of parents and children, relative to its scale
+    if scheme in ("ec_implicit", "mc_implicit"):  # abar of parents and children, relative to its scale
         for sp in ("e", "i"):
             a, b = by_id(gpu.get_particles(sp)), by_id(orc.get_species(sp))
             d = np.abs(a["abar"].astype(np.float64) - b["abar"]) / np.abs(b["abar"]).max()
@@ -337,11 +347,12 @@ def test_many_births_per_step_ranked_like_oracle(n):
     compare_particles(gpu, orc, cfg, quantile=0.999, max_tol=1e-4)
 
 
-def test_sorting_and_graph_replay_do_not_change_results():
+@pytest.mark.parametrize("scheme", ["ec_explicit", "ec3_explicit"])
+def test_sorting_and_graph_replay_do_not_change_results(scheme):
     """Charge sums are integers and draws are keyed on (id, step), so the
     slot order (sorted or not) and graph replay leave every particle
     bit-identical."""
-    base = dict(workloads.CFG_SMALL_CCP, np_init=12_800)
+    base = dict(workloads.CFG_SMALL_CCP, np_init=12_800, scheme=scheme)
     outs = []
     for sp in (0, 1, 16):
         cfg = dict(base, sort_period=sp)

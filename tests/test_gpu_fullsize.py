@@ -1,0 +1,115 @@
+"""Parity at the benchmark's full size, in the launch configuration bench.py
+times: the production explicit workload ccp_512cells_2048000ppsp (6.7 cm,
+512 cells, 2,048,000 macro-particles per species, 450 V, 13.56 MHz,
+30 mTorr, null-collision MCC on), loaded and sorted on the GPU, stepped with
+pic_step(1).  The FP64 oracle takes the GPU's own state and steps it too
+(about 0.15 s a step for 4.1 M particles), so every particle is compared,
+not a sample.
+
+Bars: the uniform load's positions bit-exact against the oracle's load; the
+int64 node charges of the state bit-exact; after five steps, per particle
+|dx| <= 1e-5 L and |dv| <= 1e-5 max(|v|, v_th) for 99.9 % of the particles
+and 1e-4 for all (collision kinematics in FP32, as in the small collision
+test); the selection count exact (an integer test on the same Philox words).
+A collision's outcome or an absorption decided on a float within rounding
+of its threshold may differ between FP32 and FP64 for a handful of the
+4.1 M particles: those tallies and the particle sets may differ by a few.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+E = 1.602176634e-19
+ME = 9.1093837015e-31
+AMU = 1.66053906660e-27
+FEW = 6  # threshold decisions that FP32 and FP64 may take differently in 5 steps
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def vth(cfg, k):
+    m = ME if k == 0 else cfg.get("ion_mass_amu", 39.948) * AMU
+    t = cfg.get("te_ev", 2.0) if k == 0 else cfg.get("ti_ev", 0.026)
+    return float(np.sqrt(E * t / m))
+
+
+def by_id(d):
+    o = np.argsort(d["id"], kind="stable")
+    return {k: (v[o] if isinstance(v, np.ndarray) else v) for k, v in d.items()}
+
+
+@pytest.mark.parametrize("scheme", ["ec_explicit", "ec3_explicit"])
+def test_full_size_load_charge_and_steps_match_oracle(scheme):
+    from paper_1310_5284_gb300.sim import Sim
+    cfg = dict(workloads.CFG_WIDE_EXPLICIT, scheme=scheme)
+    n = cfg["np_init"]
+    gpu = Sim(cfg, device="cuda:0")
+    # the load: positions are exact (24-bit offsets) and keyed on the id
+    ref = oracle.Sim(cfg).load(n, n)
+    for k, sp in enumerate(("e", "i")):
+        a = by_id(gpu.get_particles(sp))
+        b = by_id(ref.get_species(sp))
+        assert np.array_equal(a["id"], np.arange(n))
+        assert np.array_equal(a["cell"].astype(np.float64) + a["off"].astype(np.float64), b["xi"])
+    del ref
+    # the GPU's sorted state, as stored, into the oracle
+    orc = oracle.Sim(cfg)
+    for sp in ("e", "i"):
+        s = gpu.get_particles(sp)
+        orc.set_species(sp, workloads.xi_of(s), s["vx"].astype(np.float64), s["vy"].astype(np.float64),
+                        s["vz"].astype(np.float64), s["id"], next_id=n)
+    orc.init_field(set_abar=False)
+    g, o = gpu.grids(), orc.grids()
+    unit = 6 * 2 ** 36 if scheme == "ec3_explicit" else 2 ** 33
+    assert np.array_equal(g["rho_q_e"], o["rho_q_e"]) and np.array_equal(g["rho_q_i"], o["rho_q_i"])
+    assert g["rho_q_e"].sum() == n * unit == g["rho_q_i"].sum()
+    np.testing.assert_allclose(g["e_cc"], o["e_cc"], rtol=0, atol=1e-9 * np.abs(o["e_cc"]).max())
+    # five steps, one launch each, as the benchmark steps
+    for _ in range(5):
+        gpu.step(1)
+    orc.step(5)
+    assert gpu.status() == 0
+    dg, do = gpu.diag(), orc.diag()
+    assert dg["step"] == do["step"] == 5
+    L = cfg["n_cells"]
+    same_sets = True
+    states = []
+    for sp in ("e", "i"):
+        a = by_id(gpu.get_particles(sp))
+        b = by_id(orc.get_species(sp))
+        common, ia, ib = np.intersect1d(a["id"], b["id"], assume_unique=True, return_indices=True)
+        assert len(a["id"]) - len(common) <= FEW and len(b["id"]) - len(common) <= FEW
+        same_sets &= len(common) == len(a["id"]) == len(b["id"])
+        states.append((a, b, ia, ib))
+    # selections are an integer test on the same Philox words: exact while the
+    # particle sets agree
+    assert abs(sum(dg["coll"]) - sum(do["coll"])) <= (0 if same_sets else FEW)
+    assert sum(do["coll"]) > 100_000
+    for a, b in zip(dg["coll"], do["coll"]):
+        assert abs(a - b) <= FEW
+    assert abs(dg["births"] - do["births"]) <= FEW and do["births"] > 0
+    for k in range(2):
+        assert abs(dg["count"][k] - do["count"][k]) <= FEW
+        for w in range(2):
+            assert abs(dg["wall_count"][k][w] - do["wall_count"][k][w]) <= FEW
+    for k, sp in enumerate(("e", "i")):
+        a, b, ia, ib = states[k]
+        dxi = np.abs(a["cell"][ia].astype(np.float64) + a["off"][ia].astype(np.float64) - b["xi"][ib])
+        dv = np.zeros_like(dxi)
+        for comp in ("vx", "vy", "vz"):
+            bound = np.maximum(np.abs(b[comp][ib]), vth(cfg, k))
+            dv = np.maximum(dv, np.abs(a[comp][ia].astype(np.float64) - b[comp][ib]) / bound)
+        assert np.quantile(dxi, 0.999) <= 1e-5 * L and np.quantile(dv, 0.999) <= 1e-5, (sp, scheme)
+        assert dxi.max() <= 1e-4 * L and dv.max() <= 1e-4, (sp, scheme, dxi.max(), dv.max())
+    for k in range(2):
+        assert dg["ke_x"][k] == pytest.approx(do["ke_x"][k], rel=1e-4)
+    assert dg["field_energy"] == pytest.approx(do["field_energy"], rel=1e-3)
+    gpu.close()

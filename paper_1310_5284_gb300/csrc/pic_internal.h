@@ -229,6 +229,9 @@ cudaError_t launch_set_abar(const Run &r, cudaStream_t s);
 cudaError_t launch_check_particles(const int32_t *cell, const float *off, long long n, int n_cells,
                                    unsigned int *flag, cudaStream_t s);
 cudaError_t launch_perp_energy(const Run &r, cudaStream_t s);
+cudaError_t launch_apply_particles(const Species &dst, const Species &src, long long n, bool abar_given,
+                                   const unsigned int *flag, DevState *st, int S, unsigned int next_id,
+                                   cudaStream_t s);
 cudaError_t launch_finalize(const Run &r, cudaStream_t s);
 cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
                                uint32_t c3, long long n, uint32_t *out, cudaStream_t s);

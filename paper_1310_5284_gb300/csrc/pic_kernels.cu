@@ -2677,16 +2677,72 @@ cudaError_t launch_check_particles(const int32_t *cell, const float *off, long l
     return cudaGetLastError();
 }
 
-// Kinetic energy of the transverse velocities (diagnostics only).
+// After the check (flag clear): the uploaded particles of one species from
+// the idle buffer into the current one, and the species' counters.  A set
+// flag leaves everything as it was; the caller reads the flag afterwards.
+// 16-byte copies: every array starts 256-byte aligned.
+__global__ void k_apply_particles(Species dst, Species src, long long n, bool abar_given, const unsigned int *flag,
+                                  DevState *st, int S, unsigned int next_id) {
+    if (*flag) return;
+    const long long n4 = n >> 2, stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long j = t0; j < n4; j += stride) {
+        reinterpret_cast<int4 *>(dst.cell)[j] = reinterpret_cast<const int4 *>(src.cell)[j];
+        reinterpret_cast<float4 *>(dst.off)[j] = reinterpret_cast<const float4 *>(src.off)[j];
+        reinterpret_cast<float4 *>(dst.vx)[j] = reinterpret_cast<const float4 *>(src.vx)[j];
+        reinterpret_cast<float4 *>(dst.vy)[j] = reinterpret_cast<const float4 *>(src.vy)[j];
+        reinterpret_cast<float4 *>(dst.vz)[j] = reinterpret_cast<const float4 *>(src.vz)[j];
+        reinterpret_cast<uint4 *>(dst.id)[j] = reinterpret_cast<const uint4 *>(src.id)[j];
+        if (dst.abar)
+            reinterpret_cast<float4 *>(dst.abar)[j] =
+                abar_given ? reinterpret_cast<const float4 *>(src.abar)[j] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    for (long long i = 4 * n4 + t0; i < n; i += stride) {
+        dst.cell[i] = src.cell[i];
+        dst.off[i] = src.off[i];
+        dst.vx[i] = src.vx[i];
+        dst.vy[i] = src.vy[i];
+        dst.vz[i] = src.vz[i];
+        dst.id[i] = src.id[i];
+        if (dst.abar) dst.abar[i] = abar_given ? src.abar[i] : 0.0f;
+    }
+    if (t0 == 0) {
+        st->n_slots[S] = n;
+        st->n_live[S] = n;
+        st->next_id[S] = next_id;
+    }
+}
+
+cudaError_t launch_apply_particles(const Species &dst, const Species &src, long long n, bool abar_given,
+                                   const unsigned int *flag, DevState *st, int S, unsigned int next_id,
+                                   cudaStream_t s) {
+    long long grid = (n / 4 + kThreads - 1) / kThreads;
+    if (grid < 1) grid = 1;
+    if (grid > 4096) grid = 4096;
+    k_apply_particles<<<(int)grid, kThreads, 0, s>>>(dst, src, n, abar_given, flag, st, S, next_id);
+    return cudaGetLastError();
+}
+
+// Kinetic energy of the transverse velocities (diagnostics only): four
+// particles a thread per pass with 16-byte loads (slot arrays are 256-byte
+// aligned), their FP32 sum added in FP64.
 __global__ void k_perp_energy(Run R) {
     const DevState *st = R.st;
     const int par = st->parity;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
     for (int S = 0; S < 2; ++S) {
         const Species sp = R.buf[par][S];
-        const long long n = st->n_slots[S];
+        const long long n = st->n_slots[S], n4 = n >> 2;
         double acc = 0.0;
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-             i += (long long)gridDim.x * blockDim.x) {
+        for (long long j = t0; j < n4; j += stride) {
+            const int4 c = reinterpret_cast<const int4 *>(sp.cell)[j];
+            const float4 y = reinterpret_cast<const float4 *>(sp.vy)[j];
+            const float4 z = reinterpret_cast<const float4 *>(sp.vz)[j];
+            const float e = (c.x >= 0 ? y.x * y.x + z.x * z.x : 0.0f) + (c.y >= 0 ? y.y * y.y + z.y * z.y : 0.0f) +
+                            (c.z >= 0 ? y.z * y.z + z.z * z.z : 0.0f) + (c.w >= 0 ? y.w * y.w + z.w * z.w : 0.0f);
+            acc += (double)e;
+        }
+        for (long long i = 4 * n4 + t0; i < n; i += stride) {
             if (sp.cell[i] < 0) continue;
             const float vy = sp.vy[i], vz = sp.vz[i];
             acc += (double)(vy * vy + vz * vz);
@@ -3027,7 +3083,11 @@ cudaError_t launch_set_abar(const Run &r, cudaStream_t s) {
 }
 
 cudaError_t launch_perp_energy(const Run &r, cudaStream_t s) {
-    k_perp_energy<<<1024, kThreads, 0, s>>>(r);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    k_perp_energy<<<sms * 4, kThreads, 0, s>>>(r);
     return cudaGetLastError();
 }
 

@@ -229,8 +229,7 @@ def run_e2e(sim, steps, dev):
     n_proc = 0
     d2h = 0
     for _ in range(steps):
-        for sp in ("e", "i"):
-            sim.set_particles(sp, host[sp][0], next_id=host[sp][1])
+        sim.set_state(host["e"][0], host["i"][0], next_id_e=host["e"][1], next_id_i=host["i"][1])
         sim.init_field(set_abar=False)
         sim.step(1)
         d = sim.diag()

@@ -220,6 +220,13 @@ int pic_get_particles(pic_handle *h, int species, pic_host_particles *out);
    pic_init_field() after setting both species. */
 int pic_set_particles(pic_handle *h, int species, const pic_host_particles *in);
 
+/* Both species at once, as pic_set_particles does one: the uploads, both
+   checks and then both moves into the current buffer run back to back on the
+   run's stream with one synchronisation at the end; if a particle of either
+   species is off the grid the call returns PIC_EINVAL and neither species
+   changes.  PIC_EINVAL for a NULL argument. */
+int pic_set_state(pic_handle *h, const pic_host_particles *electrons, const pic_host_particles *ions);
+
 /* Assign charge for the current particles and solve for the field at the
    current time level; set_abar != 0 also sets abar = (q/m) E(x) for the
    implicit scheme. */

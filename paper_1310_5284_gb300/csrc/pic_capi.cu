@@ -334,11 +334,10 @@ int sync(pic_handle *h) {
     return PIC_OK;
 }
 
+// The device state record after everything enqueued so far (one sync).
 int read_state(pic_handle *h, DevState *st) {
-    int r = sync(h);
-    if (r) return r;
-    CK(h, cudaMemcpy(st, h->run.st, sizeof(DevState), cudaMemcpyDeviceToHost));
-    return PIC_OK;
+    CK(h, cudaMemcpyAsync(st, h->run.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    return sync(h);
 }
 
 }  // namespace
@@ -370,9 +369,9 @@ int run_diag(const Run &R, const pic_config &c, const Layout &L, unsigned char *
     CKE(launch_finalize(R, s));  // work the last tail left to the next launch
     CKE(cudaMemsetAsync(R.st->ke_perp, 0, sizeof(double) * 2, s));
     CKE(launch_perp_energy(R, s));
-    CKE(cudaStreamSynchronize(s));
     DevState st;
-    CKE(cudaMemcpy(&st, R.st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    CKE(cudaMemcpyAsync(&st, R.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CKE(cudaStreamSynchronize(s));
     std::memset(out, 0, sizeof *out);
     out->step = st.step;
     for (int k = 0; k < 2; ++k) {
@@ -673,44 +672,92 @@ int pic_get_particles(pic_handle *h, int species, pic_host_particles *out) {
     return run_get_particles(h->run, h->stream, species, out, &h->err);
 }
 
-int pic_set_particles(pic_handle *h, int species, const pic_host_particles *in) {
-    if (!h || !in || species < 0 || species > 1) return fail(PIC_EINVAL, "bad argument");
+namespace {
+
+int check_upload_args(const pic_handle *h, int species, const pic_host_particles *in) {
+    if (!in || species < 0 || species > 1) return fail(PIC_EINVAL, "bad argument");
     const long long n = in->count;
     if (n < 0 || n > h->cfg.capacity[species]) return fail(PIC_EOVERFLOW, "count %lld exceeds capacity", (long long)n);
     if (species == 1 && !h->cfg.ions_mobile && n > 0) return fail(PIC_EINVAL, "ions are frozen in this run");
     if (n > 0 && (!in->cell || !in->off || !in->vx || !in->vy || !in->vz || !in->id))
         return fail(PIC_EINVAL, "NULL particle array");
+    return PIC_OK;
+}
+
+// Host arrays of one species into the idle second buffer, and their check
+// (cell in [0, n_cells), offset in [0, 1)) into the state's check word.
+int enqueue_upload(pic_handle *h, unsigned int parity, int species, const pic_host_particles *in) {
+    const long long n = in->count;
+    const Species &sp = h->run.buf[parity][species];
+    const Species &up = h->run.buf[parity ^ 1u][species];
+    if (n <= 0) return PIC_OK;
+    const bool abar_given = sp.abar && in->abar;
+    const void *src[7] = {in->cell, in->off, in->vx, in->vy, in->vz, in->id, in->abar};
+    void *tmp[7] = {up.cell, up.off, up.vx, up.vy, up.vz, up.id, up.abar};
+    for (int f = 0; f < (abar_given ? 7 : 6); ++f)
+        CK(h, cudaMemcpyAsync(tmp[f], src[f], 4 * n, cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_check_particles(up.cell, up.off, n, h->cfg.n_cells, &h->run.st->check, h->stream));
+    return PIC_OK;
+}
+
+// The checked upload into the current buffer, with the species' counters,
+// unless a check set the flag (then nothing changes).
+int enqueue_apply(pic_handle *h, unsigned int parity, int species, const pic_host_particles *in) {
+    const Species &sp = h->run.buf[parity][species];
+    const Species &up = h->run.buf[parity ^ 1u][species];
+    CK(h, launch_apply_particles(sp, up, in->count, sp.abar && in->abar, &h->run.st->check, h->run.st, species,
+                                 in->next_id, h->stream));
+    return PIC_OK;
+}
+
+// After the sync: name the first particle off the grid, if the flag is set.
+int name_offender(pic_handle *h, const pic_host_particles *in) {
+    for (long long i = 0; i < in->count; ++i)
+        if (in->cell[i] < 0 || in->cell[i] >= h->cfg.n_cells || !(in->off[i] >= 0.0f) || !(in->off[i] < 1.0f))
+            return fail(PIC_EINVAL, "particle %lld outside the grid (cell %d, offset %g)", i, in->cell[i],
+                        (double)in->off[i]);
+    return PIC_OK;
+}
+
+// Upload, check and apply the given species (nullptr: left as it is); if any
+// particle of any of them is off the grid nothing is applied.
+int set_species(pic_handle *h, const pic_host_particles *const in[2]) {
+    for (int S = 0; S < 2; ++S) {
+        if (!in[S]) continue;
+        int r = check_upload_args(h, S, in[S]);
+        if (r) return r;
+    }
     DevState st;
     int r = read_state(h, &st);
     if (r) return r;
-    // Upload into the idle second buffer and check the positions there; a
-    // device kernel then moves them into the current buffer and sets the
-    // counters only if the check found nothing (so nothing is applied when a
-    // particle is off the grid), and the host reads the flag after one sync.
-    const Species &sp = h->run.buf[st.parity][species];
-    const Species &up = h->run.buf[st.parity ^ 1u][species];
-    const bool abar_given = sp.abar && in->abar;
-    if (n > 0) {
-        const void *src[7] = {in->cell, in->off, in->vx, in->vy, in->vz, in->id, in->abar};
-        void *tmp[7] = {up.cell, up.off, up.vx, up.vy, up.vz, up.id, up.abar};
-        for (int f = 0; f < (abar_given ? 7 : 6); ++f)
-            CK(h, cudaMemcpyAsync(tmp[f], src[f], 4 * n, cudaMemcpyHostToDevice, h->stream));
-    }
     CK(h, cudaMemsetAsync(&h->run.st->check, 0, 4, h->stream));
-    if (n > 0) CK(h, launch_check_particles(up.cell, up.off, n, h->cfg.n_cells, &h->run.st->check, h->stream));
-    CK(h, launch_apply_particles(sp, up, n, abar_given, &h->run.st->check, h->run.st, species, in->next_id,
-                                 h->stream));
+    for (int S = 0; S < 2; ++S)
+        if (in[S] && (r = enqueue_upload(h, st.parity, S, in[S]))) return r;
+    for (int S = 0; S < 2; ++S)
+        if (in[S] && (r = enqueue_apply(h, st.parity, S, in[S]))) return r;
     CK(h, cudaMemcpyAsync(&h->check_host, &h->run.st->check, 4, cudaMemcpyDeviceToHost, h->stream));
     r = sync(h);
     if (r) return r;
     if (h->check_host) {
-        for (long long i = 0; i < n; ++i)  // name the first offender
-            if (in->cell[i] < 0 || in->cell[i] >= h->cfg.n_cells || !(in->off[i] >= 0.0f) || !(in->off[i] < 1.0f))
-                return fail(PIC_EINVAL, "particle %lld outside the grid (cell %d, offset %g)", i, in->cell[i],
-                            (double)in->off[i]);
+        for (int S = 0; S < 2; ++S)
+            if (in[S] && (r = name_offender(h, in[S]))) return r;
         return fail(PIC_EINVAL, "a particle is outside the grid");
     }
     return PIC_OK;
+}
+
+}  // namespace
+
+int pic_set_particles(pic_handle *h, int species, const pic_host_particles *in) {
+    if (!h || !in || species < 0 || species > 1) return fail(PIC_EINVAL, "bad argument");
+    const pic_host_particles *both[2] = {species == 0 ? in : nullptr, species == 1 ? in : nullptr};
+    return set_species(h, both);
+}
+
+int pic_set_state(pic_handle *h, const pic_host_particles *electrons, const pic_host_particles *ions) {
+    if (!h || !electrons || !ions) return fail(PIC_EINVAL, "bad argument");
+    const pic_host_particles *both[2] = {electrons, ions};
+    return set_species(h, both);
 }
 
 int pic_set_step(pic_handle *h, int64_t step) {

@@ -187,8 +187,9 @@ class Sim:
         res["next_id"] = int(hp.next_id)
         return res
 
-    def set_particles(self, species, state: dict, next_id: int | None = None):
-        k = SPECIES[species]
+    @staticmethod
+    def _host_particles(state: dict, next_id: int | None):
+        """(pic_host_particles, the arrays it points into) for one species."""
         arrs = {
             "cell": np.ascontiguousarray(state["cell"], np.int32),
             "off": np.ascontiguousarray(state["off"], np.float32),
@@ -206,7 +207,19 @@ class Sim:
                                    _fptr(arrs["vx"], ctypes.c_float), _fptr(arrs["vy"], ctypes.c_float),
                                    _fptr(arrs["vz"], ctypes.c_float), _fptr(arrs["id"], ctypes.c_uint32),
                                    _fptr(arrs["abar"], ctypes.c_float), int(next_id))
-        self._check(_abi.lib().pic_set_particles(self._h, k, ctypes.byref(hp)))
+        return hp, arrs
+
+    def set_particles(self, species, state: dict, next_id: int | None = None):
+        hp, _arrs = self._host_particles(state, next_id)
+        self._check(_abi.lib().pic_set_particles(self._h, SPECIES[species], ctypes.byref(hp)))
+        return self
+
+    def set_state(self, electrons: dict, ions: dict, next_id_e: int | None = None, next_id_i: int | None = None):
+        """Both species in one call (pic_set_state): neither changes if a
+        particle of either is off the grid."""
+        he, _ae = self._host_particles(electrons, next_id_e)
+        hi, _ai = self._host_particles(ions, next_id_i)
+        self._check(_abi.lib().pic_set_state(self._h, ctypes.byref(he), ctypes.byref(hi)))
         return self
 
     # ---- checkpoint ----

@@ -439,6 +439,44 @@ def test_set_particles_rejects_off_grid_and_applies_nothing(bad):
     gpu.close()
 
 
+@pytest.mark.parametrize("scheme", ["ec_explicit", "ec_implicit"])
+def test_set_state_is_both_uploads_in_one_call(scheme):
+    """pic_set_state gives the run exactly what two pic_set_particles calls
+    give (every particle after ten steps), and a particle off the grid in
+    either species leaves both species as they were."""
+    from paper_1310_5284_gb300._abi import PicError
+
+    cfg = dict(workloads.CFG_SMALL_CCP, np_init=6000, scheme=scheme)
+    st = states_for(cfg, 5000, 21)
+    if scheme == "ec_implicit":
+        rng = np.random.default_rng(5)
+        for s in st:
+            s["abar"] = rng.normal(size=len(s["id"])).astype(np.float32) * 1e12
+    a, b = gpu_sim(cfg), gpu_sim(cfg)
+    a.set_particles("e", st[0])
+    a.set_particles("i", st[1])
+    b.set_state(st[0], st[1])
+    for g in (a, b):
+        g.set_step(11)
+        g.init_field(set_abar=False)
+        g.step(10)
+    for sp in ("e", "i"):
+        pa, pb = by_id(a.get_particles(sp)), by_id(b.get_particles(sp))
+        for key in ("id", "cell", "off", "vx", "vy", "vz", "abar"):
+            assert np.array_equal(pa[key], pb[key]), (sp, key)
+    before = {sp: by_id(b.get_particles(sp)) for sp in ("e", "i")}
+    bad = {k: v.copy() for k, v in st[1].items()}
+    bad["cell"][77] = cfg["n_cells"]
+    with pytest.raises(PicError, match="particle 77 outside the grid"):
+        b.set_state(st[0], bad)
+    for sp in ("e", "i"):
+        after = by_id(b.get_particles(sp))
+        for key in ("id", "cell", "off", "vx", "vy", "vz"):
+            assert np.array_equal(before[sp][key], after[key]), (sp, key)
+    a.close()
+    b.close()
+
+
 def test_high_selection_implicit_run_keeps_the_drain_in_step():
     """A direct-implicit discharge at omega_p dt = 2 selects about a third of
     its particles for a collision every step, so the collision queue crosses

@@ -56,7 +56,8 @@ extern "C" {
 /* Device status bits (pic_diag_t.status, pic_status). */
 #define PIC_STATUS_CAPACITY 0x1u    /* particles dropped: slot capacity exhausted */
 #define PIC_STATUS_BIRTHS 0x2u      /* births dropped: per-step birth buffer full */
-#define PIC_STATUS_TIMEOUT 0x4u     /* a bounded wait ran out (batched driver) */
+#define PIC_STATUS_TIMEOUT 0x4u     /* a bounded device wait ran out (about a second; the launch
+                                       ended its stream early: the step is incomplete) */
 #define PIC_STATUS_QUEUE 0x8u       /* a selected collision found the collision queue full
                                        (drains keep room for a whole tile: not expected) */
 
@@ -188,7 +189,9 @@ int pic_init(const pic_config *cfg, const pic_buffers *bufs, void *stream, pic_h
 int pic_step(pic_handle *h, int64_t n);
 
 /* Synchronise and read the diagnostics.  reset_avg != 0 clears the running
-   time averages (densities, potential, heating, EEDF) after reading. */
+   time averages (densities, potential, heating, EEDF) after reading.
+   Returns PIC_ETIMEOUT (with *out filled) once the sticky status holds
+   PIC_STATUS_TIMEOUT. */
 int pic_diag(pic_handle *h, pic_diag_t *out, int reset_avg);
 
 /* Time-averaged profiles since the last reset, each may be NULL:
@@ -243,6 +246,17 @@ int pic_status(pic_handle *h, uint32_t *status);
    continues exactly as the original would have. */
 int pic_save(pic_handle *h, void *host_buf, size_t nbytes);
 int pic_load(pic_handle *h, const void *host_buf, size_t nbytes);
+
+/* Self-test of the bounded device waits.  Every wait of the particle
+   launches (a staged copy landing in shared memory) gives up after about a
+   second, sets PIC_STATUS_TIMEOUT and lets the launch end, so a copy that
+   never lands cannot hang the GPU.  This call runs that same wait once, in a
+   one-thread launch, on a barrier that nothing completes (no copy is issued)
+   with the given limit, and returns PIC_ETIMEOUT with *status =
+   PIC_STATUS_TIMEOUT and *waited_s the time the wait took; the context stays
+   usable.  limit_ns in 0 .. 1e10; PIC_EINVAL otherwise or for a NULL output;
+   PIC_ECUDA if the launch fails.  Synchronous on `stream`. */
+int pic_selftest_wait(int64_t limit_ns, uint32_t *status, double *waited_s, void *stream);
 
 /* Fill a device buffer with n Philox4x32-10 blocks: key (k0, k1), counter
    (c0 + i, c1, c2, c3) for block i; out receives 4n uint32 words. */

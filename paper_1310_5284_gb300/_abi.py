@@ -96,6 +96,7 @@ SIGNATURES = {
     "pic_get_particles": ([_vp, ctypes.c_int, _P(PicHostParticles)], ctypes.c_int),
     "pic_set_particles": ([_vp, ctypes.c_int, _P(PicHostParticles)], ctypes.c_int),
     "pic_set_state": ([_vp, _P(PicHostParticles), _P(PicHostParticles)], ctypes.c_int),
+    "pic_selftest_wait": ([ctypes.c_int64, _P(ctypes.c_uint32), _P(ctypes.c_double), _vp], ctypes.c_int),
     "pic_init_field": ([_vp, ctypes.c_int], ctypes.c_int),
     "pic_set_step": ([_vp, ctypes.c_int64], ctypes.c_int),
     "pic_status": ([_vp, _P(ctypes.c_uint32)], ctypes.c_int),

@@ -589,7 +589,12 @@ int pic_step(pic_handle *h, int64_t n) {
 
 int pic_diag(pic_handle *h, pic_diag_t *out, int reset_avg) {
     if (!h || !out) return fail(PIC_EINVAL, "NULL argument");
-    return run_diag(h->run, h->cfg, h->layout, h->arena, h->stream, out, reset_avg, &h->err);
+    const int r = run_diag(h->run, h->cfg, h->layout, h->arena, h->stream, out, reset_avg, &h->err);
+    if (r) return r;
+    if (out->status & PIC_STATUS_TIMEOUT)
+        return fail(PIC_ETIMEOUT, "a bounded device wait gave up (status 0x%x): a launch ended its stream early",
+                    out->status);
+    return PIC_OK;
 }
 
 int pic_profiles(pic_handle *h, double *ne, double *ni, double *phi, double *heat_e,

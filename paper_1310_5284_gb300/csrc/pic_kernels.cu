@@ -873,7 +873,15 @@ static_assert(kQueueDrainAbove + kTile <= kQueue, "a tile must fit the undrained
 #endif
 constexpr int kStages = PIC_STAGES;
 constexpr int kMaxFields = 5;  // cell, off, vx, abar, id
-constexpr long long kWaitLimit = 1ll << 20;
+// A wait gives up after about a second (or 2^30 polls, whichever comes first).
+constexpr unsigned long long kWaitNs = 1000000000ull;
+constexpr long long kWaitPolls = 1ll << 30;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -907,13 +915,40 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned int p
     return done != 0;
 }
 
+// Wait for one phase of a barrier for at most limit_ns; false if it never
+// completed.  The clock is read only once the first poll has failed.
+__device__ __forceinline__ bool mbar_wait_for(unsigned long long *bar, unsigned int parity,
+                                              unsigned long long limit_ns) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (long long i = 0; i < kWaitPolls; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > limit_ns) break;
+    }
+    return false;
+}
+
 // Bounded wait for one phase of a stage barrier; false (status bit set) if it
 // never completed.
 __device__ __forceinline__ bool mbar_wait(const Run &R, unsigned long long *bar, unsigned int parity) {
-    for (long long i = 0; i < kWaitLimit; ++i)
-        if (mbar_try(bar, parity)) return true;
+    if (mbar_wait_for(bar, parity, kWaitNs)) return true;
     atomicOr(&R.st->status, 0x4u);
     return false;
+}
+
+// The wait of the particle launches on a barrier that nothing completes: one
+// arrival with 16 bytes expected and no copy issued, so the phase never ends,
+// no memory is ever written to it and the wait can only run out.
+__global__ void k_wait_selftest(unsigned long long limit_ns, unsigned int *status, unsigned long long *waited_ns) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1u);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&bar, 16u);
+    const unsigned long long t0 = globaltimer_ns();
+    const bool done = mbar_wait_for(&bar, 0u, limit_ns);
+    *waited_ns = globaltimer_ns() - t0;
+    *status = done ? 0u : 0x4u;
 }
 
 // The ring: kStages x nf arrays of kTile words, one barrier per stage.  The
@@ -3715,3 +3750,42 @@ cudaError_t launch_adj_rev(const Run &r, const AdjRev &a, int grid, cudaStream_t
 }
 
 }  // namespace pic
+
+// ===========================================================================
+// Self-test of the bounded waits (see pic.h): one launch of k_wait_selftest.
+// ===========================================================================
+namespace pic {
+namespace selftest {
+struct WaitResult {
+    unsigned long long waited_ns;
+    unsigned int status;
+    unsigned int pad;
+};
+static __device__ WaitResult g_wait_result;
+}  // namespace selftest
+}  // namespace pic
+
+extern "C" int pic_selftest_wait(int64_t limit_ns, uint32_t *status, double *waited_s, void *stream) {
+    using namespace pic;
+    if (limit_ns < 0 || limit_ns > 10ll * 1000000000ll || !status || !waited_s) {
+        set_last_error("pic_selftest_wait: limit_ns outside 0..1e10 or a NULL output");
+        return -1;
+    }
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, selftest::g_wait_result) != cudaSuccess || !p) {
+        set_last_error("pic_selftest_wait: cudaGetSymbolAddress failed");
+        return -5;
+    }
+    selftest::WaitResult *d = (selftest::WaitResult *)p;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_wait_selftest<<<1, 32, 0, s>>>((unsigned long long)limit_ns, &d->status, &d->waited_ns);
+    selftest::WaitResult h{};
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_last_error("pic_selftest_wait: launch or read-back failed");
+        return -5;
+    }
+    *status = h.status;
+    *waited_s = 1e-9 * (double)h.waited_ns;
+    return h.status ? -6 : 0;
+}

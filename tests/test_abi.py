@@ -120,3 +120,11 @@ def test_init_rejects_small_or_misaligned_arena(abi):
     odd = abi.PicBuffers(256 + 8, s.arena_bytes)
     assert abi.lib().pic_init(ctypes.byref(c), ctypes.byref(odd), None, ctypes.byref(h)) == -3
     assert not h.value
+
+
+def test_wait_selftest_rejects_bad_arguments_before_any_launch(abi):
+    st, waited = ctypes.c_uint32(), ctypes.c_double()
+    assert abi.lib().pic_selftest_wait(-1, ctypes.byref(st), ctypes.byref(waited), None) == -1
+    assert abi.lib().pic_selftest_wait(11 * 10 ** 9, ctypes.byref(st), ctypes.byref(waited), None) == -1
+    assert abi.lib().pic_selftest_wait(1000, None, ctypes.byref(waited), None) == -1
+    assert b"pic_selftest_wait" in abi.lib().pic_last_error(None)

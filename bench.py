@@ -123,6 +123,27 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_config(cfg: dict, rank: int) -> dict:
+    """Rank r's replica: an independent discharge of the same workload (its
+    own load seed and Philox run index); replicas exchange no data."""
+    return dict(cfg, seed=cfg.get("seed", 1) + 1000 * rank, run=rank)
+
+
+def job_totals(total_ms: float, particle_steps: float, world: int, device=None):
+    """Whole-job aggregate over `world` ranks of the initialised process
+    group: the slowest rank's timed total and the sum of all ranks'
+    particle-steps (value = the latter over the former)."""
+    if world <= 1:
+        return total_ms, particle_steps
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([particle_steps], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def run_gpu(args, wl_name, cfg, rank, world):
     import torch
     from paper_1310_5284_gb300.sim import Sim
@@ -130,7 +151,7 @@ def run_gpu(args, wl_name, cfg, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    cfg = dict(cfg, seed=cfg.get("seed", 1) + 1000 * rank, run=rank)
+    cfg = replica_config(cfg, rank)
     sim = Sim(cfg, device=dev)
     stream = sim.stream
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -163,17 +184,7 @@ def run_gpu(args, wl_name, cfg, rank, world):
     d1 = sim.diag()
     n_avg = 0.5 * (sum(d0["count"]) + sum(d1["count"]))
     total_ms = sum(times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms_max = float(t.item())
-        c = torch.tensor([n_avg * K], dtype=torch.float64, device=dev)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        particle_steps = float(c.item())
-    else:
-        total_ms_max = total_ms
-        particle_steps = n_avg * K
+    total_ms_max, particle_steps = job_totals(total_ms, n_avg * K, world, device=dev)
     value = particle_steps / (total_ms_max * 1e-3)
 
     # dominant kernel: the fused particle launch (non-sort steps hold exactly it,

@@ -41,6 +41,8 @@ WORKLOADS = {
     "ccp_512cells_2048000ppsp": workloads.CFG_WIDE_EXPLICIT,
     "ccp_128cells_implicit": workloads.CFG_IMPLICIT,
     "ccp_64cells_12800ppsp": workloads.CFG_SMALL_CCP,
+    # the production explicit workload with the m = 3 scheme
+    "ccp_512cells_2048000ppsp_m3": dict(workloads.CFG_WIDE_EXPLICIT, scheme="ec3_explicit"),
 }
 
 

@@ -300,11 +300,13 @@ __device__ __forceinline__ int deposit_key_s3(int cell, float off, uint32_t &a) 
 // Per-block accumulators, four 32-bit counters per key: count, sum of a, and
 // the sums of the high and low 16 bits of a^2.  Exact while a block adds at
 // most 2^16 particles between two flushes (each term is below 2^16).  The
-// m = 3 modes use cnt, a (sum of F < 2^12), s2 (sum of F^2, 64-bit, in the
-// storage of bh and bl) and s3 (sum of F^3, 64-bit, an array of its own).
+// m = 3 modes keep every sum in 32-bit counters too (native shared atomics):
+// cnt, a (sum of F < 2^12), bh and bl (the sum of F^2 in 12-bit pieces of
+// warp sums: sum = bh 2^12 + bl) and s3h, s3m, s3l (the sum of F^3 in the
+// three 12-bit pieces of each F^3 < 2^36); each stays below 2^28 per flush.
 struct Acc {
     unsigned int *cnt, *a, *bh, *bl;
-    unsigned long long *s2, *s3;
+    unsigned int *s3h, *s3m, *s3l;
 };
 
 constexpr long long kFlushEvery = 65536;
@@ -361,26 +363,29 @@ __device__ __forceinline__ void warp_agg(int key, uint32_t c, uint32_t a, uint32
     }
 }
 
-// m = 3: the warp aggregation of (count, F, F^2, F^3) with F^3 split into its
-// high and low 16 bits.  Per warp slot (at most 32 x kUnroll = 128 particles,
-// F < 2^12): sum F^2 < 2^31, sum (F^3 >> 16) < 2^27, sum (F^3 & 0xffff) <
-// 2^23, so each reduction is exact in 32 bits.
+// m = 3: the warp aggregation of (count, F, F^2, F^3) with F^3 in its three
+// 12-bit pieces.  Per warp slot (at most 32 x kUnroll = 128 particles,
+// F < 2^12): sum F^2 < 2^31 and each piece sum < 2^19, so every reduction is
+// exact in 32 bits; the sum of F^2 is split into 12-bit pieces when added.
 __device__ __forceinline__ void acc_add3(const Acc &acc, int key, uint32_t c, uint32_t a, uint32_t s2,
-                                         uint32_t s3h, uint32_t s3l) {
+                                         uint32_t s3h, uint32_t s3m, uint32_t s3l) {
     atomicAdd(&acc.cnt[key], c);
     atomicAdd(&acc.a[key], a);
-    atomicAdd(&acc.s2[key], (unsigned long long)s2);
-    atomicAdd(&acc.s3[key], ((unsigned long long)s3h << 16) + s3l);
+    atomicAdd(&acc.bh[key], s2 >> 12);
+    atomicAdd(&acc.bl[key], s2 & 0xfffu);
+    atomicAdd(&acc.s3h[key], s3h);
+    atomicAdd(&acc.s3m[key], s3m);
+    atomicAdd(&acc.s3l[key], s3l);
 }
 
-__device__ __forceinline__ void warp_agg3(int key, uint32_t c, uint32_t a, uint32_t s2, uint32_t s3h, uint32_t s3l,
-                                          const Acc &acc) {
+__device__ __forceinline__ void warp_agg3(int key, uint32_t c, uint32_t a, uint32_t s2, uint32_t s3h, uint32_t s3m,
+                                          uint32_t s3l, const Acc &acc) {
     const int lane = threadIdx.x & 31;
     unsigned int pending = __ballot_sync(FULL_MASK, key >= 0);
     int iter = 0;
     while (pending) {
         if (iter == 4) {  // widely spread warp: the rest add lane by lane
-            if ((pending >> lane) & 1u) acc_add3(acc, key, c, a, s2, s3h, s3l);
+            if ((pending >> lane) & 1u) acc_add3(acc, key, c, a, s2, s3h, s3m, s3l);
             break;
         }
         const int leader = __ffs(pending) - 1;
@@ -391,8 +396,9 @@ __device__ __forceinline__ void warp_agg3(int key, uint32_t c, uint32_t a, uint3
         const uint32_t sa = __reduce_add_sync(FULL_MASK, mine ? a : 0u);
         const uint32_t s2s = __reduce_add_sync(FULL_MASK, mine ? s2 : 0u);
         const uint32_t sh = __reduce_add_sync(FULL_MASK, mine ? s3h : 0u);
+        const uint32_t sm_ = __reduce_add_sync(FULL_MASK, mine ? s3m : 0u);
         const uint32_t sl = __reduce_add_sync(FULL_MASK, mine ? s3l : 0u);
-        if (lane == leader) acc_add3(acc, lk, sc, sa, s2s, sh, sl);
+        if (lane == leader) acc_add3(acc, lk, sc, sa, s2s, sh, sm_, sl);
         pending &= ~grp;
         ++iter;
     }
@@ -404,32 +410,34 @@ __device__ __forceinline__ void deposit_tile3(const int (&key)[kUnroll], const u
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u)
         if (key[u] >= 0 && key[u] < kmin) kmin = key[u];
-    uint32_t c0 = 0, a0 = 0, q0 = 0, h0 = 0, l0 = 0, c1 = 0, a1 = 0, q1 = 0, h1 = 0, l1 = 0;
+    uint32_t c0 = 0, a0 = 0, q0 = 0, h0 = 0, m0 = 0, l0 = 0, c1 = 0, a1 = 0, q1 = 0, h1 = 0, m1 = 0, l1 = 0;
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
         const int k = key[u];
         if (k < 0) continue;
         const uint32_t f = a[u], f2 = f * f;
         const unsigned long long f3 = (unsigned long long)f2 * f;
-        const uint32_t hi = (uint32_t)(f3 >> 16), lo = (uint32_t)(f3 & 0xffffull);
+        const uint32_t hi = (uint32_t)(f3 >> 24), mid = (uint32_t)(f3 >> 12) & 0xfffu, lo = (uint32_t)f3 & 0xfffu;
         if (k == kmin) {
             c0 += 1u;
             a0 += f;
             q0 += f2;
             h0 += hi;
+            m0 += mid;
             l0 += lo;
         } else if (k == kmin + 1) {
             c1 += 1u;
             a1 += f;
             q1 += f2;
             h1 += hi;
+            m1 += mid;
             l1 += lo;
         } else {
-            acc_add3(acc, k, 1u, f, f2, hi, lo);
+            acc_add3(acc, k, 1u, f, f2, hi, mid, lo);
         }
     }
-    warp_agg3(kmin == 0x7fffffff ? -1 : kmin, c0, a0, q0, h0, l0, acc);
-    warp_agg3(c1 ? kmin + 1 : -1, c1, a1, q1, h1, l1, acc);
+    warp_agg3(kmin == 0x7fffffff ? -1 : kmin, c0, a0, q0, h0, m0, l0, acc);
+    warp_agg3(c1 ? kmin + 1 : -1, c1, a1, q1, h1, m1, l1, acc);
 }
 
 // The kUnroll particles of a thread usually share one or two adjacent keys
@@ -577,7 +585,7 @@ struct SmemMain {
 __host__ __device__ inline size_t align8(size_t x) { return (x + 7) & ~size_t(7); }
 
 __host__ __device__ inline size_t main_smem_bytes(int n, int bins, bool ec3) {
-    return align8(4 * (size_t)(n + 2)) + 4 * align8(4 * (size_t)(n + 1)) + (ec3 ? 8 * (size_t)(n + 1) : 0) +
+    return align8(4 * (size_t)(n + 2)) + (ec3 ? 7 : 4) * align8(4 * (size_t)(n + 1)) +
            align8(4 * (size_t)n) + align8(4 * (size_t)(bins + 1)) + 8 * (size_t)kQueue + 16;
 }
 
@@ -605,13 +613,13 @@ __device__ SmemMain carve_main(unsigned char *base, int n, int bins, bool ec3 = 
         *slots[k] = (unsigned int *)(base + o);
         o += align8(4 * (size_t)(n + 1));
     }
-    // bh and bl are adjacent, 8-byte aligned and 2 x align8(4 (n+1)) >= 8 (n+1)
-    // bytes together: the m = 3 sum of F^2 lives there
-    s.acc.s2 = (unsigned long long *)s.acc.bh;
-    s.acc.s3 = nullptr;
+    s.acc.s3h = s.acc.s3m = s.acc.s3l = nullptr;
     if (ec3) {
-        s.acc.s3 = (unsigned long long *)(base + o);
-        o += 8 * (size_t)(n + 1);
+        unsigned int **s3[3] = {&s.acc.s3h, &s.acc.s3m, &s.acc.s3l};
+        for (int k = 0; k < 3; ++k) {
+            *s3[k] = (unsigned int *)(base + o);
+            o += align8(4 * (size_t)(n + 1));
+        }
     }
     s.heat = (float *)(base + o);
     o += align8(4 * (size_t)n);
@@ -1163,12 +1171,16 @@ __device__ void flush_species(const Run &R, const SmemMain &sm, int S, bool coun
         if (c && ec3) {
             atomicAdd(&R.acc_cnt[S][k], (unsigned long long)c);
             atomicAdd(&R.acc_a[S][k], (unsigned long long)sm.acc.a[k]);
-            atomicAdd(&R.acc_b[S][k], sm.acc.s2[k]);
-            atomicAdd(&R.acc_c[S][k], sm.acc.s3[k]);
+            atomicAdd(&R.acc_b[S][k], ((unsigned long long)sm.acc.bh[k] << 12) + sm.acc.bl[k]);
+            atomicAdd(&R.acc_c[S][k], ((unsigned long long)sm.acc.s3h[k] << 24) +
+                                          ((unsigned long long)sm.acc.s3m[k] << 12) + sm.acc.s3l[k]);
             sm.acc.cnt[k] = 0u;
             sm.acc.a[k] = 0u;
-            sm.acc.s2[k] = 0ull;
-            sm.acc.s3[k] = 0ull;
+            sm.acc.bh[k] = 0u;
+            sm.acc.bl[k] = 0u;
+            sm.acc.s3h[k] = 0u;
+            sm.acc.s3m[k] = 0u;
+            sm.acc.s3l[k] = 0u;
         } else if (c) {
             atomicAdd(&R.acc_cnt[S][k], (unsigned long long)c);
             if (!count_only) {
@@ -2483,12 +2495,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
     for (int k = threadIdx.x; k <= n; k += kThreads) {
         sm.acc.cnt[k] = 0u;
         sm.acc.a[k] = 0u;
-        if (MI::ec3) {  // s2 spans bh, bl and the padding between them
-            sm.acc.s2[k] = 0ull;
-            sm.acc.s3[k] = 0ull;
-        } else {
-            sm.acc.bh[k] = 0u;
-            sm.acc.bl[k] = 0u;
+        sm.acc.bh[k] = 0u;
+        sm.acc.bl[k] = 0u;
+        if (MI::ec3) {
+            sm.acc.s3h[k] = 0u;
+            sm.acc.s3m[k] = 0u;
+            sm.acc.s3l[k] = 0u;
         }
     }
     if (diag) {

@@ -2460,8 +2460,11 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
 // ---------------------------------------------------------------------------
 // The particle kernel: one launch per explicit step / implicit pass / deposit.
 // ---------------------------------------------------------------------------
+// The m = 3 modes hold three blocks per SM (their shared memory), so they
+// may use the registers of three.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_particles(Run R) {
+__global__ void __launch_bounds__(kThreads, (MODE == kExplicitEC3 || MODE == kDepositEC3) ? 3 : kMinBlocks)
+    k_particles(Run R) {
     extern __shared__ __align__(128) unsigned char smem_all[];
     __shared__ bool s_last;
     __shared__ int s_warm;

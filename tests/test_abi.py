@@ -128,3 +128,9 @@ def test_wait_selftest_rejects_bad_arguments_before_any_launch(abi):
     assert abi.lib().pic_selftest_wait(11 * 10 ** 9, ctypes.byref(st), ctypes.byref(waited), None) == -1
     assert abi.lib().pic_selftest_wait(1000, None, ctypes.byref(waited), None) == -1
     assert b"pic_selftest_wait" in abi.lib().pic_last_error(None)
+
+
+def test_set_state_rejects_null_arguments_before_any_device_work(abi):
+    hp = abi.PicHostParticles()
+    assert abi.lib().pic_set_state(None, ctypes.byref(hp), ctypes.byref(hp)) == -1
+    assert abi.lib().pic_set_particles(None, 0, ctypes.byref(hp)) == -1

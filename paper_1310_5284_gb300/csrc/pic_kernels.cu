@@ -66,16 +66,46 @@ __device__ __forceinline__ uint4 draw(const Run &R, uint32_t id, long long step,
                             R.rk0, R.rk1);
 }
 
-// Uniform on (0, 1) from the top 24 bits.
+// Uniform on (0, 1) from the top 24 bits k of a word: u = (k + 1/2) 2^-24.
 __device__ __forceinline__ float u24(uint32_t w) {
     return fmaf((float)(w >> 8), 5.9604644775390625e-8f, 2.98023223876953125e-8f);
 }
 
+// The same uniform with its complement 1 - u = (2^24 - 1 - k + 1/2) 2^-24,
+// each formed from its own integer with one rounding.  u needs 25 bits once
+// k >= 2^23, so 1.0f - u24(w) would carry an absolute error of 2^-25: near
+// u = 1 that is a large relative error of 1 - u, which sqrt(u (1 - u)) and
+// log(u) magnify (a back-scattered direction, a small Box-Muller radius).
+struct U24 {
+    float u, c;  // u and 1 - u
+};
+
+__device__ __forceinline__ U24 u24c(uint32_t w) {
+    const uint32_t k = w >> 8;
+    return {fmaf((float)k, 5.9604644775390625e-8f, 2.98023223876953125e-8f),
+            fmaf((float)(0xFFFFFFu - k), 5.9604644775390625e-8f, 2.98023223876953125e-8f)};
+}
+
+// sin and cos of 2 pi u, from whichever of u, 1 - u is below one half.
+__device__ __forceinline__ void sincos_2pi(const U24 &x, float &s, float &c) {
+    if (x.u <= 0.5f) {
+        sincospif(2.0f * x.u, &s, &c);
+    } else {
+        sincospif(2.0f * x.c, &s, &c);
+        s = -s;
+    }
+}
+
+// -log(u), through log1p(-(1 - u)) above one half.
+__device__ __forceinline__ float neg_log_u(const U24 &x) {
+    return x.u <= 0.5f ? -logf(x.u) : -log1pf(-x.c);
+}
+
 // Box-Muller: two uniforms -> two standard normals.
-__device__ __forceinline__ void box_muller(float u1, float u2, float &n1, float &n2) {
-    const float r = sqrtf(-2.0f * logf(u1));
+__device__ __forceinline__ void box_muller(const U24 &u1, const U24 &u2, float &n1, float &n2) {
+    const float r = sqrtf(2.0f * neg_log_u(u1));
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
+    sincos_2pi(u2, s, c);
     n1 = r * c;
     n2 = r * s;
 }
@@ -130,12 +160,12 @@ __device__ __forceinline__ bool collide_electron_body(const Run &R, uint4 w, uin
     const float nu_el = R.sig_el * ngv;
     const float nu_ex = sigma_exc(R, eps) * ngv;
     const float nu_iz = sigma_iz(R, eps) * ngv;
-    // isotropic: cos chi = 1 - 2u, sin chi = 2 sqrt(u (1 - u)) (no cancellation)
-    const float uc = u24(w.z);
-    const float cos_chi = 1.0f - 2.0f * uc;
-    const float sin_chi = 2.0f * sqrtf(uc * (1.0f - uc));
+    // isotropic: cos chi = 1 - 2u = (1 - u) - u, sin chi = 2 sqrt(u (1 - u))
+    const U24 uc = u24c(w.z);
+    const float cos_chi = uc.c - uc.u;
+    const float sin_chi = 2.0f * sqrtf(uc.u * uc.c);
     float sp, cp;
-    sincospif(2.0f * u24(w.w), &sp, &cp);
+    sincos_2pi(u24c(w.w), sp, cp);
     float dx_ = 1.0f, dy = 0.0f, dz = 0.0f;
     if (g > 0.0f) {
         const float inv = 1.0f / g;
@@ -146,7 +176,7 @@ __device__ __forceinline__ bool collide_electron_body(const Run &R, uint4 w, uin
     float g_new;
     if (r < nu_el) {
         // elastic: the electron keeps 1 - (2m/M)(1 - cos chi) of its energy
-        g_new = g * sqrtf(1.0f - R.two_m_over_M * (2.0f * uc));
+        g_new = g * sqrtf(1.0f - R.two_m_over_M * (2.0f * uc.u));
         t.el++;
     } else if (r < nu_el + nu_ex) {
         g_new = sqrtf(R.two_e_over_me * (eps - R.exc_thr));
@@ -157,14 +187,14 @@ __device__ __forceinline__ bool collide_electron_body(const Run &R, uint4 w, uin
         g_new = sqrtf(R.two_e_over_me * 0.5f * (eps - R.iz_thr));
         const uint4 w1 = draw(R, id, step, 0, kTagMcc, 1);
         const uint4 w2 = draw(R, id, step, 0, kTagMcc, 2);
-        const float u1 = u24(w1.x);
-        const float ct = 1.0f - 2.0f * u1;
-        const float st = 2.0f * sqrtf(u1 * (1.0f - u1));
+        const U24 u1 = u24c(w1.x);
+        const float ct = u1.c - u1.u;
+        const float st = 2.0f * sqrtf(u1.u * u1.c);
         float sps, cps;
-        sincospif(2.0f * u24(w1.y), &sps, &cps);
+        sincos_2pi(u24c(w1.y), sps, cps);
         float n1, n2, n3, n4;
-        box_muller(u24(w1.z), u24(w1.w), n1, n2);
-        box_muller(u24(w2.x), u24(w2.y), n3, n4);
+        box_muller(u24c(w1.z), u24c(w1.w), n1, n2);
+        box_muller(u24c(w2.x), u24c(w2.y), n3, n4);
         const unsigned int slot = atomicAdd(&R.st->n_births, 1u);
         if (slot < (unsigned int)R.births_cap) {
             Birth b;
@@ -198,8 +228,8 @@ __device__ __forceinline__ bool collide_ion_body(const Run &R, uint4 w, uint32_t
                                                 float &vx, float &vy, float &vz, Tally &t) {
     const uint4 w1 = draw(R, id, step, 1, kTagMcc, 1);
     float n1, n2, n3, n4;
-    box_muller(u24(w.z), u24(w.w), n1, n2);
-    box_muller(u24(w1.x), u24(w1.y), n3, n4);
+    box_muller(u24c(w.z), u24c(w.w), n1, n2);
+    box_muller(u24c(w1.x), u24c(w1.y), n3, n4);
     const float vnx = R.vth_gas * n1, vny = R.vth_gas * n2, vnz = R.vth_gas * n3;
     const float ux = vx - vnx, uy = vy - vny, uz = vz - vnz;
     const float g = sqrtf(ux * ux + uy * uy + uz * uz);
@@ -2671,8 +2701,8 @@ __global__ void k_load(Run R, int S, long long count, float vth) {
         sp.cell[i] = (int32_t)(t >> 32);
         sp.off[i] = (float)((uint32_t)t >> 8) * 5.9604644775390625e-8f;
         float n1, n2, n3, n4;
-        box_muller(u24(w.y), u24(w.z), n1, n2);
-        box_muller(u24(w.w), u24(w2.x), n3, n4);
+        box_muller(u24c(w.y), u24c(w.z), n1, n2);
+        box_muller(u24c(w.w), u24c(w2.x), n3, n4);
         sp.vx[i] = vth * n1;
         sp.vy[i] = vth * n2;
         sp.vz[i] = vth * n3;
@@ -3254,9 +3284,12 @@ __global__ void __launch_bounds__(kThreads) k_deposit(const int32_t *__restrict_
                 key[u] = -1;
                 a[u] = 0u;
                 if (i < se) {
+                    // an entry off the grid (cell outside 0..n_cells-1, or an
+                    // offset outside [0, 1), NaN included) assigns nothing
                     const int c = cell[i];
-                    if (c >= 0 && c < n_cells)
-                        key[u] = s1 ? deposit_key_s1(c, off[i], a[u]) : deposit_key_s2(c, off[i], a[u]);
+                    const float f = off[i];
+                    if (c >= 0 && c < n_cells && f >= 0.0f && f < 1.0f)
+                        key[u] = s1 ? deposit_key_s1(c, f, a[u]) : deposit_key_s2(c, f, a[u]);
                 }
             }
             deposit_tile(key, a, acc, false);
@@ -3367,18 +3400,26 @@ extern "C" int pic_deposit_noalloc(int32_t scheme, int32_t boundary, int32_t n_c
         scratch = g_slots[dev].ptr;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // the array keeps the previous call's sums: clear it on this stream first
-    if (cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (3 * kScratchKeys + 32), s) != cudaSuccess)
+    auto cuda_fail = [](const char *what, cudaError_t e) {
+        std::string m = std::string("pic_deposit_noalloc: ") + what + ": " + cudaGetErrorString(e);
+        set_last_error(m.c_str());
         return -5;
+    };
+    // the array keeps the previous call's sums: clear it on this stream first
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (3 * kScratchKeys + 32), s);
+    if (e != cudaSuccess) return cuda_fail("clearing the static scratch", e);
     int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -5;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail("cudaDeviceGetAttribute", e);
     long long grid = (n + 8191) / 8192;
     if (grid < 1) grid = 1;
     if (grid > 4ll * sms) grid = 4ll * sms;
     const int smem = 16 * kScratchKeys;
     k_deposit<<<(int)grid, kThreads, smem, s>>>(cell, off, (long long)n, n_cells, boundary == 1,
                                                scheme == 1 || scheme == 3, scratch, (long long *)rho_q_out);
-    return cudaGetLastError() == cudaSuccess ? 0 : -5;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("kernel launch", e);
+    return 0;
 }
 
 // ===========================================================================

@@ -308,7 +308,8 @@ void pic_batch_free(pic_batch *b);
    arrays).  The paper has no counterpart: this is a library convenience
    beside the run API.
    cell, off: device arrays of n particles in the storage form (cell index,
-   offset in [0,1)); entries with a cell outside [0, n_cells) are skipped.
+   offset in [0,1)); entries with a cell outside [0, n_cells) or an offset
+   outside [0, 1) (NaN included) assign nothing.
    rho_q_out: device array of n_cells+1 int64 receiving the node charge in
    units of 2^-33 macro-particle charges, quadratic S_2 weights (EC schemes)
    or linear S_1 (PIC_MC_EXPLICIT, PIC_MC_IMPLICIT), electrodes or periodic as `boundary` -
@@ -317,12 +318,15 @@ void pic_batch_free(pic_batch *b);
    n_cells <= 1024 (about 25 KB on every GPU that loads the library, held
    until the process exits); no other memory is used and nothing is
    allocated.  The first call on a device looks up that array's device
-   address; make it before any stream capture on that device.  All calls on
-   one device share the array: calls that overlap on the GPU race (calls on
-   one stream are ordered).  Asynchronous on `stream`.  Returns PIC_OK;
-   PIC_EINVAL for n_cells outside 2..1024, n outside 0..2^29-1, an unknown
-   scheme or boundary (PIC_EC3_EXPLICIT included), or a NULL array;
-   PIC_ECUDA if a launch fails. */
+   address; make it before any stream capture on that device.  The address
+   is kept for the life of the process, so cudaDeviceReset() between calls
+   is not supported (the reset unloads the module that holds the array).
+   All calls on one device share the array: calls that overlap on the GPU
+   race (calls on one stream are ordered); each call clears it first.
+   Asynchronous on `stream`.  Returns PIC_OK; PIC_EINVAL for n_cells outside
+   2..1024, n outside 0..2^29-1, an unknown scheme or boundary
+   (PIC_EC3_EXPLICIT included), or a NULL array; PIC_ECUDA if a CUDA call
+   fails (message in pic_last_error(NULL)). */
 int pic_deposit_noalloc(int32_t scheme, int32_t boundary, int32_t n_cells, const int32_t *cell,
                         const float *off, int64_t n, int64_t *rho_q_out, void *stream);
 

@@ -109,44 +109,201 @@ def compare_particles(gpu, orc, cfg, tol=1e-5, species=("e", "i"), quantile=1.0,
             assert dxi.max() <= max_tol * cfg["n_cells"] and dv.max() <= max_tol, ("max", sp, dxi.max(), dv.max())
 
 
-def fp32_sensitivity(cfg, states, steps, abar=None, factor=4.0):
+def fp32_sensitivity(cfg, states, steps, abar=None, factor=4.0, step0=0, next_ids=None, ulps=2):
     """How far the FP64 oracle drifts from itself when its particle state is
-    rounded to the device storage form (cell + FP32 offset, FP32 velocities)
-    after every step: the chaotic amplification of FP32 rounding alone.
-    Returns per species (factor * max |dx|, factor * max |dv|/scale)."""
+    put through the FP32 arithmetic of a device step after every step: the
+    state is rounded to the storage form (cell + FP32 offset, FP32
+    velocities) and each stored value moved by a seeded random whole number
+    of FP32 ulps in [-ulps, ulps], the size of the few roundings the push
+    makes per value (acceleration, velocity, displacement, renormalisation;
+    in the implicit push, predictor and corrector).  This is the chaotic
+    amplification of FP32 arithmetic alone, over the same Philox streams as
+    the test (same first step and next ids), compared over the ids both runs
+    hold.  Returns per species the floor (factor times the 99th percentile
+    and the maximum of |dx| in cells and of |dv| / max(|v|, v_th)), plus the
+    relative change that this makes to the kinetic energy of each species."""
     ref = oracle.Sim(cfg)
     rnd = oracle.Sim(cfg)
+    nid = list(next_ids) if next_ids is not None else [None, None]
     for s in (ref, rnd):
         for k, sp in enumerate(("e", "i")):
             st = states[k]
             if st is None:
                 continue
+            if nid[k] is None:
+                nid[k] = int(st["id"].max()) + 1 if len(st["id"]) else 0
+            ab = None if abar is None or abar[k] is None else abar[k].astype(np.float64)
             s.set_species(sp, workloads.xi_of(st), st["vx"].astype(np.float64), st["vy"].astype(np.float64),
-                          st["vz"].astype(np.float64), st["id"])
-        s.init_field(set_abar=True)
+                          st["vz"].astype(np.float64), st["id"], abar=ab, next_id=nid[k])
+        s.set_step(step0)
+        s.init_field(set_abar=abar is None)
+    births0 = rnd.diag()["births"]
     ref.step(steps)
-    f32 = lambda x: np.asarray(x, dtype=np.float32).astype(np.float64)
+    rng = np.random.default_rng(12345)
+
+    def f32(x):
+        y = np.asarray(x, dtype=np.float32)
+        if ulps:
+            y = y + np.spacing(y) * rng.integers(-ulps, ulps + 1, y.shape).astype(np.float32)
+        return y.astype(np.float64)
+
     for _ in range(steps):
         rnd.step(1)
-        for sp in ("e", "i"):
+        born = rnd.diag()["births"] - births0
+        for k, sp in enumerate(("e", "i")):
             d = rnd.get_species(sp)
             if len(d["id"]) == 0:
                 continue
             c = np.floor(d["xi"])
-            xi = c + f32(d["xi"] - c)
-            rnd.set_species(sp, xi, f32(d["vx"]), f32(d["vy"]), f32(d["vz"]), d["id"], abar=f32(d["abar"]),
-                            next_id=int(d["id"].max()) + 1)
+            o = np.clip(f32(d["xi"] - c), 0.0, np.nextafter(np.float32(1.0), np.float32(0.0)))
+            rnd.set_species(sp, c + o, f32(d["vx"]), f32(d["vy"]), f32(d["vz"]), d["id"], abar=f32(d["abar"]),
+                            next_id=int(nid[k] + born))
         rnd.init_field(set_abar=False)
     out = []
+    da, db = rnd.diag(), ref.diag()
     for k, sp in enumerate(("e", "i")):
         a, b = by_id(rnd.get_species(sp)), by_id(ref.get_species(sp))
-        if len(a["id"]) == 0 or not np.array_equal(a["id"], b["id"]):
-            out.append(None)  # rounding alone changed which particles were absorbed
+        common, ia, ib = np.intersect1d(a["id"], b["id"], assume_unique=True, return_indices=True)
+        if len(common) == 0:
+            out.append(None)
             continue
+        a = {key: v[ia] for key, v in a.items()}
+        b = {key: v[ib] for key, v in b.items()}
         dxi, dv = _divergence(a, b, cfg, k)
+        ke = abs(da["ke_x"][k] - db["ke_x"][k]) / max(abs(db["ke_x"][k]), 1e-300)
+        ab = np.abs(a["abar"] - b["abar"]).max() / max(np.abs(b["abar"]).max(), 1e-300)
         out.append(dict(x99=factor * np.quantile(dxi, 0.99), v99=factor * np.quantile(dv, 0.99),
-                        xmax=factor * dxi.max(), vmax=factor * dv.max()))
+                        xmax=factor * dxi.max(), vmax=factor * dv.max(), ke=ke, abar=factor * ab,
+                        same_set=len(common) == len(rnd.get_species(sp)["id"]) == len(ref.get_species(sp)["id"])))
     return out
+
+
+def ke_bar(tol, floor):
+    """Relative bar on the kinetic energy of a species implied by the
+    per-particle one: with |dv| <= t max(|v|, v_th) for every particle,
+    |d(v^2)| <= 2 t (v^2 + v_th |v|), and the sum over particles stays within
+    2 t (1 + <v_th |v|> / <v^2>) <= 4 t of the total (|v| is of order v_th
+    on average)."""
+    t = tol if floor is None else max(tol, floor["vmax"])
+    return 4.0 * t
+
+
+def _oracle_of(cfg, st, step, implicit, extra=4096):
+    """An oracle run holding the given device-form state at the given step,
+    with the field of that state."""
+    orc = oracle.Sim(cfg, cap_e=len(st[0]["id"]) + extra, cap_i=len(st[1]["id"]) + extra)
+    for k, sp in enumerate(("e", "i")):
+        x = st[k]
+        orc.set_species(sp, workloads.xi_of(x), x["vx"].astype(np.float64), x["vy"].astype(np.float64),
+                        x["vz"].astype(np.float64), x["id"],
+                        abar=x["abar"].astype(np.float64) if implicit else None, next_id=x["next_id"])
+    orc.set_step(step)
+    orc.init_field(set_abar=False)
+    return orc
+
+
+def one_step_diagnostics(gpu, cfg, eedf_tol=None):
+    """Every diagnostic of the GPU's next step against one oracle step taken
+    from the GPU's own state (FP32 storage read exactly into FP64), so the
+    plasma's chaos plays no part and the bars follow from FP32 arithmetic:
+    * counts, wall counts, collision and birth tallies exact (integer
+      decisions on the same Philox words);
+    * kinetic energy, wall energy and the energy of the field the push used
+      within 1e-5 relative (FP32 velocities carry 6e-8 of rounding, and FP32
+      sums of a few hundred terms per thread a few 1e-7 more);
+    * power and the J.E heating profile within 1e-5 of their magnitude scale
+      |q w| max|E| sum|v_x| (sums of terms of both signs);
+    * explicit schemes: the node charges after the step bit-exact against
+      the oracle's assignment of the GPU's own new state, and the new field,
+      potential, field energy and averaged profiles within 1e-9 of scale
+      (the new positions themselves are compared per particle elsewhere: an
+      FP32 and an FP64 push may put a particle on either side of a 2^-16
+      quantisation boundary);
+    * direct implicit: the predicted positions are FP32 on the GPU and FP64
+      in the oracle, so about 1 % of them (those within two FP32 ulps of a
+      2^-16 boundary) may take the neighbouring quantisation code: each moves
+      a node charge by at most 2^19 units (2^-14 of a particle) and the
+      susceptibility of a cell by at most one 2^-16 quantum; the bars are the
+      summed node-charge change below 1e-5 of the total (about 60x the
+      expected 1.2e-6), chi within 1e-5 relative, and the field change within
+      the charge change times e w / eps0 (Gauss's law) plus 1e-9 of scale;
+    * the EEDF within a few particles that FP32 and FP64 bin differently."""
+    d0 = gpu.diag()
+    scheme = cfg.get("scheme", "ec_explicit")
+    implicit = scheme in ("ec_implicit", "mc_implicit")
+    st = [gpu.get_particles(sp) for sp in ("e", "i")]
+    orc = _oracle_of(cfg, st, d0["step"], implicit)
+    g_pre = gpu.grids()
+    if not implicit:  # the field the push uses is that of the state
+        assert np.array_equal(g_pre["rho_q_e"], orc.grids()["rho_q_e"])
+        assert np.array_equal(g_pre["rho_q_i"], orc.grids()["rho_q_i"])
+    gpu.diag(reset_avg=True)
+    orc.reset_averages()
+    w0 = (np.array(d0["wall_count"]), np.array(d0["wall_energy_ev"]), np.array(d0["coll"]), d0["births"])
+    do0 = orc.diag()
+    gpu.step(1)
+    orc.step(1)
+    dg, do = gpu.diag(), orc.diag()
+    assert dg["count"] == do["count"]
+    assert (np.array(dg["wall_count"]) - w0[0]).tolist() == (np.array(do["wall_count"]) - np.array(do0["wall_count"])).tolist()
+    assert (np.array(dg["coll"]) - w0[2]).tolist() == (np.array(do["coll"]) - np.array(do0["coll"])).tolist()
+    assert dg["births"] - w0[3] == do["births"] - do0["births"]
+    we_g = np.array(dg["wall_energy_ev"]) - w0[1]
+    we_o = np.array(do["wall_energy_ev"]) - np.array(do0["wall_energy_ev"])
+    np.testing.assert_allclose(we_g, we_o, rtol=1e-5, atol=1e-9)
+    for k in range(2):
+        assert dg["ke_x"][k] == pytest.approx(do["ke_x"][k], rel=1e-5, abs=1e-30)
+        assert dg["ke_perp"][k] == pytest.approx(do["ke_perp"][k], rel=1e-5, abs=1e-30)
+    der = oracle.derive(cfg)
+    emax = float(np.abs(g_pre["e_cc"]).max())
+    for k, sp in enumerate(("e", "i")):
+        scale = abs(der["q"][k]) * der["weight"] * emax * float(np.abs(st[k]["vx"].astype(np.float64)).sum())
+        assert abs(dg["power"][k] - do["power"][k]) <= 1e-5 * scale + 1e-30, (sp, dg["power"][k], do["power"][k])
+    g1, pg = gpu.grids(), gpu.profiles()
+    if not implicit:
+        assert dg["field_energy_push"] == pytest.approx(do["field_energy_push"], rel=1e-9, abs=1e-30)
+        post = [gpu.get_particles(sp) for sp in ("e", "i")]
+        o2 = _oracle_of(cfg, post, dg["step"], False)
+        o1 = o2.grids()
+        assert np.array_equal(g1["rho_q_e"], o1["rho_q_e"]) and np.array_equal(g1["rho_q_i"], o1["rho_q_i"])
+        e_tol = 1e-9 * max(np.abs(o1["e_cc"]).max(), 1e-300)
+        np.testing.assert_allclose(g1["e_cc"], o1["e_cc"], rtol=0, atol=e_tol)
+        np.testing.assert_allclose(g1["phi"], o1["phi"], rtol=0, atol=1e-9 * max(np.abs(o1["phi"]).max(), 1e-300))
+        assert dg["field_energy"] == pytest.approx(o2.diag()["field_energy"], rel=1e-8, abs=1e-30)
+        # one step's averages: the potential and densities of the new field
+        np.testing.assert_allclose(pg["phi"], o1["phi"], rtol=0, atol=1e-9 * max(np.abs(o1["phi"]).max(), 1e-300))
+        pn = o2.averages()  # nothing averaged yet: compare against the charge itself
+        unit = der["weight"] / der["dx"] / oracle.charge_unit(cfg)
+        for key, q in (("ne", o1["rho_q_e"]), ("ni", o1["rho_q_i"])):
+            ref = q.astype(np.float64) * unit
+            np.testing.assert_allclose(pg[key], ref, rtol=1e-12, atol=1e-12 * max(np.abs(ref).max(), 1e-300))
+    else:
+        o1 = orc.grids()
+        unit = oracle.charge_unit(cfg)
+        n_tot = [len(x["id"]) for x in st]
+        for k, key in enumerate(("rho_q_e", "rho_q_i")):
+            moved = np.abs(g1[key] - o1[key]).sum()
+            assert moved <= 1e-5 * max(n_tot[k], 1) * unit, (key, moved / (max(n_tot[k], 1) * unit))
+        moved_q = np.abs((g1["rho_q_i"] - g1["rho_q_e"]) - (o1["rho_q_i"] - o1["rho_q_e"])).sum()
+        de = 2.0 * 1.602176634e-19 * der["weight"] / 8.8541878128e-12 * moved_q / unit
+        e_tol = de + 1e-9 * max(np.abs(o1["e_cc"]).max(), 1e-300)
+        np.testing.assert_allclose(g1["e_cc"], o1["e_cc"], rtol=0, atol=e_tol)
+        np.testing.assert_allclose(g1["phi"], o1["phi"], rtol=0,
+                                   atol=cfg["length"] * e_tol + 1e-9 * max(np.abs(o1["phi"]).max(), 1e-300))
+        np.testing.assert_allclose(g1["chi"], o1["chi"], rtol=1e-5, atol=0)
+        assert np.abs(o1["chi"]).max() > 0
+        w_tol = 8.8541878128e-12 * der["dx"] * (np.abs(o1["e_cc"]).sum() * e_tol + 0.5 * len(o1["e_cc"]) * e_tol ** 2)
+        assert abs(dg["field_energy"] - do["field_energy"]) <= w_tol + 1e-9 * abs(do["field_energy"])
+    diag_step = cfg.get("diag_period", 0) > 0 and d0["step"] % cfg["diag_period"] == 0
+    if diag_step:
+        po = orc.averages()
+        for k, key in enumerate(("heat_e", "heat_i")):
+            scale = abs(der["q"][k]) * der["weight"] * emax * float(np.abs(st[k]["vx"].astype(np.float64)).sum())
+            assert np.abs(pg[key] - po[key]).sum() * der["dx"] <= 1e-5 * scale + 1e-30, key
+        if cfg.get("eedf_bins", 0) > 0:
+            diff = np.abs(pg["eedf"].astype(np.int64) - po["eedf"].astype(np.int64)).sum()
+            assert diff <= (eedf_tol if eedf_tol is not None else 4), diff
+    return dg, do
 
 
 # ------------------------------------------------------------------ Philox
@@ -283,17 +440,57 @@ def test_steps_match_oracle(name, over, strict, steps):
     dg, do = gpu.diag(), orc.diag()
     assert dg["step"] == do["step"] == steps
     floor = fp32_sensitivity(cfg, states, steps)
-    if all(f is not None for f in floor):
+    if all(f is not None and f["same_set"] for f in floor):
         assert dg["count"] == do["count"], name
         assert dg["wall_count"] == do["wall_count"], name
         compare_particles(gpu, orc, cfg, floor=floor)
-    else:
-        # FP32 rounding alone changes which particles reach an electrode
+        # the kinetic energy follows from the per-particle bar (ke_bar); the
+        # field energy of a noisy 64-cell plasma is checked where chaos plays
+        # no part, in the one-step comparison below
         for k in range(2):
-            assert dg["count"][k] == pytest.approx(do["count"][k], rel=0.01)
-    for k in range(2):
-        assert dg["ke_x"][k] == pytest.approx(do["ke_x"][k], rel=1e-2, abs=1e-12)
-    assert dg["field_energy"] == pytest.approx(do["field_energy"], rel=5e-2)
+            assert abs(dg["ke_x"][k] - do["ke_x"][k]) <= ke_bar(1e-5, floor[k]) * abs(do["ke_x"][k]) + 1e-30
+    else:
+        # FP32 rounding alone changes which particles reach an electrode: the
+        # counts may differ by the decisions rounding flips, a few at most
+        for k in range(2):
+            assert abs(dg["count"][k] - do["count"][k]) <= 8
+    one_step_diagnostics(gpu, cfg)
+
+
+IMPLICIT_GRID_CASES = [
+    ("ec_implicit_electrodes_64", dict(n_cells=64, scheme="ec_implicit", dt=8e-10)),
+    ("ec_implicit_periodic_50", dict(n_cells=50, periodic=True, rf_volt=0.0, scheme="ec_implicit", dt=8e-10)),
+    ("mc_implicit_electrodes_45", dict(n_cells=45, scheme="mc_implicit", dt=3e-10)),
+    ("mc_implicit_periodic_33", dict(n_cells=33, periodic=True, rf_volt=0.0, scheme="mc_implicit", dt=8e-10)),
+]
+
+
+@pytest.mark.parametrize("name,over", IMPLICIT_GRID_CASES, ids=[c[0] for c in IMPLICIT_GRID_CASES])
+def test_implicit_susceptibility_and_modified_poisson_grid(name, over):
+    """Direct-implicit steps from a seeded state with a given abar: the
+    susceptibility the predictor assigns, the node charges of the predicted
+    positions, and the potential and field of the modified Poisson equation
+    grid point by grid point against the oracle, with every other diagnostic
+    of the step (one_step_diagnostics; the bars follow from the FP32
+    predictor's quantisation decisions)."""
+    cfg = dict(workloads.CFG_SMALL_CCP, np_init=12_800, sort_period=4, diag_period=1, eedf_bins=30)
+    cfg.update(over)
+    n = cfg["np_init"]
+    gpu = gpu_sim(cfg)
+    orc = oracle.Sim(cfg)
+    states = states_for(cfg, n, 300 + cfg["n_cells"])
+    rng = np.random.default_rng(cfg["n_cells"])
+    qm = [-E / ME, E / (cfg.get("ion_mass_amu", 39.948) * AMU)]
+    abar = [np.float32(0.3 * qm[k] * 1e3) * rng.standard_normal(n).astype(np.float32) for k in range(2)]
+    inject(gpu, orc, cfg, states, step=7, abar=abar)
+    # the first step's predictor: its positions differ from the oracle's only
+    # by FP32 rounding of two products (see one_step_diagnostics for the bar)
+    gpu.step(1)
+    orc.step(1)
+    g, o = gpu.grids(), orc.grids()
+    assert np.abs(o["chi"]).max() > 0
+    np.testing.assert_allclose(g["chi"], o["chi"], rtol=1e-5, atol=0)
+    one_step_diagnostics(gpu, cfg, eedf_tol=4)
 
 
 @pytest.mark.parametrize("scheme", ["ec_explicit", "ec_implicit", "mc_implicit", "ec3_explicit"])
@@ -301,11 +498,13 @@ def test_collisions_counts_exact_and_births_ranked(scheme):
     """Null-collision MCC on the same Philox stream: selection is an integer
     compare, so tallies and births agree exactly; children get the same ids
     (and, in the implicit schemes, the parent's abar)."""
-    cfg = dict(workloads.CFG_SMALL_CCP, np_init=20_000, sort_period=4, te_ev=6.0, scheme=scheme)
+    cfg = dict(workloads.CFG_SMALL_CCP, np_init=20_000, sort_period=4, te_ev=6.0, scheme=scheme,
+               diag_period=1, eedf_bins=40)
     n = cfg["np_init"]
     gpu = gpu_sim(cfg)
     orc = oracle.Sim(cfg)
-    inject(gpu, orc, cfg, states_for(cfg, n, 77), step=1000)
+    states = states_for(cfg, n, 77)
+    inject(gpu, orc, cfg, states, step=1000)
     for _ in range(4):
         gpu.step(5)
         orc.step(5)
@@ -315,14 +514,19 @@ def test_collisions_counts_exact_and_births_ranked(scheme):
     assert dg["count"] == do["count"]
     assert dg["wall_count"] == do["wall_count"]
     assert dg["overflow"] == do["overflow"]
-    # the collision kinematics (sqrt, sincospi, log in FP32) add their own
-    # rounding to that of the push: 99.9% within 1e-5, all within 1e-4
-    compare_particles(gpu, orc, cfg, quantile=0.999, max_tol=1e-4)
+    # The collision kinematics amplify rounding near a threshold (the speed
+    # after excitation or ionisation is sqrt(eps - threshold)); the bar is the
+    # one of the collisionless runs: 1e-5, or 4x the oracle's own divergence
+    # when its state is rounded to FP32 after every step, over the same steps
+    # and Philox streams.
+    floor = fp32_sensitivity(cfg, states, 20, step0=1000)
+    compare_particles(gpu, orc, cfg, floor=floor)
     if scheme in ("ec_implicit", "mc_implicit"):  # abar of parents and children, relative to its scale
-        for sp in ("e", "i"):
+        for k, sp in enumerate(("e", "i")):
             a, b = by_id(gpu.get_particles(sp)), by_id(orc.get_species(sp))
             d = np.abs(a["abar"].astype(np.float64) - b["abar"]) / np.abs(b["abar"]).max()
-            assert np.quantile(d, 0.999) <= 1e-5 and d.max() <= 1e-4, (sp, d.max())
+            assert d.max() <= max(1e-5, floor[k]["abar"]), (sp, d.max(), floor[k]["abar"])
+    one_step_diagnostics(gpu, cfg, eedf_tol=8)
 
 
 @pytest.mark.parametrize("n", [40_000, 120_000])
@@ -335,7 +539,8 @@ def test_many_births_per_step_ranked_like_oracle(n):
                births_capacity=8192)
     gpu = gpu_sim(cfg)
     orc = oracle.Sim(cfg)
-    inject(gpu, orc, cfg, states_for(cfg, n, 91), step=500)
+    states = states_for(cfg, n, 91)
+    inject(gpu, orc, cfg, states, step=500)
     for _ in range(3):
         gpu.step(1)
         orc.step(1)
@@ -344,7 +549,7 @@ def test_many_births_per_step_ranked_like_oracle(n):
     assert dg["births"] == do["births"] > 3 * (300 if n < 100_000 else 1100)
     assert dg["coll"] == do["coll"]
     assert dg["count"] == do["count"]
-    compare_particles(gpu, orc, cfg, quantile=0.999, max_tol=1e-4)
+    compare_particles(gpu, orc, cfg, floor=fp32_sensitivity(cfg, states, 3, step0=500))
 
 
 @pytest.mark.parametrize("scheme", ["ec_explicit", "ec3_explicit"])
@@ -487,9 +692,9 @@ def test_high_selection_implicit_run_keeps_the_drain_in_step():
     steps through the single-run path (one sort among them) end with a clean
     status word, particle counts conserved by the tallies, and the same
     particles as a second run of the same configuration."""
-    from paper_1310_5284_gb300.batch import discharge_from_spec
 
-    cfg = discharge_from_spec(workloads.batch_configs(256)[47])
+    spec = dict(workloads.batch_configs(256)[47], omega_p_dt=2.0)  # the run's step when it faulted
+    cfg = workloads.discharge_from_spec(spec)
     assert cfg["scheme"] == "ec_implicit" and cfg["np_init"] > 1_500_000
     runs = []
     for _ in range(2):

@@ -185,16 +185,36 @@ def run_gpu(args, wl_name, cfg, rank, world):
     times = [a.elapsed_time(b) for a, b in evs]  # ms
     d1 = sim.diag()
     n_avg = 0.5 * (sum(d0["count"]) + sum(d1["count"]))
-    total_ms = sum(times)
-    total_ms_max, particle_steps = job_totals(total_ms, n_avg * K, world, device=dev)
-    value = particle_steps / (total_ms_max * 1e-3)
 
     # dominant kernel: the fused particle launch (non-sort steps hold exactly it,
     # or the implicit predictor + corrector pair)
     sort_idx = [k for k in range(K) if sort_period > 0 and (step0 + k + 1) % sort_period == 0]
     plain = [times[k] for k in range(K) if k not in set(sort_idx)]
-    t_push = sum(plain) / len(plain)
-    t_sort = (sum(times[k] for k in sort_idx) / len(sort_idx) - t_push) if sort_idx else 0.0
+    t_push = sum(plain) / len(plain) if plain else min(times)
+    sort_times = [times[k] for k in sort_idx]
+    if sort_period > 0 and not sort_times:
+        # the window held no sort step: time steps after it, flushed alike,
+        # up to and including the next one (outside the window's totals)
+        with torch.cuda.stream(stream):
+            extra = []
+            while True:
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.fill_(-1.0)
+                a_.record(stream)
+                sim.step(1)
+                b_.record(stream)
+                torch.cuda.synchronize(dev)
+                extra.append(a_.elapsed_time(b_))
+                if (step0 + K + len(extra)) % sort_period == 0:
+                    break
+            sort_times = extra[-1:]
+    t_sort = (sum(sort_times) / len(sort_times) - t_push) if sort_times else 0.0
+    # every step carries 1/sort_period of a sort: the K steps are charged their
+    # plain launches plus that share, whatever share of sorts the window held
+    ms_amortised = t_push + (t_sort / sort_period if sort_period > 0 else 0.0)
+    total_ms = ms_amortised * K
+    total_ms_max, particle_steps = job_totals(total_ms, n_avg * K, world, device=dev)
+    value = particle_steps / (total_ms_max * 1e-3)
     sel = sum(d1["coll"]) - sum(d0["coll"])  # selected particles over the K steps
     bpp = algorithmic_bytes_per_particle(cfg["scheme"])
     slots = n_avg
@@ -219,6 +239,7 @@ def run_gpu(args, wl_name, cfg, rank, world):
     e2e = run_e2e(sim, args.e2e_steps, dev) if args.e2e_steps > 0 else None
     sim.close()
     return dict(value=value, total_ms=total_ms_max, times=times, t_push=t_push, t_sort=t_sort,
+                window_ms=sum(times),
                 achieved=achieved, peak=peak, peak_kind=peak_kind, bytes_launch=bytes_launch,
                 traffic=traffic, clocks=clk, gpu_launches=gpu_launches, n_avg=n_avg, e2e=e2e,
                 wall_s=t_wall, counts=d1["count"], sort_steps=len(sort_idx))
@@ -306,34 +327,83 @@ def energy_drift(steps=2000):
     return out
 
 
-def bench_batched(n_runs=256, steps=12, warmup=3):
+def _oracle_run_sample(args):
+    """One run of the batched sweep in the FP64 oracle: load (untimed), then
+    `steps` timed steps.  Runs in a worker process of its own."""
+    cfg, steps = args
+    import oracle
+    n = int(cfg["np_init"])
+    sim = oracle.Sim(cfg).load(n, n)
+    parts = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        parts += sum(sim.diag()["count"])
+        sim.step(1)
+    return os.getpid(), parts, time.perf_counter() - t0
+
+
+def oracle_batched_baseline(cfgs, steps=1):
+    """The FP64 oracle over the runs of the batched sweep, one process per
+    host core (spawned, so no GPU context is inherited): each run loaded,
+    then `steps` steps timed.  Aggregate = all particle-steps / the busiest
+    worker's stepping time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    busy, parts = {}, 0
+    with ctx.Pool(cores) as pool:
+        for pid, p_, t in pool.imap_unordered(_oracle_run_sample, [(c, steps) for c in cfgs]):
+            busy[pid] = busy.get(pid, 0.0) + t
+            parts += p_
+    return {"value": parts / max(busy.values()), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "all %d runs of the batched sweep, %d step(s) each after the load, FP64, one process "
+                      "per core" % (len(cfgs), steps)}
+
+
+def bench_batched(n_runs=256, steps=2000, warmup=3, single_steps=12):
     """Batched persistent launches over the sweep of uneven discharges (cells
-    64..1024, 1e4..2e6 particles per species, explicit and implicit) against
-    the same runs advanced one by one through the single-run path on the same
-    GPU.  Both forms give bit-identical particles (tests/test_gpu_batch.py)."""
+    64..1024, 1e4..2e6 particles per species, explicit and implicit) timed
+    over `steps` steps (the particles, about 4 GB, are far larger than the
+    L2), with the roofline of the launches from each run's algorithmic bytes;
+    against the same runs advanced one by one through the single-run path
+    (`single_steps` steps each) on the same GPU.  Both forms give
+    bit-identical particles (tests/test_gpu_batch.py)."""
     import torch
-    from paper_1310_5284_gb300.batch import BatchSim, discharge_from_spec
+    from paper_1310_5284_gb300.batch import BatchSim
     from paper_1310_5284_gb300.sim import Sim
 
-    cfgs = [discharge_from_spec(s) for s in workloads.batch_configs(n_runs)]
+    cfgs = workloads.batch_discharges(n_runs)
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     batch = BatchSim(cfgs, device=dev)
     tune = batch.autotune(trial_steps=4)
     batch.step(warmup)
     torch.cuda.synchronize(dev)
-    c0 = sum(sum(batch.diag(r)["count"]) for r in range(n_runs))
+    d0 = [batch.diag(r) for r in range(n_runs)]
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
     a.record(batch.stream)
     batch.step(steps)
     b.record(batch.stream)
     torch.cuda.synchronize(dev)
+    clk = clocks.stop()
     t_batch = a.elapsed_time(b) * 1e-3
-    c1 = sum(sum(batch.diag(r)["count"]) for r in range(n_runs))
+    d1 = [batch.diag(r) for r in range(n_runs)]
+    status = batch.status()
     batch.close()
     del batch
     torch.cuda.empty_cache()
-    ps_batch = 0.5 * (c0 + c1) * steps
-    # the single-run form: each run alone, K steps, times summed
+    ps_batch, bytes_total = 0.0, 0.0
+    for cfg, x0, x1 in zip(cfgs, d0, d1):
+        n_avg = 0.5 * (sum(x0["count"]) + sum(x1["count"]))
+        bpp = algorithmic_bytes_per_particle(cfg["scheme"])
+        per = bpp["per_particle"] + bpp.get("predictor_per_particle", 0)
+        sel = sum(x1["coll"]) - sum(x0["coll"])
+        ps_batch += n_avg * steps
+        bytes_total += per * n_avg * steps + bpp["per_selected"] * sel
+    achieved = bytes_total / t_batch / 1e9
+    peak, kind = measured_peak()
+    # the single-run form: each run alone, single_steps steps, times summed
     t_single, ps_single = 0.0, 0.0
     for cfg in cfgs:
         sim = Sim(cfg, device=dev)
@@ -341,16 +411,23 @@ def bench_batched(n_runs=256, steps=12, warmup=3):
         torch.cuda.synchronize(dev)
         n0_ = sum(sim.diag()["count"])
         a.record(sim.stream)
-        sim.step(steps)
+        sim.step(single_steps)
         b.record(sim.stream)
         torch.cuda.synchronize(dev)
         t_single += a.elapsed_time(b) * 1e-3
-        ps_single += 0.5 * (n0_ + sum(sim.diag()["count"])) * steps
+        ps_single += 0.5 * (n0_ + sum(sim.diag()["count"])) * single_steps
         sim.close()
-    return {"n_runs": n_runs, "steps": steps, "particles": int(0.5 * (c0 + c1)),
-            "value": ps_batch / t_batch, "single_run_value": ps_single / t_single,
-            "speedup_vs_single_runs": (ps_batch / t_batch) / (ps_single / t_single), "unit": UNIT,
-            "autotuned": tune, "accuracy": "bit-identical to the single-run form"}
+    parts = sum(0.5 * (sum(x0["count"]) + sum(x1["count"])) for x0, x1 in zip(d0, d1))
+    out = {"n_runs": n_runs, "steps": steps, "window_s": t_batch, "particles": int(parts),
+           "value": ps_batch / t_batch, "unit": UNIT, "status": status, "clocks": clk,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "peak_source": kind,
+                        "bytes": "per run 28 B (explicit) or 52 B (direct implicit) per particle + 16 B per "
+                                 "selected particle"},
+           "single_run_value": ps_single / t_single, "single_run_steps": single_steps,
+           "speedup_vs_single_runs": (ps_batch / t_batch) / (ps_single / t_single),
+           "autotuned": tune, "accuracy": "bit-identical to the single-run form"}
+    return out
 
 
 def bench_adjoint(n_particles=1_000_000, n_cells=256, nsteps=200, checkpoint_every=20):
@@ -397,6 +474,10 @@ def bench_adjoint(n_particles=1_000_000, n_cells=256, nsteps=200, checkpoint_eve
             am = run.final_state()["cell"] >= 0
             res["dP_dV0_central_difference"] = (pp - pm) / (2 * h)
             res["absorption_events_changed_by_h"] = int(np.sum(ap != am))
+            res["central_difference_note"] = (
+                "not comparable with dP_dV0: the +-h runs absorb different particles, and the adjoint holds "
+                "absorption events fixed; the finite-difference check of the gradient is the event-free case "
+                "of tests/test_gpu_adjoint.py")
         run.close()
         # the plain single-run form of the same configuration
         cfg = dict(n_cells=n_cells, periodic=periodic, length=length, dt=dt, rf_freq=spec["rf_freq"],
@@ -478,36 +559,59 @@ def bench_self_heating(steps=2000):
     return out
 
 
-def bench_implicit(steps=16, warmup=3):
-    """Throughput of the direct-implicit workload (128 cells, 1.02 M per
-    species, omega_p dt = 5): two launches per step plus the sort.  The
-    window is the run's first steps: with the analytic cross sections this
-    discharge later runs into an ionisation avalanche (births grow a
-    thousandfold and fill the births buffer by step 70), so a longer window
-    would time a run that has left the workload's regime; `status` says
-    whether the window stayed clean."""
+def bench_implicit(steps=4000, warmup=20):
+    """The direct-implicit workload (128 cells, 1.02 M per species, omega_p dt
+    = 2, 300 V, 50 mTorr): a step is the predictor and corrector launches,
+    plus the sort every sort_period steps.  4000 steps timed one by one, the
+    L2 flushed between them; the sort is charged to every step at its
+    measured cost / sort_period.  Roofline of the launch pair: 52 B per
+    particle (predictor reads cell, offset, vx, abar; corrector reads those
+    and the id and writes cell, offset, vx, abar) + 16 B per selected
+    particle.  `status` says whether the window stayed clean (no dropped
+    births or particles)."""
     import torch
     from paper_1310_5284_gb300.sim import Sim
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    sim = Sim(dict(workloads.CFG_IMPLICIT), device=dev)
+    cfg = dict(workloads.CFG_IMPLICIT)
+    sim = Sim(cfg, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     sim.step(warmup)
     torch.cuda.synchronize(dev)
-    n0_ = sum(sim.diag()["count"])
+    d0 = sim.diag()
+    step0 = d0["step"]
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for k in range(steps):
-        flush.fill_(float(k))
-        evs[k][0].record(sim.stream)
-        sim.step(1)
-        evs[k][1].record(sim.stream)
+    with torch.cuda.stream(sim.stream):
+        for k in range(steps):
+            flush.fill_(float(k))
+            evs[k][0].record(sim.stream)
+            sim.step(1)
+            evs[k][1].record(sim.stream)
     torch.cuda.synchronize(dev)
-    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
-    n1_ = sum(sim.diag()["count"])
+    d1 = sim.diag()
     status = sim.status()
     sim.close()
-    return {"workload": "ccp_128cells_implicit", "ms_per_step": ms, "steps": steps, "warmup": warmup,
-            "value": 0.5 * (n0_ + n1_) / (ms * 1e-3), "unit": UNIT, "status": status}
+    times = [a.elapsed_time(b) for a, b in evs]
+    sp = cfg["sort_period"]
+    is_sort = [(step0 + k + 1) % sp == 0 for k in range(steps)]
+    plain = [t for t, srt in zip(times, is_sort) if not srt]
+    sorts = [t for t, srt in zip(times, is_sort) if srt]
+    t_pair = sum(plain) / len(plain)
+    t_sort = sum(sorts) / len(sorts) - t_pair if sorts else 0.0
+    ms = t_pair + t_sort / sp
+    n_avg = 0.5 * (sum(d0["count"]) + sum(d1["count"]))
+    sel = sum(d1["coll"]) - sum(d0["coll"])
+    bpp = algorithmic_bytes_per_particle("ec_implicit")
+    bytes_pair = (bpp["per_particle"] + bpp["predictor_per_particle"]) * n_avg + bpp["per_selected"] * sel / steps
+    achieved = bytes_pair / (t_pair * 1e-3) / 1e9
+    peak, kind = measured_peak()
+    return {"workload": "ccp_128cells_implicit (omega_p dt = 2)", "ms_per_step": ms, "launch_pair_ms": t_pair,
+            "sort_ms": t_sort, "steps": steps, "warmup": warmup, "value": n_avg / (ms * 1e-3), "unit": UNIT,
+            "status": status, "counts_start_end": [d0["count"], d1["count"]],
+            "births_per_step": (d1["births"] - d0["births"]) / steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": kind,
+                         "bytes": "52 B per particle + 16 B per selected, predictor + corrector"}}
 
 
 def bench_ec3(steps=96, warmup=10):
@@ -612,7 +716,10 @@ def main():
                      "algorithmic_bytes_per_launch": r["bytes_launch"], "launch_ms": r["t_push"],
                      "peak_source": r["peak_kind"]},
         "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
-        "kernels": {"particles_ms": r["t_push"], "sort_ms": r["t_sort"], "sort_steps": r["sort_steps"]},
+        "kernels": {"particles_ms": r["t_push"], "sort_ms": r["t_sort"], "sort_steps": r["sort_steps"],
+                    "sort_period": cfg.get("sort_period"),
+                    "ms_per_step_in_window": r["window_ms"] / args.steps,
+                    "ms_per_step": "particle launch + sort_ms / sort_period (a sort every sort_period steps)"},
         "particles_live": r["counts"],
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -623,6 +730,8 @@ def main():
         line["adjoint"] = bench_adjoint()
     if world == 1 and not args.no_batched:
         line["batched"] = bench_batched()
+        if not args.no_cpu_baseline:
+            line["batched"]["cpu_baseline"] = oracle_batched_baseline(workloads.batch_discharges(256))
     if world == 1 and not args.no_extras:
         line["implicit"] = bench_implicit()
         line["ec3"] = bench_ec3()

@@ -1,46 +1,16 @@
 """Python binding of a batch of independent runs (pic_batch_* in include/pic.h).
 
 Argument marshalling only; the runs advance in the library's persistent
-batched kernels.  `discharge_from_spec` turns a sweep description (grid
-spacing in Debye lengths, omega_p dt) into a run configuration.
+batched kernels.
 """
 from __future__ import annotations
 
 import ctypes
-import math
 
 import numpy as np
 
 from . import _abi
 from .sim import SPECIES, _fptr, make_config
-
-_E = 1.602176634e-19
-_ME = 9.1093837015e-31
-_EPS0 = 8.8541878128e-12
-
-
-def discharge_from_spec(spec: dict, te_ev: float = 2.0) -> dict:
-    """A discharge configuration from a sweep point: the load density puts
-    dx at `dx_over_lambda_d` Debye lengths of `te_ev` electrons; explicit runs
-    take dt = min(0.2 / omega_p, 0.25 dx / v_th), implicit runs dt =
-    omega_p_dt / omega_p."""
-    c = dict(spec)
-    dx = c["length"] / c["n_cells"]
-    lam = dx / c.pop("dx_over_lambda_d")
-    n0 = _EPS0 * te_ev / (_E * lam * lam)
-    wp = math.sqrt(n0 * _E * _E / (_EPS0 * _ME))
-    vth = math.sqrt(_E * te_ev / _ME)
-    wpdt = c.pop("omega_p_dt", None)
-    if c.get("scheme", "ec_explicit") in ("ec_implicit", "mc_implicit"):
-        dt = (wpdt if wpdt is not None else 2.0) / wp
-    else:
-        dt = min(0.2 / wp, 0.25 * dx / vth)
-    c.update(n0=n0, dt=dt, te_ev=te_ev)
-    c.setdefault("cap_factor", 1.25)
-    c.setdefault("sort_period", 8)
-    c.setdefault("cx_vmax", 2.0 * c.get("rf_volt", 0.0) + 50.0)
-    return c
-
 
 class BatchSim:
     """Many runs advanced together (pic_batch_init / pic_batch_step)."""

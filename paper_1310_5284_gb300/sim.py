@@ -35,7 +35,8 @@ def make_config(cfg: dict) -> _abi.PicConfig:
     cap = int(cfg.get("capacity", max(1024, int(np_init * cap_factor))))
     c.capacity[0] = cap
     c.capacity[1] = int(cfg.get("capacity_i", cap)) if c.ions_mobile else 1
-    c.births_capacity = int(cfg.get("births_capacity", max(4096, np_init // 64)))
+    # one step may record the births of up to an eighth of the slots
+    c.births_capacity = int(cfg.get("births_capacity", min(1 << 24, max(4096, cap // 8))))
     c.length = float(cfg["length"])
     c.dt = float(cfg["dt"])
     c.rf_freq = float(cfg.get("rf_freq", 0.0))

@@ -81,6 +81,7 @@ class Derived(ctypes.Structure):
         ("p_null_e", ctypes.c_double), ("p_null_i", ctypes.c_double),
         ("thr_e", ctypes.c_uint32), ("thr_i", ctypes.c_uint32),
         ("g_max_i", ctypes.c_double),
+        ("wait_thr", ((ctypes.c_uint32 * 64) * 3) * 2),
     ]
 
 
@@ -117,6 +118,8 @@ def lib():
         L.orc_philox4x32_10.argtypes = [_u32, _u32, _u32]
         L.orc_philox_stream.argtypes = [ctypes.c_uint32] * 6 + [ctypes.c_int64, _u32]
         L.orc_derive.argtypes = [_P(Params), _P(Derived)]
+        L.orc_wait_draws.argtypes = [_P(Params), ctypes.c_int, ctypes.c_int64, _u32, ctypes.c_int64,
+                                     ctypes.c_uint32, _u32]
         L.orc_deposit_s2_fixed.argtypes = [_P(Params), ctypes.c_int64, _d, _i64]
         L.orc_deposit_s2_fp64.argtypes = [_P(Params), ctypes.c_int64, _d, _d]
         L.orc_deposit_s1_fixed.argtypes = [_P(Params), ctypes.c_int64, _d, _i64]
@@ -210,7 +213,20 @@ def derive(cfg_or_params) -> dict:
         "vth": tuple(d.vth), "vth_gas": d.vth_gas, "nu_max_e": d.nu_max_e,
         "nu_max_i": d.nu_max_i, "p_null_e": d.p_null_e, "p_null_i": d.p_null_i,
         "thr_e": d.thr_e, "thr_i": d.thr_i, "g_max_i": d.g_max_i,
+        "wait_thr": np.array([[list(d.wait_thr[k][g]) for g in range(3)] for k in range(2)], dtype=np.uint64),
     }
+
+
+def wait_draws(cfg, species, ids, step, sub=1) -> np.ndarray:
+    """Steps to the next null-collision selection drawn for each id at `step`
+    (sub 0: after a selection, 1: on entering the run); bit 30 marks a count
+    that ends in a fresh draw instead of a selection."""
+    p = params(cfg)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    out = np.zeros(len(ids), dtype=np.uint32)
+    lib().orc_wait_draws(ctypes.byref(p), int(SPECIES.get(species, species)), len(ids),
+                         _ptr(ids, ctypes.c_uint32), int(step), int(sub), _ptr(out, ctypes.c_uint32))
+    return out
 
 
 def philox(key, ctr) -> np.ndarray:

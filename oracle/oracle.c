@@ -29,6 +29,9 @@
 /* Philox stream tags (fourth counter word = species << 24 | tag << 16 | sub). */
 #define TAG_LOAD 1u
 #define TAG_MCC  2u
+#define TAG_WAIT 3u
+#define WAIT_CAP 262144u          /* 64^3 steps: the longest count a draw gives */
+#define WAIT_REDRAW 0x40000000u   /* the count ends in a fresh draw, not a selection */
 
 #define TWO_POW_16 65536
 #define TWO_POW_33 ((int64_t)1 << 33)
@@ -111,6 +114,40 @@ static double sigma_iz(const orc_params *p, double eps)
     return p->sig_iz_peak * EULER_N * (p->iz_thr / eps) * log(eps / p->iz_thr);
 }
 
+/* Null-collision selection by waiting times (reading of the null-collision
+   method, whose selection the paper does not spell out): the number of steps
+   W from a particle's selection, or from its entry into the run, to its next
+   selection is geometric, P(W > k) = (1 - P_null)^k -- the law of one
+   Bernoulli(P_null) trial per step, drawn once per selection.  W - 1 = X is
+   made of three independent base-64 digits, X = 4096 a + 64 b + c: c and b
+   follow the geometric laws of ratio q = 1 - P_null and q^64 cut to 0..63,
+   a the geometric law of ratio q^4096, where a = 64 stands for X >= 64^3
+   (the count of WAIT_CAP steps then ends in a fresh draw, not a selection;
+   the law is memoryless).  Each digit is the number of thresholds
+   T_j = floor(2^32 P(digit >= j)), j = 1..63 (1..64 for a), above a 32-bit
+   Philox word; the thresholds come from FP64 pow on the host. */
+static void wait_tables(double p_null, uint32_t t[3][64])
+{
+    double q = 1.0 - p_null;
+    for (int dgt = 0; dgt < 3; ++dgt) {
+        double r = dgt == 0 ? q : (dgt == 1 ? pow(q, 64.0) : pow(q, 4096.0));
+        double r64 = pow(r, 64.0);
+        for (int j = 1; j <= 64; ++j) {
+            double frac;
+            if (dgt == 2) {
+                frac = pow(r, (double)j);                       /* P(a >= j) */
+            } else if (j == 64) {
+                t[dgt][63] = 0u;                                /* unused */
+                continue;
+            } else {
+                frac = 1.0 - r64 > 0.0 ? (pow(r, (double)j) - r64) / (1.0 - r64) : 1.0;
+            }
+            double v = floor(ldexp(frac, 32));
+            t[dgt][j - 1] = v >= 4294967295.0 ? 0xffffffffu : (uint32_t)v;
+        }
+    }
+}
+
 void orc_derive(const orc_params *p, orc_derived *d)
 {
     memset(d, 0, sizeof(*d));
@@ -140,6 +177,38 @@ void orc_derive(const orc_params *p, orc_derived *d)
     d->p_null_i = 1.0 - exp(-d->nu_max_i * p->dt);
     d->thr_e = (uint32_t)floor(d->p_null_e * 16777216.0);
     d->thr_i = (uint32_t)floor(d->p_null_i * 16777216.0);
+    wait_tables(d->p_null_e, d->wait_thr[0]);
+    wait_tables(d->p_null_i, d->wait_thr[1]);
+}
+
+/* One digit of the waiting time: the number of thresholds above u. */
+static uint32_t wait_digit(const uint32_t *t, int n, uint32_t u)
+{
+    uint32_t d = 0;
+    for (int j = 0; j < n; ++j)
+        if (u < t[j]) d += 1;
+    return d;
+}
+
+uint32_t orc_wait_draw(const orc_params *p, const orc_derived *d, int species, uint32_t id,
+                       int64_t step, uint32_t sub)
+{
+    if ((species == 0 ? d->p_null_e : d->p_null_i) <= 0.0) return WAIT_CAP | WAIT_REDRAW;
+    uint32_t w[4];
+    draw(p, id, step, (uint32_t)species, TAG_WAIT, sub, w);
+    uint32_t a = wait_digit(d->wait_thr[species][2], 64, w[0]);
+    if (a == 64u) return WAIT_CAP | WAIT_REDRAW;
+    uint32_t b = wait_digit(d->wait_thr[species][1], 63, w[1]);
+    uint32_t c = wait_digit(d->wait_thr[species][0], 63, w[2]);
+    return 1u + 4096u * a + 64u * b + c;
+}
+
+void orc_wait_draws(const orc_params *p, int species, int64_t n, const uint32_t *id, int64_t step,
+                    uint32_t sub, uint32_t *out)
+{
+    orc_derived d;
+    orc_derive(p, &d);
+    for (int64_t k = 0; k < n; ++k) out[k] = orc_wait_draw(p, &d, species, id[k], step, sub);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -438,6 +507,7 @@ typedef struct {
     int64_t n, cap;
     double *xi, *vx, *vy, *vz, *abar;
     uint32_t *id;
+    uint32_t *wait;   /* steps to the next null-collision selection (| WAIT_REDRAW) */
     uint8_t *dead;
     uint32_t next_id;
 } species_t;
@@ -477,14 +547,15 @@ static int species_alloc(species_t *s, int64_t cap)
     s->vz = (double *)calloc(c, sizeof(double));
     s->abar = (double *)calloc(c, sizeof(double));
     s->id = (uint32_t *)calloc(c, sizeof(uint32_t));
+    s->wait = (uint32_t *)calloc(c, sizeof(uint32_t));
     s->dead = (uint8_t *)calloc(c, 1);
-    return s->xi && s->vx && s->vy && s->vz && s->abar && s->id && s->dead ? 0 : -1;
+    return s->xi && s->vx && s->vy && s->vz && s->abar && s->id && s->wait && s->dead ? 0 : -1;
 }
 
 static void species_free(species_t *s)
 {
     free(s->xi); free(s->vx); free(s->vy); free(s->vz); free(s->abar); free(s->id);
-    free(s->dead);
+    free(s->wait); free(s->dead);
 }
 
 orc_sim *orc_sim_create(const orc_params *p, int64_t cap_e, int64_t cap_i)
@@ -682,6 +753,7 @@ int orc_sim_load(orc_sim *s, int64_t n_e, int64_t n_i)
             sp->vz[i] = s->d.vth[k] * n3;
             sp->abar[i] = 0.0;
             sp->id[i] = (uint32_t)i;
+            sp->wait[i] = p->mcc ? orc_wait_draw(p, &s->d, k, (uint32_t)i, 0, 1) : 0u;
             sp->dead[i] = 0;
         }
         sp->next_id = (uint32_t)sp->n;
@@ -705,6 +777,7 @@ int orc_sim_set(orc_sim *s, int species, int64_t n, const double *xi, const doub
         sp->vz[i] = vz[i];
         sp->id[i] = id[i];
         sp->abar[i] = abar ? abar[i] : 0.0;
+        sp->wait[i] = s->p.mcc ? orc_wait_draw(&s->p, &s->d, species, id[i], s->step, 1) : 0u;
         sp->dead[i] = 0;
     }
     sp->next_id = next_id;
@@ -745,17 +818,35 @@ void orc_sim_set_step(orc_sim *s, int64_t step) { s->step = step; }
 
 /* ------------------------------------------------------------------------- */
 /* Monte Carlo collisions (Sec. 3: electron-atom and ion-atom collisions).    */
-/* Null-collision selection: one Bernoulli draw per particle per step with    */
-/* the bound probability; a selected particle then picks a process by          */
-/* comparing u * nu_max with the running sum of n_g sigma_k(eps) v.            */
+/* Null-collision selection with the bound probability P_null per step, by   */
+/* waiting times (wait_tables): each step counts a particle's wait down; a    */
+/* count that runs out selects it (or only draws a new wait, for a count      */
+/* that stood for a wait beyond the longest one draw gives).  A selected      */
+/* particle picks a process by comparing u * nu_max with the running sum of   */
+/* n_g sigma_k(eps) v.                                                         */
 /* ------------------------------------------------------------------------- */
+/* Count down particle i of species k: 1 if it is selected in this step, else
+   0; an expired count draws the next wait. */
+static int selected(orc_sim *s, int k, int64_t i)
+{
+    species_t *sp = &s->sp[k];
+    if ((k == 0 ? s->d.p_null_e : s->d.p_null_i) <= 0.0) return 0;
+    uint32_t wv = sp->wait[i];
+    if ((wv & ~WAIT_REDRAW) > 1u) {
+        sp->wait[i] = wv - 1u;
+        return 0;
+    }
+    sp->wait[i] = orc_wait_draw(&s->p, &s->d, k, sp->id[i], s->step, 0);
+    return (wv & WAIT_REDRAW) ? 0 : 1;
+}
+
 static int collide_electron(orc_sim *s, int64_t i)
 {
     const orc_params *p = &s->p;
     species_t *sp = &s->sp[0];
+    if (!selected(s, 0, i)) return 0;
     uint32_t w[4];
     draw(p, sp->id[i], s->step, 0, TAG_MCC, 0, w);
-    if ((w[0] >> 8) >= s->d.thr_e) return 0;
     double v[3] = {sp->vx[i], sp->vy[i], sp->vz[i]};
     double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     double g = sqrt(v2);
@@ -828,9 +919,9 @@ static void collide_ion(orc_sim *s, int64_t i)
 {
     const orc_params *p = &s->p;
     species_t *sp = &s->sp[1];
+    if (!selected(s, 1, i)) return;
     uint32_t w[4];
     draw(p, sp->id[i], s->step, 1, TAG_MCC, 0, w);
-    if ((w[0] >> 8) >= s->d.thr_i) return;
     uint32_t w1[4];
     draw(p, sp->id[i], s->step, 1, TAG_MCC, 1, w1);
     double n1, n2, n3, n4;
@@ -873,6 +964,7 @@ static int finish_population(orc_sim *s)
             sp->vz[w] = sp->vz[i];
             sp->abar[w] = sp->abar[i];
             sp->id[w] = sp->id[i];
+            sp->wait[w] = sp->wait[i];
             sp->dead[w] = 0;
             ++w;
         }
@@ -892,6 +984,8 @@ static int finish_population(orc_sim *s)
             sp->vz[i] = v[2];
             sp->abar[i] = k == 0 ? bb->abar_e : bb->abar_i;
             sp->id[i] = sp->next_id + (uint32_t)b;
+            /* a child's first wait is drawn on its birth step */
+            sp->wait[i] = orc_wait_draw(&s->p, &s->d, k, sp->id[i], s->step, 1);
             sp->dead[i] = 0;
         }
     }

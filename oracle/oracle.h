@@ -66,10 +66,18 @@ void orc_philox_stream(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint3
 typedef struct orc_derived {
     double dx, weight, q[2], m[2], vth[2], vth_gas;
     double nu_max_e, nu_max_i, p_null_e, p_null_i;
-    uint32_t thr_e, thr_i;   /* selection thresholds on 24-bit uniforms */
+    uint32_t thr_e, thr_i;   /* P_null on the 24-bit scale (nonzero: the species collides) */
     double g_max_i;
+    uint32_t wait_thr[2][3][64]; /* [species][digit c, b, a][j - 1]: waiting-time thresholds */
 } orc_derived;
 void orc_derive(const orc_params *p, orc_derived *d);
+/* Steps to the next null-collision selection of particle `id` of a species,
+   drawn at `step` (sub 0: after a selection, 1: on entering the run), with
+   bit 30 set when the count ends in a fresh draw rather than a selection. */
+uint32_t orc_wait_draw(const orc_params *p, const orc_derived *d, int species, uint32_t id,
+                       int64_t step, uint32_t sub);
+void orc_wait_draws(const orc_params *p, int species, int64_t n, const uint32_t *id, int64_t step,
+                    uint32_t sub, uint32_t *out);
 
 /* ---- stand-alone pieces used by the pin tests ---- */
 /* S_2 charge assignment of n particles to nodes, in units of 2^-33 particle

@@ -126,8 +126,8 @@ def test_null_collision_waiting_time_is_geometric():
     sim.init_field()
     d = oracle.derive(c)
     p_theory = 1.0 - math.exp(-gas_density(30.0) * sig * speed(eps_cap) * dt)
-    p = d["thr_e"] / 2 ** 24
-    assert abs(p - p_theory) <= 2 ** -24 + 1e-9 * p_theory
+    p = d["p_null_e"]
+    assert abs(p - p_theory) <= 1e-12 * p_theory
     first = np.zeros(n, dtype=np.int64)
     prev = sim.get_species("e")
     order = np.argsort(prev["id"])
@@ -146,6 +146,95 @@ def test_null_collision_waiting_time_is_geometric():
     exp_ = n * (1 - p) ** (np.arange(steps + 1) - 1) * p
     exp_[0] = n * (1 - p) ** steps
     assert stats.chisquare(obs, exp_).pvalue > 1e-4
+
+
+WAIT_CAP = 64 ** 3
+REDRAW = 1 << 30
+
+
+def _wait_cfg(mtorr, dt):
+    return box(pressure_mtorr=mtorr, dt=dt, np_init=1)
+
+
+# P_null from 0.36 down to 5e-7 (where most draws reach the cap)
+WAIT_CASES = [(30.0, 6e-10), (30.0, 1e-10), (30.0, 2e-12), (10.0, 1e-13), (0.3, 3e-13), (1.0, 2e-14)]
+
+
+@pytest.mark.parametrize("mtorr,dt", WAIT_CASES)
+def test_waiting_time_tables_compose_to_the_geometric_law(mtorr, dt):
+    """Selection by waiting times: W - 1 = X = 4096 a + 64 b + c from three
+    independent digits, each the number of thresholds above a 32-bit word.
+    From the tables alone, P(X >= x) = P(a > a') + P(a = a') (P(b > b') +
+    P(b = b') P(c >= c')) must equal q^x, q = 1 - P_null, for every x below the
+    cap (here a spread of x from one step to past 64^3), and P(a = 64) must be
+    q^(64^3): a wrong ratio, an off-by-one threshold or a wrong digit weight
+    breaks this identity.  Exact up to the 2^-32 rounding of each threshold."""
+    c = _wait_cfg(mtorr, dt)
+    d = oracle.derive(c)
+    P = d["p_null_e"]
+    assert 1e-7 < P < 0.4
+    q = 1.0 - P
+    t = d["wait_thr"][0].astype(np.float64) / 2 ** 32  # [digit c, b, a][j - 1]
+
+    def ge(digit, j, n):  # P(digit >= j), j in 0..n
+        return 1.0 if j == 0 else (0.0 if j > n else t[digit][j - 1])
+
+    xs = sorted({0, 1, 2, 3, 31, 63, 64, 65, 127, 4095, 4096, 4097, 12345, 99999, 262143}
+                | set(range(0, 400, 7)))
+    for x in xs:
+        a, b, cc = x // 4096, (x // 64) % 64, x % 64
+        pa_gt = ge(2, a + 1, 64)
+        pa_eq = ge(2, a, 64) - ge(2, a + 1, 64)
+        pb_gt = ge(1, b + 1, 63)
+        pb_eq = ge(1, b, 63) - ge(1, b + 1, 63)
+        pc_ge = ge(0, cc, 63)
+        got = pa_gt + pa_eq * (pb_gt + pb_eq * pc_ge)
+        assert abs(got - q ** x) <= 6 * 2 ** -32, (x, got, q ** x)
+    assert abs(ge(2, 64, 64) - q ** WAIT_CAP) <= 2 * 2 ** -32
+
+
+@pytest.mark.parametrize("mtorr,dt", [(30.0, 1e-10), (10.0, 1e-13), (0.3, 3e-13)])
+def test_waiting_time_draws_follow_the_geometric_law(mtorr, dt):
+    """Drawn waits (entry draws of 300,000 ids) against the geometric law
+    P(W = k) = q^(k-1) P_null: chi-square over bins of equal probability, and
+    the share of capped draws (a count of 64^3 steps marked for a fresh draw)
+    equal to q^(64^3)."""
+    c = _wait_cfg(mtorr, dt)
+    P = oracle.derive(c)["p_null_e"]
+    q = 1.0 - P
+    n = 300_000
+    w = oracle.wait_draws(c, "e", np.arange(n, dtype=np.uint32), step=17, sub=1).astype(np.int64)
+    capped = (w & REDRAW) != 0
+    assert np.all((w[capped] & ~REDRAW) == WAIT_CAP)
+    p_cap = q ** WAIT_CAP
+    assert abs(capped.mean() - p_cap) <= 5 * math.sqrt(p_cap * (1 - p_cap) / n) + 1e-12
+    W = w[~capped]
+    assert W.min() >= 1 and W.max() <= WAIT_CAP
+    # 20 bins of equal probability under the law cut at the cap
+    edges = [1]
+    for j in range(1, 20):  # P(W > k) = q^k: the k that leaves 1 - j/20 of the uncut part above it
+        k = math.log(1 - (1 - p_cap) * j / 20) / math.log(q)
+        edges.append(int(math.floor(k)) + 1)
+    edges.append(WAIT_CAP + 1)
+    edges = sorted(set(edges))
+    obs = np.histogram(W, bins=edges)[0]
+    cdf = lambda k: 1.0 - q ** (k - 1)  # P(W < k)
+    exp_ = np.array([cdf(edges[i + 1]) - cdf(edges[i]) for i in range(len(edges) - 1)]) * n
+    exp_ *= obs.sum() / exp_.sum()
+    assert stats.chisquare(obs, exp_).pvalue > 1e-4
+    assert abs(W.mean() - (1 / P)) < 6 * math.sqrt(q) / P / math.sqrt(len(W)) + (1 / P) * p_cap * 2
+
+
+def test_waiting_time_draws_are_keyed_on_id_step_and_kind():
+    """Draws depend on (id, step, entry or reselection) and nothing else:
+    repeated calls agree, and changing any key gives a different stream."""
+    c = _wait_cfg(30.0, 1e-10)
+    ids = np.arange(5000, dtype=np.uint32)
+    a = oracle.wait_draws(c, "e", ids, step=3, sub=1)
+    assert np.array_equal(a, oracle.wait_draws(c, "e", ids, step=3, sub=1))
+    for other in (oracle.wait_draws(c, "e", ids, step=4, sub=1), oracle.wait_draws(c, "e", ids, step=3, sub=0),
+                  oracle.wait_draws(c, "i", ids, step=3, sub=1), oracle.wait_draws(c, "e", ids + 1, step=3, sub=1)):
+        assert np.mean(a != other) > 0.9
 
 
 def test_process_frequencies_follow_cross_sections():

@@ -53,13 +53,15 @@ def kernel_source_sha() -> str:
 
 def algorithmic_bytes_per_particle(scheme: str) -> dict:
     """Bytes one launch must move per particle (structure of arrays, 4 B per
-    field): explicit reads cell, offset, vx, id and writes cell, offset, vx;
-    a particle selected for a collision also reads and writes vy, vz.  The
-    implicit corrector reads cell, offset, vx, abar, id and writes cell,
-    offset, vx, abar; its predictor reads cell, offset, vx, abar."""
+    field): explicit reads cell word, offset and vx and writes them back (the
+    cell word carries the wait to the particle's next null-collision
+    selection); a particle whose wait runs out also reads its id, vy and vz
+    and writes vx, vy, vz and its cell word (new wait).  The implicit
+    corrector reads cell word, offset, vx and abar and writes them; its
+    predictor reads cell word, offset, vx and abar."""
     if scheme in ("ec_implicit", "mc_implicit"):
-        return {"per_particle": 36, "per_selected": 16, "predictor_per_particle": 16}
-    return {"per_particle": 28, "per_selected": 16}
+        return {"per_particle": 32, "per_selected": 28, "predictor_per_particle": 16}
+    return {"per_particle": 24, "per_selected": 28}
 
 
 def measured_peak():
@@ -422,7 +424,7 @@ def bench_batched(n_runs=256, steps=2000, warmup=3, single_steps=12):
            "value": ps_batch / t_batch, "unit": UNIT, "status": status, "clocks": clk,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_source": kind,
-                        "bytes": "per run 28 B (explicit) or 52 B (direct implicit) per particle + 16 B per "
+                        "bytes": "per run 24 B (explicit) or 48 B (direct implicit) per particle + 28 B per "
                                  "selected particle"},
            "single_run_value": ps_single / t_single, "single_run_steps": single_steps,
            "speedup_vs_single_runs": (ps_batch / t_batch) / (ps_single / t_single),
@@ -564,10 +566,9 @@ def bench_implicit(steps=4000, warmup=20):
     = 2, 300 V, 50 mTorr): a step is the predictor and corrector launches,
     plus the sort every sort_period steps.  4000 steps timed one by one, the
     L2 flushed between them; the sort is charged to every step at its
-    measured cost / sort_period.  Roofline of the launch pair: 52 B per
-    particle (predictor reads cell, offset, vx, abar; corrector reads those
-    and the id and writes cell, offset, vx, abar) + 16 B per selected
-    particle.  `status` says whether the window stayed clean (no dropped
+    measured cost / sort_period.  Roofline of the launch pair: 48 B per
+    particle (predictor reads cell word, offset, vx, abar; corrector reads
+    those and writes them) + 28 B per particle whose wait runs out.  `status` says whether the window stayed clean (no dropped
     births or particles)."""
     import torch
     from paper_1310_5284_gb300.sim import Sim
@@ -611,7 +612,7 @@ def bench_implicit(steps=4000, warmup=20):
             "births_per_step": (d1["births"] - d0["births"]) / steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": kind,
-                         "bytes": "52 B per particle + 16 B per selected, predictor + corrector"}}
+                         "bytes": "48 B per particle + 28 B per selected, predictor + corrector"}}
 
 
 def bench_ec3(steps=96, warmup=10):

@@ -143,11 +143,11 @@ def lib():
         L.orc_sim_free.argtypes = [ctypes.c_void_p]
         L.orc_sim_load.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]
         L.orc_sim_set.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, _d, _d, _d,
-                                  _d, _u32, _d, ctypes.c_uint32]
+                                  _d, _u32, _d, ctypes.c_uint32, _u32]
         L.orc_sim_init_field.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_sim_count.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_sim_count.restype = ctypes.c_int64
-        L.orc_sim_get.argtypes = [ctypes.c_void_p, ctypes.c_int, _d, _d, _d, _d, _u32, _d]
+        L.orc_sim_get.argtypes = [ctypes.c_void_p, ctypes.c_int, _d, _d, _d, _d, _u32, _d, _u32]
         L.orc_sim_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
         L.orc_sim_set_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
         L.orc_sim_diag.argtypes = [ctypes.c_void_p, _P(Diag)]
@@ -380,7 +380,10 @@ class Sim:
             raise ValueError("oracle load exceeds capacity")
         return self
 
-    def set_species(self, species, xi, vx, vy, vz, ids, abar=None, next_id=None):
+    def set_species(self, species, xi, vx, vy, vz, ids, abar=None, next_id=None, wait=None):
+        """Inject a state; `wait` (as get_species returns it) keeps each
+        particle's steps to its next null-collision selection, None draws
+        them as for particles entering the run at the current step."""
         k = SPECIES.get(species, species)
         xi = np.ascontiguousarray(xi, dtype=np.float64)
         n = len(xi)
@@ -391,10 +394,11 @@ class Sim:
         ab = None if abar is None else np.ascontiguousarray(abar, dtype=np.float64)
         if next_id is None:
             next_id = int(ids.max()) + 1 if n else 0
+        wt = None if wait is None else np.ascontiguousarray(wait, dtype=np.uint32)
         r = lib().orc_sim_set(self._h, k, n, _ptr(xi, ctypes.c_double), _ptr(vx, ctypes.c_double),
                               _ptr(vy, ctypes.c_double), _ptr(vz, ctypes.c_double),
                               _ptr(ids, ctypes.c_uint32), _ptr(ab, ctypes.c_double),
-                              int(next_id))
+                              int(next_id), _ptr(wt, ctypes.c_uint32))
         if r:
             raise ValueError("oracle set exceeds capacity")
         return self
@@ -420,10 +424,11 @@ class Sim:
         n = self.count(k)
         out = {name: np.zeros(n) for name in ("xi", "vx", "vy", "vz", "abar")}
         out["id"] = np.zeros(n, dtype=np.uint32)
+        out["wait"] = np.zeros(n, dtype=np.uint32)
         lib().orc_sim_get(self._h, k, _ptr(out["xi"], ctypes.c_double),
                           _ptr(out["vx"], ctypes.c_double), _ptr(out["vy"], ctypes.c_double),
                           _ptr(out["vz"], ctypes.c_double), _ptr(out["id"], ctypes.c_uint32),
-                          _ptr(out["abar"], ctypes.c_double))
+                          _ptr(out["abar"], ctypes.c_double), _ptr(out["wait"], ctypes.c_uint32))
         return out
 
     def diag(self) -> dict:

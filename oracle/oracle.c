@@ -765,7 +765,7 @@ int orc_sim_load(orc_sim *s, int64_t n_e, int64_t n_i)
 
 int orc_sim_set(orc_sim *s, int species, int64_t n, const double *xi, const double *vx,
                 const double *vy, const double *vz, const uint32_t *id, const double *abar,
-                uint32_t next_id)
+                uint32_t next_id, const uint32_t *wait)
 {
     species_t *sp = &s->sp[species];
     if (n > sp->cap) return -1;
@@ -777,7 +777,10 @@ int orc_sim_set(orc_sim *s, int species, int64_t n, const double *xi, const doub
         sp->vz[i] = vz[i];
         sp->id[i] = id[i];
         sp->abar[i] = abar ? abar[i] : 0.0;
-        sp->wait[i] = s->p.mcc ? orc_wait_draw(&s->p, &s->d, species, id[i], s->step, 1) : 0u;
+        if (wait)
+            sp->wait[i] = wait[i];
+        else
+            sp->wait[i] = s->p.mcc ? orc_wait_draw(&s->p, &s->d, species, id[i], s->step, 1) : 0u;
         sp->dead[i] = 0;
     }
     sp->next_id = next_id;
@@ -801,7 +804,7 @@ void orc_sim_init_field(orc_sim *s, int set_abar)
 int64_t orc_sim_count(const orc_sim *s, int species) { return s->sp[species].n; }
 
 void orc_sim_get(const orc_sim *s, int species, double *xi, double *vx, double *vy, double *vz,
-                 uint32_t *id, double *abar)
+                 uint32_t *id, double *abar, uint32_t *wait)
 {
     const species_t *sp = &s->sp[species];
     for (int64_t i = 0; i < sp->n; ++i) {
@@ -811,6 +814,7 @@ void orc_sim_get(const orc_sim *s, int species, double *xi, double *vx, double *
         if (vz) vz[i] = sp->vz[i];
         if (id) id[i] = sp->id[i];
         if (abar) abar[i] = sp->abar[i];
+        if (wait) wait[i] = sp->wait[i];
     }
 }
 

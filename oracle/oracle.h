@@ -140,15 +140,17 @@ void     orc_sim_free(orc_sim *s);
 /* uniform load of n_e electrons and n_i ions (ids 0..n-1) followed by the t=0 field */
 int      orc_sim_load(orc_sim *s, int64_t n_e, int64_t n_i);
 /* inject a state: positions in cell units, velocities in m/s, ids; abar may be NULL.
-   next_id: first id given to a particle born later. */
+   next_id: first id given to a particle born later.  wait: the steps to each
+   particle's next null-collision selection (as orc_sim_get returns them), or
+   NULL to draw them as for particles entering the run at the current step. */
 int      orc_sim_set(orc_sim *s, int species, int64_t n, const double *xi, const double *vx,
                      const double *vy, const double *vz, const uint32_t *id, const double *abar,
-                     uint32_t next_id);
+                     uint32_t next_id, const uint32_t *wait);
 /* deposit + field solve for the current state (and abar = a^0 for the implicit scheme) */
 void     orc_sim_init_field(orc_sim *s, int set_abar);
 int64_t  orc_sim_count(const orc_sim *s, int species);
 void     orc_sim_get(const orc_sim *s, int species, double *xi, double *vx, double *vy,
-                     double *vz, uint32_t *id, double *abar);
+                     double *vz, uint32_t *id, double *abar, uint32_t *wait);
 int      orc_sim_step(orc_sim *s, int64_t nsteps);
 void     orc_sim_set_step(orc_sim *s, int64_t step);
 void     orc_sim_diag(const orc_sim *s, orc_diag *d);

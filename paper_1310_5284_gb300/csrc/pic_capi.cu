@@ -181,6 +181,36 @@ int cuda_fail(pic_handle *h, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
     } while (0)
 
+// Thresholds of the waiting time between null-collision selections.  The
+// steps W from a selection (or from entering the run) to the next one follow
+// the geometric law P(W > k) = q^k, q = 1 - P_null (the law of one
+// Bernoulli(P_null) trial per step).  W - 1 = 4096 a + 64 b + c with three
+// independent digits: c and b geometric with ratios q and q^64 cut to 0..63,
+// a geometric with ratio q^4096 where a = 64 stands for a wait beyond 64^3
+// steps (it ends in a fresh draw).  A digit is the number of thresholds
+// T_j = floor(2^32 P(digit >= j)) above a 32-bit Philox word: t[0] for c and
+// t[1] for b (j = 1..63), t[2] for a (j = 1..64).
+void wait_thresholds(double p_null, uint32_t t[3][64]) {
+    const double q = 1.0 - p_null;
+    for (int dg = 0; dg < 3; ++dg) {
+        const double r = dg == 0 ? q : (dg == 1 ? std::pow(q, 64.0) : std::pow(q, 4096.0));
+        const double r64 = std::pow(r, 64.0);
+        for (int j = 1; j <= 64; ++j) {
+            double f;
+            if (dg == 2) {
+                f = std::pow(r, (double)j);
+            } else if (j == 64) {
+                t[dg][63] = 0u;
+                continue;
+            } else {
+                f = 1.0 - r64 > 0.0 ? (std::pow(r, (double)j) - r64) / (1.0 - r64) : 1.0;
+            }
+            const double v = std::floor(std::ldexp(f, 32));
+            t[dg][j - 1] = v >= 4294967295.0 ? 0xffffffffu : (uint32_t)v;
+        }
+    }
+}
+
 void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R) {
     std::memset(&R, 0, sizeof R);
     R.n_cells = c.n_cells;
@@ -253,8 +283,10 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
         const double nu_i = ng * c.sig_cx * g_max;
         const double p_e = 1.0 - std::exp(-nu_e * c.dt);
         const double p_i = 1.0 - std::exp(-nu_i * c.dt);
-        R.thr[0] = (uint32_t)std::floor(p_e * 16777216.0);
-        R.thr[1] = (uint32_t)std::floor(p_i * 16777216.0);
+        R.thr[0] = p_e > 0.0 ? 1u : 0u;
+        R.thr[1] = p_i > 0.0 ? 1u : 0u;
+        wait_thresholds(p_e, R.wait_thr[0]);
+        wait_thresholds(p_i, R.wait_thr[1]);
         R.nu_max_e = (float)nu_e;
         R.nu_max_i = (float)nu_i;
         R.g_max_i = (float)g_max;
@@ -461,7 +493,7 @@ int run_get_particles(const Run &R, cudaStream_t s, int species, pic_host_partic
     long long k = 0;
     for (long long i = 0; i < ns; ++i) {
         if (cell[i] < 0) continue;
-        if (out->cell) out->cell[k] = cell[i];
+        if (out->cell) out->cell[k] = cell[i] & (int32_t)kCellMask;  // without the wait bits
         if (out->off) out->off[k] = off[i];
         if (out->vx) out->vx[k] = vx[i];
         if (out->vy) out->vy[k] = vy[i];
@@ -710,7 +742,7 @@ int enqueue_upload(pic_handle *h, unsigned int parity, int species, const pic_ho
 int enqueue_apply(pic_handle *h, unsigned int parity, int species, const pic_host_particles *in) {
     const Species &sp = h->run.buf[parity][species];
     const Species &up = h->run.buf[parity ^ 1u][species];
-    CK(h, launch_apply_particles(sp, up, in->count, sp.abar && in->abar, &h->run.st->check, h->run.st, species,
+    CK(h, launch_apply_particles(h->run, sp, up, in->count, sp.abar && in->abar, &h->run.st->check, species,
                                  in->next_id, h->stream));
     return PIC_OK;
 }

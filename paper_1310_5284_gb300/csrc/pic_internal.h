@@ -44,6 +44,17 @@ enum Mode : int {
     kDepositEC3 = 9,
 };
 
+// The cell word of a particle.  A hole left by an absorbed particle is -1.
+// A live particle holds its cell in bits 0..10 and, in runs with collisions,
+// the steps left to its next null-collision selection in bits 11..29 (at most
+// kWaitCap), with bit 30 set when that count ends in a fresh draw of the wait
+// instead of a selection.  Runs without collisions hold the plain cell.
+constexpr int kCellBits = 11;
+constexpr uint32_t kCellMask = (1u << kCellBits) - 1u;
+constexpr uint32_t kWaitCap = 262144u;          // 64^3 steps: the longest wait one draw gives
+constexpr uint32_t kRedrawBit = 0x40000000u;    // in a drawn wait and in the cell word alike
+constexpr uint32_t kWaitOne = 1u << kCellBits;  // one step of the count in the cell word
+
 // One species' particle arrays (structure of arrays).
 struct Species {
     int32_t *cell;
@@ -137,7 +148,10 @@ struct Run {
     float qw[2];           // q w: power per particle per (V/m * m/s)
     float half_m_over_e[2];// 0.5 m / e: energy [eV] per (m/s)^2
     // collisions (FP32)
-    uint32_t thr[2];       // selection thresholds on 24-bit uniforms
+    uint32_t thr[2];       // nonzero: the species collides (P_null > 0)
+    // waiting-time thresholds [species][digit c, b, a][j - 1] of the geometric
+    // law of the steps between selections (draw_wait)
+    uint32_t wait_thr[2][3][64];
     float nu_max_e, nu_max_i, n_g;
     float sig_el, exc_thr, exc_ramp_end, exc_slope, sig_exc_max, iz_thr, sig_iz_k, sig_cx;
     float eps_cap, g_max_i, two_m_over_M, two_e_over_me, vth_gas;
@@ -229,8 +243,9 @@ cudaError_t launch_set_abar(const Run &r, cudaStream_t s);
 cudaError_t launch_check_particles(const int32_t *cell, const float *off, long long n, int n_cells,
                                    unsigned int *flag, cudaStream_t s);
 cudaError_t launch_perp_energy(const Run &r, cudaStream_t s);
-cudaError_t launch_apply_particles(const Species &dst, const Species &src, long long n, bool abar_given,
-                                   const unsigned int *flag, DevState *st, int S, unsigned int next_id,
+// (with collisions, each particle draws its first wait at the run's step)
+cudaError_t launch_apply_particles(const Run &r, const Species &dst, const Species &src, long long n,
+                                   bool abar_given, const unsigned int *flag, int S, unsigned int next_id,
                                    cudaStream_t s);
 cudaError_t launch_finalize(const Run &r, cudaStream_t s);
 cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,

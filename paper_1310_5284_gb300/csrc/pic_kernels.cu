@@ -56,6 +56,7 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk0)
 
 constexpr uint32_t kTagLoad = 1u;
 constexpr uint32_t kTagMcc = 2u;
+constexpr uint32_t kTagWait = 3u;
 
 // Counter layout: (id, step low word, step high word, species<<24 | tag<<16 | sub).
 __device__ __forceinline__ uint4 draw(const Run &R, uint32_t id, long long step, int species,
@@ -64,6 +65,47 @@ __device__ __forceinline__ uint4 draw(const Run &R, uint32_t id, long long step,
     return philox4x32_10_rk(make_uint4(id, (uint32_t)s, (uint32_t)(s >> 32),
                                        ((uint32_t)species << 24) | (tag << 16) | sub),
                             R.rk0, R.rk1);
+}
+
+// ---------------------------------------------------------------------------
+// Null-collision selection by waiting times.  One Bernoulli(P_null) trial per
+// particle and step is replaced by its equivalent: the steps W between a
+// particle's selections (or from its entry into the run) follow the geometric
+// law P(W > k) = (1 - P_null)^k, drawn once per selection.  W - 1 =
+// 4096 a + 64 b + c with three independent digits, each the number of
+// thresholds of its table (computed on the host) above one 32-bit Philox word;
+// a = 64 stands for a wait beyond 64^3 steps, which ends in a fresh draw.  The
+// push only counts down the wait held in the cell word's upper bits.
+// ---------------------------------------------------------------------------
+// Number of entries of the non-increasing table t[0, n) above u.
+__device__ __forceinline__ uint32_t wait_digit(const uint32_t *t, int n, uint32_t u) {
+    int lo = 0, hi = n;  // t[j] > u for j < lo; t[j] <= u for j >= hi
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (u < t[mid])
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (uint32_t)lo;
+}
+
+// The wait of particle `id` of species S drawn at `step` (sub 0: after a
+// selection; 1: on entering the run), kRedrawBit set when the count ends in
+// a fresh draw instead of a selection.
+__device__ __forceinline__ uint32_t draw_wait(const Run &R, int S, uint32_t id, long long step, uint32_t sub) {
+    if (!R.thr[S]) return kWaitCap | kRedrawBit;  // P_null = 0: never selected
+    const uint4 w = draw(R, id, step, S, kTagWait, sub);
+    const uint32_t a = wait_digit(R.wait_thr[S][2], 64, w.x);
+    if (a == 64u) return kWaitCap | kRedrawBit;
+    const uint32_t b = wait_digit(R.wait_thr[S][1], 63, w.y);
+    const uint32_t c = wait_digit(R.wait_thr[S][0], 63, w.z);
+    return 1u + 4096u * a + 64u * b + c;
+}
+
+// The upper bits of a cell word that holds the wait w.
+__device__ __forceinline__ uint32_t wait_bits(uint32_t w) {
+    return ((w & ~kRedrawBit) << kCellBits) | (w & kRedrawBit);
 }
 
 // Uniform on (0, 1) from the top 24 bits k of a word: u = (k + 1/2) 2^-24.
@@ -589,18 +631,20 @@ __device__ void block_sum2(double &x, double &y, double *scratch /*[2*kThreads/3
 // ---------------------------------------------------------------------------
 // Shared-memory layout of the particle kernels.
 // ---------------------------------------------------------------------------
-// Deferred collisions: selected particles wait here (slot and id; the
-// collision redraws its Philox words from them) and are collided later by
-// full warps.  The queue is drained before a tile whenever fewer than a
-// tile's worth of entries are free, so it cannot overflow.
+// Deferred collisions: particles whose wait ran out in the push wait here
+// (their slot; kQueueRedraw marks a count that only ends in a fresh draw of
+// the wait) and are collided later by full warps, which read their ids and
+// draw their Philox words and next waits.  The queue is drained before a tile
+// whenever fewer than a tile's worth of entries are free, so it cannot
+// overflow.
 #ifndef PIC_QDRAIN
 #define PIC_QDRAIN 128
 #endif
 constexpr unsigned int kQueueDrainAbove = PIC_QDRAIN;
 constexpr int kQueue = (int)kQueueDrainAbove + kThreads * kUnroll;  // + one tile
+constexpr uint32_t kQueueRedraw = 0x80000000u;  // in a queue entry: no collision, only a new wait
 struct CollQueue {
-    int *slot;                 // [kQueue]
-    uint32_t *id;              // [kQueue]
+    uint32_t *slot;            // [kQueue] slot | kQueueRedraw
     unsigned int *n;           // entries queued
 };
 
@@ -616,7 +660,7 @@ __host__ __device__ inline size_t align8(size_t x) { return (x + 7) & ~size_t(7)
 
 __host__ __device__ inline size_t main_smem_bytes(int n, int bins, bool ec3) {
     return align8(4 * (size_t)(n + 2)) + (ec3 ? 7 : 4) * align8(4 * (size_t)(n + 1)) +
-           align8(4 * (size_t)n) + align8(4 * (size_t)(bins + 1)) + 8 * (size_t)kQueue + 16;
+           align8(4 * (size_t)n) + align8(4 * (size_t)(bins + 1)) + 4 * (size_t)kQueue + 16;
 }
 
 // The tail's scratch: the field solve's arrays (32 bytes a node), or, before
@@ -655,9 +699,7 @@ __device__ SmemMain carve_main(unsigned char *base, int n, int bins, bool ec3 = 
     o += align8(4 * (size_t)n);
     s.eedf = (unsigned int *)(base + o);
     o += align8(4 * (size_t)(bins + 1));
-    s.q.slot = (int *)(base + o);
-    o += 4 * (size_t)kQueue;
-    s.q.id = (uint32_t *)(base + o);
+    s.q.slot = (uint32_t *)(base + o);
     o += 4 * (size_t)kQueue;
     s.q.n = (unsigned int *)(base + o);
     return s;
@@ -714,30 +756,36 @@ __device__ __forceinline__ void eedf_sample(const Run &R, const SmemMain &sm, fl
     atomicAdd(&sm.eedf[bin], 1u);
 }
 
-// Collide the queued particles, one per thread.  Their post-push position
-// and velocity were stored before the barrier that precedes this call.
+// Collide the queued particles, one per thread, and draw their next waits.
+// Their post-push cell word (count zero), position and velocity were stored
+// before the barrier that precedes this call.
 template <int S, bool INL>
 __device__ __forceinline__ void drain_body(const Run &R, const SmemMain &sm, Species sp, long long step, bool diag,
                                            Tally &t) {
     __syncthreads();
     const unsigned int nq = min(*sm.q.n, (unsigned int)kQueue);
     for (unsigned int q = threadIdx.x; q < nq; q += kThreads) {
-        const int idx = sm.q.slot[q];
-        const uint32_t id = sm.q.id[q];
-        const uint4 w = draw(R, id, step, S, kTagMcc, 0);  // the selection's draw
+        const uint32_t entry = sm.q.slot[q];
+        const int idx = (int)(entry & ~kQueueRedraw);
+        const uint32_t id = sp.id[idx];
+        const int c = sp.cell[idx] & (int)kCellMask;
         float vx = sp.vx[idx], vy = sp.vy[idx], vz = sp.vz[idx];
-        bool changed;
-        if (S == 0) {
-            const float abar = sp.abar ? sp.abar[idx] : 0.0f;
-            changed = collide_e<INL>(R, w, id, step, sp.cell[idx], sp.off[idx], abar, vx, vy, vz, t);
-        } else {
-            changed = collide_i<INL>(R, w, id, step, vx, vy, vz, t);
+        if (!(entry & kQueueRedraw)) {  // selected: the collision's words
+            const uint4 w = draw(R, id, step, S, kTagMcc, 0);
+            bool changed;
+            if (S == 0) {
+                const float abar = sp.abar ? sp.abar[idx] : 0.0f;
+                changed = collide_e<INL>(R, w, id, step, c, sp.off[idx], abar, vx, vy, vz, t);
+            } else {
+                changed = collide_i<INL>(R, w, id, step, vx, vy, vz, t);
+            }
+            if (changed) {
+                sp.vx[idx] = vx;
+                sp.vy[idx] = vy;
+                sp.vz[idx] = vz;
+            }
         }
-        if (changed) {
-            sp.vx[idx] = vx;
-            sp.vy[idx] = vy;
-            sp.vz[idx] = vz;
-        }
+        sp.cell[idx] = c | (int)wait_bits(draw_wait(R, S, id, step, 0));
         if (S == 0 && diag && R.eedf_bins > 0) eedf_sample(R, sm, vx, vy, vz);
     }
     __syncthreads();
@@ -765,7 +813,7 @@ __device__ __forceinline__ void drain_q(const Run &R, const SmemMain &sm, Specie
 // hot loop's instruction footprint).
 struct SpK {
     float qm, qw, qm_dt;
-    uint32_t thr;
+    uint32_t collides;  // the species' P_null > 0
     int S;
 };
 
@@ -774,22 +822,24 @@ __device__ __forceinline__ SpK species_k(const Run &R, int S) {
 }
 
 // ---------------------------------------------------------------------------
-// One particle of each mode.  Returns its deposit key (-1: none) and value a.
+// One particle of each mode.  `cell` is the particle's cell word (cell and,
+// with collisions, its wait).  Returns its deposit key (-1: none) and value a.
 // On return cell < 0 marks an absorbed particle.
 // ---------------------------------------------------------------------------
 template <int MODE, bool INL>
 __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, const Species &sp, const SpK &k,
                                              long long idx, int &cell, float &off, float &vx,
-                                             float &abar, uint32_t id, bool sel, bool diag, long long step,
+                                             float &abar, bool diag, long long step,
                                              Tally &t, float &kx, float &pw, uint32_t &a_out) {
     using MI = ModeInfo<MODE>;
     const int N = R.n_cells;
-    if (MODE == kDepositEC) return deposit_key_s2(cell, off, a_out);
-    if (MODE == kDepositMC) return deposit_key_s1(cell, off, a_out);
-    if (MODE == kDepositEC3) return deposit_key_s3(cell, off, a_out);
+    const int c0 = cell & (int)kCellMask;
+    if (MODE == kDepositEC) return deposit_key_s2(c0, off, a_out);
+    if (MODE == kDepositMC) return deposit_key_s1(c0, off, a_out);
+    if (MODE == kDepositEC3) return deposit_key_s3(c0, off, a_out);
     const float v_old = vx;
     float e_field, v_new, s;
-    int c = cell;
+    int c = c0;
     if (MI::implicit) {
         // predictor: v~ = v + dt abar / 2, x~ = x + dt v~
         const float vt = fmaf(R.half_dt, abar, vx);
@@ -816,10 +866,10 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         abar = 0.5f * (abar + acc);
     } else {
         // explicit leapfrog with E^n at x^n (Sec. 2 schemes (1), (2))
-        e_field = MI::mc ? (1.0f - off) * sm.e[cell] + off * sm.e[cell + 1]
-                         : (MI::ec3 ? gather_ec3(sm.e, cell, off) : gather_ec(sm.e, cell, off));
+        e_field = MI::mc ? (1.0f - off) * sm.e[c0] + off * sm.e[c0 + 1]
+                         : (MI::ec3 ? gather_ec3(sm.e, c0, off) : gather_ec(sm.e, c0, off));
         v_new = fmaf(k.qm_dt, e_field, vx);
-        if (diag) atomicAdd(&sm.heat[cell], k.qw * e_field * 0.5f * (v_old + v_new));
+        if (diag) atomicAdd(&sm.heat[c0], k.qw * e_field * 0.5f * (v_old + v_new));
         s = fmaf(v_new, R.dt_dx, off);
     }
     kx += 0.5f * (v_old * v_old + v_new * v_new);  // kept in registers: t lives in memory
@@ -836,22 +886,27 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         cell = -1;
         return -1;
     }
-    cell = c;
-    // null-collision Monte Carlo: `sel` is this particle's selection (one
-    // Philox draw per particle and step, made by the caller); a selected
-    // particle is queued and collided later by full warps (its position,
-    // hence its charge assignment, does not change in a collision)
+    // null-collision Monte Carlo: count the wait down; a wait that runs out
+    // queues the particle, which full warps collide later and give its next
+    // wait (a collision leaves the position, hence the charge assignment, as
+    // it is)
+    uint32_t hi = (uint32_t)cell & ~kCellMask;
     bool queued = false;
-    if (R.mcc && sel) {
-        const unsigned int pos = atomicAdd(sm.q.n, 1u);
-        if (pos < (unsigned int)kQueue) {  // always: drains keep a tile's room
-            sm.q.slot[pos] = (int)idx;
-            sm.q.id[pos] = id;
-            queued = true;
+    if (R.mcc && k.collides) {
+        if (((hi & ~kRedrawBit) >> kCellBits) > 1u) {
+            hi -= kWaitOne;
         } else {
-            atomicOr(&R.st->status, 0x8u);
+            const unsigned int pos = atomicAdd(sm.q.n, 1u);
+            if (pos < (unsigned int)kQueue) {  // always: drains keep a tile's room
+                sm.q.slot[pos] = (uint32_t)idx | (hi & kRedrawBit ? kQueueRedraw : 0u);
+                queued = true;
+            } else {
+                atomicOr(&R.st->status, 0x8u);
+            }
+            hi = 0u;  // the drain stores the next wait
         }
     }
+    cell = c | (int)hi;
     if (k.S == 0 && diag && R.eedf_bins > 0 && !queued) eedf_sample(R, sm, vx, sp.vy[idx], sp.vz[idx]);
     if (MI::mc) return deposit_key_s1(c, s, a_out);
     if (MI::ec3) return deposit_key_s3(c, s, a_out);
@@ -910,7 +965,7 @@ static_assert(kQueueDrainAbove + kTile <= kQueue, "a tile must fit the undrained
 #define PIC_STAGES 2
 #endif
 constexpr int kStages = PIC_STAGES;
-constexpr int kMaxFields = 5;  // cell, off, vx, abar, id
+constexpr int kMaxFields = 4;  // cell, off, vx, abar
 // A wait gives up after about a second (or 2^30 polls, whichever comes first).
 constexpr unsigned long long kWaitNs = 1000000000ull;
 constexpr long long kWaitPolls = 1ll << 30;
@@ -990,13 +1045,13 @@ __global__ void k_wait_selftest(unsigned long long limit_ns, unsigned int *statu
 }
 
 // The ring: kStages x nf arrays of kTile words, one barrier per stage.  The
-// implicit passes stage all five fields (cell, off, vx, abar, id); the other
-// modes have no abar, and id takes its place.
+// implicit passes stage cell, off, vx and abar; the other modes cell, off and
+// vx (the id of a particle is read only when its wait runs out).
 struct Ring {
     uint32_t *buf;               // [kStages][nf][kTile]
     unsigned long long *bar;     // [kStages] (static shared)
     unsigned int *uses;          // tiles issued so far by this block (static shared)
-    int nf;                      // 4 or kMaxFields
+    int nf;                      // 3 or kMaxFields
 };
 
 __host__ __device__ constexpr size_t ring_bytes(bool implicit) {
@@ -1005,8 +1060,7 @@ __host__ __device__ constexpr size_t ring_bytes(bool implicit) {
 // The idle ring holds the tail's copy of the per-key sums (6 x 8 bytes a key).
 
 __device__ __forceinline__ uint32_t *ring_field(const Ring &g, int stage, int f) {
-    const int slot = (f == kMaxFields - 1 && g.nf < kMaxFields) ? f - 1 : f;
-    return g.buf + ((size_t)stage * g.nf + slot) * kTile;
+    return g.buf + ((size_t)stage * g.nf + f) * kTile;
 }
 
 // A thread's kUnroll consecutive words of a staged field, from place s0 of the
@@ -1029,9 +1083,9 @@ __device__ __forceinline__ void ring_words(const Ring &g, int stage, int f, int 
 // Load a thread's particles of a staged tile: n_ok of them are real (cell -1
 // marks the rest); fields a mode does not use read as zero.
 template <int MODE>
-__device__ __forceinline__ void ring_particles(const Ring &g, int stage, int s0, int n_ok, bool need_id,
-                                               int (&cell)[kUnroll], float (&off)[kUnroll], float (&vx)[kUnroll],
-                                               float (&abar)[kUnroll], uint32_t (&id)[kUnroll]) {
+__device__ __forceinline__ void ring_particles(const Ring &g, int stage, int s0, int n_ok, int (&cell)[kUnroll],
+                                               float (&off)[kUnroll], float (&vx)[kUnroll],
+                                               float (&abar)[kUnroll]) {
     using MI = ModeInfo<MODE>;
     uint32_t w[kUnroll];
     ring_words(g, stage, 0, s0, w);
@@ -1041,7 +1095,7 @@ __device__ __forceinline__ void ring_particles(const Ring &g, int stage, int s0,
 #pragma unroll
     for (int q = 0; q < kUnroll; ++q) off[q] = q < n_ok ? __uint_as_float(w[q]) : 0.0f;
 #pragma unroll
-    for (int q = 0; q < kUnroll; ++q) vx[q] = abar[q] = 0.0f, id[q] = 0u;
+    for (int q = 0; q < kUnroll; ++q) vx[q] = abar[q] = 0.0f;
     if (MI::loads_v) {
         ring_words(g, stage, 2, s0, w);
 #pragma unroll
@@ -1052,36 +1106,19 @@ __device__ __forceinline__ void ring_particles(const Ring &g, int stage, int s0,
 #pragma unroll
         for (int q = 0; q < kUnroll; ++q) abar[q] = q < n_ok ? __uint_as_float(w[q]) : 0.0f;
     }
-    if (need_id) {
-        ring_words(g, stage, 4, s0, w);
-#pragma unroll
-        for (int q = 0; q < kUnroll; ++q) id[q] = q < n_ok ? w[q] : 0u;
-    }
-}
-
-// The null-collision selections of a thread's particles, one Philox draw
-// each (only the first word decides), computed side by side without
-// branches so that the independent multiply chains overlap.
-__device__ __forceinline__ void mcc_select(const Run &R, const uint32_t (&id)[kUnroll], long long step, int S,
-                                           uint32_t thr, bool (&sel)[kUnroll]) {
-    uint32_t x[kUnroll];
-#pragma unroll
-    for (int q = 0; q < kUnroll; ++q) x[q] = draw(R, id[q], step, S, kTagMcc, 0).x;
-#pragma unroll
-    for (int q = 0; q < kUnroll; ++q) sel[q] = (x[q] >> 8) < thr;
 }
 
 // Issue the copies of tile t (block-relative tile counter u) of segment
-// [b, b + len): fields in the order cell, off, vx, abar, id.
+// [b, b + len): fields in the order cell, off, vx, abar.
 template <int MODE>
 __device__ __forceinline__ void ring_issue(const Ring &g, const Species &sp0, long long b, int len, int t,
-                                           unsigned int u, bool need_id) {
+                                           unsigned int u) {
     using MI = ModeInfo<MODE>;
     const int stage = (int)(u % kStages);
     const int first = t * kTile;
     const int n = min(kTile, len - first);
     const unsigned int bytes = (unsigned int)(((n * 4) + 15) & ~15);  // arrays are padded to 16 bytes
-    const int nf = 2 + (MI::loads_v ? 1 : 0) + (MI::implicit ? 1 : 0) + (need_id ? 1 : 0);
+    const int nf = 2 + (MI::loads_v ? 1 : 0) + (MI::implicit ? 1 : 0);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&g.bar[stage], bytes * nf);
     const long long o = b + first;
@@ -1089,7 +1126,6 @@ __device__ __forceinline__ void ring_issue(const Ring &g, const Species &sp0, lo
     bulk_g2s(ring_field(g, stage, 1), sp0.off + o, bytes, &g.bar[stage]);
     if (MI::loads_v) bulk_g2s(ring_field(g, stage, 2), sp0.vx + o, bytes, &g.bar[stage]);
     if (MI::implicit) bulk_g2s(ring_field(g, stage, 3), sp0.abar + o, bytes, &g.bar[stage]);
-    if (need_id) bulk_g2s(ring_field(g, stage, 4), sp0.id + o, bytes, &g.bar[stage]);
 }
 
 // Stream one species segment [b, e) through the block in staged tiles; each
@@ -1110,17 +1146,16 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
     sp.id = sp0.id + b;
     sp.abar = MI::implicit ? sp0.abar + b : nullptr;
     const int len = (int)(e - b);
-    const bool need_id = MI::push && R.mcc;
     const int ntiles = (len + kTile - 1) / kTile;
     const unsigned int u0 = *g.uses;  // tiles this block issued before this segment
     float kx = 0.0f, pw = 0.0f;
     if (threadIdx.x == 0)
-        for (int tt = 0; tt < kStages - 1 && tt < ntiles; ++tt) ring_issue<MODE>(g, sp0, b, len, tt, u0 + tt, need_id);
+        for (int tt = 0; tt < kStages - 1 && tt < ntiles; ++tt) ring_issue<MODE>(g, sp0, b, len, tt, u0 + tt);
     for (int tl = 0; tl < ntiles; ++tl) {
         const unsigned int u = u0 + tl;
         const int stage = (int)(u % kStages);
         if (threadIdx.x == 0 && tl + kStages - 1 < ntiles)
-            ring_issue<MODE>(g, sp0, b, len, tl + kStages - 1, u + kStages - 1, need_id);
+            ring_issue<MODE>(g, sp0, b, len, tl + kStages - 1, u + kStages - 1);
         if (!mbar_wait(R, &g.bar[stage], (u / kStages) & 1u)) {
             // give up on this segment, but not before the copies already
             // issued into the ring have landed (bounded as well)
@@ -1139,11 +1174,8 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
         const bool full = i0 + U - 1 < len;
         int cell[U];
         float off[U], vx[U], abar[U];
-        uint32_t id[U];
-        ring_particles<MODE>(g, stage, s0, len - i0, need_id, cell, off, vx, abar, id);
-        bool sel[U] = {};
+        ring_particles<MODE>(g, stage, s0, len - i0, cell, off, vx, abar);
         const SpK k = species_k(R, S);
-        if (need_id) mcc_select(R, id, step, S, k.thr, sel);
         int key[U];
         uint32_t a[U];
 #pragma unroll
@@ -1152,7 +1184,7 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
             key[q] = -1;
             if (cell[q] < 0) continue;  // beyond the segment, or a hole left by absorption
             key[q] = step_particle<MODE, false>(R, sm, sp, k, (long long)(i0 + q), cell[q], off[q], vx[q],
-                                            abar[q], id[q], sel[q], diag, step, t, kx, pw, a[q]);
+                                            abar[q], diag, step, t, kx, pw, a[q]);
         }
         if (MI::push) {
             if (full) {
@@ -1435,7 +1467,7 @@ struct TailHead {
 // the caller.
 template <int MODE>
 __device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag, const TailHead &hd,
-                            const Birth &my, bool dry) {
+                            const Birth &my, bool dry, long long step) {
     const unsigned int B = hd.B, ok = hd.ok;
     if (B == 0) return;
     const Species se = R.buf[hd.parity][0], si = R.buf[hd.parity][1];
@@ -1456,13 +1488,14 @@ __device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag
             }
         }
         if (dry) return;
-        se.cell[je] = bb.cell;
+        // each child draws its first wait on its birth step
+        se.cell[je] = bb.cell | (R.mcc ? (int)wait_bits(draw_wait(R, 0, id_e + r, step, 1)) : 0);
         se.off[je] = bb.off;
         se.vx[je] = bb.ve[0];
         se.vy[je] = bb.ve[1];
         se.vz[je] = bb.ve[2];
         se.id[je] = id_e + r;
-        si.cell[ji] = bb.cell;
+        si.cell[ji] = bb.cell | (R.mcc ? (int)wait_bits(draw_wait(R, 1, id_i + r, step, 1)) : 0);
         si.off[ji] = bb.off;
         si.vx[ji] = bb.vi[0];
         si.vy[ji] = bb.vi[1];
@@ -2156,7 +2189,7 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
         hd.ok = ok;
     }
     __syncthreads();
-    if (births && ph_lo <= 1 && 1 < ph_hi) tail_births<MODE>(R, Ks, smem, diag, hd, my, dry);
+    if (births && ph_lo <= 1 && 1 < ph_hi) tail_births<MODE>(R, Ks, smem, diag, hd, my, dry, step);
     if (ph_lo <= 2 && 2 < ph_hi) {
         const Volt vl = {hd.vl_v, hd.vl_hi, hd.vl_lo};  // read only if vl_state
         if (MI::explicit_push)
@@ -2276,8 +2309,8 @@ __device__ __forceinline__ void producer_items(Producer &p, long long ne, long l
 // waited on (a claim kept in shared memory would stall the issuing warp on
 // the store of its result).  can_claim: `claim` outlives this call.
 __device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, const Stream &ms, Producer &p,
-                                               int par, unsigned int u, bool need_id, int mode_fields,
-                                               bool implicit, unsigned int &claim, bool can_claim) {
+                                               int par, unsigned int u, int mode_fields, bool implicit,
+                                               unsigned int &claim, bool can_claim) {
     const int stage = (int)(u % kStages);
     if (p.pos >= p.end) {
         long long it = p.total;
@@ -2313,7 +2346,7 @@ __device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, cons
     ms.o[stage] = p.pos;
     ms.n[stage] = n;
     const unsigned int bytes = (unsigned int)(((n * 4) + 15) & ~15);  // arrays are padded to 16 bytes
-    const int nf = mode_fields + (implicit ? 1 : 0) + (need_id ? 1 : 0);
+    const int nf = mode_fields + (implicit ? 1 : 0);
     const Species &s = R.buf[par][p.S];
     const long long o = p.pos;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -2322,7 +2355,6 @@ __device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, cons
     bulk_g2s(ring_field(g, stage, 1), s.off + o, bytes, &g.bar[stage]);
     if (mode_fields >= 3) bulk_g2s(ring_field(g, stage, 2), s.vx + o, bytes, &g.bar[stage]);
     if (implicit) bulk_g2s(ring_field(g, stage, 3), s.abar + o, bytes, &g.bar[stage]);
-    if (need_id) bulk_g2s(ring_field(g, stage, 4), s.id + o, bytes, &g.bar[stage]);
     p.pos += n;
 }
 
@@ -2330,7 +2362,7 @@ __device__ __forceinline__ void producer_issue(const Run &R, const Ring &g, cons
 // step_particle and the collision queue are absolute slots of sp.
 template <int MODE>
 __device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, const Ring &g, int stage, int S,
-                                            const Species &sp, long long o, int len, bool need_id, bool diag,
+                                            const Species &sp, long long o, int len, bool diag,
                                             long long step, Tally &t, float &kx, float &pw) {
     constexpr int U = kUnroll;
     using MI = ModeInfo<MODE>;
@@ -2338,11 +2370,8 @@ __device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, co
     const bool full = i0 + U - 1 < len;
     int cell[U];
     float off[U], vx[U], abar[U];
-    uint32_t id[U];
-    ring_particles<MODE>(g, stage, i0, len - i0, need_id, cell, off, vx, abar, id);
-    bool sel[U] = {};
+    ring_particles<MODE>(g, stage, i0, len - i0, cell, off, vx, abar);
     const SpK k = species_k(R, S);
-    if (need_id) mcc_select(R, id, step, S, k.thr, sel);
     int key[U];
     uint32_t a[U];
 #pragma unroll
@@ -2350,8 +2379,8 @@ __device__ __forceinline__ void stream_tile(const Run &R, const SmemMain &sm, co
         a[q] = 0u;
         key[q] = -1;
         if (cell[q] < 0) continue;  // beyond the tile, or a hole left by absorption
-        key[q] = step_particle<MODE, true>(R, sm, sp, k, o + i0 + q, cell[q], off[q], vx[q], abar[q], id[q],
-                                        sel[q], diag, step, t, kx, pw, a[q]);
+        key[q] = step_particle<MODE, true>(R, sm, sp, k, o + i0 + q, cell[q], off[q], vx[q], abar[q], diag, step,
+                                        t, kx, pw, a[q]);
     }
     if (MI::push) {
         const long long b = o + i0;
@@ -2412,8 +2441,7 @@ __device__ __forceinline__ void stream_prime(const Run &R, const Ring &g, const 
     p.inflight = p.done = false;
     unsigned int unused = 0u;
     for (int k = 0; k < kStages - 1; ++k)
-        producer_issue(R, g, ms, p, par, (unsigned int)k, MI::push && R.mcc, MI::loads_v ? 3 : 2, MI::implicit,
-                       unused, false);
+        producer_issue(R, g, ms, p, par, (unsigned int)k, MI::loads_v ? 3 : 2, MI::implicit, unused, false);
 }
 
 // The block's stream of tiles (primed by stream_prime; the caller's barrier
@@ -2425,7 +2453,6 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
     DevState *st = R.st;
     const int par = st->parity;
     const Species sp[2] = {R.buf[par][0], R.buf[par][1]};
-    const bool need_id = MI::push && R.mcc;
     const int mode_fields = MI::loads_v ? 3 : 2;
     Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
     float kx = 0.0f, pw = 0.0f;  // the per-particle sums stay in registers
@@ -2469,14 +2496,14 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
         cur = S;
         const long long o = ms.o[stage];
         if (threadIdx.x == 0)
-            producer_issue(R, g, ms, p, par, u + kStages - 1, need_id, mode_fields, MI::implicit, claim, true);
+            producer_issue(R, g, ms, p, par, u + kStages - 1, mode_fields, MI::implicit, claim, true);
         if (!mbar_wait(R, &g.bar[stage], (u / kStages) & 1u)) {
             // give up, but not before the copies already issued have landed (bounded)
             for (unsigned int w = u + 1; w < u + kStages; ++w)
                 if (ms.n[w % kStages] > 0) mbar_wait(R, &g.bar[w % kStages], (w / kStages) & 1u);
             gave_up = true;
         } else {
-            stream_tile<MODE>(R, sm, g, stage, S, S ? sp[1] : sp[0], o, n, need_id, diag, step, t, kx, pw);
+            stream_tile<MODE>(R, sm, g, stage, S, S ? sp[1] : sp[0], o, n, diag, step, t, kx, pw);
         }
         added += n;
         // The stage is free again.  The thread that queued the tile's last
@@ -2634,7 +2661,8 @@ __device__ void sort_chunk(const Run &R, int par, int S, long long b, long long 
 #pragma unroll
         for (int q = 0; q < V; ++q) {
             uint32_t a;
-            key[q] = cell[q] < 0 ? -1 : (mc ? deposit_key_s1(cell[q], off[q], a) : deposit_key_s2(cell[q], off[q], a));
+            const int c = cell[q] & (int)kCellMask;
+            key[q] = cell[q] < 0 ? -1 : (mc ? deposit_key_s1(c, off[q], a) : deposit_key_s2(c, off[q], a));
             peers[q] = __match_any_sync(FULL_MASK, key[q]);
             claim[q] = 0u;
             if (key[q] >= 0 && lane == __ffs(peers[q]) - 1)
@@ -2698,7 +2726,8 @@ __global__ void k_load(Run R, int S, long long count, float vth) {
         const uint4 w = draw(R, (uint32_t)i, 0, S, kTagLoad, 0);
         const uint4 w2 = draw(R, (uint32_t)i, 0, S, kTagLoad, 1);
         const unsigned long long t = (unsigned long long)w.x * (unsigned long long)R.n_cells;
-        sp.cell[i] = (int32_t)(t >> 32);
+        // the first wait to a null-collision selection is drawn at the load
+        sp.cell[i] = (int32_t)(t >> 32) | (R.mcc ? (int32_t)wait_bits(draw_wait(R, S, (uint32_t)i, 0, 1)) : 0);
         sp.off[i] = (float)((uint32_t)t >> 8) * 5.9604644775390625e-8f;
         float n1, n2, n3, n4;
         box_muller(u24c(w.y), u24c(w.z), n1, n2);
@@ -2720,8 +2749,8 @@ __global__ void k_set_abar(Run R) {
         const long long n = st->n_slots[S];
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
              i += (long long)gridDim.x * blockDim.x) {
-            const int cell = sp.cell[i];
-            if (cell < 0) continue;
+            if (sp.cell[i] < 0) continue;
+            const int cell = sp.cell[i] & (int)kCellMask;
             const float off = sp.off[i];
             float e;
             if (R.scheme == 3) {  // node field, linear weights
@@ -2760,25 +2789,39 @@ cudaError_t launch_check_particles(const int32_t *cell, const float *off, long l
 // After the check (flag clear): the uploaded particles of one species from
 // the idle buffer into the current one, and the species' counters.  A set
 // flag leaves everything as it was; the caller reads the flag afterwards.
-// 16-byte copies: every array starts 256-byte aligned.
-__global__ void k_apply_particles(Species dst, Species src, long long n, bool abar_given, const unsigned int *flag,
-                                  DevState *st, int S, unsigned int next_id) {
+// With collisions every uploaded particle draws its first wait to a
+// selection at the run's current step.  16-byte copies: every array starts
+// 256-byte aligned.
+__device__ __forceinline__ int32_t entry_word(const Run &R, int S, int32_t cell, uint32_t id, long long step) {
+    return R.mcc ? cell | (int32_t)wait_bits(draw_wait(R, S, id, step, 1)) : cell;
+}
+
+__global__ void k_apply_particles(Run R, Species dst, Species src, long long n, bool abar_given,
+                                  const unsigned int *flag, int S, unsigned int next_id) {
     if (*flag) return;
+    DevState *st = R.st;
+    const long long step = st->step;
     const long long n4 = n >> 2, stride = (long long)gridDim.x * blockDim.x;
     const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     for (long long j = t0; j < n4; j += stride) {
-        reinterpret_cast<int4 *>(dst.cell)[j] = reinterpret_cast<const int4 *>(src.cell)[j];
+        int4 c = reinterpret_cast<const int4 *>(src.cell)[j];
+        const uint4 id = reinterpret_cast<const uint4 *>(src.id)[j];
+        c.x = entry_word(R, S, c.x, id.x, step);
+        c.y = entry_word(R, S, c.y, id.y, step);
+        c.z = entry_word(R, S, c.z, id.z, step);
+        c.w = entry_word(R, S, c.w, id.w, step);
+        reinterpret_cast<int4 *>(dst.cell)[j] = c;
         reinterpret_cast<float4 *>(dst.off)[j] = reinterpret_cast<const float4 *>(src.off)[j];
         reinterpret_cast<float4 *>(dst.vx)[j] = reinterpret_cast<const float4 *>(src.vx)[j];
         reinterpret_cast<float4 *>(dst.vy)[j] = reinterpret_cast<const float4 *>(src.vy)[j];
         reinterpret_cast<float4 *>(dst.vz)[j] = reinterpret_cast<const float4 *>(src.vz)[j];
-        reinterpret_cast<uint4 *>(dst.id)[j] = reinterpret_cast<const uint4 *>(src.id)[j];
+        reinterpret_cast<uint4 *>(dst.id)[j] = id;
         if (dst.abar)
             reinterpret_cast<float4 *>(dst.abar)[j] =
                 abar_given ? reinterpret_cast<const float4 *>(src.abar)[j] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     for (long long i = 4 * n4 + t0; i < n; i += stride) {
-        dst.cell[i] = src.cell[i];
+        dst.cell[i] = entry_word(R, S, src.cell[i], src.id[i], step);
         dst.off[i] = src.off[i];
         dst.vx[i] = src.vx[i];
         dst.vy[i] = src.vy[i];
@@ -2793,13 +2836,13 @@ __global__ void k_apply_particles(Species dst, Species src, long long n, bool ab
     }
 }
 
-cudaError_t launch_apply_particles(const Species &dst, const Species &src, long long n, bool abar_given,
-                                   const unsigned int *flag, DevState *st, int S, unsigned int next_id,
+cudaError_t launch_apply_particles(const Run &r, const Species &dst, const Species &src, long long n,
+                                   bool abar_given, const unsigned int *flag, int S, unsigned int next_id,
                                    cudaStream_t s) {
     long long grid = (n / 4 + kThreads - 1) / kThreads;
     if (grid < 1) grid = 1;
     if (grid > 4096) grid = 4096;
-    k_apply_particles<<<(int)grid, kThreads, 0, s>>>(dst, src, n, abar_given, flag, st, S, next_id);
+    k_apply_particles<<<(int)grid, kThreads, 0, s>>>(r, dst, src, n, abar_given, flag, S, next_id);
     return cudaGetLastError();
 }
 

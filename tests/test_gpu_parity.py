@@ -157,7 +157,7 @@ def fp32_sensitivity(cfg, states, steps, abar=None, factor=4.0, step0=0, next_id
             c = np.floor(d["xi"])
             o = np.clip(f32(d["xi"] - c), 0.0, np.nextafter(np.float32(1.0), np.float32(0.0)))
             rnd.set_species(sp, c + o, f32(d["vx"]), f32(d["vy"]), f32(d["vz"]), d["id"], abar=f32(d["abar"]),
-                            next_id=int(nid[k] + born))
+                            next_id=int(nid[k] + born), wait=d["wait"])
         rnd.init_field(set_abar=False)
     out = []
     da, db = rnd.diag(), ref.diag()
@@ -192,12 +192,12 @@ def _oracle_of(cfg, st, step, implicit, extra=4096):
     """An oracle run holding the given device-form state at the given step,
     with the field of that state."""
     orc = oracle.Sim(cfg, cap_e=len(st[0]["id"]) + extra, cap_i=len(st[1]["id"]) + extra)
+    orc.set_step(step)  # particles entering at `step` draw their waits there, as uploads to the GPU do
     for k, sp in enumerate(("e", "i")):
         x = st[k]
         orc.set_species(sp, workloads.xi_of(x), x["vx"].astype(np.float64), x["vy"].astype(np.float64),
                         x["vz"].astype(np.float64), x["id"],
                         abar=x["abar"].astype(np.float64) if implicit else None, next_id=x["next_id"])
-    orc.set_step(step)
     orc.init_field(set_abar=False)
     return orc
 
@@ -232,6 +232,12 @@ def one_step_diagnostics(gpu, cfg, eedf_tol=None):
     scheme = cfg.get("scheme", "ec_explicit")
     implicit = scheme in ("ec_implicit", "mc_implicit")
     st = [gpu.get_particles(sp) for sp in ("e", "i")]
+    # the GPU re-enters its own state at this step, so both sides draw every
+    # particle's wait to its next null-collision selection alike (the waits
+    # are state that the particle read-back leaves out)
+    for k, sp in enumerate(("e", "i")):
+        gpu.set_particles(sp, dict(st[k], abar=st[k]["abar"] if implicit else None), next_id=st[k]["next_id"])
+    gpu.init_field(set_abar=False)
     orc = _oracle_of(cfg, st, d0["step"], implicit)
     g_pre = gpu.grids()
     if not implicit:  # the field the push uses is that of the state

@@ -65,6 +65,7 @@ Layout make_layout(const pic_config &c) {
     L.eedf = take(8 * ((size_t)c.eedf_bins + 1));
     const size_t nb = (size_t)(c.births_capacity > 0 ? c.births_capacity : 1);
     L.births = take(sizeof(Birth) * nb + 8 * nb);  // records + rank and sort scratch
+    L.wait_tab = take(4 * 2 * 3 * 64);
     L.total = o;
     return L;
 }
@@ -285,8 +286,8 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
         const double p_i = 1.0 - std::exp(-nu_i * c.dt);
         R.thr[0] = p_e > 0.0 ? 1u : 0u;
         R.thr[1] = p_i > 0.0 ? 1u : 0u;
-        wait_thresholds(p_e, R.wait_thr[0]);
-        wait_thresholds(p_i, R.wait_thr[1]);
+        R.p_null[0] = p_e;
+        R.p_null[1] = p_i;
         R.nu_max_e = (float)nu_e;
         R.nu_max_i = (float)nu_i;
         R.g_max_i = (float)g_max;
@@ -325,6 +326,7 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
     }
     R.e_gather = (float *)(A + L.e_gather);
     R.e_hi = (float *)(A + L.e_hi);
+    R.wait_tab = (const uint32_t *)(A + L.wait_tab);
     R.e_lo = (float *)(A + L.e_lo);
     R.e_cc = (double *)(A + L.e_cc);
     R.chi = (double *)(A + L.chi);
@@ -449,6 +451,13 @@ int init_run_state(const pic_config &c, const Run &R, unsigned char *arena, size
     st.next_id[0] = (unsigned int)c.np_init;
     st.next_id[1] = (unsigned int)st.n_slots[1];
     CKE(cudaMemcpyAsync(R.st, &st, sizeof st, cudaMemcpyHostToDevice, s));
+    uint32_t tab[2][3][64];
+    std::memset(tab, 0, sizeof tab);
+    if (c.mcc) {
+        wait_thresholds(R.p_null[0], tab[0]);
+        wait_thresholds(R.p_null[1], tab[1]);
+    }
+    CKE(cudaMemcpyAsync((void *)R.wait_tab, tab, sizeof tab, cudaMemcpyHostToDevice, s));
     CKE(cudaStreamSynchronize(s));
     const double vth_e = std::sqrt(kE * c.te_ev / kMe);
     const double vth_i = std::sqrt(kE * c.ti_ev / (c.ion_mass_amu * kAmu));

@@ -149,9 +149,10 @@ struct Run {
     float half_m_over_e[2];// 0.5 m / e: energy [eV] per (m/s)^2
     // collisions (FP32)
     uint32_t thr[2];       // nonzero: the species collides (P_null > 0)
+    double p_null[2];      // null-collision probability per step (host-derived)
     // waiting-time thresholds [species][digit c, b, a][j - 1] of the geometric
-    // law of the steps between selections (draw_wait)
-    uint32_t wait_thr[2][3][64];
+    // law of the steps between selections (draw_wait), in the arena
+    const uint32_t *wait_tab;
     float nu_max_e, nu_max_i, n_g;
     float sig_el, exc_thr, exc_ramp_end, exc_slope, sig_exc_max, iz_thr, sig_iz_k, sig_cx;
     float eps_cap, g_max_i, two_m_over_M, two_e_over_me, vth_gas;
@@ -177,7 +178,7 @@ struct Layout {
     size_t state;
     size_t sp[2][2][7];  // [parity][species][field] offsets (cell, off, vx, vy, vz, id, abar)
     size_t acc_cnt[2], acc_a[2], acc_b[2], acc_c[2], cursor[2], rho_q[2];
-    size_t e_gather, e_cc, chi, avg_ne, avg_ni, avg_e, heat[2], eedf, births, e_hi, e_lo;
+    size_t e_gather, e_cc, chi, avg_ne, avg_ni, avg_e, heat[2], eedf, births, e_hi, e_lo, wait_tab;
     size_t total;
 };
 

@@ -92,14 +92,18 @@ __device__ __forceinline__ uint32_t wait_digit(const uint32_t *t, int n, uint32_
 
 // The wait of particle `id` of species S drawn at `step` (sub 0: after a
 // selection; 1: on entering the run), kRedrawBit set when the count ends in
-// a fresh draw instead of a selection.
-__device__ __forceinline__ uint32_t draw_wait(const Run &R, int S, uint32_t id, long long step, uint32_t sub) {
+// a fresh draw instead of a selection.  tab: the run's [2][3][64] thresholds
+// (a shared-memory copy in the particle launches: each digit is a chain of
+// dependent reads).
+__device__ __forceinline__ uint32_t draw_wait(const Run &R, const uint32_t *tab, int S, uint32_t id, long long step,
+                                              uint32_t sub) {
     if (!R.thr[S]) return kWaitCap | kRedrawBit;  // P_null = 0: never selected
     const uint4 w = draw(R, id, step, S, kTagWait, sub);
-    const uint32_t a = wait_digit(R.wait_thr[S][2], 64, w.x);
+    const uint32_t *t = tab + S * 192;
+    const uint32_t a = wait_digit(t + 128, 64, w.x);
     if (a == 64u) return kWaitCap | kRedrawBit;
-    const uint32_t b = wait_digit(R.wait_thr[S][1], 63, w.y);
-    const uint32_t c = wait_digit(R.wait_thr[S][0], 63, w.z);
+    const uint32_t b = wait_digit(t + 64, 63, w.y);
+    const uint32_t c = wait_digit(t, 63, w.z);
     return 1u + 4096u * a + 64u * b + c;
 }
 
@@ -644,8 +648,9 @@ constexpr unsigned int kQueueDrainAbove = PIC_QDRAIN;
 constexpr int kQueue = (int)kQueueDrainAbove + kThreads * kUnroll;  // + one tile
 constexpr uint32_t kQueueRedraw = 0x80000000u;  // in a queue entry: no collision, only a new wait
 struct CollQueue {
-    uint32_t *slot;            // [kQueue] slot | kQueueRedraw
+    uint32_t *slot;            // [cap] slot | kQueueRedraw
     unsigned int *n;           // entries queued
+    unsigned int cap;          // entries the queue holds
 };
 
 struct SmemMain {
@@ -654,7 +659,17 @@ struct SmemMain {
     float *heat;               // [n]
     unsigned int *eedf;        // [bins+1]
     CollQueue q;
+    const uint32_t *wtab;      // [2][3][64] waiting-time thresholds (static shared memory)
 };
+
+constexpr int kWaitTab = 2 * 3 * 64;
+
+// The run's waiting-time thresholds into shared memory (every thread calls
+// this before a barrier).
+__device__ __forceinline__ void load_wait_tab(const Run &R, uint32_t *dst) {
+    if (!R.mcc) return;
+    for (int k = threadIdx.x; k < kWaitTab; k += kThreads) dst[k] = R.wait_tab[k];
+}
 
 __host__ __device__ inline size_t align8(size_t x) { return (x + 7) & ~size_t(7); }
 
@@ -677,8 +692,9 @@ __host__ __device__ inline size_t tail_stage_bytes(int n, bool ec3 = false) {
     return ((size_t)(ec3 ? 64 : 48) * (n + 1) + 255) & ~size_t(255);
 }
 
-__device__ SmemMain carve_main(unsigned char *base, int n, int bins, bool ec3 = false) {
+__device__ SmemMain carve_main(unsigned char *base, int n, int bins, bool ec3, const uint32_t *wtab) {
     SmemMain s;
+    s.wtab = wtab;
     size_t o = 0;
     s.e = (float *)(base + o);
     o += align8(4 * (size_t)(n + 2));
@@ -702,6 +718,7 @@ __device__ SmemMain carve_main(unsigned char *base, int n, int bins, bool ec3 = 
     s.q.slot = (uint32_t *)(base + o);
     o += 4 * (size_t)kQueue;
     s.q.n = (unsigned int *)(base + o);
+    s.q.cap = (unsigned int)kQueue;
     return s;
 }
 
@@ -785,7 +802,7 @@ __device__ __forceinline__ void drain_body(const Run &R, const SmemMain &sm, Spe
                 sp.vz[idx] = vz;
             }
         }
-        sp.cell[idx] = c | (int)wait_bits(draw_wait(R, S, id, step, 0));
+        sp.cell[idx] = c | (int)wait_bits(draw_wait(R, sm.wtab, S, id, step, 0));
         if (S == 0 && diag && R.eedf_bins > 0) eedf_sample(R, sm, vx, vy, vz);
     }
     __syncthreads();
@@ -897,7 +914,7 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
             hi -= kWaitOne;
         } else {
             const unsigned int pos = atomicAdd(sm.q.n, 1u);
-            if (pos < (unsigned int)kQueue) {  // always: drains keep a tile's room
+            if (pos < sm.q.cap) {  // always: drains keep a tile's room
                 sm.q.slot[pos] = (uint32_t)idx | (hi & kRedrawBit ? kQueueRedraw : 0u);
                 queued = true;
             } else {
@@ -1467,7 +1484,7 @@ struct TailHead {
 // the caller.
 template <int MODE>
 __device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag, const TailHead &hd,
-                            const Birth &my, bool dry, long long step) {
+                            const Birth &my, bool dry, long long step, const uint32_t *wtab) {
     const unsigned int B = hd.B, ok = hd.ok;
     if (B == 0) return;
     const Species se = R.buf[hd.parity][0], si = R.buf[hd.parity][1];
@@ -1489,13 +1506,13 @@ __device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag
         }
         if (dry) return;
         // each child draws its first wait on its birth step
-        se.cell[je] = bb.cell | (R.mcc ? (int)wait_bits(draw_wait(R, 0, id_e + r, step, 1)) : 0);
+        se.cell[je] = bb.cell | (R.mcc ? (int)wait_bits(draw_wait(R, wtab, 0, id_e + r, step, 1)) : 0);
         se.off[je] = bb.off;
         se.vx[je] = bb.ve[0];
         se.vy[je] = bb.ve[1];
         se.vz[je] = bb.ve[2];
         se.id[je] = id_e + r;
-        si.cell[ji] = bb.cell | (R.mcc ? (int)wait_bits(draw_wait(R, 1, id_i + r, step, 1)) : 0);
+        si.cell[ji] = bb.cell | (R.mcc ? (int)wait_bits(draw_wait(R, wtab, 1, id_i + r, step, 1)) : 0);
         si.off[ji] = bb.off;
         si.vx[ji] = bb.vi[0];
         si.vy[ji] = bb.vi[1];
@@ -2091,8 +2108,8 @@ template <int MODE>
 // vl_state: the electrode voltage was stored in the run state at launch start
 // (else the field phase computes it).
 __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, unsigned char *stage, bool diag,
-                                          bool defer, bool vl_state, bool dry = false, int ph_lo = 0,
-                                          int ph_hi = 4) {
+                                          bool defer, bool vl_state, const uint32_t *wtab, bool dry = false,
+                                          int ph_lo = 0, int ph_hi = 4) {
     using MI = ModeInfo<MODE>;
     constexpr bool births = MI::explicit_push || MI::pass2;
     DevState *st = R.st;
@@ -2189,7 +2206,7 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
         hd.ok = ok;
     }
     __syncthreads();
-    if (births && ph_lo <= 1 && 1 < ph_hi) tail_births<MODE>(R, Ks, smem, diag, hd, my, dry, step);
+    if (births && ph_lo <= 1 && 1 < ph_hi) tail_births<MODE>(R, Ks, smem, diag, hd, my, dry, step, wtab);
     if (ph_lo <= 2 && 2 < ph_hi) {
         const Volt vl = {hd.vl_v, hd.vl_hi, hd.vl_lo};  // read only if vl_state
         if (MI::explicit_push)
@@ -2234,8 +2251,8 @@ __device__ __forceinline__ void tail_body(const Run &R, unsigned char *smem, uns
 // kernel inlines the body.
 template <int MODE>
 __device__ __noinline__ void tail(const Run &R, unsigned char *smem, unsigned char *stage, bool diag, bool defer,
-                                  bool vl_state) {
-    tail_body<MODE>(R, smem, stage, diag, defer, vl_state);
+                                  bool vl_state, const uint32_t *wtab) {
+    tail_body<MODE>(R, smem, stage, diag, defer, vl_state, wtab);
 }
 
 // The block's share of the particles: blocks are split between the species in
@@ -2540,7 +2557,8 @@ __global__ void __launch_bounds__(kThreads, (MODE == kExplicitEC3 || MODE == kDe
     g.nf = MI::implicit ? kMaxFields : kMaxFields - 1;
     const Stream ms = {s_ms_S, s_ms_o, s_ms_n};
     unsigned char *smem = smem_all + ring_bytes(MI::implicit);  // grid, accumulators, queue; the tail's space
-    const SmemMain sm = carve_main(smem, n, R.eedf_bins, MI::ec3);
+    __shared__ uint32_t s_wtab[kWaitTab];
+    const SmemMain sm = carve_main(smem, n, R.eedf_bins, MI::ec3, s_wtab);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1u);
         s_uses = 0u;
@@ -2552,6 +2570,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == kExplicitEC3 || MODE == kDe
     // shared-memory grid
     if (MI::needs_field)
         for (int k = threadIdx.x; k < n + 2; k += kThreads) sm.e[k] = R.e_gather[k];
+    if (MI::push) load_wait_tab(R, s_wtab);
     for (int k = threadIdx.x; k <= n; k += kThreads) {
         sm.acc.cnt[k] = 0u;
         sm.acc.a[k] = 0u;
@@ -2603,7 +2622,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == kExplicitEC3 || MODE == kDe
     __syncthreads();
     if (!s_last && s_warm < 0) return;
     if (s_last) __threadfence();
-    tail_body<MODE>(R, smem_all + tail_stage_bytes(n, MI::ec3), smem_all, diag, true, true, !s_last,
+    tail_body<MODE>(R, smem_all + tail_stage_bytes(n, MI::ec3), smem_all, diag, true, true, s_wtab, !s_last,
                     s_last ? 0 : s_warm, s_last ? 4 : s_warm + 1);
 }
 
@@ -2727,7 +2746,7 @@ __global__ void k_load(Run R, int S, long long count, float vth) {
         const uint4 w2 = draw(R, (uint32_t)i, 0, S, kTagLoad, 1);
         const unsigned long long t = (unsigned long long)w.x * (unsigned long long)R.n_cells;
         // the first wait to a null-collision selection is drawn at the load
-        sp.cell[i] = (int32_t)(t >> 32) | (R.mcc ? (int32_t)wait_bits(draw_wait(R, S, (uint32_t)i, 0, 1)) : 0);
+        sp.cell[i] = (int32_t)(t >> 32) | (R.mcc ? (int32_t)wait_bits(draw_wait(R, R.wait_tab, S, (uint32_t)i, 0, 1)) : 0);
         sp.off[i] = (float)((uint32_t)t >> 8) * 5.9604644775390625e-8f;
         float n1, n2, n3, n4;
         box_muller(u24c(w.y), u24c(w.z), n1, n2);
@@ -2793,7 +2812,7 @@ cudaError_t launch_check_particles(const int32_t *cell, const float *off, long l
 // selection at the run's current step.  16-byte copies: every array starts
 // 256-byte aligned.
 __device__ __forceinline__ int32_t entry_word(const Run &R, int S, int32_t cell, uint32_t id, long long step) {
-    return R.mcc ? cell | (int32_t)wait_bits(draw_wait(R, S, id, step, 1)) : cell;
+    return R.mcc ? cell | (int32_t)wait_bits(draw_wait(R, R.wait_tab, S, id, step, 1)) : cell;
 }
 
 __global__ void k_apply_particles(Run R, Species dst, Species src, long long n, bool abar_given,
@@ -2896,17 +2915,18 @@ __global__ void k_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1
 // ---------------------------------------------------------------------------
 template <int MODE>
 __device__ void batch_item(const Run &R, unsigned char *smem, const Ring &g, int S, long long b, long long e,
-                           unsigned int items_r, int r, int &loaded_run) {
+                           unsigned int items_r, int r, int &loaded_run, uint32_t *wtab) {
     using MI = ModeInfo<MODE>;
     __shared__ bool s_last;
     DevState *st = R.st;
     const int n = R.n_cells;
-    const SmemMain sm = carve_main(smem, n, R.eedf_bins);
+    const SmemMain sm = carve_main(smem, n, R.eedf_bins, false, wtab);
     const long long step = st->step;
     const bool diag = MI::push && R.diag_period > 0 && (step % R.diag_period) == 0;
     if (loaded_run != r) {
         if (MI::needs_field)
             for (int k = threadIdx.x; k < n + 2; k += kThreads) sm.e[k] = R.e_gather[k];
+        if (MI::push || MI::pass2) load_wait_tab(R, wtab);
         for (int k = threadIdx.x; k <= n; k += kThreads) {
             sm.acc.cnt[k] = 0u;
             sm.acc.a[k] = 0u;
@@ -2949,7 +2969,7 @@ __device__ void batch_item(const Run &R, unsigned char *smem, const Ring &g, int
     __syncthreads();
     if (s_last) {
         __threadfence();
-        tail<MODE>(R, (unsigned char *)g.buf + tail_stage_bytes(n), (unsigned char *)g.buf, diag, false, false);
+        tail<MODE>(R, (unsigned char *)g.buf + tail_stage_bytes(n), (unsigned char *)g.buf, diag, false, false, wtab);
         loaded_run = -1;  // the tail reused the shared memory
         __syncthreads();
     }
@@ -2980,6 +3000,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ r
     __shared__ bool s_glast;
     __shared__ __align__(8) unsigned long long s_bar[kStages];
     __shared__ unsigned int s_uses;
+    __shared__ uint32_t s_wtab[kWaitTab];
     unsigned int *table = (unsigned int *)(smem_all + table_off);  // [2 nruns + 1] item prefix
     Ring g;
     g.buf = (uint32_t *)smem_all;
@@ -3050,17 +3071,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ r
             batch_sort_item(R, S, b, e, items_r);
         } else if (PHASE == 1) {
             if (R.scheme == 3)
-                batch_item<kImplicit2MC>(R, smem, g, S, b, e, items_r, r, loaded_run);
+                batch_item<kImplicit2MC>(R, smem, g, S, b, e, items_r, r, loaded_run, s_wtab);
             else
-                batch_item<kImplicit2>(R, smem, g, S, b, e, items_r, r, loaded_run);
+                batch_item<kImplicit2>(R, smem, g, S, b, e, items_r, r, loaded_run, s_wtab);
         } else if (R.scheme == 0) {
-            batch_item<kExplicitEC>(R, smem, g, S, b, e, items_r, r, loaded_run);
+            batch_item<kExplicitEC>(R, smem, g, S, b, e, items_r, r, loaded_run, s_wtab);
         } else if (R.scheme == 1) {
-            batch_item<kExplicitMC>(R, smem, g, S, b, e, items_r, r, loaded_run);
+            batch_item<kExplicitMC>(R, smem, g, S, b, e, items_r, r, loaded_run, s_wtab);
         } else if (R.scheme == 2) {
-            batch_item<kImplicit1>(R, smem, g, S, b, e, items_r, r, loaded_run);
+            batch_item<kImplicit1>(R, smem, g, S, b, e, items_r, r, loaded_run, s_wtab);
         } else {
-            batch_item<kImplicit1MC>(R, smem, g, S, b, e, items_r, r, loaded_run);
+            batch_item<kImplicit1MC>(R, smem, g, S, b, e, items_r, r, loaded_run, s_wtab);
         }
     }
     // the last block of the launch publishes the work counts of the next one
@@ -3551,7 +3572,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_adj_fwd(Run R, AdjFwd 
     __shared__ double s_obj[2][kThreads / 32];
     constexpr int U = kUnroll;
     const int n = R.n_cells;
-    const SmemMain sm = carve_main(smem, n, 0);
+    const SmemMain sm = carve_main(smem, n, 0, false, nullptr);
     if (PUSH)
         for (int k = threadIdx.x; k < n + 2; k += kThreads) sm.e[k] = A.e_in[k];
     for (int k = threadIdx.x; k <= n; k += kThreads) {

@@ -69,6 +69,7 @@ class Params(ctypes.Structure):
         ("iz_thr", ctypes.c_double), ("sig_iz_peak", ctypes.c_double),
         ("sig_cx", ctypes.c_double), ("eps_cap", ctypes.c_double),
         ("cx_vmax", ctypes.c_double), ("eedf_max_ev", ctypes.c_double),
+        ("coll_model", ctypes.c_int32), ("reserved", ctypes.c_int32), ("iz_split_b", ctypes.c_double),
     ]
 
 
@@ -138,6 +139,10 @@ def lib():
         L.orc_gather_mc.argtypes = [_P(Params), _d, ctypes.c_double]
         L.orc_gather_mc.restype = ctypes.c_double
         L.orc_rotate.argtypes = [_d, ctypes.c_double, ctypes.c_double, _d]
+        L.orc_vs_cos_chi.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.orc_vs_cos_chi.restype = ctypes.c_double
+        L.orc_opal_secondary.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.orc_opal_secondary.restype = ctypes.c_double
         L.orc_sim_create.argtypes = [_P(Params), ctypes.c_int64, ctypes.c_int64]
         L.orc_sim_create.restype = ctypes.c_void_p
         L.orc_sim_free.argtypes = [ctypes.c_void_p]
@@ -201,6 +206,9 @@ def params(cfg: dict) -> Params:
     p.eps_cap = float(cfg.get("eps_cap", 100.0))
     p.cx_vmax = float(cfg.get("cx_vmax", 2.0 * p.rf_volt + 50.0))
     p.eedf_max_ev = float(cfg.get("eedf_max_ev", 50.0))
+    p.coll_model = (1 if cfg.get("iz_split", "equal") == "opal" else 0) | \
+        (2 if cfg.get("scattering", "isotropic") == "vahedi_surendra" else 0)
+    p.iz_split_b = float(cfg.get("iz_split_b", 10.0))
     return p
 
 
@@ -227,6 +235,18 @@ def wait_draws(cfg, species, ids, step, sub=1) -> np.ndarray:
     lib().orc_wait_draws(ctypes.byref(p), int(SPECIES.get(species, species)), len(ids),
                          _ptr(ids, ctypes.c_uint32), int(step), int(sub), _ptr(out, ctypes.c_uint32))
     return out
+
+
+def vs_cos_chi(eps_ev, u) -> np.ndarray:
+    """cos chi of Vahedi-Surendra anisotropic scattering at energy eps_ev for uniforms u."""
+    u = np.atleast_1d(np.asarray(u, dtype=np.float64))
+    return np.array([lib().orc_vs_cos_chi(float(eps_ev), float(x)) for x in u])
+
+
+def opal_secondary(excess_ev, b_ev, u) -> np.ndarray:
+    """Secondary-electron energy of an ionisation (Opal-Pollock-Wagner) for uniforms u."""
+    u = np.atleast_1d(np.asarray(u, dtype=np.float64))
+    return np.array([lib().orc_opal_secondary(float(excess_ev), float(b_ev), float(x)) for x in u])
 
 
 def philox(key, ctr) -> np.ndarray:

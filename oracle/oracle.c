@@ -500,6 +500,25 @@ void orc_rotate(const double d[3], double cos_chi, double phi, double out[3])
     }
 }
 
+/* Vahedi & Surendra's anisotropic scattering law (their screened-Coulomb fit
+   to the differential cross section sigma(eps, chi) proportional to
+   eps / ((1 + eps sin^2(chi/2)) ln(1 + eps)), eps in eV), sampled by inverting
+   its cumulative distribution: cos chi = (2 + eps - 2 (1 + eps)^u) / eps. */
+double orc_vs_cos_chi(double eps, double u)
+{
+    if (eps <= 0.0) return 1.0 - 2.0 * u;  /* the isotropic limit */
+    return (2.0 + eps - 2.0 * pow(1.0 + eps, u)) / eps;
+}
+
+/* Opal, Pollock & Wagner's secondary-electron spectrum, proportional to
+   1 / (1 + (eps_s / B)^2) on [0, excess / 2], sampled by inverting its
+   cumulative distribution arctan(eps_s / B) / arctan(excess / (2B)). */
+double orc_opal_secondary(double excess, double b, double u)
+{
+    if (excess <= 0.0) return 0.0;
+    return b * tan(u * atan(excess / (2.0 * b)));
+}
+
 /* ------------------------------------------------------------------------- */
 /* Simulation state                                                           */
 /* ------------------------------------------------------------------------- */
@@ -860,7 +879,7 @@ static int collide_electron(orc_sim *s, int64_t i)
     double nu_el = p->gas_density * p->sig_el * g;
     double nu_ex = p->gas_density * sigma_exc(p, eps) * g;
     double nu_iz = p->gas_density * sigma_iz(p, eps) * g;
-    double cos_chi = 1.0 - 2.0 * uniform24(w[2]);
+    const int vs = (p->coll_model & ORC_SCATTER_VS) != 0;
     double phi = 2.0 * PI_D * uniform24(w[3]);
     double d[3] = {1.0, 0.0, 0.0};
     if (g > 0.0) {
@@ -868,28 +887,47 @@ static int collide_electron(orc_sim *s, int64_t i)
         d[1] = v[1] / g;
         d[2] = v[2] / g;
     }
-    double dn[3];
-    orc_rotate(d, cos_chi, phi, dn);
-    double g_new;
+    double g_new, cos_chi;
     if (r < nu_el) {
-        /* elastic: isotropic, energy loss fraction (2m/M)(1 - cos chi) */
+        /* elastic: energy loss fraction (2m/M)(1 - cos chi); the angle law is
+           taken at the incident energy */
+        cos_chi = vs ? orc_vs_cos_chi(eps, uniform24(w[2])) : 1.0 - 2.0 * uniform24(w[2]);
         g_new = g * sqrt(1.0 - 2.0 * M_E / s->d.m[1] * (1.0 - cos_chi));
         s->dg.coll[0] += 1;
     } else if (r < nu_el + nu_ex) {
-        g_new = sqrt(2.0 * Q_E * (eps - p->exc_thr) / M_E);
+        double e_out = eps - p->exc_thr;
+        cos_chi = vs ? orc_vs_cos_chi(e_out, uniform24(w[2])) : 1.0 - 2.0 * uniform24(w[2]);
+        g_new = sqrt(2.0 * Q_E * e_out / M_E);
         s->dg.coll[1] += 1;
     } else if (r < nu_el + nu_ex + nu_iz) {
-        /* Reading: the energy left after the ionisation threshold is shared
-           equally between the two electrons, each scattered isotropically;
-           the new ion is drawn from the 300 K gas Maxwellian. */
-        double e_share = 0.5 * (eps - p->iz_thr);
-        g_new = sqrt(2.0 * Q_E * e_share / M_E);
+        /* Reading: the excess eps - I is shared equally between the two
+           electrons (or, with ORC_IZ_OPAL, the secondary takes the
+           Opal-Pollock-Wagner share); each electron is scattered at the
+           energy it leaves with; the new ion is drawn from the 300 K gas
+           Maxwellian. */
         uint32_t w1[4], w2[4];
         draw(p, sp->id[i], s->step, 0, TAG_MCC, 1, w1);
         draw(p, sp->id[i], s->step, 0, TAG_MCC, 2, w2);
-        double ct = 1.0 - 2.0 * uniform24(w1[0]);
-        double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+        double excess = eps - p->iz_thr;
+        double e_sec = (p->coll_model & ORC_IZ_OPAL) ? orc_opal_secondary(excess, p->iz_split_b, uniform24(w2[2]))
+                                                     : 0.5 * excess;
+        double e_pri = (p->coll_model & ORC_IZ_OPAL) ? excess - e_sec : 0.5 * excess;
+        cos_chi = vs ? orc_vs_cos_chi(e_pri, uniform24(w[2])) : 1.0 - 2.0 * uniform24(w[2]);
+        g_new = sqrt(2.0 * Q_E * e_pri / M_E);
+        double g_sec = sqrt(2.0 * Q_E * e_sec / M_E);
         double ps = 2.0 * PI_D * uniform24(w1[1]);
+        double dc[3];
+        if (vs) {
+            /* the secondary turned from the incident direction by the law at its energy */
+            orc_rotate(d, orc_vs_cos_chi(e_sec, uniform24(w1[0])), ps, dc);
+        } else {
+            /* isotropic in the laboratory frame */
+            double ct = 1.0 - 2.0 * uniform24(w1[0]);
+            double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+            dc[0] = ct;
+            dc[1] = st * cos(ps);
+            dc[2] = st * sin(ps);
+        }
         double n1, n2, n3, n4;
         box_muller(uniform24(w1[2]), uniform24(w1[3]), &n1, &n2);
         box_muller(uniform24(w2[0]), uniform24(w2[1]), &n3, &n4);
@@ -897,9 +935,9 @@ static int collide_electron(orc_sim *s, int64_t i)
         birth_t *b = &s->births[s->n_births++];
         b->pid = sp->id[i];
         b->xi = sp->xi[i];
-        b->ve[0] = g_new * ct;
-        b->ve[1] = g_new * st * cos(ps);
-        b->ve[2] = g_new * st * sin(ps);
+        b->ve[0] = g_sec * dc[0];
+        b->ve[1] = g_sec * dc[1];
+        b->ve[2] = g_sec * dc[2];
         b->vi[0] = s->d.vth_gas * n1;
         b->vi[1] = s->d.vth_gas * n2;
         b->vi[2] = s->d.vth_gas * n3;
@@ -913,6 +951,8 @@ static int collide_electron(orc_sim *s, int64_t i)
         s->dg.coll[4] += 1;
         return 0;
     }
+    double dn[3];
+    orc_rotate(d, cos_chi, phi, dn);
     sp->vx[i] = g_new * dn[0];
     sp->vy[i] = g_new * dn[1];
     sp->vz[i] = g_new * dn[2];

@@ -54,7 +54,15 @@ typedef struct orc_params {
     double eps_cap;          /* eV: energy up to which the e- collision frequency bound holds */
     double cx_vmax;          /* V: ion energy up to which the CX bound holds */
     double eedf_max_ev;
+    /* collision model options (bits): ORC_IZ_OPAL shares the ionisation
+       excess by the Opal-Pollock-Wagner law of width iz_split_b [eV] (else
+       equally); ORC_SCATTER_VS scatters electrons by the Vahedi-Surendra
+       anisotropic law (else isotropically) */
+    int32_t coll_model;
+    int32_t reserved;
+    double iz_split_b;
 } orc_params;
+enum { ORC_IZ_OPAL = 1, ORC_SCATTER_VS = 2 };
 
 /* Philox4x32-10: key (2 words), counter (4 words) -> 4 words. */
 void orc_philox4x32_10(const uint32_t key[2], const uint32_t ctr[4], uint32_t out[4]);
@@ -114,6 +122,12 @@ double orc_gather_ec3(const orc_params *p, const double *e_cc, double xi);
 
 /* Isotropic scattering rotation used by the collision routines (exposed for tests). */
 void orc_rotate(const double d[3], double cos_chi, double phi, double out[3]);
+/* Vahedi & Surendra (1995) anisotropic electron scattering: cos chi for an
+   electron of energy eps [eV] from a uniform u in (0, 1). */
+double orc_vs_cos_chi(double eps, double u);
+/* Opal, Pollock & Wagner (1971): energy [eV] the secondary electron of an
+   ionisation takes out of the excess eps - I, from a uniform u in (0, 1). */
+double orc_opal_secondary(double excess, double b, double u);
 
 /* ---- whole simulation ---- */
 typedef struct orc_diag {

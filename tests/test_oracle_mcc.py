@@ -452,3 +452,95 @@ def test_eedf_counts_every_electron_in_its_bin():
     assert h.sum() == 5000
     ref = np.bincount(np.minimum(np.floor(eps).astype(int), 50), minlength=51)
     assert np.array_equal(h, ref)
+
+
+# ---------------------------------------------------------------- collision model options
+def _vs_law(eps):
+    """The Vahedi-Surendra law as a density in mu = cos chi: the screened
+    Coulomb differential cross section ~ 1 / (1 + eps sin^2(chi/2)) per solid
+    angle, sin^2(chi/2) = (1 - mu)/2; normalised by quadrature."""
+    from scipy import integrate
+    f = lambda mu: 1.0 / (1.0 + eps * (1.0 - mu) / 2.0)
+    z = integrate.quad(f, -1.0, 1.0)[0]
+    mom = lambda k: integrate.quad(lambda mu: mu ** k * f(mu), -1.0, 1.0)[0] / z
+    cdf = np.vectorize(lambda m: integrate.quad(f, -1.0, m)[0] / z)
+    return mom(1), mom(2), cdf
+
+
+@pytest.mark.parametrize("eps", [0.5, 5.0, 30.0, 120.0])
+def test_vahedi_surendra_angles_follow_their_cross_section(eps):
+    """Sampled cos chi against the law integrated from its differential cross
+    section (an independent route from the inverse-CDF formula): first and
+    second moments within 5 sigma, and a Kolmogorov-Smirnov test."""
+    u = np.random.default_rng(int(eps * 10)).uniform(0.0, 1.0, 40_000)
+    mu = oracle.vs_cos_chi(eps, u)
+    assert np.all(mu >= -1.0 - 1e-12) and np.all(mu <= 1.0 + 1e-12)
+    m1, m2, cdf = _vs_law(eps)
+    se = np.std(mu) / math.sqrt(len(mu))
+    assert abs(mu.mean() - m1) < 5 * se, (mu.mean(), m1)
+    assert abs((mu ** 2).mean() - m2) < 5 * np.std(mu ** 2) / math.sqrt(len(mu))
+    assert stats.kstest(mu[:4000], cdf).pvalue > 1e-4
+    # low energy tends to isotropy, high energy to forward scattering
+    assert (m1 > 0.3) == (eps > 5.0)
+
+
+@pytest.mark.parametrize("excess,b", [(5.0, 10.0), (44.2, 10.0), (200.0, 10.0)])
+def test_opal_secondary_energy_law(excess, b):
+    """Secondary energies of the Opal-Pollock-Wagner spectrum ~ 1/(1 + (e/B)^2)
+    on [0, excess/2]: the mean B ln(1 + x^2) / (2 arctan x), x = excess/(2B)
+    (closed form), and a Kolmogorov-Smirnov test against the CDF
+    arctan(e/B) / arctan(x)."""
+    u = np.random.default_rng(3).uniform(0.0, 1.0, 60_000)
+    es = oracle.opal_secondary(excess, b, u)
+    assert es.min() >= 0.0 and es.max() <= excess / 2 + 1e-12
+    x = excess / (2 * b)
+    mean = b * math.log(1 + x * x) / (2 * math.atan(x))
+    assert abs(es.mean() - mean) < 5 * es.std() / math.sqrt(len(es))
+    assert stats.kstest(es[:5000], lambda e: np.arctan(e / b) / math.atan(x)).pvalue > 1e-4
+
+
+def test_opal_split_conserves_the_excess_in_a_run():
+    """With the Opal split the primary and its secondary leave an ionisation
+    with energies that add up to eps - I, the secondary below (eps - I)/2."""
+    cs = workloads.CROSS_SECTIONS
+    n = 50_000
+    sim, c, v0, xi0 = _one_step_beam(60.0, n, 6, sig_el=0.0, sig_exc_max=0.0, dt=2e-9, iz_split="opal",
+                                     iz_split_b=10.0)
+    nb = sim.diag()["coll"][2]
+    assert nb > 1000 and sim.count("e") == n + nb
+    e = sim.get_species("e")
+    en = 0.5 * ME * (e["vx"] ** 2 + e["vy"] ** 2 + e["vz"] ** 2) / E
+    parent = e["id"] < n
+    changed = parent & (np.abs(en - 60.0) > 1e-6)
+    assert changed.sum() == nb
+    pid_sorted = np.sort(e["id"][changed])
+    e_par = dict(zip(e["id"][changed].tolist(), en[changed].tolist()))
+    e_chi = dict(zip(e["id"][~parent].tolist(), en[~parent].tolist()))
+    excess = 60.0 - cs["iz_thr"]
+    for rank, pid in enumerate(pid_sorted.tolist()):
+        assert abs(e_par[pid] + e_chi[n + rank] - excess) < 1e-9 * excess
+        assert e_chi[n + rank] <= excess / 2 + 1e-9
+    x = excess / 20.0
+    mean = 10.0 * math.log(1 + x * x) / (2 * math.atan(x))
+    sec = np.array(list(e_chi.values()))
+    assert abs(sec.mean() - mean) < 5 * sec.std() / math.sqrt(len(sec))
+
+
+def test_vahedi_surendra_elastic_deflection_in_a_run():
+    """Elastic scattering with the anisotropic law: the mean cosine between
+    incident and scattered directions of 30 eV electrons equals the law's mean
+    at 30 eV, and the energy kept is 1 - (2m/M)(1 - cos chi) per electron."""
+    sim, c, v0, _ = _one_step_beam(30.0, 100_000, 8, sig_exc_max=0.0, sig_iz_peak=0.0, ion_mass_amu=0.01,
+                                   dt=2e-9, scattering="vahedi_surendra")
+    s = sim.get_species("e")
+    o = np.argsort(s["id"])
+    v1 = np.stack([s[k][o] for k in ("vx", "vy", "vz")], 1)
+    moved = np.linalg.norm(v1 - v0, axis=1) > 1e-6 * speed(30.0)
+    assert moved.sum() == sim.diag()["coll"][0] > 5000
+    a, b = v0[moved], v1[moved]
+    cos_chi = np.sum(a * b, 1) / (np.linalg.norm(a, axis=1) * np.linalg.norm(b, axis=1))
+    m1, _, _ = _vs_law(30.0)
+    assert abs(cos_chi.mean() - m1) < 5 * cos_chi.std() / math.sqrt(len(cos_chi))
+    ratio = np.sum(b * b, 1) / np.sum(a * a, 1)
+    two_m_over_M = 2 * ME / (0.01 * AMU)
+    np.testing.assert_allclose(ratio, 1 - two_m_over_M * (1 - cos_chi), rtol=0, atol=1e-9)

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define PIC_ABI_VERSION 1
+#define PIC_ABI_VERSION 2
 
 /* Error codes. */
 #define PIC_OK 0
@@ -84,6 +84,19 @@ extern "C" {
 #define PIC_BC_ELECTRODES 0
 #define PIC_BC_PERIODIC 1
 
+/* Collision-model options (bits of pic_config.collision_model; 0 is the
+   equal ionisation split and isotropic scattering).  PIC_IZ_OPAL: the
+   secondary electron of an ionisation takes eps_s of the excess eps - I from
+   the Opal-Pollock-Wagner spectrum 1 / (1 + (eps_s / B)^2) on [0, (eps - I)/2]
+   (B = iz_split_b), the primary the rest.  PIC_SCATTER_VS: electrons scatter
+   by the Vahedi-Surendra anisotropic law cos chi = (2 + eps - 2 (1 + eps)^u)
+   / eps (eps in eV), at the incident energy for elastic scattering and at the
+   energy each electron leaves with after excitation or ionisation (the
+   secondary turned from the incident direction).  Sec. 3 takes its collision
+   model from its MCC reference; these are the published forms. */
+#define PIC_IZ_OPAL 1
+#define PIC_SCATTER_VS 2
+
 typedef struct pic_config {
     int32_t scheme;          /* PIC_EC_EXPLICIT / PIC_MC_EXPLICIT / PIC_EC_IMPLICIT / PIC_MC_IMPLICIT /
                                 PIC_EC3_EXPLICIT */
@@ -97,7 +110,7 @@ typedef struct pic_config {
     int32_t eedf_bins;       /* EEDF bins over [0, eedf_max_ev), plus one overflow bin */
     uint32_t seed;           /* Philox key word 0 */
     uint32_t run;            /* Philox key word 1 (run index in a batch) */
-    int32_t reserved0;
+    int32_t collision_model; /* PIC_IZ_OPAL | PIC_SCATTER_VS bits (0: equal split, isotropic) */
     int64_t np_init;         /* macro-particles per species placed by pic_init (uniform load) */
     int64_t capacity[2];     /* particle slots per species (electrons, ions) */
     int64_t births_capacity; /* ionisation events one step can record */
@@ -121,6 +134,7 @@ typedef struct pic_config {
     double eps_cap;          /* e- energy up to which the collision bound holds [eV] */
     double cx_vmax;          /* ion energy up to which the charge-exchange bound holds [V] */
     double eedf_max_ev;
+    double iz_split_b;       /* Opal-Pollock-Wagner width B [eV] (PIC_IZ_OPAL) */
 } pic_config;
 
 typedef struct pic_sizes {

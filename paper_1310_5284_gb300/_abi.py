@@ -19,6 +19,7 @@ ERRORS = {-1: "PIC_EINVAL", -2: "PIC_EUNSTABLE", -3: "PIC_ENOMEM", -4: "PIC_EOVE
 PIC_STATUS_CAPACITY, PIC_STATUS_BIRTHS, PIC_STATUS_TIMEOUT = 0x1, 0x2, 0x4
 SCHEMES = {"ec_explicit": 0, "mc_explicit": 1, "ec_implicit": 2, "mc_implicit": 3, "ec3_explicit": 4}
 BOUNDARY_ELECTRODES, BOUNDARY_PERIODIC = 0, 1
+IZ_OPAL, SCATTER_VS = 1, 2  # collision-model option bits
 
 
 class PicConfig(ctypes.Structure):
@@ -27,7 +28,7 @@ class PicConfig(ctypes.Structure):
         ("mcc", ctypes.c_int32), ("ions_mobile", ctypes.c_int32), ("strict", ctypes.c_int32),
         ("sort_period", ctypes.c_int32), ("diag_period", ctypes.c_int32),
         ("eedf_bins", ctypes.c_int32), ("seed", ctypes.c_uint32), ("run", ctypes.c_uint32),
-        ("reserved0", ctypes.c_int32), ("np_init", ctypes.c_int64),
+        ("collision_model", ctypes.c_int32), ("np_init", ctypes.c_int64),
         ("capacity", ctypes.c_int64 * 2), ("births_capacity", ctypes.c_int64),
         ("length", ctypes.c_double), ("dt", ctypes.c_double), ("rf_freq", ctypes.c_double),
         ("rf_volt", ctypes.c_double), ("n0", ctypes.c_double), ("bg_density", ctypes.c_double),
@@ -36,7 +37,7 @@ class PicConfig(ctypes.Structure):
         ("sig_el", ctypes.c_double), ("exc_thr", ctypes.c_double), ("exc_ramp_end", ctypes.c_double),
         ("sig_exc_max", ctypes.c_double), ("iz_thr", ctypes.c_double),
         ("sig_iz_peak", ctypes.c_double), ("sig_cx", ctypes.c_double), ("eps_cap", ctypes.c_double),
-        ("cx_vmax", ctypes.c_double), ("eedf_max_ev", ctypes.c_double),
+        ("cx_vmax", ctypes.c_double), ("eedf_max_ev", ctypes.c_double), ("iz_split_b", ctypes.c_double),
     ]
 
 

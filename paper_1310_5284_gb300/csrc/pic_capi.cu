@@ -122,6 +122,9 @@ int validate(const pic_config *c) {
     if (c->births_capacity < 0 || c->births_capacity > (1ll << 24))
         return fail(PIC_EINVAL, "births_capacity outside 0..2^24");
     if (c->eedf_bins < 1 || c->eedf_bins > 1024) return fail(PIC_EINVAL, "eedf_bins outside 1..1024");
+    if (c->collision_model & ~(PIC_IZ_OPAL | PIC_SCATTER_VS)) return fail(PIC_EINVAL, "unknown collision_model bits");
+    if ((c->collision_model & PIC_IZ_OPAL) && !(c->iz_split_b > 0.0))
+        return fail(PIC_EINVAL, "iz_split_b must be positive with PIC_IZ_OPAL");
     if (!(c->eedf_max_ev > 0)) return fail(PIC_EINVAL, "eedf_max_ev must be positive");
     if (!(c->ion_mass_amu > 0) || !(c->te_ev >= 0) || !(c->ti_ev >= 0))
         return fail(PIC_EINVAL, "bad species parameters");
@@ -292,6 +295,9 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
         R.nu_max_i = (float)nu_i;
         R.g_max_i = (float)g_max;
     }
+    R.iz_opal = (c.collision_model & PIC_IZ_OPAL) ? 1 : 0;
+    R.scatter_vs = (c.collision_model & PIC_SCATTER_VS) ? 1 : 0;
+    R.iz_b = (float)c.iz_split_b;
     R.sig_el = (float)c.sig_el;
     R.exc_thr = (float)c.exc_thr;
     R.exc_ramp_end = (float)c.exc_ramp_end;

@@ -157,6 +157,8 @@ struct Run {
     float sig_el, exc_thr, exc_ramp_end, exc_slope, sig_exc_max, iz_thr, sig_iz_k, sig_cx;
     float eps_cap, g_max_i, two_m_over_M, two_e_over_me, vth_gas;
     float abar_ion_over_e; // (q_i/m_i) / (q_e/m_e)
+    int iz_opal, scatter_vs; // collision-model options (PIC_IZ_OPAL, PIC_SCATTER_VS)
+    float iz_b;            // Opal-Pollock-Wagner width B [eV]
     float eedf_inv_width;
     // pointers into the arena
     Species buf[2][2];     // [parity][species]

@@ -190,6 +190,27 @@ struct Tally {
     unsigned int el, ex, iz, cx, nul, ovf;
 };
 
+// 1 - cos chi and 1 + cos chi of the Vahedi-Surendra law at energy eps [eV]
+// for the uniform x: cos chi = (2 + eps - 2 (1 + eps)^u) / eps, written as
+// 1 - cos chi = 2 expm1(u L) / eps and 1 + cos chi = -2 (1 + eps)
+// expm1(-(1 - u) L) / eps with L = log1p(eps), so neither end cancels.
+__device__ __forceinline__ void vs_angle(float eps, const U24 &x, float &dm, float &dp) {
+    if (!(eps > 1e-6f)) {  // the isotropic limit
+        dm = 2.0f * x.u;
+        dp = 2.0f * x.c;
+        return;
+    }
+    const float L = log1pf(eps), inv = 2.0f / eps;
+    dm = expm1f(x.u * L) * inv;
+    dp = -(1.0f + eps) * expm1f(-x.c * L) * inv;
+}
+
+// Opal-Pollock-Wagner: the secondary electron's share of an ionisation's
+// excess, B tan(u arctan(excess / 2B)).
+__device__ __forceinline__ float opal_secondary(float excess, float b, float u) {
+    return excess > 0.0f ? b * tanf(u * atanf(excess / (2.0f * b))) : 0.0f;
+}
+
 // Electron collision (null-collision MC): elastic, excitation or ionisation
 // chosen by u * nu_max against the running sum of n_g sigma_k(eps) v.
 // Kept out of line: only the few selected particles take this path.
@@ -206,10 +227,7 @@ __device__ __forceinline__ bool collide_electron_body(const Run &R, uint4 w, uin
     const float nu_el = R.sig_el * ngv;
     const float nu_ex = sigma_exc(R, eps) * ngv;
     const float nu_iz = sigma_iz(R, eps) * ngv;
-    // isotropic: cos chi = 1 - 2u = (1 - u) - u, sin chi = 2 sqrt(u (1 - u))
     const U24 uc = u24c(w.z);
-    const float cos_chi = uc.c - uc.u;
-    const float sin_chi = 2.0f * sqrtf(uc.u * uc.c);
     float sp, cp;
     sincos_2pi(u24c(w.w), sp, cp);
     float dx_ = 1.0f, dy = 0.0f, dz = 0.0f;
@@ -219,25 +237,43 @@ __device__ __forceinline__ bool collide_electron_body(const Run &R, uint4 w, uin
         dy = vy * inv;
         dz = vz * inv;
     }
-    float g_new;
+    // the angle: isotropic, cos chi = 1 - 2u = (1 - u) - u, sin chi =
+    // 2 sqrt(u (1 - u)); or the Vahedi-Surendra law at energy e_ang
+    float e_ang, g_new;
     if (r < nu_el) {
-        // elastic: the electron keeps 1 - (2m/M)(1 - cos chi) of its energy
-        g_new = g * sqrtf(1.0f - R.two_m_over_M * (2.0f * uc.u));
+        // elastic: the electron keeps 1 - (2m/M)(1 - cos chi) of its energy;
+        // the law is taken at the incident energy
+        e_ang = eps;
         t.el++;
     } else if (r < nu_el + nu_ex) {
-        g_new = sqrtf(R.two_e_over_me * (eps - R.exc_thr));
+        e_ang = eps - R.exc_thr;
+        g_new = sqrtf(R.two_e_over_me * e_ang);
         t.ex++;
     } else if (r < nu_el + nu_ex + nu_iz) {
-        // Reading: the energy above threshold is shared equally by the two
-        // electrons, each scattered isotropically; the ion comes from the gas.
-        g_new = sqrtf(R.two_e_over_me * 0.5f * (eps - R.iz_thr));
+        // Reading: the excess eps - I is shared equally by the two electrons
+        // (or the secondary takes the Opal-Pollock-Wagner share), each
+        // scattered at the energy it leaves with; the ion comes from the gas.
         const uint4 w1 = draw(R, id, step, 0, kTagMcc, 1);
         const uint4 w2 = draw(R, id, step, 0, kTagMcc, 2);
+        const float excess = eps - R.iz_thr;
+        const float e_sec = R.iz_opal ? opal_secondary(excess, R.iz_b, u24(w2.z)) : 0.5f * excess;
+        e_ang = R.iz_opal ? excess - e_sec : 0.5f * excess;
+        g_new = sqrtf(R.two_e_over_me * e_ang);
+        const float g_sec = sqrtf(R.two_e_over_me * e_sec);
         const U24 u1 = u24c(w1.x);
-        const float ct = u1.c - u1.u;
-        const float st = 2.0f * sqrtf(u1.u * u1.c);
         float sps, cps;
         sincos_2pi(u24c(w1.y), sps, cps);
+        float sx, sy, sz;
+        if (R.scatter_vs) {  // turned from the incident direction
+            float dm, dp;
+            vs_angle(e_sec, u1, dm, dp);
+            rotate(dx_, dy, dz, 0.5f * (dp - dm), sqrtf(dm * dp), sps, cps, sx, sy, sz);
+        } else {  // isotropic in the laboratory frame
+            const float st = 2.0f * sqrtf(u1.u * u1.c);
+            sx = u1.c - u1.u;
+            sy = st * cps;
+            sz = st * sps;
+        }
         float n1, n2, n3, n4;
         box_muller(u24c(w1.z), u24c(w1.w), n1, n2);
         box_muller(u24c(w2.x), u24c(w2.y), n3, n4);
@@ -248,9 +284,9 @@ __device__ __forceinline__ bool collide_electron_body(const Run &R, uint4 w, uin
             b.cell = cell;
             b.off = off;
             b.abar_e = abar;
-            b.ve[0] = g_new * ct;
-            b.ve[1] = g_new * st * cps;
-            b.ve[2] = g_new * st * sps;
+            b.ve[0] = g_sec * sx;
+            b.ve[1] = g_sec * sy;
+            b.ve[2] = g_sec * sz;
             b.vi[0] = R.vth_gas * n1;
             b.vi[1] = R.vth_gas * n2;
             b.vi[2] = R.vth_gas * n3;
@@ -260,6 +296,18 @@ __device__ __forceinline__ bool collide_electron_body(const Run &R, uint4 w, uin
     } else {
         t.nul++;
         return false;
+    }
+    float cos_chi, sin_chi;
+    if (R.scatter_vs) {
+        float dm, dp;
+        vs_angle(e_ang, uc, dm, dp);
+        cos_chi = 0.5f * (dp - dm);
+        sin_chi = sqrtf(dm * dp);
+        if (r < nu_el) g_new = g * sqrtf(1.0f - R.two_m_over_M * dm);
+    } else {
+        cos_chi = uc.c - uc.u;
+        sin_chi = 2.0f * sqrtf(uc.u * uc.c);
+        if (r < nu_el) g_new = g * sqrtf(1.0f - R.two_m_over_M * (2.0f * uc.u));
     }
     float ox, oy, oz;
     rotate(dx_, dy, dz, cos_chi, sin_chi, sp, cp, ox, oy, oz);

@@ -58,6 +58,9 @@ def make_config(cfg: dict) -> _abi.PicConfig:
     c.eps_cap = float(cfg.get("eps_cap", 100.0))
     c.cx_vmax = float(cfg.get("cx_vmax", 2.0 * c.rf_volt + 50.0))
     c.eedf_max_ev = float(cfg.get("eedf_max_ev", 50.0))
+    c.collision_model = (_abi.IZ_OPAL if cfg.get("iz_split", "equal") == "opal" else 0) | \
+        (_abi.SCATTER_VS if cfg.get("scattering", "isotropic") == "vahedi_surendra" else 0)
+    c.iz_split_b = float(cfg.get("iz_split_b", 10.0))
     return c
 
 

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(abi):
 
 
 def test_version_and_build_info(abi):
-    assert abi.lib().pic_version() == 1
+    assert abi.lib().pic_version() == 2
     assert b"sm_103a" in abi.lib().pic_build_info()
 
 

@@ -499,13 +499,24 @@ def test_implicit_susceptibility_and_modified_poisson_grid(name, over):
     one_step_diagnostics(gpu, cfg, eedf_tol=4)
 
 
-@pytest.mark.parametrize("scheme", ["ec_explicit", "ec_implicit", "mc_implicit", "ec3_explicit"])
-def test_collisions_counts_exact_and_births_ranked(scheme):
+COLLISION_CASES = [
+    ("ec_explicit", {}), ("ec_implicit", {}), ("mc_implicit", {}), ("ec3_explicit", {}),
+    # the collision-model options: Opal-Pollock-Wagner split, Vahedi-Surendra scattering
+    ("ec_explicit", dict(iz_split="opal")),
+    ("ec_explicit", dict(scattering="vahedi_surendra")),
+    ("ec_implicit", dict(iz_split="opal", scattering="vahedi_surendra", te_ev=10.0)),
+]
+
+
+@pytest.mark.parametrize("scheme,opts", COLLISION_CASES,
+                         ids=["%s%s" % (c[0], "".join("-" + str(v) for v in c[1].values())) for c in COLLISION_CASES])
+def test_collisions_counts_exact_and_births_ranked(scheme, opts):
     """Null-collision MCC on the same Philox stream: selection is an integer
     compare, so tallies and births agree exactly; children get the same ids
     (and, in the implicit schemes, the parent's abar)."""
     cfg = dict(workloads.CFG_SMALL_CCP, np_init=20_000, sort_period=4, te_ev=6.0, scheme=scheme,
                diag_period=1, eedf_bins=40)
+    cfg.update(opts)
     n = cfg["np_init"]
     gpu = gpu_sim(cfg)
     orc = oracle.Sim(cfg)

@@ -1205,13 +1205,16 @@ static int step_implicit(orc_sim *s, int diag_step)
             double e = inside ? gather(s, x) : 0.0;
             double a = qm * e;
             double v_new = vt + 0.5 * dt * a;
+            double abar_new = 0.5 * (sp->abar[i] + a);
             kx += 0.5 * (v_old * v_old + v_new * v_new);
-            double work = s->d.q[k] * s->d.weight * e * 0.5 * (v_old + v_new);
+            /* Reading: the step changes v by dt abar^n, so the work done on the
+               particle is m w abar^n vbar (the field (m/q) abar^n, not E^{n+1}) */
+            double work = s->d.m[k] * s->d.weight * abar_new * 0.5 * (v_old + v_new);
             pw += work;
             if (diag_step && inside) s->heat[k][(int64_t)floor(x)] += work / dx;
             sp->xi[i] = x + 0.5 * dt * dt * a / dx;
             sp->vx[i] = v_new;
-            sp->abar[i] = 0.5 * (sp->abar[i] + a);
+            sp->abar[i] = abar_new;
             boundary(s, k, i);
         }
         s->dg.ke_x[k] = 0.5 * s->d.m[k] * s->d.weight * kx;

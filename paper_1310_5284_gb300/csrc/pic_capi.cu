@@ -264,6 +264,7 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
         R.half_m_w[s] = 0.5 * m[s] * w;
         R.qm_dt[s] = (float)(q[s] / m[s] * c.dt);
         R.qm[s] = (float)(q[s] / m[s]);
+        R.mq[s] = (float)(m[s] / q[s]);
         R.qw[s] = (float)(q[s] * w);
         R.half_m_over_e[s] = (float)(0.5 * m[s] / kE);
     }

@@ -142,6 +142,7 @@ struct Run {
     // push (FP32)
     float qm_dt[2];        // (q/m) dt
     float qm[2];
+    float mq[2];           // m/q
     float dt_dx;           // dt / dx
     float half_dt;         // dt / 2
     float half_dt2_dx;     // dt^2 / (2 dx)

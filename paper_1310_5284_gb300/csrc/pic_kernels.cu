@@ -877,13 +877,14 @@ __device__ __forceinline__ void drain_q(const Run &R, const SmemMain &sm, Specie
 // particle code exists once for both species (two copies would double the
 // hot loop's instruction footprint).
 struct SpK {
-    float qm, qw, qm_dt;
-    uint32_t collides;  // the species' P_null > 0
+    float qm, qw, qm_dt, mq;  // q/m, q w, (q/m) dt, m/q
+    uint32_t collides;        // the species' P_null > 0
     int S;
 };
 
 __device__ __forceinline__ SpK species_k(const Run &R, int S) {
-    return S ? SpK{R.qm[1], R.qw[1], R.qm_dt[1], R.thr[1], 1} : SpK{R.qm[0], R.qw[0], R.qm_dt[0], R.thr[0], 0};
+    return S ? SpK{R.qm[1], R.qw[1], R.qm_dt[1], R.mq[1], R.thr[1], 1}
+             : SpK{R.qm[0], R.qw[0], R.qm_dt[0], R.mq[0], R.thr[0], 0};
 }
 
 // ---------------------------------------------------------------------------
@@ -926,9 +927,12 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         e_field = !inside ? 0.0f : (MI::mc ? (1.0f - s) * sm.e[c] + s * sm.e[c + 1] : gather_ec(sm.e, c, s));
         const float acc = k.qm * e_field;
         v_new = fmaf(R.half_dt, acc, vt);
-        if (diag && inside) atomicAdd(&sm.heat[c], k.qw * e_field * 0.5f * (v_old + v_new));
         s = fmaf(acc, R.half_dt2_dx, s);
         abar = 0.5f * (abar + acc);
+        // Reading: the step changes v by dt abar^n, so the work done on the
+        // particle is that of the field (m/q) abar^n, not of E^{n+1}
+        e_field = abar * k.mq;
+        if (diag && inside) atomicAdd(&sm.heat[c], k.qw * e_field * 0.5f * (v_old + v_new));
     } else {
         // explicit leapfrog with E^n at x^n (Sec. 2 schemes (1), (2))
         e_field = MI::mc ? (1.0f - off) * sm.e[c0] + off * sm.e[c0 + 1]

@@ -303,6 +303,10 @@ int pic_batch_step(pic_batch *b, int64_t n);
    pic_get_particles). */
 int pic_batch_diag(pic_batch *b, int32_t run, pic_diag_t *out, int reset_avg);
 int pic_batch_get_particles(pic_batch *b, int32_t run, int species, pic_host_particles *out);
+/* Time-averaged profiles of one run (synchronising; as pic_profiles: the
+   averages since the run's last reset through pic_batch_diag(..., 1)). */
+int pic_batch_profiles(pic_batch *b, int32_t run, double *ne, double *ni, double *phi, double *heat_e,
+                       double *heat_i, uint64_t *eedf);
 /* Work-item size (particles per item, 256..2^24) and sort period (0: never)
    of the batched launches.  Results do not depend on them. */
 int pic_batch_set_schedule(pic_batch *b, int64_t chunk, int32_t sort_period);

@@ -109,6 +109,7 @@ SIGNATURES = {
     "pic_batch_step": ([_vp, ctypes.c_int64], ctypes.c_int),
     "pic_batch_diag": ([_vp, ctypes.c_int32, _P(PicDiag), ctypes.c_int], ctypes.c_int),
     "pic_batch_get_particles": ([_vp, ctypes.c_int32, ctypes.c_int, _P(PicHostParticles)], ctypes.c_int),
+    "pic_batch_profiles": ([_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "pic_batch_set_schedule": ([_vp, ctypes.c_int64, ctypes.c_int32], ctypes.c_int),
     "pic_batch_autotune": ([_vp, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int32),
                             _P(ctypes.c_double)], ctypes.c_int),

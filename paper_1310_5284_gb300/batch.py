@@ -73,6 +73,19 @@ class BatchSim:
                 "ke_perp": list(d.ke_perp), "field_energy": d.field_energy,
                 "field_energy_push": d.field_energy_push, "status": d.status}
 
+    def profiles(self, run: int) -> dict:
+        """Time-averaged profiles of one run since its last reset (as Sim.profiles)."""
+        c = self.cfgs[run]
+        n = int(c["n_cells"])
+        out = {k: np.zeros(n + 1) for k in ("ne", "ni", "phi")}
+        out["heat_e"] = np.zeros(n)
+        out["heat_i"] = np.zeros(n)
+        out["eedf"] = np.zeros(int(c.get("eedf_bins", 100)) + 1, dtype=np.uint64)
+        _abi.check(_abi.lib().pic_batch_profiles(
+            self._h, int(run), out["ne"].ctypes.data, out["ni"].ctypes.data, out["phi"].ctypes.data,
+            out["heat_e"].ctypes.data, out["heat_i"].ctypes.data, out["eedf"].ctypes.data))
+        return out
+
     def get_particles(self, run: int, species) -> dict:
         k = SPECIES[species]
         n = self.diag(run)["count"][k]

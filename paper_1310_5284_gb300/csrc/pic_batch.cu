@@ -260,6 +260,12 @@ int pic_batch_get_particles(pic_batch *b, int32_t run, int species, pic_host_par
     return run_get_particles(b->runs[run], b->stream, species, out, &b->err);
 }
 
+int pic_batch_profiles(pic_batch *b, int32_t run, double *ne, double *ni, double *phi, double *heat_e,
+                       double *heat_i, uint64_t *eedf) {
+    if (!b || run < 0 || run >= b->nruns) return fail_b(b, PIC_EINVAL, "bad argument");
+    return run_profiles(b->runs[run], b->cfgs[run], b->stream, ne, ni, phi, heat_e, heat_i, eedf, &b->err);
+}
+
 int pic_batch_set_schedule(pic_batch *b, int64_t chunk, int32_t sort_period) {
     if (!b || chunk < 256 || chunk > (1ll << 24) || sort_period < 0)
         return fail_b(b, PIC_EINVAL, "chunk outside 256..2^24 or negative sort period");

@@ -480,6 +480,43 @@ int init_run_state(const pic_config &c, const Run &R, unsigned char *arena, size
     return PIC_OK;
 }
 
+int run_profiles(const Run &R, const pic_config &c, cudaStream_t s, double *ne, double *ni, double *phi,
+                 double *heat_e, double *heat_i, uint64_t *eedf, std::string *err) {
+    CKE(launch_finalize(R, s));
+    CKE(cudaStreamSynchronize(s));
+    DevState st;
+    CKE(cudaMemcpy(&st, R.st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    const size_t n1 = (size_t)c.n_cells + 1, n = (size_t)c.n_cells;
+    const double na = st.n_avg > 0 ? (double)st.n_avg : 1.0;
+    const double nd = st.n_diag > 0 ? (double)st.n_diag : 1.0;
+    auto fetch = [&](double *dst, const double *src, size_t cnt, double scale) -> cudaError_t {
+        if (!dst) return cudaSuccess;
+        const cudaError_t e = cudaMemcpy(dst, src, 8 * cnt, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            for (size_t k = 0; k < cnt; ++k) dst[k] *= scale;
+        return e;
+    };
+    CKE(fetch(ne, R.avg_ne, n1, R.dens_scale / na));
+    CKE(fetch(ni, R.avg_ni, n1, R.dens_scale / na));
+    CKE(fetch(heat_e, R.heat[0], n, 1.0 / nd));
+    CKE(fetch(heat_i, R.heat[1], n, 1.0 / nd));
+    if (phi) {
+        // the averaged potential follows linearly from the averaged field and
+        // electrode voltage: phi_g = <V> - dx sum_{c<g} <E_c>
+        std::vector<double> e(n);
+        CKE(fetch(e.data(), R.avg_e, n, 1.0 / na));
+        const bool periodic = c.boundary == PIC_BC_PERIODIC;
+        double acc = periodic ? 0.0 : st.v_sum / na;
+        for (size_t g = 0; g < n; ++g) {
+            phi[g] = acc;
+            acc -= R.dx * e[g];
+        }
+        phi[n] = periodic ? phi[0] : 0.0;
+    }
+    if (eedf) CKE(cudaMemcpy(eedf, R.eedf, 8 * ((size_t)c.eedf_bins + 1), cudaMemcpyDeviceToHost));
+    return PIC_OK;
+}
+
 int run_get_particles(const Run &R, cudaStream_t s, int species, pic_host_particles *out, std::string *err) {
     CKE(cudaStreamSynchronize(s));
     DevState st;
@@ -648,38 +685,7 @@ int pic_diag(pic_handle *h, pic_diag_t *out, int reset_avg) {
 int pic_profiles(pic_handle *h, double *ne, double *ni, double *phi, double *heat_e,
                  double *heat_i, uint64_t *eedf) {
     if (!h) return fail(PIC_EINVAL, "handle is NULL");
-    CK(h, launch_finalize(h->run, h->stream));
-    DevState st;
-    int r = read_state(h, &st);
-    if (r) return r;
-    const size_t n1 = (size_t)h->cfg.n_cells + 1, n = (size_t)h->cfg.n_cells;
-    const double na = st.n_avg > 0 ? (double)st.n_avg : 1.0;
-    const double nd = st.n_diag > 0 ? (double)st.n_diag : 1.0;
-    auto fetch = [&](double *dst, double *src, size_t cnt, double scale) -> int {
-        if (!dst) return PIC_OK;
-        CK(h, cudaMemcpy(dst, src, 8 * cnt, cudaMemcpyDeviceToHost));
-        for (size_t k = 0; k < cnt; ++k) dst[k] *= scale;
-        return PIC_OK;
-    };
-    if ((r = fetch(ne, h->run.avg_ne, n1, h->run.dens_scale / na))) return r;
-    if ((r = fetch(ni, h->run.avg_ni, n1, h->run.dens_scale / na))) return r;
-    if ((r = fetch(heat_e, h->run.heat[0], n, 1.0 / nd))) return r;
-    if ((r = fetch(heat_i, h->run.heat[1], n, 1.0 / nd))) return r;
-    if (phi) {
-        // the averaged potential follows linearly from the averaged field and
-        // electrode voltage: phi_g = <V> - dx sum_{c<g} <E_c>
-        std::vector<double> e(n);
-        if ((r = fetch(e.data(), h->run.avg_e, n, 1.0 / na))) return r;
-        const bool periodic = h->cfg.boundary == PIC_BC_PERIODIC;
-        double acc = periodic ? 0.0 : st.v_sum / na;
-        for (size_t g = 0; g < n; ++g) {
-            phi[g] = acc;
-            acc -= h->run.dx * e[g];
-        }
-        phi[n] = periodic ? phi[0] : 0.0;
-    }
-    if (eedf) CK(h, cudaMemcpy(eedf, h->run.eedf, 8 * ((size_t)h->cfg.eedf_bins + 1), cudaMemcpyDeviceToHost));
-    return PIC_OK;
+    return run_profiles(h->run, h->cfg, h->stream, ne, ni, phi, heat_e, heat_i, eedf, &h->err);
 }
 
 int pic_grids(pic_handle *h, int64_t *rho_q_e, int64_t *rho_q_i, double *phi, double *e_cc,

@@ -231,6 +231,9 @@ Mode deposit_mode_of(const pic_config &c);
 int run_diag(const Run &R, const pic_config &c, const Layout &L, unsigned char *arena, cudaStream_t s,
              pic_diag_t *out, int reset_avg, std::string *err);
 int run_get_particles(const Run &R, cudaStream_t s, int species, pic_host_particles *out, std::string *err);
+// time-averaged profiles of one run (as pic_profiles)
+int run_profiles(const Run &R, const pic_config &c, cudaStream_t s, double *ne, double *ni, double *phi,
+                 double *heat_e, double *heat_i, uint64_t *eedf, std::string *err);
 // zero a run's arena, load its particles, assign charge, solve, sort
 int init_run_state(const pic_config &c, const Run &R, unsigned char *arena, size_t arena_bytes, int grid,
                    cudaStream_t s, std::string *err);

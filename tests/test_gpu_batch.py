@@ -80,3 +80,32 @@ def test_batch_autotune_keeps_results():
             for key in ("id", "cell", "off", "vx", "vy", "vz"):
                 assert np.array_equal(a[key], b[key]), (r, sp, key)
         single.close()
+
+
+def test_batch_profiles_equal_the_single_run_profiles():
+    """pic_batch_profiles: the time-averaged densities, potential, heating
+    profiles and EEDF of each batched run, after a reset and 30 steps with
+    diagnostics every 3 steps, equal those of the same run alone (the runs are
+    bit-identical; the FP64 averages are summed in the same order)."""
+    from paper_1310_5284_gb300.batch import BatchSim
+    from paper_1310_5284_gb300.sim import Sim
+
+    cfgs = [dict(c, diag_period=3, eedf_bins=32) for c in batch_cases()[:5]]
+    batch = BatchSim(cfgs)
+    batch.step(9)
+    for r in range(len(cfgs)):
+        batch.diag(r, reset_avg=True)
+    batch.step(30)
+    for r, cfg in enumerate(cfgs):
+        single = Sim(cfg)
+        single.step(9)
+        single.diag(reset_avg=True)
+        single.step(30)
+        pb, ps = batch.profiles(r), single.profiles()
+        for key in ("ne", "ni", "phi", "eedf"):
+            assert np.array_equal(pb[key], ps[key]), (r, key)
+        for key in ("heat_e", "heat_i"):  # per-block FP32 heating sums: order of blocks may differ
+            np.testing.assert_allclose(pb[key], ps[key], rtol=1e-5, atol=1e-6 * max(np.abs(ps[key]).max(), 1e-30))
+        assert pb["ne"].sum() > 0
+        single.close()
+    batch.close()

@@ -53,7 +53,7 @@ CASES = [
     ("ccp_512cells_2048000ppsp", "ec_explicit", 5),
     ("ccp_512cells_2048000ppsp", "ec3_explicit", 5),
     # the direct-implicit workload (128 cells, 1,024,000 per species,
-    # omega_p dt = 5, predictor and corrector launches)
+    # omega_p dt = 2, predictor and corrector launches)
     ("ccp_128cells_implicit", "ec_implicit", 3),
 ]
 

@@ -202,6 +202,18 @@ def _oracle_of(cfg, st, step, implicit, extra=4096):
     return orc
 
 
+def _rel(a, b):
+    """Largest relative difference of a against b (elementwise)."""
+    a, b = np.atleast_1d(np.asarray(a, dtype=np.float64)), np.atleast_1d(np.asarray(b, dtype=np.float64))
+    return float((np.abs(a - b) / np.maximum(np.abs(b), 1e-300)).max()) if a.size else 0.0
+
+
+def _of_scale(a, b):
+    """Largest difference of a against b relative to max |b|."""
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)) if a.size else 0.0
+
+
 def one_step_diagnostics(gpu, cfg, eedf_tol=None):
     """Every diagnostic of the GPU's next step against one oracle step taken
     from the GPU's own state (FP32 storage read exactly into FP64), so the
@@ -227,7 +239,9 @@ def one_step_diagnostics(gpu, cfg, eedf_tol=None):
       summed node-charge change below 1e-5 of the total (about 60x the
       expected 1.2e-6), chi within 1e-5 relative, and the field change within
       the charge change times e w / eps0 (Gauss's law) plus 1e-9 of scale;
-    * the EEDF within a few particles that FP32 and FP64 bin differently."""
+    * the EEDF within a few particles that FP32 and FP64 bin differently.
+    The measured error of every diagnostic is printed (one line, prefix
+    "diagnostic errors") and returned as the third value."""
     d0 = gpu.diag()
     scheme = cfg.get("scheme", "ec_explicit")
     implicit = scheme in ("ec_implicit", "mc_implicit")
@@ -257,6 +271,10 @@ def one_step_diagnostics(gpu, cfg, eedf_tol=None):
     we_g = np.array(dg["wall_energy_ev"]) - w0[1]
     we_o = np.array(do["wall_energy_ev"]) - np.array(do0["wall_energy_ev"])
     np.testing.assert_allclose(we_g, we_o, rtol=1e-5, atol=1e-9)
+    errs = {"wall_energy": _rel(we_g, we_o)}
+    for k, sp in enumerate(("e", "i")):
+        errs["ke_x_" + sp] = _rel(dg["ke_x"][k], do["ke_x"][k])
+        errs["ke_perp_" + sp] = _rel(dg["ke_perp"][k], do["ke_perp"][k])
     for k in range(2):
         assert dg["ke_x"][k] == pytest.approx(do["ke_x"][k], rel=1e-5, abs=1e-30)
         assert dg["ke_perp"][k] == pytest.approx(do["ke_perp"][k], rel=1e-5, abs=1e-30)
@@ -265,6 +283,7 @@ def one_step_diagnostics(gpu, cfg, eedf_tol=None):
     for k, sp in enumerate(("e", "i")):
         scale = abs(der["q"][k]) * der["weight"] * emax * float(np.abs(st[k]["vx"].astype(np.float64)).sum())
         assert abs(dg["power"][k] - do["power"][k]) <= 1e-5 * scale + 1e-30, (sp, dg["power"][k], do["power"][k])
+        errs["power_" + sp + "_of_scale"] = abs(dg["power"][k] - do["power"][k]) / max(scale, 1e-300)
     g1, pg = gpu.grids(), gpu.profiles()
     if not implicit:
         assert dg["field_energy_push"] == pytest.approx(do["field_energy_push"], rel=1e-9, abs=1e-30)
@@ -276,6 +295,11 @@ def one_step_diagnostics(gpu, cfg, eedf_tol=None):
         np.testing.assert_allclose(g1["e_cc"], o1["e_cc"], rtol=0, atol=e_tol)
         np.testing.assert_allclose(g1["phi"], o1["phi"], rtol=0, atol=1e-9 * max(np.abs(o1["phi"]).max(), 1e-300))
         assert dg["field_energy"] == pytest.approx(o2.diag()["field_energy"], rel=1e-8, abs=1e-30)
+        errs["field_energy_push"] = _rel(dg["field_energy_push"], do["field_energy_push"])
+        errs["field_energy"] = _rel(dg["field_energy"], o2.diag()["field_energy"])
+        errs["e_cc_of_scale"] = _of_scale(g1["e_cc"], o1["e_cc"])
+        errs["phi_of_scale"] = _of_scale(g1["phi"], o1["phi"])
+        errs["phi_avg_of_scale"] = _of_scale(pg["phi"], o1["phi"])
         # one step's averages: the potential and densities of the new field
         np.testing.assert_allclose(pg["phi"], o1["phi"], rtol=0, atol=1e-9 * max(np.abs(o1["phi"]).max(), 1e-300))
         pn = o2.averages()  # nothing averaged yet: compare against the charge itself
@@ -283,6 +307,7 @@ def one_step_diagnostics(gpu, cfg, eedf_tol=None):
         for key, q in (("ne", o1["rho_q_e"]), ("ni", o1["rho_q_i"])):
             ref = q.astype(np.float64) * unit
             np.testing.assert_allclose(pg[key], ref, rtol=1e-12, atol=1e-12 * max(np.abs(ref).max(), 1e-300))
+            errs[key + "_of_scale"] = _of_scale(pg[key], ref)
     else:
         o1 = orc.grids()
         unit = oracle.charge_unit(cfg)
@@ -290,6 +315,7 @@ def one_step_diagnostics(gpu, cfg, eedf_tol=None):
         for k, key in enumerate(("rho_q_e", "rho_q_i")):
             moved = np.abs(g1[key] - o1[key]).sum()
             assert moved <= 1e-5 * max(n_tot[k], 1) * unit, (key, moved / (max(n_tot[k], 1) * unit))
+            errs[key + "_moved_of_total"] = float(moved / (max(n_tot[k], 1) * unit))
         moved_q = np.abs((g1["rho_q_i"] - g1["rho_q_e"]) - (o1["rho_q_i"] - o1["rho_q_e"])).sum()
         de = 2.0 * 1.602176634e-19 * der["weight"] / 8.8541878128e-12 * moved_q / unit
         e_tol = de + 1e-9 * max(np.abs(o1["e_cc"]).max(), 1e-300)
@@ -297,19 +323,27 @@ def one_step_diagnostics(gpu, cfg, eedf_tol=None):
         np.testing.assert_allclose(g1["phi"], o1["phi"], rtol=0,
                                    atol=cfg["length"] * e_tol + 1e-9 * max(np.abs(o1["phi"]).max(), 1e-300))
         np.testing.assert_allclose(g1["chi"], o1["chi"], rtol=1e-5, atol=0)
+        errs["chi"] = _rel(g1["chi"], o1["chi"])
+        errs["e_cc_of_scale"] = _of_scale(g1["e_cc"], o1["e_cc"])
+        errs["phi_of_scale"] = _of_scale(g1["phi"], o1["phi"])
         assert np.abs(o1["chi"]).max() > 0
         w_tol = 8.8541878128e-12 * der["dx"] * (np.abs(o1["e_cc"]).sum() * e_tol + 0.5 * len(o1["e_cc"]) * e_tol ** 2)
         assert abs(dg["field_energy"] - do["field_energy"]) <= w_tol + 1e-9 * abs(do["field_energy"])
+        errs["field_energy"] = _rel(dg["field_energy"], do["field_energy"])
     diag_step = cfg.get("diag_period", 0) > 0 and d0["step"] % cfg["diag_period"] == 0
     if diag_step:
         po = orc.averages()
         for k, key in enumerate(("heat_e", "heat_i")):
             scale = abs(der["q"][k]) * der["weight"] * emax * float(np.abs(st[k]["vx"].astype(np.float64)).sum())
             assert np.abs(pg[key] - po[key]).sum() * der["dx"] <= 1e-5 * scale + 1e-30, key
+            errs[key + "_of_scale"] = float(np.abs(pg[key] - po[key]).sum() * der["dx"] / max(scale, 1e-300))
         if cfg.get("eedf_bins", 0) > 0:
             diff = np.abs(pg["eedf"].astype(np.int64) - po["eedf"].astype(np.int64)).sum()
             assert diff <= (eedf_tol if eedf_tol is not None else 4), diff
-    return dg, do
+            errs["eedf_particles_binned_apart"] = int(diff)
+    print("diagnostic errors (%s, step %d):" % (scheme, d0["step"]),
+          {k: (v if isinstance(v, int) else float("%.3g" % v)) for k, v in errs.items()})
+    return dg, do, errs
 
 
 # ------------------------------------------------------------------ Philox

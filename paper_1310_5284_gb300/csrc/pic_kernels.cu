@@ -445,48 +445,6 @@ __device__ __forceinline__ void acc_add(const Acc &acc, int key, uint32_t c, uin
     }
 }
 
-// Warp aggregation of per-lane partial sums that share a key (key < 0: none):
-// redux.sync sums each group, one lane per group updates shared memory.
-// Every lane of the warp must call this.
-__device__ __forceinline__ void warp_agg(int key, uint32_t c, uint32_t a, uint32_t bh, uint32_t bl,
-                                         const Acc &acc, bool count_only) {
-    const int lane = threadIdx.x & 31;
-    const int k0 = __shfl_sync(FULL_MASK, key, 0);
-    if (__all_sync(FULL_MASK, key == k0) && k0 >= 0) {  // common case: one key for the warp
-        const uint32_t sc = __reduce_add_sync(FULL_MASK, c);
-        uint32_t sa = 0, sh = 0, sl = 0;
-        if (!count_only) {
-            sa = __reduce_add_sync(FULL_MASK, a);
-            sh = __reduce_add_sync(FULL_MASK, bh);
-            sl = __reduce_add_sync(FULL_MASK, bl);
-        }
-        if (lane == 0) acc_add(acc, k0, sc, sa, sh, sl, count_only);
-        return;
-    }
-    unsigned int pending = __ballot_sync(FULL_MASK, key >= 0);
-    int iter = 0;
-    while (pending) {
-        if (iter == 4) {  // widely spread warp: the rest add lane by lane
-            if ((pending >> lane) & 1u) acc_add(acc, key, c, a, bh, bl, count_only);
-            break;
-        }
-        const int leader = __ffs(pending) - 1;
-        const int lk = __shfl_sync(FULL_MASK, key, leader);
-        const bool mine = ((pending >> lane) & 1u) && key == lk;
-        const unsigned int grp = __ballot_sync(FULL_MASK, mine);
-        const uint32_t sc = __reduce_add_sync(FULL_MASK, mine ? c : 0u);
-        uint32_t sa = 0, sh = 0, sl = 0;
-        if (!count_only) {
-            sa = __reduce_add_sync(FULL_MASK, mine ? a : 0u);
-            sh = __reduce_add_sync(FULL_MASK, mine ? bh : 0u);
-            sl = __reduce_add_sync(FULL_MASK, mine ? bl : 0u);
-        }
-        if (lane == leader) acc_add(acc, lk, sc, sa, sh, sl, count_only);
-        pending &= ~grp;
-        ++iter;
-    }
-}
-
 // m = 3: the warp aggregation of (count, F, F^2, F^3) with F^3 in its three
 // 12-bit pieces.  Per warp slot (at most 32 x kUnroll = 128 particles,
 // F < 2^12): sum F^2 < 2^31 and each piece sum < 2^19, so every reduction is
@@ -564,37 +522,69 @@ __device__ __forceinline__ void deposit_tile3(const int (&key)[kUnroll], const u
     warp_agg3(c1 ? kmin + 1 : -1, c1, a1, q1, h1, m1, l1, acc);
 }
 
-// The kUnroll particles of a thread usually share one or two adjacent keys
-// (particles are kept sorted by key): fold them into two register slots,
-// then aggregate each slot across the warp.
+// Deposit of a warp's tile share (32 x kUnroll particles).  Kept sorted by
+// key between sorts, a warp's particles span a narrow window of keys: the
+// ions one or two, the electrons (which cross about a tenth of a cell a
+// step) a few more.  The warp finds its window [K0, K1] with two
+// reductions, sums each key of the window across the warp (count and sum of
+// a packed in one word, the halves of a^2 in two), and lane d adds key
+// K0 + d: one set of shared atomics per warp, on consecutive words.  A
+// warp spread wider than kDepWindow keys adds particle by particle.
+constexpr int kDepWindow = 4;
+
 __device__ __forceinline__ void deposit_tile(const int (&key)[kUnroll], const uint32_t (&a)[kUnroll],
                                              const Acc &acc, bool count_only) {
-    int kmin = 0x7fffffff;
+    const int lane = threadIdx.x & 31;
+    int lo = 0x7fffffff, hi = -1;
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u)
-        if (key[u] >= 0 && key[u] < kmin) kmin = key[u];
-    uint32_t c0 = 0, a0 = 0, h0 = 0, l0 = 0, c1 = 0, a1 = 0, h1 = 0, l1 = 0;
+        if (key[u] >= 0) {
+            lo = min(lo, key[u]);
+            hi = max(hi, key[u]);
+        }
+    const int K1 = __reduce_max_sync(FULL_MASK, hi);
+    if (K1 < 0) return;  // no particle in the warp
+    const int K0 = __reduce_min_sync(FULL_MASK, lo);
+    const int D = K1 - K0 + 1;
+    if (D > kDepWindow) {
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-        const int k = key[u];
-        if (k < 0) continue;
-        const uint32_t aa = a[u], q = aa * aa;
-        if (k == kmin) {
-            c0 += 1u;
-            a0 += aa;
-            h0 += q >> 16;
-            l0 += q & 0xffffu;
-        } else if (k == kmin + 1) {
-            c1 += 1u;
-            a1 += aa;
-            h1 += q >> 16;
-            l1 += q & 0xffffu;
-        } else {
-            acc_add(acc, k, 1u, aa, q >> 16, q & 0xffffu, count_only);
+        for (int u = 0; u < kUnroll; ++u)
+            if (key[u] >= 0) {
+                const uint32_t q = a[u] * a[u];
+                acc_add(acc, key[u], 1u, a[u], q >> 16, q & 0xffffu, count_only);
+            }
+        return;
+    }
+    // per lane: count <= kUnroll and a < 2^16, so over the warp the count
+    // stays below 2^8 and the sum of a below 2^23: (sum a) << 8 | count is
+    // exact in 32 bits; each half of a^2 sums below 2^23
+    uint32_t m_ca = 0u, m_h = 0u, m_l = 0u;
+#pragma unroll
+    for (int d = 0; d < kDepWindow; ++d) {
+        if (d >= D) break;  // the same in every lane
+        uint32_t ca = 0u, h = 0u, l = 0u;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (key[u] == K0 + d) {
+                ca += (a[u] << 8) | 1u;
+                if (!count_only) {
+                    const uint32_t q = a[u] * a[u];
+                    h += q >> 16;
+                    l += q & 0xffffu;
+                }
+            }
+        ca = __reduce_add_sync(FULL_MASK, ca);
+        if (!count_only) {
+            h = __reduce_add_sync(FULL_MASK, h);
+            l = __reduce_add_sync(FULL_MASK, l);
+        }
+        if (lane == d) {
+            m_ca = ca;
+            m_h = h;
+            m_l = l;
         }
     }
-    warp_agg(kmin == 0x7fffffff ? -1 : kmin, c0, a0, h0, l0, acc, count_only);
-    warp_agg(c1 ? kmin + 1 : -1, c1, a1, h1, l1, acc, count_only);
+    if (lane < D && (m_ca & 0xffu)) acc_add(acc, K0 + lane, m_ca & 0xffu, m_ca >> 8, m_h, m_l, count_only);
 }
 
 // ---------------------------------------------------------------------------
@@ -1157,23 +1147,31 @@ __device__ __forceinline__ void ring_particles(const Ring &g, int stage, int s0,
                                                float (&abar)[kUnroll]) {
     using MI = ModeInfo<MODE>;
     uint32_t w[kUnroll];
-    ring_words(g, stage, 0, s0, w);
-#pragma unroll
-    for (int q = 0; q < kUnroll; ++q) cell[q] = q < n_ok ? (int)w[q] : -1;
-    ring_words(g, stage, 1, s0, w);
-#pragma unroll
-    for (int q = 0; q < kUnroll; ++q) off[q] = q < n_ok ? __uint_as_float(w[q]) : 0.0f;
 #pragma unroll
     for (int q = 0; q < kUnroll; ++q) vx[q] = abar[q] = 0.0f;
+    ring_words(g, stage, 0, s0, w);
+#pragma unroll
+    for (int q = 0; q < kUnroll; ++q) cell[q] = (int)w[q];
+    ring_words(g, stage, 1, s0, w);
+#pragma unroll
+    for (int q = 0; q < kUnroll; ++q) off[q] = __uint_as_float(w[q]);
     if (MI::loads_v) {
         ring_words(g, stage, 2, s0, w);
 #pragma unroll
-        for (int q = 0; q < kUnroll; ++q) vx[q] = q < n_ok ? __uint_as_float(w[q]) : 0.0f;
+        for (int q = 0; q < kUnroll; ++q) vx[q] = __uint_as_float(w[q]);
     }
     if (MI::implicit) {
         ring_words(g, stage, 3, s0, w);
 #pragma unroll
-        for (int q = 0; q < kUnroll; ++q) abar[q] = q < n_ok ? __uint_as_float(w[q]) : 0.0f;
+        for (int q = 0; q < kUnroll; ++q) abar[q] = __uint_as_float(w[q]);
+    }
+    if (n_ok < kUnroll) {  // the tile's ragged end: the words beyond it are stale
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q)
+            if (q >= n_ok) {
+                cell[q] = -1;
+                off[q] = vx[q] = abar[q] = 0.0f;
+            }
     }
 }
 

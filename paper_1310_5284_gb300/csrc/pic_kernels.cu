@@ -187,7 +187,7 @@ __device__ __forceinline__ float sigma_iz(const Run &R, float eps) {
 // Per-thread counters of one species segment.
 struct Tally {
     float kx, pw;
-    unsigned int el, ex, iz, cx, nul, ovf;
+    unsigned int el, ex, iz, cx, nul, ovf_e, ovf_i;  // collisions of both species; overflow per species
 };
 
 // 1 - cos chi and 1 + cos chi of the Vahedi-Surendra law at energy eps [eV]
@@ -221,7 +221,7 @@ __device__ __forceinline__ bool collide_electron_body(const Run &R, uint4 w, uin
     const float v2 = vx * vx + vy * vy + vz * vz;
     const float g = sqrtf(v2);
     const float eps = R.half_m_over_e[0] * v2;
-    if (eps > R.eps_cap) t.ovf++;
+    if (eps > R.eps_cap) t.ovf_e++;
     const float r = u24(w.y) * R.nu_max_e;
     const float ngv = R.n_g * g;
     const float nu_el = R.sig_el * ngv;
@@ -253,6 +253,9 @@ __device__ __forceinline__ bool collide_electron_body(const Run &R, uint4 w, uin
         // Reading: the excess eps - I is shared equally by the two electrons
         // (or the secondary takes the Opal-Pollock-Wagner share), each
         // scattered at the energy it leaves with; the ion comes from the gas.
+        // The births slot is taken first: the atomic's round trip overlaps
+        // the draws and the kinematics below.
+        const unsigned int slot = atomicAdd(&R.st->n_births, 1u);
         const uint4 w1 = draw(R, id, step, 0, kTagMcc, 1);
         const uint4 w2 = draw(R, id, step, 0, kTagMcc, 2);
         const float excess = eps - R.iz_thr;
@@ -277,7 +280,6 @@ __device__ __forceinline__ bool collide_electron_body(const Run &R, uint4 w, uin
         float n1, n2, n3, n4;
         box_muller(u24c(w1.z), u24c(w1.w), n1, n2);
         box_muller(u24c(w2.x), u24c(w2.y), n3, n4);
-        const unsigned int slot = atomicAdd(&R.st->n_births, 1u);
         if (slot < (unsigned int)R.births_cap) {
             Birth b;
             b.pid = id;
@@ -327,7 +329,7 @@ __device__ __forceinline__ bool collide_ion_body(const Run &R, uint4 w, uint32_t
     const float vnx = R.vth_gas * n1, vny = R.vth_gas * n2, vnz = R.vth_gas * n3;
     const float ux = vx - vnx, uy = vy - vny, uz = vz - vnz;
     const float g = sqrtf(ux * ux + uy * uy + uz * uz);
-    if (g > R.g_max_i) t.ovf++;
+    if (g > R.g_max_i) t.ovf_i++;
     const float r = u24(w.y) * R.nu_max_i;
     if (r < R.n_g * R.sig_cx * g) {
         vx = vnx;
@@ -674,19 +676,22 @@ __device__ void block_sum2(double &x, double &y, double *scratch /*[2*kThreads/3
 // Shared-memory layout of the particle kernels.
 // ---------------------------------------------------------------------------
 // Deferred collisions: particles whose wait ran out in the push wait here
-// (their slot; kQueueRedraw marks a count that only ends in a fresh draw of
-// the wait) and are collided later by full warps, which read their ids and
-// draw their Philox words and next waits.  The queue is drained before a tile
-// whenever fewer than a tile's worth of entries are free, so it cannot
-// overflow.
+// (their slot and species; kQueueRedraw marks a count that only ends in a
+// fresh draw of the wait) and are collided later by full warps, which read
+// their ids and draw their Philox words and next waits.  The queue is
+// drained before a tile whenever fewer than a tile's worth of entries are
+// free, so it cannot overflow, and at the end of the block's stream; a
+// block's switch from electrons to ions leaves it as it is.  Slots are below
+// 2^29.
 #ifndef PIC_QDRAIN
 #define PIC_QDRAIN 128
 #endif
 constexpr unsigned int kQueueDrainAbove = PIC_QDRAIN;
 constexpr int kQueue = (int)kQueueDrainAbove + kThreads * kUnroll;  // + one tile
 constexpr uint32_t kQueueRedraw = 0x80000000u;  // in a queue entry: no collision, only a new wait
+constexpr uint32_t kQueueIon = 0x40000000u;     // in a queue entry: an ion
 struct CollQueue {
-    uint32_t *slot;            // [cap] slot | kQueueRedraw
+    uint32_t *slot;            // [cap] slot | kQueueIon | kQueueRedraw
     unsigned int *n;           // entries queued
     unsigned int cap;          // entries the queue holds
 };
@@ -813,24 +818,29 @@ __device__ __forceinline__ void eedf_sample(const Run &R, const SmemMain &sm, fl
 
 // Collide the queued particles, one per thread, and draw their next waits.
 // Their post-push cell word (count zero), position and velocity were stored
-// before the barrier that precedes this call.
-template <int S, bool INL>
-__device__ __forceinline__ void drain_body(const Run &R, const SmemMain &sm, Species sp, long long step, bool diag,
-                                           Tally &t) {
+// before the barrier that precedes this call.  se, si: the arrays the
+// queued slots of electrons and ions index.
+template <bool INL>
+__device__ __forceinline__ void drain_body(const Run &R, const SmemMain &sm, const Species &se, const Species &si,
+                                           long long step, bool diag, Tally &t) {
     __syncthreads();
     const unsigned int nq = min(*sm.q.n, (unsigned int)kQueue);
     for (unsigned int q = threadIdx.x; q < nq; q += kThreads) {
         const uint32_t entry = sm.q.slot[q];
-        const int idx = (int)(entry & ~kQueueRedraw);
+        const int S = (entry & kQueueIon) ? 1 : 0;
+        const Species &sp = S ? si : se;
+        const int idx = (int)(entry & ~(kQueueRedraw | kQueueIon));
+        // every load first, so their latencies overlap
         const uint32_t id = sp.id[idx];
         const int c = sp.cell[idx] & (int)kCellMask;
         float vx = sp.vx[idx], vy = sp.vy[idx], vz = sp.vz[idx];
+        const float off = sp.off[idx];
+        const float abar = (S == 0 && sp.abar) ? sp.abar[idx] : 0.0f;
         if (!(entry & kQueueRedraw)) {  // selected: the collision's words
             const uint4 w = draw(R, id, step, S, kTagMcc, 0);
             bool changed;
             if (S == 0) {
-                const float abar = sp.abar ? sp.abar[idx] : 0.0f;
-                changed = collide_e<INL>(R, w, id, step, c, sp.off[idx], abar, vx, vy, vz, t);
+                changed = collide_e<INL>(R, w, id, step, c, off, abar, vx, vy, vz, t);
             } else {
                 changed = collide_i<INL>(R, w, id, step, vx, vy, vz, t);
             }
@@ -848,19 +858,18 @@ __device__ __forceinline__ void drain_body(const Run &R, const SmemMain &sm, Spe
     __syncthreads();
 }
 
-template <int S>
-__device__ __noinline__ void drain_collisions(const Run &R, const SmemMain &sm, Species sp, long long step,
-                                              bool diag, Tally &t) {
-    drain_body<S, false>(R, sm, sp, step, diag, t);
+__device__ __noinline__ void drain_collisions(const Run &R, const SmemMain &sm, Species se, Species si,
+                                              long long step, bool diag, Tally &t) {
+    drain_body<false>(R, sm, se, si, step, diag, t);
 }
 
-template <int S, bool INL>
-__device__ __forceinline__ void drain_q(const Run &R, const SmemMain &sm, Species sp, long long step, bool diag,
-                                        Tally &t) {
+template <bool INL>
+__device__ __forceinline__ void drain_q(const Run &R, const SmemMain &sm, const Species &se, const Species &si,
+                                        long long step, bool diag, Tally &t) {
     if (INL)
-        drain_body<S, true>(R, sm, sp, step, diag, t);
+        drain_body<true>(R, sm, se, si, step, diag, t);
     else
-        drain_collisions<S>(R, sm, sp, step, diag, t);
+        drain_collisions(R, sm, se, si, step, diag, t);
 }
 
 // The per-species constants of the push, selected once per tile: the
@@ -957,7 +966,7 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         } else {
             const unsigned int pos = atomicAdd(sm.q.n, 1u);
             if (pos < sm.q.cap) {  // always: drains keep a tile's room
-                sm.q.slot[pos] = (uint32_t)idx | (hi & kRedrawBit ? kQueueRedraw : 0u);
+                sm.q.slot[pos] = (uint32_t)idx | (k.S ? kQueueIon : 0u) | (hi & kRedrawBit ? kQueueRedraw : 0u);
                 queued = true;
             } else {
                 atomicOr(&R.st->status, 0x8u);
@@ -1278,11 +1287,11 @@ __device__ void process_segment(const Run &R, const SmemMain &sm, const Ring &g,
         // reads the count after doing so (a count read after the barrier could
         // already include the next tile's particles in some threads only).
         const bool drain = __syncthreads_or((MI::push && R.mcc && *sm.q.n > kQueueDrainAbove) ? 1 : 0) != 0;
-        if (drain) drain_collisions<S>(R, sm, sp, step, diag, t);
+        if (drain) drain_collisions(R, sm, sp, sp, step, diag, t);
     }
     if (MI::push && R.mcc) {
         __syncthreads();
-        if (*sm.q.n > 0u) drain_collisions<S>(R, sm, sp, step, diag, t);
+        if (*sm.q.n > 0u) drain_collisions(R, sm, sp, sp, step, diag, t);
     }
     t.kx += kx;
     t.pw += pw;
@@ -1329,18 +1338,18 @@ __device__ void flush_species(const Run &R, const SmemMain &sm, int S, bool coun
 __device__ void flush_tally(const Run &R, int S, const Tally &t) {
     constexpr int nw = kThreads / 32;
     __shared__ float s_f[2][nw];
-    __shared__ unsigned int s_u[6][nw];
+    __shared__ unsigned int s_u[7][nw];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const float kx = warp_sum(t.kx), pw = warp_sum(t.pw);
-    const unsigned int u[6] = {warp_sum(t.el), warp_sum(t.ex), warp_sum(t.iz), warp_sum(t.cx),
-                               warp_sum(t.nul), warp_sum(t.ovf)};
+    const unsigned int u[7] = {warp_sum(t.el), warp_sum(t.ex), warp_sum(t.iz), warp_sum(t.cx),
+                               warp_sum(t.nul), warp_sum(t.ovf_e), warp_sum(t.ovf_i)};
     if (lane == 0) {
         s_f[0][wid] = kx;
         s_f[1][wid] = pw;
-        for (int k = 0; k < 6; ++k) s_u[k][wid] = u[k];
+        for (int k = 0; k < 7; ++k) s_u[k][wid] = u[k];
     }
     __syncthreads();
-    if (threadIdx.x < 8) {
+    if (threadIdx.x < 9) {
         const int k = threadIdx.x;
         if (k < 2) {
             double acc = 0.0;
@@ -1349,7 +1358,7 @@ __device__ void flush_tally(const Run &R, int S, const Tally &t) {
         } else {
             unsigned long long acc = 0;
             for (int w = 0; w < nw; ++w) acc += s_u[k - 2][w];
-            if (acc) atomicAdd(k - 2 < 5 ? &R.st->coll[k - 2] : &R.st->overflow[S], acc);
+            if (acc) atomicAdd(k - 2 < 5 ? &R.st->coll[k - 2] : &R.st->overflow[k - 7], acc);
         }
     }
     __syncthreads();
@@ -1532,11 +1541,31 @@ struct TailHead {
 // each thread holds one record, loaded with the staged sums (`my`); more go
 // through a bucketed ranking in global memory.  The counters are advanced by
 // the caller.
+// A store, or an add, to global memory that takes effect only if `p`: a
+// warming pass executes the instruction (so its code is fetched) with p false.
+__device__ __forceinline__ void st_g32_if(bool p, const void *addr, uint32_t v) {
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.global.b32 [%1], %2;\n}" ::"r"((unsigned)p),
+                 "l"(__cvta_generic_to_global(addr)), "r"(v)
+                 : "memory");
+}
+__device__ __forceinline__ void red_g64_if(bool p, const void *addr, unsigned long long v) {
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q red.global.add.u64 [%1], %2;\n}" ::"r"((unsigned)p),
+                 "l"(__cvta_generic_to_global(addr)), "l"(v)
+                 : "memory");
+}
+
 template <int MODE>
 __device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag, const TailHead &hd,
-                            const Birth &my, bool dry, long long step, const uint32_t *wtab) {
-    const unsigned int B = hd.B, ok = hd.ok;
+                            const Birth &my_rec, bool dry, long long step, const uint32_t *wtab) {
+    // A warming pass takes one made-up birth (cell 0, no global write)
+    // through the code of the few-births path, whatever the step's count.
+    const unsigned int B = dry ? 1u : hd.B, ok = dry ? 1u : hd.ok;
     if (B == 0) return;
+    Birth my = my_rec;
+    if (dry) {
+        my = Birth{};
+        my.off = 0.25f;
+    }
     const Species se = R.buf[hd.parity][0], si = R.buf[hd.parity][1];
     const unsigned int id_e = hd.id_e, id_i = hd.id_i;
     const long long s_ne = hd.ne, s_ni = hd.ni;
@@ -1554,30 +1583,33 @@ __device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag
                 if (ModeInfo<MODE>::ec3) atomicAdd(&K.d[S][key], (unsigned long long)a * a * a);
             }
         }
-        if (dry) return;
-        // each child draws its first wait on its birth step
-        se.cell[je] = bb.cell | (R.mcc ? (int)wait_bits(draw_wait(R, wtab, 0, id_e + r, step, 1)) : 0);
-        se.off[je] = bb.off;
-        se.vx[je] = bb.ve[0];
-        se.vy[je] = bb.ve[1];
-        se.vz[je] = bb.ve[2];
-        se.id[je] = id_e + r;
-        si.cell[ji] = bb.cell | (R.mcc ? (int)wait_bits(draw_wait(R, wtab, 1, id_i + r, step, 1)) : 0);
-        si.off[ji] = bb.off;
-        si.vx[ji] = bb.vi[0];
-        si.vy[ji] = bb.vi[1];
-        si.vz[ji] = bb.vi[2];
-        si.id[ji] = id_i + r;
+        // each child draws its first wait on its birth step; a warming pass
+        // runs the stores with their predicate off
+        const bool w = !dry;
+        const uint32_t ce = (uint32_t)bb.cell | (R.mcc ? wait_bits(draw_wait(R, wtab, 0, id_e + r, step, 1)) : 0u);
+        const uint32_t ci = (uint32_t)bb.cell | (R.mcc ? wait_bits(draw_wait(R, wtab, 1, id_i + r, step, 1)) : 0u);
+        st_g32_if(w, se.cell + je, ce);
+        st_g32_if(w, se.off + je, __float_as_uint(bb.off));
+        st_g32_if(w, se.vx + je, __float_as_uint(bb.ve[0]));
+        st_g32_if(w, se.vy + je, __float_as_uint(bb.ve[1]));
+        st_g32_if(w, se.vz + je, __float_as_uint(bb.ve[2]));
+        st_g32_if(w, se.id + je, id_e + r);
+        st_g32_if(w, si.cell + ji, ci);
+        st_g32_if(w, si.off + ji, __float_as_uint(bb.off));
+        st_g32_if(w, si.vx + ji, __float_as_uint(bb.vi[0]));
+        st_g32_if(w, si.vy + ji, __float_as_uint(bb.vi[1]));
+        st_g32_if(w, si.vz + ji, __float_as_uint(bb.vi[2]));
+        st_g32_if(w, si.id + ji, id_i + r);
         if (ModeInfo<MODE>::implicit) {
-            se.abar[je] = bb.abar_e;
-            si.abar[ji] = bb.abar_e * R.abar_ion_over_e;
+            st_g32_if(w, se.abar + je, __float_as_uint(bb.abar_e));
+            st_g32_if(w, si.abar + ji, __float_as_uint(bb.abar_e * R.abar_ion_over_e));
         }
         if (diag && R.eedf_bins > 0) {
             const float en = R.half_m_over_e[0] *
                              (bb.ve[0] * bb.ve[0] + bb.ve[1] * bb.ve[1] + bb.ve[2] * bb.ve[2]);
             int bin = (int)floorf(en * R.eedf_inv_width);
             bin = bin > R.eedf_bins ? R.eedf_bins : (bin < 0 ? 0 : bin);
-            atomicAdd(&R.eedf[bin], 1ull);
+            red_g64_if(w, R.eedf + bin, 1ull);
         }
     };
     if (B <= (unsigned int)kThreads) {
@@ -2481,7 +2513,7 @@ __device__ void stream_flush(const Run &R, const SmemMain &sm, int S, bool diag,
     using MI = ModeInfo<MODE>;
     flush_species(R, sm, S, MI::count_only, MI::ec3);
     if (MI::push) flush_tally(R, S, t);
-    t = Tally{0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
+    t = Tally{0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     if (diag) {
         __syncthreads();
         for (int k = threadIdx.x; k < R.n_cells; k += kThreads) {
@@ -2521,7 +2553,7 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
     const int par = st->parity;
     const Species sp[2] = {R.buf[par][0], R.buf[par][1]};
     const int mode_fields = MI::loads_v ? 3 : 2;
-    Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
+    Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     float kx = 0.0f, pw = 0.0f;  // the per-particle sums stay in registers
     int cur = -1;
     long long added = 0;
@@ -2537,20 +2569,18 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
         const int S = n ? ms.S[stage] : cur;
         const bool closing = cur >= 0 && (n == 0 || S != cur || added + n > kFlushEvery);
         // the one place the queue is drained (keeps a single inlined copy of
-        // the collision code in the loop): above the drain mark, or before the
-        // block's sums of this species are flushed.  Every thread must take
-        // the same branch: the count is read only where no thread can queue
-        // before the next barrier (the drain's or the flush's); a thread that
-        // read it after another had started the next tile would enter the
-        // drain's barriers alone.
+        // the collision code in the loop): above the drain mark, or at the end
+        // of the block's stream.  The queue holds both species, so the switch
+        // from electrons to ions does not drain it (a drain is a few
+        // microseconds of latency for the whole block).  Every thread must take
+        // the same branch: the count decides only where the barrier that ended
+        // the last tile had already seen it above the mark (`flag`), or at the
+        // end of the stream, after which nothing is queued; a thread that read
+        // it after another had started the next tile would enter the drain's
+        // barriers alone.
         if (MI::push && R.mcc && cur >= 0) {
             const unsigned int qn = *sm.q.n;
-            if (closing ? qn > 0u : (flag && qn > kQueueDrainAbove)) {
-                if (cur == 0)
-                    drain_q<0, true>(R, sm, sp[0], step, diag, t);
-                else
-                    drain_q<1, true>(R, sm, sp[1], step, diag, t);
-            }
+            if (n == 0 ? qn > 0u : (flag && qn > kQueueDrainAbove)) drain_q<true>(R, sm, sp[0], sp[1], step, diag, t);
         }
         if (closing) {
             t.kx += kx;
@@ -2992,7 +3022,7 @@ __device__ void batch_item(const Run &R, unsigned char *smem, const Ring &g, int
     if (threadIdx.x == 0) *sm.q.n = 0u;
     __syncthreads();
     if (b < e) {
-        Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u};
+        Tally t = {0.0f, 0.0f, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
         const Species sp = R.buf[st->parity][S];
         for (long long sb = b; sb < e; sb += kFlushEvery) {
             const long long se = sb + kFlushEvery < e ? sb + kFlushEvery : e;

@@ -447,10 +447,11 @@ __device__ __forceinline__ void acc_add(const Acc &acc, int key, uint32_t c, uin
     }
 }
 
-// m = 3: the warp aggregation of (count, F, F^2, F^3) with F^3 in its three
-// 12-bit pieces.  Per warp slot (at most 32 x kUnroll = 128 particles,
-// F < 2^12): sum F^2 < 2^31 and each piece sum < 2^19, so every reduction is
-// exact in 32 bits; the sum of F^2 is split into 12-bit pieces when added.
+// m = 3: per key of the warp's window (see deposit_tile below) the count
+// and the sum of F packed in one word (below 2^8 and 2^20 over a warp), the
+// sum of F^2 (below 2^31) and the three 12-bit pieces of each F^3 < 2^36
+// summed apart (each below 2^19); the sum of F^2 is split into 12-bit pieces
+// when added to the block's 32-bit counters.
 __device__ __forceinline__ void acc_add3(const Acc &acc, int key, uint32_t c, uint32_t a, uint32_t s2,
                                          uint32_t s3h, uint32_t s3m, uint32_t s3l) {
     atomicAdd(&acc.cnt[key], c);
@@ -462,66 +463,63 @@ __device__ __forceinline__ void acc_add3(const Acc &acc, int key, uint32_t c, ui
     atomicAdd(&acc.s3l[key], s3l);
 }
 
-__device__ __forceinline__ void warp_agg3(int key, uint32_t c, uint32_t a, uint32_t s2, uint32_t s3h, uint32_t s3m,
-                                          uint32_t s3l, const Acc &acc) {
-    const int lane = threadIdx.x & 31;
-    unsigned int pending = __ballot_sync(FULL_MASK, key >= 0);
-    int iter = 0;
-    while (pending) {
-        if (iter == 4) {  // widely spread warp: the rest add lane by lane
-            if ((pending >> lane) & 1u) acc_add3(acc, key, c, a, s2, s3h, s3m, s3l);
-            break;
-        }
-        const int leader = __ffs(pending) - 1;
-        const int lk = __shfl_sync(FULL_MASK, key, leader);
-        const bool mine = ((pending >> lane) & 1u) && key == lk;
-        const unsigned int grp = __ballot_sync(FULL_MASK, mine);
-        const uint32_t sc = __reduce_add_sync(FULL_MASK, mine ? c : 0u);
-        const uint32_t sa = __reduce_add_sync(FULL_MASK, mine ? a : 0u);
-        const uint32_t s2s = __reduce_add_sync(FULL_MASK, mine ? s2 : 0u);
-        const uint32_t sh = __reduce_add_sync(FULL_MASK, mine ? s3h : 0u);
-        const uint32_t sm_ = __reduce_add_sync(FULL_MASK, mine ? s3m : 0u);
-        const uint32_t sl = __reduce_add_sync(FULL_MASK, mine ? s3l : 0u);
-        if (lane == leader) acc_add3(acc, lk, sc, sa, s2s, sh, sm_, sl);
-        pending &= ~grp;
-        ++iter;
-    }
-}
+constexpr int kDepWindow = 4;
 
 __device__ __forceinline__ void deposit_tile3(const int (&key)[kUnroll], const uint32_t (&a)[kUnroll],
                                               const Acc &acc) {
-    int kmin = 0x7fffffff;
+    const int lane = threadIdx.x & 31;
+    int lo = 0x7fffffff, hi = -1;
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u)
-        if (key[u] >= 0 && key[u] < kmin) kmin = key[u];
-    uint32_t c0 = 0, a0 = 0, q0 = 0, h0 = 0, m0 = 0, l0 = 0, c1 = 0, a1 = 0, q1 = 0, h1 = 0, m1 = 0, l1 = 0;
+        if (key[u] >= 0) {
+            lo = min(lo, key[u]);
+            hi = max(hi, key[u]);
+        }
+    const int K1 = __reduce_max_sync(FULL_MASK, hi);
+    if (K1 < 0) return;
+    const int K0 = __reduce_min_sync(FULL_MASK, lo);
+    const int D = K1 - K0 + 1;
+    if (D > kDepWindow) {
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-        const int k = key[u];
-        if (k < 0) continue;
-        const uint32_t f = a[u], f2 = f * f;
-        const unsigned long long f3 = (unsigned long long)f2 * f;
-        const uint32_t hi = (uint32_t)(f3 >> 24), mid = (uint32_t)(f3 >> 12) & 0xfffu, lo = (uint32_t)f3 & 0xfffu;
-        if (k == kmin) {
-            c0 += 1u;
-            a0 += f;
-            q0 += f2;
-            h0 += hi;
-            m0 += mid;
-            l0 += lo;
-        } else if (k == kmin + 1) {
-            c1 += 1u;
-            a1 += f;
-            q1 += f2;
-            h1 += hi;
-            m1 += mid;
-            l1 += lo;
-        } else {
-            acc_add3(acc, k, 1u, f, f2, hi, mid, lo);
+        for (int u = 0; u < kUnroll; ++u)
+            if (key[u] >= 0) {
+                const uint32_t f = a[u], f2 = f * f;
+                const unsigned long long f3 = (unsigned long long)f2 * f;
+                acc_add3(acc, key[u], 1u, f, f2, (uint32_t)(f3 >> 24), (uint32_t)(f3 >> 12) & 0xfffu,
+                         (uint32_t)f3 & 0xfffu);
+            }
+        return;
+    }
+    uint32_t m_cf = 0u, m_s2 = 0u, m_h = 0u, m_m = 0u, m_l = 0u;
+#pragma unroll
+    for (int d = 0; d < kDepWindow; ++d) {
+        if (d >= D) break;
+        uint32_t cf = 0u, s2 = 0u, h = 0u, mm = 0u, l = 0u;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (key[u] == K0 + d) {
+                const uint32_t f = a[u], f2 = f * f;
+                const unsigned long long f3 = (unsigned long long)f2 * f;
+                cf += (f << 8) | 1u;
+                s2 += f2;
+                h += (uint32_t)(f3 >> 24);
+                mm += (uint32_t)(f3 >> 12) & 0xfffu;
+                l += (uint32_t)f3 & 0xfffu;
+            }
+        cf = __reduce_add_sync(FULL_MASK, cf);
+        s2 = __reduce_add_sync(FULL_MASK, s2);
+        h = __reduce_add_sync(FULL_MASK, h);
+        mm = __reduce_add_sync(FULL_MASK, mm);
+        l = __reduce_add_sync(FULL_MASK, l);
+        if (lane == d) {
+            m_cf = cf;
+            m_s2 = s2;
+            m_h = h;
+            m_m = mm;
+            m_l = l;
         }
     }
-    warp_agg3(kmin == 0x7fffffff ? -1 : kmin, c0, a0, q0, h0, m0, l0, acc);
-    warp_agg3(c1 ? kmin + 1 : -1, c1, a1, q1, h1, m1, l1, acc);
+    if (lane < D && (m_cf & 0xffu)) acc_add3(acc, K0 + lane, m_cf & 0xffu, m_cf >> 8, m_s2, m_h, m_m, m_l);
 }
 
 // Deposit of a warp's tile share (32 x kUnroll particles).  Kept sorted by
@@ -532,7 +530,6 @@ __device__ __forceinline__ void deposit_tile3(const int (&key)[kUnroll], const u
 // a packed in one word, the halves of a^2 in two), and lane d adds key
 // K0 + d: one set of shared atomics per warp, on consecutive words.  A
 // warp spread wider than kDepWindow keys adds particle by particle.
-constexpr int kDepWindow = 4;
 
 __device__ __forceinline__ void deposit_tile(const int (&key)[kUnroll], const uint32_t (&a)[kUnroll],
                                              const Acc &acc, bool count_only) {

@@ -1,6 +1,6 @@
 """The discharge study of Sec. 3.1 rerun with the library, qualitatively.
 
-    python -m workloads.study [--periods P] [--avg-periods A] [--out workloads/discharge_study.json]
+    python -m workloads.study [--periods 1800] [--avg-periods 300] [--out workloads/discharge_study.json]
 
 The paper's benchmark discharge (Sec. 3: 4 cm argon gap, 27 MHz, 200 V on one
 electrode, 50 mTorr, 2e16 m^-3 uniform start, 400 macro-particles per cell,
@@ -159,8 +159,8 @@ def run_study(periods: int, avg_periods: int, device="cuda:0") -> dict:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--periods", type=int, default=600)
-    ap.add_argument("--avg-periods", type=int, default=100)
+    ap.add_argument("--periods", type=int, default=1800)
+    ap.add_argument("--avg-periods", type=int, default=300)
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
                                                   "discharge_study.json"))
     a = ap.parse_args()

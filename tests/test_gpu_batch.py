@@ -109,3 +109,24 @@ def test_batch_profiles_equal_the_single_run_profiles():
         assert pb["ne"].sum() > 0
         single.close()
     batch.close()
+
+
+def test_benchmark_sweep_stays_clean_over_its_window():
+    """The 256 uneven runs the benchmark times (cells 64..1024, 1e4..2e6
+    particles per species, explicit and direct implicit) over the benchmark's
+    2000 steps: no run drops a birth or a particle (its status word stays 0)
+    and none grows beyond three times its load, so the throughput is that of
+    discharges in regime."""
+    from paper_1310_5284_gb300.batch import BatchSim
+
+    cfgs = workloads.batch_discharges(256)
+    batch = BatchSim(cfgs)
+    c0 = [sum(batch.diag(i)["count"]) for i in range(len(cfgs))]
+    batch.step(2000)
+    assert batch.status() == 0
+    for i in range(len(cfgs)):
+        d = batch.diag(i)
+        assert d["status"] == 0, (i, d["status"])
+        assert d["step"] == 2000
+        assert sum(d["count"]) <= 3 * c0[i], (i, sum(d["count"]), c0[i])
+    batch.close()

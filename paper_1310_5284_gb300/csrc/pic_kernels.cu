@@ -1566,49 +1566,81 @@ __device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag
     const Species se = R.buf[hd.parity][0], si = R.buf[hd.parity][1];
     const unsigned int id_e = hd.id_e, id_i = hd.id_i;
     const long long s_ne = hd.ne, s_ni = hd.ni;
-    auto place = [&](const Birth &bb, unsigned int r) {
-        const long long je = s_ne + r, ji = s_ni + r;
+    // One child of birth bb (rank r): species S's key sums, its first wait
+    // (drawn on its birth step) and its slot; a warming pass runs the stores
+    // with their predicate off.
+    auto place_child = [&](int cell, float off, float vx, float vy, float vz, float abar, unsigned int r, int S) {
+        const long long j = (S ? s_ni : s_ne) + r;
+        const Species &sp = S ? si : se;
+        const uint32_t id = (S ? id_i : id_e) + r;
         uint32_t a;
-        const int key = ModeInfo<MODE>::mc    ? deposit_key_s1(bb.cell, bb.off, a)
-                        : ModeInfo<MODE>::ec3 ? deposit_key_s3(bb.cell, bb.off, a)
-                                              : deposit_key_s2(bb.cell, bb.off, a);
-        for (int S = 0; S < 2; ++S) {
-            atomicAdd(&K.c[S][key], 1ull);
-            if (!ModeInfo<MODE>::count_only) {
-                atomicAdd(&K.a[S][key], (unsigned long long)a);
-                atomicAdd(&K.b[S][key], (unsigned long long)a * a);
-                if (ModeInfo<MODE>::ec3) atomicAdd(&K.d[S][key], (unsigned long long)a * a * a);
-            }
+        const int key = ModeInfo<MODE>::mc    ? deposit_key_s1(cell, off, a)
+                        : ModeInfo<MODE>::ec3 ? deposit_key_s3(cell, off, a)
+                                              : deposit_key_s2(cell, off, a);
+        atomicAdd(&K.c[S][key], 1ull);
+        if (!ModeInfo<MODE>::count_only) {
+            atomicAdd(&K.a[S][key], (unsigned long long)a);
+            atomicAdd(&K.b[S][key], (unsigned long long)a * a);
+            if (ModeInfo<MODE>::ec3) atomicAdd(&K.d[S][key], (unsigned long long)a * a * a);
         }
-        // each child draws its first wait on its birth step; a warming pass
-        // runs the stores with their predicate off
         const bool w = !dry;
-        const uint32_t ce = (uint32_t)bb.cell | (R.mcc ? wait_bits(draw_wait(R, wtab, 0, id_e + r, step, 1)) : 0u);
-        const uint32_t ci = (uint32_t)bb.cell | (R.mcc ? wait_bits(draw_wait(R, wtab, 1, id_i + r, step, 1)) : 0u);
-        st_g32_if(w, se.cell + je, ce);
-        st_g32_if(w, se.off + je, __float_as_uint(bb.off));
-        st_g32_if(w, se.vx + je, __float_as_uint(bb.ve[0]));
-        st_g32_if(w, se.vy + je, __float_as_uint(bb.ve[1]));
-        st_g32_if(w, se.vz + je, __float_as_uint(bb.ve[2]));
-        st_g32_if(w, se.id + je, id_e + r);
-        st_g32_if(w, si.cell + ji, ci);
-        st_g32_if(w, si.off + ji, __float_as_uint(bb.off));
-        st_g32_if(w, si.vx + ji, __float_as_uint(bb.vi[0]));
-        st_g32_if(w, si.vy + ji, __float_as_uint(bb.vi[1]));
-        st_g32_if(w, si.vz + ji, __float_as_uint(bb.vi[2]));
-        st_g32_if(w, si.id + ji, id_i + r);
-        if (ModeInfo<MODE>::implicit) {
-            st_g32_if(w, se.abar + je, __float_as_uint(bb.abar_e));
-            st_g32_if(w, si.abar + ji, __float_as_uint(bb.abar_e * R.abar_ion_over_e));
-        }
-        if (diag && R.eedf_bins > 0) {
-            const float en = R.half_m_over_e[0] *
-                             (bb.ve[0] * bb.ve[0] + bb.ve[1] * bb.ve[1] + bb.ve[2] * bb.ve[2]);
+        const uint32_t cw = (uint32_t)cell | (R.mcc ? wait_bits(draw_wait(R, wtab, S, id, step, 1)) : 0u);
+        st_g32_if(w, sp.cell + j, cw);
+        st_g32_if(w, sp.off + j, __float_as_uint(off));
+        st_g32_if(w, sp.vx + j, __float_as_uint(vx));
+        st_g32_if(w, sp.vy + j, __float_as_uint(vy));
+        st_g32_if(w, sp.vz + j, __float_as_uint(vz));
+        st_g32_if(w, sp.id + j, id);
+        if (ModeInfo<MODE>::implicit) st_g32_if(w, sp.abar + j, __float_as_uint(abar));
+        if (S == 0 && diag && R.eedf_bins > 0) {
+            const float en = R.half_m_over_e[0] * (vx * vx + vy * vy + vz * vz);
             int bin = (int)floorf(en * R.eedf_inv_width);
             bin = bin > R.eedf_bins ? R.eedf_bins : (bin < 0 ? 0 : bin);
             red_g64_if(w, R.eedf + bin, 1ull);
         }
     };
+    auto place = [&](const Birth &bb, unsigned int r) {
+        place_child(bb.cell, bb.off, bb.ve[0], bb.ve[1], bb.ve[2], bb.abar_e, r, 0);
+        place_child(bb.cell, bb.off, bb.vi[0], bb.vi[1], bb.vi[2], bb.abar_e * R.abar_ion_over_e, r, 1);
+    };
+    auto rank_of = [&](const uint32_t *spid, uint32_t p) {
+        // rank = number of births with a smaller parent id (ids are unique),
+        // against all parent ids staged in shared memory (padded to a
+        // multiple of 4 with the largest id)
+        const uint4 *sp4 = (const uint4 *)spid;
+        const unsigned int nq = (B + 3u) / 4u;
+        unsigned int r = 0;
+        for (unsigned int k = 0; k < nq; ++k) {
+            const uint4 v = sp4[k];
+            r += (v.x < p ? 1u : 0u) + (v.y < p ? 1u : 0u) + (v.z < p ? 1u : 0u) + (v.w < p ? 1u : 0u);
+        }
+        return r;
+    };
+    if (B <= (unsigned int)kThreads / 2) {
+        // thread t places the electron child of birth t and thread
+        // kThreads/2 + t its ion child, side by side
+        uint32_t *spid = (uint32_t *)smem;  // [kThreads]
+        spid[threadIdx.x] = threadIdx.x < B ? my.pid : 0xffffffffu;
+        __syncthreads();
+        const unsigned int t = threadIdx.x % (kThreads / 2);
+        const int S = (int)(threadIdx.x / (kThreads / 2));
+        if (t < B) {
+            // the ion side reads birth t's record (the electron side holds it)
+            const Birth *g = (S == 1 && !dry) ? R.births + t : nullptr;
+            const uint32_t pid = g ? g->pid : my.pid;
+            const unsigned int r = rank_of(spid, pid);
+            if (r < ok) {
+                if (S == 0)
+                    place_child(my.cell, my.off, my.ve[0], my.ve[1], my.ve[2], my.abar_e, r, 0);
+                else if (g)
+                    place_child(g->cell, g->off, g->vi[0], g->vi[1], g->vi[2], g->abar_e * R.abar_ion_over_e, r, 1);
+                else
+                    place_child(my.cell, my.off, my.vi[0], my.vi[1], my.vi[2], my.abar_e * R.abar_ion_over_e, r, 1);
+            }
+        }
+        __syncthreads();
+        return;
+    }
     if (B <= (unsigned int)kThreads) {
         // rank = number of births with a smaller parent id (ids are unique),
         // by comparison against all parent ids staged in shared memory (padded
@@ -1617,14 +1649,7 @@ __device__ void tail_births(const Run &R, Keys K, unsigned char *smem, bool diag
         spid[threadIdx.x] = threadIdx.x < B ? my.pid : 0xffffffffu;
         __syncthreads();
         if (threadIdx.x < B) {
-            const uint4 *sp4 = (const uint4 *)spid;
-            const unsigned int nq = (B + 3u) / 4u;
-            const uint32_t p = my.pid;
-            unsigned int r = 0;
-            for (unsigned int k = 0; k < nq; ++k) {
-                const uint4 v = sp4[k];
-                r += (v.x < p ? 1u : 0u) + (v.y < p ? 1u : 0u) + (v.z < p ? 1u : 0u) + (v.w < p ? 1u : 0u);
-            }
+            const unsigned int r = rank_of(spid, my.pid);
             if (r < ok) place(my, r);
         }
         __syncthreads();

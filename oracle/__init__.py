@@ -70,6 +70,7 @@ class Params(ctypes.Structure):
         ("sig_cx", ctypes.c_double), ("eps_cap", ctypes.c_double),
         ("cx_vmax", ctypes.c_double), ("eedf_max_ev", ctypes.c_double),
         ("coll_model", ctypes.c_int32), ("reserved", ctypes.c_int32), ("iz_split_b", ctypes.c_double),
+        ("cell_width", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -138,6 +139,12 @@ def lib():
         L.orc_gather_ec.restype = ctypes.c_double
         L.orc_gather_mc.argtypes = [_P(Params), _d, ctypes.c_double]
         L.orc_gather_mc.restype = ctypes.c_double
+        L.orc_grid_nodes.argtypes = [ctypes.c_int, _d, _d]
+        L.orc_locate.argtypes = [ctypes.c_int, _d, _d, ctypes.c_double, _i64, _d]
+        L.orc_solve_dirichlet_h.argtypes = [ctypes.c_int, _d, _d, ctypes.c_double, _d]
+        L.orc_solve_periodic_h.argtypes = [ctypes.c_int, _d, _d, _d]
+        L.orc_gather_ec_h.argtypes = [_P(Params), _d, ctypes.c_double]
+        L.orc_gather_ec_h.restype = ctypes.c_double
         L.orc_rotate.argtypes = [_d, ctypes.c_double, ctypes.c_double, _d]
         L.orc_vs_cos_chi.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_vs_cos_chi.restype = ctypes.c_double
@@ -209,6 +216,14 @@ def params(cfg: dict) -> Params:
     p.coll_model = (1 if cfg.get("iz_split", "equal") == "opal" else 0) | \
         (2 if cfg.get("scattering", "isotropic") == "vahedi_surendra" else 0)
     p.iz_split_b = float(cfg.get("iz_split_b", 10.0))
+    if cfg.get("cell_width") is not None:
+        h = np.ascontiguousarray(cfg["cell_width"], dtype=np.float64)
+        if h.shape != (p.n_cells,) or not np.all(h > 0):
+            raise ValueError("cell_width must hold n_cells positive widths")
+        if abs(h.sum() - p.length) > 1e-9 * p.length:
+            raise ValueError("cell widths must sum to length")
+        p._cell_width = h  # keeps the array alive while the struct points at it
+        p.cell_width = h.ctypes.data_as(_P(ctypes.c_double))
     return p
 
 
@@ -366,6 +381,50 @@ def gather_mc(cfg, e_node, xi) -> float:
     return lib().orc_gather_mc(ctypes.byref(p), _ptr(e, ctypes.c_double), float(xi))
 
 
+def grid_nodes(h) -> np.ndarray:
+    """Node positions of a non-uniform grid from its cell widths."""
+    h = np.ascontiguousarray(h, np.float64)
+    x = np.zeros(h.size + 1)
+    lib().orc_grid_nodes(h.size, _ptr(h, ctypes.c_double), _ptr(x, ctypes.c_double))
+    return x
+
+
+def locate(h, x_nodes, x):
+    """(where, cell, off) of a physical position: where -1 / 0 / 1 below, inside, beyond."""
+    h = np.ascontiguousarray(h, np.float64)
+    xn = np.ascontiguousarray(x_nodes, np.float64)
+    c, o = ctypes.c_int64(), ctypes.c_double()
+    w = lib().orc_locate(h.size, _ptr(xn, ctypes.c_double), _ptr(h, ctypes.c_double), float(x),
+                         ctypes.byref(c), ctypes.byref(o))
+    return int(w), int(c.value), float(o.value)
+
+
+def solve_dirichlet_h(h, q_node, v_left) -> np.ndarray:
+    h = np.ascontiguousarray(h, np.float64)
+    q = np.ascontiguousarray(q_node, np.float64)
+    phi = np.zeros(h.size + 1)
+    lib().orc_solve_dirichlet_h(h.size, _ptr(h, ctypes.c_double), _ptr(q, ctypes.c_double), float(v_left),
+                                _ptr(phi, ctypes.c_double))
+    return phi
+
+
+def solve_periodic_h(h, q_node) -> np.ndarray:
+    h = np.ascontiguousarray(h, np.float64)
+    q = np.ascontiguousarray(q_node, np.float64)
+    phi = np.zeros(h.size + 1)
+    lib().orc_solve_periodic_h(h.size, _ptr(h, ctypes.c_double), _ptr(q, ctypes.c_double),
+                               _ptr(phi, ctypes.c_double))
+    return phi
+
+
+def gather_ec_h(cfg, u_cc, xi) -> float:
+    """Field [V/m] at cell coordinate xi on the non-uniform grid of cfg from
+    the cells' voltage drops."""
+    p = params(cfg)
+    u = np.ascontiguousarray(u_cc, np.float64)
+    return float(lib().orc_gather_ec_h(ctypes.byref(p), _ptr(u, ctypes.c_double), float(xi)))
+
+
 def rotate(d, cos_chi, phi) -> np.ndarray:
     dd = np.ascontiguousarray(d, dtype=np.float64)
     out = np.zeros(3)
@@ -383,6 +442,9 @@ class Sim:
         npi = int(cfg["np_init"])
         cap_e = cap_e if cap_e is not None else max(1024, int(npi * cfg.get("cap_factor", 2.0)))
         cap_i = cap_i if cap_i is not None else cap_e
+        if cfg.get("cell_width") is not None and (
+                cfg.get("scheme", "ec_explicit") != "ec_explicit" or not cfg.get("ions_mobile", True)):
+            raise ValueError("the non-uniform grid takes the explicit EC scheme with mobile ions")
         self._h = lib().orc_sim_create(ctypes.byref(self.p), int(cap_e), int(cap_i))
         if not self._h:
             raise MemoryError("oracle allocation failed")

@@ -479,6 +479,94 @@ double orc_gather_mc(const orc_params *p, const double *e_node, double xi)
 }
 
 /* ------------------------------------------------------------------------- */
+/* Non-uniform grid (the multi-scale grid of Sec. 4).  The paper gives no form */
+/* of Eq. (2)-(3) for unequal cells; the reading here keeps them in the cell  */
+/* coordinate xi (the uniform-grid weights of xi) and takes as the force the  */
+/* exact x-derivative of the particle's potential energy, so that the energy */
+/* argument of the EC scheme carries over: with xi(x) linear inside each cell,*/
+/* d/dx = (1/h_c) d/dxi there.  The field equation is the Gauss law between   */
+/* the physical nodes, whose matrix is symmetric.                             */
+/* ------------------------------------------------------------------------- */
+void orc_grid_nodes(int n_cells, const double *h, double *x)
+{
+    x[0] = 0.0;
+    for (int c = 0; c < n_cells; ++c) x[c + 1] = x[c] + h[c];
+}
+
+int orc_locate(int n_cells, const double *x_nodes, const double *h, double x, int64_t *cell,
+               double *off)
+{
+    if (x < x_nodes[0]) return -1;
+    if (x >= x_nodes[n_cells]) return 1;
+    /* bisection for the last node at or below x */
+    int lo = 0, hi = n_cells;  /* x_nodes[lo] <= x < x_nodes[hi] */
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (x_nodes[mid] <= x)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    *cell = lo;
+    *off = (x - x_nodes[lo]) / h[lo];
+    if (*off >= 1.0) *off = nextafter(1.0, 0.0);  /* rounding at the right node */
+    return 0;
+}
+
+void orc_solve_dirichlet_h(int n_cells, const double *h, const double *q_node, double v_left,
+                           double *phi)
+{
+    int n = n_cells;
+    phi[0] = v_left;
+    phi[n] = 0.0;
+    if (n < 2) return;
+    int m = n - 1; /* unknowns phi[1..n-1] */
+    double *cp = (double *)malloc(sizeof(double) * (size_t)m);
+    double *dp = (double *)malloc(sizeof(double) * (size_t)m);
+    for (int k = 0; k < m; ++k) {
+        int g = k + 1;
+        double a = -1.0 / h[g - 1], c = -1.0 / h[g];
+        double b = -a - c;
+        double d = q_node[g] / EPS_0;
+        if (g == 1) d -= a * v_left;
+        if (k == 0) {
+            cp[k] = c / b;
+            dp[k] = d / b;
+        } else {
+            double den = b - a * cp[k - 1];
+            cp[k] = c / den;
+            dp[k] = (d - a * dp[k - 1]) / den;
+        }
+    }
+    phi[m] = dp[m - 1];
+    for (int k = m - 2; k >= 0; --k) phi[k + 1] = dp[k] - cp[k] * phi[k + 2];
+    free(cp);
+    free(dp);
+}
+
+void orc_solve_periodic_h(int n_cells, const double *h, const double *q_node, double *phi)
+{
+    int n = n_cells;
+    double len = 0.0, tot = 0.0;
+    for (int c = 0; c < n; ++c) len += h[c];
+    for (int g = 0; g < n; ++g) tot += q_node[g];
+    double *r = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    for (int g = 0; g < n; ++g) {
+        double hl = h[(g - 1 + n) % n], hr = h[g];
+        r[g] = q_node[g] - tot * 0.5 * (hl + hr) / len;
+    }
+    r[n] = 0.0;
+    orc_solve_dirichlet_h(n, h, r, 0.0, phi);
+    free(r);
+}
+
+double orc_gather_ec_h(const orc_params *p, const double *u_cc, double xi)
+{
+    int64_t c = (int64_t)floor(xi);
+    return orc_gather_ec(p, u_cc, xi) / p->cell_width[c];
+}
+
+/* ------------------------------------------------------------------------- */
 /* Scattering geometry: turn the unit vector d by polar angle chi and azimuth */
 /* phi.  The azimuth is measured in the basis e1 = d(theta)/dtheta,           */
 /* e2 = d(psi)/dpsi / sin(theta) of the polar angles of d about the x axis.   */
@@ -547,6 +635,9 @@ struct orc_sim {
     double *rho_f[2];   /* [N+1], particle units (fp64 mode) */
     int64_t *chi_q[2];  /* [N], units 2^-16 */
     double *rho, *chi, *phi, *e_cc, *e_node;
+    /* non-uniform grid (NULL on the uniform grid): cell widths, node
+       positions, voltage drops phi_c - phi_{c+1} of the cells */
+    double *h, *xn, *u_cc;
     birth_t *births;
     int64_t n_births, cap_births;
     /* diagnostics */
@@ -603,6 +694,19 @@ orc_sim *orc_sim_create(const orc_params *p, int64_t cap_e, int64_t cap_i)
     s->avg_ni = (double *)calloc((size_t)nn, sizeof(double));
     s->avg_phi = (double *)calloc((size_t)nn, sizeof(double));
     s->eedf = (int64_t *)calloc((size_t)(p->eedf_bins + 1), sizeof(int64_t));
+    if (p->cell_width) {
+        /* the explicit EC scheme with mobile ions is the one defined on it */
+        if (p->scheme != ORC_EC_EXPLICIT || !p->ions_mobile) {
+            orc_sim_free(s);
+            return NULL;
+        }
+        s->h = (double *)malloc(sizeof(double) * (size_t)p->n_cells);
+        s->xn = (double *)malloc(sizeof(double) * (size_t)nn);
+        s->u_cc = (double *)calloc((size_t)nn, sizeof(double));
+        memcpy(s->h, p->cell_width, sizeof(double) * (size_t)p->n_cells);
+        orc_grid_nodes(p->n_cells, s->h, s->xn);
+        s->p.cell_width = s->h;  /* the caller's array may go away */
+    }
     s->cap_births = cap_e > 1024 ? cap_e : 1024;
     s->births = (birth_t *)calloc((size_t)s->cap_births, sizeof(birth_t));
     return s;
@@ -618,6 +722,7 @@ void orc_sim_free(orc_sim *s)
     }
     free(s->rho); free(s->chi); free(s->phi); free(s->e_cc); free(s->e_node);
     free(s->avg_ne); free(s->avg_ni); free(s->avg_phi); free(s->eedf); free(s->births);
+    free(s->h); free(s->xn); free(s->u_cc);
     free(s);
 }
 
@@ -627,13 +732,32 @@ static int is_mc(const orc_params *p) { return p->scheme == ORC_MC_EXPLICIT || p
 static int is_implicit(const orc_params *p) { return p->scheme == ORC_EC_IMPLICIT || p->scheme == ORC_MC_IMPLICIT; }
 static int uses_fixed(const orc_params *p) { return p->quantized || is_mc(p); }
 
+/* The length a node's charge is spread over in the densities: dx on the
+   uniform grid; on a non-uniform one the mean (h_{g-1} + h_g) / 2 of the two
+   cells beside it, the wall nodes taking the one cell they have twice (as
+   the uniform grid's wall nodes take dx), wrapped in a periodic box. */
+static double node_len(const orc_sim *s, int64_t g)
+{
+    if (!s->h) return s->d.dx;
+    int64_t n = s->p.n_cells;
+    double hl, hr;
+    if (s->p.periodic) {
+        hl = s->h[(g - 1 + n) % n];
+        hr = s->h[g % n];
+    } else {
+        hl = s->h[g > 0 ? g - 1 : 0];
+        hr = s->h[g < n ? g : n - 1];
+    }
+    return 0.5 * (hl + hr);
+}
+
 /* Charge density at the nodes [C/m^3] from the per-species assignments. */
 static void assemble_rho(orc_sim *s)
 {
     const orc_params *p = &s->p;
     int64_t nn = p->n_cells + 1;
-    double scale = s->d.weight / s->d.dx;
     for (int64_t g = 0; g < nn; ++g) {
+        double scale = s->d.weight / node_len(s, g);
         double ne, ni;
         if (uses_fixed(p)) {
             ne = (double)s->rho_q[0][g] / (double)orc_charge_unit(p);
@@ -698,6 +822,25 @@ static void solve_field(orc_sim *s, const double *chi, int64_t level)
     const orc_params *p = &s->p;
     int n = p->n_cells;
     double dx = s->d.dx;
+    if (s->h) {
+        /* Gauss law on the physical nodes with the node charges per area */
+        double *qn = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+        for (int g = 0; g <= n; ++g) qn[g] = s->rho[g] * node_len(s, g);
+        if (p->periodic)
+            orc_solve_periodic_h(n, s->h, qn, s->phi);
+        else
+            orc_solve_dirichlet_h(n, s->h, qn, rf_voltage(p, level), s->phi);
+        free(qn);
+        double w = 0.0;
+        for (int c = 0; c < n; ++c) {
+            double right = (p->periodic && c + 1 == n) ? s->phi[0] : s->phi[c + 1];
+            s->u_cc[c] = s->phi[c] - right;
+            s->e_cc[c] = s->u_cc[c] / s->h[c];
+            w += s->e_cc[c] * s->e_cc[c] * s->h[c];
+        }
+        s->dg.field_energy = 0.5 * EPS_0 * w;
+        return;
+    }
     if (p->periodic)
         orc_solve_periodic(n, dx, s->rho, chi, s->phi);
     else
@@ -710,6 +853,7 @@ static void solve_field(orc_sim *s, const double *chi, int64_t level)
 
 static double gather(const orc_sim *s, double xi)
 {
+    if (s->h) return orc_gather_ec_h(&s->p, s->u_cc, xi);
     if (is_mc(&s->p)) return orc_gather_mc(&s->p, s->e_node, xi);
     if (s->p.scheme == ORC_EC3_EXPLICIT) return orc_gather_ec3(&s->p, s->e_cc, xi);
     return orc_gather_ec(&s->p, s->e_cc, xi);
@@ -729,8 +873,8 @@ static void accumulate_averages(orc_sim *s)
 {
     const orc_params *p = &s->p;
     int64_t nn = p->n_cells + 1;
-    double scale = s->d.weight / s->d.dx;
     for (int64_t g = 0; g < nn; ++g) {
+        double scale = s->d.weight / node_len(s, g);
         double ne, ni;
         if (uses_fixed(p)) {
             ne = (double)s->rho_q[0][g] / (double)orc_charge_unit(p);
@@ -763,6 +907,25 @@ int orc_sim_load(orc_sim *s, int64_t n_e, int64_t n_i)
             uint64_t t = (uint64_t)w[0] * (uint64_t)p->n_cells;
             double cell = (double)(t >> 32);
             double off = (double)((uint32_t)t >> 8) * (1.0 / 16777216.0);
+            if (s->h) {
+                /* non-uniform grid: uniform in x = (w0 / 2^32) L, the offset
+                   kept to FP32 (the storage precision of the particle) */
+                int64_t c;
+                double o;
+                double x = ldexp((double)w[0], -32) * s->xn[p->n_cells];
+                orc_locate(p->n_cells, s->xn, s->h, x, &c, &o);
+                float of = (float)o;
+                if (of >= 1.0f) {  /* rounds onto the next node */
+                    if (c + 1 < p->n_cells) {
+                        of = 0.0f;
+                        c += 1;
+                    } else {
+                        of = nextafterf(1.0f, 0.0f);  /* stays below x = L */
+                    }
+                }
+                cell = (double)c;
+                off = (double)of;
+            }
             sp->xi[i] = cell + off;
             double n1, n2, n3, n4;
             box_muller(uniform24(w[1]), uniform24(w[2]), &n1, &n2);
@@ -1090,6 +1253,26 @@ static int collisions_and_population(orc_sim *s)
     return finish_population(s);
 }
 
+/* The cell coordinate after a move by d metres on the non-uniform grid:
+   through the physical position, wrapped in a periodic box; a position
+   beyond an electrode comes back outside [0, N) for the absorption. */
+static double move_on_grid(const orc_sim *s, double xi, double d)
+{
+    int64_t n = s->p.n_cells, c = (int64_t)floor(xi);
+    double len = s->xn[n];
+    double x = s->xn[c] + (xi - (double)c) * s->h[c] + d;
+    if (s->p.periodic) {
+        x -= len * floor(x / len);
+        if (x >= len) x -= len;
+    }
+    int64_t cell;
+    double off;
+    int where = orc_locate((int)n, s->xn, s->h, x, &cell, &off);
+    if (where < 0) return -0.5;
+    if (where > 0) return (double)n + 0.5;
+    return (double)cell + off;
+}
+
 /* One explicit step n -> n+1 (Sec. 2 schemes (1) and (2)): gather E^n at x^n,
    leapfrog v^{n-1/2} -> v^{n+1/2}, x^n -> x^{n+1}, absorb, collide, assign
    charge at x^{n+1} and solve for E^{n+1} with the electrode at V(t_{n+1}). */
@@ -1109,9 +1292,13 @@ static int step_explicit(orc_sim *s, int diag_step)
             kx += 0.5 * (v_old * v_old + v_new * v_new);
             double work = s->d.q[k] * s->d.weight * e * 0.5 * (v_old + v_new);
             pw += work;
-            if (diag_step) s->heat[k][(int64_t)floor(sp->xi[i])] += work / dx;
+            int64_t c = (int64_t)floor(sp->xi[i]);
+            if (diag_step) s->heat[k][c] += work / (s->h ? s->h[c] : dx);
             sp->vx[i] = v_new;
-            sp->xi[i] += v_new * p->dt / dx;
+            if (s->h)
+                sp->xi[i] = move_on_grid(s, sp->xi[i], v_new * p->dt);
+            else
+                sp->xi[i] += v_new * p->dt / dx;
             boundary(s, k, i);
         }
         s->dg.ke_x[k] = 0.5 * s->d.m[k] * s->d.weight * kx;

@@ -61,6 +61,12 @@ typedef struct orc_params {
     int32_t coll_model;
     int32_t reserved;
     double iz_split_b;
+    /* Non-uniform grid, the multi-scale grid Sec. 4 proposes: the widths [m]
+       of the n_cells cells, summing to `length`; NULL for the uniform grid of
+       width length / n_cells.  Positions stay in cell units (cell index plus
+       the fraction of that cell's width); the explicit EC scheme with mobile
+       ions is the one scheme defined on it (orc_sim_create refuses others). */
+    const double *cell_width;
 } orc_params;
 enum { ORC_IZ_OPAL = 1, ORC_SCATTER_VS = 2 };
 
@@ -119,6 +125,32 @@ double orc_gather_ec(const orc_params *p, const double *e_cc, double xi);
 double orc_gather_mc(const orc_params *p, const double *e_node, double xi);
 /* m = 3: S_2 from the three nearest cell centres (ghost cells E = 0). */
 double orc_gather_ec3(const orc_params *p, const double *e_cc, double xi);
+
+/* ---- non-uniform grid (cell widths h[0..N-1], nodes x[0..N]) ----
+   The EC scheme there keeps Eq. (2)-(3) in the cell coordinate xi: the S_2
+   assignment of xi to the nodes and the S_1 interpolation between cell
+   centres are those of the uniform grid.  The particle's potential energy
+   q sum_g phi_g S_2(xi(x) - g) then has the x-derivative
+   -(q / h_c) sum_c (phi_c - phi_{c+1}) S_1(xi - c - 1/2) inside cell c, which
+   is the force; the Poisson equation is the Gauss law on the physical node
+   spacing.  Node positions: x[0] = 0, x[g+1] = x[g] + h[g]. */
+void orc_grid_nodes(int n_cells, const double *h, double *x);
+/* The cell holding the physical position x (x[c] <= x < x[c+1]) and the
+   fraction off = (x - x[c]) / h[c] in [0, 1); returns 0 inside, -1 below x[0],
+   1 at or beyond x[N]. */
+int orc_locate(int n_cells, const double *x_nodes, const double *h, double x, int64_t *cell,
+               double *off);
+/* Gauss law eps0 [(phi_g - phi_{g+1})/h_g - (phi_{g-1} - phi_g)/h_{g-1}] = q_g
+   for the interior nodes, node charges q_g per unit area [C/m^2], phi[0] =
+   v_left, phi[N] = 0 (Thomas algorithm). */
+void orc_solve_dirichlet_h(int n_cells, const double *h, const double *q_node, double v_left,
+                           double *phi);
+/* Periodic: the net charge is spread over the nodes in proportion to their
+   lengths (h_{g-1} + h_g) / 2, gauge phi[0] = phi[N] = 0. */
+void orc_solve_periodic_h(int n_cells, const double *h, const double *q_node, double *phi);
+/* Field at the particle [V/m] from the voltage drops u[c] = phi_c - phi_{c+1}
+   of the cells (ghost cells 0 beyond the walls, wrapped in a periodic box). */
+double orc_gather_ec_h(const orc_params *p, const double *u_cc, double xi);
 
 /* Isotropic scattering rotation used by the collision routines (exposed for tests). */
 void orc_rotate(const double d[3], double cos_chi, double phi, double out[3]);

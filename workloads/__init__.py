@@ -102,6 +102,42 @@ def cfg_periodic(n_cells=256, np_e=1_000_000, n0=1.0e15, length=None, dt=None, t
     return c
 
 
+# Non-uniform (multi-scale) grids, the form Sec. 4 proposes for future work:
+# node g of N sits at x_g = L (u - beta sin(2 pi u) / (2 pi)), u = g / N, so the
+# cells are about (1 - beta) L / N wide at the electrodes, where the sheaths
+# want resolving, and (1 + beta) L / N in the middle of the gap.  beta = 0 is
+# the uniform grid.  The widths go into a configuration as `cell_width`.
+def stretched_widths(n_cells: int, length: float, beta: float) -> list[float]:
+    u = np.arange(n_cells + 1, dtype=np.float64) / n_cells
+    x = length * (u - beta * np.sin(2.0 * np.pi * u) / (2.0 * np.pi))
+    x[0], x[-1] = 0.0, length
+    return np.diff(x).tolist()
+
+
+def with_stretch(cfg: dict, beta: float, name: str | None = None) -> dict:
+    """The configuration on the stretched grid of the given beta."""
+    c = dict(cfg, cell_width=stretched_widths(cfg["n_cells"], cfg["length"], beta), grid_beta=beta)
+    c["name"] = name if name is not None else "%s_stretched%g" % (cfg.get("name", "run"), beta)
+    return c
+
+
+# The production explicit discharge on a stretched grid: cells 0.5x the
+# uniform width at the electrodes and 1.5x in the bulk.
+CFG_WIDE_STRETCHED = with_stretch(CFG_WIDE_EXPLICIT, 0.5, name="ccp_512cells_2048000ppsp_stretched")
+
+
+# Collisionless periodic plasma with mobile ions on a stretched grid (the
+# non-uniform grid takes mobile ions: the frozen background of cfg_periodic
+# has no node charges there): electrons and ions loaded uniformly in x.
+def cfg_periodic_stretched(n_cells=64, np_sp=20000, n0=1.0e15, length=0.01, dt=1e-10, te_ev=2.0,
+                           beta=0.5, seed=11) -> dict:
+    c = _cfg(name="periodic_stretched_%dcells_%dppsp" % (n_cells, np_sp), n_cells=n_cells, periodic=True,
+             mcc=False, ions_mobile=True, np_init=np_sp, n0=n0, te_ev=te_ev, ti_ev=0.026,
+             pressure_mtorr=0.0, rf_freq=0.0, rf_volt=0.0, seed=seed, scheme="ec_explicit",
+             length=length, dt=dt)
+    return with_stretch(c, beta, name=c["name"] + "_b%g" % beta)
+
+
 def batch_configs(n_runs: int = 256, seed: int = 1000, scale: float = 1.0) -> list[dict]:
     """Many independent discharges of uneven size: cells uniform in 64..1024,
     macro-particles per species log-uniform in 1e4..2e6 (times `scale`),

@@ -43,6 +43,8 @@ WORKLOADS = {
     "ccp_64cells_12800ppsp": workloads.CFG_SMALL_CCP,
     # the production explicit workload with the m = 3 scheme
     "ccp_512cells_2048000ppsp_m3": dict(workloads.CFG_WIDE_EXPLICIT, scheme="ec3_explicit"),
+    # the same on a stretched grid (Sec. 4's multi-scale grid)
+    "ccp_512cells_2048000ppsp_stretched": workloads.CFG_WIDE_STRETCHED,
 }
 
 
@@ -621,11 +623,23 @@ def bench_ec3(steps=96, warmup=10):
     the fused launch alone (steps without a sort), timed like the headline
     (L2 flushed between steps), with the fused launch's share of the HBM copy
     bandwidth on the same algorithmic bytes as m = 2."""
+    return bench_fused_variant(dict(workloads.CFG_WIDE_EXPLICIT, scheme="ec3_explicit"),
+                               "ccp_512cells_2048000ppsp_ec3", steps, warmup)
+
+
+def bench_stretched(steps=96, warmup=10):
+    """The production explicit workload on a stretched grid (cells 0.5x the
+    uniform width at the electrodes, 1.5x mid-gap; Sec. 4's multi-scale
+    grid): the same particles, MCC and algorithmic bytes as the uniform grid
+    (the cell widths sit in shared memory), timed like the headline."""
+    return bench_fused_variant(workloads.CFG_WIDE_STRETCHED, "ccp_512cells_2048000ppsp_stretched", steps, warmup)
+
+
+def bench_fused_variant(cfg, label, steps, warmup):
     import torch
     from paper_1310_5284_gb300.sim import Sim
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    cfg = dict(workloads.CFG_WIDE_EXPLICIT, scheme="ec3_explicit")
     sim = Sim(cfg, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     sim.step(warmup)
@@ -647,12 +661,12 @@ def bench_ec3(steps=96, warmup=10):
     plain = [times[k] for k in range(steps) if (step0 + k + 1) % sp != 0]
     n_avg = 0.5 * (sum(d0["count"]) + sum(d1["count"]))
     sel = sum(d1["coll"]) - sum(d0["coll"])
-    bpp = algorithmic_bytes_per_particle("ec3_explicit")
+    bpp = algorithmic_bytes_per_particle(cfg.get("scheme", "ec_explicit"))
     t_push = sum(plain) / len(plain)
     achieved = (bpp["per_particle"] * n_avg + bpp["per_selected"] * sel / steps) / (t_push * 1e-3) / 1e9
     peak, kind = measured_peak()
     ms = sum(times) / steps
-    return {"workload": "ccp_512cells_2048000ppsp_ec3", "ms_per_step": ms, "launch_ms": t_push,
+    return {"workload": label, "ms_per_step": ms, "launch_ms": t_push,
             "value": n_avg / (ms * 1e-3), "unit": UNIT, "status": status,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": kind}}
@@ -737,6 +751,8 @@ def main():
         line["implicit"] = bench_implicit()
         line["ec3"] = bench_ec3()
         line["ec3"]["over_m2_value"] = line["ec3"]["value"] / line["value"]
+        line["stretched"] = bench_stretched()
+        line["stretched"]["over_uniform_value"] = line["stretched"]["value"] / line["value"]
         line["self_heating"] = bench_self_heating()
         line["paper_table1"] = bench_paper_table()
     print(json.dumps(line))

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define PIC_ABI_VERSION 2
+#define PIC_ABI_VERSION 3
 
 /* Error codes. */
 #define PIC_OK 0
@@ -135,6 +135,25 @@ typedef struct pic_config {
     double cx_vmax;          /* ion energy up to which the charge-exchange bound holds [V] */
     double eedf_max_ev;
     double iz_split_b;       /* Opal-Pollock-Wagner width B [eV] (PIC_IZ_OPAL) */
+    /* Non-uniform grid, the multi-scale grid Sec. 4 proposes for resolving
+       the sheaths without resolving the bulk: NULL for the uniform grid of
+       width length / n_cells, else a host array of n_cells cell widths [m],
+       each positive, summing to `length` within 1e-9 relative.  pic_init
+       copies it (the caller keeps ownership).  Taken by PIC_EC_EXPLICIT
+       with mobile ions, in single runs (pic_batch_init rejects it).  The
+       paper gives no form of Eq. (2)-(3) for unequal cells; this library's:
+       a particle's position stays (cell, offset in [0, 1) of that cell's
+       width); the charge assignment and the interpolation weights are those
+       of the uniform grid in that cell coordinate; the force is the
+       x-derivative of the particle's potential energy, the interpolated
+       voltage drop divided by the particle's own cell width; the field
+       solve is the Gauss law on the physical node spacing, with sum_c h_c
+       E_c = V(t) between electrodes, and in a periodic box zero with the
+       net charge spread over the nodes in proportion to (h_{g-1} + h_g)/2.
+       Energy conservation (Sec. 2) carries over.  pic_profiles divides a
+       node's charge by (h_{g-1} + h_g)/2, and the heating of a cell by its
+       width. */
+    const double *cell_width;
 } pic_config;
 
 typedef struct pic_sizes {

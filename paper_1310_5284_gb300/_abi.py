@@ -38,6 +38,7 @@ class PicConfig(ctypes.Structure):
         ("sig_exc_max", ctypes.c_double), ("iz_thr", ctypes.c_double),
         ("sig_iz_peak", ctypes.c_double), ("sig_cx", ctypes.c_double), ("eps_cap", ctypes.c_double),
         ("cx_vmax", ctypes.c_double), ("eedf_max_ev", ctypes.c_double), ("iz_split_b", ctypes.c_double),
+        ("cell_width", ctypes.POINTER(ctypes.c_double)),
     ]
 
 

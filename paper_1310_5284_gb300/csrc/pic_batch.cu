@@ -82,9 +82,9 @@ int batch_layout(const pic_config *cfgs, int nruns, BatchLayout *out) {
     for (int r = 0; r < nruns; ++r) {
         int code = validate_run_config(&cfgs[r]);
         if (code) return code;
-        if (cfgs[r].scheme == PIC_EC3_EXPLICIT) {
+        if (cfgs[r].scheme == PIC_EC3_EXPLICIT || cfgs[r].cell_width) {
             char msg[96];
-            snprintf(msg, sizeof msg, "run %d: the m = 3 scheme runs through pic_init only", r);
+            snprintf(msg, sizeof msg, "run %d: the m = 3 scheme and non-uniform grids run through pic_init only", r);
             return fail_b(nullptr, PIC_EINVAL, msg);
         }
         out->L[r] = make_run_layout(cfgs[r]);

@@ -66,6 +66,14 @@ Layout make_layout(const pic_config &c) {
     const size_t nb = (size_t)(c.births_capacity > 0 ? c.births_capacity : 1);
     L.births = take(sizeof(Birth) * nb + 8 * nb);  // records + rank and sort scratch
     L.wait_tab = take(4 * 2 * 3 * 64);
+    L.hw = L.h64 = L.xnode = L.wbg = 0;
+    if (c.cell_width) {
+        const size_t n = (size_t)c.n_cells;
+        L.hw = take(8 * n);
+        L.h64 = take(8 * n);
+        L.xnode = take(8 * n1);
+        L.wbg = take(8 * n);
+    }
     L.total = o;
     return L;
 }
@@ -132,6 +140,18 @@ int validate(const pic_config *c) {
                    c->exc_ramp_end <= c->exc_thr || !(c->iz_thr > 0)))
         return fail(PIC_EINVAL, "bad collision parameters");
     if (c->sort_period < 0 || c->diag_period < 0) return fail(PIC_EINVAL, "negative period");
+    if (c->cell_width) {
+        if (c->scheme != PIC_EC_EXPLICIT || !c->ions_mobile)
+            return fail(PIC_EINVAL, "a non-uniform grid takes PIC_EC_EXPLICIT with mobile ions");
+        double sum = 0.0;
+        for (int k = 0; k < c->n_cells; ++k) {
+            const double w = c->cell_width[k];
+            if (!(w > 0.0) || !std::isfinite(w)) return fail(PIC_EINVAL, "cell_width[%d] = %g is not a positive width", k, w);
+            sum += w;
+        }
+        if (!(std::fabs(sum - c->length) <= 1e-9 * c->length))
+            return fail(PIC_EINVAL, "cell widths sum to %.12g m, length is %.12g m", sum, c->length);
+    }
     // Eq. (1): the leapfrog push is stable only for omega_p dt < 2.
     const double wp = std::sqrt(c->n0 * kE * kE / (kEps0 * kMe));
     if (c->strict && !implicit_scheme(*c) && !(wp * c->dt < 2.0))
@@ -167,6 +187,7 @@ struct pic_handle {
     cudaGraphExec_t cycle_graph;
     int cycle_len;
     unsigned int check_host;  // pic_set_particles: the device check's flag, read back
+    std::vector<double> widths;  // the non-uniform grid's cell widths (cfg.cell_width points here)
 };
 
 namespace {
@@ -343,9 +364,46 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
     R.eedf = (unsigned long long *)(A + L.eedf);
     R.births = (Birth *)(A + L.births);
     R.st = (DevState *)(A + L.state);
+    R.dt_f = (float)c.dt;
+    R.len_f = (float)c.length;
+    R.eps0_half = 0.5 * kEps0;
+    R.inv_len = 1.0 / c.length;
+    R.stretched = c.cell_width ? 1 : 0;
+    if (R.stretched) {
+        R.hw = (const float2 *)(A + L.hw);
+        R.h64 = (const double *)(A + L.h64);
+        R.xnode = (const double *)(A + L.xnode);
+        R.wbg = (const double *)(A + L.wbg);
+    }
+}
+
+// The non-uniform grid's tables from the cell widths: (h, 1/h) in FP32 for
+// the push, h in FP64 for the field, node positions x_0 = 0, x_{g+1} = x_g +
+// h_g for the load, and for the periodic box the share W_c of the net
+// charge the nodes 0..c carry when it is spread in proportion to the node
+// lengths (h_{g-1} + h_g) / 2.
+void grid_tables(const pic_config &c, std::vector<float2> &hw, std::vector<double> &xn,
+                 std::vector<double> &wbg) {
+    const int n = c.n_cells;
+    hw.resize(n);
+    xn.assign(n + 1, 0.0);
+    wbg.resize(n);
+    double len = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const double h = c.cell_width[k];
+        hw[k] = make_float2((float)h, (float)(1.0 / h));
+        xn[k + 1] = xn[k] + h;
+        len += h;
+    }
+    double acc = 0.0;
+    for (int g = 0; g < n; ++g) {
+        acc += 0.5 * (c.cell_width[(g - 1 + n) % n] + c.cell_width[g]) / len;
+        wbg[g] = acc;
+    }
 }
 
 Mode push_mode(const pic_config &c) {
+    if (c.cell_width) return kExplicitNU;
     if (c.scheme == PIC_EC3_EXPLICIT) return kExplicitEC3;
     return c.scheme == PIC_MC_EXPLICIT ? kExplicitMC : kExplicitEC;
 }
@@ -465,6 +523,16 @@ int init_run_state(const pic_config &c, const Run &R, unsigned char *arena, size
         wait_thresholds(R.p_null[1], tab[1]);
     }
     CKE(cudaMemcpyAsync((void *)R.wait_tab, tab, sizeof tab, cudaMemcpyHostToDevice, s));
+    std::vector<float2> hw;
+    std::vector<double> xn, wbg;
+    if (R.stretched) {
+        grid_tables(c, hw, xn, wbg);
+        const size_t n = (size_t)c.n_cells;
+        CKE(cudaMemcpyAsync((void *)R.hw, hw.data(), 8 * n, cudaMemcpyHostToDevice, s));
+        CKE(cudaMemcpyAsync((void *)R.h64, c.cell_width, 8 * n, cudaMemcpyHostToDevice, s));
+        CKE(cudaMemcpyAsync((void *)R.xnode, xn.data(), 8 * (n + 1), cudaMemcpyHostToDevice, s));
+        CKE(cudaMemcpyAsync((void *)R.wbg, wbg.data(), 8 * n, cudaMemcpyHostToDevice, s));
+    }
     CKE(cudaStreamSynchronize(s));
     const double vth_e = std::sqrt(kE * c.te_ev / kMe);
     const double vth_i = std::sqrt(kE * c.ti_ev / (c.ion_mass_amu * kAmu));
@@ -498,18 +566,29 @@ int run_profiles(const Run &R, const pic_config &c, cudaStream_t s, double *ne, 
     };
     CKE(fetch(ne, R.avg_ne, n1, R.dens_scale / na));
     CKE(fetch(ni, R.avg_ni, n1, R.dens_scale / na));
+    const bool periodic = c.boundary == PIC_BC_PERIODIC;
+    if (c.cell_width) {
+        // a node's charge spread over its length (h_{g-1} + h_g) / 2 (the wall
+        // nodes take their one cell twice, as the uniform grid's take dx)
+        for (size_t g = 0; g < n1; ++g) {
+            const double hl = periodic ? c.cell_width[(g + n - 1) % n] : c.cell_width[g > 0 ? g - 1 : 0];
+            const double hr = periodic ? c.cell_width[g % n] : c.cell_width[g < n ? g : n - 1];
+            const double f = R.dx / (0.5 * (hl + hr));
+            if (ne) ne[g] *= f;
+            if (ni) ni[g] *= f;
+        }
+    }
     CKE(fetch(heat_e, R.heat[0], n, 1.0 / nd));
     CKE(fetch(heat_i, R.heat[1], n, 1.0 / nd));
     if (phi) {
         // the averaged potential follows linearly from the averaged field and
-        // electrode voltage: phi_g = <V> - dx sum_{c<g} <E_c>
+        // electrode voltage: phi_g = <V> - sum_{c<g} h_c <E_c>
         std::vector<double> e(n);
         CKE(fetch(e.data(), R.avg_e, n, 1.0 / na));
-        const bool periodic = c.boundary == PIC_BC_PERIODIC;
         double acc = periodic ? 0.0 : st.v_sum / na;
         for (size_t g = 0; g < n; ++g) {
             phi[g] = acc;
-            acc -= R.dx * e[g];
+            acc -= (c.cell_width ? c.cell_width[g] : R.dx) * e[g];
         }
         phi[n] = periodic ? phi[0] : 0.0;
     }
@@ -590,6 +669,10 @@ int pic_init(const pic_config *cfg, const pic_buffers *bufs, void *stream, pic_h
     if (((uintptr_t)bufs->arena & 255u) != 0) return fail(PIC_ENOMEM, "arena not 256-byte aligned");
     pic_handle *h = new pic_handle();
     h->cfg = *cfg;
+    if (cfg->cell_width) {  // the caller's array may go away after this call
+        h->widths.assign(cfg->cell_width, cfg->cell_width + cfg->n_cells);
+        h->cfg.cell_width = h->widths.data();
+    }
     h->layout = L;
     h->arena = (unsigned char *)bufs->arena;
     h->arena_bytes = L.total;
@@ -699,7 +782,7 @@ int pic_grids(pic_handle *h, int64_t *rho_q_e, int64_t *rho_q_i, double *phi, do
     if (rho_q_i) CK(h, cudaMemcpy(rho_q_i, h->run.rho_q[1], 8 * n1, cudaMemcpyDeviceToHost));
     if (e_cc) CK(h, cudaMemcpy(e_cc, h->run.e_cc, 8 * n, cudaMemcpyDeviceToHost));
     if (phi) {
-        // node potential from the cell-centred field: phi_g = V - dx sum_{c<g} E_c
+        // node potential from the cell-centred field: phi_g = V - sum_{c<g} h_c E_c
         std::vector<double> e(n);
         DevState st;
         CK(h, cudaMemcpy(e.data(), h->run.e_cc, 8 * n, cudaMemcpyDeviceToHost));
@@ -708,7 +791,7 @@ int pic_grids(pic_handle *h, int64_t *rho_q_e, int64_t *rho_q_i, double *phi, do
         double acc = periodic ? 0.0 : st.v_left;
         for (size_t g = 0; g < n; ++g) {
             phi[g] = acc;
-            acc -= h->run.dx * e[g];
+            acc -= (h->cfg.cell_width ? h->cfg.cell_width[g] : h->run.dx) * e[g];
         }
         phi[n] = periodic ? phi[0] : 0.0;
     }

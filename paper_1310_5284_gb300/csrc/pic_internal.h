@@ -42,6 +42,7 @@ enum Mode : int {
     kImplicit2MC = 7,
     kExplicitEC3 = 8,  // explicit EC with m = 3: S_3 assignment, S_2 interpolation
     kDepositEC3 = 9,
+    kExplicitNU = 10,  // explicit EC on a non-uniform grid (cell widths h_c)
 };
 
 // The cell word of a particle.  A hole left by an absorbed particle is -1.
@@ -174,6 +175,16 @@ struct Run {
     unsigned long long *eedf;
     Birth *births;
     DevState *st;
+    // non-uniform grid (stretched != 0; the pointers are in the arena)
+    int stretched;
+    float dt_f;            // dt (FP32)
+    float len_f;           // L (FP32)
+    double inv_len;        // 1 / L
+    double eps0_half;      // eps0 / 2 (field energy sum_c h_c E_c^2)
+    const float2 *hw;      // [n_cells] (h_c, 1/h_c) in FP32 for the push
+    const double *h64;     // [n_cells] h_c
+    const double *xnode;   // [n_cells + 1] node positions, x_0 = 0
+    const double *wbg;     // [n_cells] periodic box: share of the net charge on nodes 0..c
 };
 
 // Byte offsets of one run's buffers inside its arena.
@@ -182,6 +193,7 @@ struct Layout {
     size_t sp[2][2][7];  // [parity][species][field] offsets (cell, off, vx, vy, vz, id, abar)
     size_t acc_cnt[2], acc_a[2], acc_b[2], acc_c[2], cursor[2], rho_q[2];
     size_t e_gather, e_cc, chi, avg_ne, avg_ni, avg_e, heat[2], eedf, births, e_hi, e_lo, wait_tab;
+    size_t hw, h64, xnode, wbg;  // non-uniform grid tables (0 bytes on the uniform grid)
     size_t total;
 };
 

@@ -700,6 +700,7 @@ struct SmemMain {
     unsigned int *eedf;        // [bins+1]
     CollQueue q;
     const uint32_t *wtab;      // [2][3][64] waiting-time thresholds (static shared memory)
+    float2 *hw;                // non-uniform grid: [n] (h_c, 1/h_c)
 };
 
 constexpr int kWaitTab = 2 * 3 * 64;
@@ -713,9 +714,10 @@ __device__ __forceinline__ void load_wait_tab(const Run &R, uint32_t *dst) {
 
 __host__ __device__ inline size_t align8(size_t x) { return (x + 7) & ~size_t(7); }
 
-__host__ __device__ inline size_t main_smem_bytes(int n, int bins, bool ec3) {
+__host__ __device__ inline size_t main_smem_bytes(int n, int bins, bool ec3, bool nu = false) {
     return align8(4 * (size_t)(n + 2)) + (ec3 ? 7 : 4) * align8(4 * (size_t)(n + 1)) +
-           align8(4 * (size_t)n) + align8(4 * (size_t)(bins + 1)) + 4 * (size_t)kQueue + 16;
+           align8(4 * (size_t)n) + align8(4 * (size_t)(bins + 1)) + 4 * (size_t)kQueue + 16 +
+           (nu ? 8 + 8 * (size_t)n : 0);
 }
 
 // The tail's scratch: the field solve's arrays (32 bytes a node), or, before
@@ -732,9 +734,11 @@ __host__ __device__ inline size_t tail_stage_bytes(int n, bool ec3 = false) {
     return ((size_t)(ec3 ? 64 : 48) * (n + 1) + 255) & ~size_t(255);
 }
 
-__device__ SmemMain carve_main(unsigned char *base, int n, int bins, bool ec3, const uint32_t *wtab) {
+__device__ SmemMain carve_main(unsigned char *base, int n, int bins, bool ec3, const uint32_t *wtab,
+                               bool nu = false) {
     SmemMain s;
     s.wtab = wtab;
+    s.hw = nullptr;
     size_t o = 0;
     s.e = (float *)(base + o);
     o += align8(4 * (size_t)(n + 2));
@@ -759,6 +763,7 @@ __device__ SmemMain carve_main(unsigned char *base, int n, int bins, bool ec3, c
     o += 4 * (size_t)kQueue;
     s.q.n = (unsigned int *)(base + o);
     s.q.cap = (unsigned int)kQueue;
+    if (nu) s.hw = (float2 *)(base + align8(o + 16));
     return s;
 }
 
@@ -767,15 +772,18 @@ struct ModeInfo {
     static constexpr bool pass1 = (MODE == kImplicit1 || MODE == kImplicit1MC);
     static constexpr bool pass2 = (MODE == kImplicit2 || MODE == kImplicit2MC);
     static constexpr bool ec3 = (MODE == kExplicitEC3 || MODE == kDepositEC3);
+    static constexpr bool nu = (MODE == kExplicitNU);  // non-uniform grid
     static constexpr bool deposit = (MODE == kDepositEC || MODE == kDepositMC || MODE == kDepositEC3);
     static constexpr bool push = !(deposit || pass1);
-    static constexpr bool needs_field = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kExplicitEC3 || pass2);
+    static constexpr bool needs_field = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kExplicitEC3 ||
+                                         MODE == kExplicitNU || pass2);
     static constexpr bool implicit = pass1 || pass2;
     static constexpr bool count_only = pass2;
     static constexpr bool mc = (MODE == kExplicitMC || MODE == kDepositMC || MODE == kImplicit1MC ||
                                 MODE == kImplicit2MC);
     static constexpr bool loads_v = !deposit;
-    static constexpr bool explicit_push = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kExplicitEC3);
+    static constexpr bool explicit_push = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kExplicitEC3 ||
+                                           MODE == kExplicitNU);
 };
 
 // Renormalise an offset that left [0, 1) into the cell index.
@@ -789,6 +797,58 @@ __device__ __forceinline__ void renormalise(int &c, float &s) {
             c += 1;
         }
     }
+}
+
+// A move by d metres on the non-uniform grid that leaves the particle's cell
+// (c, s): walk cell by cell with the distance left, from the cell's left
+// node (d >= 0) or right node (d < 0).  Returns 0 <= s < 1 inside the grid,
+// or c = -1 / c = N past an electrode; wraps in the periodic box.  At most
+// N + 2 cells are visited (|d| < L after the wrap or the electrode test).
+__device__ __noinline__ void walk_nu(const float2 *hw, int N, bool periodic, float len, int &c, float &s,
+                                     float d) {
+    constexpr float kBelowOne = 0.99999994f;  // the largest FP32 below 1
+    if (periodic) {
+        d = fmodf(d, len);
+    } else if (!(fabsf(d) < len)) {  // beyond the gap (or not a number)
+        c = d > 0.0f ? N : -1;
+        s = 0.0f;
+        return;
+    }
+    int k = c;
+    if (d >= 0.0f) {
+        float r = fmaf(s, hw[k].x, d);  // from the left node of cell k
+        for (int it = 0; it < N + 2; ++it) {
+            const float2 h = hw[k];
+            if (r < h.x) {
+                c = k;
+                s = fminf(fmaxf(r * h.y, 0.0f), kBelowOne);
+                return;
+            }
+            r -= h.x;
+            if (++k == N) {
+                if (!periodic) break;
+                k = 0;
+            }
+        }
+        c = N;  // past the right electrode
+    } else {
+        float l = fmaf(1.0f - s, hw[k].x, -d);  // back from the right node of cell k
+        for (int it = 0; it < N + 2; ++it) {
+            const float2 h = hw[k];
+            if (l <= h.x) {
+                c = k;
+                s = fminf(fmaxf(1.0f - l * h.y, 0.0f), kBelowOne);
+                return;
+            }
+            l -= h.x;
+            if (--k < 0) {
+                if (!periodic) break;
+                k = N - 1;
+            }
+        }
+        c = -1;  // past the left electrode
+    }
+    s = 0.0f;
 }
 
 // EC force interpolation, Eq. (3) with m = 2: S_1 from the cell-centred field
@@ -929,6 +989,21 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         // particle is that of the field (m/q) abar^n, not of E^{n+1}
         e_field = abar * k.mq;
         if (diag && inside) atomicAdd(&sm.heat[c], k.qw * e_field * 0.5f * (v_old + v_new));
+    } else if (MI::nu) {
+        // non-uniform grid: the table holds the cells' voltage drops; the
+        // force is their S_1 interpolation over the particle's own cell
+        // width (the x-derivative of its potential energy), and the move is
+        // d / h_c of the cell unless it leaves the cell
+        const float2 hc = sm.hw[c0];
+        e_field = gather_ec(sm.e, c0, off) * hc.y;
+        v_new = fmaf(k.qm_dt, e_field, vx);
+        if (diag) atomicAdd(&sm.heat[c0], k.qw * e_field * 0.5f * (v_old + v_new));
+        const float d = v_new * R.dt_f;
+        s = fmaf(d, hc.y, off);
+        if (!(s >= 0.0f && s < 1.0f)) {
+            s = off;
+            walk_nu(sm.hw, N, R.periodic != 0, R.len_f, c, s, d);
+        }
     } else {
         // explicit leapfrog with E^n at x^n (Sec. 2 schemes (1), (2))
         e_field = MI::mc ? (1.0f - off) * sm.e[c0] + off * sm.e[c0 + 1]
@@ -939,8 +1014,10 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
     }
     kx += 0.5f * (v_old * v_old + v_new * v_new);  // kept in registers: t lives in memory
     pw += k.qw * e_field * 0.5f * (v_old + v_new);
-    if (!(fabsf(s) < 1.0e6f)) s = (float)(2 * N + 2);
-    renormalise(c, s);
+    if (!MI::nu) {
+        if (!(fabsf(s) < 1.0e6f)) s = (float)(2 * N + 2);
+        renormalise(c, s);
+    }
     vx = v_new;
     off = s;
     // electrodes (Sec. 3) or periodic wrap
@@ -1911,6 +1988,7 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
     constexpr bool ec3 = ModeInfo<MODE>::ec3;
     constexpr bool implicit = ModeInfo<MODE>::implicit;
     if (threadIdx.x == 0) s_vl = vl_ok ? vl : electrode_volt(R, level);
+    if (R.stretched) defer = false;  // the non-uniform grid's field is finished here
     const bool acc_now = accumulate && (implicit || !defer);
     // node charges, densities, susceptibility (pointers and scalars held in
     // registers: the stores below cannot alias them)
@@ -2060,6 +2138,50 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
             P += (R.periodic || c >= 1) ? q[c] : 0ll;
             q[c] = P;  // this thread's own cells only
         }
+    }
+    if (R.stretched) {
+        // Non-uniform grid, FP64: E_c = D_0 + kappa (P_c - Q W_c), where the
+        // periodic box spreads the net charge Q over the nodes in proportion
+        // to their lengths (W_c: the share of nodes 0..c; no spreading between
+        // electrodes), and D_0 makes sum_c h_c E_c = V (zero in the box).
+        const double qnet = R.periodic ? (double)totP : 0.0;
+        double sh = 0.0;
+        for (int k = 0; k < per; ++k) {
+            const int c = c_begin + k;
+            if (c < n) {
+                const double pc = (double)q[c] - qnet * R.wbg[c];
+                pp[c] = pc;
+                sh += R.h64[c] * pc;
+            }
+        }
+        sh = block_sum_lean(sh, sc_d);
+        const double d0 = ((R.periodic ? 0.0 : s_vl.v) - R.kappa * sh) * R.inv_len;
+        double wsum = 0.0;
+        for (int k = 0; k < per; ++k) {
+            const int c = c_begin + k;
+            if (c < n) {
+                const double hc = R.h64[c];
+                const double e = d0 + R.kappa * pp[c];
+                pp[c] = e * hc;  // the cell's voltage drop, the gather table's entry
+                wsum += e * e * hc;
+                if (dry) continue;
+                R.e_gather[c + 1] = (float)(e * hc);
+                R.e_cc[c] = e;
+                if (accumulate) atomicAdd(&R.avg_e[c], e);
+            }
+        }
+        wsum = block_sum_lean(wsum, sc_d);  // includes the barrier that publishes pp[]
+        if (threadIdx.x == 0 && !dry) {
+            R.e_gather[0] = R.periodic ? (float)pp[n - 1] : 0.0f;
+            R.e_gather[n + 1] = R.periodic ? (float)pp[0] : 0.0f;
+            st->v_left = s_vl.v;
+            if (ModeInfo<MODE>::explicit_push) st->field_energy_push = st->field_energy;
+            st->field_energy = R.eps0_half * wsum;
+            if (accumulate) st->v_sum += s_vl.v;
+            st->pending = 0u;
+        }
+        __syncthreads();
+        return;
     }
     const dw sum_p = dw_add(dw_mul(dw_from_i64(tot_hi), dw{4294967296.0f, 0.0f}), dw_from_i64((long long)tot_lo));
     const dw mean_p = dw_mul(sum_p, dw_of(R.inv_n_ff));
@@ -2540,7 +2662,7 @@ __device__ void stream_flush(const Run &R, const SmemMain &sm, int S, bool diag,
         __syncthreads();
         for (int k = threadIdx.x; k < R.n_cells; k += kThreads) {
             const float h = sm.heat[k];
-            if (h != 0.0f) atomicAdd(&R.heat[S][k], (double)h / R.dx);
+            if (h != 0.0f) atomicAdd(&R.heat[S][k], (double)h / (MI::nu ? R.h64[k] : R.dx));
             sm.heat[k] = 0.0f;
         }
         __syncthreads();
@@ -2660,7 +2782,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == kExplicitEC3 || MODE == kDe
     const Stream ms = {s_ms_S, s_ms_o, s_ms_n};
     unsigned char *smem = smem_all + ring_bytes(MI::implicit);  // grid, accumulators, queue; the tail's space
     __shared__ uint32_t s_wtab[kWaitTab];
-    const SmemMain sm = carve_main(smem, n, R.eedf_bins, MI::ec3, s_wtab);
+    const SmemMain sm = carve_main(smem, n, R.eedf_bins, MI::ec3, s_wtab, MI::nu);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1u);
         s_uses = 0u;
@@ -2672,6 +2794,8 @@ __global__ void __launch_bounds__(kThreads, (MODE == kExplicitEC3 || MODE == kDe
     // shared-memory grid
     if (MI::needs_field)
         for (int k = threadIdx.x; k < n + 2; k += kThreads) sm.e[k] = R.e_gather[k];
+    if (MI::nu)
+        for (int k = threadIdx.x; k < n; k += kThreads) sm.hw[k] = R.hw[k];
     if (MI::push) load_wait_tab(R, s_wtab);
     for (int k = threadIdx.x; k <= n; k += kThreads) {
         sm.acc.cnt[k] = 0u;
@@ -2847,9 +2971,36 @@ __global__ void k_load(Run R, int S, long long count, float vth) {
         const uint4 w = draw(R, (uint32_t)i, 0, S, kTagLoad, 0);
         const uint4 w2 = draw(R, (uint32_t)i, 0, S, kTagLoad, 1);
         const unsigned long long t = (unsigned long long)w.x * (unsigned long long)R.n_cells;
+        int cell = (int)(t >> 32);
+        float off = (float)((uint32_t)t >> 8) * 5.9604644775390625e-8f;
+        if (R.stretched) {
+            // non-uniform grid: uniform in x = (w / 2^32) L; the cell by
+            // bisection over the node positions, the offset rounded to FP32
+            const double x = ldexp((double)w.x, -32) * R.xnode[R.n_cells];
+            int lo = 0, hi = R.n_cells;  // xnode[lo] <= x < xnode[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (R.xnode[mid] <= x)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            double o = (x - R.xnode[lo]) / R.h64[lo];
+            if (o >= 1.0) o = 0.99999999999999989;  // rounding at the right node
+            cell = lo;
+            off = (float)o;
+            if (off >= 1.0f) {  // rounds onto the next node
+                if (cell + 1 < R.n_cells) {
+                    off = 0.0f;
+                    cell += 1;
+                } else {
+                    off = 0.99999994f;  // stays below x = L
+                }
+            }
+        }
         // the first wait to a null-collision selection is drawn at the load
-        sp.cell[i] = (int32_t)(t >> 32) | (R.mcc ? (int32_t)wait_bits(draw_wait(R, R.wait_tab, S, (uint32_t)i, 0, 1)) : 0);
-        sp.off[i] = (float)((uint32_t)t >> 8) * 5.9604644775390625e-8f;
+        sp.cell[i] = cell | (R.mcc ? (int32_t)wait_bits(draw_wait(R, R.wait_tab, S, (uint32_t)i, 0, 1)) : 0);
+        sp.off[i] = off;
         float n1, n2, n3, n4;
         box_muller(u24c(w.y), u24c(w.z), n1, n2);
         box_muller(u24c(w.w), u24c(w2.x), n3, n4);
@@ -3206,7 +3357,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const Run *__restrict__ r
 // ---------------------------------------------------------------------------
 int block_smem_bytes(const Run &r) {
     const bool implicit = r.scheme == 2 || r.scheme == 3, ec3 = r.scheme == 4;
-    const size_t a = ring_bytes(implicit) + main_smem_bytes(r.n_cells, r.eedf_bins, ec3);
+    const size_t a = ring_bytes(implicit) + main_smem_bytes(r.n_cells, r.eedf_bins, ec3, r.stretched != 0);
     const size_t b = tail_stage_bytes(r.n_cells, ec3) + tail_smem_bytes(r.n_cells);
     return (int)(a > b ? a : b);
 }
@@ -3232,6 +3383,7 @@ cudaError_t launch_particles(const Run &r, Mode m, int grid, cudaStream_t s) {
         case kImplicit2MC: return launch_mode<kImplicit2MC>(r, grid, s);
         case kExplicitEC3: return launch_mode<kExplicitEC3>(r, grid, s);
         case kDepositEC3: return launch_mode<kDepositEC3>(r, grid, s);
+        case kExplicitNU: return launch_mode<kExplicitNU>(r, grid, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -3267,7 +3419,7 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    for (int k = 0; k < 10; ++k) {  // raise the shared-memory limit of every mode
+    for (int k = 0; k < 11; ++k) {  // raise the shared-memory limit of every mode
         int dummy = 0;
         switch (k) {
             case 0: e = occ<kExplicitEC>(r, &dummy); break;
@@ -3279,7 +3431,8 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
             case 6: e = occ<kImplicit1MC>(r, &dummy); break;
             case 7: e = occ<kImplicit2MC>(r, &dummy); break;
             case 8: e = occ<kExplicitEC3>(r, &dummy); break;
-            default: e = occ<kDepositEC3>(r, &dummy); break;
+            case 9: e = occ<kDepositEC3>(r, &dummy); break;
+            default: e = occ<kExplicitNU>(r, &dummy); break;
         }
         if (e != cudaSuccess) return e;
     }
@@ -3294,6 +3447,7 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
         case kImplicit2MC: e = occ<kImplicit2MC>(r, &per); break;
         case kExplicitEC3: e = occ<kExplicitEC3>(r, &per); break;
         case kDepositEC3: e = occ<kDepositEC3>(r, &per); break;
+        case kExplicitNU: e = occ<kExplicitNU>(r, &per); break;
     }
     if (e != cudaSuccess) return e;
     *grid = sms * (per > 0 ? per : 1);

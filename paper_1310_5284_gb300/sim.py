@@ -61,6 +61,15 @@ def make_config(cfg: dict) -> _abi.PicConfig:
     c.collision_model = (_abi.IZ_OPAL if cfg.get("iz_split", "equal") == "opal" else 0) | \
         (_abi.SCATTER_VS if cfg.get("scattering", "isotropic") == "vahedi_surendra" else 0)
     c.iz_split_b = float(cfg.get("iz_split_b", 10.0))
+    if cfg.get("cell_width") is not None:
+        # non-uniform grid: the array stays referenced by the struct
+        import numpy as np
+
+        h = np.ascontiguousarray(cfg["cell_width"], dtype=np.float64)
+        if h.shape != (c.n_cells,):
+            raise ValueError("cell_width must hold n_cells widths")
+        c._cell_width = h
+        c.cell_width = h.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     return c
 
 

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(abi):
 
 
 def test_version_and_build_info(abi):
-    assert abi.lib().pic_version() == 2
+    assert abi.lib().pic_version() == 3
     assert b"sm_103a" in abi.lib().pic_build_info()
 
 
@@ -134,3 +134,31 @@ def test_set_state_rejects_null_arguments_before_any_device_work(abi):
     hp = abi.PicHostParticles()
     assert abi.lib().pic_set_state(None, ctypes.byref(hp), ctypes.byref(hp)) == -1
     assert abi.lib().pic_set_particles(None, 0, ctypes.byref(hp)) == -1
+
+
+def test_non_uniform_grid_configs(abi):
+    """cell_width: positive widths summing to the gap, the explicit EC scheme
+    with mobile ions, single runs; the arena grows by the grid's tables."""
+    from paper_1310_5284_gb300.sim import make_config
+    base = dict(workloads.CFG_SMALL_CCP)
+    s = abi.PicSizes()
+    c = make_config(base)
+    assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == 0
+    uniform = s.arena_bytes
+    good = workloads.with_stretch(base, 0.6)
+    c = make_config(good)
+    assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == 0
+    assert s.arena_bytes > uniform
+    n, length = base["n_cells"], base["length"]
+    for bad in ([length / n] * (n - 1) + [0.0],                      # an empty cell
+                [length / n] * (n - 1) + [-length / n],              # a negative width
+                [1.01 * length / n] * n,                              # widths do not sum to the gap
+                [length / n] * (n - 1) + [float("nan")]):
+        c = make_config(dict(base, cell_width=bad))
+        assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == -1
+    for over in (dict(scheme="mc_explicit"), dict(scheme="ec_implicit"), dict(scheme="ec3_explicit"),
+                 dict(ions_mobile=False, mcc=False, bg_density=1e15)):
+        c = make_config(dict(good, **over))
+        assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == -1, over
+    arr = (abi.PicConfig * 1)(make_config(good))
+    assert abi.lib().pic_batch_required_sizes(arr, 1, ctypes.byref(s)) == -1

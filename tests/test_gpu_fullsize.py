@@ -55,19 +55,23 @@ CASES = [
     # the direct-implicit workload (128 cells, 1,024,000 per species,
     # omega_p dt = 2, predictor and corrector launches)
     ("ccp_128cells_implicit", "ec_implicit", 3),
+    # the production explicit workload on a stretched grid (cells 0.5x the
+    # uniform width at the electrodes, 1.5x mid-gap; Sec. 4's multi-scale grid)
+    ("ccp_512cells_2048000ppsp_stretched", "ec_explicit", 5),
 ]
+BASES = {c["name"]: c for c in (workloads.CFG_WIDE_EXPLICIT, workloads.CFG_IMPLICIT, workloads.CFG_WIDE_STRETCHED)}
 
 
 @pytest.mark.parametrize("name,scheme,steps", CASES, ids=["%s-%s" % (c[0], c[1]) for c in CASES])
 def test_full_size_load_charge_and_steps_match_oracle(name, scheme, steps):
     from paper_1310_5284_gb300.sim import Sim
-    base = workloads.CFG_WIDE_EXPLICIT if name == workloads.CFG_WIDE_EXPLICIT["name"] else workloads.CFG_IMPLICIT
-    assert base["name"] == name
+    base = BASES[name]
     cfg = dict(base, scheme=scheme)
     implicit = scheme == "ec_implicit"
     n = cfg["np_init"]
     gpu = Sim(cfg, device="cuda:0")
-    # the load: positions are exact (24-bit offsets) and keyed on the id
+    # the load: positions are exact (24-bit offsets, or on the stretched grid
+    # FP32 offsets decided in FP64 alike) and keyed on the id
     ref = oracle.Sim(cfg).load(n, n)
     for k, sp in enumerate(("e", "i")):
         a = by_id(gpu.get_particles(sp))

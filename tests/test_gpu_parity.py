@@ -30,6 +30,28 @@ def _built():
     __graft_entry__.build()
 
 
+def with_grid(cfg):
+    """A configuration with `grid_beta` gets the stretched grid of that beta
+    (non-uniform cells, Sec. 4) as its cell widths."""
+    if cfg.get("grid_beta") is not None and cfg.get("cell_width") is None:
+        cfg = dict(cfg, cell_width=workloads.stretched_widths(cfg["n_cells"], cfg["length"], cfg["grid_beta"]))
+    return cfg
+
+
+def node_lengths(cfg, dx):
+    """The length a node's charge is spread over in the densities: dx, or on
+    a non-uniform grid (h_{g-1} + h_g)/2 (wall nodes: their one cell;
+    periodic: wrapped)."""
+    if cfg.get("cell_width") is None:
+        return dx
+    h = np.asarray(cfg["cell_width"], dtype=np.float64)
+    n = h.size
+    g = np.arange(n + 1)
+    if cfg.get("periodic"):
+        return 0.5 * (h[(g - 1) % n] + h[g % n])
+    return 0.5 * (h[np.maximum(g - 1, 0)] + h[np.minimum(g, n - 1)])
+
+
 def gpu_sim(cfg):
     from paper_1310_5284_gb300.sim import Sim
     return Sim(cfg, device="cuda:0")
@@ -302,8 +324,7 @@ def one_step_diagnostics(gpu, cfg, eedf_tol=None):
         errs["phi_avg_of_scale"] = _of_scale(pg["phi"], o1["phi"])
         # one step's averages: the potential and densities of the new field
         np.testing.assert_allclose(pg["phi"], o1["phi"], rtol=0, atol=1e-9 * max(np.abs(o1["phi"]).max(), 1e-300))
-        pn = o2.averages()  # nothing averaged yet: compare against the charge itself
-        unit = der["weight"] / der["dx"] / oracle.charge_unit(cfg)
+        unit = der["weight"] / node_lengths(cfg, der["dx"]) / oracle.charge_unit(cfg)
         for key, q in (("ne", o1["rho_q_e"]), ("ni", o1["rho_q_i"])):
             ref = q.astype(np.float64) * unit
             np.testing.assert_allclose(pg[key], ref, rtol=1e-12, atol=1e-12 * max(np.abs(ref).max(), 1e-300))
@@ -333,10 +354,12 @@ def one_step_diagnostics(gpu, cfg, eedf_tol=None):
     diag_step = cfg.get("diag_period", 0) > 0 and d0["step"] % cfg["diag_period"] == 0
     if diag_step:
         po = orc.averages()
+        cw = np.asarray(cfg["cell_width"]) if cfg.get("cell_width") is not None else der["dx"]
         for k, key in enumerate(("heat_e", "heat_i")):
             scale = abs(der["q"][k]) * der["weight"] * emax * float(np.abs(st[k]["vx"].astype(np.float64)).sum())
-            assert np.abs(pg[key] - po[key]).sum() * der["dx"] <= 1e-5 * scale + 1e-30, key
-            errs[key + "_of_scale"] = float(np.abs(pg[key] - po[key]).sum() * der["dx"] / max(scale, 1e-300))
+            dev = float((np.abs(pg[key] - po[key]) * cw).sum())
+            assert dev <= 1e-5 * scale + 1e-30, key
+            errs[key + "_of_scale"] = dev / max(scale, 1e-300)
         if cfg.get("eedf_bins", 0) > 0:
             diff = np.abs(pg["eedf"].astype(np.int64) - po["eedf"].astype(np.int64)).sum()
             assert diff <= (eedf_tol if eedf_tol is not None else 4), diff
@@ -378,6 +401,25 @@ def test_uniform_load_matches_oracle():
     assert np.array_equal(g["rho_q_e"], o["rho_q_e"]) and np.array_equal(g["rho_q_i"], o["rho_q_i"])
 
 
+def test_stretched_load_matches_oracle():
+    """The load on a non-uniform grid is uniform in x: the cell by bisection
+    over the node positions and the FP32 offset, both decided in FP64 from
+    the same Philox word, so positions agree exactly."""
+    cfg = workloads.with_stretch(dict(workloads.CFG_SMALL_CCP, mcc=False), 0.6)
+    gpu = gpu_sim(cfg)
+    orc = oracle.Sim(cfg).load(cfg["np_init"], cfg["np_init"])
+    for k, sp in enumerate(("e", "i")):
+        a = by_id(gpu.get_particles(sp))
+        b = by_id(orc.get_species(sp))
+        xa = a["cell"].astype(np.float64) + a["off"].astype(np.float64)
+        assert np.array_equal(xa, b["xi"])
+        for comp in ("vx", "vy", "vz"):
+            np.testing.assert_allclose(a[comp], b[comp], rtol=2e-6, atol=2e-6 * vth(cfg, k))
+    g, o = gpu.grids(), orc.grids()
+    assert np.array_equal(g["rho_q_e"], o["rho_q_e"]) and np.array_equal(g["rho_q_i"], o["rho_q_i"])
+    np.testing.assert_allclose(g["e_cc"], o["e_cc"], rtol=0, atol=1e-9 * np.abs(o["e_cc"]).max())
+
+
 # ------------------------------------------------------------------ deposit + field
 DEPOSIT_CASES = [
     ("ec_dirichlet_64", dict(n_cells=64), 12_800, False),
@@ -393,6 +435,11 @@ DEPOSIT_CASES = [
     ("ec3_dirichlet_1024_sorted", dict(n_cells=1024, scheme="ec3_explicit"), 300_001, True),
     ("ec3_periodic_3", dict(n_cells=3, periodic=True, rf_volt=0.0, scheme="ec3_explicit"), 1_001, False),
     ("ec3_tiny_2cells", dict(n_cells=2, scheme="ec3_explicit"), 5, False),
+    # non-uniform grids (cells (1 -/+ beta) L/N at the electrodes / mid-gap)
+    ("nu_dirichlet_64_b06", dict(n_cells=64, grid_beta=0.6), 12_800, False),
+    ("nu_periodic_100_b05", dict(n_cells=100, periodic=True, rf_volt=0.0, grid_beta=0.5), 10_007, False),
+    ("nu_dirichlet_1024_sorted_b07", dict(n_cells=1024, grid_beta=0.7), 300_001, True),
+    ("nu_tiny_2cells", dict(n_cells=2, cell_width=[0.006, 0.014]), 5, False),
 ]
 
 
@@ -400,6 +447,7 @@ DEPOSIT_CASES = [
 def test_deposit_bitexact_and_field(name, over, n, srt):
     cfg = dict(workloads.CFG_SMALL_CCP, mcc=False, np_init=n)
     cfg.update(over)
+    cfg = with_grid(cfg)
     gpu = gpu_sim(cfg)
     orc = oracle.Sim(cfg, cap_e=n + 16, cap_i=n + 16)
     inject(gpu, orc, cfg, states_for(cfg, n, 100 + n, sorted_cells=srt), step=37)
@@ -450,6 +498,10 @@ STEP_CASES = [
                                         scheme="ec3_explicit"), 30, 100),
     ("ec3_electrodes_rf_collisionless", dict(n_cells=64, mcc=False, scheme="ec3_explicit"), 30, 100),
     ("ec3_ragged_37", dict(n_cells=37, mcc=False, scheme="ec3_explicit"), 30, 60),
+    ("nu_periodic_collisionless_b06", dict(n_cells=64, periodic=True, mcc=False, rf_volt=0.0, grid_beta=0.6),
+     30, 100),
+    ("nu_electrodes_rf_collisionless_b06", dict(n_cells=64, mcc=False, grid_beta=0.6), 30, 100),
+    ("nu_ragged_37_b08", dict(n_cells=37, mcc=False, grid_beta=0.8), 30, 60),
 ]
 
 
@@ -464,6 +516,7 @@ def test_steps_match_oracle(name, over, strict, steps):
     divergence under FP32 rounding (99th percentile and maximum)."""
     cfg = dict(workloads.CFG_SMALL_CCP, np_init=12_800, sort_period=8)
     cfg.update(over)
+    cfg = with_grid(cfg)
     n = cfg["np_init"]
     gpu = gpu_sim(cfg)
     orc = oracle.Sim(cfg)
@@ -539,6 +592,7 @@ COLLISION_CASES = [
     ("ec_explicit", dict(iz_split="opal")),
     ("ec_explicit", dict(scattering="vahedi_surendra")),
     ("ec_implicit", dict(iz_split="opal", scattering="vahedi_surendra", te_ev=10.0)),
+    ("ec_explicit", dict(grid_beta=0.6)),  # non-uniform grid
 ]
 
 
@@ -551,6 +605,7 @@ def test_collisions_counts_exact_and_births_ranked(scheme, opts):
     cfg = dict(workloads.CFG_SMALL_CCP, np_init=20_000, sort_period=4, te_ev=6.0, scheme=scheme,
                diag_period=1, eedf_bins=40)
     cfg.update(opts)
+    cfg = with_grid(cfg)
     n = cfg["np_init"]
     gpu = gpu_sim(cfg)
     orc = oracle.Sim(cfg)
@@ -603,12 +658,15 @@ def test_many_births_per_step_ranked_like_oracle(n):
     compare_particles(gpu, orc, cfg, floor=fp32_sensitivity(cfg, states, 3, step0=500))
 
 
-@pytest.mark.parametrize("scheme", ["ec_explicit", "ec3_explicit"])
+@pytest.mark.parametrize("scheme", ["ec_explicit", "ec3_explicit", "nu"])
 def test_sorting_and_graph_replay_do_not_change_results(scheme):
     """Charge sums are integers and draws are keyed on (id, step), so the
     slot order (sorted or not) and graph replay leave every particle
-    bit-identical."""
-    base = dict(workloads.CFG_SMALL_CCP, np_init=12_800, scheme=scheme)
+    bit-identical (nu: the explicit EC scheme on a stretched grid)."""
+    if scheme == "nu":
+        base = workloads.with_stretch(dict(workloads.CFG_SMALL_CCP, np_init=12_800), 0.6)
+    else:
+        base = dict(workloads.CFG_SMALL_CCP, np_init=12_800, scheme=scheme)
     outs = []
     for sp in (0, 1, 16):
         cfg = dict(base, sort_period=sp)

@@ -1,0 +1,87 @@
+"""The explicit EC scheme on a non-uniform grid (the multi-scale grid of
+Sec. 4) on the GPU: properties that hold at any size, beside the element-wise
+parity cases of test_gpu_parity.py (load, deposit and field, steps,
+collisions, sort and graph replay) and test_gpu_fullsize.py.
+
+Energy: a collisionless periodic plasma on cells 5 to 15 Debye lengths wide
+keeps its total energy within 1 % over 1000 / omega_p at omega_p dt = 0.1, as
+the FP64 oracle does on the same grid (its pin), and the GPU's history stays
+within 2x the oracle's own deviation plus 1e-3.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+E = 1.602176634e-19
+ME = 9.1093837015e-31
+EPS0 = 8.8541878128e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def thermal_cfg(wdt=0.1, beta=0.5):
+    n0, te = 1e15, 2.0
+    lam = math.sqrt(EPS0 * te / (n0 * E))
+    n_cells, ppc = 64, 64
+    wp = math.sqrt(n0 * E * E / (EPS0 * ME))
+    c = workloads.cfg_periodic_stretched(n_cells=n_cells, np_sp=n_cells * ppc, n0=n0,
+                                         length=n_cells * 10 * lam, dt=wdt / wp, te_ev=te, beta=beta)
+    return dict(c, sort_period=16)
+
+
+def test_stretched_grid_conserves_energy_like_the_oracle():
+    from paper_1310_5284_gb300.sim import Sim
+    cfg = thermal_cfg()
+    n = cfg["np_init"]
+    gpu = Sim(cfg, device="cuda:0")
+    orc = oracle.Sim(dict(cfg, quantized=True)).load(n, n)
+    gpu.step(1)
+    orc.step(1)
+    eg, eo = [gpu.energy()], [orc.energy()]
+    for _ in range(100):
+        gpu.step(100)
+        orc.step(100)
+        eg.append(gpu.energy())
+        eo.append(orc.energy())
+    assert gpu.status() == 0
+    eg, eo = np.array(eg), np.array(eo)
+    dev_g = np.max(np.abs(eg / eg[0] - 1.0))
+    dev_o = np.max(np.abs(eo / eo[0] - 1.0))
+    print("energy deviation over 10000 steps: gpu %.3g oracle %.3g" % (dev_g, dev_o))
+    assert eg[0] == pytest.approx(eo[0], rel=1e-5)
+    assert dev_g < 0.01
+    assert dev_g <= 2.0 * dev_o + 1e-3
+
+
+def test_stretched_discharge_steps_cleanly_with_sheaths():
+    """The stretched production discharge (cells 0.5x the uniform width at
+    the electrodes, 1.5x mid-gap) with a quarter of its particles, for two RF
+    periods: clean status, every particle accounted for by the walls and the
+    births, electrons depleted next to both electrodes (the sheaths) and the
+    bulk density within a factor 2 of the load density."""
+    from paper_1310_5284_gb300.sim import Sim
+    cfg = dict(workloads.CFG_WIDE_STRETCHED, np_init=512_000)
+    gpu = Sim(cfg, device="cuda:0")
+    gpu.step(3000)  # one RF period
+    gpu.diag(reset_avg=True)
+    gpu.step(3000)
+    d = gpu.diag()
+    assert gpu.status() == 0
+    for k in range(2):
+        assert d["count"][k] == cfg["np_init"] + d["births"] - sum(d["wall_count"][k])
+    prof = gpu.profiles()
+    ne, ni = prof["ne"], prof["ni"]
+    n = len(ne) - 1
+    edge = n // 20
+    assert ne[1:edge].mean() < ni[1:edge].mean() and ne[n - edge:n].mean() < ni[n - edge:n].mean()
+    assert 0.5 * cfg["n0"] < ne[n // 2] < 2.0 * cfg["n0"]

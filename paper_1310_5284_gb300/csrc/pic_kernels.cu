@@ -1001,8 +1001,23 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         const float d = v_new * R.dt_f;
         s = fmaf(d, hc.y, off);
         if (!(s >= 0.0f && s < 1.0f)) {
-            s = off;
-            walk_nu(sm.hw, N, R.periodic != 0, R.len_f, c, s, d);
+            // into the next cell over (the common crossing), else the walk
+            const bool right = s >= 1.0f;
+            const int cn = right ? c0 + 1 : c0 - 1;
+            bool done = false;
+            if (cn >= 0 && cn < N) {
+                const float hn_inv = sm.hw[cn].y;
+                const float t = right ? (s - 1.0f) * hc.x * hn_inv : fmaf(s * hc.x, hn_inv, 1.0f);
+                if (t >= 0.0f && t < 1.0f) {
+                    c = cn;
+                    s = t;
+                    done = true;
+                }
+            }
+            if (!done) {
+                s = off;
+                walk_nu(sm.hw, N, R.periodic != 0, R.len_f, c, s, d);
+            }
         }
     } else {
         // explicit leapfrog with E^n at x^n (Sec. 2 schemes (1), (2))
@@ -1988,7 +2003,10 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
     constexpr bool ec3 = ModeInfo<MODE>::ec3;
     constexpr bool implicit = ModeInfo<MODE>::implicit;
     if (threadIdx.x == 0) s_vl = vl_ok ? vl : electrode_volt(R, level);
-    if (R.stretched) defer = false;  // the non-uniform grid's field is finished here
+    // the modes that run on a non-uniform grid (the others never see one, and
+    // their tails carry none of its code)
+    constexpr bool nu_capable = MODE == kExplicitNU || MODE == kDepositEC;
+    if (nu_capable && R.stretched) defer = false;  // the non-uniform grid's field is finished here
     const bool acc_now = accumulate && (implicit || !defer);
     // node charges, densities, susceptibility (pointers and scalars held in
     // registers: the stores below cannot alias them)
@@ -2139,7 +2157,7 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
             q[c] = P;  // this thread's own cells only
         }
     }
-    if (R.stretched) {
+    if constexpr (nu_capable) if (R.stretched) {
         // Non-uniform grid, FP64: E_c = D_0 + kappa (P_c - Q W_c), where the
         // periodic box spreads the net charge Q over the nodes in proportion
         // to their lengths (W_c: the share of nodes 0..c; no spreading between

@@ -526,7 +526,14 @@ def test_steps_match_oracle(name, over, strict, steps):
     assert np.array_equal(g0["rho_q_e"], orc.grids()["rho_q_e"])
     gpu.step(strict)
     orc.step(strict)
-    compare_particles(gpu, orc, cfg)
+    if cfg.get("cell_width") is None:
+        compare_particles(gpu, orc, cfg)
+    else:
+        # on a non-uniform grid the force jumps at a node where the cell width
+        # changes (by the width ratio, up to 6 % here), so a particle that FP32
+        # and FP64 put on either side of a node in a strong field diverges from
+        # the first steps: the bar is the oracle's own FP32 sensitivity
+        compare_particles(gpu, orc, cfg, floor=fp32_sensitivity(cfg, states, strict))
     gpu.step(steps - strict)
     orc.step(steps - strict)
     assert gpu.status() == 0  # no capacity, birth-buffer or bounded-wait flag

@@ -66,13 +66,14 @@ Layout make_layout(const pic_config &c) {
     const size_t nb = (size_t)(c.births_capacity > 0 ? c.births_capacity : 1);
     L.births = take(sizeof(Birth) * nb + 8 * nb);  // records + rank and sort scratch
     L.wait_tab = take(4 * 2 * 3 * 64);
-    L.hw = L.h64 = L.xnode = L.wbg = 0;
+    L.hw = L.h64 = L.xnode = L.hdw = L.wdw = 0;
     if (c.cell_width) {
         const size_t n = (size_t)c.n_cells;
         L.hw = take(8 * n);
         L.h64 = take(8 * n);
         L.xnode = take(8 * n1);
-        L.wbg = take(8 * n);
+        L.hdw = take(8 * n);
+        L.wdw = take(8 * n);
     }
     L.total = o;
     return L;
@@ -367,38 +368,45 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
     R.dt_f = (float)c.dt;
     R.len_f = (float)c.length;
     R.eps0_half = 0.5 * kEps0;
-    R.inv_len = 1.0 / c.length;
+    split(1.0 / c.length, R.inv_len_ff);
     R.stretched = c.cell_width ? 1 : 0;
     if (R.stretched) {
         R.hw = (const float2 *)(A + L.hw);
         R.h64 = (const double *)(A + L.h64);
         R.xnode = (const double *)(A + L.xnode);
-        R.wbg = (const double *)(A + L.wbg);
+        R.hdw = (const float2 *)(A + L.hdw);
+        R.wdw = (const float2 *)(A + L.wdw);
     }
 }
 
 // The non-uniform grid's tables from the cell widths: (h, 1/h) in FP32 for
-// the push, h in FP64 for the field, node positions x_0 = 0, x_{g+1} = x_g +
-// h_g for the load, and for the periodic box the share W_c of the net
-// charge the nodes 0..c carry when it is spread in proportion to the node
-// lengths (h_{g-1} + h_g) / 2.
+// the push, node positions x_0 = 0, x_{g+1} = x_g + h_g for the load, h as
+// a double-word pair for the field, and for the periodic box the share W_c
+// of the net charge the nodes 0..c carry when it is spread in proportion to
+// the node lengths (h_{g-1} + h_g) / 2 (double-word).
 void grid_tables(const pic_config &c, std::vector<float2> &hw, std::vector<double> &xn,
-                 std::vector<double> &wbg) {
+                 std::vector<float2> &hdw, std::vector<float2> &wdw) {
     const int n = c.n_cells;
+    auto pair = [](double v) {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    };
     hw.resize(n);
     xn.assign(n + 1, 0.0);
-    wbg.resize(n);
+    hdw.resize(n);
+    wdw.resize(n);
     double len = 0.0;
     for (int k = 0; k < n; ++k) {
         const double h = c.cell_width[k];
         hw[k] = make_float2((float)h, (float)(1.0 / h));
+        hdw[k] = pair(h);
         xn[k + 1] = xn[k] + h;
         len += h;
     }
     double acc = 0.0;
     for (int g = 0; g < n; ++g) {
         acc += 0.5 * (c.cell_width[(g - 1 + n) % n] + c.cell_width[g]) / len;
-        wbg[g] = acc;
+        wdw[g] = pair(acc);
     }
 }
 
@@ -523,15 +531,16 @@ int init_run_state(const pic_config &c, const Run &R, unsigned char *arena, size
         wait_thresholds(R.p_null[1], tab[1]);
     }
     CKE(cudaMemcpyAsync((void *)R.wait_tab, tab, sizeof tab, cudaMemcpyHostToDevice, s));
-    std::vector<float2> hw;
-    std::vector<double> xn, wbg;
+    std::vector<float2> hw, hdw, wdw;
+    std::vector<double> xn;
     if (R.stretched) {
-        grid_tables(c, hw, xn, wbg);
+        grid_tables(c, hw, xn, hdw, wdw);
         const size_t n = (size_t)c.n_cells;
         CKE(cudaMemcpyAsync((void *)R.hw, hw.data(), 8 * n, cudaMemcpyHostToDevice, s));
         CKE(cudaMemcpyAsync((void *)R.h64, c.cell_width, 8 * n, cudaMemcpyHostToDevice, s));
         CKE(cudaMemcpyAsync((void *)R.xnode, xn.data(), 8 * (n + 1), cudaMemcpyHostToDevice, s));
-        CKE(cudaMemcpyAsync((void *)R.wbg, wbg.data(), 8 * n, cudaMemcpyHostToDevice, s));
+        CKE(cudaMemcpyAsync((void *)R.hdw, hdw.data(), 8 * n, cudaMemcpyHostToDevice, s));
+        CKE(cudaMemcpyAsync((void *)R.wdw, wdw.data(), 8 * n, cudaMemcpyHostToDevice, s));
     }
     CKE(cudaStreamSynchronize(s));
     const double vth_e = std::sqrt(kE * c.te_ev / kMe);

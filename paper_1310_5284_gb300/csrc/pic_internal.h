@@ -179,12 +179,13 @@ struct Run {
     int stretched;
     float dt_f;            // dt (FP32)
     float len_f;           // L (FP32)
-    double inv_len;        // 1 / L
     double eps0_half;      // eps0 / 2 (field energy sum_c h_c E_c^2)
+    float inv_len_ff[2];   // 1 / L as a double-word pair
     const float2 *hw;      // [n_cells] (h_c, 1/h_c) in FP32 for the push
     const double *h64;     // [n_cells] h_c
     const double *xnode;   // [n_cells + 1] node positions, x_0 = 0
-    const double *wbg;     // [n_cells] periodic box: share of the net charge on nodes 0..c
+    const float2 *hdw;     // [n_cells] h_c as a double-word pair
+    const float2 *wdw;     // [n_cells] periodic box: share of the net charge on nodes 0..c (double-word)
 };
 
 // Byte offsets of one run's buffers inside its arena.
@@ -193,7 +194,7 @@ struct Layout {
     size_t sp[2][2][7];  // [parity][species][field] offsets (cell, off, vx, vy, vz, id, abar)
     size_t acc_cnt[2], acc_a[2], acc_b[2], acc_c[2], cursor[2], rho_q[2];
     size_t e_gather, e_cc, chi, avg_ne, avg_ni, avg_e, heat[2], eedf, births, e_hi, e_lo, wait_tab;
-    size_t hw, h64, xnode, wbg;  // non-uniform grid tables (0 bytes on the uniform grid)
+    size_t hw, h64, xnode, hdw, wdw;  // non-uniform grid tables (0 bytes on the uniform grid)
     size_t total;
 };
 

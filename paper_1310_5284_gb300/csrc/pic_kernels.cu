@@ -1964,6 +1964,28 @@ __device__ __forceinline__ dw dw_from_i64(long long v) {
 
 __device__ __forceinline__ dw dw_of(const float (&p)[2]) { return {p[0], p[1]}; }
 
+// Sum of a double-word value over the block (all threads get it).
+__device__ dw block_sum_dw(dw x, float2 *scratch /*[kThreads/32 + 1]*/) {
+    constexpr int nw = kThreads / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        x = dw_add(x, dw{__shfl_xor_sync(FULL_MASK, x.hi, o), __shfl_xor_sync(FULL_MASK, x.lo, o)});
+    if (lane == 0) scratch[wid] = make_float2(x.hi, x.lo);
+    __syncthreads();
+    if (wid == 0) {
+        dw y = lane < nw ? dw{scratch[lane].x, scratch[lane].y} : dw{0.0f, 0.0f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            y = dw_add(y, dw{__shfl_xor_sync(FULL_MASK, y.hi, o), __shfl_xor_sync(FULL_MASK, y.lo, o)});
+        if (lane == 0) scratch[nw] = make_float2(y.hi, y.lo);
+    }
+    __syncthreads();
+    const float2 r = scratch[nw];
+    __syncthreads();
+    return dw{r.x, r.y};
+}
+
 // Electrode voltage V(t) = rf_volt sin(2 pi f t) at time level `level` (0 in
 // the periodic box), with its double-word split.
 struct Volt {
@@ -2006,7 +2028,6 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
     // the modes that run on a non-uniform grid (the others never see one, and
     // their tails carry none of its code)
     constexpr bool nu_capable = MODE == kExplicitNU || MODE == kDepositEC;
-    if (nu_capable && R.stretched) defer = false;  // the non-uniform grid's field is finished here
     const bool acc_now = accumulate && (implicit || !defer);
     // node charges, densities, susceptibility (pointers and scalars held in
     // registers: the stores below cannot alias them)
@@ -2158,45 +2179,73 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
         }
     }
     if constexpr (nu_capable) if (R.stretched) {
-        // Non-uniform grid, FP64: E_c = D_0 + kappa (P_c - Q W_c), where the
-        // periodic box spreads the net charge Q over the nodes in proportion
-        // to their lengths (W_c: the share of nodes 0..c; no spreading between
-        // electrodes), and D_0 makes sum_c h_c E_c = V (zero in the box).
-        const double qnet = R.periodic ? (double)totP : 0.0;
-        double sh = 0.0;
+        // Non-uniform grid, double-word FP32 like the uniform grid's solve:
+        // E_c = D_0 + kappa P'_c, P'_c = P_c - Q W_c, where the periodic box
+        // spreads the net charge Q over the nodes in proportion to their
+        // lengths (W_c: the share of nodes 0..c; none between electrodes),
+        // and D_0 = (V - kappa sum_c h_c P'_c) / L makes sum_c h_c E_c = V
+        // (zero in the box).  The gather table takes the cells' voltage drops
+        // h_c E_c; FP64 conversion, averages and energy are left to the next
+        // launch as on the uniform grid.
+        __shared__ float2 s_dw[kThreads / 32 + 1];
+        const dw qnet = R.periodic ? dw_from_i64(totP) : dw{0.0f, 0.0f};
+        const dw kap = dw_of(R.kappa_ff);
+        dw sh = {0.0f, 0.0f};
         for (int k = 0; k < per; ++k) {
             const int c = c_begin + k;
             if (c < n) {
-                const double pc = (double)q[c] - qnet * R.wbg[c];
-                pp[c] = pc;
-                sh += R.h64[c] * pc;
+                const float2 w = R.wdw[c];
+                const float2 h = R.hdw[c];
+                const dw pc = dw_add(dw_from_i64(q[c]), dw_neg(dw_mul(qnet, dw{w.x, w.y})));
+                ew[c] = make_float2(pc.hi, pc.lo);
+                sh = dw_add(sh, dw_mul(dw{h.x, h.y}, pc));
             }
         }
-        sh = block_sum_lean(sh, sc_d);
-        const double d0 = ((R.periodic ? 0.0 : s_vl.v) - R.kappa * sh) * R.inv_len;
+        sh = block_sum_dw(sh, s_dw);
+        const dw v = R.periodic ? dw{0.0f, 0.0f} : dw{s_vl.hi, s_vl.lo};
+        const dw d0 = dw_mul(dw_add(v, dw_neg(dw_mul(kap, sh))), dw_of(R.inv_len_ff));
         double wsum = 0.0;
         for (int k = 0; k < per; ++k) {
             const int c = c_begin + k;
             if (c < n) {
-                const double hc = R.h64[c];
-                const double e = d0 + R.kappa * pp[c];
-                pp[c] = e * hc;  // the cell's voltage drop, the gather table's entry
-                wsum += e * e * hc;
+                const float2 p2 = ew[c];
+                const float2 h = R.hdw[c];
+                const dw e = dw_add(d0, dw_mul(kap, dw{p2.x, p2.y}));
+                const dw u = dw_mul(e, dw{h.x, h.y});  // the cell's voltage drop
+                ew[c] = make_float2(u.hi, u.lo);
                 if (dry) continue;
-                R.e_gather[c + 1] = (float)(e * hc);
-                R.e_cc[c] = e;
-                if (accumulate) atomicAdd(&R.avg_e[c], e);
+                R.e_gather[c + 1] = u.hi;
+                if (defer) {
+                    R.e_hi[c] = e.hi;
+                    R.e_lo[c] = e.lo;
+                } else {
+                    const double ed = (double)e.hi + (double)e.lo;
+                    R.e_cc[c] = ed;
+                    if (accumulate) atomicAdd(&R.avg_e[c], ed);
+                    wsum += ed * ed * R.h64[c];
+                }
             }
         }
-        wsum = block_sum_lean(wsum, sc_d);  // includes the barrier that publishes pp[]
+        __syncthreads();  // publishes ew[]
         if (threadIdx.x == 0 && !dry) {
-            R.e_gather[0] = R.periodic ? (float)pp[n - 1] : 0.0f;
-            R.e_gather[n + 1] = R.periodic ? (float)pp[0] : 0.0f;
+            R.e_gather[0] = R.periodic ? ew[n - 1].x : 0.0f;
+            R.e_gather[n + 1] = R.periodic ? ew[0].x : 0.0f;
             st->v_left = s_vl.v;
-            if (ModeInfo<MODE>::explicit_push) st->field_energy_push = st->field_energy;
-            st->field_energy = R.eps0_half * wsum;
-            if (accumulate) st->v_sum += s_vl.v;
-            st->pending = 0u;
+        }
+        if (defer) {
+            if (threadIdx.x == 0 && !dry) {
+                if (ModeInfo<MODE>::explicit_push) st->field_energy_push = R.eps0_half * fe_acc;
+                st->fe_acc = 0.0;
+                st->pending = (accumulate ? 1u : 0u) | 2u;
+            }
+        } else {
+            wsum = block_sum_lean(wsum, sc_d);
+            if (threadIdx.x == 0 && !dry) {
+                if (ModeInfo<MODE>::explicit_push) st->field_energy_push = st->field_energy;
+                st->field_energy = R.eps0_half * wsum;
+                if (accumulate) st->v_sum += s_vl.v;
+                st->pending = 0u;
+            }
         }
         __syncthreads();
         return;
@@ -2284,7 +2333,10 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
 
 // The FP64 work a deferring tail left for nodes and cells of part `part` of
 // `parts`: the newest field to FP64, the running averages, the field energy
-// summed into st->fe_acc.  Every thread of the block calls this.
+// summed into st->fe_acc (NU: the caller may run on a non-uniform grid, where
+// the energy weights each cell by its width).  Every thread of the block
+// calls this.
+template <bool NU>
 __device__ void deferred_work(const Run &R, unsigned int pend, int part, int parts) {
     __shared__ double sc_d[kThreads / 32 + 1];
     const int n = R.n_cells;
@@ -2295,7 +2347,7 @@ __device__ void deferred_work(const Run &R, unsigned int pend, int part, int par
         if (k < n) {
             const double e = (double)R.e_hi[k] + (double)R.e_lo[k];
             R.e_cc[k] = e;
-            fe += e * e;
+            fe += (NU && R.stretched) ? e * e * R.h64[k] : e * e;  // sum_c h_c E_c^2 on a non-uniform grid
             if (pend & 1u) atomicAdd(&R.avg_e[k], e);
         }
         if (pend & 1u) {
@@ -2835,7 +2887,8 @@ __global__ void __launch_bounds__(kThreads, (MODE == kExplicitEC3 || MODE == kDe
     // the FP64 work the previous tail left (a few blocks; the others start streaming)
     {
         const unsigned int pend = st->pending;
-        if (pend && blockIdx.x < kDeferParts) deferred_work(R, pend, (int)blockIdx.x, kDeferParts);
+        if (pend && blockIdx.x < kDeferParts)
+            deferred_work<MI::nu || MODE == kDepositEC>(R, pend, (int)blockIdx.x, kDeferParts);
     }
     // The electrode voltage of the field the tail solves: FP64 is slow here,
     // so one thread of one block (past the deferring ones) computes it while
@@ -2874,10 +2927,10 @@ __global__ void __launch_bounds__(kThreads, (MODE == kExplicitEC3 || MODE == kDe
 __global__ void __launch_bounds__(kThreads) k_finalize(Run R) {
     const unsigned int pend = R.st->pending;
     if (!pend) return;
-    deferred_work(R, pend, 0, 1);
+    deferred_work<true>(R, pend, 0, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
-        R.st->field_energy = R.eps0_dx_half * R.st->fe_acc;
+        R.st->field_energy = (R.stretched ? R.eps0_half : R.eps0_dx_half) * R.st->fe_acc;
         R.st->pending = 0u;
     }
 }

@@ -687,8 +687,13 @@ def test_sorting_and_graph_replay_do_not_change_results(scheme):
                 assert np.array_equal(o[s][key], outs[0][s][key]), (s, key)
 
 
-def test_checkpoint_resume_is_bit_identical():
+@pytest.mark.parametrize("beta", [None, 0.6])
+def test_checkpoint_resume_is_bit_identical(beta):
+    """A snapshot restores the run exactly (beta: on a stretched grid, whose
+    width tables travel in the arena)."""
     cfg = dict(workloads.CFG_SMALL_CCP, np_init=8000, sort_period=4)
+    if beta is not None:
+        cfg = workloads.with_stretch(cfg, beta)
     gpu = gpu_sim(cfg)
     gpu.step(20)
     snap = gpu.save()

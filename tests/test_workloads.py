@@ -66,3 +66,19 @@ def test_discharge_study_runs_follow_the_paper_shape():
     assert sorted((r["scheme"], r["cells"], r["ppc"]) for r in groups["ppc"]) == sorted(
         (s, n, p) for s in ("ec_explicit", "ec_implicit") for n in (100, 200) for p in (400, 600, 800))
     assert len({r["cfg"]["seed"] for r in runs}) == 32
+
+
+def test_stretched_benchmark_grid():
+    """The stretched form of the production workload: 512 widths summing to
+    the 6.7 cm gap, 0.5x the uniform width at the electrodes and 1.5x
+    mid-gap (beta = 0.5), symmetric about the middle; everything else as the
+    uniform workload."""
+    c = workloads.CFG_WIDE_STRETCHED
+    u = workloads.CFG_WIDE_EXPLICIT
+    h = np.asarray(c["cell_width"])
+    dx = u["length"] / u["n_cells"]
+    assert h.size == 512 and abs(h.sum() - u["length"]) <= 1e-12 * u["length"]
+    assert abs(h[0] / dx - 0.5) < 0.01 and abs(h[255] / dx - 1.5) < 0.01
+    assert np.allclose(h, h[::-1], rtol=1e-10)
+    for key in ("n_cells", "np_init", "n0", "rf_volt", "rf_freq", "dt", "pressure_mtorr", "sort_period", "scheme"):
+        assert c[key] == u[key], key

@@ -753,6 +753,9 @@ def main():
         line["ec3"]["over_m2_value"] = line["ec3"]["value"] / line["value"]
         line["stretched"] = bench_stretched()
         line["stretched"]["over_uniform_value"] = line["stretched"]["value"] / line["value"]
+        if not args.no_cpu_baseline:
+            line["stretched"]["cpu_baseline"] = oracle_baseline(workloads.CFG_WIDE_STRETCHED, budget_s=8.0,
+                                                                max_steps=20)
         line["self_heating"] = bench_self_heating()
         line["paper_table1"] = bench_paper_table()
     print(json.dumps(line))

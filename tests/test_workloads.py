@@ -82,3 +82,21 @@ def test_stretched_benchmark_grid():
     assert np.allclose(h, h[::-1], rtol=1e-10)
     for key in ("n_cells", "np_init", "n0", "rf_volt", "rf_freq", "dt", "pressure_mtorr", "sort_period", "scheme"):
         assert c[key] == u[key], key
+
+
+def test_grid_study_runs():
+    """The multi-scale grid study: the paper's discharge with 320 000
+    macro-particles per species on 800 and 200 uniform cells and on 200 and
+    100 stretched cells (beta = 0.75) whose electrode cells match the 800-
+    and 400-cell widths."""
+    from workloads.grid_study import grid_runs, NP
+    runs = grid_runs()
+    assert [(r["cells"], r["beta"]) for r in runs] == [(800, None), (200, None), (200, 0.75), (100, 0.75)]
+    for r in runs:
+        c = r["cfg"]
+        assert c["np_init"] == NP == 320_000 and c["scheme"] == "ec_explicit"
+        assert c["length"] == 0.04 and c["rf_freq"] == 27.0e6 and c["dt"] == 1.5e-11
+        if r["beta"] is not None:
+            h = np.asarray(c["cell_width"])
+            assert abs(h.sum() - 0.04) < 1e-15 and abs(h[0] / (0.04 / (4 * c["n_cells"])) - 1.0) < 0.01
+    assert len({r["cfg"]["seed"] for r in runs}) == 4

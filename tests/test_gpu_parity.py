@@ -502,6 +502,9 @@ STEP_CASES = [
      30, 100),
     ("nu_electrodes_rf_collisionless_b06", dict(n_cells=64, mcc=False, grid_beta=0.6), 30, 100),
     ("nu_ragged_37_b08", dict(n_cells=37, mcc=False, grid_beta=0.8), 30, 60),
+    # the largest grid the library takes: the width table beside the largest
+    # accumulators in shared memory
+    ("nu_1024_cells_b07", dict(n_cells=1024, np_init=40_000, mcc=False, grid_beta=0.7), 10, 30),
 ]
 
 
@@ -600,6 +603,7 @@ COLLISION_CASES = [
     ("ec_explicit", dict(scattering="vahedi_surendra")),
     ("ec_implicit", dict(iz_split="opal", scattering="vahedi_surendra", te_ev=10.0)),
     ("ec_explicit", dict(grid_beta=0.6)),  # non-uniform grid
+    ("ec_explicit", dict(grid_beta=0.5, periodic=True, rf_volt=0.0)),  # non-uniform periodic box
 ]
 
 

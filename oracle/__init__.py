@@ -141,8 +141,8 @@ def lib():
         L.orc_gather_mc.restype = ctypes.c_double
         L.orc_grid_nodes.argtypes = [ctypes.c_int, _d, _d]
         L.orc_locate.argtypes = [ctypes.c_int, _d, _d, ctypes.c_double, _i64, _d]
-        L.orc_solve_dirichlet_h.argtypes = [ctypes.c_int, _d, _d, ctypes.c_double, _d]
-        L.orc_solve_periodic_h.argtypes = [ctypes.c_int, _d, _d, _d]
+        L.orc_solve_dirichlet_h.argtypes = [ctypes.c_int, _d, _d, _d, ctypes.c_double, _d]
+        L.orc_solve_periodic_h.argtypes = [ctypes.c_int, _d, _d, _d, _d]
         L.orc_gather_ec_h.argtypes = [_P(Params), _d, ctypes.c_double]
         L.orc_gather_ec_h.restype = ctypes.c_double
         L.orc_rotate.argtypes = [_d, ctypes.c_double, ctypes.c_double, _d]
@@ -399,21 +399,23 @@ def locate(h, x_nodes, x):
     return int(w), int(c.value), float(o.value)
 
 
-def solve_dirichlet_h(h, q_node, v_left) -> np.ndarray:
+def solve_dirichlet_h(h, q_node, v_left, chi=None) -> np.ndarray:
     h = np.ascontiguousarray(h, np.float64)
     q = np.ascontiguousarray(q_node, np.float64)
+    ch = None if chi is None else np.ascontiguousarray(chi, np.float64)
     phi = np.zeros(h.size + 1)
-    lib().orc_solve_dirichlet_h(h.size, _ptr(h, ctypes.c_double), _ptr(q, ctypes.c_double), float(v_left),
-                                _ptr(phi, ctypes.c_double))
+    lib().orc_solve_dirichlet_h(h.size, _ptr(h, ctypes.c_double), _ptr(q, ctypes.c_double),
+                                _ptr(ch, ctypes.c_double), float(v_left), _ptr(phi, ctypes.c_double))
     return phi
 
 
-def solve_periodic_h(h, q_node) -> np.ndarray:
+def solve_periodic_h(h, q_node, chi=None) -> np.ndarray:
     h = np.ascontiguousarray(h, np.float64)
     q = np.ascontiguousarray(q_node, np.float64)
+    ch = None if chi is None else np.ascontiguousarray(chi, np.float64)
     phi = np.zeros(h.size + 1)
     lib().orc_solve_periodic_h(h.size, _ptr(h, ctypes.c_double), _ptr(q, ctypes.c_double),
-                               _ptr(phi, ctypes.c_double))
+                               _ptr(ch, ctypes.c_double), _ptr(phi, ctypes.c_double))
     return phi
 
 
@@ -443,8 +445,9 @@ class Sim:
         cap_e = cap_e if cap_e is not None else max(1024, int(npi * cfg.get("cap_factor", 2.0)))
         cap_i = cap_i if cap_i is not None else cap_e
         if cfg.get("cell_width") is not None and (
-                cfg.get("scheme", "ec_explicit") != "ec_explicit" or not cfg.get("ions_mobile", True)):
-            raise ValueError("the non-uniform grid takes the explicit EC scheme with mobile ions")
+                cfg.get("scheme", "ec_explicit") not in ("ec_explicit", "ec_implicit")
+                or not cfg.get("ions_mobile", True)):
+            raise ValueError("the non-uniform grid takes the EC schemes with m = 2 and mobile ions")
         self._h = lib().orc_sim_create(ctypes.byref(self.p), int(cap_e), int(cap_i))
         if not self._h:
             raise MemoryError("oracle allocation failed")

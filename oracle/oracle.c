@@ -513,8 +513,8 @@ int orc_locate(int n_cells, const double *x_nodes, const double *h, double x, in
     return 0;
 }
 
-void orc_solve_dirichlet_h(int n_cells, const double *h, const double *q_node, double v_left,
-                           double *phi)
+void orc_solve_dirichlet_h(int n_cells, const double *h, const double *q_node, const double *chi,
+                           double v_left, double *phi)
 {
     int n = n_cells;
     phi[0] = v_left;
@@ -525,7 +525,8 @@ void orc_solve_dirichlet_h(int n_cells, const double *h, const double *q_node, d
     double *dp = (double *)malloc(sizeof(double) * (size_t)m);
     for (int k = 0; k < m; ++k) {
         int g = k + 1;
-        double a = -1.0 / h[g - 1], c = -1.0 / h[g];
+        double a = -(1.0 + (chi ? chi[g - 1] : 0.0)) / h[g - 1];
+        double c = -(1.0 + (chi ? chi[g] : 0.0)) / h[g];
         double b = -a - c;
         double d = q_node[g] / EPS_0;
         if (g == 1) d -= a * v_left;
@@ -544,7 +545,8 @@ void orc_solve_dirichlet_h(int n_cells, const double *h, const double *q_node, d
     free(dp);
 }
 
-void orc_solve_periodic_h(int n_cells, const double *h, const double *q_node, double *phi)
+void orc_solve_periodic_h(int n_cells, const double *h, const double *q_node, const double *chi,
+                          double *phi)
 {
     int n = n_cells;
     double len = 0.0, tot = 0.0;
@@ -556,7 +558,7 @@ void orc_solve_periodic_h(int n_cells, const double *h, const double *q_node, do
         r[g] = q_node[g] - tot * 0.5 * (hl + hr) / len;
     }
     r[n] = 0.0;
-    orc_solve_dirichlet_h(n, h, r, 0.0, phi);
+    orc_solve_dirichlet_h(n, h, r, chi, 0.0, phi);
     free(r);
 }
 
@@ -695,8 +697,9 @@ orc_sim *orc_sim_create(const orc_params *p, int64_t cap_e, int64_t cap_i)
     s->avg_phi = (double *)calloc((size_t)nn, sizeof(double));
     s->eedf = (int64_t *)calloc((size_t)(p->eedf_bins + 1), sizeof(int64_t));
     if (p->cell_width) {
-        /* the explicit EC scheme with mobile ions is the one defined on it */
-        if (p->scheme != ORC_EC_EXPLICIT || !p->ions_mobile) {
+        /* the EC schemes with m = 2 (explicit and direct implicit) and mobile
+           ions are the ones defined on it */
+        if ((p->scheme != ORC_EC_EXPLICIT && p->scheme != ORC_EC_IMPLICIT) || !p->ions_mobile) {
             orc_sim_free(s);
             return NULL;
         }
@@ -827,9 +830,9 @@ static void solve_field(orc_sim *s, const double *chi, int64_t level)
         double *qn = (double *)malloc(sizeof(double) * (size_t)(n + 1));
         for (int g = 0; g <= n; ++g) qn[g] = s->rho[g] * node_len(s, g);
         if (p->periodic)
-            orc_solve_periodic_h(n, s->h, qn, s->phi);
+            orc_solve_periodic_h(n, s->h, qn, chi, s->phi);
         else
-            orc_solve_dirichlet_h(n, s->h, qn, rf_voltage(p, level), s->phi);
+            orc_solve_dirichlet_h(n, s->h, qn, chi, rf_voltage(p, level), s->phi);
         free(qn);
         double w = 0.0;
         for (int c = 0; c < n; ++c) {
@@ -1331,12 +1334,18 @@ static int step_implicit(orc_sim *s, int diag_step)
         int64_t m = 0;
         for (int64_t i = 0; i < sp->n; ++i) {
             double vt = sp->vx[i] + 0.5 * dt * sp->abar[i];
-            double x = sp->xi[i] + vt * dt / dx;
-            if (p->periodic) {
-                x -= n * floor(x / n);
-                if (x >= n) x -= n;
-            } else if (x < 0.0 || x >= n) {
-                continue;
+            double x;
+            if (s->h) {
+                x = move_on_grid(s, sp->xi[i], vt * dt);  /* wraps in the periodic box */
+                if (x < 0.0 || x >= n) continue;
+            } else {
+                x = sp->xi[i] + vt * dt / dx;
+                if (p->periodic) {
+                    x -= n * floor(x / n);
+                    if (x >= n) x -= n;
+                } else if (x < 0.0 || x >= n) {
+                    continue;
+                }
             }
             xt[m++] = x;
         }
@@ -1353,13 +1362,15 @@ static int step_implicit(orc_sim *s, int diag_step)
     }
     assemble_rho(s);
     /* EC: chi_{c+1/2} = dt^2/2 sum_s (q_s^2 w / (m_s eps0 dx)) S_1-weighted count at
-       the cell centres.  MC (reading): the same density-like sum at the nodes with
-       the S_1 weights of the charge assignment, averaged onto each face. */
+       the cell centres (on a non-uniform grid the count over the cell's own
+       width h_c: a density, as on the uniform grid).  MC (reading): the same
+       density-like sum at the nodes with the S_1 weights of the charge
+       assignment, averaged onto each face. */
     for (int c = 0; c < n; ++c) {
         double chi = 0.0;
         for (int k = 0; k < 2; ++k) {
             double coef = 0.5 * dt * dt * s->d.q[k] * s->d.q[k] * s->d.weight /
-                          (s->d.m[k] * EPS_0 * dx);
+                          (s->d.m[k] * EPS_0 * (s->h ? s->h[c] : dx));
             if (is_mc(p)) {
                 int64_t right = (p->periodic && c + 1 == n) ? 0 : c + 1;
                 double wl = (double)s->rho_q[k][c] / (double)TWO_POW_33;
@@ -1383,10 +1394,15 @@ static int step_implicit(orc_sim *s, int diag_step)
         for (int64_t i = 0; i < sp->n; ++i) {
             double v_old = sp->vx[i];
             double vt = v_old + 0.5 * dt * sp->abar[i];
-            double x = sp->xi[i] + vt * dt / dx;
-            if (p->periodic) {
-                x -= n * floor(x / n);
-                if (x >= n) x -= n;
+            double x;
+            if (s->h) {
+                x = move_on_grid(s, sp->xi[i], vt * dt);
+            } else {
+                x = sp->xi[i] + vt * dt / dx;
+                if (p->periodic) {
+                    x -= n * floor(x / n);
+                    if (x >= n) x -= n;
+                }
             }
             int inside = x >= 0.0 && x < n;
             double e = inside ? gather(s, x) : 0.0;
@@ -1398,8 +1414,14 @@ static int step_implicit(orc_sim *s, int diag_step)
                particle is m w abar^n vbar (the field (m/q) abar^n, not E^{n+1}) */
             double work = s->d.m[k] * s->d.weight * abar_new * 0.5 * (v_old + v_new);
             pw += work;
-            if (diag_step && inside) s->heat[k][(int64_t)floor(x)] += work / dx;
-            sp->xi[i] = x + 0.5 * dt * dt * a / dx;
+            if (diag_step && inside) {
+                int64_t c = (int64_t)floor(x);
+                s->heat[k][c] += work / (s->h ? s->h[c] : dx);
+            }
+            if (s->h)
+                sp->xi[i] = inside ? move_on_grid(s, x, 0.5 * dt * dt * a) : x;
+            else
+                sp->xi[i] = x + 0.5 * dt * dt * a / dx;
             sp->vx[i] = v_new;
             sp->abar[i] = abar_new;
             boundary(s, k, i);

@@ -64,8 +64,9 @@ typedef struct orc_params {
     /* Non-uniform grid, the multi-scale grid Sec. 4 proposes: the widths [m]
        of the n_cells cells, summing to `length`; NULL for the uniform grid of
        width length / n_cells.  Positions stay in cell units (cell index plus
-       the fraction of that cell's width); the explicit EC scheme with mobile
-       ions is the one scheme defined on it (orc_sim_create refuses others). */
+       the fraction of that cell's width); the EC schemes with m = 2 (explicit
+       and direct implicit) with mobile ions are the ones defined on it
+       (orc_sim_create refuses others). */
     const double *cell_width;
 } orc_params;
 enum { ORC_IZ_OPAL = 1, ORC_SCATTER_VS = 2 };
@@ -140,14 +141,16 @@ void orc_grid_nodes(int n_cells, const double *h, double *x);
    1 at or beyond x[N]. */
 int orc_locate(int n_cells, const double *x_nodes, const double *h, double x, int64_t *cell,
                double *off);
-/* Gauss law eps0 [(phi_g - phi_{g+1})/h_g - (phi_{g-1} - phi_g)/h_{g-1}] = q_g
-   for the interior nodes, node charges q_g per unit area [C/m^2], phi[0] =
-   v_left, phi[N] = 0 (Thomas algorithm). */
-void orc_solve_dirichlet_h(int n_cells, const double *h, const double *q_node, double v_left,
-                           double *phi);
+/* Gauss law eps0 [(1+chi_g)(phi_g - phi_{g+1})/h_g - (1+chi_{g-1})(phi_{g-1} -
+   phi_g)/h_{g-1}] = q_g for the interior nodes, node charges q_g per unit
+   area [C/m^2], the implicit susceptibility chi of each cell (NULL: none),
+   phi[0] = v_left, phi[N] = 0 (Thomas algorithm). */
+void orc_solve_dirichlet_h(int n_cells, const double *h, const double *q_node, const double *chi,
+                           double v_left, double *phi);
 /* Periodic: the net charge is spread over the nodes in proportion to their
    lengths (h_{g-1} + h_g) / 2, gauge phi[0] = phi[N] = 0. */
-void orc_solve_periodic_h(int n_cells, const double *h, const double *q_node, double *phi);
+void orc_solve_periodic_h(int n_cells, const double *h, const double *q_node, const double *chi,
+                          double *phi);
 /* Field at the particle [V/m] from the voltage drops u[c] = phi_c - phi_{c+1}
    of the cells (ghost cells 0 beyond the walls, wrapped in a periodic box). */
 double orc_gather_ec_h(const orc_params *p, const double *u_cc, double xi);

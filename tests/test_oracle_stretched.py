@@ -113,18 +113,20 @@ def test_force_is_minus_gradient_of_the_assigned_potential_energy(periodic):
     assert tested > 150
 
 
-def _free_streaming_cfg(n=16, beta=0.7, periodic=True):
+def _free_streaming_cfg(n=16, beta=0.7, periodic=True, scheme="ec_explicit"):
     length = 0.016
     c = dict(n_cells=n, periodic=periodic, length=length, dt=1e-9, n0=1e-6, np_init=4.0,
-             scheme="ec_explicit", mcc=False, ions_mobile=True, quantized=False, rf_volt=0.0,
+             scheme=scheme, mcc=False, ions_mobile=True, quantized=False, rf_volt=0.0,
              cell_width=widths(n, length, beta), te_ev=1.0, ti_ev=0.026)
     return c
 
 
-def test_free_streaming_crosses_cells_of_different_width():
+@pytest.mark.parametrize("scheme", ["ec_explicit", "ec_implicit"])
+def test_free_streaming_crosses_cells_of_different_width(scheme):
     """With a vanishing weight the field is negligible, so x(t) = x0 + v t,
-    wrapped in the periodic box; velocities cross up to several cells a step."""
-    c = _free_streaming_cfg()
+    wrapped in the periodic box; velocities cross up to several cells a step
+    (the direct-implicit push: predictor and corrector moves alike)."""
+    c = _free_streaming_cfg(scheme=scheme)
     h, xn, length = np.asarray(c["cell_width"]), oracle.grid_nodes(c["cell_width"]), c["length"]
     x0 = np.array([0.0005, 0.004, 0.0101, 0.0159])
     v = np.array([3.0e5, -2.2e6, 4.1e6, -7.0e5])
@@ -210,11 +212,110 @@ def test_uniform_load_gives_the_load_density_at_every_node():
 
 
 def test_other_schemes_are_refused_on_a_non_uniform_grid():
-    for scheme in ("mc_explicit", "ec_implicit", "ec3_explicit"):
+    for scheme in ("mc_explicit", "mc_implicit", "ec3_explicit"):
         with pytest.raises(ValueError):
             oracle.Sim(dict(workloads.cfg_periodic_stretched(), scheme=scheme))
     with pytest.raises(ValueError):
         oracle.Sim(dict(workloads.cfg_periodic_stretched(), ions_mobile=False))
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.5])
+def test_modified_poisson_is_the_series_capacitor_in_vacuum(beta):
+    """No charge, a susceptibility that varies from cell to cell: D = (1 +
+    chi_c) E_c is the same in every cell and sum_c h_c E_c = V, so
+    D = V / sum_c h_c / (1 + chi_c) and phi_g = V - D sum_{c<g} h_c / (1 + chi_c)."""
+    n, length, v = 30, 0.03, 120.0
+    h = widths(n, length, beta)
+    chi = np.random.default_rng(8).uniform(0.0, 5.0, n)
+    phi = oracle.solve_dirichlet_h(h, np.zeros(n + 1), v, chi=chi)
+    d = v / np.sum(h / (1.0 + chi))
+    exact = v - d * np.concatenate([[0.0], np.cumsum(h / (1.0 + chi))])
+    assert np.allclose(phi, exact, rtol=1e-12, atol=1e-12 * v)
+
+
+def test_modified_poisson_with_uniform_chi_scales_the_parabola():
+    """Uniform space charge and a uniform susceptibility: the parabola of the
+    plain Gauss law divided by 1 + chi, on any spacing."""
+    n, length, rho0, v, chi0 = 24, 0.03, 3.0e-6, 150.0, 2.5
+    h = widths(n, length, 0.7)
+    xn = oracle.grid_nodes(h)
+    q = np.zeros(n + 1)
+    q[1:n] = rho0 * 0.5 * (h[:-1] + h[1:])
+    phi = oracle.solve_dirichlet_h(h, q, v, chi=np.full(n, chi0))
+    exact = v * (1.0 - xn / length) + rho0 * xn * (length - xn) / (2.0 * EPS0 * (1.0 + chi0))
+    assert np.allclose(phi, exact, rtol=1e-11, atol=1e-11 * np.abs(exact).max())
+
+
+def test_susceptibility_of_a_uniform_plasma_is_the_same_in_every_cell():
+    """The direct-implicit susceptibility is (omega_p dt)^2 / 2 summed over
+    the species for a uniform density: on a stretched grid a uniform load
+    puts counts in proportion to the cell widths, and every cell's chi must
+    still come out at that value (within the count noise, 2 % here)."""
+    n0, te, dt = 1e15, 2.0, 2e-10
+    c = workloads.cfg_periodic_stretched(n_cells=64, np_sp=400_000, n0=n0, length=0.05, dt=dt, te_ev=te, beta=0.6)
+    c.update(scheme="ec_implicit", quantized=True)
+    sim = oracle.Sim(c).load(400_000, 400_000)
+    sim.step(1)
+    chi = sim.grids()["chi"]
+    mi = c["ion_mass_amu"] * 1.66053906660e-27
+    expect = 0.5 * dt * dt * n0 * E * E / EPS0 * (1.0 / ME + 1.0 / mi)
+    assert np.allclose(chi, expect, rtol=0.06), (chi.min() / expect, chi.max() / expect)
+    assert abs(chi.mean() / expect - 1.0) < 0.01
+
+
+def test_equal_widths_reproduce_the_uniform_implicit_scheme():
+    """The direct-implicit push (Sec. 2 scheme (4)) with cell_width = L/N:
+    predictor, susceptibility, modified Poisson and corrector as on the
+    uniform grid, 30 steps at omega_p dt = 2 (MCC off, FP64 weights)."""
+    base = dict(workloads.CFG_IMPLICIT, n_cells=64, np_init=6000, mcc=False, quantized=False)
+    n, length = base["n_cells"], base["length"]
+    stretched = dict(base, cell_width=[length / n] * n)
+    vth = math.sqrt(E * 2.0 / ME)
+    st = workloads.injected_particles(23, 6000, n, vth)
+    xi = workloads.xi_of(st)
+    sims = []
+    for c in (base, stretched):
+        s = oracle.Sim(c, cap_e=8192, cap_i=8192)
+        s.set_species(0, xi, st["vx"], st["vy"], st["vz"], st["id"])
+        s.set_species(1, xi, 0.01 * st["vx"], st["vy"], st["vz"], st["id"])
+        s.init_field()
+        s.step(30)
+        sims.append(s)
+    a, b = sims[0].get_species(0), sims[1].get_species(0)
+    assert sims[0].count(0) == sims[1].count(0)
+    assert np.allclose(a["xi"], b["xi"], rtol=0, atol=1e-8)
+    assert np.allclose(a["vx"], b["vx"], rtol=1e-7, atol=1e-5)
+    assert np.allclose(a["abar"], b["abar"], rtol=1e-6, atol=1e-6 * np.abs(a["abar"]).max())
+    ga, gb = sims[0].grids(), sims[1].grids()
+    assert np.allclose(ga["chi"], gb["chi"], rtol=1e-12)
+    assert np.allclose(ga["phi"], gb["phi"], rtol=1e-7, atol=1e-8 * np.abs(ga["phi"]).max())
+
+
+def test_implicit_on_stretched_cells_follows_the_uniform_grid():
+    """omega_p dt = 2 (beyond the explicit limit of Eq. (1)) with cells 5 to
+    15 Debye lengths: the direct-implicit push damps the load's charge
+    fluctuations and cools the plasma (three quarters of the total energy
+    go in 1000 steps, on the uniform grid as well); the stretched grid's
+    energy history stays within 5 % of the total of the uniform grid's of
+    the same mean width (2.2 % measured)."""
+    out = []
+    for beta in (0.0, 0.5):
+        n0, te = 1e15, 2.0
+        lam = math.sqrt(EPS0 * te / (n0 * E))
+        wp = math.sqrt(n0 * E * E / (EPS0 * ME))
+        c = workloads.cfg_periodic_stretched(n_cells=64, np_sp=64 * 64, n0=n0, length=64 * 10 * lam,
+                                             dt=2.0 / wp, te_ev=te, beta=beta)
+        c.update(scheme="ec_implicit", quantized=False)
+        sim = oracle.Sim(c).load(64 * 64, 64 * 64)
+        sim.step(1)
+        tot = [sim.energy()]
+        for _ in range(10):
+            sim.step(100)
+            tot.append(sim.energy())
+        out.append(np.array(tot) / tot[0] - 1.0)
+    uni, st = out
+    assert uni[-1] < -0.5 and st[-1] < -0.5
+    assert np.max(np.abs(st - uni)) < 0.05
 
 
 def _thermal(wdt, steps, beta=0.5):

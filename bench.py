@@ -45,6 +45,7 @@ WORKLOADS = {
     "ccp_512cells_2048000ppsp_m3": dict(workloads.CFG_WIDE_EXPLICIT, scheme="ec3_explicit"),
     # the same on a stretched grid (Sec. 4's multi-scale grid)
     "ccp_512cells_2048000ppsp_stretched": workloads.CFG_WIDE_STRETCHED,
+    "ccp_128cells_implicit_stretched": workloads.CFG_IMPLICIT_STRETCHED,
 }
 
 
@@ -563,7 +564,7 @@ def bench_self_heating(steps=2000):
     return out
 
 
-def bench_implicit(steps=4000, warmup=20):
+def bench_implicit(steps=4000, warmup=20, cfg=None, label="ccp_128cells_implicit (omega_p dt = 2)"):
     """The direct-implicit workload (128 cells, 1.02 M per species, omega_p dt
     = 2, 300 V, 50 mTorr): a step is the predictor and corrector launches,
     plus the sort every sort_period steps.  4000 steps timed one by one, the
@@ -576,7 +577,7 @@ def bench_implicit(steps=4000, warmup=20):
     from paper_1310_5284_gb300.sim import Sim
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    cfg = dict(workloads.CFG_IMPLICIT)
+    cfg = dict(workloads.CFG_IMPLICIT if cfg is None else cfg)
     sim = Sim(cfg, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     sim.step(warmup)
@@ -608,7 +609,7 @@ def bench_implicit(steps=4000, warmup=20):
     bytes_pair = (bpp["per_particle"] + bpp["predictor_per_particle"]) * n_avg + bpp["per_selected"] * sel / steps
     achieved = bytes_pair / (t_pair * 1e-3) / 1e9
     peak, kind = measured_peak()
-    return {"workload": "ccp_128cells_implicit (omega_p dt = 2)", "ms_per_step": ms, "launch_pair_ms": t_pair,
+    return {"workload": label, "ms_per_step": ms, "launch_pair_ms": t_pair,
             "sort_ms": t_sort, "steps": steps, "warmup": warmup, "value": n_avg / (ms * 1e-3), "unit": UNIT,
             "status": status, "counts_start_end": [d0["count"], d1["count"]],
             "births_per_step": (d1["births"] - d0["births"]) / steps,
@@ -756,6 +757,11 @@ def main():
         if not args.no_cpu_baseline:
             line["stretched"]["cpu_baseline"] = oracle_baseline(workloads.CFG_WIDE_STRETCHED, budget_s=8.0,
                                                                 max_steps=20)
+        # the direct-implicit workload on the stretched grid (cells 0.5x the
+        # uniform width at the electrodes, 1.5x mid-gap)
+        line["stretched_implicit"] = bench_implicit(1000, 20, workloads.CFG_IMPLICIT_STRETCHED,
+                                                    "ccp_128cells_implicit_stretched (omega_p dt = 2)")
+        line["stretched_implicit"]["over_uniform_value"] = line["stretched_implicit"]["value"] / line["implicit"]["value"]
         line["self_heating"] = bench_self_heating()
         line["paper_table1"] = bench_paper_table()
     print(json.dumps(line))

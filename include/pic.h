@@ -139,8 +139,9 @@ typedef struct pic_config {
        the sheaths without resolving the bulk: NULL for the uniform grid of
        width length / n_cells, else a host array of n_cells cell widths [m],
        each positive, summing to `length` within 1e-9 relative.  pic_init
-       copies it (the caller keeps ownership).  Taken by PIC_EC_EXPLICIT
-       with mobile ions, in single runs (pic_batch_init rejects it).  The
+       copies it (the caller keeps ownership).  Taken by PIC_EC_EXPLICIT and
+       PIC_EC_IMPLICIT with mobile ions, in single runs (pic_batch_init
+       rejects it).  The
        paper gives no form of Eq. (2)-(3) for unequal cells; this library's:
        a particle's position stays (cell, offset in [0, 1) of that cell's
        width); the charge assignment and the interpolation weights are those
@@ -150,7 +151,10 @@ typedef struct pic_config {
        solve is the Gauss law on the physical node spacing, with sum_c h_c
        E_c = V(t) between electrodes, and in a periodic box zero with the
        net charge spread over the nodes in proportion to (h_{g-1} + h_g)/2.
-       Energy conservation (Sec. 2) carries over.  pic_profiles divides a
+       Energy conservation (Sec. 2) carries over.  The direct-implicit
+       scheme moves the predicted and corrected positions the same way, takes
+       a cell's susceptibility from its S_1-weighted count over its own
+       width, and solves (1 + chi_c) E_c in the same Gauss law.  pic_profiles divides a
        node's charge by (h_{g-1} + h_g)/2, and the heating of a cell by its
        width. */
     const double *cell_width;

@@ -142,8 +142,8 @@ int validate(const pic_config *c) {
         return fail(PIC_EINVAL, "bad collision parameters");
     if (c->sort_period < 0 || c->diag_period < 0) return fail(PIC_EINVAL, "negative period");
     if (c->cell_width) {
-        if (c->scheme != PIC_EC_EXPLICIT || !c->ions_mobile)
-            return fail(PIC_EINVAL, "a non-uniform grid takes PIC_EC_EXPLICIT with mobile ions");
+        if ((c->scheme != PIC_EC_EXPLICIT && c->scheme != PIC_EC_IMPLICIT) || !c->ions_mobile)
+            return fail(PIC_EINVAL, "a non-uniform grid takes PIC_EC_EXPLICIT or PIC_EC_IMPLICIT with mobile ions");
         double sum = 0.0;
         for (int k = 0; k < c->n_cells; ++k) {
             const double w = c->cell_width[k];
@@ -293,6 +293,7 @@ void derive_impl(const pic_config &c, const Layout &L, unsigned char *A, Run &R)
     R.dt_dx = (float)(c.dt / dx);
     R.half_dt = (float)(0.5 * c.dt);
     R.half_dt2_dx = (float)(0.5 * c.dt * c.dt / dx);
+    R.half_dt2 = (float)(0.5 * c.dt * c.dt);
     R.abar_ion_over_e = (float)((kE / m[1]) / (-kE / kMe));
     R.eedf_inv_width = (float)(c.eedf_bins / c.eedf_max_ev);
     // Null-collision bounds (Vahedi & Surendra): per process the maximum of
@@ -411,7 +412,7 @@ void grid_tables(const pic_config &c, std::vector<float2> &hw, std::vector<doubl
 }
 
 Mode push_mode(const pic_config &c) {
-    if (c.cell_width) return kExplicitNU;
+    if (c.cell_width && c.scheme == PIC_EC_EXPLICIT) return kExplicitNU;
     if (c.scheme == PIC_EC3_EXPLICIT) return kExplicitEC3;
     return c.scheme == PIC_MC_EXPLICIT ? kExplicitMC : kExplicitEC;
 }
@@ -419,8 +420,14 @@ Mode deposit_mode(const pic_config &c) {
     if (c.scheme == PIC_EC3_EXPLICIT) return kDepositEC3;
     return (c.scheme == PIC_MC_EXPLICIT || c.scheme == PIC_MC_IMPLICIT) ? kDepositMC : kDepositEC;
 }
-Mode pass1_mode(const pic_config &c) { return c.scheme == PIC_MC_IMPLICIT ? kImplicit1MC : kImplicit1; }
-Mode pass2_mode(const pic_config &c) { return c.scheme == PIC_MC_IMPLICIT ? kImplicit2MC : kImplicit2; }
+Mode pass1_mode(const pic_config &c) {
+    if (c.cell_width) return kImplicit1NU;
+    return c.scheme == PIC_MC_IMPLICIT ? kImplicit1MC : kImplicit1;
+}
+Mode pass2_mode(const pic_config &c) {
+    if (c.cell_width) return kImplicit2NU;
+    return c.scheme == PIC_MC_IMPLICIT ? kImplicit2MC : kImplicit2;
+}
 
 // Enqueue one step (and the sort that closes a sort cycle) on stream s.
 int enqueue_step(pic_handle *h, long long step_index, cudaStream_t s) {

@@ -43,6 +43,8 @@ enum Mode : int {
     kExplicitEC3 = 8,  // explicit EC with m = 3: S_3 assignment, S_2 interpolation
     kDepositEC3 = 9,
     kExplicitNU = 10,  // explicit EC on a non-uniform grid (cell widths h_c)
+    kImplicit1NU = 11, // direct implicit pass 1 on a non-uniform grid
+    kImplicit2NU = 12, // direct implicit pass 2 on a non-uniform grid
 };
 
 // The cell word of a particle.  A hole left by an absorbed particle is -1.
@@ -147,6 +149,7 @@ struct Run {
     float dt_dx;           // dt / dx
     float half_dt;         // dt / 2
     float half_dt2_dx;     // dt^2 / (2 dx)
+    float half_dt2;        // dt^2 / 2 (the corrector's move on a non-uniform grid)
     float qw[2];           // q w: power per particle per (V/m * m/s)
     float half_m_over_e[2];// 0.5 m / e: energy [eV] per (m/s)^2
     // collisions (FP32)

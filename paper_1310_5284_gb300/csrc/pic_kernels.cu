@@ -769,10 +769,11 @@ __device__ SmemMain carve_main(unsigned char *base, int n, int bins, bool ec3, c
 
 template <int MODE>
 struct ModeInfo {
-    static constexpr bool pass1 = (MODE == kImplicit1 || MODE == kImplicit1MC);
-    static constexpr bool pass2 = (MODE == kImplicit2 || MODE == kImplicit2MC);
+    static constexpr bool pass1 = (MODE == kImplicit1 || MODE == kImplicit1MC || MODE == kImplicit1NU);
+    static constexpr bool pass2 = (MODE == kImplicit2 || MODE == kImplicit2MC || MODE == kImplicit2NU);
     static constexpr bool ec3 = (MODE == kExplicitEC3 || MODE == kDepositEC3);
-    static constexpr bool nu = (MODE == kExplicitNU);  // non-uniform grid
+    // non-uniform grid
+    static constexpr bool nu = (MODE == kExplicitNU || MODE == kImplicit1NU || MODE == kImplicit2NU);
     static constexpr bool deposit = (MODE == kDepositEC || MODE == kDepositMC || MODE == kDepositEC3);
     static constexpr bool push = !(deposit || pass1);
     static constexpr bool needs_field = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kExplicitEC3 ||
@@ -851,6 +852,29 @@ __device__ __forceinline__ void walk_nu(const float2 *hw, int N, bool periodic, 
         c = -1;  // past the left electrode
     }
     s = 0.0f;
+}
+
+// A move by d metres on the non-uniform grid from (c, s), hc = (h_c, 1/h_c):
+// d / h_c of the cell while it stays inside; into the next cell over (the
+// common crossing) from the two widths; further by the walk.
+__device__ __forceinline__ void move_nu(const float2 *hw, int N, bool periodic, float len, int &c, float &s,
+                                        float d, float2 hc) {
+    const float off = s;
+    s = fmaf(d, hc.y, off);
+    if (s >= 0.0f && s < 1.0f) return;
+    const bool right = s >= 1.0f;
+    const int cn = right ? c + 1 : c - 1;
+    if (cn >= 0 && cn < N) {
+        const float hn_inv = hw[cn].y;
+        const float t = right ? (s - 1.0f) * hc.x * hn_inv : fmaf(s * hc.x, hn_inv, 1.0f);
+        if (t >= 0.0f && t < 1.0f) {
+            c = cn;
+            s = t;
+            return;
+        }
+    }
+    s = off;  // further: walk
+    walk_nu(hw, N, periodic, len, c, s, d);
 }
 
 // EC force interpolation, Eq. (3) with m = 2: S_1 from the cell-centred field
@@ -967,60 +991,56 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
     if (MI::implicit) {
         // predictor: v~ = v + dt abar / 2, x~ = x + dt v~
         const float vt = fmaf(R.half_dt, abar, vx);
-        s = fmaf(vt, R.dt_dx, off);
-        if (!(fabsf(s) < 1.0e6f)) s = (float)(2 * N + 2);  // runaway: lands outside
-        renormalise(c, s);
         bool inside = true;
-        if (R.periodic) {
-            if (c < 0 || c >= N) c = ((c % N) + N) % N;
-        } else if (c < 0 || c >= N) {
-            inside = false;
+        if (MI::nu) {
+            // non-uniform grid: through the physical position (wraps in the
+            // periodic box; c = -1 / N past an electrode)
+            s = off;
+            move_nu(sm.hw, N, R.periodic != 0, R.len_f, c, s, vt * R.dt_f, sm.hw[c0]);
+            inside = c >= 0 && c < N;
+        } else {
+            s = fmaf(vt, R.dt_dx, off);
+            if (!(fabsf(s) < 1.0e6f)) s = (float)(2 * N + 2);  // runaway: lands outside
+            renormalise(c, s);
+            if (R.periodic) {
+                if (c < 0 || c >= N) c = ((c % N) + N) % N;
+            } else if (c < 0 || c >= N) {
+                inside = false;
+            }
         }
         if (MI::pass1) {
             if (!inside) return -1;  // Reading: nothing assigned beyond an electrode
             return MI::mc ? deposit_key_s1(c, s, a_out) : deposit_key_s2(c, s, a_out);
         }
         // corrector with E^{n+1} at x~ (S_1 from the cell-centred field, or
-        // linear from the node field of the momentum-conserving scheme)
-        e_field = !inside ? 0.0f : (MI::mc ? (1.0f - s) * sm.e[c] + s * sm.e[c + 1] : gather_ec(sm.e, c, s));
+        // linear from the node field of the momentum-conserving scheme; on a
+        // non-uniform grid the voltage drops over x~'s own cell width)
+        if (MI::nu) {
+            e_field = !inside ? 0.0f : gather_ec(sm.e, c, s) * sm.hw[c].y;
+        } else {
+            e_field = !inside ? 0.0f
+                              : (MI::mc ? (1.0f - s) * sm.e[c] + s * sm.e[c + 1] : gather_ec(sm.e, c, s));
+        }
         const float acc = k.qm * e_field;
         v_new = fmaf(R.half_dt, acc, vt);
-        s = fmaf(acc, R.half_dt2_dx, s);
+        if (!MI::nu) s = fmaf(acc, R.half_dt2_dx, s);
         abar = 0.5f * (abar + acc);
         // Reading: the step changes v by dt abar^n, so the work done on the
         // particle is that of the field (m/q) abar^n, not of E^{n+1}
         e_field = abar * k.mq;
-        if (diag && inside) atomicAdd(&sm.heat[c], k.qw * e_field * 0.5f * (v_old + v_new));
+        if (diag && inside) atomicAdd(&sm.heat[c], k.qw * e_field * 0.5f * (v_old + v_new));  // x~'s cell
+        if (MI::nu && inside) move_nu(sm.hw, N, R.periodic != 0, R.len_f, c, s, acc * R.half_dt2, sm.hw[c]);
     } else if (MI::nu) {
         // non-uniform grid: the table holds the cells' voltage drops; the
         // force is their S_1 interpolation over the particle's own cell
-        // width (the x-derivative of its potential energy), and the move is
-        // d / h_c of the cell unless it leaves the cell
+        // width (the x-derivative of its potential energy), and the move of
+        // v dt goes through the physical position
         const float2 hc = sm.hw[c0];
         e_field = gather_ec(sm.e, c0, off) * hc.y;
         v_new = fmaf(k.qm_dt, e_field, vx);
         if (diag) atomicAdd(&sm.heat[c0], k.qw * e_field * 0.5f * (v_old + v_new));
-        const float d = v_new * R.dt_f;
-        s = fmaf(d, hc.y, off);
-        if (!(s >= 0.0f && s < 1.0f)) {
-            // into the next cell over (the common crossing), else the walk
-            const bool right = s >= 1.0f;
-            const int cn = right ? c0 + 1 : c0 - 1;
-            bool done = false;
-            if (cn >= 0 && cn < N) {
-                const float hn_inv = sm.hw[cn].y;
-                const float t = right ? (s - 1.0f) * hc.x * hn_inv : fmaf(s * hc.x, hn_inv, 1.0f);
-                if (t >= 0.0f && t < 1.0f) {
-                    c = cn;
-                    s = t;
-                    done = true;
-                }
-            }
-            if (!done) {  // further: walk
-                s = off;
-                walk_nu(sm.hw, N, R.periodic != 0, R.len_f, c, s, d);
-            }
-        }
+        s = off;
+        move_nu(sm.hw, N, R.periodic != 0, R.len_f, c, s, v_new * R.dt_f, hc);
     } else {
         // explicit leapfrog with E^n at x^n (Sec. 2 schemes (1), (2))
         e_field = MI::mc ? (1.0f - off) * sm.e[c0] + off * sm.e[c0 + 1]
@@ -2060,6 +2080,8 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
             }
         }
     }
+    // the direct-implicit passes on a non-uniform grid
+    constexpr bool nu_implicit = MODE == kImplicit1NU || MODE == kImplicit2NU;
     if (implicit) {
         for (int c = threadIdx.x; c < n; c += kThreads) {
             double chi;
@@ -2071,6 +2093,8 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
                       ldexp(R.chi_coef[1], -18) * (double)(node_charge_s1(R, K, 1, c) + node_charge_s1(R, K, 1, r));
             } else {
                 chi = R.chi_coef[0] * (double)chi_count(R, K, 0, c) + R.chi_coef[1] * (double)chi_count(R, K, 1, c);
+                // non-uniform grid: the count over the cell's own width
+                if constexpr (nu_implicit) chi *= R.dx / R.h64[c];
             }
             if (!dry) R.chi[c] = chi;
             rinv[c] = 1.0 / (1.0 + chi);
@@ -2112,34 +2136,48 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
             }
             if (c < n) {
                 P += (R.periodic || c >= 1) ? q[c] : 0ll;
-                const double qbar = R.periodic ? (double)totP / (double)n : 0.0;
-                const double v = R.periodic ? R.kappa * ((double)P - (double)(c + 1) * qbar)
-                                            : R.kappa * (double)P + R.kappa_bg * (double)c;
-                pp[c] = v;
-                s1 += rinv[c] * v;
-                s0 += rinv[c];
+                double v;
+                if constexpr (nu_implicit) {
+                    // non-uniform grid: the periodic box's net charge spread by
+                    // node lengths, and sum_c h_c E_c = V weighting each cell
+                    const float2 w = R.wdw[c];
+                    v = R.periodic ? R.kappa * ((double)P - (double)totP * ((double)w.x + (double)w.y))
+                                   : R.kappa * (double)P;
+                    pp[c] = v;
+                    s1 += R.h64[c] * rinv[c] * v;
+                    s0 += R.h64[c] * rinv[c];
+                } else {
+                    const double qbar = R.periodic ? (double)totP / (double)n : 0.0;
+                    v = R.periodic ? R.kappa * ((double)P - (double)(c + 1) * qbar)
+                                   : R.kappa * (double)P + R.kappa_bg * (double)c;
+                    pp[c] = v;
+                    s1 += rinv[c] * v;
+                    s0 += rinv[c];
+                }
             }
         }
         s1 = block_sum_lean(s1, sc_d);
         s0 = block_sum_lean(s0, sc_d);
         const double v_left = s_vl.v;
-        const double d0 = R.periodic ? -s1 / s0 : (v_left / R.dx - s1) / s0;
+        const double d0 = R.periodic ? -s1 / s0 : ((nu_implicit ? v_left : v_left / R.dx) - s1) / s0;
         double wsum = 0.0;
         for (int k = 0; k < per; ++k) {
             const int c = c_begin + k;
             if (c < n) {
                 const double e = rinv[c] * (d0 + pp[c]);
-                pp[c] = e;  // now the face field
-                wsum += e * e;
+                // now the face field (a non-uniform grid's gather table: the
+                // cell's voltage drop)
+                pp[c] = nu_implicit ? e * R.h64[c] : e;
+                wsum += nu_implicit ? e * e * R.h64[c] : e * e;
                 if (dry) continue;
                 R.e_cc[c] = e;
                 if (accumulate) atomicAdd(&R.avg_e[c], e);
-                if (!mc) R.e_gather[c + 1] = (float)e;
+                if (!mc) R.e_gather[c + 1] = (float)pp[c];
             }
         }
         wsum = block_sum_lean(wsum, sc_d);  // includes the barrier that publishes pp[]
         if (threadIdx.x == 0 && !dry) {
-            st->field_energy = R.eps0_dx_half * wsum;
+            st->field_energy = (nu_implicit ? R.eps0_half : R.eps0_dx_half) * wsum;
             if (ModeInfo<MODE>::pass1) st->field_energy_push = st->field_energy;
             st->v_left = v_left;
             if (accumulate) st->v_sum += v_left;
@@ -3104,6 +3142,7 @@ __global__ void k_set_abar(Run R) {
                 const int j = cell + (off >= 0.5f ? 1 : 0);
                 const float w1 = off >= 0.5f ? off - 0.5f : off + 0.5f;
                 e = (1.0f - w1) * R.e_gather[j] + w1 * R.e_gather[j + 1];
+                if (R.stretched) e *= R.hw[cell].y;  // voltage drops over the cell width
             }
             sp.abar[i] = R.qm[S] * e;
         }
@@ -3457,6 +3496,8 @@ cudaError_t launch_particles(const Run &r, Mode m, int grid, cudaStream_t s) {
         case kExplicitEC3: return launch_mode<kExplicitEC3>(r, grid, s);
         case kDepositEC3: return launch_mode<kDepositEC3>(r, grid, s);
         case kExplicitNU: return launch_mode<kExplicitNU>(r, grid, s);
+        case kImplicit1NU: return launch_mode<kImplicit1NU>(r, grid, s);
+        case kImplicit2NU: return launch_mode<kImplicit2NU>(r, grid, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -3492,7 +3533,7 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    for (int k = 0; k < 11; ++k) {  // raise the shared-memory limit of every mode
+    for (int k = 0; k < 13; ++k) {  // raise the shared-memory limit of every mode
         int dummy = 0;
         switch (k) {
             case 0: e = occ<kExplicitEC>(r, &dummy); break;
@@ -3505,7 +3546,9 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
             case 7: e = occ<kImplicit2MC>(r, &dummy); break;
             case 8: e = occ<kExplicitEC3>(r, &dummy); break;
             case 9: e = occ<kDepositEC3>(r, &dummy); break;
-            default: e = occ<kExplicitNU>(r, &dummy); break;
+            case 10: e = occ<kExplicitNU>(r, &dummy); break;
+            case 11: e = occ<kImplicit1NU>(r, &dummy); break;
+            default: e = occ<kImplicit2NU>(r, &dummy); break;
         }
         if (e != cudaSuccess) return e;
     }
@@ -3521,6 +3564,8 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
         case kExplicitEC3: e = occ<kExplicitEC3>(r, &per); break;
         case kDepositEC3: e = occ<kDepositEC3>(r, &per); break;
         case kExplicitNU: e = occ<kExplicitNU>(r, &per); break;
+        case kImplicit1NU: e = occ<kImplicit1NU>(r, &per); break;
+        case kImplicit2NU: e = occ<kImplicit2NU>(r, &per); break;
     }
     if (e != cudaSuccess) return e;
     *grid = sms * (per > 0 ? per : 1);

@@ -16,6 +16,10 @@ exact (an integer test on the same Philox words).
 A collision's outcome or an absorption decided on a float within rounding
 of its threshold may differ between FP32 and FP64 for a handful of the
 4.1 M particles: those tallies and the particle sets may differ by a few.
+On a stretched grid the force jumps at a node by the ratio of the two cell
+widths, so a particle that FP32 and FP64 put on either side of a node is
+such a decision too: there the per-particle maxima hold for all but the
+few particles furthest apart.
 """
 import numpy as np
 import pytest
@@ -58,8 +62,10 @@ CASES = [
     # the production explicit workload on a stretched grid (cells 0.5x the
     # uniform width at the electrodes, 1.5x mid-gap; Sec. 4's multi-scale grid)
     ("ccp_512cells_2048000ppsp_stretched", "ec_explicit", 5),
+    ("ccp_128cells_implicit_stretched", "ec_implicit", 3),
 ]
-BASES = {c["name"]: c for c in (workloads.CFG_WIDE_EXPLICIT, workloads.CFG_IMPLICIT, workloads.CFG_WIDE_STRETCHED)}
+BASES = {c["name"]: c for c in (workloads.CFG_WIDE_EXPLICIT, workloads.CFG_IMPLICIT, workloads.CFG_WIDE_STRETCHED,
+                                 workloads.CFG_IMPLICIT_STRETCHED)}
 
 
 @pytest.mark.parametrize("name,scheme,steps", CASES, ids=["%s-%s" % (c[0], c[1]) for c in CASES])
@@ -136,8 +142,13 @@ def test_full_size_load_charge_and_steps_match_oracle(name, scheme, steps):
         f = floor[k]
         assert np.quantile(dxi, 0.99) <= max(1e-5 * L, f["x99"]), (sp, scheme, np.quantile(dxi, 0.99), f)
         assert np.quantile(dv, 0.99) <= max(1e-5, f["v99"]), (sp, scheme, np.quantile(dv, 0.99), f)
-        assert dxi.max() <= max(1e-5 * L, f["xmax"]), (sp, scheme, dxi.max(), f)
-        assert dv.max() <= max(1e-5, f["vmax"]), (sp, scheme, dv.max(), f)
+        skip = FEW if cfg.get("cell_width") is not None else 0  # node decisions on a stretched grid
+        xmax = np.sort(dxi)[-1 - skip] if len(dxi) > skip else 0.0
+        vmax = np.sort(dv)[-1 - skip] if len(dv) > skip else 0.0
+        assert xmax <= max(1e-5 * L, f["xmax"]), (sp, scheme, xmax, f)
+        assert vmax <= max(1e-5, f["vmax"]), (sp, scheme, vmax, f)
+        print("full size %s %s %s: x max %.3g, v max %.3g (all but %d), beyond the floor: %d / %d" % (
+            name, scheme, sp, xmax, vmax, skip, int(np.sum(dv > max(1e-5, f["vmax"]))), len(dv)))
         # kinetic energy: implied by the per-particle bar, plus the few
         # particles whose threshold decisions differ
         assert abs(dg["ke_x"][k] - do["ke_x"][k]) <= (ke_bar(1e-5, f) + 1e-5) * abs(do["ke_x"][k])

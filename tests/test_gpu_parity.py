@@ -348,7 +348,8 @@ def one_step_diagnostics(gpu, cfg, eedf_tol=None):
         errs["e_cc_of_scale"] = _of_scale(g1["e_cc"], o1["e_cc"])
         errs["phi_of_scale"] = _of_scale(g1["phi"], o1["phi"])
         assert np.abs(o1["chi"]).max() > 0
-        w_tol = 8.8541878128e-12 * der["dx"] * (np.abs(o1["e_cc"]).sum() * e_tol + 0.5 * len(o1["e_cc"]) * e_tol ** 2)
+        hmax = float(np.max(cfg["cell_width"])) if cfg.get("cell_width") is not None else der["dx"]
+        w_tol = 8.8541878128e-12 * hmax * (np.abs(o1["e_cc"]).sum() * e_tol + 0.5 * len(o1["e_cc"]) * e_tol ** 2)
         assert abs(dg["field_energy"] - do["field_energy"]) <= w_tol + 1e-9 * abs(do["field_energy"])
         errs["field_energy"] = _rel(dg["field_energy"], do["field_energy"])
     diag_step = cfg.get("diag_period", 0) > 0 and d0["step"] % cfg["diag_period"] == 0
@@ -505,6 +506,9 @@ STEP_CASES = [
     # the largest grid the library takes: the width table beside the largest
     # accumulators in shared memory
     ("nu_1024_cells_b07", dict(n_cells=1024, np_init=40_000, mcc=False, grid_beta=0.7), 10, 30),
+    ("nu_implicit_electrodes_b06", dict(n_cells=64, mcc=False, scheme="ec_implicit", dt=8e-10, grid_beta=0.6), 5, 30),
+    ("nu_implicit_periodic_b05", dict(n_cells=50, periodic=True, mcc=False, rf_volt=0.0, scheme="ec_implicit",
+                                      dt=8e-10, grid_beta=0.5), 10, 100),
 ]
 
 
@@ -565,6 +569,9 @@ IMPLICIT_GRID_CASES = [
     ("ec_implicit_periodic_50", dict(n_cells=50, periodic=True, rf_volt=0.0, scheme="ec_implicit", dt=8e-10)),
     ("mc_implicit_electrodes_45", dict(n_cells=45, scheme="mc_implicit", dt=3e-10)),
     ("mc_implicit_periodic_33", dict(n_cells=33, periodic=True, rf_volt=0.0, scheme="mc_implicit", dt=8e-10)),
+    ("nu_implicit_electrodes_64_b06", dict(n_cells=64, scheme="ec_implicit", dt=8e-10, grid_beta=0.6)),
+    ("nu_implicit_periodic_50_b05", dict(n_cells=50, periodic=True, rf_volt=0.0, scheme="ec_implicit", dt=8e-10,
+                                         grid_beta=0.5)),
 ]
 
 
@@ -578,6 +585,7 @@ def test_implicit_susceptibility_and_modified_poisson_grid(name, over):
     predictor's quantisation decisions)."""
     cfg = dict(workloads.CFG_SMALL_CCP, np_init=12_800, sort_period=4, diag_period=1, eedf_bins=30)
     cfg.update(over)
+    cfg = with_grid(cfg)
     n = cfg["np_init"]
     gpu = gpu_sim(cfg)
     orc = oracle.Sim(cfg)
@@ -604,6 +612,7 @@ COLLISION_CASES = [
     ("ec_implicit", dict(iz_split="opal", scattering="vahedi_surendra", te_ev=10.0)),
     ("ec_explicit", dict(grid_beta=0.6)),  # non-uniform grid
     ("ec_explicit", dict(grid_beta=0.5, periodic=True, rf_volt=0.0)),  # non-uniform periodic box
+    ("ec_implicit", dict(grid_beta=0.6)),  # direct implicit on a non-uniform grid
 ]
 
 

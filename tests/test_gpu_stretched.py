@@ -63,18 +63,22 @@ def test_stretched_grid_conserves_energy_like_the_oracle():
     assert dev_g <= 2.0 * dev_o + 1e-3
 
 
-def test_stretched_discharge_steps_cleanly_with_sheaths():
-    """The stretched production discharge (cells 0.5x the uniform width at
-    the electrodes, 1.5x mid-gap) with a quarter of its particles, for two RF
-    periods: clean status, every particle accounted for by the walls and the
-    births, electrons depleted next to both electrodes (the sheaths) and the
-    bulk density within a factor 2 of the load density."""
+@pytest.mark.parametrize("scheme", ["ec_explicit", "ec_implicit"])
+def test_stretched_discharge_steps_cleanly_with_sheaths(scheme):
+    """The stretched production discharges (cells 0.5x the uniform width at
+    the electrodes, 1.5x mid-gap; explicit at 512 cells, direct implicit at
+    128 cells and omega_p dt = 2) with a quarter of their particles, for two
+    RF periods: clean status, every particle accounted for by the walls and
+    the births, electrons depleted next to both electrodes (the sheaths) and
+    the bulk density within a factor 2 of the load density."""
     from paper_1310_5284_gb300.sim import Sim
-    cfg = dict(workloads.CFG_WIDE_STRETCHED, np_init=512_000)
+    base = workloads.CFG_WIDE_STRETCHED if scheme == "ec_explicit" else workloads.CFG_IMPLICIT_STRETCHED
+    cfg = dict(base, np_init=base["np_init"] // 4)
+    period = int(round(1.0 / (cfg["rf_freq"] * cfg["dt"])))
     gpu = Sim(cfg, device="cuda:0")
-    gpu.step(3000)  # one RF period
+    gpu.step(period)
     gpu.diag(reset_avg=True)
-    gpu.step(3000)
+    gpu.step(period)
     d = gpu.diag()
     assert gpu.status() == 0
     for k in range(2):

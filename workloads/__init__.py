@@ -124,6 +124,8 @@ def with_stretch(cfg: dict, beta: float, name: str | None = None) -> dict:
 # The production explicit discharge on a stretched grid: cells 0.5x the
 # uniform width at the electrodes and 1.5x in the bulk.
 CFG_WIDE_STRETCHED = with_stretch(CFG_WIDE_EXPLICIT, 0.5, name="ccp_512cells_2048000ppsp_stretched")
+# The direct-implicit workload on the same kind of grid.
+CFG_IMPLICIT_STRETCHED = with_stretch(CFG_IMPLICIT, 0.5, name="ccp_128cells_implicit_stretched")
 
 
 # Collisionless periodic plasma with mobile ions on a stretched grid (the

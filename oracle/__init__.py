@@ -145,6 +145,8 @@ def lib():
         L.orc_solve_periodic_h.argtypes = [ctypes.c_int, _d, _d, _d, _d]
         L.orc_gather_ec_h.argtypes = [_P(Params), _d, ctypes.c_double]
         L.orc_gather_ec_h.restype = ctypes.c_double
+        L.orc_gather_ec3_h.argtypes = [_P(Params), _d, ctypes.c_double]
+        L.orc_gather_ec3_h.restype = ctypes.c_double
         L.orc_rotate.argtypes = [_d, ctypes.c_double, ctypes.c_double, _d]
         L.orc_vs_cos_chi.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_vs_cos_chi.restype = ctypes.c_double
@@ -427,6 +429,14 @@ def gather_ec_h(cfg, u_cc, xi) -> float:
     return float(lib().orc_gather_ec_h(ctypes.byref(p), _ptr(u, ctypes.c_double), float(xi)))
 
 
+def gather_ec3_h(cfg, u_cc, xi) -> float:
+    """m = 3: field [V/m] at cell coordinate xi on the non-uniform grid of
+    cfg from the cells' voltage drops."""
+    p = params(cfg)
+    u = np.ascontiguousarray(u_cc, np.float64)
+    return float(lib().orc_gather_ec3_h(ctypes.byref(p), _ptr(u, ctypes.c_double), float(xi)))
+
+
 def rotate(d, cos_chi, phi) -> np.ndarray:
     dd = np.ascontiguousarray(d, dtype=np.float64)
     out = np.zeros(3)
@@ -445,9 +455,9 @@ class Sim:
         cap_e = cap_e if cap_e is not None else max(1024, int(npi * cfg.get("cap_factor", 2.0)))
         cap_i = cap_i if cap_i is not None else cap_e
         if cfg.get("cell_width") is not None and (
-                cfg.get("scheme", "ec_explicit") not in ("ec_explicit", "ec_implicit")
+                cfg.get("scheme", "ec_explicit") not in ("ec_explicit", "ec_implicit", "ec3_explicit")
                 or not cfg.get("ions_mobile", True)):
-            raise ValueError("the non-uniform grid takes the EC schemes with m = 2 and mobile ions")
+            raise ValueError("the non-uniform grid takes the EC schemes and mobile ions")
         self._h = lib().orc_sim_create(ctypes.byref(self.p), int(cap_e), int(cap_i))
         if not self._h:
             raise MemoryError("oracle allocation failed")

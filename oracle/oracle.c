@@ -568,6 +568,15 @@ double orc_gather_ec_h(const orc_params *p, const double *u_cc, double xi)
     return orc_gather_ec(p, u_cc, xi) / p->cell_width[c];
 }
 
+/* m = 3: U = q sum_g phi_g S_3(xi - g) has the x-derivative
+   -(q / h_c) sum_c (phi_c - phi_{c+1}) S_2(xi - c - 1/2): Eq. (3)'s S_2
+   interpolation of the voltage drops over the particle's own cell width. */
+double orc_gather_ec3_h(const orc_params *p, const double *u_cc, double xi)
+{
+    int64_t c = (int64_t)floor(xi);
+    return orc_gather_ec3(p, u_cc, xi) / p->cell_width[c];
+}
+
 /* ------------------------------------------------------------------------- */
 /* Scattering geometry: turn the unit vector d by polar angle chi and azimuth */
 /* phi.  The azimuth is measured in the basis e1 = d(theta)/dtheta,           */
@@ -697,9 +706,10 @@ orc_sim *orc_sim_create(const orc_params *p, int64_t cap_e, int64_t cap_i)
     s->avg_phi = (double *)calloc((size_t)nn, sizeof(double));
     s->eedf = (int64_t *)calloc((size_t)(p->eedf_bins + 1), sizeof(int64_t));
     if (p->cell_width) {
-        /* the EC schemes with m = 2 (explicit and direct implicit) and mobile
-           ions are the ones defined on it */
-        if ((p->scheme != ORC_EC_EXPLICIT && p->scheme != ORC_EC_IMPLICIT) || !p->ions_mobile) {
+        /* the EC schemes (explicit with m = 2 or 3, direct implicit) with
+           mobile ions are the ones defined on it */
+        if ((p->scheme != ORC_EC_EXPLICIT && p->scheme != ORC_EC_IMPLICIT && p->scheme != ORC_EC3_EXPLICIT) ||
+            !p->ions_mobile) {
             orc_sim_free(s);
             return NULL;
         }
@@ -856,7 +866,9 @@ static void solve_field(orc_sim *s, const double *chi, int64_t level)
 
 static double gather(const orc_sim *s, double xi)
 {
-    if (s->h) return orc_gather_ec_h(&s->p, s->u_cc, xi);
+    if (s->h)
+        return s->p.scheme == ORC_EC3_EXPLICIT ? orc_gather_ec3_h(&s->p, s->u_cc, xi)
+                                               : orc_gather_ec_h(&s->p, s->u_cc, xi);
     if (is_mc(&s->p)) return orc_gather_mc(&s->p, s->e_node, xi);
     if (s->p.scheme == ORC_EC3_EXPLICIT) return orc_gather_ec3(&s->p, s->e_cc, xi);
     return orc_gather_ec(&s->p, s->e_cc, xi);

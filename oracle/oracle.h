@@ -64,9 +64,9 @@ typedef struct orc_params {
     /* Non-uniform grid, the multi-scale grid Sec. 4 proposes: the widths [m]
        of the n_cells cells, summing to `length`; NULL for the uniform grid of
        width length / n_cells.  Positions stay in cell units (cell index plus
-       the fraction of that cell's width); the EC schemes with m = 2 (explicit
-       and direct implicit) with mobile ions are the ones defined on it
-       (orc_sim_create refuses others). */
+       the fraction of that cell's width); the EC schemes (explicit with m = 2
+       or 3, direct implicit) with mobile ions are the ones defined on it
+       (orc_sim_create refuses the momentum-conserving ones). */
     const double *cell_width;
 } orc_params;
 enum { ORC_IZ_OPAL = 1, ORC_SCATTER_VS = 2 };
@@ -154,6 +154,9 @@ void orc_solve_periodic_h(int n_cells, const double *h, const double *q_node, co
 /* Field at the particle [V/m] from the voltage drops u[c] = phi_c - phi_{c+1}
    of the cells (ghost cells 0 beyond the walls, wrapped in a periodic box). */
 double orc_gather_ec_h(const orc_params *p, const double *u_cc, double xi);
+/* The same for m = 3: S_2 interpolation of the voltage drops from the three
+   nearest cell centres over the particle's own cell width. */
+double orc_gather_ec3_h(const orc_params *p, const double *u_cc, double xi);
 
 /* Isotropic scattering rotation used by the collision routines (exposed for tests). */
 void orc_rotate(const double d[3], double cos_chi, double phi, double out[3]);

@@ -80,22 +80,25 @@ def test_periodic_solve_spreads_the_net_charge_by_node_length():
     assert np.allclose(phi[:n], exact[:n], rtol=1e-11, atol=1e-11 * np.abs(exact).max())
 
 
-def _potential_energy(c, phi, xn, h, x):
-    """q = 1: U(x) = sum_g phi_g S_2(xi(x) - g), ghost nodes folded or wrapped."""
+def _potential_energy(c, phi, xn, h, x, m=2):
+    """q = 1: U(x) = sum_g phi_g S_m(xi(x) - g), ghost nodes folded or wrapped."""
     w, cell, off = oracle.locate(h, xn, x)
     assert w == 0
-    return float(oracle.deposit_s2_fp64(c, [cell + off]) @ phi)
+    dep = oracle.deposit_s2_fp64 if m == 2 else oracle.deposit_s3_fp64
+    return float(dep(c, [cell + off]) @ phi)
 
 
-@pytest.mark.parametrize("periodic", [False, True])
-def test_force_is_minus_gradient_of_the_assigned_potential_energy(periodic):
+@pytest.mark.parametrize("periodic,m", [(False, 2), (True, 2), (False, 3), (True, 3)])
+def test_force_is_minus_gradient_of_the_assigned_potential_energy(periodic, m):
     """The gathered field is -dU/dx for a unit charge, by central differences
-    in the physical coordinate, on a grid whose cells differ by up to 5x."""
+    in the physical coordinate, on a grid whose cells differ by up to 5x
+    (m = 2: S_2 assignment, S_1 interpolation; m = 3: S_3 and S_2)."""
     n, length = 12, 0.012
     h = widths(n, length, 0.65)
     xn = oracle.grid_nodes(h)
     c = dict(n_cells=n, periodic=periodic, length=length, dt=1e-10, n0=1.0, np_init=1.0,
-             scheme="ec_explicit", cell_width=h)
+             scheme="ec_explicit" if m == 2 else "ec3_explicit", cell_width=h)
+    gather = oracle.gather_ec_h if m == 2 else oracle.gather_ec3_h
     rng = np.random.default_rng(3)
     phi = rng.normal(size=n + 1) * 10.0
     if periodic:
@@ -107,8 +110,8 @@ def test_force_is_minus_gradient_of_the_assigned_potential_energy(periodic):
         w, cell, off = oracle.locate(h, xn, x)
         if min(off, 1.0 - off) * h[cell] < 10 * d:  # the map's kinks at the nodes
             continue
-        grad = -(_potential_energy(c, phi, xn, h, x + d) - _potential_energy(c, phi, xn, h, x - d)) / (2 * d)
-        assert oracle.gather_ec_h(c, u, cell + off) == pytest.approx(grad, rel=1e-6, abs=1e-6 * np.abs(u).max() / h.min())
+        grad = -(_potential_energy(c, phi, xn, h, x + d, m) - _potential_energy(c, phi, xn, h, x - d, m)) / (2 * d)
+        assert gather(c, u, cell + off) == pytest.approx(grad, rel=1e-6, abs=1e-6 * np.abs(u).max() / h.min())
         tested += 1
     assert tested > 150
 
@@ -165,10 +168,11 @@ def test_free_streaming_is_absorbed_at_the_electrodes():
     assert sim.count(0) == 0 and d["wall_count"][0] == [1, 1]
 
 
-def test_equal_widths_reproduce_the_uniform_scheme():
+@pytest.mark.parametrize("scheme", ["ec_explicit", "ec3_explicit"])
+def test_equal_widths_reproduce_the_uniform_scheme(scheme):
     """cell_width = L/N everywhere is the uniform grid: the same run (MCC
     off, FP64 weights) through both code paths for 30 steps."""
-    base = dict(workloads.CFG_SMALL_CCP, mcc=False, quantized=False)
+    base = dict(workloads.CFG_SMALL_CCP, mcc=False, quantized=False, scheme=scheme)
     n, length = base["n_cells"], base["length"]
     stretched = dict(base, cell_width=[length / n] * n)
     vth = math.sqrt(E * 2.0 / ME)
@@ -212,7 +216,7 @@ def test_uniform_load_gives_the_load_density_at_every_node():
 
 
 def test_other_schemes_are_refused_on_a_non_uniform_grid():
-    for scheme in ("mc_explicit", "mc_implicit", "ec3_explicit"):
+    for scheme in ("mc_explicit", "mc_implicit"):
         with pytest.raises(ValueError):
             oracle.Sim(dict(workloads.cfg_periodic_stretched(), scheme=scheme))
     with pytest.raises(ValueError):
@@ -318,14 +322,14 @@ def test_implicit_on_stretched_cells_follows_the_uniform_grid():
     assert np.max(np.abs(st - uni)) < 0.05
 
 
-def _thermal(wdt, steps, beta=0.5):
+def _thermal(wdt, steps, beta=0.5, scheme="ec_explicit"):
     n0, te = 1e15, 2.0
     lam = math.sqrt(EPS0 * te / (n0 * E))
     n_cells, ppc = 64, 64
     wp = math.sqrt(n0 * E * E / (EPS0 * ME))
     c = workloads.cfg_periodic_stretched(n_cells=n_cells, np_sp=n_cells * ppc, n0=n0,
                                          length=n_cells * 10 * lam, dt=wdt / wp, te_ev=te, beta=beta)
-    c["quantized"] = False
+    c.update(quantized=False, scheme=scheme)
     sim = oracle.Sim(c).load(n_cells * ppc, n_cells * ppc)
     sim.step(1)
     tot = [sim.energy()]
@@ -335,12 +339,13 @@ def _thermal(wdt, steps, beta=0.5):
     return np.array(tot)
 
 
-def test_stretched_grid_conserves_energy_with_second_order_error():
+@pytest.mark.parametrize("scheme", ["ec_explicit", "ec3_explicit"])
+def test_stretched_grid_conserves_energy_with_second_order_error(scheme):
     """Mean dx = 10 lambda_D, cells from 5 to 15 lambda_D, 1000 / omega_p:
     total energy within 1% at omega_p dt = 0.1 and the error grows as dt^2
-    (ratio 4 for a doubled step), as on the uniform grid."""
-    tot2 = _thermal(0.2, 5000)
-    tot1 = _thermal(0.1, 10000)
+    (ratio 4 for a doubled step), as on the uniform grid (m = 2 and 3)."""
+    tot2 = _thermal(0.2, 5000, scheme=scheme)
+    tot1 = _thermal(0.1, 10000, scheme=scheme)
     dev2 = np.max(np.abs(tot2 / tot2[0] - 1.0))
     dev1 = np.max(np.abs(tot1 / tot1[0] - 1.0))
     assert dev1 < 0.01

@@ -142,8 +142,10 @@ int validate(const pic_config *c) {
         return fail(PIC_EINVAL, "bad collision parameters");
     if (c->sort_period < 0 || c->diag_period < 0) return fail(PIC_EINVAL, "negative period");
     if (c->cell_width) {
-        if ((c->scheme != PIC_EC_EXPLICIT && c->scheme != PIC_EC_IMPLICIT) || !c->ions_mobile)
-            return fail(PIC_EINVAL, "a non-uniform grid takes PIC_EC_EXPLICIT or PIC_EC_IMPLICIT with mobile ions");
+        if ((c->scheme != PIC_EC_EXPLICIT && c->scheme != PIC_EC_IMPLICIT && c->scheme != PIC_EC3_EXPLICIT) ||
+            !c->ions_mobile)
+            return fail(PIC_EINVAL, "a non-uniform grid takes the EC schemes (PIC_EC_EXPLICIT, PIC_EC_IMPLICIT, "
+                                    "PIC_EC3_EXPLICIT) with mobile ions");
         double sum = 0.0;
         for (int k = 0; k < c->n_cells; ++k) {
             const double w = c->cell_width[k];
@@ -413,7 +415,7 @@ void grid_tables(const pic_config &c, std::vector<float2> &hw, std::vector<doubl
 
 Mode push_mode(const pic_config &c) {
     if (c.cell_width && c.scheme == PIC_EC_EXPLICIT) return kExplicitNU;
-    if (c.scheme == PIC_EC3_EXPLICIT) return kExplicitEC3;
+    if (c.scheme == PIC_EC3_EXPLICIT) return c.cell_width ? kExplicitEC3NU : kExplicitEC3;
     return c.scheme == PIC_MC_EXPLICIT ? kExplicitMC : kExplicitEC;
 }
 Mode deposit_mode(const pic_config &c) {

@@ -45,6 +45,7 @@ enum Mode : int {
     kExplicitNU = 10,  // explicit EC on a non-uniform grid (cell widths h_c)
     kImplicit1NU = 11, // direct implicit pass 1 on a non-uniform grid
     kImplicit2NU = 12, // direct implicit pass 2 on a non-uniform grid
+    kExplicitEC3NU = 13, // explicit EC with m = 3 on a non-uniform grid
 };
 
 // The cell word of a particle.  A hole left by an absorbed particle is -1.

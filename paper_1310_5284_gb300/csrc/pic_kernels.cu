@@ -771,20 +771,21 @@ template <int MODE>
 struct ModeInfo {
     static constexpr bool pass1 = (MODE == kImplicit1 || MODE == kImplicit1MC || MODE == kImplicit1NU);
     static constexpr bool pass2 = (MODE == kImplicit2 || MODE == kImplicit2MC || MODE == kImplicit2NU);
-    static constexpr bool ec3 = (MODE == kExplicitEC3 || MODE == kDepositEC3);
+    static constexpr bool ec3 = (MODE == kExplicitEC3 || MODE == kDepositEC3 || MODE == kExplicitEC3NU);
     // non-uniform grid
-    static constexpr bool nu = (MODE == kExplicitNU || MODE == kImplicit1NU || MODE == kImplicit2NU);
+    static constexpr bool nu = (MODE == kExplicitNU || MODE == kImplicit1NU || MODE == kImplicit2NU ||
+                                MODE == kExplicitEC3NU);
     static constexpr bool deposit = (MODE == kDepositEC || MODE == kDepositMC || MODE == kDepositEC3);
     static constexpr bool push = !(deposit || pass1);
     static constexpr bool needs_field = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kExplicitEC3 ||
-                                         MODE == kExplicitNU || pass2);
+                                         MODE == kExplicitNU || MODE == kExplicitEC3NU || pass2);
     static constexpr bool implicit = pass1 || pass2;
     static constexpr bool count_only = pass2;
     static constexpr bool mc = (MODE == kExplicitMC || MODE == kDepositMC || MODE == kImplicit1MC ||
                                 MODE == kImplicit2MC);
     static constexpr bool loads_v = !deposit;
     static constexpr bool explicit_push = (MODE == kExplicitEC || MODE == kExplicitMC || MODE == kExplicitEC3 ||
-                                           MODE == kExplicitNU);
+                                           MODE == kExplicitNU || MODE == kExplicitEC3NU);
 };
 
 // Renormalise an offset that left [0, 1) into the cell index.
@@ -1036,7 +1037,7 @@ __device__ __forceinline__ int step_particle(const Run &R, const SmemMain &sm, c
         // width (the x-derivative of its potential energy), and the move of
         // v dt goes through the physical position
         const float2 hc = sm.hw[c0];
-        e_field = gather_ec(sm.e, c0, off) * hc.y;
+        e_field = (MI::ec3 ? gather_ec3(sm.e, c0, off) : gather_ec(sm.e, c0, off)) * hc.y;
         v_new = fmaf(k.qm_dt, e_field, vx);
         if (diag) atomicAdd(&sm.heat[c0], k.qw * e_field * 0.5f * (v_old + v_new));
         s = off;
@@ -2049,7 +2050,7 @@ __device__ void tail_field(const Run &R, Keys K, unsigned char *smem, long long 
     if (threadIdx.x == 0) s_vl = vl_ok ? vl : electrode_volt(R, level);
     // the modes that run on a non-uniform grid (the others never see one, and
     // their tails carry none of its code)
-    constexpr bool nu_capable = MODE == kExplicitNU || MODE == kDepositEC;
+    constexpr bool nu_capable = MODE == kExplicitNU || MODE == kDepositEC || MODE == kExplicitEC3NU || MODE == kDepositEC3;
     const bool acc_now = accumulate && (implicit || !defer);
     // node charges, densities, susceptibility (pointers and scalars held in
     // registers: the stores below cannot alias them)
@@ -2871,7 +2872,8 @@ __device__ void stream_block(const Run &R, const SmemMain &sm, const Ring &g, co
 // The m = 3 modes hold three blocks per SM (their shared memory), so they
 // may use the registers of three.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, (MODE == kExplicitEC3 || MODE == kDepositEC3) ? 3 : kMinBlocks)
+__global__ void __launch_bounds__(kThreads,
+                                  (MODE == kExplicitEC3 || MODE == kDepositEC3 || MODE == kExplicitEC3NU) ? 3 : kMinBlocks)
     k_particles(Run R) {
     extern __shared__ __align__(128) unsigned char smem_all[];
     __shared__ bool s_last;
@@ -2928,7 +2930,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == kExplicitEC3 || MODE == kDe
     {
         const unsigned int pend = st->pending;
         if (pend && blockIdx.x < kDeferParts)
-            deferred_work<MI::nu || MODE == kDepositEC>(R, pend, (int)blockIdx.x, kDeferParts);
+            deferred_work<MI::nu || MODE == kDepositEC || MODE == kDepositEC3>(R, pend, (int)blockIdx.x, kDeferParts);
     }
     // The electrode voltage of the field the tail solves: FP64 is slow here,
     // so one thread of one block (past the deferring ones) computes it while
@@ -3498,6 +3500,7 @@ cudaError_t launch_particles(const Run &r, Mode m, int grid, cudaStream_t s) {
         case kExplicitNU: return launch_mode<kExplicitNU>(r, grid, s);
         case kImplicit1NU: return launch_mode<kImplicit1NU>(r, grid, s);
         case kImplicit2NU: return launch_mode<kImplicit2NU>(r, grid, s);
+        case kExplicitEC3NU: return launch_mode<kExplicitEC3NU>(r, grid, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -3533,7 +3536,7 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    for (int k = 0; k < 13; ++k) {  // raise the shared-memory limit of every mode
+    for (int k = 0; k < 14; ++k) {  // raise the shared-memory limit of every mode
         int dummy = 0;
         switch (k) {
             case 0: e = occ<kExplicitEC>(r, &dummy); break;
@@ -3548,7 +3551,8 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
             case 9: e = occ<kDepositEC3>(r, &dummy); break;
             case 10: e = occ<kExplicitNU>(r, &dummy); break;
             case 11: e = occ<kImplicit1NU>(r, &dummy); break;
-            default: e = occ<kImplicit2NU>(r, &dummy); break;
+            case 12: e = occ<kImplicit2NU>(r, &dummy); break;
+            default: e = occ<kExplicitEC3NU>(r, &dummy); break;
         }
         if (e != cudaSuccess) return e;
     }
@@ -3566,6 +3570,7 @@ cudaError_t occupancy_grid(const Run &r, Mode m, int *grid) {
         case kExplicitNU: e = occ<kExplicitNU>(r, &per); break;
         case kImplicit1NU: e = occ<kImplicit1NU>(r, &per); break;
         case kImplicit2NU: e = occ<kImplicit2NU>(r, &per); break;
+        case kExplicitEC3NU: e = occ<kExplicitEC3NU>(r, &per); break;
     }
     if (e != cudaSuccess) return e;
     *grid = sms * (per > 0 ? per : 1);

@@ -137,9 +137,9 @@ def test_set_state_rejects_null_arguments_before_any_device_work(abi):
 
 
 def test_non_uniform_grid_configs(abi):
-    """cell_width: positive widths summing to the gap, the EC schemes with
-    m = 2 (explicit, direct implicit) with mobile ions, single runs; the arena
-    grows by the grid's tables."""
+    """cell_width: positive widths summing to the gap, the EC schemes
+    (explicit with m = 2 or 3, direct implicit) with mobile ions, single runs;
+    the arena grows by the grid's tables."""
     from paper_1310_5284_gb300.sim import make_config
     base = dict(workloads.CFG_SMALL_CCP)
     s = abi.PicSizes()
@@ -157,9 +157,10 @@ def test_non_uniform_grid_configs(abi):
                 [length / n] * (n - 1) + [float("nan")]):
         c = make_config(dict(base, cell_width=bad))
         assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == -1
-    c = make_config(dict(good, scheme="ec_implicit"))
-    assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == 0
-    for over in (dict(scheme="mc_explicit"), dict(scheme="mc_implicit"), dict(scheme="ec3_explicit"),
+    for scheme in ("ec_implicit", "ec3_explicit"):
+        c = make_config(dict(good, scheme=scheme))
+        assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == 0, scheme
+    for over in (dict(scheme="mc_explicit"), dict(scheme="mc_implicit"),
                  dict(ions_mobile=False, mcc=False, bg_density=1e15)):
         c = make_config(dict(good, **over))
         assert abi.lib().pic_required_sizes(ctypes.byref(c), ctypes.byref(s)) == -1, over

@@ -441,6 +441,9 @@ DEPOSIT_CASES = [
     ("nu_periodic_100_b05", dict(n_cells=100, periodic=True, rf_volt=0.0, grid_beta=0.5), 10_007, False),
     ("nu_dirichlet_1024_sorted_b07", dict(n_cells=1024, grid_beta=0.7), 300_001, True),
     ("nu_tiny_2cells", dict(n_cells=2, cell_width=[0.006, 0.014]), 5, False),
+    ("nu_ec3_dirichlet_64_b06", dict(n_cells=64, scheme="ec3_explicit", grid_beta=0.6), 12_800, False),
+    ("nu_ec3_periodic_100_b05", dict(n_cells=100, periodic=True, rf_volt=0.0, scheme="ec3_explicit", grid_beta=0.5),
+     10_007, False),
 ]
 
 
@@ -509,6 +512,9 @@ STEP_CASES = [
     ("nu_implicit_electrodes_b06", dict(n_cells=64, mcc=False, scheme="ec_implicit", dt=8e-10, grid_beta=0.6), 5, 30),
     ("nu_implicit_periodic_b05", dict(n_cells=50, periodic=True, mcc=False, rf_volt=0.0, scheme="ec_implicit",
                                       dt=8e-10, grid_beta=0.5), 10, 100),
+    ("nu_ec3_electrodes_b06", dict(n_cells=64, mcc=False, scheme="ec3_explicit", grid_beta=0.6), 30, 100),
+    ("nu_ec3_periodic_b05", dict(n_cells=64, periodic=True, mcc=False, rf_volt=0.0, scheme="ec3_explicit",
+                                 grid_beta=0.5), 30, 100),
 ]
 
 
@@ -613,6 +619,7 @@ COLLISION_CASES = [
     ("ec_explicit", dict(grid_beta=0.6)),  # non-uniform grid
     ("ec_explicit", dict(grid_beta=0.5, periodic=True, rf_volt=0.0)),  # non-uniform periodic box
     ("ec_implicit", dict(grid_beta=0.6)),  # direct implicit on a non-uniform grid
+    ("ec3_explicit", dict(grid_beta=0.6)),  # m = 3 on a non-uniform grid
 ]
 
 

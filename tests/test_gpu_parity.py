@@ -140,6 +140,24 @@ def compare_particles(gpu, orc, cfg, tol=1e-5, species=("e", "i"), quantile=1.0,
 
 
 def fp32_sensitivity(cfg, states, steps, abar=None, factor=4.0, step0=0, next_ids=None, ulps=2):
+    """The oracle's FP32 sensitivity (fp32_sensitivity_once); on a
+    non-uniform grid the largest over two rounding realisations, since the
+    force jumps at the nodes make one realisation's divergence vary by up to
+    ten times from another's in chaotic cases."""
+    seeds = (12345, 777) if cfg.get("cell_width") is not None else (12345,)
+    runs = [fp32_sensitivity_once(cfg, states, steps, abar, factor, step0, next_ids, ulps, seed) for seed in seeds]
+    out = []
+    for k in range(len(runs[0])):
+        fs = [r[k] for r in runs]
+        if any(f is None for f in fs):
+            out.append(None)
+            continue
+        out.append({key: (all(f[key] for f in fs) if key == "same_set" else max(f[key] for f in fs))
+                    for key in fs[0]})
+    return out
+
+
+def fp32_sensitivity_once(cfg, states, steps, abar=None, factor=4.0, step0=0, next_ids=None, ulps=2, seed=12345):
     """How far the FP64 oracle drifts from itself when its particle state is
     put through the FP32 arithmetic of a device step after every step: the
     state is rounded to the storage form (cell + FP32 offset, FP32
@@ -169,7 +187,7 @@ def fp32_sensitivity(cfg, states, steps, abar=None, factor=4.0, step0=0, next_id
         s.init_field(set_abar=abar is None)
     births0 = rnd.diag()["births"]
     ref.step(steps)
-    rng = np.random.default_rng(12345)
+    rng = np.random.default_rng(seed)
 
     def f32(x):
         y = np.asarray(x, dtype=np.float32)

@@ -139,9 +139,9 @@ typedef struct pic_config {
        the sheaths without resolving the bulk: NULL for the uniform grid of
        width length / n_cells, else a host array of n_cells cell widths [m],
        each positive, summing to `length` within 1e-9 relative.  pic_init
-       copies it (the caller keeps ownership).  Taken by PIC_EC_EXPLICIT and
-       PIC_EC_IMPLICIT with mobile ions, in single runs (pic_batch_init
-       rejects it).  The
+       copies it (the caller keeps ownership).  Taken by the EC schemes
+       (PIC_EC_EXPLICIT, PIC_EC_IMPLICIT, PIC_EC3_EXPLICIT) with mobile ions,
+       in single runs (pic_batch_init rejects it).  The
        paper gives no form of Eq. (2)-(3) for unequal cells; this library's:
        a particle's position stays (cell, offset in [0, 1) of that cell's
        width); the charge assignment and the interpolation weights are those
@@ -154,7 +154,10 @@ typedef struct pic_config {
        Energy conservation (Sec. 2) carries over.  The direct-implicit
        scheme moves the predicted and corrected positions the same way, takes
        a cell's susceptibility from its S_1-weighted count over its own
-       width, and solves (1 + chi_c) E_c in the same Gauss law.  pic_profiles divides a
+       width, and solves (1 + chi_c) E_c in the same Gauss law.  With m = 3
+       the S_3 assignment and the S_2 interpolation of the voltage drops are
+       those of the uniform grid in the cell coordinate, the force again over
+       the particle's own cell width.  pic_profiles divides a
        node's charge by (h_{g-1} + h_g)/2, and the heating of a cell by its
        width. */
     const double *cell_width;
